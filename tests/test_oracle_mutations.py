@@ -1,0 +1,53 @@
+"""Plants plausible mistakes in a scratch copy of the oracle (on the CPU)
+and checks that the oracle pins catch every one of them."""
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+MUTATIONS = {
+    "drop_delta_in_dm1": ("m[13 + 3 * a + g] += Vj * (x[a] * dW[g] + (a == g ? W : 0.0));",
+                          "m[13 + 3 * a + g] += Vj * (x[a] * dW[g]);"),
+    "drop_B_term_in_corrected_gradient": ("Ai * (dBx + Bi[g]) * W;", "Ai * (dBx) * W;"),
+    "transposed_dB": ("double dBx = dBi[0 * 3 + g] * x[0] + dBi[1 * 3 + g] * x[1] + dBi[2 * 3 + g] * x[2];",
+                      "double dBx = dBi[g * 3 + 0] * x[0] + dBi[g * 3 + 1] * x[1] + dBi[g * 3 + 2] * x[2];"),
+    "dA_cross_term_factor": ("dA[3 * i + g] = -Ai * Ai * (dm0 + 2.0 * Bdm1 + BdmB);",
+                             "dA[3 * i + g] = -Ai * Ai * (dm0 + 1.0 * Bdm1 + BdmB);"),
+    "viscosity_of_j_uses_h_i": ("double Qj = orc_visc_Q(xji, vji, h[j], rho[j], c[j], p);",
+                                "double Qj = orc_visc_Q(xji, vji, h[i], rho[j], c[j], p);"),
+    "energy_rate_sign": ("du += -0.5 * (F[0]", "du += 0.5 * (F[0]"),
+    "split_factor_sign": ("return erfc(t) + r / (sqrt(ORC_PI) * r_s) * exp(-t * t);",
+                          "return erfc(t) - r / (sqrt(ORC_PI) * r_s) * exp(-t * t);"),
+    "kernel_normalisation": ("double norm = 495.0 / (32.0 * ORC_PI * H * H * H);",
+                             "double norm = 495.0 / (32.0 * ORC_PI * H * H * H) * 1.001;"),
+    "non_strict_predicate": ("return r2 < H * H;", "return r2 <= H * H;"),
+    "m2_packing_index": ("static const int ORC_SYM_B[6] = {0, 1, 2, 1, 2, 2};",
+                         "static const int ORC_SYM_B[6] = {0, 1, 2, 1, 1, 2};"),
+    "gravity_drops_softening": ("double s2 = r2 + e2;", "double s2 = r2;"),
+}
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(MUTATIONS))
+def test_pins_catch_planted_mistake(tmp_path, name):
+    before, after = MUTATIONS[name]
+    src = open(os.path.join(ROOT, "oracle", "crk_oracle.c")).read()
+    assert before in src, name
+    work = tmp_path / "tree"
+    shutil.copytree(os.path.join(ROOT, "oracle"), work / "oracle",
+                    ignore=shutil.ignore_patterns("_build", "__pycache__"))
+    shutil.copytree(os.path.join(ROOT, "tests"), work / "tests",
+                    ignore=shutil.ignore_patterns("__pycache__"))
+    os.makedirs(work / "paper_2510_03557_gb300")
+    for f in ("__init__.py", "workloads.py"):
+        shutil.copy(os.path.join(ROOT, "paper_2510_03557_gb300", f), work / "paper_2510_03557_gb300" / f)
+    shutil.copy(os.path.join(ROOT, "pytest.ini"), work / "pytest.ini")
+    (work / "oracle" / "crk_oracle.c").write_text(src.replace(before, after))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:randomly",
+                        "tests/test_oracle_pins.py"], cwd=work, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 1, f"mutation {name} survived:\n{r.stdout[-2000:]}"

@@ -1,0 +1,414 @@
+"""Pins of the CPU oracle against what the mathematics and the paper fix.
+
+None of these tests re-types the oracle's formulas: each checks a property
+that a dropped term, a wrong sign, a wrong index or a transposed operand
+would break (quadrature, finite differences, integer lattice counts,
+reproducing identities, conservation laws, antisymmetry, a textbook limit,
+an independent Gaussian-enclosed-mass integral, brute force).
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy import integrate
+
+from paper_2510_03557_gb300 import workloads as wl
+from tests.golden.figures import paper_figures
+
+
+def _params(oracle, box, **kw):
+    base = dict(box=box.L, G=box.G, gamma=box.gamma, r_cut=box.r_cut, r_split=box.r_split,
+                eps_soft=box.eps_soft)
+    base.update(kw)
+    return oracle.make_params(**base)
+
+
+# ---------------------------------------------------------------- kernel
+@pytest.mark.parametrize("h", [0.01, 0.3, 2.0])
+def test_kernel_normalisation_by_quadrature(oracle_lib, h):
+    """The 3-D kernel integrates to one over its support (Wendland C4 reading)."""
+    H = 2.0 * h
+    val, err = integrate.quad(lambda r: 4.0 * math.pi * r * r * oracle_lib.W(r, h), 0.0, H,
+                              epsabs=0, epsrel=1e-13, limit=200)
+    assert abs(val - 1.0) < 1e-12
+
+
+@pytest.mark.parametrize("h", [0.05, 1.0])
+def test_kernel_gradient_matches_finite_difference(oracle_lib, h):
+    H = 2.0 * h
+    for q in (0.01, 0.2, 0.5, 0.77, 0.95):
+        r = q * H
+        d = 1e-6 * H
+        fd = (oracle_lib.W(r + d, h) - oracle_lib.W(r - d, h)) / (2 * d)
+        # grad_i W = g(r) x_ij, so dW/dr = g(r) r
+        an = oracle_lib.gradW_factor(r, h) * r
+        assert abs(fd - an) <= 1e-7 * abs(an) + 1e-12
+
+
+def test_kernel_compact_support_and_smooth_edge(oracle_lib):
+    h = 0.5
+    assert oracle_lib.W(1.0, h) == 0.0 and oracle_lib.W(1.5, h) == 0.0
+    assert oracle_lib.gradW_factor(1.0, h) == 0.0
+    # (1-q)^6 edge: value and slope vanish continuously
+    assert oracle_lib.W(1.0 - 1e-4, h) < 1e-20
+    # finite, negative slope factor at the origin (analytic r -> 0 limit)
+    g0 = oracle_lib.gradW_factor(0.0, h)
+    assert np.isfinite(g0) and g0 < 0
+
+
+# ---------------------------------------------------------- neighbours
+def test_lattice_neighbour_count_is_integer_ball_count(oracle_lib):
+    """Perfect lattice, H = 4 spacings: every gas particle has exactly the
+    number of nonzero integer points with a^2 + b^2 + c^2 < 16 (strict)."""
+    box = wl.jittered_lattice(16, seed=0, jitter=0.0)
+    p = _params(oracle_lib, box)
+    r = np.arange(-4, 5)
+    a, b, c = np.meshgrid(r, r, r, indexing="ij")
+    d2 = a * a + b * b + c * c
+    expected = int(((d2 < 16) & (d2 > 0)).sum())
+    cnt, _ = oracle_lib.neighbours(box.pos, box.h, box.species, p, 0)
+    gas = box.species == wl.GAS
+    assert np.all(cnt[gas] == expected)
+    assert np.all(cnt[~gas] == 0)
+
+
+def test_mean_neighbour_count_matches_paper(oracle_lib):
+    """Uniformly random gas at the configs' density with h = 2 mean spacings
+    has (4/3) pi 4^3 = 268 neighbours on average, the paper's ~270."""
+    rng = np.random.default_rng(7)
+    n = 24
+    N = n ** 3
+    pos = rng.uniform(0, 1, size=(N, 3))
+    h = np.full(N, 2.0 / n)
+    sp = np.ones(N, np.uint8)
+    p = oracle_lib.make_params(box=1.0, r_cut=3.0 / n)
+    cnt, _ = oracle_lib.neighbours(pos, h, sp, p, 0)
+    expected = 4.0 / 3.0 * math.pi * 4.0 ** 3
+    assert abs(cnt.mean() - expected) < 3.0
+    paper = paper_figures()["neighbours_per_crksph_evaluation"]
+    assert abs(cnt.mean() - paper) / paper < 0.05
+
+
+def _numpy_brute_sets(pos, h, species, L, r_cut):
+    """Independent all-pairs neighbour sets with the same predicate."""
+    n = pos.shape[0]
+    d = pos[None, :, :] - pos[:, None, :]            # x_j - x_i
+    d = np.where(d >= 0.5 * L, d - L, d)
+    d = np.where(d < -0.5 * L, d + L, d)
+    r2 = (d[..., 0] * d[..., 0] + d[..., 1] * d[..., 1]) + d[..., 2] * d[..., 2]
+    H2 = (2.0 * h) ** 2
+    gas = species == wl.GAS
+    eye = np.eye(n, dtype=bool)
+    gather = (r2 < H2[:, None]) & gas[:, None] & gas[None, :] & ~eye
+    union = ((r2 < H2[:, None]) | (r2 < H2[None, :])) & gas[:, None] & gas[None, :] & ~eye
+    grav = (r2 < r_cut * r_cut) & ~eye
+    return gather, union, grav
+
+
+@pytest.mark.parametrize("brute", [False, True])
+def test_neighbour_sets_match_independent_brute_force(oracle_lib, brute):
+    rng = np.random.default_rng(11)
+    N = 1200
+    pos = rng.uniform(0, 1, size=(N, 3))
+    pos[:5] = [[0.0, 0.0, 0.0], [0.999999, 0.0, 0.5], [0.5, 0.0, 0.999], [0.02, 0.98, 0.01],
+               [np.nextafter(1.0, 0.0), 0.5, 0.5]]
+    sp = (rng.uniform(size=N) < 0.5).astype(np.uint8)
+    h = rng.uniform(0.03, 0.07, size=N)
+    r_cut = 0.11
+    p = oracle_lib.make_params(box=1.0, r_cut=r_cut, brute=brute)
+    sets = _numpy_brute_sets(pos, h, sp, 1.0, r_cut)
+    ids = wl.splitmix64(np.arange(N, dtype=np.uint64))
+    for kind, m in enumerate(sets):
+        cnt, hs = oracle_lib.neighbours(pos, h, sp, p, kind)
+        assert np.array_equal(cnt, m.sum(1).astype(np.int32))
+        with np.errstate(over="ignore"):
+            exp_hash = np.array([np.sum(ids[row], dtype=np.uint64) for row in m], dtype=np.uint64)
+        assert np.array_equal(hs, exp_hash)
+
+
+# --------------------------------------------------------------- density
+def test_lattice_density_equals_mean_density(oracle_lib):
+    """On a perfect lattice the kernel estimate of the density equals the
+    mean gas density (0.16 in a unit box) up to the small lattice error of
+    a normalised kernel with 250 neighbours."""
+    box = wl.jittered_lattice(16, seed=0, jitter=0.0)
+    p = _params(oracle_lib, box)
+    rho, V, P, c = oracle_lib.density(box.pos, box.mass, box.u, box.h, box.species, p)
+    gas = box.species == wl.GAS
+    assert np.allclose(rho[gas], 0.16, rtol=1e-3)
+    assert np.ptp(rho[gas]) < 1e-14
+    assert np.allclose(V[gas] * rho[gas], box.mass[gas], rtol=1e-14)
+    # ideal-gas closure: P = (gamma-1) rho u, c^2 = gamma P / rho
+    assert np.allclose(c[gas] ** 2, box.gamma * P[gas] / rho[gas], rtol=1e-13)
+    assert np.all(rho[~gas] == 0)
+
+
+# ----------------------------------------------------------- corrections
+def _clustered_small(seed=5, n_gas=700, n_dm=300):
+    rng = np.random.default_rng(seed)
+    g1 = rng.uniform(0, 1, size=(n_gas // 2, 3))
+    g2 = (0.5 + 0.06 * rng.standard_normal((n_gas - n_gas // 2, 3))) % 1.0
+    dm = rng.uniform(0, 1, size=(n_dm, 3))
+    pos = np.concatenate([g1, g2, dm])
+    sp = np.concatenate([np.ones(n_gas, np.uint8), np.zeros(n_dm, np.uint8)])
+    N = pos.shape[0]
+    mass = np.where(sp == 1, 1.0 / n_gas, 2.0 / n_dm)
+    # spatially varying h so neighbour sets are asymmetric
+    h = np.where(sp == 1, 0.15 + 0.03 * np.sin(6.0 * pos[:, 0]), 0.0)
+    u = np.where(sp == 1, np.exp(rng.normal(0, 0.5, size=N)), 0.0)
+    vel = 0.3 * rng.standard_normal((N, 3))
+    return dict(pos=pos, vel=vel, mass=mass, u=u, h=h, species=sp)
+
+
+@pytest.mark.parametrize("kind", ["lattice", "clustered"])
+def test_corrected_kernel_reproduces_constant_and_linear(oracle_lib, kind):
+    if kind == "lattice":
+        box = wl.jittered_lattice(12, seed=3)
+        s = dict(pos=box.pos, h=box.h, species=box.species, mass=box.mass, u=box.u)
+        p = _params(oracle_lib, box)
+    else:
+        s = _clustered_small()
+        p = oracle_lib.make_params(box=1.0, r_cut=0.1, r_split=0.02)
+    rho, V, P, c = oracle_lib.density(s["pos"], s["mass"], s["u"], s["h"], s["species"], p)
+    mom = oracle_lib.moments(s["pos"], V, s["h"], s["species"], p)
+    rc, bad, A, B, dA, dB = oracle_lib.corrections(mom, s["species"])
+    assert rc == 0
+    ident = oracle_lib.crk_identities(s["pos"], V, s["h"], s["species"], A, B, dA, dB, p)
+    gas = s["species"] == wl.GAS
+    I = ident[gas]
+    assert np.max(np.abs(I[:, 0] - 1.0)) < 1e-11                       # sum V W^R = 1
+    scale = np.max(s["h"])
+    assert np.max(np.abs(I[:, 1:4])) < 1e-11 * scale                   # sum V x W^R = 0
+    gscale = np.max(np.abs(ident[gas, 4:7])) + 1.0 / scale
+    assert np.max(np.abs(I[:, 4:7])) < 1e-10 * gscale                  # sum V dW^R = 0
+    G1 = I[:, 7:16].reshape(-1, 3, 3)
+    assert np.max(np.abs(G1 + np.eye(3)[None])) < 1e-10                # sum V x^b d_g W^R = -delta
+
+
+def test_correction_gradients_match_finite_differences(oracle_lib):
+    """dA and dB are the x_i-derivatives of A and B with the volumes V_j and
+    every x_j held fixed, the copy of i in its own sum included.  The finite
+    difference moves a zero-volume probe with h = h_i from x_i: at zero
+    offset its moments are exactly particle i's, and since V_probe = 0 it
+    contributes to no sum, so it sees every particle (i too) at rest."""
+    s = _clustered_small(seed=9, n_gas=500, n_dm=10)
+    p = oracle_lib.make_params(box=1.0, r_cut=0.1, r_split=0.02)
+    rho, V, P, c = oracle_lib.density(s["pos"], s["mass"], s["u"], s["h"], s["species"], p)
+    mom = oracle_lib.moments(s["pos"], V, s["h"], s["species"], p)
+    _, _, A, B, dA, dB = oracle_lib.corrections(mom, s["species"])
+    gas_idx = np.nonzero(s["species"] == wl.GAS)[0]
+    rng = np.random.default_rng(1)
+    sp2 = np.append(s["species"], np.uint8(wl.GAS))
+    V2 = np.append(V, 0.0)
+    for i in rng.choice(gas_idx, size=6, replace=False):
+        h2 = np.append(s["h"], s["h"][i])
+        # zero offset: the probe reproduces particle i's corrections
+        pos0 = np.vstack([s["pos"], s["pos"][i]])
+        m0 = oracle_lib.moments(pos0, V2, h2, sp2, p)
+        _, _, A0, B0, _, _ = oracle_lib.corrections(m0, sp2)
+        assert abs(A0[-1] - A[i]) <= 1e-13 * abs(A[i])
+        for g in range(3):
+            vals = []
+            for sgn in (+1, -1):
+                pos = pos0.copy()
+                pos[-1, g] += sgn * 1e-6
+                m = oracle_lib.moments(pos, V2, h2, sp2, p)
+                _, _, Ap, Bp, _, _ = oracle_lib.corrections(m, sp2)
+                vals.append((Ap[-1], Bp[-1].copy()))
+            fdA = (vals[0][0] - vals[1][0]) / 2e-6
+            fdB = (vals[0][1] - vals[1][1]) / 2e-6
+            assert abs(fdA - dA[i, g]) < 1e-6 * (abs(dA[i]).max() + 1.0)
+            assert np.max(np.abs(fdB - dB[i, :, g])) < 1e-6 * (np.abs(dB[i]).max() + 1.0)
+
+
+def test_singular_second_moment_is_reported(oracle_lib):
+    """All gas at one point: m2 = 0, reported instead of producing NaN."""
+    N = 40
+    pos = np.full((N, 3), 0.5)
+    sp = np.ones(N, np.uint8)
+    p = oracle_lib.make_params(box=1.0, r_cut=0.1)
+    out = oracle_lib.forces(pos, np.zeros((N, 3)), np.full(N, 1.0 / N), np.ones(N),
+                            np.full(N, 0.05), sp, p)
+    assert out["rc"] == oracle_lib.ORC_ESINGULAR
+    assert out["bad"] == 0
+
+
+# ----------------------------------------------------------------- hydro
+def test_hydro_pair_force_is_antisymmetric(oracle_lib):
+    s = _clustered_small(seed=2)
+    p = oracle_lib.make_params(box=1.0, r_cut=0.1, r_split=0.02, eps_soft=1e-3)
+    out = oracle_lib.forces(s["pos"], s["vel"], s["mass"], s["u"], s["h"], s["species"], p)
+    assert out["rc"] == 0
+    cnt, _ = oracle_lib.neighbours(s["pos"], s["h"], s["species"], p, 1)
+    gas_idx = np.nonzero(s["species"] == wl.GAS)[0]
+    pos = s["pos"]
+    checked = 0
+    for i in gas_idx[:40]:
+        d = pos - pos[i]
+        d = np.where(d >= 0.5, d - 1, d)
+        d = np.where(d < -0.5, d + 1, d)
+        r = np.sqrt((d ** 2).sum(1))
+        for j in np.nonzero((r < 2 * max(s["h"][i], 1e-9) * 1.2) & (np.arange(len(r)) != i))[0][:5]:
+            Fh_ij, Fg_ij = oracle_lib.pair_forces(out, p, int(i), int(j))
+            Fh_ji, Fg_ji = oracle_lib.pair_forces(out, p, int(j), int(i))
+            scale = np.abs(Fh_ij).max() + 1e-300
+            assert np.max(np.abs(Fh_ij + Fh_ji)) <= 1e-13 * scale
+            assert np.max(np.abs(Fg_ij + Fg_ji)) <= 1e-13 * (np.abs(Fg_ij).max() + 1e-300)
+            checked += 1
+    assert checked > 50
+
+
+def test_hydro_conserves_momentum_and_energy(oracle_lib):
+    s = _clustered_small(seed=4)
+    p = oracle_lib.make_params(box=1.0, r_cut=0.1, r_split=0.02)
+    rho, V, P, c = oracle_lib.density(s["pos"], s["mass"], s["u"], s["h"], s["species"], p)
+    mom = oracle_lib.moments(s["pos"], V, s["h"], s["species"], p)
+    _, _, A, B, dA, dB = oracle_lib.corrections(mom, s["species"])
+    acc, dudt = oracle_lib.hydro(s["pos"], s["vel"], s["mass"], s["h"], s["species"], rho, V, P, c,
+                                 A, B, dA, dB, p)
+    m = s["mass"]
+    ma = m[:, None] * acc
+    scale = np.abs(ma).sum()
+    assert np.max(np.abs(ma.sum(0))) < 1e-13 * scale
+    edot = (m[:, None] * s["vel"] * acc).sum() + (m * dudt).sum()
+    escale = np.abs(m[:, None] * s["vel"] * acc).sum() + np.abs(m * dudt).sum()
+    assert abs(edot) < 1e-13 * escale
+    # compression heats: the sum of m du/dt is not trivially zero
+    assert np.abs(m * dudt).sum() > 0
+
+
+def test_hydro_reduces_to_textbook_sph(oracle_lib):
+    """With A = 1, B = 0, dA = dB = 0 and no viscosity the pair force is
+    F_ij = -V_i V_j (P_i + P_j) grad_i W_ij for equal smoothing lengths."""
+    rng = np.random.default_rng(8)
+    N = 600
+    pos = rng.uniform(0, 1, size=(N, 3))
+    sp = np.ones(N, np.uint8)
+    h = np.full(N, 0.07)
+    mass = np.full(N, 1.0 / N)
+    u = np.exp(rng.normal(0, 0.3, size=N))
+    vel = rng.standard_normal((N, 3))
+    p = oracle_lib.make_params(box=1.0, r_cut=0.1, av_alpha=0.0, av_beta=0.0)
+    rho, V, P, c = oracle_lib.density(pos, mass, u, h, sp, p)
+    A = np.ones(N)
+    Z3 = np.zeros((N, 3))
+    acc, dudt = oracle_lib.hydro(pos, vel, mass, h, sp, rho, V, P, c, A, Z3, Z3,
+                                 np.zeros((N, 3, 3)), p)
+    d = pos[None, :, :] - pos[:, None, :]
+    d = np.where(d >= 0.5, d - 1, d)
+    d = np.where(d < -0.5, d + 1, d)
+    xij = -d
+    r = np.sqrt((d ** 2).sum(-1))
+    g = np.vectorize(lambda rr: oracle_lib.gradW_factor(rr, 0.07))(r)
+    g[np.eye(N, dtype=bool)] = 0.0
+    gradW = g[..., None] * xij
+    F = -(V[:, None] * V[None, :] * (P[:, None] + P[None, :]))[..., None] * gradW
+    a_ref = F.sum(1) / mass[:, None]
+    vij = vel[:, None, :] - vel[None, :, :]
+    du_ref = -0.5 * (F * vij).sum(-1).sum(1) / mass
+    assert np.max(np.abs(acc - a_ref)) < 1e-11 * np.abs(a_ref).max()
+    assert np.max(np.abs(dudt - du_ref)) < 1e-11 * np.abs(du_ref).max()
+
+
+def test_uniform_lattice_uniform_pressure_has_no_acceleration(oracle_lib):
+    box = wl.jittered_lattice(12, seed=0, jitter=0.0)
+    p = _params(oracle_lib, box, G=0.0)
+    out = oracle_lib.forces(box.pos, box.vel, box.mass, box.u, box.h, box.species, p)
+    gas = box.species == wl.GAS
+    assert out["rc"] == 0
+    typical = np.max(out["P"][gas] * out["V"][gas] / box.mass[gas]) / (2 * box.h[gas].max())
+    assert np.max(np.abs(out["acc"][gas])) < 1e-11 * typical
+    assert np.allclose(out["A"][gas], out["A"][gas][0], rtol=1e-12)
+    assert np.max(np.abs(out["B"][gas])) < 1e-10 / box.h[gas].max()
+
+
+# --------------------------------------------------------------- gravity
+def _gaussian_enclosed_fraction(r, r_s):
+    """Mass fraction of a 3-D Gaussian cloud (sigma = sqrt(2) r_s, the pair
+    convolution of two r_s Gaussians) inside radius r, by quadrature."""
+    sig = math.sqrt(2.0) * r_s
+    dens = lambda s: 4 * math.pi * s * s * math.exp(-s * s / (2 * sig * sig)) / ((2 * math.pi * sig * sig) ** 1.5)
+    return integrate.quad(dens, 0.0, r, epsabs=0, epsrel=1e-13, limit=200)[0]
+
+
+def test_split_factor_long_range_part_is_gaussian_enclosed_mass(oracle_lib):
+    r_s = 0.01
+    for r in (1e-4, 0.005, 0.01, 0.02, 0.045):
+        lr = 1.0 - oracle_lib.S(r, r_s)
+        assert abs(lr - _gaussian_enclosed_fraction(r, r_s)) < 1e-12
+    assert oracle_lib.S(0.0, r_s) == 1.0
+
+
+def test_gravity_equals_direct_sum_minus_long_range_part(oracle_lib):
+    """Tiny cluster, all pairs inside r_cut, no softening: the short-range
+    force equals direct Newtonian summation minus the long-range pair force
+    G m_i m_j x (1 - S)/r^3 of the Gaussian split, with 1 - S taken from the
+    independent enclosed-mass quadrature."""
+    rng = np.random.default_rng(3)
+    N = 48
+    pos = 0.5 + 0.01 * rng.standard_normal((N, 3))
+    mass = rng.uniform(0.5, 1.5, size=N) / N
+    sp = (np.arange(N) % 2).astype(np.uint8)
+    r_s = 0.01
+    p = oracle_lib.make_params(box=1.0, G=1.0, r_cut=0.2, r_split=r_s, eps_soft=0.0)
+    acc = oracle_lib.gravity(pos, mass, sp, p)
+    ref = np.zeros((N, 3))
+    for i in range(N):
+        for j in range(N):
+            if i == j:
+                continue
+            x = pos[i] - pos[j]
+            r = np.linalg.norm(x)
+            newton = -mass[j] * x / r ** 3
+            longr = -mass[j] * x * _gaussian_enclosed_fraction(r, r_s) / r ** 3
+            ref[i] += newton - longr
+    assert np.max(np.abs(acc - ref)) < 1e-11 * np.abs(ref).max()
+    ma = mass[:, None] * acc
+    assert np.max(np.abs(ma.sum(0))) < 1e-13 * np.abs(ma).sum()
+
+
+def test_gravity_is_newtonian_well_inside_split_scale(oracle_lib):
+    pos = np.array([[0.5, 0.5, 0.5], [0.5 + 1e-6, 0.5, 0.5]])
+    mass = np.array([1.0, 2.0])
+    p = oracle_lib.make_params(box=1.0, G=1.0, r_cut=0.1, r_split=0.01, eps_soft=0.0)
+    acc = oracle_lib.gravity(pos, mass, np.zeros(2, np.uint8), p)
+    assert abs(acc[0, 0] - 2.0 / 1e-12) / (2.0 / 1e-12) < 1e-6
+    assert abs(acc[1, 0] + 1.0 / 1e-12) / (1.0 / 1e-12) < 1e-6
+
+
+def test_gravity_softening_is_plummer_potential_gradient(oracle_lib):
+    """Far inside the split scale S = 1, and the softened pair force is minus
+    the gradient of the Plummer potential -G m / sqrt(r^2 + eps^2), taken here
+    by central finite differences of the potential."""
+    eps = 1e-3
+    m_j = 3.0
+    p = oracle_lib.make_params(box=1.0, G=1.0, r_cut=0.1, r_split=1.0, eps_soft=eps)
+    phi = lambda r: -m_j / math.sqrt(r * r + eps * eps)
+    for r in (2e-4, 1e-3, 3e-3):
+        pos = np.array([[0.5, 0.5, 0.5], [0.5 + r, 0.5, 0.5]])
+        acc = oracle_lib.gravity(pos, np.array([1.0, m_j]), np.zeros(2, np.uint8), p)
+        d = 1e-7
+        dphi = (phi(r + d) - phi(r - d)) / (2 * d)      # d phi / dr; force on 0 points to 1
+        assert abs(acc[0, 0] - dphi) < 1e-6 * abs(dphi) and acc[0, 0] > 0
+
+
+# ------------------------------------------------------------------- KDK
+def test_kdk_conserves_momentum(oracle_lib):
+    s = _clustered_small(seed=6, n_gas=400, n_dm=400)
+    p = oracle_lib.make_params(box=1.0, r_cut=0.1, r_split=0.02, eps_soft=1e-3)
+    m = s["mass"]
+    P0 = (m[:, None] * s["vel"]).sum(0)
+    out = oracle_lib.kdk(s["pos"], s["vel"], m, s["u"], s["h"], s["species"], p, 1e-4, 3)
+    P1 = (m[:, None] * out["vel"]).sum(0)
+    assert np.max(np.abs(P1 - P0)) < 1e-13 * np.abs(m[:, None] * s["vel"]).sum()
+    assert np.all(out["pos"] >= 0) and np.all(out["pos"] < 1)
+
+
+def test_sampled_outputs_equal_full_outputs(oracle_lib):
+    box = wl.jittered_lattice(10, seed=1)
+    p = _params(oracle_lib, box)
+    full = oracle_lib.forces(box.pos, box.vel, box.mass, box.u, box.h, box.species, p)
+    sample = np.array([0, 5, 999, 1000, 1500, 1999])
+    part = oracle_lib.forces(box.pos, box.vel, box.mass, box.u, box.h, box.species, p, sample=sample)
+    for k in ("acc", "dudt", "rho", "A", "B", "dA", "dB"):
+        assert np.array_equal(full[k][sample], part[k][sample]), k
