@@ -1,0 +1,319 @@
+"""Benchmark: particles/s per CRKSPH + short-range-gravity step.
+
+One step = one pass of the whole hot path on one batch of particles: first
+half kick and drift, Morton keys, radix sort, permutation, leaves, leaf
+hierarchy, leaf-pair lists, density, moments + corrections, hydro, gravity,
+second half kick.  Workload: the 2 x 128^3 Gaussian-random-field box
+(P(k) ~ k^-2, 0.3-cell rms displacement, ~270 gas neighbours), FP32-mixed
+form, inputs resident in HBM (about 2.5 GB of state, far larger than L2).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs its own independent box (weak
+scaling, no collective on the data path); the barrier and the max over
+ranks only bracket the timing.  Rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particles/s per CRKSPH+SR-gravity step, mixed vs FP64; serve p50/p99 ms"
+UNIT = "particles/s"
+
+# Algorithmic FP32 operations of one in-range pair, counted from the kernels'
+# pair bodies in csrc/passes.cu with the paper's convention (Sec. VI-B: FMA =
+# 2, add/mul = 1, sqrt/rsqrt/exp/reciprocal = 1).  Pairs outside the support
+# (leaf-pair overlap) are not counted.
+FLOP_PER_PAIR = {"density": 22, "moments": 125, "hydro": 183, "gravity": 41}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def fp32_peak_tflops(sm_mhz: float) -> float:
+    """152 SMs x 128 FP32 lanes x 2 flop (FMA) x SM clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is None:
+            self.samples = []
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        self.samples = [l.split(",") for l in out.strip().splitlines() if l.count(",") >= 8]
+
+    def summary(self):
+        if not getattr(self, "samples", None):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[1]) for s in self.samples if s[1].strip().replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = []
+        for k, name in enumerate(names):
+            if any(s[5 + k].strip().lower() == "active" for s in self.samples):
+                reasons.append(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+def cpu_baseline(n: int = 80):
+    """The CPU oracle as it stands, on a bounded sample of the same workload:
+    one force evaluation plus one KDK step of a 2 x n^3 box from the same
+    generator (same density, neighbour counts and h in spacing units)."""
+    import oracle
+    from paper_2510_03557_gb300 import workloads as wl
+
+    oracle.build()
+    box = wl.gaussian_field_box(n, seed=1)
+    op = oracle.make_params(**box.params())
+    t0 = time.perf_counter()
+    ref = oracle.forces(box.pos, box.vel, box.mass, box.u, box.h, box.species, op)
+    t1 = time.perf_counter()
+    oracle.kdk(box.pos, box.vel, box.mass, box.u, box.h, box.species, op, box.dt, 1,
+               acc=ref["acc"], dudt=ref["dudt"])
+    t2 = time.perf_counter()
+    step_s = t2 - t1  # one KDK step = one force evaluation plus kicks and drift
+    return {"value": box.n / step_s, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "sample": f"one KDK step of a 2x{n}^3 box from the same generator (N={box.n}), "
+                      f"force evaluation {t1 - t0:.2f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    steps = []
+    cb = None
+    for _ in range(args.warmup):
+        cpu_baseline(40)
+    for _ in range(args.steps):
+        cb = cpu_baseline(40)
+        steps.append(cb["value"])
+    value = statistics.median(steps)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "gaussian-field 2x40^3 sample of the 2x128^3 workload"},
+            "cpu_baseline": dict(cb, value=value),
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=128, help="lattice size per species (2 n^3 particles)")
+    ap.add_argument("--leaf-cap", type=int, default=64)
+    ap.add_argument("--fp64-steps", type=int, default=2)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v: float) -> float:
+        if dist is None:
+            return v
+        t = torch.tensor([v], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    from paper_2510_03557_gb300 import crk
+    from paper_2510_03557_gb300 import workloads as wl
+
+    crk.lib()
+    box = wl.gaussian_field_box(args.n, seed=1)
+    N = box.n
+    dt = box.dt
+    phys = crk.box_physics(box)
+    stream = torch.cuda.Stream()
+
+    # ---------------- mixed form, device-resident (the headline value)
+    sim = crk.Sim(phys, leaf_cap=args.leaf_cap, precision=crk.CRK_MIXED, stream=stream)
+    sim.load(box)
+    counts = sim.forces(counts=True)      # untimed: the true pair counts for the roofline
+    gas = box.species == wl.GAS
+    pairs = {"density": int(counts["nbr_count"][gas].sum()) + int(gas.sum()),
+             "moments": int(counts["nbr_count"][gas].sum()) + int(gas.sum()),
+             "hydro": int(counts["nbr_count"][gas].sum()),
+             "gravity": int(counts["grav_count"].sum())}
+    for _ in range(args.warmup):
+        sim.step(dt, 1)
+    crk.crk_set_timing(sim.handle, True)
+    barrier()
+    with ClockSampler(local) as clocks:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(dt, args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    t_max = max_over_ranks(ms)
+    tim = crk.crk_get_timings(sim.handle)
+    value = world * N * args.steps / (t_max / 1e3)
+    per_pass_ms = {"density": tim["density_ms"], "moments": tim["moments_ms"],
+                   "hydro": tim["hydro_ms"], "gravity": tim["gravity_ms"]}
+    calls = max(tim["calls"], 1)
+    dom = max(per_pass_ms, key=per_pass_ms.get)
+    dom_ms = per_pass_ms[dom] / calls
+    clk = clocks.summary()
+    peaks, peak_kind = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = fp32_peak_tflops(sm_max)
+    achieved = pairs[dom] * FLOP_PER_PAIR[dom] / (dom_ms / 1e3) / 1e12
+    pass_tflops = {k: pairs[k] * FLOP_PER_PAIR[k] / (per_pass_ms[k] / calls / 1e3) / 1e12
+                   for k in per_pass_ms}
+    breakdown = {k: round(v / calls, 4) for k, v in
+                 (("tree_ms", tim["tree_ms"]), ("pairs_ms", tim["pairs_ms"]),
+                  ("density_ms", tim["density_ms"]), ("moments_ms", tim["moments_ms"]),
+                  ("hydro_ms", tim["hydro_ms"]), ("gravity_ms", tim["gravity_ms"]),
+                  ("kdk_ms", tim["kdk_ms"]))}
+    launches = int(tim["launches"])
+    sim.close()
+
+    # ---------------- FP64 plain form on the same box
+    fp64 = None
+    if args.fp64_steps > 0:
+        s64 = crk.Sim(phys, leaf_cap=args.leaf_cap, precision=crk.CRK_FP64, stream=stream)
+        s64.load(box)
+        s64.step(dt, 1)
+        barrier()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        s64.step(dt, args.fp64_steps)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        t64 = max_over_ranks(f0.elapsed_time(f1))
+        fp64 = {"value": world * N * args.fp64_steps / (t64 / 1e3), "unit": UNIT,
+                "ms_per_step": t64 / args.fp64_steps, "steps": args.fp64_steps, "dtype": "f64"}
+        s64.close()
+
+    # ---------------- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        se = crk.Sim(phys, leaf_cap=args.leaf_cap, precision=crk.CRK_MIXED, stream=stream)
+        se.load(box)
+        se.step(dt, 1)
+        pin = lambda shape: torch.empty(shape, dtype=torch.float64).pin_memory().numpy()
+        hp, hv, hu = pin((N, 3)), pin((N, 3)), pin(N)
+        crk.crk_get_state(se.handle, hp, hv, hu)
+        k_e2e = max(2, min(args.steps, 5))
+        barrier()
+        t0 = time.perf_counter()
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for _ in range(k_e2e):
+            crk.crk_set_state(se.handle, hp, hv, hu)     # H2D of the step's inputs
+            crk.crk_step(se.handle, dt, 1)
+            crk.crk_get_state(se.handle, hp, hv, hu)     # D2H of the step's result
+        g1.record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        te = max_over_ranks(max(g0.elapsed_time(g1), wall * 1e3))
+        e2e = {"value": world * N * k_e2e / (te / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(hp.nbytes + hv.nbytes + hu.nbytes),
+               "d2h_bytes_per_step": int(hp.nbytes + hv.nbytes + hu.nbytes), "steps": k_e2e}
+        se.close()
+
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cb = cpu_baseline()
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"gaussian-field 2x{args.n}^3, FP32-mixed, KDK dt={dt}",
+                       "particles": N, "leaf_cap": args.leaf_cap, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (~2.5 GB resident state)"},
+            "roofline": {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3),
+                         "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
+                         "traffic": None,
+                         "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
+                                        f"({peak_kind} sm_max_mhz)"},
+            "pass_tflops": {k: round(v, 3) for k, v in pass_tflops.items()},
+            "pairs_per_step": pairs,
+            "breakdown_ms": breakdown,
+            "fp64_plain": fp64,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "cpu_baseline": cb,
+        }
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

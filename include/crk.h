@@ -1,0 +1,253 @@
+/*
+ * crk.h -- C ABI of libcrk, a single-GPU (GB300, sm_103a) implementation of
+ * the short-range particle-particle solver of CRK-HACC (arXiv 2510.03557):
+ * base leaves of a spatial tree (Sec. IV-B1), leaf-pair interaction lists
+ * (Sec. IV-B1), the CRKSPH passes (Sec. IV-A: density, kernel moments, the
+ * linear reproducing-kernel corrections A and B with their gradients, the
+ * pairwise-antisymmetric momentum and energy rates with artificial
+ * viscosity) and the short-range gravity pair force of the long/short-range
+ * split (Sec. IV-A), evaluated as the pair sums of Eq. 1-2, plus a fixed-step
+ * kick-drift-kick integrator.
+ *
+ * Conventions shared by every call:
+ *   - Return codes: CRK_OK (0) or a negative CRK_E* code; crk_last_error()
+ *     then holds a thread-local message.
+ *   - Arrays are in the caller's particle order.  Vectors are AoS: particle i
+ *     owns pos[3i .. 3i+2].  Tensors: gradA[3i+g] = d A_i / d x^g,
+ *     gradB[9i + 3a + g] = d B_i^a / d x^g.
+ *   - `mem` selects where every pointer of a call lives: CRK_MEM_HOST or
+ *     CRK_MEM_DEVICE (CUDA device memory of the current device).
+ *   - Inputs are copied into library-owned device memory; outputs go to
+ *     caller-owned buffers.  Handles are opaque and freed by *_destroy only.
+ *   - All GPU work of a crk_sim is ordered on the stream given at creation.
+ *     Calls on one crk_sim are not thread-safe; the service calls are.
+ *   - Species: CRK_DM particles get gravity only (du/dt = 0, A = B = 0);
+ *     CRK_GAS particles get hydro and gravity.
+ *   - Positions must lie in [0, L) of their box; max(2 h_max, r_cut) < L/2.
+ */
+#ifndef CRK_H
+#define CRK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes */
+#define CRK_OK 0
+#define CRK_EINVAL (-1)     /* bad argument, size or precondition */
+#define CRK_ENOMEM (-2)     /* device or host allocation failed */
+#define CRK_ECUDA (-3)      /* a CUDA runtime call failed */
+#define CRK_EOVERFLOW (-4)  /* a leaf or pair-list capacity limit was exceeded */
+#define CRK_ESINGULAR (-5)  /* the second-moment matrix m2 of a gas particle is not invertible */
+#define CRK_EPENDING (-6)   /* crk_poll: the job has not finished yet */
+#define CRK_ETIMEOUT (-7)   /* a bounded wait ran out */
+#define CRK_ENOTFOUND (-8)  /* crk_poll: unknown or already collected ticket */
+
+/* Precision of the pair passes */
+#define CRK_FP64 0          /* every operation in FP64 (the plain form) */
+#define CRK_MIXED 1         /* FP32 pair arithmetic on leaf-relative coordinates and FP32
+                               accumulation; FP64 masters, drift, 3x3 solve, global sums */
+
+#define CRK_WENDLAND_C4 0   /* smoothing kernel, support H = 2h */
+
+#define CRK_MEM_HOST 0
+#define CRK_MEM_DEVICE 1
+
+#define CRK_DM 0
+#define CRK_GAS 1
+
+/* Physics of one periodic box (paper Sec. IV-A; constants are inputs). */
+typedef struct {
+    double box;        /* periodic side L */
+    double G;          /* gravitational constant */
+    double gamma;      /* adiabatic index of the ideal-gas closure P = (gamma-1) rho u */
+    double r_cut;      /* short-range gravity cut-off radius */
+    double r_split;    /* Gaussian long/short split scale r_s */
+    double eps_soft;   /* Plummer softening length */
+    double av_alpha;   /* Monaghan viscosity alpha */
+    double av_beta;    /* Monaghan viscosity beta */
+    double av_eps2;    /* viscosity regulariser epsilon^2 */
+    double u_floor;    /* floor on the gas specific thermal energy */
+} crk_physics;
+
+/* Simulation-wide settings. */
+typedef struct {
+    crk_physics phys;  /* physics for crk_load (crk_load_boxes passes its own per box) */
+    int kernel;        /* CRK_WENDLAND_C4 */
+    int leaf_cap;      /* leaf capacity C: 32, 64 or 128 particles */
+    int precision;     /* CRK_FP64 or CRK_MIXED */
+    int cm_level;      /* chaining-mesh Morton level b (2^b bins per side); 0 = automatic */
+    int flags;         /* reserved, 0 */
+    int reserved[3];
+} crk_params;
+
+/* Outputs of crk_forces.  Every pointer is optional (NULL skips it); all
+ * live where `mem` says.  Sizes in particles N of the loaded set. */
+typedef struct {
+    double *acc;          /* 3N: hydro + short-range gravity acceleration */
+    double *dudt;         /* N: du/dt (0 for DM) */
+    double *rho;          /* N: density (0 for DM) */
+    double *A;            /* N: CRK correction A (0 for DM) */
+    double *B;            /* 3N: CRK correction B */
+    double *gradA;        /* 3N */
+    double *gradB;        /* 9N */
+    int32_t *nbr_count;   /* N: size of the hydro gather set {gas j != i : r^2 < (2h_i)^2} */
+    uint64_t *nbr_hash;   /* N: sum over that set of splitmix64(original index of j), mod 2^64 */
+    int32_t *grav_count;  /* N: size of the gravity set {j != i : r^2 < r_cut^2} */
+    uint64_t *grav_hash;  /* N: hash of the gravity set as above */
+    int mem;              /* CRK_MEM_HOST or CRK_MEM_DEVICE for every pointer above */
+    int reserved;
+    double momentum_rate[3];  /* written: sum_i m_i a_i (FP64 reduction; ~0 by antisymmetry) */
+    double energy_rate;       /* written: sum_i m_i (v_i . a_i^hydro + du_i/dt) (~0) */
+} crk_outputs;
+
+/* Per-phase device times of the calls made while timing is on (CUDA events
+ * on the sim's stream), accumulated in milliseconds. */
+typedef struct {
+    double tree_ms;       /* keys, radix sort, permutation, leaves, bounding boxes (S1) */
+    double pairs_ms;      /* leaf hierarchy and leaf-pair lists (S2) */
+    double density_ms;    /* D (S3) */
+    double moments_ms;    /* M + C fused (S4, S5) */
+    double hydro_ms;      /* H (S6) */
+    double gravity_ms;    /* G (S7) */
+    double kdk_ms;        /* kick, drift, predictor, sums (S8) */
+    double total_ms;      /* whole calls */
+    int64_t calls;        /* force evaluations timed */
+    int64_t pairs_hydro;  /* leaf pairs in the last hydro list (ordered) */
+    int64_t pairs_grav;   /* leaf pairs in the last gravity list (ordered) */
+    int64_t nleaves;      /* leaves in the last tree */
+    int64_t launches;     /* CUDA kernels the library launched in the timed calls */
+} crk_timings;
+
+typedef struct crk_sim crk_sim;
+
+/* Creates a solver handle bound to the current CUDA device.
+ * cuda_stream: a cudaStream_t (NULL = the legacy default stream); every GPU
+ * operation of the handle is ordered on it.  Errors: CRK_EINVAL for an
+ * unsupported leaf_cap / precision / kernel, CRK_ECUDA, CRK_ENOMEM. */
+int crk_create(const crk_params *params, void *cuda_stream, crk_sim **out);
+
+/* Loads one periodic box of n particles with the physics of crk_create's
+ * params (copied; replaces any previous load).  pos/vel: 3n AoS; mass, u, h:
+ * n; species: n bytes, CRK_DM or CRK_GAS.  h is read for gas only.
+ * Errors: CRK_EINVAL (n < 0, a position outside [0, L), non-finite input,
+ * or max(2 h_max, r_cut) >= L/2), CRK_ENOMEM, CRK_ECUDA. */
+int crk_load(crk_sim *sim, int64_t n, const double *pos, const double *vel, const double *mass,
+             const double *u, const double *h, const uint8_t *species, int mem);
+
+/* Loads nbox independent periodic boxes back to back (the batched form):
+ * box b holds counts[b] consecutive particles of the arrays and has the
+ * physics phys[b].  Boxes never interact; one launch per pass covers all.
+ * counts and phys are host arrays.  Errors as crk_load. */
+int crk_load_boxes(crk_sim *sim, int nbox, const int64_t *counts, const crk_physics *phys,
+                   const double *pos, const double *vel, const double *mass, const double *u,
+                   const double *h, const uint8_t *species, int mem);
+
+/* One force evaluation at the current state: tree build, leaf-pair lists,
+ * density, moments, corrections, hydro and gravity, with the velocities and
+ * energies as loaded (or, after crk_step, the KDK predictor values).
+ * Writes the requested outputs in the caller's order.  Errors:
+ * CRK_ESINGULAR (message names the first particle), CRK_EOVERFLOW,
+ * CRK_ECUDA. */
+int crk_forces(crk_sim *sim, crk_outputs *out);
+
+/* nsteps fixed-step kick-drift-kick steps of size dt for every box:
+ *   v += dt/2 a; u += dt/2 du; x = wrap(x + dt v);
+ *   forces at (x, v + dt/2 a_old, u + dt/2 du_old);
+ *   v += dt/2 a; u += dt/2 du    (gas u floored at u_floor each time).
+ * If no forces exist yet, one force evaluation at the loaded state comes
+ * first.  State stays on the device.  Errors as crk_forces. */
+int crk_step(crk_sim *sim, double dt, int nsteps);
+
+/* As crk_step with a per-box step size (dt: host array of nbox values). */
+int crk_step_boxes(crk_sim *sim, const double *dt, int nsteps);
+
+/* Copies the current state out in the caller's order (any pointer may be
+ * NULL).  pos/vel 3N, u N. */
+int crk_get_state(crk_sim *sim, double *pos, double *vel, double *u, int mem);
+
+/* Replaces the positions, velocities and energies of the loaded particles
+ * (caller's order; any pointer may be NULL to keep that quantity) and keeps
+ * masses, species, h and the rates of the last force evaluation, so a
+ * following crk_step continues the KDK from the new state.  Positions must
+ * lie in [0, L).  Errors: CRK_EINVAL (bad value; the state is then
+ * unspecified until the next crk_load), CRK_ECUDA. */
+int crk_set_state(crk_sim *sim, const double *pos, const double *vel, const double *u, int mem);
+
+/* FP64 device reductions of the current state over all boxes:
+ * momentum = sum m v, energy = sum (1/2 m v^2 + m u); nfloor = floor events
+ * since load. */
+int crk_get_sums(crk_sim *sim, double momentum[3], double *energy, int64_t *nfloor);
+
+/* Number of particles and boxes loaded. */
+int crk_get_size(crk_sim *sim, int64_t *n, int *nbox);
+
+/* Turns per-phase CUDA-event timing on (1) or off (0) and resets it. */
+int crk_set_timing(crk_sim *sim, int enable);
+int crk_get_timings(crk_sim *sim, crk_timings *out);
+
+/* Frees every resource of the handle (synchronises its stream first). */
+int crk_destroy(crk_sim *sim);
+
+/* ------------------------------------------------------------------ */
+/* Service: continuous batching of many small-box force-and-KDK jobs.   */
+/* A host thread admits submitted jobs while slots and the HBM budget    */
+/* allow, keeps every admitted job's particles and tree resident in one  */
+/* batched device state, advances all resident jobs one KDK step per     */
+/* batched launch sequence, and publishes each job when its steps are    */
+/* done; new jobs join at the next step boundary.                       */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    size_t hbm_budget_bytes;   /* admission limit on the device memory of resident jobs */
+    int max_slots;             /* at most this many resident jobs */
+    int precision;             /* CRK_MIXED or CRK_FP64 */
+    int leaf_cap;              /* 32, 64 or 128 */
+    int device;                /* CUDA device ordinal */
+    int reserved[4];
+} crk_service_params;
+
+typedef struct {
+    crk_physics phys;          /* the box's physics */
+    int64_t n;                 /* particles */
+    const double *pos, *vel, *mass, *u, *h;   /* host arrays, copied by crk_submit */
+    const uint8_t *species;
+    double dt;                 /* KDK step */
+    int nsteps;                /* KDK steps to run */
+    int reserved;
+} crk_job;
+
+typedef struct {
+    double *pos, *vel, *u;     /* caller-owned host buffers (3n, 3n, n) or NULL */
+    int64_t n;                 /* written: particles */
+    int64_t latency_ns;        /* written: submit to completion */
+    int64_t queue_ns;          /* written: submit to admission */
+    int status;                /* written: CRK_OK or the job's error */
+    int reserved;
+} crk_job_result;
+
+typedef struct crk_service crk_service;
+
+/* Creates the service and starts its host thread on params->device.
+ * Errors: CRK_EINVAL, CRK_ENOMEM, CRK_ECUDA. */
+int crk_service_create(const crk_service_params *params, crk_service **out);
+/* Copies the job's arrays and enqueues it; *ticket identifies it.  Errors:
+ * CRK_EINVAL (bad job, or a job that alone exceeds the budget). Thread-safe. */
+int crk_submit(crk_service *service, const crk_job *job, uint64_t *ticket);
+/* Waits up to timeout_us (0 = do not wait, < 0 = forever) for the job;
+ * CRK_EPENDING if still running, CRK_ENOTFOUND for an unknown ticket.  On
+ * completion copies the final state and frees the ticket.  Thread-safe. */
+int crk_poll(crk_service *service, uint64_t ticket, crk_job_result *result, int64_t timeout_us);
+/* Stops the service thread after the resident jobs finish and frees it. */
+int crk_service_destroy(crk_service *service);
+
+/* Thread-local message of the last failing call on this thread. */
+const char *crk_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CRK_H */

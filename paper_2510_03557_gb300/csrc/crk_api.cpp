@@ -1,0 +1,908 @@
+// Host side of the C ABI declared in include/crk.h: handle lifetime, input
+// checks, device memory, and the per-step launch sequence
+//   [kick + drift] -> Morton keys -> radix sort -> permute -> leaves ->
+//   leaf hierarchy -> leaf-pair lists -> predictor records -> D -> M+C -> H
+//   -> G -> [second kick] -> sums
+// all ordered on the handle's stream (paper Sec. IV-A/IV-B: the data stays on
+// the device for the whole run; only leaf and pair counts come back to size
+// the next launches).
+#include "sim.h"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+using namespace crk;
+
+#include <atomic>
+
+namespace {
+thread_local std::string g_err;
+std::atomic<int64_t> g_launches{0};
+}
+
+namespace crk {
+
+void note_launches(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+int64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+int DBuf::ensure_impl(size_t b)
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    size_t nb = std::max<size_t>(b + b / 8, 256);
+    cudaError_t e = cudaMalloc(&p, nb);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CRK_ENOMEM, "cudaMalloc(%zu) failed: %s", nb, cudaGetErrorString(e));
+    }
+    bytes = nb;
+    return CRK_OK;
+}
+
+int DBuf::ensure(size_t b)
+{
+    if (b <= bytes) return CRK_OK;
+    return ensure_impl(b);
+}
+
+// Grows the buffer keeping its first `keep` bytes (stream-ordered copy).
+int DBuf::ensure_keep(size_t b, size_t keep, cudaStream_t st)
+{
+    if (b <= bytes) return CRK_OK;
+    void *old = p;
+    size_t nb = std::max<size_t>(b + b / 2, 256);
+    void *q = nullptr;
+    cudaError_t e = cudaMalloc(&q, nb);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(CRK_ENOMEM, "cudaMalloc(%zu) failed: %s", nb, cudaGetErrorString(e));
+    }
+    if (old && keep) {
+        e = cudaMemcpyAsync(q, old, std::min(keep, bytes), cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            cudaFree(q);
+            return fail(CRK_ECUDA, "buffer growth copy failed: %s", cudaGetErrorString(e));
+        }
+    }
+    if (old) cudaFree(old);
+    p = q;
+    bytes = nb;
+    return CRK_OK;
+}
+
+}  // namespace crk
+
+extern "C" const char *crk_last_error(void) { return g_err.c_str(); }
+
+namespace {
+
+size_t rsize(const crk_sim *s) { return s->mixed ? sizeof(float) : sizeof(double); }
+
+void mark(crk_sim *s, int ph, int which)
+{
+    if (s->timing) {
+        cudaEventRecord(s->ev[ph][which], s->st);
+        if (which == 1) s->recorded[ph] = true;
+    }
+}
+
+int alloc_state(DBuf *b, State &s, int64_t n)
+{
+    size_t nd = (size_t)std::max<int64_t>(n, 1);
+    double **dp[13] = {&s.x, &s.y, &s.z, &s.vx, &s.vy, &s.vz, &s.u, &s.m, &s.h, &s.ax, &s.ay, &s.az, &s.du};
+    for (int k = 0; k < 13; ++k) {
+        RET(b[k].ensure(nd * sizeof(double)));
+        *dp[k] = b[k].as<double>();
+    }
+    RET(b[13].ensure(nd));
+    s.species = b[13].as<uint8_t>();
+    RET(b[14].ensure(nd * sizeof(uint32_t)));
+    s.slot = b[14].as<uint32_t>();
+    RET(b[15].ensure(nd * sizeof(uint32_t)));
+    s.id = b[15].as<uint32_t>();
+    return CRK_OK;
+}
+
+// Buffers whose size depends on n only.
+int reserve(crk_sim *s, int64_t n)
+{
+    const size_t nn = (size_t)std::max<int64_t>(n, 1);
+    RET(alloc_state(s->stA, s->sa, n));
+    RET(alloc_state(s->stB, s->sb, n));
+    RET(s->keys.ensure(nn * 8));
+    RET(s->keys_alt.ensure(nn * 8));
+    RET(s->vals.ensure(nn * 4));
+    RET(s->vals_alt.ensure(nn * 4));
+    RET(s->counts.ensure(radix_count_words(n) * 4 + 4));
+    RET(s->scan_tmp.ensure((scan_tmp_words((int64_t)radix_count_words(n)) + scan_tmp_words(n) + 8) * 4));
+    RET(s->flags.ensure(nn * 4));
+    RET(s->flag_scan.ensure(nn * 4));
+    RET(s->scalars.ensure(64));
+    // leaves: at most n
+    for (int k = 0; k < 3; ++k) RET(s->lv_u32[k].ensure(nn * 4));
+    RET(s->lv_sp.ensure(nn));
+    for (int k = 0; k < 3; ++k) RET(s->lv_c[k].ensure(nn * 8));
+    for (int k = 0; k < 3; ++k) RET(s->lv_e[k].ensure(nn * 4));
+    RET(s->lv_h.ensure(nn * 4));
+    s->lv.start = s->lv_u32[0].as<uint32_t>();
+    s->lv.count = s->lv_u32[1].as<uint32_t>();
+    s->lv.slot = s->lv_u32[2].as<uint32_t>();
+    s->lv.species = s->lv_sp.as<uint8_t>();
+    s->lv.cx = s->lv_c[0].as<double>();
+    s->lv.cy = s->lv_c[1].as<double>();
+    s->lv.cz = s->lv_c[2].as<double>();
+    s->lv.ex = s->lv_e[0].as<float>();
+    s->lv.ey = s->lv_e[1].as<float>();
+    s->lv.ez = s->lv_e[2].as<float>();
+    s->lv.hmax = s->lv_h.as<float>();
+    const size_t nnode = 2 * nn + 64;
+    for (int k = 0; k < 7; ++k) RET(s->nd_f[k].ensure(nnode * 4));
+    RET(s->nd_slot.ensure(nnode * 4));
+    s->nd.lox = s->nd_f[0].as<float>();
+    s->nd.loy = s->nd_f[1].as<float>();
+    s->nd.loz = s->nd_f[2].as<float>();
+    s->nd.hix = s->nd_f[3].as<float>();
+    s->nd.hiy = s->nd_f[4].as<float>();
+    s->nd.hiz = s->nd_f[5].as<float>();
+    s->nd.hmax = s->nd_f[6].as<float>();
+    s->nd.slot = s->nd_slot.as<int32_t>();
+    RET(s->hrow.ensure((nn + 1) * 4));
+    RET(s->grow.ensure((nn + 1) * 4));
+    RET(s->hcnt.ensure((nn + 1) * 4));
+    RET(s->gcnt.ensure((nn + 1) * 4));
+    const size_t r4 = 4 * rsize(s);
+    RET(s->pm.ensure(nn * r4));
+    for (int k = 0; k < 7; ++k) RET(s->hrec[k].ensure(nn * r4));
+    RET(s->uhat.ensure(nn * rsize(s)));
+    RET(s->acc_h.ensure(nn * r4));
+    RET(s->acc_g.ensure(nn * r4));
+    RET(s->nbrc.ensure(nn * 4));
+    RET(s->nbrh.ensure(nn * 8));
+    RET(s->gravc.ensure(nn * 4));
+    RET(s->gravh.ensure(nn * 8));
+    RET(s->err.ensure(16));
+    RET(s->nfloor.ensure(16));
+    RET(s->partial.ensure((size_t)sums_blocks(n) * 4 * 8 + 64));
+    RET(s->sums.ensure(64));
+    s->cap_n = std::max<int64_t>(s->cap_n, n);
+    return CRK_OK;
+}
+
+PassArgs pass_args(crk_sim *s)
+{
+    PassArgs a{};
+    a.n = s->n;
+    a.nleaf = s->nleaf;
+    a.boxes = s->boxes_d.as<BoxDev>();
+    a.s = s->sa;
+    a.lv = s->lv;
+    a.hrow = s->hrow.as<uint32_t>();
+    a.hcol = s->hcol.as<uint32_t>();
+    a.grow = s->grow.as<uint32_t>();
+    a.gcol = s->gcol.as<uint32_t>();
+    a.pm = s->pm.p;
+    for (int k = 0; k < 7; ++k) a.hrec[k] = s->hrec[k].p;
+    a.uhat = s->uhat.p;
+    a.acc_h = s->acc_h.p;
+    a.acc_g = s->acc_g.p;
+    a.nbr_count = s->nbrc.as<int32_t>();
+    a.nbr_hash = s->nbrh.as<uint64_t>();
+    a.grav_count = s->gravc.as<int32_t>();
+    a.grav_hash = s->gravh.as<uint64_t>();
+    a.err = s->err.as<int>();
+    a.nfloor = s->nfloor.as<unsigned long long>();
+    return a;
+}
+
+int check_physics(const crk_physics &p)
+{
+    if (!(p.box > 0.0) || !std::isfinite(p.box)) return fail(CRK_EINVAL, "box side must be > 0");
+    if (!(p.r_cut > 0.0) || !(p.r_cut < 0.5 * p.box))
+        return fail(CRK_EINVAL, "r_cut must satisfy 0 < r_cut < L/2 (got %g, L=%g)", p.r_cut, p.box);
+    if (!(p.r_split > 0.0)) return fail(CRK_EINVAL, "r_split must be > 0");
+    if (!(p.eps_soft >= 0.0)) return fail(CRK_EINVAL, "eps_soft must be >= 0");
+    if (!(p.gamma > 1.0)) return fail(CRK_EINVAL, "gamma must be > 1");
+    if (!(p.u_floor >= 0.0)) return fail(CRK_EINVAL, "u_floor must be >= 0");
+    return CRK_OK;
+}
+
+BoxDev box_dev(const crk_physics &p)
+{
+    BoxDev b{};
+    b.L = p.box;
+    b.halfL = 0.5 * p.box;
+    b.G = p.G;
+    b.gamma = p.gamma;
+    b.r_cut = p.r_cut;
+    b.r_split = p.r_split;
+    b.eps_soft = p.eps_soft;
+    b.av_alpha = p.av_alpha;
+    b.av_beta = p.av_beta;
+    b.av_eps2 = p.av_eps2;
+    b.u_floor = p.u_floor;
+    b.dt = 0.0;
+    b.hdt = 0.0;
+    b.cm_shift = 63;
+    b.active = 1;
+    return b;
+}
+
+// Chaining-mesh level of a box: the Morton level b (2^b bins per side) that
+// gives about four leaves of each species per bin, the paper's coarse bins
+// (Sec. IV-B1) sized to the leaf capacity.
+int auto_cm_level(int64_t n_species, int cap)
+{
+    double per_side = std::cbrt((double)std::max<int64_t>(n_species, 1) / (4.0 * cap));
+    int b = (int)std::floor(std::log2(std::max(per_side, 1.0)));
+    return std::min(std::max(b, 0), 10);
+}
+
+int upload_boxes(crk_sim *s)
+{
+    RET(s->boxes_d.ensure(std::max<size_t>(s->boxes.size(), 1) * sizeof(BoxDev)));
+    CK(cudaMemcpyAsync(s->boxes_d.p, s->boxes.data(), s->boxes.size() * sizeof(BoxDev),
+                       cudaMemcpyHostToDevice, s->st));
+    return CRK_OK;
+}
+
+int read_error(crk_sim *s)
+{
+    CK(cudaMemcpyAsync(s->host_err, s->err.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    const int code = s->host_err[0], idx = s->host_err[1];
+    if (code == CRK_ESINGULAR)
+        return fail(CRK_ESINGULAR, "second-moment matrix of gas particle %d is singular", idx);
+    if (code == CRK_EINVAL)
+        return fail(CRK_EINVAL, "particle %d is invalid (position outside [0,L), non-finite value, "
+                                "mass <= 0, or gas h with 2h <= 0 or 2h >= L/2)", idx);
+    if (code != 0) return fail(code, "device error %d at particle %d", code, idx);
+    return CRK_OK;
+}
+
+int reset_error(crk_sim *s)
+{
+    int init[2] = {0, 0x7fffffff};
+    CK(cudaMemcpyAsync(s->err.p, init, sizeof init, cudaMemcpyHostToDevice, s->st));
+    return CRK_OK;
+}
+
+// Tree build (S1) and leaf-pair lists (S2).
+int build_tree(crk_sim *s)
+{
+    const int64_t n = s->n;
+    cudaStream_t st = s->st;
+    mark(s, PH_TREE, 0);
+    launch_morton_keys(s->sa, s->boxes_d.as<BoxDev>(), n, s->slot_bits, s->keys.as<uint64_t>(),
+                       s->vals.as<uint32_t>(), st);
+    uint64_t *ko;
+    uint32_t *vo;
+    uint32_t *tmp = s->scan_tmp.as<uint32_t>();
+    radix_sort_u64(s->keys.as<uint64_t>(), s->vals.as<uint32_t>(), s->keys_alt.as<uint64_t>(),
+                   s->vals_alt.as<uint32_t>(), n, s->counts.as<uint32_t>(), tmp, 0, 64, st, &ko, &vo);
+    launch_permute(s->sa, s->sb, vo, n, st);
+    std::swap(s->sa, s->sb);
+    for (int k = 0; k < 16; ++k) std::swap(s->stA[k], s->stB[k]);
+    if (s->n_dead > 0) {
+        // particles of removed slots carry the largest key and now sit at the end
+        s->n -= s->n_dead;
+        s->n_dead = 0;
+    }
+    const int64_t nlive = s->n;
+    uint32_t *sc = s->scalars.as<uint32_t>();
+    launch_leaf_flags(ko, s->sa, s->boxes_d.as<BoxDev>(), nlive, s->cap, s->flags.as<uint32_t>(), st);
+    scan_exclusive_u32(s->flags.as<uint32_t>(), s->flag_scan.as<uint32_t>(), nlive, sc + 0, tmp, st);
+    CK(cudaMemcpyAsync(s->host_scalars, sc, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    s->nleaf = (int)s->host_scalars[0];
+    launch_leaf_setup(s->flags.as<uint32_t>(), s->flag_scan.as<uint32_t>(), nlive, s->nleaf, s->lv, st);
+    launch_leaf_bounds(s->sa, s->boxes_d.as<BoxDev>(), s->lv, s->nleaf, s->mixed ? 1 : 0, s->pm.p,
+                       s->nd, st);
+    mark(s, PH_TREE, 1);
+    mark(s, PH_PAIRS, 0);
+    launch_build_nodes(s->nd, s->nleaf, st);
+    const BoxDev *bd = s->boxes_d.as<BoxDev>();
+    launch_pair_count(s->nd, s->lv, bd, s->nleaf, 1, s->hcnt.as<uint32_t>(), st);
+    launch_pair_count(s->nd, s->lv, bd, s->nleaf, 0, s->gcnt.as<uint32_t>(), st);
+    scan_exclusive_u32(s->hcnt.as<uint32_t>(), s->hrow.as<uint32_t>(), s->nleaf, sc + 1, tmp, st);
+    scan_exclusive_u32(s->gcnt.as<uint32_t>(), s->grow.as<uint32_t>(), s->nleaf, sc + 2, tmp, st);
+    CK(cudaMemcpyAsync(s->host_scalars + 1, sc + 1, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    s->npair_h = s->host_scalars[1];
+    s->npair_g = s->host_scalars[2];
+    // row[nleaf] = total
+    CK(cudaMemcpyAsync(s->hrow.as<uint32_t>() + s->nleaf, sc + 1, 4, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(s->grow.as<uint32_t>() + s->nleaf, sc + 2, 4, cudaMemcpyDeviceToDevice, st));
+    RET(s->hcol.ensure((size_t)std::max<int64_t>(s->npair_h, 1) * 4));
+    RET(s->gcol.ensure((size_t)std::max<int64_t>(s->npair_g, 1) * 4));
+    launch_pair_fill(s->nd, s->lv, bd, s->nleaf, 1, s->hrow.as<uint32_t>(), s->hcol.as<uint32_t>(), st);
+    launch_pair_fill(s->nd, s->lv, bd, s->nleaf, 0, s->grow.as<uint32_t>(), s->gcol.as<uint32_t>(), st);
+    mark(s, PH_PAIRS, 1);
+    return CRK_OK;
+}
+
+// One step.  kdk = false: a force evaluation at the current state (dt = 0).
+int run_step(crk_sim *s, const double *dt_per_box, bool want_counts)
+{
+    cudaStream_t st = s->st;
+    for (int b = 0; b < s->nbox; ++b) {
+        const double dt = dt_per_box ? dt_per_box[b] : 0.0;
+        s->boxes[b].dt = dt;
+        s->boxes[b].hdt = 0.5 * dt;
+    }
+    RET(upload_boxes(s));
+    RET(reset_error(s));
+    if (s->timing) cudaEventRecord(s->ev_all[0], st);
+    for (bool &r : s->recorded) r = false;
+    const int64_t launches0 = launches_so_far();
+    if (dt_per_box) {
+        mark(s, PH_KICK, 0);
+        launch_kick_drift(s->sa, s->boxes_d.as<BoxDev>(), s->n, s->nfloor.as<unsigned long long>(), st);
+        mark(s, PH_KICK, 1);
+    }
+    RET(build_tree(s));
+    PassArgs a = pass_args(s);
+    if (!want_counts) {
+        a.nbr_count = nullptr;
+        a.nbr_hash = nullptr;
+        a.grav_count = nullptr;
+        a.grav_hash = nullptr;
+    }
+    const int mixed = s->mixed ? 1 : 0;
+    mark(s, PH_D, 0);
+    launch_records(a, mixed, st);
+    launch_density(a, mixed, s->cap, want_counts, st);
+    mark(s, PH_D, 1);
+    mark(s, PH_M, 0);
+    launch_moments(a, mixed, s->cap, st);
+    mark(s, PH_M, 1);
+    mark(s, PH_H, 0);
+    launch_hydro(a, mixed, s->cap, st);
+    mark(s, PH_H, 1);
+    mark(s, PH_G, 0);
+    launch_gravity(a, mixed, s->cap, want_counts, st);
+    mark(s, PH_G, 1);
+    mark(s, PH_KDK, 0);
+    launch_final_kick(a, mixed, s->nfloor.as<unsigned long long>(), st);
+    mark(s, PH_KDK, 1);
+    if (s->timing) cudaEventRecord(s->ev_all[1], st);
+    CK(cudaGetLastError());
+    RET(read_error(s));
+    if (s->timing) {
+        for (int ph = 0; ph < PH_N; ++ph) {
+            if (!s->recorded[ph]) continue;
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, s->ev[ph][0], s->ev[ph][1]) == cudaSuccess) s->acc_ms[ph] += ms;
+            else cudaGetLastError();
+        }
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, s->ev_all[0], s->ev_all[1]) == cudaSuccess) s->total_ms += ms;
+        else cudaGetLastError();
+        s->calls++;
+        s->launches += launches_so_far() - launches0;
+    }
+    s->have_forces = true;
+    return CRK_OK;
+}
+
+int copy_in(crk_sim *s, void *dst, const void *src, size_t bytes, int mem)
+{
+    if (bytes == 0) return CRK_OK;
+    CK(cudaMemcpyAsync(dst, src, bytes,
+                       mem == CRK_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->st));
+    return CRK_OK;
+}
+
+int load_impl(crk_sim *s, int nbox, const int64_t *counts, const crk_physics *phys,
+              const double *pos, const double *vel, const double *mass, const double *u,
+              const double *h, const uint8_t *species, int mem)
+{
+    if (nbox < 1) return fail(CRK_EINVAL, "nbox must be >= 1");
+    if (mem != CRK_MEM_HOST && mem != CRK_MEM_DEVICE) return fail(CRK_EINVAL, "bad mem flag");
+    int64_t n = 0;
+    for (int b = 0; b < nbox; ++b) {
+        if (counts[b] < 0) return fail(CRK_EINVAL, "negative particle count in box %d", b);
+        RET(check_physics(phys[b]));
+        n += counts[b];
+    }
+    if (n > 0 && (!pos || !vel || !mass || !u || !h || !species))
+        return fail(CRK_EINVAL, "null input array");
+    if (n >= (int64_t)1 << 31) return fail(CRK_EINVAL, "at most 2^31 - 1 particles");
+    CK(cudaSetDevice(s->device));
+    RET(reserve(s, n));
+    s->n = n;
+    s->nbox = nbox;
+    int sb = 0;
+    while ((1 << sb) < nbox) ++sb;
+    s->slot_bits = sb;
+    s->boxes.assign(nbox, BoxDev{});
+    s->box_count.assign(counts, counts + nbox);
+    // species counts per box for the chaining-mesh level (host arrays or a copy)
+    std::vector<uint8_t> sp_host;
+    const uint8_t *sp = species;
+    if (mem == CRK_MEM_DEVICE && n > 0) {
+        sp_host.resize((size_t)n);
+        CK(cudaMemcpy(sp_host.data(), species, (size_t)n, cudaMemcpyDeviceToHost));
+        sp = sp_host.data();
+    }
+    std::vector<uint32_t> slot_of((size_t)std::max<int64_t>(n, 1));
+    int64_t off = 0;
+    for (int b = 0; b < nbox; ++b) {
+        int64_t ng = 0;
+        for (int64_t k = off; k < off + counts[b]; ++k) {
+            slot_of[(size_t)k] = (uint32_t)b;
+            ng += sp[k] == CRK_GAS;
+        }
+        const int64_t ns = std::max(ng, counts[b] - ng);
+        int lvl = s->prm.cm_level > 0 ? s->prm.cm_level : auto_cm_level(ns, s->cap);
+        lvl = std::min(lvl, (63 - sb) / 3);
+        s->boxes[b] = box_dev(phys[b]);
+        s->boxes[b].cm_shift = 63 - sb - 3 * lvl;
+        off += counts[b];
+    }
+    RET(upload_boxes(s));
+    // Stage inputs on the device, then scatter into the SoA state.
+    const size_t nn = (size_t)n;
+    const size_t need = nn * (3 + 3 + 1 + 1 + 1) * sizeof(double) + nn + nn * 4 + 64;
+    RET(s->in_stage.ensure(need));
+    char *base = s->in_stage.as<char>();
+    double *d_pos = (double *)base;
+    double *d_vel = d_pos + 3 * nn;
+    double *d_mass = d_vel + 3 * nn;
+    double *d_u = d_mass + nn;
+    double *d_h = d_u + nn;
+    uint32_t *d_slot = (uint32_t *)(d_h + nn);
+    uint8_t *d_sp = (uint8_t *)(d_slot + nn);
+    RET(copy_in(s, d_pos, pos, 3 * nn * 8, mem));
+    RET(copy_in(s, d_vel, vel, 3 * nn * 8, mem));
+    RET(copy_in(s, d_mass, mass, nn * 8, mem));
+    RET(copy_in(s, d_u, u, nn * 8, mem));
+    RET(copy_in(s, d_h, h, nn * 8, mem));
+    RET(copy_in(s, d_sp, species, nn, mem));
+    if (n > 0) CK(cudaMemcpyAsync(d_slot, slot_of.data(), nn * 4, cudaMemcpyHostToDevice, s->st));
+    launch_load_state(s->sa, n, d_pos, d_vel, d_mass, d_u, d_h, d_sp, d_slot, s->st);
+    RET(reset_error(s));
+    launch_validate(s->sa, s->boxes_d.as<BoxDev>(), n, s->err.as<int>(), s->st);
+    CK(cudaMemsetAsync(s->nfloor.p, 0, 8, s->st));
+    CK(cudaGetLastError());
+    int rc = read_error(s);
+    if (rc != CRK_OK) {
+        s->n = 0;
+        return rc;
+    }
+    s->have_forces = false;
+    return CRK_OK;
+}
+
+template <typename T>
+int deliver(crk_sim *s, T *user, size_t count, int mem, T **dev_target, size_t &stage_off)
+{
+    // Where the un-permute kernel writes: the user's device buffer directly,
+    // or a slice of the staging buffer for host outputs.
+    if (!user) {
+        *dev_target = nullptr;
+        return CRK_OK;
+    }
+    if (mem == CRK_MEM_DEVICE) {
+        *dev_target = user;
+        return CRK_OK;
+    }
+    *dev_target = reinterpret_cast<T *>(s->staging.as<char>() + stage_off);
+    stage_off += (count * sizeof(T) + 255) & ~size_t(255);
+    return CRK_OK;
+}
+
+}  // namespace
+
+extern "C" int crk_create(const crk_params *params, void *cuda_stream, crk_sim **out)
+{
+    if (!params || !out) return fail(CRK_EINVAL, "null argument");
+    if (params->leaf_cap != 32 && params->leaf_cap != 64 && params->leaf_cap != 128)
+        return fail(CRK_EINVAL, "leaf_cap must be 32, 64 or 128 (got %d)", params->leaf_cap);
+    if (params->precision != CRK_FP64 && params->precision != CRK_MIXED)
+        return fail(CRK_EINVAL, "precision must be CRK_FP64 or CRK_MIXED");
+    if (params->kernel != CRK_WENDLAND_C4) return fail(CRK_EINVAL, "unsupported kernel");
+    if (params->cm_level < 0 || params->cm_level > 10) return fail(CRK_EINVAL, "cm_level in [0, 10]");
+    crk_sim *s = new crk_sim();
+    s->prm = *params;
+    s->mixed = params->precision == CRK_MIXED;
+    s->cap = params->leaf_cap;
+    s->st = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e == cudaSuccess) e = cudaMallocHost(&s->host_scalars, 64);
+    if (e == cudaSuccess) e = cudaMallocHost(&s->host_err, 64);
+    if (e != cudaSuccess) {
+        int code = fail(CRK_ECUDA, "CUDA initialisation failed: %s", cudaGetErrorString(e));
+        cudaGetLastError();
+        delete s;
+        return code;
+    }
+    for (int ph = 0; ph < PH_N; ++ph)
+        for (int w = 0; w < 2; ++w) cudaEventCreate(&s->ev[ph][w]);
+    cudaEventCreate(&s->ev_all[0]);
+    cudaEventCreate(&s->ev_all[1]);
+    *out = s;
+    return CRK_OK;
+}
+
+extern "C" int crk_load(crk_sim *sim, int64_t n, const double *pos, const double *vel,
+                        const double *mass, const double *u, const double *h,
+                        const uint8_t *species, int mem)
+{
+    if (!sim) return fail(CRK_EINVAL, "null handle");
+    if (n < 0) return fail(CRK_EINVAL, "n must be >= 0");
+    return load_impl(sim, 1, &n, &sim->prm.phys, pos, vel, mass, u, h, species, mem);
+}
+
+extern "C" int crk_load_boxes(crk_sim *sim, int nbox, const int64_t *counts,
+                              const crk_physics *phys, const double *pos, const double *vel,
+                              const double *mass, const double *u, const double *h,
+                              const uint8_t *species, int mem)
+{
+    if (!sim || !counts || !phys) return fail(CRK_EINVAL, "null argument");
+    return load_impl(sim, nbox, counts, phys, pos, vel, mass, u, h, species, mem);
+}
+
+extern "C" int crk_forces(crk_sim *s, crk_outputs *out)
+{
+    if (!s || !out) return fail(CRK_EINVAL, "null argument");
+    if (out->mem != CRK_MEM_HOST && out->mem != CRK_MEM_DEVICE) return fail(CRK_EINVAL, "bad mem flag");
+    CK(cudaSetDevice(s->device));
+    const bool counts = out->nbr_count || out->nbr_hash || out->grav_count || out->grav_hash;
+    RET(run_step(s, nullptr, counts));
+    PassArgs a = pass_args(s);
+    if (!counts) {
+        a.nbr_count = nullptr;
+        a.nbr_hash = nullptr;
+        a.grav_count = nullptr;
+        a.grav_hash = nullptr;
+    }
+    const size_t n = (size_t)s->n;
+    if (out->mem == CRK_MEM_HOST) RET(s->staging.ensure(std::max<size_t>(n, 1) * 8 * 24 + 4096));
+    size_t off = 0;
+    double *acc, *dudt, *rho, *A, *B, *gA, *gB;
+    int32_t *nc, *gc;
+    uint64_t *nh, *gh;
+    RET(deliver(s, out->acc, 3 * n, out->mem, &acc, off));
+    RET(deliver(s, out->dudt, n, out->mem, &dudt, off));
+    RET(deliver(s, out->rho, n, out->mem, &rho, off));
+    RET(deliver(s, out->A, n, out->mem, &A, off));
+    RET(deliver(s, out->B, 3 * n, out->mem, &B, off));
+    RET(deliver(s, out->gradA, 3 * n, out->mem, &gA, off));
+    RET(deliver(s, out->gradB, 9 * n, out->mem, &gB, off));
+    RET(deliver(s, out->nbr_count, n, out->mem, &nc, off));
+    RET(deliver(s, out->nbr_hash, n, out->mem, &nh, off));
+    RET(deliver(s, out->grav_count, n, out->mem, &gc, off));
+    RET(deliver(s, out->grav_hash, n, out->mem, &gh, off));
+    launch_unpermute_outputs(a, s->mixed ? 1 : 0, acc, dudt, rho, A, B, gA, gB, nc, nh, gc, gh, s->st);
+    if (out->mem == CRK_MEM_HOST && n > 0) {
+        struct { void *u; const void *d; size_t b; } cp[] = {
+            {out->acc, acc, 3 * n * 8}, {out->dudt, dudt, n * 8}, {out->rho, rho, n * 8},
+            {out->A, A, n * 8}, {out->B, B, 3 * n * 8}, {out->gradA, gA, 3 * n * 8},
+            {out->gradB, gB, 9 * n * 8}, {out->nbr_count, nc, n * 4}, {out->nbr_hash, nh, n * 8},
+            {out->grav_count, gc, n * 4}, {out->grav_hash, gh, n * 8}};
+        for (auto &c : cp)
+            if (c.u) CK(cudaMemcpyAsync(c.u, c.d, c.b, cudaMemcpyDeviceToHost, s->st));
+    }
+    launch_rate_sums(a, s->mixed ? 1 : 0, s->partial.as<double>(), sums_blocks(s->n), s->sums.as<double>(), s->st);
+    double sums[4];
+    CK(cudaMemcpyAsync(sums, s->sums.p, sizeof sums, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    out->momentum_rate[0] = sums[0];
+    out->momentum_rate[1] = sums[1];
+    out->momentum_rate[2] = sums[2];
+    out->energy_rate = sums[3];
+    return CRK_OK;
+}
+
+extern "C" int crk_step_boxes(crk_sim *s, const double *dt, int nsteps)
+{
+    if (!s || !dt) return fail(CRK_EINVAL, "null argument");
+    if (nsteps < 0) return fail(CRK_EINVAL, "nsteps must be >= 0");
+    for (int b = 0; b < s->nbox; ++b)
+        if (!(dt[b] >= 0.0) || !std::isfinite(dt[b])) return fail(CRK_EINVAL, "dt must be finite and >= 0");
+    CK(cudaSetDevice(s->device));
+    if (s->n == 0) return CRK_OK;
+    if (!s->have_forces) RET(run_step(s, nullptr, false));
+    for (int k = 0; k < nsteps; ++k) RET(run_step(s, dt, false));
+    return CRK_OK;
+}
+
+extern "C" int crk_step(crk_sim *s, double dt, int nsteps)
+{
+    if (!s) return fail(CRK_EINVAL, "null handle");
+    std::vector<double> d((size_t)std::max(s->nbox, 1), dt);
+    return crk_step_boxes(s, d.data(), nsteps);
+}
+
+extern "C" int crk_get_state(crk_sim *s, double *pos, double *vel, double *u, int mem)
+{
+    if (!s) return fail(CRK_EINVAL, "null handle");
+    if (mem != CRK_MEM_HOST && mem != CRK_MEM_DEVICE) return fail(CRK_EINVAL, "bad mem flag");
+    CK(cudaSetDevice(s->device));
+    const size_t n = (size_t)s->n;
+    if (n == 0) return CRK_OK;
+    if (mem == CRK_MEM_DEVICE) {
+        launch_unpermute_state(s->sa, s->n, pos, vel, u, s->st);
+    } else {
+        RET(s->staging.ensure(n * 8 * 7 + 1024));
+        double *dp = s->staging.as<double>(), *dv = dp + 3 * n, *du = dv + 3 * n;
+        launch_unpermute_state(s->sa, s->n, pos ? dp : nullptr, vel ? dv : nullptr, u ? du : nullptr, s->st);
+        if (pos) CK(cudaMemcpyAsync(pos, dp, 3 * n * 8, cudaMemcpyDeviceToHost, s->st));
+        if (vel) CK(cudaMemcpyAsync(vel, dv, 3 * n * 8, cudaMemcpyDeviceToHost, s->st));
+        if (u) CK(cudaMemcpyAsync(u, du, n * 8, cudaMemcpyDeviceToHost, s->st));
+    }
+    CK(cudaStreamSynchronize(s->st));
+    return CRK_OK;
+}
+
+extern "C" int crk_get_sums(crk_sim *s, double momentum[3], double *energy, int64_t *nfloor)
+{
+    if (!s) return fail(CRK_EINVAL, "null handle");
+    CK(cudaSetDevice(s->device));
+    double v[4] = {0, 0, 0, 0};
+    unsigned long long nf = 0;
+    if (s->n > 0) {
+        launch_state_sums(s->sa, s->n, s->partial.as<double>(), sums_blocks(s->n), s->sums.as<double>(), s->st);
+        CK(cudaMemcpyAsync(v, s->sums.p, sizeof v, cudaMemcpyDeviceToHost, s->st));
+        CK(cudaMemcpyAsync(&nf, s->nfloor.p, 8, cudaMemcpyDeviceToHost, s->st));
+        CK(cudaStreamSynchronize(s->st));
+    }
+    if (momentum) {
+        momentum[0] = v[0];
+        momentum[1] = v[1];
+        momentum[2] = v[2];
+    }
+    if (energy) *energy = v[3];
+    if (nfloor) *nfloor = (int64_t)nf;
+    return CRK_OK;
+}
+
+extern "C" int crk_get_size(crk_sim *s, int64_t *n, int *nbox)
+{
+    if (!s) return fail(CRK_EINVAL, "null handle");
+    if (n) *n = s->n;
+    if (nbox) *nbox = s->nbox;
+    return CRK_OK;
+}
+
+extern "C" int crk_set_timing(crk_sim *s, int enable)
+{
+    if (!s) return fail(CRK_EINVAL, "null handle");
+    s->timing = enable != 0;
+    for (double &v : s->acc_ms) v = 0;
+    s->total_ms = 0;
+    s->calls = 0;
+    s->launches = 0;
+    return CRK_OK;
+}
+
+extern "C" int crk_set_state(crk_sim *s, const double *pos, const double *vel, const double *u,
+                             int mem)
+{
+    if (!s) return fail(CRK_EINVAL, "null handle");
+    if (mem != CRK_MEM_HOST && mem != CRK_MEM_DEVICE) return fail(CRK_EINVAL, "bad mem flag");
+    CK(cudaSetDevice(s->device));
+    const size_t n = (size_t)s->n;
+    if (n == 0) return CRK_OK;
+    const double *dp = pos, *dv = vel, *du = u;
+    if (mem == CRK_MEM_HOST) {
+        RET(s->in_stage.ensure(n * 7 * 8 + 64));
+        double *b = s->in_stage.as<double>();
+        if (pos) CK(cudaMemcpyAsync(b, pos, n * 24, cudaMemcpyHostToDevice, s->st));
+        if (vel) CK(cudaMemcpyAsync(b + 3 * n, vel, n * 24, cudaMemcpyHostToDevice, s->st));
+        if (u) CK(cudaMemcpyAsync(b + 6 * n, u, n * 8, cudaMemcpyHostToDevice, s->st));
+        dp = pos ? b : nullptr;
+        dv = vel ? b + 3 * n : nullptr;
+        du = u ? b + 6 * n : nullptr;
+    }
+    launch_set_state(s->sa, s->n, dp, dv, du, s->st);
+    RET(reset_error(s));
+    launch_validate(s->sa, s->boxes_d.as<BoxDev>(), s->n, s->err.as<int>(), s->st);
+    CK(cudaGetLastError());
+    return read_error(s);
+}
+
+extern "C" int crk_get_timings(crk_sim *s, crk_timings *t)
+{
+    if (!s || !t) return fail(CRK_EINVAL, "null argument");
+    t->tree_ms = s->acc_ms[PH_TREE];
+    t->pairs_ms = s->acc_ms[PH_PAIRS];
+    t->density_ms = s->acc_ms[PH_D];
+    t->moments_ms = s->acc_ms[PH_M];
+    t->hydro_ms = s->acc_ms[PH_H];
+    t->gravity_ms = s->acc_ms[PH_G];
+    t->kdk_ms = s->acc_ms[PH_KDK] + s->acc_ms[PH_KICK];
+    t->total_ms = s->total_ms;
+    t->calls = s->calls;
+    t->pairs_hydro = s->npair_h;
+    t->pairs_grav = s->npair_g;
+    t->nleaves = s->nleaf;
+    t->launches = s->launches;
+    return CRK_OK;
+}
+
+extern "C" int crk_destroy(crk_sim *s)
+{
+    if (!s) return CRK_OK;
+    cudaSetDevice(s->device);
+    cudaStreamSynchronize(s->st);
+    for (int k = 0; k < 16; ++k) {
+        s->stA[k].release();
+        s->stB[k].release();
+    }
+    DBuf *bufs[] = {&s->boxes_d, &s->keys, &s->keys_alt, &s->vals, &s->vals_alt, &s->counts,
+                    &s->scan_tmp, &s->flags, &s->flag_scan, &s->scalars, &s->lv_sp, &s->lv_h,
+                    &s->nd_slot, &s->hrow, &s->grow, &s->hcnt, &s->gcnt, &s->hcol, &s->gcol,
+                    &s->pm, &s->uhat, &s->acc_h, &s->acc_g, &s->nbrc, &s->nbrh, &s->gravc,
+                    &s->gravh, &s->err, &s->nfloor, &s->partial, &s->sums, &s->staging,
+                    &s->in_stage};
+    for (DBuf *b : bufs) b->release();
+    for (int k = 0; k < 3; ++k) {
+        s->lv_u32[k].release();
+        s->lv_c[k].release();
+        s->lv_e[k].release();
+    }
+    for (int k = 0; k < 7; ++k) {
+        s->nd_f[k].release();
+        s->hrec[k].release();
+    }
+    for (int ph = 0; ph < PH_N; ++ph)
+        for (int w = 0; w < 2; ++w)
+            if (s->ev[ph][w]) cudaEventDestroy(s->ev[ph][w]);
+    if (s->ev_all[0]) cudaEventDestroy(s->ev_all[0]);
+    if (s->ev_all[1]) cudaEventDestroy(s->ev_all[1]);
+    if (s->host_scalars) cudaFreeHost(s->host_scalars);
+    if (s->host_err) cudaFreeHost(s->host_err);
+    delete s;
+    return CRK_OK;
+}
+
+// ------------------------------------------------------------------ pool
+// A handle used by the service: its boxes are `max_slots` fixed slots; jobs
+// are appended into free slots between steps and leave by deactivating their
+// slot (their particles then sort last and are dropped at the next step).
+namespace crk {
+
+size_t pool_bytes_per_particle(const crk_sim *s)
+{
+    const size_t r = s->mixed ? 4 : 8;
+    // two state copies, sort buffers, leaves/hierarchy bound, records, counts
+    return 2 * (13 * 8 + 9) + 2 * 12 + 8 + 128 + 4 * r * 10 + r + 24 + 64;
+}
+
+int pool_init(crk_sim *s, int max_slots)
+{
+    if (max_slots < 1) return fail(CRK_EINVAL, "max_slots must be >= 1");
+    CK(cudaSetDevice(s->device));
+    int sb = 0;
+    while ((1 << sb) < max_slots + 1) ++sb;
+    s->slot_bits = sb;
+    s->nbox = max_slots;
+    crk_physics dummy{};
+    dummy.box = 1.0;
+    dummy.r_cut = 0.1;
+    dummy.r_split = 0.1;
+    dummy.gamma = 5.0 / 3.0;
+    s->boxes.assign(max_slots, box_dev(dummy));
+    for (BoxDev &b : s->boxes) b.active = 0;
+    s->n = 0;
+    s->n_dead = 0;
+    RET(reserve(s, 4096));
+    RET(upload_boxes(s));
+    CK(cudaMemsetAsync(s->nfloor.p, 0, 8, s->st));
+    return CRK_OK;
+}
+
+static State shifted(const State &a, int64_t off)
+{
+    State b = a;
+    b.x += off; b.y += off; b.z += off;
+    b.vx += off; b.vy += off; b.vz += off;
+    b.u += off; b.m += off; b.h += off;
+    b.ax += off; b.ay += off; b.az += off; b.du += off;
+    b.species += off; b.slot += off; b.id += off;
+    return b;
+}
+
+static int pool_grow(crk_sim *s, int64_t need)
+{
+    if (need <= s->cap_n) return CRK_OK;
+    const int64_t cap = std::max<int64_t>(need, 2 * s->cap_n);
+    const size_t keep = (size_t)s->n;
+    for (int k = 0; k < 13; ++k) RET(s->stA[k].ensure_keep((size_t)cap * 8, keep * 8, s->st));
+    RET(s->stA[13].ensure_keep((size_t)cap, keep, s->st));
+    RET(s->stA[14].ensure_keep((size_t)cap * 4, keep * 4, s->st));
+    RET(s->stA[15].ensure_keep((size_t)cap * 4, keep * 4, s->st));
+    return reserve(s, cap);
+}
+
+int pool_add(crk_sim *s, int slot, const crk_physics &phys, int64_t n, const double *pos,
+             const double *vel, const double *mass, const double *u, const double *h,
+             const uint8_t *species)
+{
+    if (slot < 0 || slot >= s->nbox) return fail(CRK_EINVAL, "bad slot %d", slot);
+    RET(check_physics(phys));
+    if (n <= 0) return fail(CRK_EINVAL, "a job needs at least one particle");
+    CK(cudaSetDevice(s->device));
+    const int64_t n0 = s->n;
+    RET(pool_grow(s, n0 + n));
+    int64_t ng = 0;
+    for (int64_t k = 0; k < n; ++k) ng += species[k] == CRK_GAS;
+    const int lvl = std::min(auto_cm_level(std::max(ng, n - ng), s->cap), (63 - s->slot_bits) / 3);
+    BoxDev b = box_dev(phys);
+    b.cm_shift = 63 - s->slot_bits - 3 * lvl;
+    b.active = 1;
+    s->boxes[slot] = b;
+    RET(upload_boxes(s));
+    const size_t nn = (size_t)n;
+    RET(s->in_stage.ensure(nn * 9 * sizeof(double) + nn * 5 + 64));
+    double *d_pos = s->in_stage.as<double>();
+    double *d_vel = d_pos + 3 * nn, *d_mass = d_vel + 3 * nn, *d_u = d_mass + nn, *d_h = d_u + nn;
+    uint32_t *d_slot = (uint32_t *)(d_h + nn);
+    uint8_t *d_sp = (uint8_t *)(d_slot + nn);
+    std::vector<uint32_t> slot_of(nn, (uint32_t)slot);
+    CK(cudaMemcpyAsync(d_pos, pos, nn * 24, cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(d_vel, vel, nn * 24, cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(d_mass, mass, nn * 8, cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(d_u, u, nn * 8, cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(d_h, h, nn * 8, cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(d_sp, species, nn, cudaMemcpyHostToDevice, s->st));
+    CK(cudaMemcpyAsync(d_slot, slot_of.data(), nn * 4, cudaMemcpyHostToDevice, s->st));
+    const State part = shifted(s->sa, n0);
+    launch_load_state(part, n, d_pos, d_vel, d_mass, d_u, d_h, d_sp, d_slot, s->st);
+    RET(reset_error(s));
+    launch_validate(part, s->boxes_d.as<BoxDev>(), n, s->err.as<int>(), s->st);
+    CK(cudaGetLastError());
+    int rc = read_error(s);  // synchronises: the host arrays may be released after return
+    if (rc != CRK_OK) {
+        s->boxes[slot].active = 0;
+        upload_boxes(s);
+        return rc;
+    }
+    s->n = n0 + n;
+    return CRK_OK;
+}
+
+int pool_extract(crk_sim *s, int slot, int64_t n, double *pos, double *vel, double *u)
+{
+    CK(cudaSetDevice(s->device));
+    const size_t nn = (size_t)n;
+    RET(s->staging.ensure(nn * 7 * 8 + 256));
+    double *dp = s->staging.as<double>(), *dv = dp + 3 * nn, *du = dv + 3 * nn;
+    launch_extract_slot(s->sa, s->n, (uint32_t)slot, dp, dv, du, s->st);
+    if (pos) CK(cudaMemcpyAsync(pos, dp, nn * 24, cudaMemcpyDeviceToHost, s->st));
+    if (vel) CK(cudaMemcpyAsync(vel, dv, nn * 24, cudaMemcpyDeviceToHost, s->st));
+    if (u) CK(cudaMemcpyAsync(u, du, nn * 8, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    return CRK_OK;
+}
+
+void pool_remove(crk_sim *s, int slot, int64_t n)
+{
+    s->boxes[slot].active = 0;
+    s->n_dead += n;
+}
+
+int pool_step(crk_sim *s, const double *dt_per_slot)
+{
+    CK(cudaSetDevice(s->device));
+    if (s->n == 0) return CRK_OK;
+    return run_step(s, dt_per_slot, false);
+}
+
+}  // namespace crk

@@ -1,0 +1,153 @@
+// Internal declarations of libcrk (device data layout and kernel launchers).
+// Not part of the public ABI; include/crk.h is.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+
+#include "../../include/crk.h"
+
+namespace crk {
+
+// 4-vector record of the pass's real type, aligned for one vector load
+// (16 B for float, 32 B for double).
+template <typename R>
+struct alignas(4 * sizeof(R)) Vec4 {
+    R x, y, z, w;
+};
+
+// Per-box physics as the kernels read it (one entry per box slot).
+struct BoxDev {
+    double L, halfL, G, gamma, r_cut, r_split, eps_soft;
+    double av_alpha, av_beta, av_eps2, u_floor;
+    double dt, hdt;          // step of the current KDK step (0 for a force-only step)
+    int cm_shift;            // sort-key shift that leaves (box, species, chaining-mesh bin)
+    int active;              // 0: slot holds no live particles (keys sort them last)
+};
+
+// Particle state in sorted order, FP64 masters (structure of arrays).
+struct State {
+    double *x, *y, *z;       // positions in [0, L)
+    double *vx, *vy, *vz;    // velocities (after the first half kick: v_half)
+    double *u;               // specific thermal energy (gas)
+    double *m, *h;           // mass, smoothing length (gas)
+    double *ax, *ay, *az;    // acceleration of the last force evaluation
+    double *du;              // du/dt of the last force evaluation
+    uint8_t *species;        // CRK_DM or CRK_GAS
+    uint32_t *slot;          // box index
+    uint32_t *id;            // original (load-order) index
+};
+
+// Leaves: runs of <= leaf_cap consecutive sorted particles of one
+// (box, species, chaining-mesh bin).
+struct Leaves {
+    uint32_t *start, *count, *slot;
+    uint8_t *species;
+    double *cx, *cy, *cz;    // FP64 bounding-box centres
+    float *ex, *ey, *ez;     // half extents, rounded up
+    float *hmax;             // max 2h over the leaf's gas particles (0 for DM leaves)
+};
+
+// Implicit binary hierarchy over the leaf array: level l node k covers
+// leaves [k << l, min((k+1) << l, nleaf)).
+struct Nodes {
+    float *lox, *loy, *loz, *hix, *hiy, *hiz;  // conservative FP32 boxes
+    float *hmax;             // max H of gas leaves below (0: no gas)
+    int32_t *slot;           // box slot, -1 when the node spans several boxes
+    int levels;
+    int64_t level_off[40];   // first node of each level
+    int64_t total;
+};
+
+// CSR leaf-pair list: row I holds the neighbour leaves J (ascending).
+struct PairList {
+    uint32_t *row;           // nleaf + 1
+    uint32_t *col;
+    int64_t capacity;
+};
+
+// Device pointers the pair passes read and write (sorted order).  Records
+// are 4-vectors of the pass's real type; `pm` = (position, mass) where the
+// position is leaf-relative (mixed) or absolute (FP64).
+struct PassArgs {
+    int64_t n;
+    int nleaf;
+    const BoxDev *boxes;
+    State s;
+    Leaves lv;
+    const uint32_t *hrow, *hcol;   // hydro list
+    const uint32_t *grow, *gcol;   // gravity list
+    void *pm;                // R4[n]
+    void *hrec[7];           // R4[n] each: hydro records
+    void *uhat;              // R[n] predicted u
+    void *acc_h;             // R4[n]: hydro acceleration, du/dt
+    void *acc_g;             // R4[n]: gravity acceleration
+    int32_t *nbr_count;      // optional
+    uint64_t *nbr_hash;
+    int32_t *grav_count;
+    uint64_t *grav_hash;
+    int *err;                // [0] code, [1] smallest original index of a failing particle
+    unsigned long long *nfloor;  // floor events of the u predictor
+};
+
+// Host-side count of kernel launches (every launcher adds what it launched).
+void note_launches(int k);
+int64_t launches_so_far();
+
+// ---- scan / sort / tree (tree.cu) ----
+void scan_exclusive_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *total,
+                        uint32_t *tmp, cudaStream_t st);
+size_t scan_tmp_words(int64_t n);
+void radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
+                    int64_t n, uint32_t *counts, uint32_t *scan_tmp, int first_bit, int end_bit,
+                    cudaStream_t st, uint64_t **keys_out, uint32_t **vals_out);
+size_t radix_count_words(int64_t n);
+void launch_morton_keys(const State &s, const BoxDev *boxes, int64_t n, int slot_bits,
+                        uint64_t *keys, uint32_t *idx, cudaStream_t st);
+void launch_permute(const State &src, const State &dst, const uint32_t *perm, int64_t n,
+                    cudaStream_t st);
+void launch_leaf_flags(const uint64_t *keys, const State &s, const BoxDev *boxes, int64_t n,
+                       int cap, uint32_t *flags, cudaStream_t st);
+void launch_leaf_setup(const uint32_t *flags, const uint32_t *scan, int64_t n, int nleaf,
+                       Leaves lv, cudaStream_t st);
+void launch_leaf_bounds(const State &s, const BoxDev *boxes, Leaves lv, int nleaf, int mixed,
+                        void *pm, Nodes nd, cudaStream_t st);
+void launch_build_nodes(Nodes &nd, int nleaf, cudaStream_t st);
+void launch_pair_count(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, int nleaf,
+                       int hydro, uint32_t *counts, cudaStream_t st);
+void launch_pair_fill(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, int nleaf,
+                      int hydro, const uint32_t *row, uint32_t *col, cudaStream_t st);
+
+// ---- passes (passes.cu) ----
+void launch_records(const PassArgs &a, int mixed, cudaStream_t st);
+void launch_density(const PassArgs &a, int mixed, int cap, bool count, cudaStream_t st);
+void launch_moments(const PassArgs &a, int mixed, int cap, cudaStream_t st);
+void launch_hydro(const PassArgs &a, int mixed, int cap, cudaStream_t st);
+void launch_gravity(const PassArgs &a, int mixed, int cap, bool count, cudaStream_t st);
+
+// ---- integration and outputs (integrate.cu) ----
+void launch_kick_drift(const State &s, const BoxDev *boxes, int64_t n,
+                       unsigned long long *nfloor, cudaStream_t st);
+void launch_final_kick(const PassArgs &a, int mixed, unsigned long long *nfloor, cudaStream_t st);
+void launch_rate_sums(const PassArgs &a, int mixed, double *partial, int nblk, double *out6,
+                      cudaStream_t st);
+void launch_state_sums(const State &s, int64_t n, double *partial, int nblk, double *out6,
+                       cudaStream_t st);
+int sums_blocks(int64_t n);
+void launch_unpermute_outputs(const PassArgs &a, int mixed, double *acc, double *dudt,
+                              double *rho, double *A, double *B, double *gA, double *gB,
+                              int32_t *nc, uint64_t *nh, int32_t *gc, uint64_t *gh,
+                              cudaStream_t st);
+void launch_unpermute_state(const State &s, int64_t n, double *pos, double *vel, double *u,
+                            cudaStream_t st);
+void launch_validate(const State &s, const BoxDev *boxes, int64_t n, int *err, cudaStream_t st);
+void launch_set_state(const State &s, int64_t n, const double *pos, const double *vel,
+                      const double *u, cudaStream_t st);
+void launch_extract_slot(const State &s, int64_t n, uint32_t slot, double *pos, double *vel,
+                         double *u, cudaStream_t st);
+void launch_load_state(const State &s, int64_t n, const double *pos, const double *vel,
+                       const double *mass, const double *u, const double *h,
+                       const uint8_t *species, const uint32_t *slot_of, cudaStream_t st);
+
+}  // namespace crk

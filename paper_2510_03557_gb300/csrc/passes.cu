@@ -1,0 +1,749 @@
+// The leaf-to-leaf pair passes of the short-range solver (paper Sec. IV-B2,
+// Eq. 1-2): density D, kernel moments M fused with the correction solve C,
+// the CRKSPH hydro rates H, and short-range gravity G.
+//
+// Layout: one CTA per target leaf, one thread per target particle i
+// (blockDim = leaf capacity).  For every neighbour leaf J of the leaf-pair
+// list the CTA stages J's contiguous records in shared memory with coalesced
+// vector loads, then each thread sweeps them and accumulates phi_i of Eq. 1
+// in registers (no atomics, fixed order, so results are deterministic and a
+// box gives bit-identical results alone or batched with others).
+//
+// Two arithmetic forms share the code:
+//   mixed  (R = float):  positions are FP32 offsets from each leaf's FP64
+//          centre; the leaf-pair shift wrap(c_J - c_I) is formed in FP64 once
+//          per leaf pair, so FP32 differences stay small and accurate.
+//          Neighbour-set membership that decides an integer (counts, hashes)
+//          or a discontinuous force (the gravity cut) is re-decided in FP64,
+//          with the oracle's exact expression, whenever the FP32 r^2 lies in a
+//          guard band around the threshold that bounds its rounding error.
+//   plain  (R = double): absolute FP64 positions, the same minimum-image and
+//          r^2 expression (no FMA) as the definition, every operation FP64.
+#include "crk_internal.h"
+
+#include <cfloat>
+
+namespace crk {
+
+namespace {
+
+constexpr double kPi = 3.14159265358979323846;
+// Wendland C4 in 3-D with support H = 2h:
+//   W = kWn / H^3 (1-q)^6 (1 + 6q + 35 q^2 / 3),  q = r / H
+//   grad_i W = g x_ij,  g = -(56/3) kWn / H^5 (1 + 5q)(1-q)^5
+constexpr double kWn = 495.0 / (32.0 * kPi);
+constexpr double kGn = -(56.0 / 3.0) * kWn;
+// Abramowitz & Stegun 7.1.26 (Hastings): erfc(x) ~ t P(t) exp(-x^2),
+// t = 1/(1 + p x), |error| <= 1.5e-7 for x >= 0.
+constexpr float kAsP = 0.3275911f;
+constexpr float kAs1 = 0.254829592f, kAs2 = -0.284496736f, kAs3 = 1.421413741f,
+                kAs4 = -1.453152027f, kAs5 = 1.061405429f;
+constexpr double kTwoOverSqrtPi = 1.12837916709551257390;
+constexpr float kEps32 = 5.9604645e-8f;  // 2^-24
+
+template <typename R> struct Real;
+template <> struct Real<float> {
+    static constexpr bool mixed = true;
+    __device__ static float sqrt_(float x) { return sqrtf(x); }
+    __device__ static float r2(float dx, float dy, float dz) { return fmaf(dz, dz, fmaf(dy, dy, dx * dx)); }
+};
+template <> struct Real<double> {
+    static constexpr bool mixed = false;
+    __device__ static double sqrt_(double x) { return sqrt(x); }
+    // (dx*dx + dy*dy) + dz*dz with every product and sum rounded on its own,
+    // as the neighbour predicate is defined.
+    __device__ static double r2(double dx, double dy, double dz)
+    {
+        return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
+    }
+};
+
+template <typename R>
+__device__ __forceinline__ R wrap1(R d, R L, R hL)
+{
+    if (d >= hL) d -= L;
+    else if (d < -hL) d += L;
+    return d;
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t x)
+{
+    // SplitMix64 output function (Steele, Lea & Flood 2014).
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// The neighbour predicate exactly as defined: FP64 positions, one wrap,
+// (dx*dx + dy*dy) + dz*dz without contraction, strict comparison.
+__device__ __forceinline__ bool exact_lt(const State &s, uint32_t i, uint32_t j, double L,
+                                         double thr2)
+{
+    const double hL = 0.5 * L;
+    double dx = wrap1(s.x[j] - s.x[i], L, hL);
+    double dy = wrap1(s.y[j] - s.y[i], L, hL);
+    double dz = wrap1(s.z[j] - s.z[i], L, hL);
+    return Real<double>::r2(dx, dy, dz) < thr2;
+}
+
+// Frame of leaf pair (I, J) for target particle position p (record x,y,z):
+// the j-side displacement is dx = rec_j - q, q = p - shift (mixed) or p
+// (plain).  wrap tells whether a per-pair minimum-image wrap is needed, mag
+// bounds |coordinates| entering the FP32 differences (for the guard band).
+template <typename R>
+struct Frame {
+    R qx, qy, qz;
+    bool wrap;
+    R mag;
+};
+
+template <typename R>
+__device__ __forceinline__ Frame<R> make_frame(const Leaves &lv, int I, int J, double L, R px,
+                                               R py, R pz)
+{
+    Frame<R> f;
+    if (Real<R>::mixed) {
+        const double hL = 0.5 * L;
+        const float sx = (float)wrap1(lv.cx[J] - lv.cx[I], L, hL);
+        const float sy = (float)wrap1(lv.cy[J] - lv.cy[I], L, hL);
+        const float sz = (float)wrap1(lv.cz[J] - lv.cz[I], L, hL);
+        const float mx = fabsf(sx) + lv.ex[I] + lv.ex[J];
+        const float my = fabsf(sy) + lv.ey[I] + lv.ey[J];
+        const float mz = fabsf(sz) + lv.ez[I] + lv.ez[J];
+        const float lim = (float)(0.5 * L) * (1.0f - 1e-6f);
+        f.wrap = (mx >= lim) || (my >= lim) || (mz >= lim);
+        f.mag = mx + my + mz + (f.wrap ? (float)L : 0.0f);
+        f.qx = px - sx;
+        f.qy = py - sy;
+        f.qz = pz - sz;
+    } else {
+        f.wrap = true;
+        f.mag = 0;
+        f.qx = px;
+        f.qy = py;
+        f.qz = pz;
+    }
+    return f;
+}
+
+template <typename R>
+__device__ __forceinline__ void displacement(const Frame<R> &f, const Vec4<R> &rj, R L, R hL,
+                                             R &dx, R &dy, R &dz)
+{
+    dx = rj.x - f.qx;
+    dy = rj.y - f.qy;
+    dz = rj.z - f.qz;
+    if (f.wrap) {
+        dx = wrap1(dx, L, hL);
+        dy = wrap1(dy, L, hL);
+        dz = wrap1(dz, L, hL);
+    }
+}
+
+// Guard band of the mixed form around a squared threshold T2 = T^2: the FP32
+// r^2 differs from the exact one by less than 8 sqrt(3) eps T mag + 3 eps T^2
+// (four roundings per coordinate difference, three in the sum of squares);
+// the band is several times wider and never below 1e-5 T^2.
+__device__ __forceinline__ float guard_band(float T, float mag)
+{
+    return 1e-5f * T * T + 64.0f * kEps32 * T * (mag + T);
+}
+
+template <typename R>
+__device__ __forceinline__ void kernel_wg(R r, R invH, R cW, R cG, R &W, R &g)
+{
+    const R q = r * invH;
+    R om = (R)1 - q;
+    om = om > (R)0 ? om : (R)0;
+    const R om2 = om * om;
+    const R om4 = om2 * om2;
+    const R om5 = om4 * om;
+    W = cW * om5 * om * ((R)1 + q * ((R)6 + q * (R)(35.0 / 3.0)));
+    g = cG * om5 * ((R)1 + (R)5 * q);
+}
+
+__device__ __forceinline__ void set_error(int *err, int code, uint32_t id)
+{
+    atomicCAS(err, 0, code);
+    atomicMin(err + 1, (int)id);
+}
+
+// ------------------------------------------------------------- records
+// Predictor values that enter the forces: v^ = v_half + dt/2 a_old,
+// u^ = max(u_half + dt/2 du_old, u_floor) (gas).  hrec1 = (v^, h).
+template <typename R>
+__global__ void records_k(PassArgs a)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= a.n) return;
+    const BoxDev &bx = a.boxes[a.s.slot[k]];
+    const double hdt = bx.hdt;
+    const double vx = __dadd_rn(a.s.vx[k], __dmul_rn(hdt, a.s.ax[k]));
+    const double vy = __dadd_rn(a.s.vy[k], __dmul_rn(hdt, a.s.ay[k]));
+    const double vz = __dadd_rn(a.s.vz[k], __dmul_rn(hdt, a.s.az[k]));
+    double uh = 0.0;
+    if (a.s.species[k] == CRK_GAS) {
+        uh = __dadd_rn(a.s.u[k], __dmul_rn(hdt, a.s.du[k]));
+        if (uh < bx.u_floor) {
+            uh = bx.u_floor;
+            if (a.nfloor) atomicAdd(a.nfloor, 1ull);
+        }
+    }
+    Vec4<R> r1;
+    r1.x = (R)vx; r1.y = (R)vy; r1.z = (R)vz; r1.w = (R)a.s.h[k];
+    reinterpret_cast<Vec4<R> *>(a.hrec[1])[k] = r1;
+    reinterpret_cast<R *>(a.uhat)[k] = (R)uh;
+}
+
+// ------------------------------------------------------------- density D
+// rho_i = sum_{j in N_i + {i}} m_j W(r, h_i); V = m/rho; P = (gamma-1) rho u^;
+// c = sqrt(gamma (gamma-1) u^).  Optional: size and hash of N_i.
+template <typename R, int CAP, bool COUNT>
+__global__ void __launch_bounds__(CAP) density_k(PassArgs a)
+{
+    using R4 = Vec4<R>;
+    const int I = blockIdx.x;
+    if (a.lv.species[I] != CRK_GAS) return;
+    __shared__ R4 tile[CAP];
+    const R4 *__restrict__ pm = reinterpret_cast<const R4 *>(a.pm);
+    const uint32_t s0 = a.lv.start[I], cnt = a.lv.count[I];
+    const BoxDev bx = a.boxes[a.lv.slot[I]];
+    const R L = (R)bx.L, hL = (R)(0.5 * bx.L);
+    const uint32_t t = threadIdx.x;
+    const bool act = t < cnt;
+    const uint32_t i = s0 + (act ? t : 0u);
+    const R4 ri = pm[i];
+    const double h64 = a.s.h[i];
+    const double H64 = 2.0 * h64;
+    const double H2x = __dmul_rn(H64, H64);
+    const R H = (R)H64;
+    const R H2 = Real<R>::mixed ? H * H : (R)H2x;
+    const R invH = (R)1 / H;
+    const R cW = (R)kWn * invH * invH * invH;
+    R rho = 0;
+    int nc = 0;
+    uint64_t hs = 0;
+    for (uint32_t p = a.hrow[I]; p < a.hrow[I + 1]; ++p) {
+        const uint32_t J = a.hcol[p];
+        const uint32_t sJ = a.lv.start[J], cJ = a.lv.count[J];
+        __syncthreads();
+        if (t < cJ) tile[t] = pm[sJ + t];
+        __syncthreads();
+        const Frame<R> f = make_frame<R>(a.lv, I, (int)J, bx.L, ri.x, ri.y, ri.z);
+        const R gb = Real<R>::mixed ? (R)guard_band((float)H, (float)f.mag) : (R)0;
+        for (uint32_t j = 0; j < cJ; ++j) {
+            const R4 rj = tile[j];
+            R dx, dy, dz;
+            displacement(f, rj, L, hL, dx, dy, dz);
+            const R r2 = Real<R>::r2(dx, dy, dz);
+            if (r2 < H2) {
+                const R r = Real<R>::sqrt_(r2);
+                const R q = r * invH;
+                R om = (R)1 - q;
+                om = om > (R)0 ? om : (R)0;
+                const R om2 = om * om;
+                const R W = cW * om2 * om2 * om2 * ((R)1 + q * ((R)6 + q * (R)(35.0 / 3.0)));
+                rho += rj.w * W;
+            }
+            if (COUNT) {
+                bool in = r2 < H2;
+                if (Real<R>::mixed && fabs(r2 - H2) <= gb) in = exact_lt(a.s, i, sJ + j, bx.L, H2x);
+                if (in && !(J == (uint32_t)I && j == t)) {
+                    ++nc;
+                    hs += mix64((uint64_t)a.s.id[sJ + j]);
+                }
+            }
+        }
+    }
+    if (!act) return;
+    const R uh = reinterpret_cast<const R *>(a.uhat)[i];
+    const R gam = (R)bx.gamma;
+    const R V = ri.w / rho;
+    R4 r0;
+    r0.x = ri.x; r0.y = ri.y; r0.z = ri.z; r0.w = V;
+    reinterpret_cast<R4 *>(a.hrec[0])[i] = r0;
+    R4 r2v;
+    r2v.x = rho;
+    r2v.y = (gam - (R)1) * rho * uh;
+    r2v.z = Real<R>::sqrt_(gam * (gam - (R)1) * uh);
+    r2v.w = 0;
+    reinterpret_cast<R4 *>(a.hrec[2])[i] = r2v;
+    if (COUNT) {
+        if (a.nbr_count) a.nbr_count[i] = nc;
+        if (a.nbr_hash) a.nbr_hash[i] = hs;
+    }
+}
+
+// ------------------------------------------------------ correction solve C
+// FP64 per particle from the 40 moments (layout: m0, m1[3], m2[xx xy xz yy yz
+// zz], dm0[3], dm1[3a+g], dm2[3s+g]):
+//   M = m2^-1 (cofactors), singular if |det| < 1e-30 ||m2||_F^3
+//   A = 1/(m0 - m1.M m1), B = -M m1,
+//   d_g B = -M (d_g m1 + (d_g m2) B)      (= -M d_g m1 - (d_g M) m1)
+//   d_g A = -A^2 (d_g m0 + 2 B.d_g m1 + B.(d_g m2) B)
+// out: A, B[3], dA[3], dB[9] (dB[3a+g] = d_g B^a).
+__device__ bool crk_solve(const double *m, double *out)
+{
+    const double a00 = m[4], a01 = m[5], a02 = m[6], a11 = m[7], a12 = m[8], a22 = m[9];
+    const double c00 = a11 * a22 - a12 * a12;
+    const double c01 = a12 * a02 - a01 * a22;
+    const double c02 = a01 * a12 - a11 * a02;
+    const double c11 = a00 * a22 - a02 * a02;
+    const double c12 = a01 * a02 - a00 * a12;
+    const double c22 = a00 * a11 - a01 * a01;
+    const double det = a00 * c00 + a01 * c01 + a02 * c02;
+    const double fro = sqrt(a00 * a00 + a11 * a11 + a22 * a22 + 2.0 * (a01 * a01 + a02 * a02 + a12 * a12));
+    if (!(fabs(det) >= 1e-30 * fro * fro * fro) || !(fro > 0.0)) return false;
+    const double id = 1.0 / det;
+    const double M[3][3] = {{c00 * id, c01 * id, c02 * id},
+                            {c01 * id, c11 * id, c12 * id},
+                            {c02 * id, c12 * id, c22 * id}};
+    const double m1[3] = {m[1], m[2], m[3]};
+    double B[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) B[a] = -(M[a][0] * m1[0] + M[a][1] * m1[1] + M[a][2] * m1[2]);
+    const double A = 1.0 / (m[0] + B[0] * m1[0] + B[1] * m1[1] + B[2] * m1[2]);
+    out[0] = A;
+    out[1] = B[0]; out[2] = B[1]; out[3] = B[2];
+#pragma unroll
+    for (int g = 0; g < 3; ++g) {
+        const double dm0 = m[10 + g];
+        const double dm1[3] = {m[13 + g], m[16 + g], m[19 + g]};
+        const double s0 = m[22 + g], s1 = m[25 + g], s2 = m[28 + g], s3 = m[31 + g], s4 = m[34 + g],
+                     s5 = m[37 + g];
+        // w = (d_g m2) B
+        const double w0 = s0 * B[0] + s1 * B[1] + s2 * B[2];
+        const double w1 = s1 * B[0] + s3 * B[1] + s4 * B[2];
+        const double w2 = s2 * B[0] + s4 * B[1] + s5 * B[2];
+        const double y0 = dm1[0] + w0, y1 = dm1[1] + w1, y2 = dm1[2] + w2;
+#pragma unroll
+        for (int a = 0; a < 3; ++a) out[7 + 3 * a + g] = -(M[a][0] * y0 + M[a][1] * y1 + M[a][2] * y2);
+        const double bdm1 = B[0] * dm1[0] + B[1] * dm1[1] + B[2] * dm1[2];
+        const double bw = B[0] * w0 + B[1] * w1 + B[2] * w2;
+        out[4 + g] = -A * A * (dm0 + 2.0 * bdm1 + bw);
+    }
+    return true;
+}
+
+// ------------------------------------------------------------- moments M
+// Sums over N_i + {i} with W_ij = W(r, h_i), x = x_i - x_j, V_j volumes:
+//   m0 += V W, m1^a += V x^a W, m2^ab += V x^a x^b W,
+//   d_g m0 += V d_gW, d_g m1^a += V (x^a d_gW + delta_ag W),
+//   d_g m2^ab += V (x^a x^b d_gW + (delta_ag x^b + delta_bg x^a) W)
+// then the FP64 correction solve; writes hrec2.w = A and hrec3..6.
+template <typename R, int CAP>
+__global__ void __launch_bounds__(CAP) moments_k(PassArgs a)
+{
+    using R4 = Vec4<R>;
+    const int I = blockIdx.x;
+    if (a.lv.species[I] != CRK_GAS) return;
+    __shared__ R4 tile[CAP];
+    const R4 *__restrict__ rec0 = reinterpret_cast<const R4 *>(a.hrec[0]);
+    const uint32_t s0 = a.lv.start[I], cnt = a.lv.count[I];
+    const BoxDev bx = a.boxes[a.lv.slot[I]];
+    const R L = (R)bx.L, hL = (R)(0.5 * bx.L);
+    const uint32_t t = threadIdx.x;
+    const bool act = t < cnt;
+    const uint32_t i = s0 + (act ? t : 0u);
+    const R4 ri = rec0[i];
+    const double H64 = 2.0 * a.s.h[i];
+    const R H = (R)H64;
+    const R H2 = Real<R>::mixed ? H * H : (R)__dmul_rn(H64, H64);
+    const R invH = (R)1 / H;
+    const R invH2 = invH * invH;
+    const R cW = (R)kWn * invH2 * invH;
+    const R cG = (R)kGn * invH2 * invH2 * invH;
+    R m0 = 0, m1[3] = {0, 0, 0}, m2[6] = {0, 0, 0, 0, 0, 0};
+    R dm0[3] = {0, 0, 0}, dm1[9], dm2[18];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) dm1[k] = 0;
+#pragma unroll
+    for (int k = 0; k < 18; ++k) dm2[k] = 0;
+    for (uint32_t p = a.hrow[I]; p < a.hrow[I + 1]; ++p) {
+        const uint32_t J = a.hcol[p];
+        const uint32_t sJ = a.lv.start[J], cJ = a.lv.count[J];
+        __syncthreads();
+        if (t < cJ) tile[t] = rec0[sJ + t];
+        __syncthreads();
+        const Frame<R> f = make_frame<R>(a.lv, I, (int)J, bx.L, ri.x, ri.y, ri.z);
+        for (uint32_t j = 0; j < cJ; ++j) {
+            const R4 rj = tile[j];
+            R dx, dy, dz;
+            displacement(f, rj, L, hL, dx, dy, dz);
+            const R r2 = Real<R>::r2(dx, dy, dz);
+            if (!(r2 < H2)) continue;
+            const R x[3] = {-dx, -dy, -dz};
+            R W, g;
+            kernel_wg(Real<R>::sqrt_(r2), invH, cW, cG, W, g);
+            const R VW = rj.w * W;
+            const R Vg = rj.w * g;
+            const R VWx[3] = {VW * x[0], VW * x[1], VW * x[2]};
+            const R dW[3] = {Vg * x[0], Vg * x[1], Vg * x[2]};
+            const R xx[6] = {x[0] * x[0], x[0] * x[1], x[0] * x[2], x[1] * x[1], x[1] * x[2], x[2] * x[2]};
+            m0 += VW;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) m1[c] += VWx[c];
+#pragma unroll
+            for (int s = 0; s < 6; ++s) m2[s] += VW * xx[s];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) dm0[c] += dW[c];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) dm1[3 * c + q] += x[c] * dW[q] + (c == q ? VW : (R)0);
+            // packed (ab): 0 xx, 1 xy, 2 xz, 3 yy, 4 yz, 5 zz
+            constexpr int SA[6] = {0, 0, 0, 1, 1, 2};
+            constexpr int SB[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+            for (int s = 0; s < 6; ++s)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    R v = xx[s] * dW[q];
+                    if (SA[s] == q) v += VWx[SB[s]];
+                    if (SB[s] == q) v += VWx[SA[s]];
+                    dm2[3 * s + q] += v;
+                }
+        }
+    }
+    if (!act) return;
+    double m[40];
+    m[0] = (double)m0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) m[1 + c] = (double)m1[c];
+#pragma unroll
+    for (int s = 0; s < 6; ++s) m[4 + s] = (double)m2[s];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) m[10 + c] = (double)dm0[c];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) m[13 + k] = (double)dm1[k];
+#pragma unroll
+    for (int k = 0; k < 18; ++k) m[22 + k] = (double)dm2[k];
+    double o[16];
+    if (!crk_solve(m, o)) {
+#pragma unroll
+        for (int k = 0; k < 16; ++k) o[k] = 0.0;
+        set_error(a.err, CRK_ESINGULAR, a.s.id[i]);
+    }
+    R4 *rec2 = reinterpret_cast<R4 *>(a.hrec[2]);
+    R4 r2v = rec2[i];
+    r2v.w = (R)o[0];
+    rec2[i] = r2v;
+    R4 v3, v4, v5, v6;
+    v3.x = (R)o[1]; v3.y = (R)o[2]; v3.z = (R)o[3]; v3.w = (R)o[4];
+    v4.x = (R)o[5]; v4.y = (R)o[6]; v4.z = (R)o[7]; v4.w = (R)o[8];
+    v5.x = (R)o[9]; v5.y = (R)o[10]; v5.z = (R)o[11]; v5.w = (R)o[12];
+    v6.x = (R)o[13]; v6.y = (R)o[14]; v6.z = (R)o[15]; v6.w = 0;
+    reinterpret_cast<R4 *>(a.hrec[3])[i] = v3;
+    reinterpret_cast<R4 *>(a.hrec[4])[i] = v4;
+    reinterpret_cast<R4 *>(a.hrec[5])[i] = v5;
+    reinterpret_cast<R4 *>(a.hrec[6])[i] = v6;
+}
+
+// Hydro state of one particle, unpacked from its 7 records.
+template <typename R>
+struct HState {
+    R px, py, pz, V;     // position (record frame), volume
+    R vx, vy, vz, h;     // predicted velocity, smoothing length
+    R rho, P, c, A;
+    R B[3], dA[3], dB[9];
+};
+
+template <typename R>
+__device__ __forceinline__ void unpack_hstate(const Vec4<R> r[7], HState<R> &s)
+{
+    s.px = r[0].x; s.py = r[0].y; s.pz = r[0].z; s.V = r[0].w;
+    s.vx = r[1].x; s.vy = r[1].y; s.vz = r[1].z; s.h = r[1].w;
+    s.rho = r[2].x; s.P = r[2].y; s.c = r[2].z; s.A = r[2].w;
+    s.B[0] = r[3].x; s.B[1] = r[3].y; s.B[2] = r[3].z; s.dA[0] = r[3].w;
+    s.dA[1] = r[4].x; s.dA[2] = r[4].y; s.dB[0] = r[4].z; s.dB[1] = r[4].w;
+    s.dB[2] = r[5].x; s.dB[3] = r[5].y; s.dB[4] = r[5].z; s.dB[5] = r[5].w;
+    s.dB[6] = r[6].x; s.dB[7] = r[6].y; s.dB[8] = r[6].z;
+}
+
+// Corrected kernel gradient of particle s at separation x = x_s - x_other:
+//   d_g W^R = A (1 + B.x) g x^g + d_gA (1 + B.x) W + A (sum_a d_gB^a x^a + B^g) W
+template <typename R>
+__device__ __forceinline__ void corrected_grad(const HState<R> &s, const R x[3], R W, R g, R out[3])
+{
+    const R lin = (R)1 + s.B[0] * x[0] + s.B[1] * x[1] + s.B[2] * x[2];
+    const R Alg = s.A * lin * g;
+    const R lW = lin * W;
+    const R AW = s.A * W;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const R dBx = s.dB[q] * x[0] + s.dB[3 + q] * x[1] + s.dB[6 + q] * x[2];
+        out[q] = Alg * x[q] + s.dA[q] * lW + AW * (dBx + s.B[q]);
+    }
+}
+
+// --------------------------------------------------------------- hydro H
+// Over the hydro pair set (r < H_i or r < H_j, j != i):
+//   F_ij = -1/2 V_i V_j (P_i + P_j + Q_i + Q_j) (dW^R_ij - dW^R_ji)
+//   Q = rho (-alpha c mu + beta mu^2), mu = min(0, h v_ij.x_ij / (r^2 + eps^2 h^2))
+//   m_i a_i = sum F_ij,  m_i du_i = -1/2 sum F_ij . v_ij
+template <typename R, int CAP>
+__global__ void __launch_bounds__(CAP) hydro_k(PassArgs a)
+{
+    using R4 = Vec4<R>;
+    const int I = blockIdx.x;
+    if (a.lv.species[I] != CRK_GAS) return;
+    __shared__ R4 tile[7][CAP];
+    const uint32_t s0 = a.lv.start[I], cnt = a.lv.count[I];
+    const BoxDev bx = a.boxes[a.lv.slot[I]];
+    const R L = (R)bx.L, hL = (R)(0.5 * bx.L);
+    const R alpha = (R)bx.av_alpha, beta = (R)bx.av_beta, eps2 = (R)bx.av_eps2;
+    const uint32_t t = threadIdx.x;
+    const bool act = t < cnt;
+    const uint32_t i = s0 + (act ? t : 0u);
+    HState<R> si;
+    {
+        R4 r[7];
+#pragma unroll
+        for (int k = 0; k < 7; ++k) r[k] = reinterpret_cast<const R4 *>(a.hrec[k])[i];
+        unpack_hstate(r, si);
+    }
+    const R Hi = (R)2 * si.h;
+    const R H2i = Hi * Hi;
+    const R invHi = (R)1 / Hi;
+    const R cWi = (R)kWn * invHi * invHi * invHi;
+    const R cGi = (R)kGn * invHi * invHi * invHi * invHi * invHi;
+    const R hi2e = eps2 * si.h * si.h;
+    R ax = 0, ay = 0, az = 0, du = 0;
+    for (uint32_t p = a.hrow[I]; p < a.hrow[I + 1]; ++p) {
+        const uint32_t J = a.hcol[p];
+        const uint32_t sJ = a.lv.start[J], cJ = a.lv.count[J];
+        __syncthreads();
+        if (t < cJ) {
+#pragma unroll
+            for (int k = 0; k < 7; ++k) tile[k][t] = reinterpret_cast<const R4 *>(a.hrec[k])[sJ + t];
+        }
+        __syncthreads();
+        const Frame<R> f = make_frame<R>(a.lv, I, (int)J, bx.L, si.px, si.py, si.pz);
+        for (uint32_t j = 0; j < cJ; ++j) {
+            const R4 rj0 = tile[0][j];
+            const R4 rj1 = tile[1][j];
+            R dx, dy, dz;
+            displacement(f, rj0, L, hL, dx, dy, dz);
+            const R r2 = Real<R>::r2(dx, dy, dz);
+            const R Hj = (R)2 * rj1.w;
+            const R H2j = Hj * Hj;
+            if (!(r2 < H2i || r2 < H2j)) continue;
+            if (J == (uint32_t)I && j == t) continue;
+            HState<R> sj;
+            {
+                R4 r[7];
+                r[0] = rj0;
+                r[1] = rj1;
+#pragma unroll
+                for (int k = 2; k < 7; ++k) r[k] = tile[k][j];
+                unpack_hstate(r, sj);
+            }
+            const R x[3] = {-dx, -dy, -dz};  // x_ij = x_i - x_j
+            const R xm[3] = {dx, dy, dz};    // x_ji
+            const R r = Real<R>::sqrt_(r2);
+            R Wi, gi, Wj, gj;
+            kernel_wg(r, invHi, cWi, cGi, Wi, gi);
+            const R invHj = (R)1 / Hj;
+            const R invHj2 = invHj * invHj;
+            kernel_wg(r, invHj, (R)kWn * invHj2 * invHj, (R)kGn * invHj2 * invHj2 * invHj, Wj, gj);
+            R dWi[3], dWj[3];
+            corrected_grad(si, x, Wi, gi, dWi);
+            corrected_grad(sj, xm, Wj, gj, dWj);
+            const R vxij = si.vx - sj.vx, vyij = si.vy - sj.vy, vzij = si.vz - sj.vz;
+            const R vdx = vxij * x[0] + vyij * x[1] + vzij * x[2];
+            R Q = 0;
+            if (vdx < (R)0) {
+                const R mui = si.h * vdx / (r2 + hi2e);
+                const R muj = sj.h * vdx / (r2 + eps2 * sj.h * sj.h);
+                Q = si.rho * (-alpha * si.c * mui + beta * mui * mui) +
+                    sj.rho * (-alpha * sj.c * muj + beta * muj * muj);
+            }
+            const R pre = (R)(-0.5) * si.V * sj.V * (si.P + sj.P + Q);
+            const R Fx = pre * (dWi[0] - dWj[0]);
+            const R Fy = pre * (dWi[1] - dWj[1]);
+            const R Fz = pre * (dWi[2] - dWj[2]);
+            ax += Fx;
+            ay += Fy;
+            az += Fz;
+            du += Fx * vxij + Fy * vyij + Fz * vzij;
+        }
+    }
+    if (!act) return;
+    const R mi = reinterpret_cast<const R4 *>(a.pm)[i].w;
+    R4 o;
+    o.x = ax / mi;
+    o.y = ay / mi;
+    o.z = az / mi;
+    o.w = (R)(-0.5) * du / mi;
+    reinterpret_cast<R4 *>(a.acc_h)[i] = o;
+}
+
+// ------------------------------------------------------------- gravity G
+// a_i = sum_{j != i, r < r_cut} -G m_j x_ij (r^2 + eps^2)^{-3/2} S(r),
+// S(r) = erfc(r / 2r_s) + r / (sqrt(pi) r_s) exp(-r^2 / 4 r_s^2).
+template <typename R>
+__device__ __forceinline__ R split_S(R r, R inv2rs)
+{
+    if (Real<R>::mixed) {
+        const float u = (float)r * (float)inv2rs;
+        const float tt = __frcp_rn(fmaf(kAsP, u, 1.0f));
+        const float poly = tt * (kAs1 + tt * (kAs2 + tt * (kAs3 + tt * (kAs4 + tt * kAs5))));
+        const float e = __expf(-u * u);
+        return (R)(e * (poly + (float)kTwoOverSqrtPi * u));
+    } else {
+        const double u = (double)r * (double)inv2rs;
+        return (R)(erfc(u) + kTwoOverSqrtPi * u * exp(-u * u));
+    }
+}
+
+template <typename R, int CAP, bool COUNT>
+__global__ void __launch_bounds__(CAP) gravity_k(PassArgs a)
+{
+    using R4 = Vec4<R>;
+    const int I = blockIdx.x;
+    __shared__ R4 tile[CAP];
+    const R4 *__restrict__ pm = reinterpret_cast<const R4 *>(a.pm);
+    const uint32_t s0 = a.lv.start[I], cnt = a.lv.count[I];
+    const BoxDev bx = a.boxes[a.lv.slot[I]];
+    const R L = (R)bx.L, hL = (R)(0.5 * bx.L);
+    const uint32_t t = threadIdx.x;
+    const bool act = t < cnt;
+    const uint32_t i = s0 + (act ? t : 0u);
+    const R4 ri = pm[i];
+    const double rc2x = __dmul_rn(bx.r_cut, bx.r_cut);
+    const R rc = (R)bx.r_cut;
+    const R rc2 = Real<R>::mixed ? rc * rc : (R)rc2x;
+    const R e2 = (R)(bx.eps_soft * bx.eps_soft);
+    const R inv2rs = (R)(0.5 / bx.r_split);
+    const R G = (R)bx.G;
+    R ax = 0, ay = 0, az = 0;
+    int nc = 0;
+    uint64_t hs = 0;
+    for (uint32_t p = a.grow[I]; p < a.grow[I + 1]; ++p) {
+        const uint32_t J = a.gcol[p];
+        const uint32_t sJ = a.lv.start[J], cJ = a.lv.count[J];
+        __syncthreads();
+        if (t < cJ) tile[t] = pm[sJ + t];
+        __syncthreads();
+        const Frame<R> f = make_frame<R>(a.lv, I, (int)J, bx.L, ri.x, ri.y, ri.z);
+        const R gb = Real<R>::mixed ? (R)guard_band((float)rc, (float)f.mag) : (R)0;
+        for (uint32_t j = 0; j < cJ; ++j) {
+            const R4 rj = tile[j];
+            R dx, dy, dz;
+            displacement(f, rj, L, hL, dx, dy, dz);
+            const R r2 = Real<R>::r2(dx, dy, dz);
+            bool in = r2 < rc2;
+            if (Real<R>::mixed && fabs(r2 - rc2) <= gb) in = exact_lt(a.s, i, sJ + j, bx.L, rc2x);
+            if (!in || (J == (uint32_t)I && j == t)) continue;
+            const R r = Real<R>::sqrt_(r2);
+            const R S = split_S<R>(r, inv2rs);
+            const R s2 = r2 + e2;
+            R inv3;
+            if (Real<R>::mixed) {
+                const float is = rsqrtf((float)s2);
+                inv3 = (R)(is * is * is);
+            } else {
+                inv3 = (R)1 / (s2 * Real<R>::sqrt_(s2));
+            }
+            const R fr = G * rj.w * S * inv3;   // a_i += fr * (x_j - x_i)
+            ax += fr * dx;
+            ay += fr * dy;
+            az += fr * dz;
+            if (COUNT) {
+                ++nc;
+                hs += mix64((uint64_t)a.s.id[sJ + j]);
+            }
+        }
+    }
+    if (!act) return;
+    R4 o;
+    o.x = ax; o.y = ay; o.z = az; o.w = 0;
+    reinterpret_cast<R4 *>(a.acc_g)[i] = o;
+    if (COUNT) {
+        if (a.grav_count) a.grav_count[i] = nc;
+        if (a.grav_hash) a.grav_hash[i] = hs;
+    }
+}
+
+inline unsigned nblocks(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+template <int CAP>
+void density_dispatch(const PassArgs &a, int mixed, bool count, cudaStream_t st)
+{
+    if (mixed) {
+        if (count) density_k<float, CAP, true><<<a.nleaf, CAP, 0, st>>>(a);
+        else density_k<float, CAP, false><<<a.nleaf, CAP, 0, st>>>(a);
+    } else {
+        if (count) density_k<double, CAP, true><<<a.nleaf, CAP, 0, st>>>(a);
+        else density_k<double, CAP, false><<<a.nleaf, CAP, 0, st>>>(a);
+    }
+}
+
+template <int CAP>
+void gravity_dispatch(const PassArgs &a, int mixed, bool count, cudaStream_t st)
+{
+    if (mixed) {
+        if (count) gravity_k<float, CAP, true><<<a.nleaf, CAP, 0, st>>>(a);
+        else gravity_k<float, CAP, false><<<a.nleaf, CAP, 0, st>>>(a);
+    } else {
+        if (count) gravity_k<double, CAP, true><<<a.nleaf, CAP, 0, st>>>(a);
+        else gravity_k<double, CAP, false><<<a.nleaf, CAP, 0, st>>>(a);
+    }
+}
+
+}  // namespace
+
+void launch_records(const PassArgs &a, int mixed, cudaStream_t st)
+{
+    if (a.n <= 0) return;
+    if (mixed) records_k<float><<<nblocks(a.n, 256), 256, 0, st>>>(a);
+    else records_k<double><<<nblocks(a.n, 256), 256, 0, st>>>(a);
+    note_launches(1);
+}
+
+void launch_density(const PassArgs &a, int mixed, int cap, bool count, cudaStream_t st)
+{
+    if (a.nleaf <= 0) return;
+    if (cap == 32) density_dispatch<32>(a, mixed, count, st);
+    else if (cap == 64) density_dispatch<64>(a, mixed, count, st);
+    else density_dispatch<128>(a, mixed, count, st);
+    note_launches(1);
+}
+
+void launch_moments(const PassArgs &a, int mixed, int cap, cudaStream_t st)
+{
+    if (a.nleaf <= 0) return;
+#define CRK_MOM(C)                                                        \
+    if (mixed) moments_k<float, C><<<a.nleaf, C, 0, st>>>(a);           \
+    else moments_k<double, C><<<a.nleaf, C, 0, st>>>(a);
+    if (cap == 32) { CRK_MOM(32) }
+    else if (cap == 64) { CRK_MOM(64) }
+    else { CRK_MOM(128) }
+    note_launches(1);
+#undef CRK_MOM
+}
+
+void launch_hydro(const PassArgs &a, int mixed, int cap, cudaStream_t st)
+{
+    if (a.nleaf <= 0) return;
+#define CRK_HYD(C)                                                        \
+    if (mixed) hydro_k<float, C><<<a.nleaf, C, 0, st>>>(a);             \
+    else hydro_k<double, C><<<a.nleaf, C, 0, st>>>(a);
+    if (cap == 32) { CRK_HYD(32) }
+    else if (cap == 64) { CRK_HYD(64) }
+    else { CRK_HYD(128) }
+    note_launches(1);
+#undef CRK_HYD
+}
+
+void launch_gravity(const PassArgs &a, int mixed, int cap, bool count, cudaStream_t st)
+{
+    if (a.nleaf <= 0) return;
+    if (cap == 32) gravity_dispatch<32>(a, mixed, count, st);
+    else if (cap == 64) gravity_dispatch<64>(a, mixed, count, st);
+    else gravity_dispatch<128>(a, mixed, count, st);
+    note_launches(1);
+}
+
+}  // namespace crk

@@ -1,0 +1,115 @@
+// Internal definition of the solver handle shared by the C ABI (crk_api.cpp)
+// and the service (service.cpp).  Not part of the public ABI.
+#pragma once
+
+#include "crk_internal.h"
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+namespace crk {
+
+int fail(int code, const char *fmt, ...);
+
+#define CK(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return ::crk::fail(e_ == cudaErrorMemoryAllocation ? CRK_ENOMEM : CRK_ECUDA, \
+                               "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),  \
+                               __FILE__, __LINE__);                                     \
+    } while (0)
+
+#define RET(call)                    \
+    do {                             \
+        int r_ = (call);             \
+        if (r_ != CRK_OK) return r_; \
+    } while (0)
+
+// A device buffer that only grows.
+struct DBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    int ensure(size_t b);
+    int ensure_keep(size_t b, size_t keep, cudaStream_t st);
+    int ensure_impl(size_t b);
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <typename T> T *as() const { return static_cast<T *>(p); }
+};
+
+enum Phase { PH_TREE, PH_PAIRS, PH_D, PH_M, PH_H, PH_G, PH_KDK, PH_KICK, PH_N };
+
+}  // namespace crk
+
+// The opaque handle of include/crk.h.
+struct crk_sim {
+    using DBuf = crk::DBuf;
+    using State = crk::State;
+    using Leaves = crk::Leaves;
+    using Nodes = crk::Nodes;
+    using BoxDev = crk::BoxDev;
+    crk_params prm{};
+    cudaStream_t st = nullptr;
+    int device = 0;
+    bool mixed = true;
+    int cap = 64;
+    int64_t n = 0;
+    int nbox = 0;
+    int slot_bits = 0;
+    std::vector<BoxDev> boxes;
+    std::vector<int64_t> box_count;
+    bool have_forces = false;
+    int64_t n_dead = 0;      // particles of removed pool slots, sorted last and dropped next step
+    int64_t cap_n = 0;       // particles the per-particle buffers hold
+
+    // device memory
+    DBuf boxes_d;
+    DBuf stA[16], stB[16];  // state arrays, double-buffered
+    State sa{}, sb{};
+    DBuf keys, keys_alt, vals, vals_alt, counts, scan_tmp, flags, flag_scan, scalars;
+    DBuf lv_u32[3], lv_sp, lv_c[3], lv_e[3], lv_h;
+    DBuf nd_f[7], nd_slot;
+    DBuf hrow, grow, hcnt, gcnt, hcol, gcol;
+    DBuf pm, hrec[7], uhat, acc_h, acc_g;
+    DBuf nbrc, nbrh, gravc, gravh;
+    DBuf err, nfloor, partial, sums;
+    DBuf staging, in_stage;
+    Leaves lv{};
+    Nodes nd{};
+    int nleaf = 0;
+    int64_t npair_h = 0, npair_g = 0;
+    uint32_t *host_scalars = nullptr;  // pinned: [0] nleaf, [1] hydro pairs, [2] gravity pairs
+    int *host_err = nullptr;           // pinned: err[0..1]
+
+    // timing
+    bool timing = false;
+    cudaEvent_t ev[crk::PH_N][2] = {};
+    cudaEvent_t ev_all[2] = {};
+    double acc_ms[crk::PH_N] = {};
+    bool recorded[crk::PH_N] = {};
+    double total_ms = 0;
+    int64_t calls = 0;
+    int64_t launches = 0;
+};
+
+
+namespace crk {
+
+// Pool operations used by the service: a handle whose boxes are slots that
+// jobs enter and leave between steps.
+int pool_init(crk_sim *s, int max_slots);
+int pool_add(crk_sim *s, int slot, const crk_physics &phys, int64_t n, const double *pos,
+             const double *vel, const double *mass, const double *u, const double *h,
+             const uint8_t *species);
+int pool_extract(crk_sim *s, int slot, int64_t n, double *pos, double *vel, double *u);
+void pool_remove(crk_sim *s, int slot, int64_t n);
+int pool_step(crk_sim *s, const double *dt_per_slot);
+size_t pool_bytes_per_particle(const crk_sim *s);
+
+}  // namespace crk

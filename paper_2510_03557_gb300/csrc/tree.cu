@@ -1,0 +1,543 @@
+// Spatial structure of the short-range solver (paper Sec. IV-B1, "GPU Tree
+// Solver"): particles are binned by a Morton key, cut into base leaves of at
+// most leaf_cap particles that never straddle a chaining-mesh bin, and the
+// leaf-pair interaction lists are produced from conservative bounding-box
+// gaps.  Only the base leaves are kept, as in the paper; a throw-away implicit
+// binary hierarchy over the Morton-ordered leaves serves the pair search.
+//
+// Every kernel here is memory-bound: coalesced SoA loads, one pass per
+// array, grid sizes in multiples of the SM count where the work is flat.
+#include "crk_internal.h"
+
+#include <cfloat>
+
+namespace crk {
+
+namespace {
+
+constexpr int kT = 256;            // threads per block for flat kernels
+constexpr int kItems = 16;         // items per thread in scan / sort tiles
+constexpr int kTile = kT * kItems; // 4096
+
+__device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v)
+{
+    const uint32_t lane = lane_id();
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= (uint32_t)o) v += t;
+    }
+    return v;
+}
+
+// Exclusive block scan of one value per thread (blockDim.x == kT or 1024).
+template <int NT>
+__device__ uint32_t block_excl_scan(uint32_t v, uint32_t *total)
+{
+    __shared__ uint32_t wsum[NT / 32];
+    const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
+    uint32_t inc = warp_incl_scan(v);
+    if (lane == 31) wsum[w] = inc;
+    __syncthreads();
+    if (w == 0) {
+        uint32_t s = (lane < NT / 32) ? wsum[lane] : 0u;
+        uint32_t si = warp_incl_scan(s);
+        if (lane < NT / 32) wsum[lane] = si - s;
+        if (lane == NT / 32 - 1 && total) *total = si;
+    }
+    __syncthreads();
+    uint32_t r = inc - v + wsum[w];
+    __syncthreads();
+    return r;
+}
+
+__global__ void scan_reduce_k(const uint32_t *__restrict__ in, int64_t n, uint32_t *part)
+{
+    const int64_t base = (int64_t)blockIdx.x * kTile;
+    uint32_t s = 0;
+    for (int i = threadIdx.x; i < kTile; i += kT) {
+        int64_t k = base + i;
+        if (k < n) s += in[k];
+    }
+    __shared__ uint32_t tot;
+    block_excl_scan<kT>(s, &tot);
+    __syncthreads();
+    if (threadIdx.x == 0) part[blockIdx.x] = tot;
+}
+
+__global__ void scan_partials_k(uint32_t *part, int64_t nb, uint32_t *total)
+{
+    __shared__ uint32_t chunk_total;
+    uint32_t running = 0;
+    for (int64_t c = 0; c < nb; c += 1024) {
+        int64_t k = c + threadIdx.x;
+        uint32_t v = (k < nb) ? part[k] : 0u;
+        uint32_t ex = block_excl_scan<1024>(v, &chunk_total);
+        __syncthreads();
+        if (k < nb) part[k] = running + ex;
+        running += chunk_total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && total) *total = running;
+}
+
+__global__ void scan_down_k(const uint32_t *in, uint32_t *out, int64_t n, const uint32_t *part)
+{
+    const int64_t base = (int64_t)blockIdx.x * kTile + (int64_t)threadIdx.x * kItems;
+    uint32_t v[kItems];
+    uint32_t s = 0;
+#pragma unroll
+    for (int t = 0; t < kItems; ++t) {
+        int64_t k = base + t;
+        v[t] = (k < n) ? in[k] : 0u;
+        s += v[t];
+    }
+    uint32_t ex = block_excl_scan<kT>(s, nullptr) + part[blockIdx.x];
+#pragma unroll
+    for (int t = 0; t < kItems; ++t) {
+        int64_t k = base + t;
+        if (k < n) out[k] = ex;
+        ex += v[t];
+    }
+}
+
+// ---------------------------------------------------------------- radix sort
+__global__ void radix_hist_k(const uint64_t *__restrict__ keys, int64_t n, int shift,
+                             uint32_t *counts, int64_t nb)
+{
+    __shared__ uint32_t hist[256];
+    hist[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kTile;
+    for (int i = threadIdx.x; i < kTile; i += kT) {
+        int64_t k = base + i;
+        bool valid = k < n;
+        uint32_t d = valid ? (uint32_t)((keys[k] >> shift) & 255u) : 256u;
+        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        if (valid && lane_id() == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&hist[d], __popc(peers));
+    }
+    __syncthreads();
+    counts[(int64_t)threadIdx.x * nb + blockIdx.x] = hist[threadIdx.x];
+}
+
+// Stable scatter: items of a tile are ranked in order (round by round, warp
+// by warp, lane by lane) so equal digits keep their input order.
+__global__ void radix_scatter_k(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+                                uint64_t *kout, uint32_t *vout, int64_t n, int shift,
+                                const uint32_t *__restrict__ offs, int64_t nb)
+{
+    __shared__ uint32_t run[256];
+    __shared__ uint32_t wcnt[kT / 32][256];
+    const uint32_t tid = threadIdx.x, w = tid >> 5, lane = lane_id();
+    run[tid] = offs[(int64_t)tid * nb + blockIdx.x];
+    const uint32_t lt = (1u << lane) - 1u;
+    const int64_t base = (int64_t)blockIdx.x * kTile;
+    for (int r = 0; r < kItems; ++r) {
+#pragma unroll
+        for (int q = 0; q < kT / 32; ++q) wcnt[q][tid] = 0;
+        __syncthreads();
+        int64_t k = base + (int64_t)r * kT + tid;
+        bool valid = k < n;
+        uint64_t key = valid ? kin[k] : 0ull;
+        uint32_t val = valid ? vin[k] : 0u;
+        uint32_t d = valid ? (uint32_t)((key >> shift) & 255u) : 256u;
+        uint32_t peers = __match_any_sync(0xffffffffu, d);
+        uint32_t rank = __popc(peers & lt);
+        if (valid && lane == (uint32_t)(__ffs(peers) - 1)) wcnt[w][d] = __popc(peers);
+        __syncthreads();
+        {
+            uint32_t running = run[tid];
+#pragma unroll
+            for (int q = 0; q < kT / 32; ++q) {
+                uint32_t c = wcnt[q][tid];
+                wcnt[q][tid] = running;
+                running += c;
+            }
+            run[tid] = running;
+        }
+        __syncthreads();
+        if (valid) {
+            uint32_t pos = wcnt[w][d] + rank;
+            kout[pos] = key;
+            vout[pos] = val;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- keys
+__device__ __forceinline__ uint64_t spread3(uint64_t v)
+{
+    v &= 0x1fffffull;
+    v = (v | v << 32) & 0x1f00000000ffffull;
+    v = (v | v << 16) & 0x1f0000ff0000ffull;
+    v = (v | v << 8) & 0x100f00f00f00f00full;
+    v = (v | v << 4) & 0x10c30c30c30c30c3ull;
+    v = (v | v << 2) & 0x1249249249249249ull;
+    return v;
+}
+
+__device__ __forceinline__ uint32_t cell21(double x, double L)
+{
+    double c = x / L * 2097152.0;
+    if (!(c >= 0.0)) c = 0.0;
+    uint32_t ci = (uint32_t)c;
+    return ci > 2097151u ? 2097151u : ci;
+}
+
+__global__ void morton_keys_k(State s, const BoxDev *__restrict__ boxes, int64_t n, int sb,
+                              uint64_t *keys, uint32_t *idx)
+{
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    uint32_t slot = s.slot[k];
+    if (!boxes[slot].active) {
+        keys[k] = ~0ull;
+        idx[k] = (uint32_t)k;
+        return;
+    }
+    double L = boxes[slot].L;
+    uint64_t m = spread3(cell21(s.x[k], L)) | (spread3(cell21(s.y[k], L)) << 1) |
+                 (spread3(cell21(s.z[k], L)) << 2);
+    uint64_t sp = (uint64_t)(s.species[k] & 1u);
+    uint64_t key;
+    if (sb == 0) key = (sp << 63) | m;
+    else key = ((uint64_t)slot << (64 - sb)) | (sp << (63 - sb)) | (m >> sb);
+    keys[k] = key;
+    idx[k] = (uint32_t)k;
+}
+
+__global__ void permute_k(State a, State b, const uint32_t *__restrict__ perm, int64_t n)
+{
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    uint32_t p = perm[k];
+    b.x[k] = a.x[p]; b.y[k] = a.y[p]; b.z[k] = a.z[p];
+    b.vx[k] = a.vx[p]; b.vy[k] = a.vy[p]; b.vz[k] = a.vz[p];
+    b.u[k] = a.u[p]; b.m[k] = a.m[p]; b.h[k] = a.h[p];
+    b.ax[k] = a.ax[p]; b.ay[k] = a.ay[p]; b.az[k] = a.az[p]; b.du[k] = a.du[p];
+    b.species[k] = a.species[p]; b.slot[k] = a.slot[p]; b.id[k] = a.id[p];
+}
+
+// ---------------------------------------------------------------- leaves
+__global__ void leaf_flags_k(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ slot,
+                             const BoxDev *__restrict__ boxes, int64_t n, int cap, uint32_t *flags)
+{
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int gshift = boxes[slot[k]].cm_shift;
+    const uint64_t g = keys[k] >> gshift;
+    int64_t lo = 0, hi = k;
+    while (lo < hi) {
+        int64_t mid = (lo + hi) >> 1;
+        if ((keys[mid] >> gshift) < g) lo = mid + 1;
+        else hi = mid;
+    }
+    flags[k] = ((k - lo) % cap) == 0 ? 1u : 0u;
+}
+
+__global__ void leaf_setup_k(const uint32_t *__restrict__ flags, const uint32_t *__restrict__ scan,
+                             int64_t n, uint32_t *start)
+{
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    if (flags[k]) start[scan[k]] = (uint32_t)k;
+}
+
+__global__ void leaf_count_k(Leaves lv, int nleaf, int64_t n)
+{
+    int L = blockIdx.x * blockDim.x + threadIdx.x;
+    if (L >= nleaf) return;
+    uint32_t end = (L + 1 < nleaf) ? lv.start[L + 1] : (uint32_t)n;
+    lv.count[L] = end - lv.start[L];
+}
+
+__device__ __forceinline__ double wmin(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ double wmax(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// One warp per leaf: FP64 bounds, centre, half extents (rounded up), the
+// leaf's largest kernel support, the level-0 node, and the position-mass
+// records of its particles (leaf-relative FP32 in the mixed form, absolute
+// FP64 in the plain form).
+template <int MIXED>
+__global__ void leaf_bounds_k(State s, Leaves lv, int nleaf, void *pm, Nodes nd)
+{
+    const int w = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const uint32_t lane = lane_id();
+    if (w >= nleaf) return;
+    const uint32_t s0 = lv.start[w], c = lv.count[w];
+    double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+    double hm = 0.0;
+    for (uint32_t t = lane; t < c; t += 32) {
+        uint32_t i = s0 + t;
+        double p[3] = {s.x[i], s.y[i], s.z[i]};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) { lo[a] = fmin(lo[a], p[a]); hi[a] = fmax(hi[a], p[a]); }
+        if (s.species[i] == CRK_GAS) hm = fmax(hm, 2.0 * s.h[i]);
+    }
+    double cen[3];
+    float ext[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = wmin(lo[a]);
+        hi[a] = wmax(hi[a]);
+        cen[a] = 0.5 * (lo[a] + hi[a]);
+        ext[a] = __double2float_ru(fmax(hi[a] - cen[a], cen[a] - lo[a]));
+    }
+    hm = wmax(hm);
+    if (lane == 0) {
+        lv.cx[w] = cen[0]; lv.cy[w] = cen[1]; lv.cz[w] = cen[2];
+        lv.ex[w] = ext[0]; lv.ey[w] = ext[1]; lv.ez[w] = ext[2];
+        lv.hmax[w] = __double2float_ru(hm);
+        lv.slot[w] = s.slot[s0];
+        lv.species[w] = s.species[s0];
+        nd.lox[w] = __double2float_rd(lo[0]); nd.loy[w] = __double2float_rd(lo[1]);
+        nd.loz[w] = __double2float_rd(lo[2]);
+        nd.hix[w] = __double2float_ru(hi[0]); nd.hiy[w] = __double2float_ru(hi[1]);
+        nd.hiz[w] = __double2float_ru(hi[2]);
+        nd.hmax[w] = __double2float_ru(hm);
+        nd.slot[w] = (int32_t)s.slot[s0];
+    }
+    for (uint32_t t = lane; t < c; t += 32) {
+        uint32_t i = s0 + t;
+        if (MIXED) {
+            float4 r;
+            r.x = (float)(s.x[i] - cen[0]);
+            r.y = (float)(s.y[i] - cen[1]);
+            r.z = (float)(s.z[i] - cen[2]);
+            r.w = (float)s.m[i];
+            reinterpret_cast<float4 *>(pm)[i] = r;
+        } else {
+            Vec4<double> r;
+            r.x = s.x[i]; r.y = s.y[i]; r.z = s.z[i]; r.w = s.m[i];
+            reinterpret_cast<Vec4<double> *>(pm)[i] = r;
+        }
+    }
+}
+
+__global__ void node_level_k(Nodes nd, int64_t oc, int64_t ncld, int64_t op, int64_t npar)
+{
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= npar) return;
+    int64_t c0 = oc + 2 * k, c1 = oc + 2 * k + 1;
+    float lox = nd.lox[c0], loy = nd.loy[c0], loz = nd.loz[c0];
+    float hix = nd.hix[c0], hiy = nd.hiy[c0], hiz = nd.hiz[c0];
+    float hm = nd.hmax[c0];
+    int32_t sl = nd.slot[c0];
+    if (2 * k + 1 < ncld) {
+        lox = fminf(lox, nd.lox[c1]); loy = fminf(loy, nd.loy[c1]); loz = fminf(loz, nd.loz[c1]);
+        hix = fmaxf(hix, nd.hix[c1]); hiy = fmaxf(hiy, nd.hiy[c1]); hiz = fmaxf(hiz, nd.hiz[c1]);
+        hm = fmaxf(hm, nd.hmax[c1]);
+        if (nd.slot[c1] != sl) sl = -1;
+    }
+    int64_t o = op + k;
+    nd.lox[o] = lox; nd.loy[o] = loy; nd.loz[o] = loz;
+    nd.hix[o] = hix; nd.hiy[o] = hiy; nd.hiz[o] = hiz;
+    nd.hmax[o] = hm;
+    nd.slot[o] = sl;
+}
+
+// Depth-first walk of the leaf hierarchy from leaf I, left child first, so a
+// row lists its neighbour leaves in ascending order whatever else is loaded.
+// A node is kept when its periodic box gap to I is below the pair radius R
+// (hydro: max of the two largest supports; gravity: r_cut), widened by a
+// small relative and absolute margin so FP32 rounding never drops a pair.
+template <bool FILL>
+__global__ void pair_walk_k(Nodes nd, Leaves lv, const BoxDev *__restrict__ boxes, int nleaf,
+                            int hydro, uint32_t *counts, const uint32_t *__restrict__ row,
+                            uint32_t *col)
+{
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    if (I >= nleaf) return;
+    if (hydro && lv.species[I] != CRK_GAS) {
+        if (!FILL) counts[I] = 0;
+        return;
+    }
+    const int32_t slot = (int32_t)lv.slot[I];
+    const BoxDev bx = boxes[slot];
+    const float L = (float)bx.L, hL = 0.5f * L;
+    const float cix = 0.5f * (nd.lox[I] + nd.hix[I]), ciy = 0.5f * (nd.loy[I] + nd.hiy[I]),
+                ciz = 0.5f * (nd.loz[I] + nd.hiz[I]);
+    const float eix = 0.5f * (nd.hix[I] - nd.lox[I]), eiy = 0.5f * (nd.hiy[I] - nd.loy[I]),
+                eiz = 0.5f * (nd.hiz[I] - nd.loz[I]);
+    const float RI = hydro ? lv.hmax[I] : (float)bx.r_cut;
+    uint32_t base = FILL ? row[I] : 0u;
+    uint32_t cnt = 0;
+    int2 stack[96];
+    int sp = 0;
+    stack[sp++] = make_int2(nd.levels - 1, 0);
+    while (sp > 0) {
+        int2 e = stack[--sp];
+        const int l = e.x, k = e.y;
+        const int64_t off = nd.level_off[l] + k;
+        const int32_t ns = nd.slot[off];
+        if (ns != -1 && ns != slot) continue;
+        const float nh = nd.hmax[off];
+        if (hydro && !(nh > 0.f)) continue;
+        if (ns == slot) {
+            const float R = hydro ? fmaxf(RI, nh) : RI;
+            const float Rm = R * 1.0001f + 1e-5f * L;
+            float gap2 = 0.f;
+            float d, g;
+            d = 0.5f * (nd.lox[off] + nd.hix[off]) - cix;
+            if (d >= hL) d -= L; else if (d < -hL) d += L;
+            g = fabsf(d) - eix - 0.5f * (nd.hix[off] - nd.lox[off]);
+            if (g > 0.f) gap2 += g * g;
+            d = 0.5f * (nd.loy[off] + nd.hiy[off]) - ciy;
+            if (d >= hL) d -= L; else if (d < -hL) d += L;
+            g = fabsf(d) - eiy - 0.5f * (nd.hiy[off] - nd.loy[off]);
+            if (g > 0.f) gap2 += g * g;
+            d = 0.5f * (nd.loz[off] + nd.hiz[off]) - ciz;
+            if (d >= hL) d -= L; else if (d < -hL) d += L;
+            g = fabsf(d) - eiz - 0.5f * (nd.hiz[off] - nd.loz[off]);
+            if (g > 0.f) gap2 += g * g;
+            if (gap2 >= Rm * Rm) continue;
+        }
+        if (l == 0) {
+            if (FILL) col[base + cnt] = (uint32_t)k;
+            ++cnt;
+        } else {
+            const int64_t nchild = nd.level_off[l] - nd.level_off[l - 1];
+            if ((int64_t)2 * k + 1 < nchild) stack[sp++] = make_int2(l - 1, 2 * k + 1);
+            stack[sp++] = make_int2(l - 1, 2 * k);
+        }
+    }
+    if (!FILL) counts[I] = cnt;
+}
+
+inline unsigned grid_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+}  // namespace
+
+size_t scan_tmp_words(int64_t n) { return (size_t)((n + kTile - 1) / kTile) + 1; }
+
+void scan_exclusive_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *total,
+                        uint32_t *tmp, cudaStream_t st)
+{
+    if (n <= 0) {
+        if (total) cudaMemsetAsync(total, 0, sizeof(uint32_t), st);
+        return;
+    }
+    int64_t nb = (n + kTile - 1) / kTile;
+    scan_reduce_k<<<(unsigned)nb, kT, 0, st>>>(in, n, tmp);
+    scan_partials_k<<<1, 1024, 0, st>>>(tmp, nb, total);
+    scan_down_k<<<(unsigned)nb, kT, 0, st>>>(in, out, n, tmp);
+    note_launches(3);
+}
+
+size_t radix_count_words(int64_t n) { return (size_t)256 * (size_t)((n + kTile - 1) / kTile); }
+
+void radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
+                    int64_t n, uint32_t *counts, uint32_t *scan_tmp, int first_bit, int end_bit,
+                    cudaStream_t st, uint64_t **keys_out, uint32_t **vals_out)
+{
+    uint64_t *ki = keys, *ko = keys_alt;
+    uint32_t *vi = vals, *vo = vals_alt;
+    if (n > 0) {
+        int64_t nb = (n + kTile - 1) / kTile;
+        for (int shift = first_bit; shift < end_bit; shift += 8) {
+            radix_hist_k<<<(unsigned)nb, kT, 0, st>>>(ki, n, shift, counts, nb);
+            scan_exclusive_u32(counts, counts, 256 * nb, nullptr, scan_tmp, st);
+            radix_scatter_k<<<(unsigned)nb, kT, 0, st>>>(ki, vi, ko, vo, n, shift, counts, nb);
+            note_launches(2);
+            uint64_t *tk = ki; ki = ko; ko = tk;
+            uint32_t *tv = vi; vi = vo; vo = tv;
+        }
+    }
+    *keys_out = ki;
+    *vals_out = vi;
+}
+
+void launch_morton_keys(const State &s, const BoxDev *boxes, int64_t n, int slot_bits,
+                        uint64_t *keys, uint32_t *idx, cudaStream_t st)
+{
+    if (n <= 0) return;
+    morton_keys_k<<<grid_for(n, kT), kT, 0, st>>>(s, boxes, n, slot_bits, keys, idx);
+    note_launches(1);
+}
+
+void launch_permute(const State &src, const State &dst, const uint32_t *perm, int64_t n,
+                    cudaStream_t st)
+{
+    if (n <= 0) return;
+    permute_k<<<grid_for(n, kT), kT, 0, st>>>(src, dst, perm, n);
+    note_launches(1);
+}
+
+void launch_leaf_flags(const uint64_t *keys, const State &s, const BoxDev *boxes, int64_t n,
+                       int cap, uint32_t *flags, cudaStream_t st)
+{
+    if (n <= 0) return;
+    leaf_flags_k<<<grid_for(n, kT), kT, 0, st>>>(keys, s.slot, boxes, n, cap, flags);
+    note_launches(1);
+}
+
+void launch_leaf_setup(const uint32_t *flags, const uint32_t *scan, int64_t n, int nleaf,
+                       Leaves lv, cudaStream_t st)
+{
+    if (n <= 0 || nleaf <= 0) return;
+    leaf_setup_k<<<grid_for(n, kT), kT, 0, st>>>(flags, scan, n, lv.start);
+    leaf_count_k<<<grid_for(nleaf, kT), kT, 0, st>>>(lv, nleaf, n);
+    note_launches(2);
+}
+
+void launch_leaf_bounds(const State &s, const BoxDev *boxes, Leaves lv, int nleaf, int mixed,
+                        void *pm, Nodes nd, cudaStream_t st)
+{
+    (void)boxes;
+    if (nleaf <= 0) return;
+    unsigned g = grid_for((int64_t)nleaf * 32, kT);
+    if (mixed) leaf_bounds_k<1><<<g, kT, 0, st>>>(s, lv, nleaf, pm, nd);
+    else leaf_bounds_k<0><<<g, kT, 0, st>>>(s, lv, nleaf, pm, nd);
+    note_launches(1);
+}
+
+void launch_build_nodes(Nodes &nd, int nleaf, cudaStream_t st)
+{
+    int64_t cnt = nleaf;
+    int l = 0;
+    nd.level_off[0] = 0;
+    while (cnt > 1) {
+        const int64_t np = (cnt + 1) / 2;
+        nd.level_off[l + 1] = nd.level_off[l] + cnt;
+        node_level_k<<<grid_for(np, kT), kT, 0, st>>>(nd, nd.level_off[l], cnt, nd.level_off[l + 1], np);
+        note_launches(1);
+        cnt = np;
+        ++l;
+    }
+    nd.level_off[l + 1] = nd.level_off[l] + cnt;
+    nd.levels = l + 1;
+    nd.total = nd.level_off[l + 1];
+}
+
+void launch_pair_count(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, int nleaf,
+                       int hydro, uint32_t *counts, cudaStream_t st)
+{
+    if (nleaf <= 0) return;
+    pair_walk_k<false><<<grid_for(nleaf, 128), 128, 0, st>>>(nd, lv, boxes, nleaf, hydro, counts,
+                                                               nullptr, nullptr);
+    note_launches(1);
+}
+
+void launch_pair_fill(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, int nleaf,
+                      int hydro, const uint32_t *row, uint32_t *col, cudaStream_t st)
+{
+    if (nleaf <= 0) return;
+    pair_walk_k<true><<<grid_for(nleaf, 128), 128, 0, st>>>(nd, lv, boxes, nleaf, hydro, nullptr,
+                                                              row, col);
+    note_launches(1);
+}
+
+}  // namespace crk

@@ -1,0 +1,76 @@
+"""CPU checks of the C ABI: the library builds, loads, exports every function
+include/crk.h declares, and the binding's structures have the header's
+layout.  No compute call is made (there is no GPU here)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2510_03557_gb300 import build as build_mod
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "crk.h")
+
+
+@pytest.fixture(scope="module")
+def libcrk():
+    build_mod.build()
+    from paper_2510_03557_gb300 import crk
+
+    return crk
+
+
+def _declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(crk_[a-z_]+)\s*\(", src)))
+
+
+def test_header_declares_the_abi(libcrk):
+    names = _declared_functions()
+    assert set(names) == set(libcrk.ABI)
+
+
+def test_library_exports_every_declared_symbol(libcrk):
+    L = libcrk.lib()
+    for name in _declared_functions():
+        assert hasattr(L, name), name
+    out = subprocess.run(["nm", "-D", "--defined-only", libcrk.LIB_PATH], capture_output=True,
+                         text=True, check=True).stdout
+    exported = set(re.findall(r" T (crk_[a-z_]+)", out))
+    assert set(_declared_functions()) <= exported
+
+
+def test_error_message_is_available_without_gpu(libcrk):
+    assert isinstance(libcrk.crk_last_error(), str)
+
+
+def test_struct_layouts_match_header(libcrk, tmp_path):
+    prog = tmp_path / "sizes.c"
+    prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "crk.h"\n'
+                    "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\","
+                    "sizeof(crk_physics), sizeof(crk_params), sizeof(crk_outputs),"
+                    "sizeof(crk_timings), sizeof(crk_service_params), sizeof(crk_job),"
+                    "sizeof(crk_job_result), offsetof(crk_outputs, momentum_rate),"
+                    "offsetof(crk_job, dt));return 0;}\n")
+    exe = tmp_path / "sizes"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    c = libcrk
+    want = [ctypes.sizeof(c.Physics), ctypes.sizeof(c.Params), ctypes.sizeof(c.Outputs),
+            ctypes.sizeof(c.Timings), ctypes.sizeof(c.ServiceParams), ctypes.sizeof(c.Job),
+            ctypes.sizeof(c.JobResult), c.Outputs.momentum_rate.offset, c.Job.dt.offset]
+    assert got == want
+
+
+def test_binding_rejects_mixed_memory_kinds(libcrk):
+    import numpy as np
+
+    with pytest.raises(TypeError):
+        libcrk._mem_of(libcrk.CRK_MEM_HOST, libcrk.CRK_MEM_DEVICE)
+    assert libcrk._mem_of(None, libcrk.CRK_MEM_HOST) == libcrk.CRK_MEM_HOST
+    p, m, keep = libcrk._ptr(np.zeros(4), np.float64)
+    assert m == libcrk.CRK_MEM_HOST and keep.dtype == np.float64

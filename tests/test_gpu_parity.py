@@ -1,0 +1,357 @@
+"""GPU parity of the CUDA path against the CPU oracle, through the C ABI.
+
+Bars: neighbour-set sizes and 64-bit hashes bit-exact; every floating-point
+output within relative L2 1e-10 (FP64 plain form) or 2e-4 (FP32 mixed form)
+of the oracle, where relative L2 = ||gpu - oracle||_2 / ||oracle||_2 over the
+whole array.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2510_03557_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-10, 1: 2e-4}  # CRK_FP64, CRK_MIXED
+FLOAT_OUTPUTS = ("acc", "dudt", "rho", "A", "B", "gradA", "gradB")
+ORACLE_KEY = {"acc": "acc", "dudt": "dudt", "rho": "rho", "A": "A", "B": "B", "gradA": "dA",
+              "gradB": "dB"}
+
+
+@pytest.fixture(scope="module")
+def crk():
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_2510_03557_gb300 import crk as c
+
+    return c
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / nb if nb > 0 else np.linalg.norm(a)
+
+
+def oracle_params(box_like, **kw):
+    d = dict(box_like) if isinstance(box_like, dict) else box_like.params()
+    d.update(kw)
+    return oracle.make_params(**d)
+
+
+def run_gpu(crk, s, phys, precision, leaf_cap=64, counts=True):
+    with crk.Sim(phys, leaf_cap=leaf_cap, precision=precision) as sim:
+        crk.crk_load(sim.handle, s["pos"], s["vel"], s["mass"], s["u"], s["h"], s["species"])
+        sim.n = len(s["mass"])
+        return sim.forces(counts=counts)
+
+
+def compare(out, ref, counts_ref, precision, sample=None, label=""):
+    sel = slice(None) if sample is None else sample
+    for name, (c, h) in counts_ref.items():
+        assert np.array_equal(out[name + "_count"][sel], c[sel]), f"{label} {name} counts differ"
+        assert np.array_equal(out[name + "_hash"][sel], h[sel]), f"{label} {name} hashes differ"
+    tol = TOL[precision]
+    for k in FLOAT_OUTPUTS:
+        err = rel_l2(out[k][sel], ref[ORACLE_KEY[k]][sel])
+        assert err <= tol, f"{label} {k}: relative L2 {err:.3e} > {tol:.1e}"
+
+
+def box_dict(box):
+    return dict(pos=box.pos, vel=box.vel, mass=box.mass, u=box.u, h=box.h, species=box.species)
+
+
+def oracle_counts(s, op):
+    nc, nh = oracle.neighbours(s["pos"], s["h"], s["species"], op, 0)
+    gc, gh = oracle.neighbours(s["pos"], s["h"], s["species"], op, 2)
+    return {"nbr": (nc, nh), "grav": (gc, gh)}
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_lattice_2x32_matches_oracle(crk, precision):
+    """The 2 x 32^3 jittered lattice, every output, the whole box."""
+    box = wl.jittered_lattice(32, seed=0)
+    s = box_dict(box)
+    op = oracle_params(box)
+    ref = oracle.forces(box.pos, box.vel, box.mass, box.u, box.h, box.species, op)
+    assert ref["rc"] == 0
+    out = run_gpu(crk, s, crk.box_physics(box), precision)
+    compare(out, ref, oracle_counts(s, op), precision, label="lattice")
+
+
+def _clustered(seed, n_gas=2500, n_dm=1500):
+    rng = np.random.default_rng(seed)
+    g1 = rng.uniform(0, 1, size=(n_gas // 2, 3))
+    g2 = (0.5 + 0.05 * rng.standard_normal((n_gas - n_gas // 2, 3))) % 1.0
+    dm = np.concatenate([rng.uniform(0, 1, size=(n_dm // 2, 3)),
+                         (0.3 + 0.05 * rng.standard_normal((n_dm - n_dm // 2, 3))) % 1.0])
+    pos = np.concatenate([g1, g2, dm])
+    pos[pos >= 1.0] = 0.0
+    sp = np.concatenate([np.ones(n_gas, np.uint8), np.zeros(n_dm, np.uint8)])
+    N = pos.shape[0]
+    perm = rng.permutation(N)
+    pos, sp = pos[perm], sp[perm]
+    mass = np.where(sp == 1, 1.0 / n_gas, 2.0 / n_dm) * rng.uniform(0.8, 1.2, size=N)
+    # h from a smooth field so gather sets are asymmetric (r < H_i but not H_j)
+    h = np.where(sp == 1, 0.09 + 0.04 * np.sin(5.0 * pos[:, 0]) * np.cos(3.0 * pos[:, 1]), 0.0)
+    u = np.where(sp == 1, np.exp(rng.normal(0, 0.5, size=N)), 0.0)
+    vel = 0.2 * rng.standard_normal((N, 3))
+    return dict(pos=pos, vel=vel, mass=mass, u=u, h=h, species=sp)
+
+
+@pytest.mark.parametrize("leaf_cap", [32, 64, 128])
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_clustered_variable_h_matches_oracle(crk, precision, leaf_cap):
+    """Clustered gas and DM, spatially varying h, several leaves and ragged
+    tails per bin, periodic wrap through the box faces."""
+    s = _clustered(seed=21 + leaf_cap)
+    phys = dict(box=1.0, G=1.0, gamma=5.0 / 3.0, r_cut=0.12, r_split=0.12 / 4.5, eps_soft=1e-3)
+    op = oracle.make_params(**phys)
+    ref = oracle.forces(s["pos"], s["vel"], s["mass"], s["u"], s["h"], s["species"], op)
+    assert ref["rc"] == 0
+    out = run_gpu(crk, s, crk.physics(**phys), precision, leaf_cap=leaf_cap)
+    compare(out, ref, oracle_counts(s, op), precision, label=f"clustered cap={leaf_cap}")
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_momentum_and_energy_rates_vanish(crk, precision):
+    s = _clustered(seed=5)
+    phys = dict(box=1.0, r_cut=0.12, r_split=0.12 / 4.5, eps_soft=1e-3)
+    out = run_gpu(crk, s, crk.physics(**phys), precision, counts=False)
+    ma = s["mass"][:, None] * out["acc"]
+    scale = np.abs(ma).sum()
+    rel = np.abs(out["momentum_rate"]).max() / scale
+    assert rel < (1e-13 if precision == 0 else 1e-5)
+    # the library's FP64 sum agrees with the host sum of its own outputs
+    assert np.allclose(out["momentum_rate"], ma.sum(0), rtol=0, atol=1e-9 * scale)
+
+
+def test_full_size_gaussian_field_sampled(crk):
+    """2 x 128^3 (the benchmark's workload), mixed form as benchmarked:
+    sampled particles checked one by one against the oracle."""
+    box = wl.gaussian_field_box(128, seed=1)
+    s = box_dict(box)
+    op = oracle_params(box)
+    out = run_gpu(crk, s, crk.box_physics(box), 1)
+    rng = np.random.default_rng(0)
+    gas = np.nonzero(box.species == wl.GAS)[0]
+    dm = np.nonzero(box.species == wl.DM)[0]
+    sample = np.sort(np.concatenate([rng.choice(gas, 48, replace=False), rng.choice(dm, 16, replace=False)]))
+    ref = oracle.forces(box.pos, box.vel, box.mass, box.u, box.h, box.species, op, sample=sample)
+    assert ref["rc"] == 0
+    nc, nh = oracle.neighbours(box.pos, box.h, box.species, op, 0)
+    gc, gh = oracle.neighbours(box.pos, box.h, box.species, op, 2)
+    compare(out, ref, {"nbr": (nc, nh), "grav": (gc, gh)}, 1, sample=sample, label="2x128^3")
+    # every particle has a full neighbourhood (~270 for gas, paper Sec. IV-B1)
+    assert 200 < out["nbr_count"][gas].mean() < 330
+
+
+# ------------------------------------------------------------- edge cases
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_fewer_particles_than_one_leaf_and_box_faces(crk, precision):
+    rng = np.random.default_rng(3)
+    N = 23
+    pos = 0.5 + 0.08 * rng.standard_normal((N, 3))
+    pos[0] = [0.0, 0.0, 0.0]
+    pos[1] = [np.nextafter(1.0, 0.0), 0.0, np.nextafter(1.0, 0.0)]
+    pos[2] = [0.0, np.nextafter(1.0, 0.0), 0.5]
+    pos = np.mod(pos, 1.0)
+    sp = np.array([1] * 15 + [0] * 8, np.uint8)
+    s = dict(pos=pos, vel=0.1 * rng.standard_normal((N, 3)), mass=np.full(N, 1.0 / N),
+             u=np.where(sp == 1, 1.0, 0.0), h=np.where(sp == 1, 0.2, 0.0), species=sp)
+    phys = dict(box=1.0, r_cut=0.3, r_split=0.3 / 4.5, eps_soft=1e-3)
+    op = oracle.make_params(**phys)
+    ref = oracle.forces(s["pos"], s["vel"], s["mass"], s["u"], s["h"], s["species"], op)
+    assert ref["rc"] == 0
+    out = run_gpu(crk, s, crk.physics(**phys), precision, leaf_cap=32)
+    compare(out, ref, oracle_counts(s, op), precision, label="tiny")
+
+
+@pytest.mark.parametrize("only", [0, 1], ids=["all-dm", "all-gas"])
+def test_single_species(crk, only):
+    box = wl.jittered_lattice(10, seed=4)
+    keep = box.species == only
+    s = {k: v[keep] for k, v in box_dict(box).items()}
+    op = oracle_params(box)
+    ref = oracle.forces(s["pos"], s["vel"], s["mass"], s["u"], s["h"], s["species"], op)
+    for precision in (0, 1):
+        out = run_gpu(crk, s, crk.box_physics(box), precision)
+        compare(out, ref, oracle_counts(s, op), precision, label=f"species={only}")
+
+
+def test_empty_input(crk):
+    with crk.Sim(crk.physics()) as sim:
+        z = np.zeros((0, 3))
+        crk.crk_load(sim.handle, z, z, np.zeros(0), np.zeros(0), np.zeros(0), np.zeros(0, np.uint8))
+        sim.n = 0
+        out = sim.forces()
+        assert out["acc"].shape == (0, 3)
+        sim.step(1e-3, 2)
+
+
+def test_all_gas_at_one_point_reports_singular(crk):
+    N = 40
+    s = dict(pos=np.full((N, 3), 0.5), vel=np.zeros((N, 3)), mass=np.full(N, 1.0 / N),
+             u=np.ones(N), h=np.full(N, 0.05), species=np.ones(N, np.uint8))
+    for precision in (0, 1):
+        with pytest.raises(crk.CrkError) as e:
+            run_gpu(crk, s, crk.physics(r_cut=0.1), precision)
+        assert e.value.code == crk.CRK_ESINGULAR
+
+
+def test_invalid_inputs_are_rejected(crk):
+    N = 10
+    base = dict(pos=np.full((N, 3), 0.25), vel=np.zeros((N, 3)), mass=np.full(N, 0.1),
+                u=np.ones(N), h=np.full(N, 0.05), species=np.ones(N, np.uint8))
+    bad_pos = dict(base, pos=base["pos"].copy())
+    bad_pos["pos"][3, 1] = 1.0                      # must be < L
+    bad_h = dict(base, h=np.full(N, 0.3))           # 2h >= L/2
+    bad_m = dict(base, mass=np.full(N, -1.0))
+    for s in (bad_pos, bad_h, bad_m):
+        with crk.Sim(crk.physics(r_cut=0.1)) as sim:
+            with pytest.raises(crk.CrkError) as e:
+                crk.crk_load(sim.handle, s["pos"], s["vel"], s["mass"], s["u"], s["h"], s["species"])
+            assert e.value.code == crk.CRK_EINVAL
+    with pytest.raises(crk.CrkError):
+        crk.crk_create(crk.params(leaf_cap=48))
+    with pytest.raises(crk.CrkError):
+        crk.Sim(crk.physics(r_cut=0.6)).load(wl.jittered_lattice(4))
+
+
+# ------------------------------------------------------------------ KDK
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_kdk_steps_match_oracle(crk, precision):
+    box = wl.gaussian_field_box(16, seed=7)
+    box.vel = box.vel * 20.0
+    op = oracle_params(box)
+    nsteps, dt = 3, 1e-3
+    ref = oracle.kdk(box.pos, box.vel, box.mass, box.u, box.h, box.species, op, dt, nsteps)
+    with crk.Sim(crk.box_physics(box), precision=precision) as sim:
+        sim.load(box)
+        sim.step(dt, nsteps)
+        pos, vel, u = sim.state()
+        mom, energy, nfloor = crk.crk_get_sums(sim.handle)
+    d = pos - ref["pos"]
+    d = np.where(d > 0.5, d - 1.0, d)
+    d = np.where(d < -0.5, d + 1.0, d)
+    tol = TOL[precision]
+    disp = np.linalg.norm(ref["pos"] - box.pos) + 1e-300
+    assert np.linalg.norm(d) / disp <= tol
+    assert rel_l2(vel, ref["vel"]) <= tol
+    assert rel_l2(u, ref["u"]) <= tol
+    m = box.mass
+    p0 = (m[:, None] * box.vel).sum(0)
+    assert np.max(np.abs(np.array(mom) - p0)) <= 1e-6 * np.abs(m[:, None] * box.vel).sum()
+
+
+# ---------------------------------------------------------------- batched
+def test_batched_boxes_match_each_box_alone(crk):
+    boxes = [wl.gaussian_field_box(n, seed=100 + n) for n in (8, 12, 16)]
+    cat = wl.concat_boxes(boxes)
+    phys = [crk.box_physics(b) for b in boxes]
+    for precision in (0, 1):
+        with crk.Sim(phys[0], precision=precision) as sim:
+            crk.crk_load_boxes(sim.handle, [b.n for b in boxes], phys, cat["pos"], cat["vel"],
+                               cat["mass"], cat["u"], cat["h"], cat["species"])
+            sim.n = int(cat["offsets"][-1])
+            out = sim.forces()
+        for b, box in enumerate(boxes):
+            lo, hi = cat["offsets"][b], cat["offsets"][b + 1]
+            part = {k: (v[lo:hi] if isinstance(v, np.ndarray) and v.shape[:1] == (sim.n,) else v)
+                    for k, v in out.items()}
+            op = oracle_params(box)
+            ref = oracle.forces(box.pos, box.vel, box.mass, box.u, box.h, box.species, op)
+            compare(part, ref, oracle_counts(box_dict(box), op), precision, label=f"box {b}")
+
+
+def test_batched_step_matches_single_box_steps(crk):
+    boxes = [wl.gaussian_field_box(n, seed=200 + n) for n in (8, 16)]
+    cat = wl.concat_boxes(boxes)
+    phys = [crk.box_physics(b) for b in boxes]
+    dts = [1e-3, 2e-3]
+    with crk.Sim(phys[0], precision=0) as sim:
+        crk.crk_load_boxes(sim.handle, [b.n for b in boxes], phys, cat["pos"], cat["vel"],
+                           cat["mass"], cat["u"], cat["h"], cat["species"])
+        crk.crk_step_boxes(sim.handle, dts, 2)
+        n = int(cat["offsets"][-1])
+        pos, vel, u = np.zeros((n, 3)), np.zeros((n, 3)), np.zeros(n)
+        crk.crk_get_state(sim.handle, pos, vel, u)
+    for b, box in enumerate(boxes):
+        lo, hi = cat["offsets"][b], cat["offsets"][b + 1]
+        ref = oracle.kdk(box.pos, box.vel, box.mass, box.u, box.h, box.species, oracle_params(box),
+                         dts[b], 2)
+        assert rel_l2(vel[lo:hi], ref["vel"]) <= 1e-10
+        assert rel_l2(u[lo:hi], ref["u"]) <= 1e-10
+
+
+# ---------------------------------------------------------------- service
+def _job_boxes():
+    return [wl.gaussian_field_box(n, seed=300 + i) for i, n in enumerate((8, 12, 10, 16, 8))]
+
+
+def _run_service(crk, boxes, nsteps, precision=1, max_slots=8):
+    svc = crk.crk_service_create(8 << 30, max_slots, precision=precision)
+    try:
+        tickets = [crk.crk_submit(svc, crk.box_physics(b), b.pos, b.vel, b.mass, b.u, b.h,
+                                  b.species, 1e-3, nsteps) for b in boxes]
+        return [crk.crk_poll(svc, t, b.n, -1) for t, b in zip(tickets, boxes)]
+    finally:
+        crk.crk_service_destroy(svc)
+
+
+def test_service_result_is_the_same_alone_and_in_the_mix(crk):
+    boxes = _job_boxes()
+    mixed = _run_service(crk, boxes, 4)
+    for i in (0, 3):
+        alone = _run_service(crk, [boxes[i]], 4)[0]
+        # boxes never interact and every per-leaf sum runs in a fixed order
+        assert np.array_equal(alone["pos"], mixed[i]["pos"])
+        assert np.array_equal(alone["vel"], mixed[i]["vel"])
+        assert np.array_equal(alone["u"], mixed[i]["u"])
+
+
+def test_service_matches_oracle(crk):
+    boxes = _job_boxes()[:3]
+    res = _run_service(crk, boxes, 3, precision=0)
+    for b, r in zip(boxes, res):
+        ref = oracle.kdk(b.pos, b.vel, b.mass, b.u, b.h, b.species, oracle_params(b), 1e-3, 3)
+        assert rel_l2(r["vel"], ref["vel"]) <= 1e-10
+        assert rel_l2(r["u"], ref["u"]) <= 1e-10
+        assert r["latency_ns"] > 0
+
+
+def test_service_admission_refuses_a_job_over_budget(crk):
+    svc = crk.crk_service_create(1 << 20, 4)
+    try:
+        b = wl.gaussian_field_box(16, seed=1)
+        with pytest.raises(crk.CrkError) as e:
+            crk.crk_submit(svc, crk.box_physics(b), b.pos, b.vel, b.mass, b.u, b.h, b.species, 1e-3, 1)
+        assert e.value.code == crk.CRK_EINVAL
+        with pytest.raises(crk.CrkError) as e:
+            crk.crk_poll(svc, 12345, 1, 0)
+        assert e.value.code == crk.CRK_ENOTFOUND
+    finally:
+        crk.crk_service_destroy(svc)
+
+
+def test_service_reports_a_bad_job_and_keeps_serving(crk):
+    boxes = _job_boxes()[:2]
+    bad = wl.gaussian_field_box(8, seed=9)
+    bad.pos = bad.pos.copy()
+    bad.pos[0, 0] = 2.0
+    svc = crk.crk_service_create(8 << 30, 4)
+    try:
+        t_bad = crk.crk_submit(svc, crk.box_physics(bad), bad.pos, bad.vel, bad.mass, bad.u, bad.h,
+                               bad.species, 1e-3, 2)
+        ts = [crk.crk_submit(svc, crk.box_physics(b), b.pos, b.vel, b.mass, b.u, b.h, b.species,
+                             1e-3, 2) for b in boxes]
+        with pytest.raises(crk.CrkError) as e:
+            crk.crk_poll(svc, t_bad, bad.n, -1)
+        assert e.value.code == crk.CRK_EINVAL
+        for t, b in zip(ts, boxes):
+            assert crk.crk_poll(svc, t, b.n, -1) is not None
+    finally:
+        crk.crk_service_destroy(svc)
