@@ -303,6 +303,8 @@ def main():
                                         f"({peak_kind} sm_max_mhz)"},
             "pass_tflops": {k: round(v, 3) for k, v in pass_tflops.items()},
             "pairs_per_step": pairs,
+            "leaves": int(tim["nleaves"]), "leaf_pairs": {"hydro": int(tim["pairs_hydro"]),
+                                                          "gravity": int(tim["pairs_grav"])},
             "breakdown_ms": breakdown,
             "fp64_plain": fp64,
             "e2e": e2e,

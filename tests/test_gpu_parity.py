@@ -82,12 +82,15 @@ def test_lattice_2x32_matches_oracle(crk, precision):
     compare(out, ref, oracle_counts(s, op), precision, label="lattice")
 
 
-def _clustered(seed, n_gas=2500, n_dm=1500):
+def _clustered(seed, n_gas=3000, n_dm=2000):
+    """Half uniform, half in a Gaussian clump, species shuffled; gas h from
+    the 32nd-nearest gas neighbour (as in the clustered workload), so gather
+    sets are asymmetric and every m2 is well conditioned."""
     rng = np.random.default_rng(seed)
     g1 = rng.uniform(0, 1, size=(n_gas // 2, 3))
     g2 = (0.5 + 0.05 * rng.standard_normal((n_gas - n_gas // 2, 3))) % 1.0
     dm = np.concatenate([rng.uniform(0, 1, size=(n_dm // 2, 3)),
-                         (0.3 + 0.05 * rng.standard_normal((n_dm - n_dm // 2, 3))) % 1.0])
+                         (0.95 + 0.05 * rng.standard_normal((n_dm - n_dm // 2, 3))) % 1.0])
     pos = np.concatenate([g1, g2, dm])
     pos[pos >= 1.0] = 0.0
     sp = np.concatenate([np.ones(n_gas, np.uint8), np.zeros(n_dm, np.uint8)])
@@ -95,8 +98,8 @@ def _clustered(seed, n_gas=2500, n_dm=1500):
     perm = rng.permutation(N)
     pos, sp = pos[perm], sp[perm]
     mass = np.where(sp == 1, 1.0 / n_gas, 2.0 / n_dm) * rng.uniform(0.8, 1.2, size=N)
-    # h from a smooth field so gather sets are asymmetric (r < H_i but not H_j)
-    h = np.where(sp == 1, 0.09 + 0.04 * np.sin(5.0 * pos[:, 0]) * np.cos(3.0 * pos[:, 1]), 0.0)
+    h = np.zeros(N)
+    h[sp == 1] = wl.knn_smoothing_lengths(pos[sp == 1], 32, 1.2)
     u = np.where(sp == 1, np.exp(rng.normal(0, 0.5, size=N)), 0.0)
     vel = 0.2 * rng.standard_normal((N, 3))
     return dict(pos=pos, vel=vel, mass=mass, u=u, h=h, species=sp)
@@ -154,14 +157,15 @@ def test_full_size_gaussian_field_sampled(crk):
 def test_fewer_particles_than_one_leaf_and_box_faces(crk, precision):
     rng = np.random.default_rng(3)
     N = 23
-    pos = 0.5 + 0.08 * rng.standard_normal((N, 3))
+    pos = 0.05 * rng.standard_normal((N, 3))      # a clump around the box corner
     pos[0] = [0.0, 0.0, 0.0]
     pos[1] = [np.nextafter(1.0, 0.0), 0.0, np.nextafter(1.0, 0.0)]
-    pos[2] = [0.0, np.nextafter(1.0, 0.0), 0.5]
+    pos[2] = [0.0, np.nextafter(1.0, 0.0), 0.02]
     pos = np.mod(pos, 1.0)
+    pos[pos >= 1.0] = 0.0
     sp = np.array([1] * 15 + [0] * 8, np.uint8)
     s = dict(pos=pos, vel=0.1 * rng.standard_normal((N, 3)), mass=np.full(N, 1.0 / N),
-             u=np.where(sp == 1, 1.0, 0.0), h=np.where(sp == 1, 0.2, 0.0), species=sp)
+             u=np.where(sp == 1, 1.0, 0.0), h=np.where(sp == 1, 0.12, 0.0), species=sp)
     phys = dict(box=1.0, r_cut=0.3, r_split=0.3 / 4.5, eps_soft=1e-3)
     op = oracle.make_params(**phys)
     ref = oracle.forces(s["pos"], s["vel"], s["mass"], s["u"], s["h"], s["species"], op)
@@ -248,8 +252,27 @@ def test_kdk_steps_match_oracle(crk, precision):
 
 
 # ---------------------------------------------------------------- batched
+def _global_hash(box, offset, kind):
+    """Neighbour-set hash with ids offset by the box's position in the
+    batched load (independent numpy all-pairs sets, same predicate)."""
+    pos, h, sp = box.pos, box.h, box.species
+    d = pos[None, :, :] - pos[:, None, :]
+    d = np.where(d >= 0.5, d - 1.0, d)
+    d = np.where(d < -0.5, d + 1.0, d)
+    r2 = (d[..., 0] * d[..., 0] + d[..., 1] * d[..., 1]) + d[..., 2] * d[..., 2]
+    eye = np.eye(box.n, dtype=bool)
+    if kind == 0:
+        gas = sp == wl.GAS
+        m = (r2 < ((2.0 * h) ** 2)[:, None]) & gas[:, None] & gas[None, :] & ~eye
+    else:
+        m = (r2 < box.r_cut * box.r_cut) & ~eye
+    ids = wl.splitmix64(np.arange(box.n, dtype=np.uint64) + np.uint64(offset))
+    with np.errstate(over="ignore"):
+        return np.array([np.sum(ids[row], dtype=np.uint64) for row in m], dtype=np.uint64)
+
+
 def test_batched_boxes_match_each_box_alone(crk):
-    boxes = [wl.gaussian_field_box(n, seed=100 + n) for n in (8, 12, 16)]
+    boxes = [wl.gaussian_field_box(n, seed=100 + n) for n in (10, 12, 16)]
     cat = wl.concat_boxes(boxes)
     phys = [crk.box_physics(b) for b in boxes]
     for precision in (0, 1):
@@ -264,11 +287,16 @@ def test_batched_boxes_match_each_box_alone(crk):
                     for k, v in out.items()}
             op = oracle_params(box)
             ref = oracle.forces(box.pos, box.vel, box.mass, box.u, box.h, box.species, op)
-            compare(part, ref, oracle_counts(box_dict(box), op), precision, label=f"box {b}")
+            # hashes of a batched load are over the global (load-order) index
+            counts = {}
+            for name, kind in (("nbr", 0), ("grav", 2)):
+                c, _ = oracle.neighbours(box.pos, box.h, box.species, op, kind)
+                counts[name] = (c, _global_hash(box, lo, kind))
+            compare(part, ref, counts, precision, label=f"box {b}")
 
 
 def test_batched_step_matches_single_box_steps(crk):
-    boxes = [wl.gaussian_field_box(n, seed=200 + n) for n in (8, 16)]
+    boxes = [wl.gaussian_field_box(n, seed=200 + n) for n in (10, 16)]
     cat = wl.concat_boxes(boxes)
     phys = [crk.box_physics(b) for b in boxes]
     dts = [1e-3, 2e-3]
@@ -289,7 +317,7 @@ def test_batched_step_matches_single_box_steps(crk):
 
 # ---------------------------------------------------------------- service
 def _job_boxes():
-    return [wl.gaussian_field_box(n, seed=300 + i) for i, n in enumerate((8, 12, 10, 16, 8))]
+    return [wl.gaussian_field_box(n, seed=300 + i) for i, n in enumerate((10, 12, 10, 16, 11))]
 
 
 def _run_service(crk, boxes, nsteps, precision=1, max_slots=8):
@@ -339,7 +367,7 @@ def test_service_admission_refuses_a_job_over_budget(crk):
 
 def test_service_reports_a_bad_job_and_keeps_serving(crk):
     boxes = _job_boxes()[:2]
-    bad = wl.gaussian_field_box(8, seed=9)
+    bad = wl.gaussian_field_box(10, seed=9)
     bad.pos = bad.pos.copy()
     bad.pos[0, 0] = 2.0
     svc = crk.crk_service_create(8 << 30, 4)
