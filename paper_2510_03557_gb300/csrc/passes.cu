@@ -4,10 +4,14 @@
 //
 // Layout: one CTA per target leaf, one thread per target particle i
 // (blockDim = leaf capacity).  For every neighbour leaf J of the leaf-pair
-// list the CTA stages J's contiguous records in shared memory with coalesced
-// vector loads, then each thread sweeps them and accumulates phi_i of Eq. 1
-// in registers (no atomics, fixed order, so results are deterministic and a
-// box gives bit-identical results alone or batched with others).
+// list the CTA stages J's contiguous records in shared memory (coalesced
+// vector loads, slots past the leaf's end padded with far-away sentinels),
+// and one thread forms the leaf-pair frame.  Each thread then
+//   1. tests all staged candidates with a fully unrolled, branch-free loop
+//      (about ten instructions per candidate) into a bitmask, and
+//   2. evaluates the pair function of Eq. 1 only on the set bits,
+// accumulating phi_i in registers.  No atomics and a fixed order: results
+// are deterministic, and a box gives bit-identical results alone or batched.
 //
 // Two arithmetic forms share the code:
 //   mixed  (R = float):  positions are FP32 offsets from each leaf's FP64
@@ -15,8 +19,10 @@
 //          per leaf pair, so FP32 differences stay small and accurate.
 //          Neighbour-set membership that decides an integer (counts, hashes)
 //          or a discontinuous force (the gravity cut) is re-decided in FP64,
-//          with the oracle's exact expression, whenever the FP32 r^2 lies in a
-//          guard band around the threshold that bounds its rounding error.
+//          with the exact expression of the definition, whenever the FP32 r^2
+//          lies in a guard band around the threshold that bounds its rounding
+//          error.  Square roots, reciprocals and quotients use the hardware
+//          approximations.
 //   plain  (R = double): absolute FP64 positions, the same minimum-image and
 //          r^2 expression (no FMA) as the definition, every operation FP64.
 #include "crk_internal.h"
@@ -44,12 +50,28 @@ constexpr float kEps32 = 5.9604645e-8f;  // 2^-24
 template <typename R> struct Real;
 template <> struct Real<float> {
     static constexpr bool mixed = true;
-    __device__ static float sqrt_(float x) { return sqrtf(x); }
+    static constexpr float far = 1e30f;  // sentinel coordinate: r^2 overflows to +inf
+    __device__ static float sqrt_(float x)
+    {
+        float y;
+        asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y;
+    }
+    __device__ static float rcp(float x)
+    {
+        float y;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y;
+    }
+    __device__ static float div(float a, float b) { return __fdividef(a, b); }
     __device__ static float r2(float dx, float dy, float dz) { return fmaf(dz, dz, fmaf(dy, dy, dx * dx)); }
 };
 template <> struct Real<double> {
     static constexpr bool mixed = false;
+    static constexpr double far = 1e300;
     __device__ static double sqrt_(double x) { return sqrt(x); }
+    __device__ static double rcp(double x) { return 1.0 / x; }
+    __device__ static double div(double a, double b) { return a / b; }
     // (dx*dx + dy*dy) + dz*dz with every product and sum rounded on its own,
     // as the neighbour predicate is defined.
     __device__ static double r2(double dx, double dy, double dz)
@@ -87,67 +109,113 @@ __device__ __forceinline__ bool exact_lt(const State &s, uint32_t i, uint32_t j,
     return Real<double>::r2(dx, dy, dz) < thr2;
 }
 
-// Frame of leaf pair (I, J) for target particle position p (record x,y,z):
-// the j-side displacement is dx = rec_j - q, q = p - shift (mixed) or p
-// (plain).  wrap tells whether a per-pair minimum-image wrap is needed, mag
-// bounds |coordinates| entering the FP32 differences (for the guard band).
-template <typename R>
-struct Frame {
-    R qx, qy, qz;
-    bool wrap;
-    R mag;
+// Leaf-pair frame of the mixed form, formed once per (I, J) by one thread:
+// shift s = wrap(c_J - c_I) in FP64 rounded to FP32; wrap = 1 when a per-pair
+// minimum-image wrap is still needed (|s| + e_I + e_J reaches L/2 on an axis);
+// mag bounds the magnitudes entering the FP32 differences (for the guard band).
+struct FrameS {
+    float sx, sy, sz, mag;
+    int wrap;
 };
 
-template <typename R>
-__device__ __forceinline__ Frame<R> make_frame(const Leaves &lv, int I, int J, double L, R px,
-                                               R py, R pz)
+__device__ __forceinline__ void compute_frame(const Leaves &lv, int I, int J, double L, FrameS &f)
 {
-    Frame<R> f;
-    if (Real<R>::mixed) {
-        const double hL = 0.5 * L;
-        const float sx = (float)wrap1(lv.cx[J] - lv.cx[I], L, hL);
-        const float sy = (float)wrap1(lv.cy[J] - lv.cy[I], L, hL);
-        const float sz = (float)wrap1(lv.cz[J] - lv.cz[I], L, hL);
-        const float mx = fabsf(sx) + lv.ex[I] + lv.ex[J];
-        const float my = fabsf(sy) + lv.ey[I] + lv.ey[J];
-        const float mz = fabsf(sz) + lv.ez[I] + lv.ez[J];
-        const float lim = (float)(0.5 * L) * (1.0f - 1e-6f);
-        f.wrap = (mx >= lim) || (my >= lim) || (mz >= lim);
-        f.mag = mx + my + mz + (f.wrap ? (float)L : 0.0f);
-        f.qx = px - sx;
-        f.qy = py - sy;
-        f.qz = pz - sz;
-    } else {
-        f.wrap = true;
-        f.mag = 0;
-        f.qx = px;
-        f.qy = py;
-        f.qz = pz;
-    }
-    return f;
+    const double hL = 0.5 * L;
+    const float sx = (float)wrap1(lv.cx[J] - lv.cx[I], L, hL);
+    const float sy = (float)wrap1(lv.cy[J] - lv.cy[I], L, hL);
+    const float sz = (float)wrap1(lv.cz[J] - lv.cz[I], L, hL);
+    const float mx = fabsf(sx) + lv.ex[I] + lv.ex[J];
+    const float my = fabsf(sy) + lv.ey[I] + lv.ey[J];
+    const float mz = fabsf(sz) + lv.ez[I] + lv.ez[J];
+    const float lim = (float)hL * (1.0f - 1e-6f);
+    f.wrap = (mx >= lim) || (my >= lim) || (mz >= lim);
+    f.mag = mx + my + mz + (f.wrap ? (float)L : 0.0f);
+    f.sx = sx;
+    f.sy = sy;
+    f.sz = sz;
 }
 
-template <typename R>
-__device__ __forceinline__ void displacement(const Frame<R> &f, const Vec4<R> &rj, R L, R hL,
-                                             R &dx, R &dy, R &dz)
-{
-    dx = rj.x - f.qx;
-    dy = rj.y - f.qy;
-    dz = rj.z - f.qz;
-    if (f.wrap) {
-        dx = wrap1(dx, L, hL);
-        dy = wrap1(dy, L, hL);
-        dz = wrap1(dz, L, hL);
-    }
-}
-
-// Guard band of the mixed form around a squared threshold T2 = T^2: the FP32
-// r^2 differs from the exact one by less than 8 sqrt(3) eps T mag + 3 eps T^2
+// Guard band of the mixed form around a squared threshold T^2: the FP32 r^2
+// differs from the exact one by less than 8 sqrt(3) eps T mag + 3 eps T^2
 // (four roundings per coordinate difference, three in the sum of squares);
 // the band is several times wider and never below 1e-5 T^2.
 __device__ __forceinline__ float guard_band(float T, float mag)
 {
     return 1e-5f * T * T + 64.0f * kEps32 * T * (mag + T);
+}
+
+// Target position q in the frame of the staged leaf J.
+template <typename R>
+struct Target {
+    R qx, qy, qz;
+    bool wrap;
+    float mag;
+};
+
+template <typename R>
+__device__ __forceinline__ Target<R> target_in_frame(const Vec4<R> &ri, const FrameS &f)
+{
+    Target<R> q;
+    if (Real<R>::mixed) {
+        q.qx = ri.x - (R)f.sx;
+        q.qy = ri.y - (R)f.sy;
+        q.qz = ri.z - (R)f.sz;
+        q.wrap = f.wrap != 0;
+        q.mag = f.mag;
+    } else {
+        q.qx = ri.x;
+        q.qy = ri.y;
+        q.qz = ri.z;
+        q.wrap = true;
+        q.mag = 0.f;
+    }
+    return q;
+}
+
+// r^2 and x_j - x_i for a staged record.
+template <typename R, bool WRAP>
+__device__ __forceinline__ R sep2(const Vec4<R> &rj, const Target<R> &q, R L, R hL, R &dx, R &dy, R &dz)
+{
+    dx = rj.x - q.qx;
+    dy = rj.y - q.qy;
+    dz = rj.z - q.qz;
+    if (WRAP) {
+        dx = wrap1(dx, L, hL);
+        dy = wrap1(dy, L, hL);
+        dz = wrap1(dz, L, hL);
+    }
+    return Real<R>::r2(dx, dy, dz);
+}
+
+// Candidate test over a staged tile: bit j of m[j/32] set when r^2 < thr
+// (one threshold per target) or r^2 < max(thr, thrj[j]) (per candidate).
+template <typename R, int CAP, bool WRAP, bool PERJ>
+__device__ __forceinline__ void test_tile(const Vec4<R> *tile, const float *thrj, const Target<R> &q,
+                                          R L, R hL, R thr, uint32_t (&m)[CAP / 32])
+{
+#pragma unroll
+    for (int w = 0; w < CAP / 32; ++w) {
+        uint32_t bits = 0;
+#pragma unroll
+        for (int b = 0; b < 32; ++b) {
+            const int j = 32 * w + b;
+            R dx, dy, dz;
+            const R r2 = sep2<R, WRAP>(tile[j], q, L, hL, dx, dy, dz);
+            R t = thr;
+            if (PERJ) t = fmax(thr, (R)thrj[j]);
+            bits |= (r2 < t ? 1u : 0u) << b;
+        }
+        m[w] = bits;
+    }
+}
+
+template <typename R, int CAP, bool PERJ>
+__device__ __forceinline__ void test_tile_any(const Vec4<R> *tile, const float *thrj,
+                                              const Target<R> &q, R L, R hL, R thr,
+                                              uint32_t (&m)[CAP / 32])
+{
+    if (q.wrap) test_tile<R, CAP, true, PERJ>(tile, thrj, q, L, hL, thr, m);
+    else test_tile<R, CAP, false, PERJ>(tile, thrj, q, L, hL, thr, m);
 }
 
 template <typename R>
@@ -167,6 +235,22 @@ __device__ __forceinline__ void set_error(int *err, int code, uint32_t id)
 {
     atomicCAS(err, 0, code);
     atomicMin(err + 1, (int)id);
+}
+
+template <typename R, int CAP>
+__device__ __forceinline__ void stage(Vec4<R> *tile, const Vec4<R> *__restrict__ src, uint32_t sJ,
+                                      uint32_t cJ, uint32_t t)
+{
+    Vec4<R> v;
+    if (t < cJ) {
+        v = src[sJ + t];
+    } else {
+        v.x = Real<R>::far;
+        v.y = Real<R>::far;
+        v.z = Real<R>::far;
+        v.w = 0;
+    }
+    tile[t] = v;
 }
 
 // ------------------------------------------------------------- records
@@ -206,6 +290,7 @@ __global__ void __launch_bounds__(CAP) density_k(PassArgs a)
     const int I = blockIdx.x;
     if (a.lv.species[I] != CRK_GAS) return;
     __shared__ R4 tile[CAP];
+    __shared__ FrameS fr;
     const R4 *__restrict__ pm = reinterpret_cast<const R4 *>(a.pm);
     const uint32_t s0 = a.lv.start[I], cnt = a.lv.count[I];
     const BoxDev bx = a.boxes[a.lv.slot[I]];
@@ -214,12 +299,11 @@ __global__ void __launch_bounds__(CAP) density_k(PassArgs a)
     const bool act = t < cnt;
     const uint32_t i = s0 + (act ? t : 0u);
     const R4 ri = pm[i];
-    const double h64 = a.s.h[i];
-    const double H64 = 2.0 * h64;
+    const double H64 = 2.0 * a.s.h[i];
     const double H2x = __dmul_rn(H64, H64);
     const R H = (R)H64;
     const R H2 = Real<R>::mixed ? H * H : (R)H2x;
-    const R invH = (R)1 / H;
+    const R invH = Real<R>::rcp(H);
     const R cW = (R)kWn * invH * invH * invH;
     R rho = 0;
     int nc = 0;
@@ -228,30 +312,37 @@ __global__ void __launch_bounds__(CAP) density_k(PassArgs a)
         const uint32_t J = a.hcol[p];
         const uint32_t sJ = a.lv.start[J], cJ = a.lv.count[J];
         __syncthreads();
-        if (t < cJ) tile[t] = pm[sJ + t];
+        stage<R, CAP>(tile, pm, sJ, cJ, t);
+        if (Real<R>::mixed && t == 0) compute_frame(a.lv, I, (int)J, bx.L, fr);
         __syncthreads();
-        const Frame<R> f = make_frame<R>(a.lv, I, (int)J, bx.L, ri.x, ri.y, ri.z);
-        const R gb = Real<R>::mixed ? (R)guard_band((float)H, (float)f.mag) : (R)0;
-        for (uint32_t j = 0; j < cJ; ++j) {
-            const R4 rj = tile[j];
-            R dx, dy, dz;
-            displacement(f, rj, L, hL, dx, dy, dz);
-            const R r2 = Real<R>::r2(dx, dy, dz);
-            if (r2 < H2) {
+        const Target<R> q = target_in_frame(ri, fr);
+        const R gb = Real<R>::mixed ? (R)guard_band((float)H, q.mag) : (R)0;
+        uint32_t m[CAP / 32];
+        test_tile_any<R, CAP, false>(tile, nullptr, q, L, hL, COUNT ? H2 + gb : H2, m);
+#pragma unroll
+        for (int w = 0; w < CAP / 32; ++w) {
+            uint32_t bits = m[w];
+            while (bits) {
+                const int j = 32 * w + __ffs(bits) - 1;
+                bits &= bits - 1;
+                const R4 rj = tile[j];
+                R dx, dy, dz;
+                const R r2 = q.wrap ? sep2<R, true>(rj, q, L, hL, dx, dy, dz)
+                                    : sep2<R, false>(rj, q, L, hL, dx, dy, dz);
                 const R r = Real<R>::sqrt_(r2);
-                const R q = r * invH;
-                R om = (R)1 - q;
+                const R qq = r * invH;
+                R om = (R)1 - qq;
                 om = om > (R)0 ? om : (R)0;
                 const R om2 = om * om;
-                const R W = cW * om2 * om2 * om2 * ((R)1 + q * ((R)6 + q * (R)(35.0 / 3.0)));
-                rho += rj.w * W;
-            }
-            if (COUNT) {
-                bool in = r2 < H2;
-                if (Real<R>::mixed && fabs(r2 - H2) <= gb) in = exact_lt(a.s, i, sJ + j, bx.L, H2x);
-                if (in && !(J == (uint32_t)I && j == t)) {
-                    ++nc;
-                    hs += mix64((uint64_t)a.s.id[sJ + j]);
+                rho += rj.w * cW * om2 * om2 * om2 * ((R)1 + qq * ((R)6 + qq * (R)(35.0 / 3.0)));
+                if (COUNT) {
+                    bool in = r2 < H2;
+                    if (Real<R>::mixed && r2 >= H2 - gb)
+                        in = exact_lt(a.s, i, sJ + (uint32_t)j, bx.L, H2x);
+                    if (in && !(J == (uint32_t)I && (uint32_t)j == t)) {
+                        ++nc;
+                        hs += mix64((uint64_t)a.s.id[sJ + j]);
+                    }
                 }
             }
         }
@@ -259,7 +350,7 @@ __global__ void __launch_bounds__(CAP) density_k(PassArgs a)
     if (!act) return;
     const R uh = reinterpret_cast<const R *>(a.uhat)[i];
     const R gam = (R)bx.gamma;
-    const R V = ri.w / rho;
+    const R V = Real<R>::div(ri.w, rho);
     R4 r0;
     r0.x = ri.x; r0.y = ri.y; r0.z = ri.z; r0.w = V;
     reinterpret_cast<R4 *>(a.hrec[0])[i] = r0;
@@ -339,6 +430,7 @@ __global__ void __launch_bounds__(CAP) moments_k(PassArgs a)
     const int I = blockIdx.x;
     if (a.lv.species[I] != CRK_GAS) return;
     __shared__ R4 tile[CAP];
+    __shared__ FrameS fr;
     const R4 *__restrict__ rec0 = reinterpret_cast<const R4 *>(a.hrec[0]);
     const uint32_t s0 = a.lv.start[I], cnt = a.lv.count[I];
     const BoxDev bx = a.boxes[a.lv.slot[I]];
@@ -350,7 +442,7 @@ __global__ void __launch_bounds__(CAP) moments_k(PassArgs a)
     const double H64 = 2.0 * a.s.h[i];
     const R H = (R)H64;
     const R H2 = Real<R>::mixed ? H * H : (R)__dmul_rn(H64, H64);
-    const R invH = (R)1 / H;
+    const R invH = Real<R>::rcp(H);
     const R invH2 = invH * invH;
     const R cW = (R)kWn * invH2 * invH;
     const R cG = (R)kGn * invH2 * invH2 * invH;
@@ -364,46 +456,54 @@ __global__ void __launch_bounds__(CAP) moments_k(PassArgs a)
         const uint32_t J = a.hcol[p];
         const uint32_t sJ = a.lv.start[J], cJ = a.lv.count[J];
         __syncthreads();
-        if (t < cJ) tile[t] = rec0[sJ + t];
+        stage<R, CAP>(tile, rec0, sJ, cJ, t);
+        if (Real<R>::mixed && t == 0) compute_frame(a.lv, I, (int)J, bx.L, fr);
         __syncthreads();
-        const Frame<R> f = make_frame<R>(a.lv, I, (int)J, bx.L, ri.x, ri.y, ri.z);
-        for (uint32_t j = 0; j < cJ; ++j) {
-            const R4 rj = tile[j];
-            R dx, dy, dz;
-            displacement(f, rj, L, hL, dx, dy, dz);
-            const R r2 = Real<R>::r2(dx, dy, dz);
-            if (!(r2 < H2)) continue;
-            const R x[3] = {-dx, -dy, -dz};
-            R W, g;
-            kernel_wg(Real<R>::sqrt_(r2), invH, cW, cG, W, g);
-            const R VW = rj.w * W;
-            const R Vg = rj.w * g;
-            const R VWx[3] = {VW * x[0], VW * x[1], VW * x[2]};
-            const R dW[3] = {Vg * x[0], Vg * x[1], Vg * x[2]};
-            const R xx[6] = {x[0] * x[0], x[0] * x[1], x[0] * x[2], x[1] * x[1], x[1] * x[2], x[2] * x[2]};
-            m0 += VW;
+        const Target<R> q = target_in_frame(ri, fr);
+        uint32_t m[CAP / 32];
+        test_tile_any<R, CAP, false>(tile, nullptr, q, L, hL, H2, m);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) m1[c] += VWx[c];
+        for (int w = 0; w < CAP / 32; ++w) {
+            uint32_t bits = m[w];
+            while (bits) {
+                const int j = 32 * w + __ffs(bits) - 1;
+                bits &= bits - 1;
+                const R4 rj = tile[j];
+                R dx, dy, dz;
+                const R r2 = q.wrap ? sep2<R, true>(rj, q, L, hL, dx, dy, dz)
+                                    : sep2<R, false>(rj, q, L, hL, dx, dy, dz);
+                const R x[3] = {-dx, -dy, -dz};
+                R W, g;
+                kernel_wg(Real<R>::sqrt_(r2), invH, cW, cG, W, g);
+                const R VW = rj.w * W;
+                const R Vg = rj.w * g;
+                const R VWx[3] = {VW * x[0], VW * x[1], VW * x[2]};
+                const R dW[3] = {Vg * x[0], Vg * x[1], Vg * x[2]};
+                const R xx[6] = {x[0] * x[0], x[0] * x[1], x[0] * x[2], x[1] * x[1], x[1] * x[2], x[2] * x[2]};
+                m0 += VW;
 #pragma unroll
-            for (int s = 0; s < 6; ++s) m2[s] += VW * xx[s];
+                for (int c = 0; c < 3; ++c) m1[c] += VWx[c];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) dm0[c] += dW[c];
+                for (int s = 0; s < 6; ++s) m2[s] += VW * xx[s];
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
+                for (int c = 0; c < 3; ++c) dm0[c] += dW[c];
 #pragma unroll
-                for (int q = 0; q < 3; ++q) dm1[3 * c + q] += x[c] * dW[q] + (c == q ? VW : (R)0);
-            // packed (ab): 0 xx, 1 xy, 2 xz, 3 yy, 4 yz, 5 zz
-            constexpr int SA[6] = {0, 0, 0, 1, 1, 2};
-            constexpr int SB[6] = {0, 1, 2, 1, 2, 2};
+                for (int c = 0; c < 3; ++c)
 #pragma unroll
-            for (int s = 0; s < 6; ++s)
+                    for (int qd = 0; qd < 3; ++qd) dm1[3 * c + qd] += x[c] * dW[qd] + (c == qd ? VW : (R)0);
+                // packed (ab): 0 xx, 1 xy, 2 xz, 3 yy, 4 yz, 5 zz
+                constexpr int SA[6] = {0, 0, 0, 1, 1, 2};
+                constexpr int SB[6] = {0, 1, 2, 1, 2, 2};
 #pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    R v = xx[s] * dW[q];
-                    if (SA[s] == q) v += VWx[SB[s]];
-                    if (SB[s] == q) v += VWx[SA[s]];
-                    dm2[3 * s + q] += v;
-                }
+                for (int s = 0; s < 6; ++s)
+#pragma unroll
+                    for (int qd = 0; qd < 3; ++qd) {
+                        R v = xx[s] * dW[qd];
+                        if (SA[s] == qd) v += VWx[SB[s]];
+                        if (SB[s] == qd) v += VWx[SA[s]];
+                        dm2[3 * s + qd] += v;
+                    }
+            }
         }
     }
     if (!act) return;
@@ -489,6 +589,8 @@ __global__ void __launch_bounds__(CAP) hydro_k(PassArgs a)
     const int I = blockIdx.x;
     if (a.lv.species[I] != CRK_GAS) return;
     __shared__ R4 tile[7][CAP];
+    __shared__ float h2j[CAP];
+    __shared__ FrameS fr;
     const uint32_t s0 = a.lv.start[I], cnt = a.lv.count[I];
     const BoxDev bx = a.boxes[a.lv.slot[I]];
     const R L = (R)bx.L, hL = (R)(0.5 * bx.L);
@@ -497,15 +599,17 @@ __global__ void __launch_bounds__(CAP) hydro_k(PassArgs a)
     const bool act = t < cnt;
     const uint32_t i = s0 + (act ? t : 0u);
     HState<R> si;
+    R4 ri0;
     {
         R4 r[7];
 #pragma unroll
         for (int k = 0; k < 7; ++k) r[k] = reinterpret_cast<const R4 *>(a.hrec[k])[i];
         unpack_hstate(r, si);
+        ri0 = r[0];
     }
     const R Hi = (R)2 * si.h;
     const R H2i = Hi * Hi;
-    const R invHi = (R)1 / Hi;
+    const R invHi = Real<R>::rcp(Hi);
     const R cWi = (R)kWn * invHi * invHi * invHi;
     const R cGi = (R)kGn * invHi * invHi * invHi * invHi * invHi;
     const R hi2e = eps2 * si.h * si.h;
@@ -514,80 +618,93 @@ __global__ void __launch_bounds__(CAP) hydro_k(PassArgs a)
         const uint32_t J = a.hcol[p];
         const uint32_t sJ = a.lv.start[J], cJ = a.lv.count[J];
         __syncthreads();
+        stage<R, CAP>(tile[0], reinterpret_cast<const R4 *>(a.hrec[0]), sJ, cJ, t);
         if (t < cJ) {
 #pragma unroll
-            for (int k = 0; k < 7; ++k) tile[k][t] = reinterpret_cast<const R4 *>(a.hrec[k])[sJ + t];
+            for (int k = 1; k < 7; ++k) tile[k][t] = reinterpret_cast<const R4 *>(a.hrec[k])[sJ + t];
+            const float Hj = 2.0f * (float)tile[1][t].w;
+            h2j[t] = Hj * Hj;
+        } else {
+            h2j[t] = 0.f;
         }
+        if (Real<R>::mixed && t == 0) compute_frame(a.lv, I, (int)J, bx.L, fr);
         __syncthreads();
-        const Frame<R> f = make_frame<R>(a.lv, I, (int)J, bx.L, si.px, si.py, si.pz);
-        for (uint32_t j = 0; j < cJ; ++j) {
-            const R4 rj0 = tile[0][j];
-            const R4 rj1 = tile[1][j];
-            R dx, dy, dz;
-            displacement(f, rj0, L, hL, dx, dy, dz);
-            const R r2 = Real<R>::r2(dx, dy, dz);
-            const R Hj = (R)2 * rj1.w;
-            const R H2j = Hj * Hj;
-            if (!(r2 < H2i || r2 < H2j)) continue;
-            if (J == (uint32_t)I && j == t) continue;
-            HState<R> sj;
-            {
-                R4 r[7];
-                r[0] = rj0;
-                r[1] = rj1;
+        const Target<R> q = target_in_frame(ri0, fr);
+        uint32_t m[CAP / 32];
+        test_tile_any<R, CAP, true>(tile[0], h2j, q, L, hL, H2i, m);
+        if (J == (uint32_t)I) {
 #pragma unroll
-                for (int k = 2; k < 7; ++k) r[k] = tile[k][j];
-                unpack_hstate(r, sj);
+            for (int w = 0; w < CAP / 32; ++w)
+                if (w == (int)(t / 32)) m[w] &= ~(1u << (t % 32));
+        }
+#pragma unroll
+        for (int w = 0; w < CAP / 32; ++w) {
+            uint32_t bits = m[w];
+            while (bits) {
+                const int j = 32 * w + __ffs(bits) - 1;
+                bits &= bits - 1;
+                HState<R> sj;
+                {
+                    R4 r[7];
+#pragma unroll
+                    for (int k = 0; k < 7; ++k) r[k] = tile[k][j];
+                    unpack_hstate(r, sj);
+                }
+                R dx, dy, dz;
+                const R4 rj0 = tile[0][j];
+                const R r2 = q.wrap ? sep2<R, true>(rj0, q, L, hL, dx, dy, dz)
+                                    : sep2<R, false>(rj0, q, L, hL, dx, dy, dz);
+                const R x[3] = {-dx, -dy, -dz};  // x_ij = x_i - x_j
+                const R xm[3] = {dx, dy, dz};    // x_ji
+                const R r = Real<R>::sqrt_(r2);
+                R Wi, gi, Wj, gj;
+                kernel_wg(r, invHi, cWi, cGi, Wi, gi);
+                const R invHj = Real<R>::rcp((R)2 * sj.h);
+                const R invHj2 = invHj * invHj;
+                kernel_wg(r, invHj, (R)kWn * invHj2 * invHj, (R)kGn * invHj2 * invHj2 * invHj, Wj, gj);
+                R dWi[3], dWj[3];
+                corrected_grad(si, x, Wi, gi, dWi);
+                corrected_grad(sj, xm, Wj, gj, dWj);
+                const R vxij = si.vx - sj.vx, vyij = si.vy - sj.vy, vzij = si.vz - sj.vz;
+                const R vdx = vxij * x[0] + vyij * x[1] + vzij * x[2];
+                R Q = 0;
+                if (vdx < (R)0) {
+                    const R mui = Real<R>::div(si.h * vdx, r2 + hi2e);
+                    const R muj = Real<R>::div(sj.h * vdx, r2 + eps2 * sj.h * sj.h);
+                    Q = si.rho * (-alpha * si.c * mui + beta * mui * mui) +
+                        sj.rho * (-alpha * sj.c * muj + beta * muj * muj);
+                }
+                const R pre = (R)(-0.5) * si.V * sj.V * (si.P + sj.P + Q);
+                const R Fx = pre * (dWi[0] - dWj[0]);
+                const R Fy = pre * (dWi[1] - dWj[1]);
+                const R Fz = pre * (dWi[2] - dWj[2]);
+                ax += Fx;
+                ay += Fy;
+                az += Fz;
+                du += Fx * vxij + Fy * vyij + Fz * vzij;
             }
-            const R x[3] = {-dx, -dy, -dz};  // x_ij = x_i - x_j
-            const R xm[3] = {dx, dy, dz};    // x_ji
-            const R r = Real<R>::sqrt_(r2);
-            R Wi, gi, Wj, gj;
-            kernel_wg(r, invHi, cWi, cGi, Wi, gi);
-            const R invHj = (R)1 / Hj;
-            const R invHj2 = invHj * invHj;
-            kernel_wg(r, invHj, (R)kWn * invHj2 * invHj, (R)kGn * invHj2 * invHj2 * invHj, Wj, gj);
-            R dWi[3], dWj[3];
-            corrected_grad(si, x, Wi, gi, dWi);
-            corrected_grad(sj, xm, Wj, gj, dWj);
-            const R vxij = si.vx - sj.vx, vyij = si.vy - sj.vy, vzij = si.vz - sj.vz;
-            const R vdx = vxij * x[0] + vyij * x[1] + vzij * x[2];
-            R Q = 0;
-            if (vdx < (R)0) {
-                const R mui = si.h * vdx / (r2 + hi2e);
-                const R muj = sj.h * vdx / (r2 + eps2 * sj.h * sj.h);
-                Q = si.rho * (-alpha * si.c * mui + beta * mui * mui) +
-                    sj.rho * (-alpha * sj.c * muj + beta * muj * muj);
-            }
-            const R pre = (R)(-0.5) * si.V * sj.V * (si.P + sj.P + Q);
-            const R Fx = pre * (dWi[0] - dWj[0]);
-            const R Fy = pre * (dWi[1] - dWj[1]);
-            const R Fz = pre * (dWi[2] - dWj[2]);
-            ax += Fx;
-            ay += Fy;
-            az += Fz;
-            du += Fx * vxij + Fy * vyij + Fz * vzij;
         }
     }
     if (!act) return;
     const R mi = reinterpret_cast<const R4 *>(a.pm)[i].w;
+    const R imi = Real<R>::rcp(mi);
     R4 o;
-    o.x = ax / mi;
-    o.y = ay / mi;
-    o.z = az / mi;
-    o.w = (R)(-0.5) * du / mi;
+    o.x = ax * imi;
+    o.y = ay * imi;
+    o.z = az * imi;
+    o.w = (R)(-0.5) * du * imi;
     reinterpret_cast<R4 *>(a.acc_h)[i] = o;
 }
 
 // ------------------------------------------------------------- gravity G
 // a_i = sum_{j != i, r < r_cut} -G m_j x_ij (r^2 + eps^2)^{-3/2} S(r),
-// S(r) = erfc(r / 2r_s) + r / (sqrt(pi) r_s) exp(-r^2 / 4 r_s^2).
+// S(r) = erfc(r / 2r_s) + r / (sqrt(pi) r_s) exp(-r^2 / 4r_s^2).
 template <typename R>
 __device__ __forceinline__ R split_S(R r, R inv2rs)
 {
     if (Real<R>::mixed) {
         const float u = (float)r * (float)inv2rs;
-        const float tt = __frcp_rn(fmaf(kAsP, u, 1.0f));
+        const float tt = Real<float>::rcp(fmaf(kAsP, u, 1.0f));
         const float poly = tt * (kAs1 + tt * (kAs2 + tt * (kAs3 + tt * (kAs4 + tt * kAs5))));
         const float e = __expf(-u * u);
         return (R)(e * (poly + (float)kTwoOverSqrtPi * u));
@@ -603,6 +720,7 @@ __global__ void __launch_bounds__(CAP) gravity_k(PassArgs a)
     using R4 = Vec4<R>;
     const int I = blockIdx.x;
     __shared__ R4 tile[CAP];
+    __shared__ FrameS fr;
     const R4 *__restrict__ pm = reinterpret_cast<const R4 *>(a.pm);
     const uint32_t s0 = a.lv.start[I], cnt = a.lv.count[I];
     const BoxDev bx = a.boxes[a.lv.slot[I]];
@@ -624,35 +742,49 @@ __global__ void __launch_bounds__(CAP) gravity_k(PassArgs a)
         const uint32_t J = a.gcol[p];
         const uint32_t sJ = a.lv.start[J], cJ = a.lv.count[J];
         __syncthreads();
-        if (t < cJ) tile[t] = pm[sJ + t];
+        stage<R, CAP>(tile, pm, sJ, cJ, t);
+        if (Real<R>::mixed && t == 0) compute_frame(a.lv, I, (int)J, bx.L, fr);
         __syncthreads();
-        const Frame<R> f = make_frame<R>(a.lv, I, (int)J, bx.L, ri.x, ri.y, ri.z);
-        const R gb = Real<R>::mixed ? (R)guard_band((float)rc, (float)f.mag) : (R)0;
-        for (uint32_t j = 0; j < cJ; ++j) {
-            const R4 rj = tile[j];
-            R dx, dy, dz;
-            displacement(f, rj, L, hL, dx, dy, dz);
-            const R r2 = Real<R>::r2(dx, dy, dz);
-            bool in = r2 < rc2;
-            if (Real<R>::mixed && fabs(r2 - rc2) <= gb) in = exact_lt(a.s, i, sJ + j, bx.L, rc2x);
-            if (!in || (J == (uint32_t)I && j == t)) continue;
-            const R r = Real<R>::sqrt_(r2);
-            const R S = split_S<R>(r, inv2rs);
-            const R s2 = r2 + e2;
-            R inv3;
-            if (Real<R>::mixed) {
-                const float is = rsqrtf((float)s2);
-                inv3 = (R)(is * is * is);
-            } else {
-                inv3 = (R)1 / (s2 * Real<R>::sqrt_(s2));
-            }
-            const R fr = G * rj.w * S * inv3;   // a_i += fr * (x_j - x_i)
-            ax += fr * dx;
-            ay += fr * dy;
-            az += fr * dz;
-            if (COUNT) {
-                ++nc;
-                hs += mix64((uint64_t)a.s.id[sJ + j]);
+        const Target<R> q = target_in_frame(ri, fr);
+        const R gb = Real<R>::mixed ? (R)guard_band((float)rc, q.mag) : (R)0;
+        uint32_t m[CAP / 32];
+        test_tile_any<R, CAP, false>(tile, nullptr, q, L, hL, rc2 + gb, m);
+        if (J == (uint32_t)I) {
+#pragma unroll
+            for (int w = 0; w < CAP / 32; ++w)
+                if (w == (int)(t / 32)) m[w] &= ~(1u << (t % 32));
+        }
+#pragma unroll
+        for (int w = 0; w < CAP / 32; ++w) {
+            uint32_t bits = m[w];
+            while (bits) {
+                const int j = 32 * w + __ffs(bits) - 1;
+                bits &= bits - 1;
+                const R4 rj = tile[j];
+                R dx, dy, dz;
+                const R r2 = q.wrap ? sep2<R, true>(rj, q, L, hL, dx, dy, dz)
+                                    : sep2<R, false>(rj, q, L, hL, dx, dy, dz);
+                if (Real<R>::mixed && r2 >= rc2 - gb) {
+                    if (!exact_lt(a.s, i, sJ + (uint32_t)j, bx.L, rc2x)) continue;
+                }
+                const R r = Real<R>::sqrt_(r2);
+                const R S = split_S<R>(r, inv2rs);
+                const R s2 = r2 + e2;
+                R inv3;
+                if (Real<R>::mixed) {
+                    const float is = rsqrtf((float)s2);
+                    inv3 = (R)(is * is * is);
+                } else {
+                    inv3 = (R)1 / (s2 * Real<R>::sqrt_(s2));
+                }
+                const R fr_ = G * rj.w * S * inv3;   // a_i += fr_ (x_j - x_i)
+                ax += fr_ * dx;
+                ay += fr_ * dy;
+                az += fr_ * dz;
+                if (COUNT) {
+                    ++nc;
+                    hs += mix64((uint64_t)a.s.id[sJ + j]);
+                }
             }
         }
     }
@@ -720,8 +852,8 @@ void launch_moments(const PassArgs &a, int mixed, int cap, cudaStream_t st)
     if (cap == 32) { CRK_MOM(32) }
     else if (cap == 64) { CRK_MOM(64) }
     else { CRK_MOM(128) }
-    note_launches(1);
 #undef CRK_MOM
+    note_launches(1);
 }
 
 void launch_hydro(const PassArgs &a, int mixed, int cap, cudaStream_t st)
@@ -733,8 +865,8 @@ void launch_hydro(const PassArgs &a, int mixed, int cap, cudaStream_t st)
     if (cap == 32) { CRK_HYD(32) }
     else if (cap == 64) { CRK_HYD(64) }
     else { CRK_HYD(128) }
-    note_launches(1);
 #undef CRK_HYD
+    note_launches(1);
 }
 
 void launch_gravity(const PassArgs &a, int mixed, int cap, bool count, cudaStream_t st)
