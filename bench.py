@@ -150,7 +150,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=128, help="lattice size per species (2 n^3 particles)")
-    ap.add_argument("--leaf-cap", type=int, default=64)
+    ap.add_argument("--leaf-cap", type=int, default=128)
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -195,6 +195,8 @@ PassArgs pass_args(crk_sim *s)
     a.hcol = s->hcol.as<uint32_t>();
     a.grow = s->grow.as<uint32_t>();
     a.gcol = s->gcol.as<uint32_t>();
+    a.hfr = s->hfr.as<float4>();
+    a.gfr = s->gfr.as<float4>();
     a.pm = s->pm.p;
     for (int k = 0; k < 7; ++k) a.hrec[k] = s->hrec[k].p;
     a.uhat = s->uhat.p;
@@ -206,6 +208,10 @@ PassArgs pass_args(crk_sim *s)
     a.grav_hash = s->gravh.as<uint64_t>();
     a.err = s->err.as<int>();
     a.nfloor = s->nfloor.as<unsigned long long>();
+    a.ggas = s->grp_gas.as<uint2>();
+    a.gall = s->grp_all.as<uint2>();
+    a.n_ggas = s->n_ggas;
+    a.n_gall = s->n_gall;
     return a;
 }
 
@@ -320,17 +326,36 @@ int build_tree(crk_sim *s)
     launch_pair_count(s->nd, s->lv, bd, s->nleaf, 0, s->gcnt.as<uint32_t>(), st);
     scan_exclusive_u32(s->hcnt.as<uint32_t>(), s->hrow.as<uint32_t>(), s->nleaf, sc + 1, tmp, st);
     scan_exclusive_u32(s->gcnt.as<uint32_t>(), s->grow.as<uint32_t>(), s->nleaf, sc + 2, tmp, st);
-    CK(cudaMemcpyAsync(s->host_scalars + 1, sc + 1, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    // warp work items: gas-leaf groups, then all-leaf groups
+    RET(s->grp_cnt.ensure((size_t)std::max(s->nleaf, 1) * 4 * 2));
+    RET(s->grp_off.ensure((size_t)std::max(s->nleaf, 1) * 4 * 2));
+    uint32_t *gc = s->grp_cnt.as<uint32_t>(), *go = s->grp_off.as<uint32_t>();
+    const size_t nl = (size_t)std::max(s->nleaf, 1);
+    launch_group_count(s->lv, s->nleaf, 1, gc, st);
+    launch_group_count(s->lv, s->nleaf, 0, gc + nl, st);
+    scan_exclusive_u32(gc, go, s->nleaf, sc + 3, tmp, st);
+    scan_exclusive_u32(gc + nl, go + nl, s->nleaf, sc + 4, tmp, st);
+    CK(cudaMemcpyAsync(s->host_scalars + 1, sc + 1, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     s->npair_h = s->host_scalars[1];
     s->npair_g = s->host_scalars[2];
+    s->n_ggas = s->host_scalars[3];
+    s->n_gall = s->host_scalars[4];
+    RET(s->grp_gas.ensure((size_t)std::max<uint32_t>(s->n_ggas, 1) * sizeof(uint2)));
+    RET(s->grp_all.ensure((size_t)std::max<uint32_t>(s->n_gall, 1) * sizeof(uint2)));
+    launch_group_fill(s->lv, s->nleaf, 1, go, s->grp_gas.as<uint2>(), st);
+    launch_group_fill(s->lv, s->nleaf, 0, go + nl, s->grp_all.as<uint2>(), st);
     // row[nleaf] = total
     CK(cudaMemcpyAsync(s->hrow.as<uint32_t>() + s->nleaf, sc + 1, 4, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(s->grow.as<uint32_t>() + s->nleaf, sc + 2, 4, cudaMemcpyDeviceToDevice, st));
     RET(s->hcol.ensure((size_t)std::max<int64_t>(s->npair_h, 1) * 4));
     RET(s->gcol.ensure((size_t)std::max<int64_t>(s->npair_g, 1) * 4));
-    launch_pair_fill(s->nd, s->lv, bd, s->nleaf, 1, s->hrow.as<uint32_t>(), s->hcol.as<uint32_t>(), st);
-    launch_pair_fill(s->nd, s->lv, bd, s->nleaf, 0, s->grow.as<uint32_t>(), s->gcol.as<uint32_t>(), st);
+    RET(s->hfr.ensure((size_t)std::max<int64_t>(s->npair_h, 1) * 16));
+    RET(s->gfr.ensure((size_t)std::max<int64_t>(s->npair_g, 1) * 16));
+    launch_pair_fill(s->nd, s->lv, bd, s->nleaf, 1, s->hrow.as<uint32_t>(), s->hcol.as<uint32_t>(),
+                     s->hfr.as<float4>(), st);
+    launch_pair_fill(s->nd, s->lv, bd, s->nleaf, 0, s->grow.as<uint32_t>(), s->gcol.as<uint32_t>(),
+                     s->gfr.as<float4>(), st);
     mark(s, PH_PAIRS, 1);
     return CRK_OK;
 }
@@ -750,7 +775,7 @@ extern "C" int crk_destroy(crk_sim *s)
                     &s->nd_slot, &s->hrow, &s->grow, &s->hcnt, &s->gcnt, &s->hcol, &s->gcol,
                     &s->pm, &s->uhat, &s->acc_h, &s->acc_g, &s->nbrc, &s->nbrh, &s->gravc,
                     &s->gravh, &s->err, &s->nfloor, &s->partial, &s->sums, &s->staging,
-                    &s->in_stage};
+                    &s->in_stage, &s->grp_cnt, &s->grp_off, &s->grp_gas, &s->grp_all, &s->hfr, &s->gfr};
     for (DBuf *b : bufs) b->release();
     for (int k = 0; k < 3; ++k) {
         s->lv_u32[k].release();

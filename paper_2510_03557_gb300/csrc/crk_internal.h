@@ -78,6 +78,7 @@ struct PassArgs {
     Leaves lv;
     const uint32_t *hrow, *hcol;   // hydro list
     const uint32_t *grow, *gcol;   // gravity list
+    const float4 *hfr, *gfr;       // per-entry leaf-pair frames of the two lists
     void *pm;                // R4[n]
     void *hrec[7];           // R4[n] each: hydro records
     void *uhat;              // R[n] predicted u
@@ -87,6 +88,9 @@ struct PassArgs {
     uint64_t *nbr_hash;
     int32_t *grav_count;
     uint64_t *grav_hash;
+    const uint2 *ggas;       // warp work items (leaf, first offset) of gas leaves
+    const uint2 *gall;       // warp work items of all leaves
+    uint32_t n_ggas, n_gall;
     int *err;                // [0] code, [1] smallest original index of a failing particle
     unsigned long long *nfloor;  // floor events of the u predictor
 };
@@ -114,10 +118,13 @@ void launch_leaf_setup(const uint32_t *flags, const uint32_t *scan, int64_t n, i
 void launch_leaf_bounds(const State &s, const BoxDev *boxes, Leaves lv, int nleaf, int mixed,
                         void *pm, Nodes nd, cudaStream_t st);
 void launch_build_nodes(Nodes &nd, int nleaf, cudaStream_t st);
+void launch_group_count(const Leaves &lv, int nleaf, int gas_only, uint32_t *counts, cudaStream_t st);
+void launch_group_fill(const Leaves &lv, int nleaf, int gas_only, const uint32_t *off, uint2 *groups,
+                       cudaStream_t st);
 void launch_pair_count(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, int nleaf,
                        int hydro, uint32_t *counts, cudaStream_t st);
 void launch_pair_fill(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, int nleaf,
-                      int hydro, const uint32_t *row, uint32_t *col, cudaStream_t st);
+                      int hydro, const uint32_t *row, uint32_t *col, float4 *frame, cudaStream_t st);
 
 // ---- passes (passes.cu) ----
 void launch_records(const PassArgs &a, int mixed, cudaStream_t st);

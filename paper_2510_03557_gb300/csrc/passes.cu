@@ -2,27 +2,30 @@
 // Eq. 1-2): density D, kernel moments M fused with the correction solve C,
 // the CRKSPH hydro rates H, and short-range gravity G.
 //
-// Layout: one CTA per target leaf, one thread per target particle i
-// (blockDim = leaf capacity).  For every neighbour leaf J of the leaf-pair
-// list the CTA stages J's contiguous records in shared memory (coalesced
-// vector loads, slots past the leaf's end padded with far-away sentinels),
-// and one thread forms the leaf-pair frame.  Each thread then
-//   1. tests all staged candidates with a fully unrolled, branch-free loop
-//      (about ten instructions per candidate) into a bitmask, and
-//   2. evaluates the pair function of Eq. 1 only on the set bits,
-// accumulating phi_i in registers.  No atomics and a fixed order: results
-// are deterministic, and a box gives bit-identical results alone or batched.
+// Work decomposition: every leaf is cut into target groups of at most 32
+// particles; each warp takes one group (lane = target particle i) and runs
+// on its own, without block-wide barriers.  For every neighbour leaf J of the
+// target leaf's pair list the warp
+//   0. skips J when J's box is out of range of the warp's own target box,
+//   1. stages J's contiguous records in warp-private shared memory
+//      (coalesced vector loads; slots past J's end padded with far-away
+//      sentinels, so the test needs no bounds check),
+//   2. tests the staged candidates with a fully unrolled, branch-free loop
+//      into a bitmask (about ten instructions per candidate), and
+//   3. evaluates the pair function of Eq. 1 on the set bits only,
+// accumulating phi_i in registers.  No atomics and a fixed order: results are
+// deterministic, and a box gives bit-identical results alone or batched.
 //
 // Two arithmetic forms share the code:
 //   mixed  (R = float):  positions are FP32 offsets from each leaf's FP64
-//          centre; the leaf-pair shift wrap(c_J - c_I) is formed in FP64 once
-//          per leaf pair, so FP32 differences stay small and accurate.
-//          Neighbour-set membership that decides an integer (counts, hashes)
-//          or a discontinuous force (the gravity cut) is re-decided in FP64,
-//          with the exact expression of the definition, whenever the FP32 r^2
-//          lies in a guard band around the threshold that bounds its rounding
-//          error.  Square roots, reciprocals and quotients use the hardware
-//          approximations.
+//          centre; the leaf-pair shift wrap(c_J - c_I) comes with the pair
+//          list (formed in FP64 once per pair), so FP32 differences stay
+//          small.  Neighbour-set membership that decides an integer (counts,
+//          hashes) or a discontinuous force (the gravity cut) is re-decided
+//          in FP64, with the exact expression of the definition, whenever the
+//          FP32 r^2 lies in a guard band around the threshold that bounds its
+//          rounding error.  Square roots, reciprocals and quotients use the
+//          hardware approximations.
 //   plain  (R = double): absolute FP64 positions, the same minimum-image and
 //          r^2 expression (no FMA) as the definition, every operation FP64.
 #include "crk_internal.h"
@@ -32,6 +35,9 @@
 namespace crk {
 
 namespace {
+
+constexpr int kWarps = 4;             // warps (target groups) per CTA
+constexpr int kBlock = 32 * kWarps;
 
 constexpr double kPi = 3.14159265358979323846;
 // Wendland C4 in 3-D with support H = 2h:
@@ -97,6 +103,19 @@ __device__ __forceinline__ uint64_t mix64(uint64_t x)
     return z ^ (z >> 31);
 }
 
+__device__ __forceinline__ float warp_min(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
 // The neighbour predicate exactly as defined: FP64 positions, one wrap,
 // (dx*dx + dy*dy) + dz*dz without contraction, strict comparison.
 __device__ __forceinline__ bool exact_lt(const State &s, uint32_t i, uint32_t j, double L,
@@ -109,32 +128,6 @@ __device__ __forceinline__ bool exact_lt(const State &s, uint32_t i, uint32_t j,
     return Real<double>::r2(dx, dy, dz) < thr2;
 }
 
-// Leaf-pair frame of the mixed form, formed once per (I, J) by one thread:
-// shift s = wrap(c_J - c_I) in FP64 rounded to FP32; wrap = 1 when a per-pair
-// minimum-image wrap is still needed (|s| + e_I + e_J reaches L/2 on an axis);
-// mag bounds the magnitudes entering the FP32 differences (for the guard band).
-struct FrameS {
-    float sx, sy, sz, mag;
-    int wrap;
-};
-
-__device__ __forceinline__ void compute_frame(const Leaves &lv, int I, int J, double L, FrameS &f)
-{
-    const double hL = 0.5 * L;
-    const float sx = (float)wrap1(lv.cx[J] - lv.cx[I], L, hL);
-    const float sy = (float)wrap1(lv.cy[J] - lv.cy[I], L, hL);
-    const float sz = (float)wrap1(lv.cz[J] - lv.cz[I], L, hL);
-    const float mx = fabsf(sx) + lv.ex[I] + lv.ex[J];
-    const float my = fabsf(sy) + lv.ey[I] + lv.ey[J];
-    const float mz = fabsf(sz) + lv.ez[I] + lv.ez[J];
-    const float lim = (float)hL * (1.0f - 1e-6f);
-    f.wrap = (mx >= lim) || (my >= lim) || (mz >= lim);
-    f.mag = mx + my + mz + (f.wrap ? (float)L : 0.0f);
-    f.sx = sx;
-    f.sy = sy;
-    f.sz = sz;
-}
-
 // Guard band of the mixed form around a squared threshold T^2: the FP32 r^2
 // differs from the exact one by less than 8 sqrt(3) eps T mag + 3 eps T^2
 // (four roundings per coordinate difference, three in the sum of squares);
@@ -142,6 +135,39 @@ __device__ __forceinline__ void compute_frame(const Leaves &lv, int I, int J, do
 __device__ __forceinline__ float guard_band(float T, float mag)
 {
     return 1e-5f * T * T + 64.0f * kEps32 * T * (mag + T);
+}
+
+// Box of the warp's targets relative to the target leaf's centre.
+struct WarpBox {
+    float cx, cy, cz, ex, ey, ez;
+};
+
+__device__ __forceinline__ WarpBox warp_box(float px, float py, float pz, bool act)
+{
+    const float lx = warp_min(act ? px : FLT_MAX), hx = warp_max(act ? px : -FLT_MAX);
+    const float ly = warp_min(act ? py : FLT_MAX), hy = warp_max(act ? py : -FLT_MAX);
+    const float lz = warp_min(act ? pz : FLT_MAX), hz = warp_max(act ? pz : -FLT_MAX);
+    WarpBox b;
+    b.cx = 0.5f * (lx + hx); b.cy = 0.5f * (ly + hy); b.cz = 0.5f * (lz + hz);
+    b.ex = 0.5f * (hx - lx); b.ey = 0.5f * (hy - ly); b.ez = 0.5f * (hz - lz);
+    return b;
+}
+
+// True when leaf J (box [s - e_J, s + e_J] in the target leaf's frame, from
+// the pair frame fr) lies at distance >= R from the warp's target box.  Pairs
+// that still need a per-pair wrap (fr.w < 0) are never skipped.
+__device__ __forceinline__ bool out_of_range(const WarpBox &b, const float4 &fr, float ex, float ey,
+                                             float ez, float R)
+{
+    if (fr.w < 0.f) return false;
+    float gap2 = 0.f, g;
+    g = fabsf(fr.x - b.cx) - ex - b.ex;
+    if (g > 0.f) gap2 += g * g;
+    g = fabsf(fr.y - b.cy) - ey - b.ey;
+    if (g > 0.f) gap2 += g * g;
+    g = fabsf(fr.z - b.cz) - ez - b.ez;
+    if (g > 0.f) gap2 += g * g;
+    return gap2 >= R * R;
 }
 
 // Target position q in the frame of the staged leaf J.
@@ -153,15 +179,15 @@ struct Target {
 };
 
 template <typename R>
-__device__ __forceinline__ Target<R> target_in_frame(const Vec4<R> &ri, const FrameS &f)
+__device__ __forceinline__ Target<R> target_in_frame(const Vec4<R> &ri, const float4 &fr)
 {
     Target<R> q;
     if (Real<R>::mixed) {
-        q.qx = ri.x - (R)f.sx;
-        q.qy = ri.y - (R)f.sy;
-        q.qz = ri.z - (R)f.sz;
-        q.wrap = f.wrap != 0;
-        q.mag = f.mag;
+        q.qx = ri.x - (R)fr.x;
+        q.qy = ri.y - (R)fr.y;
+        q.qz = ri.z - (R)fr.z;
+        q.wrap = fr.w < 0.f;
+        q.mag = fabsf(fr.w);
     } else {
         q.qx = ri.x;
         q.qy = ri.y;
@@ -189,13 +215,16 @@ __device__ __forceinline__ R sep2(const Vec4<R> &rj, const Target<R> &q, R L, R 
 
 // Candidate test over a staged tile: bit j of m[j/32] set when r^2 < thr
 // (one threshold per target) or r^2 < max(thr, thrj[j]) (per candidate).
-template <typename R, int CAP, bool WRAP, bool PERJ>
+// 32-slot chunks past the leaf's end are skipped.
+template <typename R, int JMAX, bool WRAP, bool PERJ>
 __device__ __forceinline__ void test_tile(const Vec4<R> *tile, const float *thrj, const Target<R> &q,
-                                          R L, R hL, R thr, uint32_t (&m)[CAP / 32])
+                                          R L, R hL, R thr, uint32_t cJ, uint32_t (&m)[JMAX / 32])
 {
 #pragma unroll
-    for (int w = 0; w < CAP / 32; ++w) {
+    for (int w = 0; w < JMAX / 32; ++w) {
         uint32_t bits = 0;
+        m[w] = 0;
+        if ((uint32_t)(32 * w) >= cJ) continue;
 #pragma unroll
         for (int b = 0; b < 32; ++b) {
             const int j = 32 * w + b;
@@ -209,13 +238,13 @@ __device__ __forceinline__ void test_tile(const Vec4<R> *tile, const float *thrj
     }
 }
 
-template <typename R, int CAP, bool PERJ>
+template <typename R, int JMAX, bool PERJ>
 __device__ __forceinline__ void test_tile_any(const Vec4<R> *tile, const float *thrj,
-                                              const Target<R> &q, R L, R hL, R thr,
-                                              uint32_t (&m)[CAP / 32])
+                                              const Target<R> &q, R L, R hL, R thr, uint32_t cJ,
+                                              uint32_t (&m)[JMAX / 32])
 {
-    if (q.wrap) test_tile<R, CAP, true, PERJ>(tile, thrj, q, L, hL, thr, m);
-    else test_tile<R, CAP, false, PERJ>(tile, thrj, q, L, hL, thr, m);
+    if (q.wrap) test_tile<R, JMAX, true, PERJ>(tile, thrj, q, L, hL, thr, cJ, m);
+    else test_tile<R, JMAX, false, PERJ>(tile, thrj, q, L, hL, thr, cJ, m);
 }
 
 template <typename R>
@@ -237,20 +266,61 @@ __device__ __forceinline__ void set_error(int *err, int code, uint32_t id)
     atomicMin(err + 1, (int)id);
 }
 
-template <typename R, int CAP>
+// Warp-cooperative staging of leaf J's records: slots [0, round32(cJ)).
+template <typename R>
 __device__ __forceinline__ void stage(Vec4<R> *tile, const Vec4<R> *__restrict__ src, uint32_t sJ,
-                                      uint32_t cJ, uint32_t t)
+                                      uint32_t cJ, uint32_t lane)
 {
-    Vec4<R> v;
-    if (t < cJ) {
-        v = src[sJ + t];
-    } else {
-        v.x = Real<R>::far;
-        v.y = Real<R>::far;
-        v.z = Real<R>::far;
-        v.w = 0;
+    const uint32_t end = (cJ + 31u) & ~31u;
+    for (uint32_t k = lane; k < end; k += 32u) {
+        Vec4<R> v;
+        if (k < cJ) {
+            v = src[sJ + k];
+        } else {
+            v.x = Real<R>::far;
+            v.y = Real<R>::far;
+            v.z = Real<R>::far;
+            v.w = 0;
+        }
+        tile[k] = v;
     }
-    tile[t] = v;
+}
+
+// The warp's target group: up to 32 consecutive particles of leaf I.
+struct Group {
+    int I;
+    uint32_t s0, cnt, i;
+    bool act;
+};
+
+__device__ __forceinline__ Group load_group(const Leaves &lv, const uint2 *groups, uint32_t gi,
+                                            uint32_t lane)
+{
+    const uint2 g = groups[gi];
+    Group r;
+    r.I = (int)g.x;
+    r.s0 = lv.start[r.I] + g.y;
+    const uint32_t left = lv.count[r.I] - g.y;
+    r.cnt = left < 32u ? left : 32u;
+    r.act = lane < r.cnt;
+    r.i = r.s0 + (r.act ? lane : 0u);
+    return r;
+}
+
+// Position of a target relative to its leaf centre, in FP32 (for the warp box).
+template <typename R>
+__device__ __forceinline__ void rel_pos(const Vec4<R> &ri, const Leaves &lv, int I, float &x, float &y,
+                                        float &z)
+{
+    if (Real<R>::mixed) {
+        x = (float)ri.x;
+        y = (float)ri.y;
+        z = (float)ri.z;
+    } else {
+        x = (float)((double)ri.x - lv.cx[I]);
+        y = (float)((double)ri.y - lv.cy[I]);
+        z = (float)((double)ri.z - lv.cz[I]);
+    }
 }
 
 // ------------------------------------------------------------- records
@@ -283,21 +353,22 @@ __global__ void records_k(PassArgs a)
 // ------------------------------------------------------------- density D
 // rho_i = sum_{j in N_i + {i}} m_j W(r, h_i); V = m/rho; P = (gamma-1) rho u^;
 // c = sqrt(gamma (gamma-1) u^).  Optional: size and hash of N_i.
-template <typename R, int CAP, bool COUNT>
-__global__ void __launch_bounds__(CAP) density_k(PassArgs a)
+template <typename R, int JMAX, bool COUNT>
+__global__ void __launch_bounds__(kBlock) density_k(PassArgs a)
 {
     using R4 = Vec4<R>;
-    const int I = blockIdx.x;
-    if (a.lv.species[I] != CRK_GAS) return;
-    __shared__ R4 tile[CAP];
-    __shared__ FrameS fr;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    const uint32_t gi = blockIdx.x * kWarps + w;
+    if (gi >= a.n_ggas) return;
+    R4 *tile = reinterpret_cast<R4 *>(smem) + w * JMAX;
+    const Group G = load_group(a.lv, a.ggas, gi, lane);
+    const int I = G.I;
+    const uint32_t i = G.i;
     const R4 *__restrict__ pm = reinterpret_cast<const R4 *>(a.pm);
-    const uint32_t s0 = a.lv.start[I], cnt = a.lv.count[I];
-    const BoxDev bx = a.boxes[a.lv.slot[I]];
-    const R L = (R)bx.L, hL = (R)(0.5 * bx.L);
-    const uint32_t t = threadIdx.x;
-    const bool act = t < cnt;
-    const uint32_t i = s0 + (act ? t : 0u);
+    const BoxDev &bx = a.boxes[a.lv.slot[I]];
+    const double Ld = bx.L;
+    const R L = (R)Ld, hL = (R)(0.5 * Ld);
     const R4 ri = pm[i];
     const double H64 = 2.0 * a.s.h[i];
     const double H2x = __dmul_rn(H64, H64);
@@ -305,25 +376,30 @@ __global__ void __launch_bounds__(CAP) density_k(PassArgs a)
     const R H2 = Real<R>::mixed ? H * H : (R)H2x;
     const R invH = Real<R>::rcp(H);
     const R cW = (R)kWn * invH * invH * invH;
+    float px, py, pz;
+    rel_pos(ri, a.lv, I, px, py, pz);
+    const WarpBox wb = warp_box(px, py, pz, G.act);
+    const float Rc = warp_max(G.act ? (float)H : 0.f) * 1.0001f + 1e-6f * (float)Ld;
     R rho = 0;
     int nc = 0;
     uint64_t hs = 0;
     for (uint32_t p = a.hrow[I]; p < a.hrow[I + 1]; ++p) {
         const uint32_t J = a.hcol[p];
+        const float4 fr = a.hfr[p];
+        if (out_of_range(wb, fr, a.lv.ex[J], a.lv.ey[J], a.lv.ez[J], Rc)) continue;
         const uint32_t sJ = a.lv.start[J], cJ = a.lv.count[J];
-        __syncthreads();
-        stage<R, CAP>(tile, pm, sJ, cJ, t);
-        if (Real<R>::mixed && t == 0) compute_frame(a.lv, I, (int)J, bx.L, fr);
-        __syncthreads();
+        __syncwarp();
+        stage(tile, pm, sJ, cJ, lane);
+        __syncwarp();
         const Target<R> q = target_in_frame(ri, fr);
         const R gb = Real<R>::mixed ? (R)guard_band((float)H, q.mag) : (R)0;
-        uint32_t m[CAP / 32];
-        test_tile_any<R, CAP, false>(tile, nullptr, q, L, hL, COUNT ? H2 + gb : H2, m);
+        uint32_t m[JMAX / 32];
+        test_tile_any<R, JMAX, false>(tile, nullptr, q, L, hL, COUNT ? H2 + gb : H2, G.act ? cJ : 0u, m);
 #pragma unroll
-        for (int w = 0; w < CAP / 32; ++w) {
-            uint32_t bits = m[w];
+        for (int ww = 0; ww < JMAX / 32; ++ww) {
+            uint32_t bits = m[ww];
             while (bits) {
-                const int j = 32 * w + __ffs(bits) - 1;
+                const int j = 32 * ww + __ffs(bits) - 1;
                 bits &= bits - 1;
                 const R4 rj = tile[j];
                 R dx, dy, dz;
@@ -337,9 +413,8 @@ __global__ void __launch_bounds__(CAP) density_k(PassArgs a)
                 rho += rj.w * cW * om2 * om2 * om2 * ((R)1 + qq * ((R)6 + qq * (R)(35.0 / 3.0)));
                 if (COUNT) {
                     bool in = r2 < H2;
-                    if (Real<R>::mixed && r2 >= H2 - gb)
-                        in = exact_lt(a.s, i, sJ + (uint32_t)j, bx.L, H2x);
-                    if (in && !(J == (uint32_t)I && (uint32_t)j == t)) {
+                    if (Real<R>::mixed && r2 >= H2 - gb) in = exact_lt(a.s, i, sJ + (uint32_t)j, Ld, H2x);
+                    if (in && sJ + (uint32_t)j != i) {
                         ++nc;
                         hs += mix64((uint64_t)a.s.id[sJ + j]);
                     }
@@ -347,7 +422,7 @@ __global__ void __launch_bounds__(CAP) density_k(PassArgs a)
             }
         }
     }
-    if (!act) return;
+    if (!G.act) return;
     const R uh = reinterpret_cast<const R *>(a.uhat)[i];
     const R gam = (R)bx.gamma;
     const R V = Real<R>::div(ri.w, rho);
@@ -423,21 +498,22 @@ __device__ bool crk_solve(const double *m, double *out)
 //   d_g m0 += V d_gW, d_g m1^a += V (x^a d_gW + delta_ag W),
 //   d_g m2^ab += V (x^a x^b d_gW + (delta_ag x^b + delta_bg x^a) W)
 // then the FP64 correction solve; writes hrec2.w = A and hrec3..6.
-template <typename R, int CAP>
-__global__ void __launch_bounds__(CAP) moments_k(PassArgs a)
+template <typename R, int JMAX>
+__global__ void __launch_bounds__(kBlock) moments_k(PassArgs a)
 {
     using R4 = Vec4<R>;
-    const int I = blockIdx.x;
-    if (a.lv.species[I] != CRK_GAS) return;
-    __shared__ R4 tile[CAP];
-    __shared__ FrameS fr;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    const uint32_t gi = blockIdx.x * kWarps + w;
+    if (gi >= a.n_ggas) return;
+    R4 *tile = reinterpret_cast<R4 *>(smem) + w * JMAX;
+    const Group G = load_group(a.lv, a.ggas, gi, lane);
+    const int I = G.I;
+    const uint32_t i = G.i;
     const R4 *__restrict__ rec0 = reinterpret_cast<const R4 *>(a.hrec[0]);
-    const uint32_t s0 = a.lv.start[I], cnt = a.lv.count[I];
-    const BoxDev bx = a.boxes[a.lv.slot[I]];
-    const R L = (R)bx.L, hL = (R)(0.5 * bx.L);
-    const uint32_t t = threadIdx.x;
-    const bool act = t < cnt;
-    const uint32_t i = s0 + (act ? t : 0u);
+    const BoxDev &bx = a.boxes[a.lv.slot[I]];
+    const double Ld = bx.L;
+    const R L = (R)Ld, hL = (R)(0.5 * Ld);
     const R4 ri = rec0[i];
     const double H64 = 2.0 * a.s.h[i];
     const R H = (R)H64;
@@ -446,6 +522,10 @@ __global__ void __launch_bounds__(CAP) moments_k(PassArgs a)
     const R invH2 = invH * invH;
     const R cW = (R)kWn * invH2 * invH;
     const R cG = (R)kGn * invH2 * invH2 * invH;
+    float px, py, pz;
+    rel_pos(ri, a.lv, I, px, py, pz);
+    const WarpBox wb = warp_box(px, py, pz, G.act);
+    const float Rc = warp_max(G.act ? (float)H : 0.f) * 1.0001f + 1e-6f * (float)Ld;
     R m0 = 0, m1[3] = {0, 0, 0}, m2[6] = {0, 0, 0, 0, 0, 0};
     R dm0[3] = {0, 0, 0}, dm1[9], dm2[18];
 #pragma unroll
@@ -454,19 +534,20 @@ __global__ void __launch_bounds__(CAP) moments_k(PassArgs a)
     for (int k = 0; k < 18; ++k) dm2[k] = 0;
     for (uint32_t p = a.hrow[I]; p < a.hrow[I + 1]; ++p) {
         const uint32_t J = a.hcol[p];
+        const float4 fr = a.hfr[p];
+        if (out_of_range(wb, fr, a.lv.ex[J], a.lv.ey[J], a.lv.ez[J], Rc)) continue;
         const uint32_t sJ = a.lv.start[J], cJ = a.lv.count[J];
-        __syncthreads();
-        stage<R, CAP>(tile, rec0, sJ, cJ, t);
-        if (Real<R>::mixed && t == 0) compute_frame(a.lv, I, (int)J, bx.L, fr);
-        __syncthreads();
+        __syncwarp();
+        stage(tile, rec0, sJ, cJ, lane);
+        __syncwarp();
         const Target<R> q = target_in_frame(ri, fr);
-        uint32_t m[CAP / 32];
-        test_tile_any<R, CAP, false>(tile, nullptr, q, L, hL, H2, m);
+        uint32_t m[JMAX / 32];
+        test_tile_any<R, JMAX, false>(tile, nullptr, q, L, hL, H2, G.act ? cJ : 0u, m);
 #pragma unroll
-        for (int w = 0; w < CAP / 32; ++w) {
-            uint32_t bits = m[w];
+        for (int ww = 0; ww < JMAX / 32; ++ww) {
+            uint32_t bits = m[ww];
             while (bits) {
-                const int j = 32 * w + __ffs(bits) - 1;
+                const int j = 32 * ww + __ffs(bits) - 1;
                 bits &= bits - 1;
                 const R4 rj = tile[j];
                 R dx, dy, dz;
@@ -506,7 +587,7 @@ __global__ void __launch_bounds__(CAP) moments_k(PassArgs a)
             }
         }
     }
-    if (!act) return;
+    if (!G.act) return;
     double m[40];
     m[0] = (double)m0;
 #pragma unroll
@@ -577,27 +658,37 @@ __device__ __forceinline__ void corrected_grad(const HState<R> &s, const R x[3],
     }
 }
 
+template <typename R, int JMAX>
+constexpr size_t hydro_warp_bytes()
+{
+    return 7 * JMAX * sizeof(Vec4<R>) + JMAX * sizeof(float);
+}
+
 // --------------------------------------------------------------- hydro H
 // Over the hydro pair set (r < H_i or r < H_j, j != i):
 //   F_ij = -1/2 V_i V_j (P_i + P_j + Q_i + Q_j) (dW^R_ij - dW^R_ji)
 //   Q = rho (-alpha c mu + beta mu^2), mu = min(0, h v_ij.x_ij / (r^2 + eps^2 h^2))
 //   m_i a_i = sum F_ij,  m_i du_i = -1/2 sum F_ij . v_ij
-template <typename R, int CAP>
-__global__ void __launch_bounds__(CAP) hydro_k(PassArgs a)
+template <typename R, int JMAX>
+__global__ void __launch_bounds__(kBlock) hydro_k(PassArgs a)
 {
     using R4 = Vec4<R>;
-    const int I = blockIdx.x;
-    if (a.lv.species[I] != CRK_GAS) return;
-    __shared__ R4 tile[7][CAP];
-    __shared__ float h2j[CAP];
-    __shared__ FrameS fr;
-    const uint32_t s0 = a.lv.start[I], cnt = a.lv.count[I];
-    const BoxDev bx = a.boxes[a.lv.slot[I]];
-    const R L = (R)bx.L, hL = (R)(0.5 * bx.L);
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    const uint32_t gi = blockIdx.x * kWarps + w;
+    if (gi >= a.n_ggas) return;
+    unsigned char *base = smem + (size_t)w * hydro_warp_bytes<R, JMAX>();
+    R4 *tile[7];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) tile[k] = reinterpret_cast<R4 *>(base) + k * JMAX;
+    float *h2j = reinterpret_cast<float *>(base + 7 * JMAX * sizeof(R4));
+    const Group G = load_group(a.lv, a.ggas, gi, lane);
+    const int I = G.I;
+    const uint32_t i = G.i;
+    const BoxDev &bx = a.boxes[a.lv.slot[I]];
+    const double Ld = bx.L;
+    const R L = (R)Ld, hL = (R)(0.5 * Ld);
     const R alpha = (R)bx.av_alpha, beta = (R)bx.av_beta, eps2 = (R)bx.av_eps2;
-    const uint32_t t = threadIdx.x;
-    const bool act = t < cnt;
-    const uint32_t i = s0 + (act ? t : 0u);
     HState<R> si;
     R4 ri0;
     {
@@ -613,35 +704,42 @@ __global__ void __launch_bounds__(CAP) hydro_k(PassArgs a)
     const R cWi = (R)kWn * invHi * invHi * invHi;
     const R cGi = (R)kGn * invHi * invHi * invHi * invHi * invHi;
     const R hi2e = eps2 * si.h * si.h;
+    float px, py, pz;
+    rel_pos(ri0, a.lv, I, px, py, pz);
+    const WarpBox wb = warp_box(px, py, pz, G.act);
+    const float Hw = warp_max(G.act ? (float)Hi : 0.f);
     R ax = 0, ay = 0, az = 0, du = 0;
     for (uint32_t p = a.hrow[I]; p < a.hrow[I + 1]; ++p) {
         const uint32_t J = a.hcol[p];
+        const float4 fr = a.hfr[p];
+        const float Rc = fmaxf(Hw, a.lv.hmax[J]) * 1.0001f + 1e-6f * (float)Ld;
+        if (out_of_range(wb, fr, a.lv.ex[J], a.lv.ey[J], a.lv.ez[J], Rc)) continue;
         const uint32_t sJ = a.lv.start[J], cJ = a.lv.count[J];
-        __syncthreads();
-        stage<R, CAP>(tile[0], reinterpret_cast<const R4 *>(a.hrec[0]), sJ, cJ, t);
-        if (t < cJ) {
+        __syncwarp();
+        stage(tile[0], reinterpret_cast<const R4 *>(a.hrec[0]), sJ, cJ, lane);
+        for (uint32_t k = lane; k < cJ; k += 32u) {
 #pragma unroll
-            for (int k = 1; k < 7; ++k) tile[k][t] = reinterpret_cast<const R4 *>(a.hrec[k])[sJ + t];
-            const float Hj = 2.0f * (float)tile[1][t].w;
-            h2j[t] = Hj * Hj;
-        } else {
-            h2j[t] = 0.f;
+            for (int r = 1; r < 7; ++r) tile[r][k] = reinterpret_cast<const R4 *>(a.hrec[r])[sJ + k];
+            const float Hj = 2.0f * (float)tile[1][k].w;
+            h2j[k] = Hj * Hj;
         }
-        if (Real<R>::mixed && t == 0) compute_frame(a.lv, I, (int)J, bx.L, fr);
-        __syncthreads();
+        for (uint32_t k = cJ + lane; k < ((cJ + 31u) & ~31u); k += 32u) h2j[k] = 0.f;
+        __syncwarp();
         const Target<R> q = target_in_frame(ri0, fr);
-        uint32_t m[CAP / 32];
-        test_tile_any<R, CAP, true>(tile[0], h2j, q, L, hL, H2i, m);
+        uint32_t m[JMAX / 32];
+        test_tile_any<R, JMAX, true>(tile[0], h2j, q, L, hL, H2i, G.act ? cJ : 0u, m);
         if (J == (uint32_t)I) {
+            // the target itself is slot (i - sJ) of its own leaf
+            const uint32_t self = i - sJ;
 #pragma unroll
-            for (int w = 0; w < CAP / 32; ++w)
-                if (w == (int)(t / 32)) m[w] &= ~(1u << (t % 32));
+            for (int ww = 0; ww < JMAX / 32; ++ww)
+                if (ww == (int)(self / 32)) m[ww] &= ~(1u << (self % 32));
         }
 #pragma unroll
-        for (int w = 0; w < CAP / 32; ++w) {
-            uint32_t bits = m[w];
+        for (int ww = 0; ww < JMAX / 32; ++ww) {
+            uint32_t bits = m[ww];
             while (bits) {
-                const int j = 32 * w + __ffs(bits) - 1;
+                const int j = 32 * ww + __ffs(bits) - 1;
                 bits &= bits - 1;
                 HState<R> sj;
                 {
@@ -657,13 +755,13 @@ __global__ void __launch_bounds__(CAP) hydro_k(PassArgs a)
                 const R x[3] = {-dx, -dy, -dz};  // x_ij = x_i - x_j
                 const R xm[3] = {dx, dy, dz};    // x_ji
                 const R r = Real<R>::sqrt_(r2);
-                R Wi, gi, Wj, gj;
-                kernel_wg(r, invHi, cWi, cGi, Wi, gi);
+                R Wi, gi_, Wj, gj;
+                kernel_wg(r, invHi, cWi, cGi, Wi, gi_);
                 const R invHj = Real<R>::rcp((R)2 * sj.h);
                 const R invHj2 = invHj * invHj;
                 kernel_wg(r, invHj, (R)kWn * invHj2 * invHj, (R)kGn * invHj2 * invHj2 * invHj, Wj, gj);
                 R dWi[3], dWj[3];
-                corrected_grad(si, x, Wi, gi, dWi);
+                corrected_grad(si, x, Wi, gi_, dWi);
                 corrected_grad(sj, xm, Wj, gj, dWj);
                 const R vxij = si.vx - sj.vx, vyij = si.vy - sj.vy, vzij = si.vz - sj.vz;
                 const R vdx = vxij * x[0] + vyij * x[1] + vzij * x[2];
@@ -685,7 +783,7 @@ __global__ void __launch_bounds__(CAP) hydro_k(PassArgs a)
             }
         }
     }
-    if (!act) return;
+    if (!G.act) return;
     const R mi = reinterpret_cast<const R4 *>(a.pm)[i].w;
     const R imi = Real<R>::rcp(mi);
     R4 o;
@@ -714,58 +812,66 @@ __device__ __forceinline__ R split_S(R r, R inv2rs)
     }
 }
 
-template <typename R, int CAP, bool COUNT>
-__global__ void __launch_bounds__(CAP) gravity_k(PassArgs a)
+template <typename R, int JMAX, bool COUNT>
+__global__ void __launch_bounds__(kBlock) gravity_k(PassArgs a)
 {
     using R4 = Vec4<R>;
-    const int I = blockIdx.x;
-    __shared__ R4 tile[CAP];
-    __shared__ FrameS fr;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    const uint32_t gi = blockIdx.x * kWarps + w;
+    if (gi >= a.n_gall) return;
+    R4 *tile = reinterpret_cast<R4 *>(smem) + w * JMAX;
+    const Group G = load_group(a.lv, a.gall, gi, lane);
+    const int I = G.I;
+    const uint32_t i = G.i;
     const R4 *__restrict__ pm = reinterpret_cast<const R4 *>(a.pm);
-    const uint32_t s0 = a.lv.start[I], cnt = a.lv.count[I];
-    const BoxDev bx = a.boxes[a.lv.slot[I]];
-    const R L = (R)bx.L, hL = (R)(0.5 * bx.L);
-    const uint32_t t = threadIdx.x;
-    const bool act = t < cnt;
-    const uint32_t i = s0 + (act ? t : 0u);
+    const BoxDev &bx = a.boxes[a.lv.slot[I]];
+    const double Ld = bx.L;
+    const R L = (R)Ld, hL = (R)(0.5 * Ld);
     const R4 ri = pm[i];
     const double rc2x = __dmul_rn(bx.r_cut, bx.r_cut);
     const R rc = (R)bx.r_cut;
     const R rc2 = Real<R>::mixed ? rc * rc : (R)rc2x;
     const R e2 = (R)(bx.eps_soft * bx.eps_soft);
     const R inv2rs = (R)(0.5 / bx.r_split);
-    const R G = (R)bx.G;
+    const R Gc = (R)bx.G;
+    float px, py, pz;
+    rel_pos(ri, a.lv, I, px, py, pz);
+    const WarpBox wb = warp_box(px, py, pz, G.act);
+    const float Rc = (float)bx.r_cut * 1.0001f + 1e-6f * (float)Ld;
     R ax = 0, ay = 0, az = 0;
     int nc = 0;
     uint64_t hs = 0;
     for (uint32_t p = a.grow[I]; p < a.grow[I + 1]; ++p) {
         const uint32_t J = a.gcol[p];
+        const float4 fr = a.gfr[p];
+        if (out_of_range(wb, fr, a.lv.ex[J], a.lv.ey[J], a.lv.ez[J], Rc)) continue;
         const uint32_t sJ = a.lv.start[J], cJ = a.lv.count[J];
-        __syncthreads();
-        stage<R, CAP>(tile, pm, sJ, cJ, t);
-        if (Real<R>::mixed && t == 0) compute_frame(a.lv, I, (int)J, bx.L, fr);
-        __syncthreads();
+        __syncwarp();
+        stage(tile, pm, sJ, cJ, lane);
+        __syncwarp();
         const Target<R> q = target_in_frame(ri, fr);
         const R gb = Real<R>::mixed ? (R)guard_band((float)rc, q.mag) : (R)0;
-        uint32_t m[CAP / 32];
-        test_tile_any<R, CAP, false>(tile, nullptr, q, L, hL, rc2 + gb, m);
+        uint32_t m[JMAX / 32];
+        test_tile_any<R, JMAX, false>(tile, nullptr, q, L, hL, rc2 + gb, G.act ? cJ : 0u, m);
         if (J == (uint32_t)I) {
+            const uint32_t self = i - sJ;
 #pragma unroll
-            for (int w = 0; w < CAP / 32; ++w)
-                if (w == (int)(t / 32)) m[w] &= ~(1u << (t % 32));
+            for (int ww = 0; ww < JMAX / 32; ++ww)
+                if (ww == (int)(self / 32)) m[ww] &= ~(1u << (self % 32));
         }
 #pragma unroll
-        for (int w = 0; w < CAP / 32; ++w) {
-            uint32_t bits = m[w];
+        for (int ww = 0; ww < JMAX / 32; ++ww) {
+            uint32_t bits = m[ww];
             while (bits) {
-                const int j = 32 * w + __ffs(bits) - 1;
+                const int j = 32 * ww + __ffs(bits) - 1;
                 bits &= bits - 1;
                 const R4 rj = tile[j];
                 R dx, dy, dz;
                 const R r2 = q.wrap ? sep2<R, true>(rj, q, L, hL, dx, dy, dz)
                                     : sep2<R, false>(rj, q, L, hL, dx, dy, dz);
                 if (Real<R>::mixed && r2 >= rc2 - gb) {
-                    if (!exact_lt(a.s, i, sJ + (uint32_t)j, bx.L, rc2x)) continue;
+                    if (!exact_lt(a.s, i, sJ + (uint32_t)j, Ld, rc2x)) continue;
                 }
                 const R r = Real<R>::sqrt_(r2);
                 const R S = split_S<R>(r, inv2rs);
@@ -777,7 +883,7 @@ __global__ void __launch_bounds__(CAP) gravity_k(PassArgs a)
                 } else {
                     inv3 = (R)1 / (s2 * Real<R>::sqrt_(s2));
                 }
-                const R fr_ = G * rj.w * S * inv3;   // a_i += fr_ (x_j - x_i)
+                const R fr_ = Gc * rj.w * S * inv3;   // a_i += fr_ (x_j - x_i)
                 ax += fr_ * dx;
                 ay += fr_ * dy;
                 az += fr_ * dz;
@@ -788,7 +894,7 @@ __global__ void __launch_bounds__(CAP) gravity_k(PassArgs a)
             }
         }
     }
-    if (!act) return;
+    if (!G.act) return;
     R4 o;
     o.x = ax; o.y = ay; o.z = az; o.w = 0;
     reinterpret_cast<R4 *>(a.acc_g)[i] = o;
@@ -800,28 +906,40 @@ __global__ void __launch_bounds__(CAP) gravity_k(PassArgs a)
 
 inline unsigned nblocks(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
-template <int CAP>
-void density_dispatch(const PassArgs &a, int mixed, bool count, cudaStream_t st)
+template <typename K>
+void launch_warp_kernel(K kernel, uint32_t ngroups, size_t smem, const PassArgs &a, cudaStream_t st)
 {
-    if (mixed) {
-        if (count) density_k<float, CAP, true><<<a.nleaf, CAP, 0, st>>>(a);
-        else density_k<float, CAP, false><<<a.nleaf, CAP, 0, st>>>(a);
-    } else {
-        if (count) density_k<double, CAP, true><<<a.nleaf, CAP, 0, st>>>(a);
-        else density_k<double, CAP, false><<<a.nleaf, CAP, 0, st>>>(a);
-    }
+    if (ngroups == 0) return;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    kernel<<<nblocks(ngroups, kWarps), kBlock, smem, st>>>(a);
 }
 
-template <int CAP>
-void gravity_dispatch(const PassArgs &a, int mixed, bool count, cudaStream_t st)
+template <typename R, int JMAX>
+void density_dispatch(const PassArgs &a, bool count, cudaStream_t st)
 {
-    if (mixed) {
-        if (count) gravity_k<float, CAP, true><<<a.nleaf, CAP, 0, st>>>(a);
-        else gravity_k<float, CAP, false><<<a.nleaf, CAP, 0, st>>>(a);
-    } else {
-        if (count) gravity_k<double, CAP, true><<<a.nleaf, CAP, 0, st>>>(a);
-        else gravity_k<double, CAP, false><<<a.nleaf, CAP, 0, st>>>(a);
-    }
+    const size_t sm = (size_t)kWarps * JMAX * sizeof(Vec4<R>);
+    if (count) launch_warp_kernel(density_k<R, JMAX, true>, a.n_ggas, sm, a, st);
+    else launch_warp_kernel(density_k<R, JMAX, false>, a.n_ggas, sm, a, st);
+}
+
+template <typename R, int JMAX>
+void gravity_dispatch(const PassArgs &a, bool count, cudaStream_t st)
+{
+    const size_t sm = (size_t)kWarps * JMAX * sizeof(Vec4<R>);
+    if (count) launch_warp_kernel(gravity_k<R, JMAX, true>, a.n_gall, sm, a, st);
+    else launch_warp_kernel(gravity_k<R, JMAX, false>, a.n_gall, sm, a, st);
+}
+
+template <typename R, int JMAX>
+void moments_dispatch(const PassArgs &a, cudaStream_t st)
+{
+    launch_warp_kernel(moments_k<R, JMAX>, a.n_ggas, (size_t)kWarps * JMAX * sizeof(Vec4<R>), a, st);
+}
+
+template <typename R, int JMAX>
+void hydro_dispatch(const PassArgs &a, cudaStream_t st)
+{
+    launch_warp_kernel(hydro_k<R, JMAX>, a.n_ggas, (size_t)kWarps * hydro_warp_bytes<R, JMAX>(), a, st);
 }
 
 }  // namespace
@@ -834,48 +952,47 @@ void launch_records(const PassArgs &a, int mixed, cudaStream_t st)
     note_launches(1);
 }
 
+#define CRK_BY_CAP(FN, ...)                                                  \
+    do {                                                                     \
+        if (mixed) {                                                         \
+            if (cap == 32) FN<float, 32>(__VA_ARGS__);                       \
+            else if (cap == 64) FN<float, 64>(__VA_ARGS__);                  \
+            else FN<float, 128>(__VA_ARGS__);                                \
+        } else {                                                             \
+            if (cap == 32) FN<double, 32>(__VA_ARGS__);                      \
+            else if (cap == 64) FN<double, 64>(__VA_ARGS__);                 \
+            else FN<double, 128>(__VA_ARGS__);                               \
+        }                                                                    \
+    } while (0)
+
 void launch_density(const PassArgs &a, int mixed, int cap, bool count, cudaStream_t st)
 {
-    if (a.nleaf <= 0) return;
-    if (cap == 32) density_dispatch<32>(a, mixed, count, st);
-    else if (cap == 64) density_dispatch<64>(a, mixed, count, st);
-    else density_dispatch<128>(a, mixed, count, st);
+    if (a.n_ggas == 0) return;
+    CRK_BY_CAP(density_dispatch, a, count, st);
     note_launches(1);
 }
 
 void launch_moments(const PassArgs &a, int mixed, int cap, cudaStream_t st)
 {
-    if (a.nleaf <= 0) return;
-#define CRK_MOM(C)                                                        \
-    if (mixed) moments_k<float, C><<<a.nleaf, C, 0, st>>>(a);           \
-    else moments_k<double, C><<<a.nleaf, C, 0, st>>>(a);
-    if (cap == 32) { CRK_MOM(32) }
-    else if (cap == 64) { CRK_MOM(64) }
-    else { CRK_MOM(128) }
-#undef CRK_MOM
+    if (a.n_ggas == 0) return;
+    CRK_BY_CAP(moments_dispatch, a, st);
     note_launches(1);
 }
 
 void launch_hydro(const PassArgs &a, int mixed, int cap, cudaStream_t st)
 {
-    if (a.nleaf <= 0) return;
-#define CRK_HYD(C)                                                        \
-    if (mixed) hydro_k<float, C><<<a.nleaf, C, 0, st>>>(a);             \
-    else hydro_k<double, C><<<a.nleaf, C, 0, st>>>(a);
-    if (cap == 32) { CRK_HYD(32) }
-    else if (cap == 64) { CRK_HYD(64) }
-    else { CRK_HYD(128) }
-#undef CRK_HYD
+    if (a.n_ggas == 0) return;
+    CRK_BY_CAP(hydro_dispatch, a, st);
     note_launches(1);
 }
 
 void launch_gravity(const PassArgs &a, int mixed, int cap, bool count, cudaStream_t st)
 {
-    if (a.nleaf <= 0) return;
-    if (cap == 32) gravity_dispatch<32>(a, mixed, count, st);
-    else if (cap == 64) gravity_dispatch<64>(a, mixed, count, st);
-    else gravity_dispatch<128>(a, mixed, count, st);
+    if (a.n_gall == 0) return;
+    CRK_BY_CAP(gravity_dispatch, a, count, st);
     note_launches(1);
 }
+
+#undef CRK_BY_CAP
 
 }  // namespace crk

@@ -75,7 +75,7 @@ struct crk_sim {
     DBuf keys, keys_alt, vals, vals_alt, counts, scan_tmp, flags, flag_scan, scalars;
     DBuf lv_u32[3], lv_sp, lv_c[3], lv_e[3], lv_h;
     DBuf nd_f[7], nd_slot;
-    DBuf hrow, grow, hcnt, gcnt, hcol, gcol;
+    DBuf hrow, grow, hcnt, gcnt, hcol, gcol, hfr, gfr;
     DBuf pm, hrec[7], uhat, acc_h, acc_g;
     DBuf nbrc, nbrh, gravc, gravh;
     DBuf err, nfloor, partial, sums;
@@ -84,6 +84,8 @@ struct crk_sim {
     Nodes nd{};
     int nleaf = 0;
     int64_t npair_h = 0, npair_g = 0;
+    DBuf grp_cnt, grp_off, grp_gas, grp_all;  // warp work items of the pair passes
+    uint32_t n_ggas = 0, n_gall = 0;
     uint32_t *host_scalars = nullptr;  // pinned: [0] nleaf, [1] hydro pairs, [2] gravity pairs
     int *host_err = nullptr;           // pinned: err[0..1]
 

@@ -222,20 +222,59 @@ __global__ void permute_k(State a, State b, const uint32_t *__restrict__ perm, i
 }
 
 // ---------------------------------------------------------------- leaves
+// True when the Morton cell of particle k at key shift s (the prefix
+// key >> s) holds at most cap particles; then lo is its first particle.
+// Both ends of such a cell lie within cap positions of k, so every probe
+// stays in [k - cap, k + cap].
+__device__ __forceinline__ bool cell_fits(const uint64_t *__restrict__ keys, int64_t n, int64_t k,
+                                          uint64_t key, int s, int cap, int64_t &lo)
+{
+    const uint64_t p = key >> s;
+    if (k >= cap && (keys[k - cap] >> s) == p) return false;
+    int64_t a = k - cap + 1 > 0 ? k - cap + 1 : 0, b = k;
+    while (a < b) {
+        const int64_t mid = (a + b) >> 1;
+        if ((keys[mid] >> s) < p) a = mid + 1;
+        else b = mid;
+    }
+    lo = a;
+    return !(lo + cap < n && (keys[lo + cap] >> s) == p);
+}
+
+// Leaves are octree cells: the coarsest Morton cell, at or below the box's
+// chaining-mesh bin, that holds at most cap particles of one (box, species).
+// Cells are found per particle by a binary search over the levels (a cell's
+// count only shrinks with depth).  Particles that share even the finest cell
+// are cut by count.  flags[k] = 1 where a leaf starts.
 __global__ void leaf_flags_k(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ slot,
                              const BoxDev *__restrict__ boxes, int64_t n, int cap, uint32_t *flags)
 {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    const int gshift = boxes[slot[k]].cm_shift;
-    const uint64_t g = keys[k] >> gshift;
-    int64_t lo = 0, hi = k;
-    while (lo < hi) {
-        int64_t mid = (lo + hi) >> 1;
-        if ((keys[mid] >> gshift) < g) lo = mid + 1;
-        else hi = mid;
+    const int s0 = boxes[slot[k]].cm_shift;  // shift of the chaining-mesh bin
+    const uint64_t key = keys[k];
+    const int lmax = s0 / 3;                 // deepest level with a non-negative shift
+    int la = 0, lb = lmax + 1;
+    int64_t lo = 0;
+    while (la < lb) {
+        const int mid = (la + lb) >> 1;
+        if (cell_fits(keys, n, k, key, s0 - 3 * mid, cap, lo)) lb = mid;
+        else la = mid + 1;
     }
-    flags[k] = ((k - lo) % cap) == 0 ? 1u : 0u;
+    if (la <= lmax) {
+        cell_fits(keys, n, k, key, s0 - 3 * la, cap, lo);
+        flags[k] = (k == lo) ? 1u : 0u;
+    } else {
+        const int s = s0 - 3 * lmax;
+        const uint64_t g = key >> s;
+        int64_t a = 0, b = k;
+        while (a < b) {
+            const int64_t mid = (a + b) >> 1;
+            if ((keys[mid] >> s) < g) a = mid + 1;
+            else b = mid;
+        }
+        flags[k] = ((k - a) % cap) == 0 ? 1u : 0u;
+    }
 }
 
 __global__ void leaf_setup_k(const uint32_t *__restrict__ flags, const uint32_t *__restrict__ scan,
@@ -354,10 +393,36 @@ __global__ void node_level_k(Nodes nd, int64_t oc, int64_t ncld, int64_t op, int
 // A node is kept when its periodic box gap to I is below the pair radius R
 // (hydro: max of the two largest supports; gravity: r_cut), widened by a
 // small relative and absolute margin so FP32 rounding never drops a pair.
+// Frame of leaf pair (I, J) for the mixed-form pair passes: the shift
+// s = wrap(c_J - c_I) formed in FP64 and rounded to FP32, and the bound
+// mag = sum over axes of |s| + e_I + e_J (plus L when a per-pair wrap is still
+// needed, flagged by a negative sign) that sizes the FP32 guard band.
+__device__ __forceinline__ float4 pair_frame(const Leaves &lv, int I, int J, double L)
+{
+    const double hL = 0.5 * L;
+    double d[3] = {lv.cx[J] - lv.cx[I], lv.cy[J] - lv.cy[I], lv.cz[J] - lv.cz[I]};
+    float s[3];
+    const float e[3] = {lv.ex[I] + lv.ex[J], lv.ey[I] + lv.ey[J], lv.ez[I] + lv.ez[J]};
+    bool wrap = false;
+    float mag = 0.f;
+    const float lim = (float)hL * (1.0f - 1e-6f);
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] >= hL) d[a] -= L;
+        else if (d[a] < -hL) d[a] += L;
+        s[a] = (float)d[a];
+        const float m = fabsf(s[a]) + e[a];
+        wrap = wrap || (m >= lim);
+        mag += m;
+    }
+    if (wrap) mag = -(mag + (float)L);
+    return make_float4(s[0], s[1], s[2], mag);
+}
+
 template <bool FILL>
 __global__ void pair_walk_k(Nodes nd, Leaves lv, const BoxDev *__restrict__ boxes, int nleaf,
                             int hydro, uint32_t *counts, const uint32_t *__restrict__ row,
-                            uint32_t *col)
+                            uint32_t *col, float4 *frame)
 {
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nleaf) return;
@@ -406,7 +471,10 @@ __global__ void pair_walk_k(Nodes nd, Leaves lv, const BoxDev *__restrict__ boxe
             if (gap2 >= Rm * Rm) continue;
         }
         if (l == 0) {
-            if (FILL) col[base + cnt] = (uint32_t)k;
+            if (FILL) {
+                col[base + cnt] = (uint32_t)k;
+                frame[base + cnt] = pair_frame(lv, I, k, bx.L);
+            }
             ++cnt;
         } else {
             const int64_t nchild = nd.level_off[l] - nd.level_off[l - 1];
@@ -417,9 +485,43 @@ __global__ void pair_walk_k(Nodes nd, Leaves lv, const BoxDev *__restrict__ boxe
     if (!FILL) counts[I] = cnt;
 }
 
+// Warp work items of the pair passes: every leaf is cut into target groups
+// of at most 32 consecutive particles; (leaf, first particle offset).
+__global__ void group_count_k(Leaves lv, int nleaf, int gas_only, uint32_t *counts)
+{
+    const int L = blockIdx.x * blockDim.x + threadIdx.x;
+    if (L >= nleaf) return;
+    counts[L] = (gas_only && lv.species[L] != CRK_GAS) ? 0u : (lv.count[L] + 31u) / 32u;
+}
+
+__global__ void group_fill_k(Leaves lv, int nleaf, int gas_only, const uint32_t *__restrict__ off,
+                             uint2 *groups)
+{
+    const int L = blockIdx.x * blockDim.x + threadIdx.x;
+    if (L >= nleaf) return;
+    if (gas_only && lv.species[L] != CRK_GAS) return;
+    const uint32_t ng = (lv.count[L] + 31u) / 32u;
+    for (uint32_t g = 0; g < ng; ++g) groups[off[L] + g] = make_uint2((uint32_t)L, 32u * g);
+}
+
 inline unsigned grid_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 }  // namespace
+
+void launch_group_count(const Leaves &lv, int nleaf, int gas_only, uint32_t *counts, cudaStream_t st)
+{
+    if (nleaf <= 0) return;
+    group_count_k<<<grid_for(nleaf, kT), kT, 0, st>>>(lv, nleaf, gas_only, counts);
+    note_launches(1);
+}
+
+void launch_group_fill(const Leaves &lv, int nleaf, int gas_only, const uint32_t *off, uint2 *groups,
+                       cudaStream_t st)
+{
+    if (nleaf <= 0) return;
+    group_fill_k<<<grid_for(nleaf, kT), kT, 0, st>>>(lv, nleaf, gas_only, off, groups);
+    note_launches(1);
+}
 
 size_t scan_tmp_words(int64_t n) { return (size_t)((n + kTile - 1) / kTile) + 1; }
 
@@ -527,16 +629,16 @@ void launch_pair_count(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, i
 {
     if (nleaf <= 0) return;
     pair_walk_k<false><<<grid_for(nleaf, 128), 128, 0, st>>>(nd, lv, boxes, nleaf, hydro, counts,
-                                                               nullptr, nullptr);
+                                                               nullptr, nullptr, nullptr);
     note_launches(1);
 }
 
 void launch_pair_fill(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, int nleaf,
-                      int hydro, const uint32_t *row, uint32_t *col, cudaStream_t st)
+                      int hydro, const uint32_t *row, uint32_t *col, float4 *frame, cudaStream_t st)
 {
     if (nleaf <= 0) return;
     pair_walk_k<true><<<grid_for(nleaf, 128), 128, 0, st>>>(nd, lv, boxes, nleaf, hydro, nullptr,
-                                                              row, col);
+                                                              row, col, frame);
     note_launches(1);
 }
 
