@@ -150,6 +150,10 @@ int reserve(crk_sim *s, int64_t n)
     s->lv.ey = s->lv_e[1].as<float>();
     s->lv.ez = s->lv_e[2].as<float>();
     s->lv.hmax = s->lv_h.as<float>();
+    RET(s->lv_chunk[0].ensure(nn * kChunks * sizeof(float4)));
+    RET(s->lv_chunk[1].ensure(nn * kChunks * sizeof(float4)));
+    s->lv.clo = s->lv_chunk[0].as<float4>();
+    s->lv.chi = s->lv_chunk[1].as<float4>();
     const size_t nnode = 2 * nn + 64;
     for (int k = 0; k < 7; ++k) RET(s->nd_f[k].ensure(nnode * 4));
     RET(s->nd_slot.ensure(nnode * 4));
@@ -300,22 +304,23 @@ int build_tree(crk_sim *s)
     uint32_t *tmp = s->scan_tmp.as<uint32_t>();
     radix_sort_u64(s->keys.as<uint64_t>(), s->vals.as<uint32_t>(), s->keys_alt.as<uint64_t>(),
                    s->vals_alt.as<uint32_t>(), n, s->counts.as<uint32_t>(), tmp, 0, 64, st, &ko, &vo);
-    launch_permute(s->sa, s->sb, vo, n, st);
-    std::swap(s->sa, s->sb);
-    for (int k = 0; k < 16; ++k) std::swap(s->stA[k], s->stB[k]);
-    if (s->n_dead > 0) {
-        // particles of removed slots carry the largest key and now sit at the end
-        s->n -= s->n_dead;
-        s->n_dead = 0;
-    }
-    const int64_t nlive = s->n;
+    // particles of removed pool slots carry the largest key and sort last
+    const int64_t nlive = n - s->n_dead;
     uint32_t *sc = s->scalars.as<uint32_t>();
-    launch_leaf_flags(ko, s->sa, s->boxes_d.as<BoxDev>(), nlive, s->cap, s->flags.as<uint32_t>(), st);
+    launch_leaf_flags(ko, s->slot_bits, s->boxes_d.as<BoxDev>(), nlive, s->cap, s->flags.as<uint32_t>(), st);
     scan_exclusive_u32(s->flags.as<uint32_t>(), s->flag_scan.as<uint32_t>(), nlive, sc + 0, tmp, st);
     CK(cudaMemcpyAsync(s->host_scalars, sc, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     s->nleaf = (int)s->host_scalars[0];
     launch_leaf_setup(s->flags.as<uint32_t>(), s->flag_scan.as<uint32_t>(), nlive, s->nleaf, s->lv, st);
+    // k-d order inside every leaf (on the unsorted state through the sort's
+    // permutation), then one gather of the whole state
+    launch_leaf_kd_order(s->sa, s->lv, s->nleaf, vo, st);
+    launch_permute(s->sa, s->sb, vo, n, st);
+    std::swap(s->sa, s->sb);
+    for (int k = 0; k < 16; ++k) std::swap(s->stA[k], s->stB[k]);
+    s->n = nlive;
+    s->n_dead = 0;
     launch_leaf_bounds(s->sa, s->boxes_d.as<BoxDev>(), s->lv, s->nleaf, s->mixed ? 1 : 0, s->pm.p,
                        s->nd, st);
     mark(s, PH_TREE, 1);
@@ -781,6 +786,7 @@ extern "C" int crk_destroy(crk_sim *s)
         s->lv_u32[k].release();
         s->lv_c[k].release();
         s->lv_e[k].release();
+        if (k < 2) s->lv_chunk[k].release();
     }
     for (int k = 0; k < 7; ++k) {
         s->nd_f[k].release();

@@ -47,7 +47,11 @@ struct Leaves {
     double *cx, *cy, *cz;    // FP64 bounding-box centres
     float *ex, *ey, *ez;     // half extents, rounded up
     float *hmax;             // max 2h over the leaf's gas particles (0 for DM leaves)
+    float4 *clo, *chi;       // boxes of the leaf's 32-particle chunks relative to its centre
+                             // (kChunks per leaf, outward-rounded; .w unused)
 };
+
+constexpr int kChunks = 4;   // chunks of 32 per leaf (leaf capacity <= 128)
 
 // Implicit binary hierarchy over the leaf array: level l node k covers
 // leaves [k << l, min((k+1) << l, nleaf)).
@@ -111,8 +115,10 @@ void launch_morton_keys(const State &s, const BoxDev *boxes, int64_t n, int slot
                         uint64_t *keys, uint32_t *idx, cudaStream_t st);
 void launch_permute(const State &src, const State &dst, const uint32_t *perm, int64_t n,
                     cudaStream_t st);
-void launch_leaf_flags(const uint64_t *keys, const State &s, const BoxDev *boxes, int64_t n,
+void launch_leaf_flags(const uint64_t *keys, int slot_bits, const BoxDev *boxes, int64_t n,
                        int cap, uint32_t *flags, cudaStream_t st);
+void launch_leaf_kd_order(const State &unsorted, const Leaves &lv, int nleaf, uint32_t *perm,
+                          cudaStream_t st);
 void launch_leaf_setup(const uint32_t *flags, const uint32_t *scan, int64_t n, int nleaf,
                        Leaves lv, cudaStream_t st);
 void launch_leaf_bounds(const State &s, const BoxDev *boxes, Leaves lv, int nleaf, int mixed,

@@ -170,6 +170,32 @@ __device__ __forceinline__ bool out_of_range(const WarpBox &b, const float4 &fr,
     return gap2 >= R * R;
 }
 
+// Mask of leaf J's 32-particle chunks whose boxes (J's frame) lie within R of
+// the warp's target box (shifted into J's frame by -s).  All of J's chunks
+// when a per-pair wrap is needed.
+__device__ __forceinline__ uint32_t chunks_in_range(const Leaves &lv, uint32_t J, uint32_t cJ,
+                                                    const WarpBox &b, const float4 &fr, float R)
+{
+    const uint32_t nch = (cJ + 31u) / 32u;
+    if (fr.w < 0.f) return (1u << nch) - 1u;
+    const float cx = b.cx - fr.x, cy = b.cy - fr.y, cz = b.cz - fr.z;
+    uint32_t mask = 0;
+#pragma unroll
+    for (int c = 0; c < kChunks; ++c) {
+        if ((uint32_t)c >= nch) break;
+        const float4 lo = lv.clo[(size_t)J * kChunks + c], hi = lv.chi[(size_t)J * kChunks + c];
+        float gap2 = 0.f, g;
+        g = fabsf(0.5f * (lo.x + hi.x) - cx) - 0.5f * (hi.x - lo.x) - b.ex;
+        if (g > 0.f) gap2 += g * g;
+        g = fabsf(0.5f * (lo.y + hi.y) - cy) - 0.5f * (hi.y - lo.y) - b.ey;
+        if (g > 0.f) gap2 += g * g;
+        g = fabsf(0.5f * (lo.z + hi.z) - cz) - 0.5f * (hi.z - lo.z) - b.ez;
+        if (g > 0.f) gap2 += g * g;
+        if (gap2 < R * R) mask |= 1u << c;
+    }
+    return mask;
+}
+
 // Target position q in the frame of the staged leaf J.
 template <typename R>
 struct Target {
@@ -215,16 +241,16 @@ __device__ __forceinline__ R sep2(const Vec4<R> &rj, const Target<R> &q, R L, R 
 
 // Candidate test over a staged tile: bit j of m[j/32] set when r^2 < thr
 // (one threshold per target) or r^2 < max(thr, thrj[j]) (per candidate).
-// 32-slot chunks past the leaf's end are skipped.
+// Only the 32-slot chunks set in cm are staged and tested.
 template <typename R, int JMAX, bool WRAP, bool PERJ>
 __device__ __forceinline__ void test_tile(const Vec4<R> *tile, const float *thrj, const Target<R> &q,
-                                          R L, R hL, R thr, uint32_t cJ, uint32_t (&m)[JMAX / 32])
+                                          R L, R hL, R thr, uint32_t cm, uint32_t (&m)[JMAX / 32])
 {
 #pragma unroll
     for (int w = 0; w < JMAX / 32; ++w) {
         uint32_t bits = 0;
         m[w] = 0;
-        if ((uint32_t)(32 * w) >= cJ) continue;
+        if (!((cm >> w) & 1u)) continue;
 #pragma unroll
         for (int b = 0; b < 32; ++b) {
             const int j = 32 * w + b;
@@ -240,11 +266,11 @@ __device__ __forceinline__ void test_tile(const Vec4<R> *tile, const float *thrj
 
 template <typename R, int JMAX, bool PERJ>
 __device__ __forceinline__ void test_tile_any(const Vec4<R> *tile, const float *thrj,
-                                              const Target<R> &q, R L, R hL, R thr, uint32_t cJ,
+                                              const Target<R> &q, R L, R hL, R thr, uint32_t cm,
                                               uint32_t (&m)[JMAX / 32])
 {
-    if (q.wrap) test_tile<R, JMAX, true, PERJ>(tile, thrj, q, L, hL, thr, cJ, m);
-    else test_tile<R, JMAX, false, PERJ>(tile, thrj, q, L, hL, thr, cJ, m);
+    if (q.wrap) test_tile<R, JMAX, true, PERJ>(tile, thrj, q, L, hL, thr, cm, m);
+    else test_tile<R, JMAX, false, PERJ>(tile, thrj, q, L, hL, thr, cm, m);
 }
 
 template <typename R>
@@ -266,13 +292,14 @@ __device__ __forceinline__ void set_error(int *err, int code, uint32_t id)
     atomicMin(err + 1, (int)id);
 }
 
-// Warp-cooperative staging of leaf J's records: slots [0, round32(cJ)).
+// Warp-cooperative staging of leaf J's records, chunks set in cm only.
 template <typename R>
 __device__ __forceinline__ void stage(Vec4<R> *tile, const Vec4<R> *__restrict__ src, uint32_t sJ,
-                                      uint32_t cJ, uint32_t lane)
+                                      uint32_t cJ, uint32_t cm, uint32_t lane)
 {
     const uint32_t end = (cJ + 31u) & ~31u;
     for (uint32_t k = lane; k < end; k += 32u) {
+        if (!((cm >> (k / 32u)) & 1u)) continue;
         Vec4<R> v;
         if (k < cJ) {
             v = src[sJ + k];
@@ -388,13 +415,15 @@ __global__ void __launch_bounds__(kBlock) density_k(PassArgs a)
         const float4 fr = a.hfr[p];
         if (out_of_range(wb, fr, a.lv.ex[J], a.lv.ey[J], a.lv.ez[J], Rc)) continue;
         const uint32_t sJ = a.lv.start[J], cJ = a.lv.count[J];
+        const uint32_t cm = chunks_in_range(a.lv, J, cJ, wb, fr, Rc);
+        if (cm == 0u) continue;
         __syncwarp();
-        stage(tile, pm, sJ, cJ, lane);
+        stage(tile, pm, sJ, cJ, cm, lane);
         __syncwarp();
         const Target<R> q = target_in_frame(ri, fr);
         const R gb = Real<R>::mixed ? (R)guard_band((float)H, q.mag) : (R)0;
         uint32_t m[JMAX / 32];
-        test_tile_any<R, JMAX, false>(tile, nullptr, q, L, hL, COUNT ? H2 + gb : H2, G.act ? cJ : 0u, m);
+        test_tile_any<R, JMAX, false>(tile, nullptr, q, L, hL, COUNT ? H2 + gb : H2, G.act ? cm : 0u, m);
 #pragma unroll
         for (int ww = 0; ww < JMAX / 32; ++ww) {
             uint32_t bits = m[ww];
@@ -498,6 +527,58 @@ __device__ bool crk_solve(const double *m, double *out)
 //   d_g m0 += V d_gW, d_g m1^a += V (x^a d_gW + delta_ag W),
 //   d_g m2^ab += V (x^a x^b d_gW + (delta_ag x^b + delta_bg x^a) W)
 // then the FP64 correction solve; writes hrec2.w = A and hrec3..6.
+// The moment sums of one in-range pair, accumulated FMA-first.
+template <typename R>
+struct MomentAcc {
+    R m0, m1[3], m2[6], dm0[3], dm1[9], dm2[18];
+
+    __device__ __forceinline__ void zero()
+    {
+        m0 = 0;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { m1[k] = 0; dm0[k] = 0; }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) m2[k] = 0;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) dm1[k] = 0;
+#pragma unroll
+        for (int k = 0; k < 18; ++k) dm2[k] = 0;
+    }
+
+    // x = x_i - x_j, VW = V_j W_ij, Vg = V_j g (V_j grad_i W = Vg x)
+    __device__ __forceinline__ void add(const R x[3], R VW, R Vg)
+    {
+        const R d[3] = {Vg * x[0], Vg * x[1], Vg * x[2]};
+        const R xx[6] = {x[0] * x[0], x[0] * x[1], x[0] * x[2], x[1] * x[1], x[1] * x[2], x[2] * x[2]};
+        constexpr int SA[6] = {0, 0, 0, 1, 1, 2};  // packed (ab): xx xy xz yy yz zz
+        constexpr int SB[6] = {0, 1, 2, 1, 2, 2};
+        m0 += VW;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            m1[c] = fma(VW, x[c], m1[c]);
+            dm0[c] += d[c];
+        }
+#pragma unroll
+        for (int s = 0; s < 6; ++s) m2[s] = fma(VW, xx[s], m2[s]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                dm1[3 * c + q] = fma(x[c], d[q], dm1[3 * c + q]);
+                if (c == q) dm1[3 * c + q] += VW;
+            }
+#pragma unroll
+        for (int s = 0; s < 6; ++s)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                R v = fma(xx[s], d[q], dm2[3 * s + q]);
+                if (SA[s] == q) v = fma(VW, x[SB[s]], v);
+                if (SB[s] == q) v = fma(VW, x[SA[s]], v);
+                dm2[3 * s + q] = v;
+            }
+    }
+};
+
 template <typename R, int JMAX>
 __global__ void __launch_bounds__(kBlock) moments_k(PassArgs a)
 {
@@ -526,23 +607,21 @@ __global__ void __launch_bounds__(kBlock) moments_k(PassArgs a)
     rel_pos(ri, a.lv, I, px, py, pz);
     const WarpBox wb = warp_box(px, py, pz, G.act);
     const float Rc = warp_max(G.act ? (float)H : 0.f) * 1.0001f + 1e-6f * (float)Ld;
-    R m0 = 0, m1[3] = {0, 0, 0}, m2[6] = {0, 0, 0, 0, 0, 0};
-    R dm0[3] = {0, 0, 0}, dm1[9], dm2[18];
-#pragma unroll
-    for (int k = 0; k < 9; ++k) dm1[k] = 0;
-#pragma unroll
-    for (int k = 0; k < 18; ++k) dm2[k] = 0;
+    MomentAcc<R> acc;
+    acc.zero();
     for (uint32_t p = a.hrow[I]; p < a.hrow[I + 1]; ++p) {
         const uint32_t J = a.hcol[p];
         const float4 fr = a.hfr[p];
         if (out_of_range(wb, fr, a.lv.ex[J], a.lv.ey[J], a.lv.ez[J], Rc)) continue;
         const uint32_t sJ = a.lv.start[J], cJ = a.lv.count[J];
+        const uint32_t cm = chunks_in_range(a.lv, J, cJ, wb, fr, Rc);
+        if (cm == 0u) continue;
         __syncwarp();
-        stage(tile, rec0, sJ, cJ, lane);
+        stage(tile, rec0, sJ, cJ, cm, lane);
         __syncwarp();
         const Target<R> q = target_in_frame(ri, fr);
         uint32_t m[JMAX / 32];
-        test_tile_any<R, JMAX, false>(tile, nullptr, q, L, hL, H2, G.act ? cJ : 0u, m);
+        test_tile_any<R, JMAX, false>(tile, nullptr, q, L, hL, H2, G.act ? cm : 0u, m);
 #pragma unroll
         for (int ww = 0; ww < JMAX / 32; ++ww) {
             uint32_t bits = m[ww];
@@ -554,52 +633,25 @@ __global__ void __launch_bounds__(kBlock) moments_k(PassArgs a)
                 const R r2 = q.wrap ? sep2<R, true>(rj, q, L, hL, dx, dy, dz)
                                     : sep2<R, false>(rj, q, L, hL, dx, dy, dz);
                 const R x[3] = {-dx, -dy, -dz};
-                R W, g;
-                kernel_wg(Real<R>::sqrt_(r2), invH, cW, cG, W, g);
-                const R VW = rj.w * W;
-                const R Vg = rj.w * g;
-                const R VWx[3] = {VW * x[0], VW * x[1], VW * x[2]};
-                const R dW[3] = {Vg * x[0], Vg * x[1], Vg * x[2]};
-                const R xx[6] = {x[0] * x[0], x[0] * x[1], x[0] * x[2], x[1] * x[1], x[1] * x[2], x[2] * x[2]};
-                m0 += VW;
-#pragma unroll
-                for (int c = 0; c < 3; ++c) m1[c] += VWx[c];
-#pragma unroll
-                for (int s = 0; s < 6; ++s) m2[s] += VW * xx[s];
-#pragma unroll
-                for (int c = 0; c < 3; ++c) dm0[c] += dW[c];
-#pragma unroll
-                for (int c = 0; c < 3; ++c)
-#pragma unroll
-                    for (int qd = 0; qd < 3; ++qd) dm1[3 * c + qd] += x[c] * dW[qd] + (c == qd ? VW : (R)0);
-                // packed (ab): 0 xx, 1 xy, 2 xz, 3 yy, 4 yz, 5 zz
-                constexpr int SA[6] = {0, 0, 0, 1, 1, 2};
-                constexpr int SB[6] = {0, 1, 2, 1, 2, 2};
-#pragma unroll
-                for (int s = 0; s < 6; ++s)
-#pragma unroll
-                    for (int qd = 0; qd < 3; ++qd) {
-                        R v = xx[s] * dW[qd];
-                        if (SA[s] == qd) v += VWx[SB[s]];
-                        if (SB[s] == qd) v += VWx[SA[s]];
-                        dm2[3 * s + qd] += v;
-                    }
+                R Wv, g;
+                kernel_wg(Real<R>::sqrt_(r2), invH, cW, cG, Wv, g);
+                acc.add(x, rj.w * Wv, rj.w * g);
             }
         }
     }
     if (!G.act) return;
     double m[40];
-    m[0] = (double)m0;
+    m[0] = (double)acc.m0;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) m[1 + c] = (double)m1[c];
+    for (int c = 0; c < 3; ++c) m[1 + c] = (double)acc.m1[c];
 #pragma unroll
-    for (int s = 0; s < 6; ++s) m[4 + s] = (double)m2[s];
+    for (int s = 0; s < 6; ++s) m[4 + s] = (double)acc.m2[s];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) m[10 + c] = (double)dm0[c];
+    for (int c = 0; c < 3; ++c) m[10 + c] = (double)acc.dm0[c];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) m[13 + k] = (double)dm1[k];
+    for (int k = 0; k < 9; ++k) m[13 + k] = (double)acc.dm1[k];
 #pragma unroll
-    for (int k = 0; k < 18; ++k) m[22 + k] = (double)dm2[k];
+    for (int k = 0; k < 18; ++k) m[22 + k] = (double)acc.dm2[k];
     double o[16];
     if (!crk_solve(m, o)) {
 #pragma unroll
@@ -715,9 +767,12 @@ __global__ void __launch_bounds__(kBlock) hydro_k(PassArgs a)
         const float Rc = fmaxf(Hw, a.lv.hmax[J]) * 1.0001f + 1e-6f * (float)Ld;
         if (out_of_range(wb, fr, a.lv.ex[J], a.lv.ey[J], a.lv.ez[J], Rc)) continue;
         const uint32_t sJ = a.lv.start[J], cJ = a.lv.count[J];
+        const uint32_t cm = chunks_in_range(a.lv, J, cJ, wb, fr, Rc);
+        if (cm == 0u) continue;
         __syncwarp();
-        stage(tile[0], reinterpret_cast<const R4 *>(a.hrec[0]), sJ, cJ, lane);
+        stage(tile[0], reinterpret_cast<const R4 *>(a.hrec[0]), sJ, cJ, cm, lane);
         for (uint32_t k = lane; k < cJ; k += 32u) {
+            if (!((cm >> (k / 32u)) & 1u)) continue;
 #pragma unroll
             for (int r = 1; r < 7; ++r) tile[r][k] = reinterpret_cast<const R4 *>(a.hrec[r])[sJ + k];
             const float Hj = 2.0f * (float)tile[1][k].w;
@@ -727,7 +782,7 @@ __global__ void __launch_bounds__(kBlock) hydro_k(PassArgs a)
         __syncwarp();
         const Target<R> q = target_in_frame(ri0, fr);
         uint32_t m[JMAX / 32];
-        test_tile_any<R, JMAX, true>(tile[0], h2j, q, L, hL, H2i, G.act ? cJ : 0u, m);
+        test_tile_any<R, JMAX, true>(tile[0], h2j, q, L, hL, H2i, G.act ? cm : 0u, m);
         if (J == (uint32_t)I) {
             // the target itself is slot (i - sJ) of its own leaf
             const uint32_t self = i - sJ;
@@ -847,13 +902,15 @@ __global__ void __launch_bounds__(kBlock) gravity_k(PassArgs a)
         const float4 fr = a.gfr[p];
         if (out_of_range(wb, fr, a.lv.ex[J], a.lv.ey[J], a.lv.ez[J], Rc)) continue;
         const uint32_t sJ = a.lv.start[J], cJ = a.lv.count[J];
+        const uint32_t cm = chunks_in_range(a.lv, J, cJ, wb, fr, Rc);
+        if (cm == 0u) continue;
         __syncwarp();
-        stage(tile, pm, sJ, cJ, lane);
+        stage(tile, pm, sJ, cJ, cm, lane);
         __syncwarp();
         const Target<R> q = target_in_frame(ri, fr);
         const R gb = Real<R>::mixed ? (R)guard_band((float)rc, q.mag) : (R)0;
         uint32_t m[JMAX / 32];
-        test_tile_any<R, JMAX, false>(tile, nullptr, q, L, hL, rc2 + gb, G.act ? cJ : 0u, m);
+        test_tile_any<R, JMAX, false>(tile, nullptr, q, L, hL, rc2 + gb, G.act ? cm : 0u, m);
         if (J == (uint32_t)I) {
             const uint32_t self = i - sJ;
 #pragma unroll

@@ -73,7 +73,7 @@ struct crk_sim {
     DBuf stA[16], stB[16];  // state arrays, double-buffered
     State sa{}, sb{};
     DBuf keys, keys_alt, vals, vals_alt, counts, scan_tmp, flags, flag_scan, scalars;
-    DBuf lv_u32[3], lv_sp, lv_c[3], lv_e[3], lv_h;
+    DBuf lv_u32[3], lv_sp, lv_c[3], lv_e[3], lv_h, lv_chunk[2];
     DBuf nd_f[7], nd_slot;
     DBuf hrow, grow, hcnt, gcnt, hcol, gcol, hfr, gfr;
     DBuf pm, hrec[7], uhat, acc_h, acc_g;

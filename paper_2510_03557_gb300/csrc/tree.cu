@@ -246,13 +246,14 @@ __device__ __forceinline__ bool cell_fits(const uint64_t *__restrict__ keys, int
 // Cells are found per particle by a binary search over the levels (a cell's
 // count only shrinks with depth).  Particles that share even the finest cell
 // are cut by count.  flags[k] = 1 where a leaf starts.
-__global__ void leaf_flags_k(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ slot,
+__global__ void leaf_flags_k(const uint64_t *__restrict__ keys, int sb,
                              const BoxDev *__restrict__ boxes, int64_t n, int cap, uint32_t *flags)
 {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    const int s0 = boxes[slot[k]].cm_shift;  // shift of the chaining-mesh bin
     const uint64_t key = keys[k];
+    const uint32_t slot = sb ? (uint32_t)(key >> (64 - sb)) : 0u;
+    const int s0 = boxes[slot].cm_shift;     // shift of the chaining-mesh bin
     const int lmax = s0 / 3;                 // deepest level with a non-negative shift
     int la = 0, lb = lmax + 1;
     int64_t lo = 0;
@@ -348,6 +349,28 @@ __global__ void leaf_bounds_k(State s, Leaves lv, int nleaf, void *pm, Nodes nd)
         nd.hiz[w] = __double2float_ru(hi[2]);
         nd.hmax[w] = __double2float_ru(hm);
         nd.slot[w] = (int32_t)s.slot[s0];
+    }
+    // Boxes of the 32-particle chunks (particle t of the leaf is in chunk t/32),
+    // relative to the leaf centre, rounded outward; empty chunks get an
+    // inverted box that is never in range.
+#pragma unroll
+    for (int ch = 0; ch < kChunks; ++ch) {
+        const uint32_t t = 32u * ch + lane;
+        const bool in = t < c;
+        const uint32_t i = s0 + (in ? t : 0u);
+        const double px = s.x[i] - cen[0], py = s.y[i] - cen[1], pz = s.z[i] - cen[2];
+        const double lx = wmin(in ? px : DBL_MAX), hx = wmax(in ? px : -DBL_MAX);
+        const double ly = wmin(in ? py : DBL_MAX), hy = wmax(in ? py : -DBL_MAX);
+        const double lz = wmin(in ? pz : DBL_MAX), hz = wmax(in ? pz : -DBL_MAX);
+        if (lane == 0) {
+            const bool any = 32u * ch < c;
+            lv.clo[(size_t)w * kChunks + ch] =
+                any ? make_float4(__double2float_rd(lx), __double2float_rd(ly), __double2float_rd(lz), 0.f)
+                    : make_float4(1e30f, 1e30f, 1e30f, 0.f);
+            lv.chi[(size_t)w * kChunks + ch] =
+                any ? make_float4(__double2float_ru(hx), __double2float_ru(hy), __double2float_ru(hz), 0.f)
+                    : make_float4(-1e30f, -1e30f, -1e30f, 0.f);
+        }
     }
     for (uint32_t t = lane; t < c; t += 32) {
         uint32_t i = s0 + t;
@@ -485,6 +508,90 @@ __global__ void pair_walk_k(Nodes nd, Leaves lv, const BoxDev *__restrict__ boxe
     if (!FILL) counts[I] = cnt;
 }
 
+// Orders the particles of every leaf so that each run of 32 (the chunks and
+// warp target groups of the pair passes) is a compact slab: a leaf's range is
+// cut at a multiple of 32 by a plane normal to its longest axis (particles
+// ranked by that coordinate, ties by position), then each side again, down to
+// 32 (k-d splits inside the base leaf).  perm maps sorted position -> original
+// index and is rewritten within each leaf.  One warp per leaf, leaf <= 128.
+constexpr int kKdWarps = 4;
+
+struct KdScratch {
+    float x[128], y[128], z[128];
+    uint32_t id[128];
+    float tx[128], ty[128], tz[128];
+    uint32_t tid[128];
+};
+
+__device__ void kd_sort_range(KdScratch &S, uint32_t lo, uint32_t hi, uint32_t lane)
+{
+    float mn[3] = {FLT_MAX, FLT_MAX, FLT_MAX}, mx[3] = {-FLT_MAX, -FLT_MAX, -FLT_MAX};
+    for (uint32_t t = lo + lane; t < hi; t += 32) {
+        const float p[3] = {S.x[t], S.y[t], S.z[t]};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) { mn[a] = fminf(mn[a], p[a]); mx[a] = fmaxf(mx[a], p[a]); }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mn[a] = fminf(mn[a], __shfl_xor_sync(0xffffffffu, mn[a], o));
+            mx[a] = fmaxf(mx[a], __shfl_xor_sync(0xffffffffu, mx[a], o));
+        }
+    int axis = 0;
+    if (mx[1] - mn[1] > mx[axis] - mn[axis]) axis = 1;
+    if (mx[2] - mn[2] > mx[axis] - mn[axis]) axis = 2;
+    const float *key = axis == 0 ? S.x : (axis == 1 ? S.y : S.z);
+    for (uint32_t t = lo + lane; t < hi; t += 32) {
+        const float kt = key[t];
+        uint32_t r = 0;
+        for (uint32_t q = lo; q < hi; ++q) {
+            const float kq = key[q];
+            r += (kq < kt || (kq == kt && q < t)) ? 1u : 0u;
+        }
+        const uint32_t d = lo + r;
+        S.tx[d] = S.x[t];
+        S.ty[d] = S.y[t];
+        S.tz[d] = S.z[t];
+        S.tid[d] = S.id[t];
+    }
+    __syncwarp();
+    for (uint32_t t = lo + lane; t < hi; t += 32) {
+        S.x[t] = S.tx[t];
+        S.y[t] = S.ty[t];
+        S.z[t] = S.tz[t];
+        S.id[t] = S.tid[t];
+    }
+    __syncwarp();
+}
+
+__global__ void kd_order_k(State s, Leaves lv, int nleaf, uint32_t *perm)
+{
+    __shared__ KdScratch scratch[kKdWarps];
+    const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    const int L = blockIdx.x * kKdWarps + (int)w;
+    if (L >= nleaf) return;
+    const uint32_t s0 = lv.start[L], c = lv.count[L];
+    if (c <= 32u) return;
+    KdScratch &S = scratch[w];
+    const uint32_t id0 = perm[s0];
+    const double x0 = s.x[id0], y0 = s.y[id0], z0 = s.z[id0];
+    for (uint32_t t = lane; t < c; t += 32) {
+        const uint32_t id = perm[s0 + t];
+        S.x[t] = (float)(s.x[id] - x0);
+        S.y[t] = (float)(s.y[id] - y0);
+        S.z[t] = (float)(s.z[id] - z0);
+        S.id[t] = id;
+    }
+    __syncwarp();
+    const uint32_t g = (c + 31u) / 32u;
+    kd_sort_range(S, 0, c, lane);
+    const uint32_t cut = 32u * ((g + 1u) / 2u);
+    if (cut > 32u) kd_sort_range(S, 0, cut, lane);
+    if (c > cut + 32u) kd_sort_range(S, cut, c, lane);
+    for (uint32_t t = lane; t < c; t += 32) perm[s0 + t] = S.id[t];
+}
+
 // Warp work items of the pair passes: every leaf is cut into target groups
 // of at most 32 consecutive particles; (leaf, first particle offset).
 __global__ void group_count_k(Leaves lv, int nleaf, int gas_only, uint32_t *counts)
@@ -507,6 +614,14 @@ __global__ void group_fill_k(Leaves lv, int nleaf, int gas_only, const uint32_t 
 inline unsigned grid_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 }  // namespace
+
+void launch_leaf_kd_order(const State &unsorted, const Leaves &lv, int nleaf, uint32_t *perm,
+                          cudaStream_t st)
+{
+    if (nleaf <= 0) return;
+    kd_order_k<<<grid_for(nleaf, kKdWarps), 32 * kKdWarps, 0, st>>>(unsorted, lv, nleaf, perm);
+    note_launches(1);
+}
 
 void launch_group_count(const Leaves &lv, int nleaf, int gas_only, uint32_t *counts, cudaStream_t st)
 {
@@ -578,11 +693,11 @@ void launch_permute(const State &src, const State &dst, const uint32_t *perm, in
     note_launches(1);
 }
 
-void launch_leaf_flags(const uint64_t *keys, const State &s, const BoxDev *boxes, int64_t n,
+void launch_leaf_flags(const uint64_t *keys, int slot_bits, const BoxDev *boxes, int64_t n,
                        int cap, uint32_t *flags, cudaStream_t st)
 {
     if (n <= 0) return;
-    leaf_flags_k<<<grid_for(n, kT), kT, 0, st>>>(keys, s.slot, boxes, n, cap, flags);
+    leaf_flags_k<<<grid_for(n, kT), kT, 0, st>>>(keys, slot_bits, boxes, n, cap, flags);
     note_launches(1);
 }
 
