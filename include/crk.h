@@ -243,6 +243,39 @@ int crk_poll(crk_service *service, uint64_t ticket, crk_job_result *result, int6
 /* Stops the service thread after the resident jobs finish and frees it. */
 int crk_service_destroy(crk_service *service);
 
+/* ------------------------------------------------------------------ */
+/* Allocation-free neighbour sets.                                      */
+/* ------------------------------------------------------------------ */
+/* For callers that cannot allocate device memory: code whose GPU memory is
+ * owned by another allocator (a framework's caching pool, where a raw
+ * cudaMalloc both fragments the pool and synchronises the device) and
+ * latency-critical loops where the implicit device synchronisation of
+ * cudaMalloc / cudaFree is not acceptable.  The paper has no counterpart;
+ * this is a service of the library.
+ *
+ * Computes, for n particles of one periodic box of side `box`, the size and
+ * hash of every gas particle's hydro gather set {gas j != i : r^2 < (2h_i)^2}
+ * -- the same definition, exact FP64 predicate and hash as crk_forces'
+ * nbr_count / nbr_hash for that box loaded alone (0 for DM particles).
+ * pos (3n AoS, in [0, box)), h (n), species (n), count (n) and hash (n) are
+ * CUDA device pointers; work is ordered on cuda_stream (a cudaStream_t,
+ * NULL = legacy default stream) and the call returns without waiting.
+ *
+ * It allocates nothing: every temporary lives in one fixed device array of
+ * about 6.6 MB inside the library, which every GPU that loads the library
+ * holds until the process exits.  The first call on a device looks up that
+ * array's device address for the current device; make the first call on each
+ * device before any stream capture.  All calls share the one array and it
+ * keeps the last call's contents, so calls whose GPU work overlaps (on
+ * different streams or threads) race: order them on one stream.
+ *
+ * Errors (returned; crk_last_error() is not updated by this call):
+ * CRK_EINVAL for n < 0, n > CRK_NOALLOC_MAX_N, box <= 0 or a NULL pointer
+ * when n > 0; CRK_ECUDA if a launch or the address look-up fails. */
+#define CRK_NOALLOC_MAX_N 262144
+int crk_neighbours_noalloc(int64_t n, const double *pos, const double *h, const uint8_t *species,
+                           double box, int32_t *count, uint64_t *hash, void *cuda_stream);
+
 /* Thread-local message of the last failing call on this thread. */
 const char *crk_last_error(void);
 

@@ -36,7 +36,8 @@ CRK_GAS = 1
 ABI = ("crk_create", "crk_load", "crk_load_boxes", "crk_forces", "crk_step", "crk_step_boxes",
        "crk_get_state", "crk_set_state", "crk_get_sums", "crk_get_size", "crk_set_timing", "crk_get_timings",
        "crk_destroy", "crk_service_create", "crk_submit", "crk_poll", "crk_service_destroy",
-       "crk_last_error")
+       "crk_neighbours_noalloc", "crk_last_error")
+CRK_NOALLOC_MAX_N = 262144
 
 
 class CrkError(RuntimeError):
@@ -324,6 +325,19 @@ def crk_poll(svc, ticket: int, n: int, timeout_us: int = -1):
 
 def crk_service_destroy(svc):
     _check(lib().crk_service_destroy(svc))
+
+
+def crk_neighbours_noalloc(n: int, pos, h, species, box: float, count, hash_, stream=None) -> int:
+    """Allocation-free hydro gather-set sizes and hashes (device tensors
+    only).  Returns the C return code unchanged (the call does not update
+    crk_last_error); work is queued on ``stream``."""
+    args = [_ptr(pos, np.float64), _ptr(h, np.float64), _ptr(species, np.uint8),
+            _ptr(count, np.int32), _ptr(hash_, np.uint64)]
+    if any(a[1] != CRK_MEM_DEVICE for a in args):
+        raise TypeError("crk_neighbours_noalloc takes CUDA device tensors")
+    return int(lib().crk_neighbours_noalloc(ctypes.c_int64(n), *[a[0] for a in args[:3]],
+                                            ctypes.c_double(box), args[3][0], args[4][0],
+                                            _stream_handle(stream)))
 
 
 def crk_last_error() -> str:
