@@ -481,15 +481,16 @@ __global__ void pair_walk_k(Nodes nd, Leaves lv, const BoxDev *__restrict__ boxe
             float d, g;
             d = 0.5f * (nd.lox[off] + nd.hix[off]) - cix;
             if (d >= hL) d -= L; else if (d < -hL) d += L;
-            g = fabsf(d) - eix - 0.5f * (nd.hix[off] - nd.lox[off]);
+            // extents summed first: the test is exactly symmetric in (I, J)
+            g = fabsf(d) - (eix + 0.5f * (nd.hix[off] - nd.lox[off]));
             if (g > 0.f) gap2 += g * g;
             d = 0.5f * (nd.loy[off] + nd.hiy[off]) - ciy;
             if (d >= hL) d -= L; else if (d < -hL) d += L;
-            g = fabsf(d) - eiy - 0.5f * (nd.hiy[off] - nd.loy[off]);
+            g = fabsf(d) - (eiy + 0.5f * (nd.hiy[off] - nd.loy[off]));
             if (g > 0.f) gap2 += g * g;
             d = 0.5f * (nd.loz[off] + nd.hiz[off]) - ciz;
             if (d >= hL) d -= L; else if (d < -hL) d += L;
-            g = fabsf(d) - eiz - 0.5f * (nd.hiz[off] - nd.loz[off]);
+            g = fabsf(d) - (eiz + 0.5f * (nd.hiz[off] - nd.loz[off]));
             if (g > 0.f) gap2 += g * g;
             if (gap2 >= Rm * Rm) continue;
         }

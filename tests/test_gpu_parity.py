@@ -119,6 +119,21 @@ def test_clustered_variable_h_matches_oracle(crk, precision, leaf_cap):
     compare(out, ref, oracle_counts(s, op), precision, label=f"clustered cap={leaf_cap}")
 
 
+@pytest.mark.parametrize("leaf_cap", [64, 128])
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_force_only_path_matches_oracle(crk, precision, leaf_cap):
+    """The force-only call (no neighbour-set outputs) runs the pass variants
+    that skip counting and hashing; the forces are the same."""
+    for s, phys in ((_clustered(seed=77),
+                     dict(box=1.0, G=1.0, gamma=5.0 / 3.0, r_cut=0.12, r_split=0.12 / 4.5, eps_soft=1e-3)),
+                    (box_dict(wl.jittered_lattice(20, seed=8)), wl.jittered_lattice(20, seed=8).params())):
+        op = oracle.make_params(**phys)
+        ref = oracle.forces(s["pos"], s["vel"], s["mass"], s["u"], s["h"], s["species"], op)
+        assert ref["rc"] == 0
+        out = run_gpu(crk, s, crk.physics(**phys), precision, leaf_cap=leaf_cap, counts=False)
+        compare(out, ref, {}, precision, label=f"force-only cap={leaf_cap}")
+
+
 @pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
 def test_momentum_and_energy_rates_vanish(crk, precision):
     s = _clustered(seed=5)
