@@ -122,6 +122,186 @@ def cpu_baseline(n: int = 80):
                       f"force evaluation {t1 - t0:.2f} s"}
 
 
+def serve_bench(crk, wl, args, stream):
+    """The serving workload on a bounded sample: the first ``count`` requests
+    of the 2,000-request stream (n log-uniform in [16, 128], 20 KDK steps at
+    dt = 1e-3, FP32-mixed, 150 GB budget).  A closed-loop calibration batch
+    fixes the saturated throughput; Poisson arrivals are then issued at 70% of
+    it and the service reports each request's submit-to-completion latency.
+    Beside it, sequential plain-FP64 solves (one handle per request, one box
+    per launch) of a few of the same requests give the FP64 rate."""
+    import concurrent.futures as cf
+
+    count = args.serve_requests
+    reqs = wl.serving_requests(2000)[:count]
+    with cf.ThreadPoolExecutor(8) as ex:
+        boxes = list(ex.map(lambda r: wl.gaussian_field_box(r[0], seed=r[1]), reqs))
+    steps = 20
+    svc = crk.crk_service_create(150 * 10**9, max_slots=64, precision=crk.CRK_MIXED,
+                                 leaf_cap=args.serve_leaf_cap)
+
+    def submit(b):
+        return crk.crk_submit(svc, crk.box_physics(b), b.pos, b.vel, b.mass, b.u, b.h, b.species,
+                              b.dt, steps)
+
+    def collect(tickets, bs):
+        return [crk.crk_poll(svc, t, b.n, -1) for t, b in zip(tickets, bs)]
+
+    # calibration: a closed batch, everything submitted at once
+    calib = boxes[:min(32, count)]
+    t0 = time.perf_counter()
+    collect([submit(b) for b in calib], calib)
+    t_cal = time.perf_counter() - t0
+    capacity = len(calib) / t_cal                       # requests/s when saturated
+    rate = 0.7 * capacity
+    arrivals = wl.poisson_arrivals(count, rate, seed=5)
+    tickets = []
+    t0 = time.perf_counter()
+    for a, b in zip(arrivals, boxes):
+        while time.perf_counter() - t0 < a:
+            time.sleep(min(1e-3, max(0.0, a - (time.perf_counter() - t0))))
+        tickets.append(submit(b))
+    res = collect(tickets, boxes)
+    wall = time.perf_counter() - t0
+    crk.crk_service_destroy(svc)
+    lat = np.array([r["latency_ns"] for r in res]) / 1e6
+    que = np.array([r["queue_ns"] for r in res]) / 1e6
+    psteps = sum(b.n for b in boxes) * steps
+
+    # sequential plain FP64: one request at a time, 2 steps each, on a few requests
+    seq = boxes[:min(6, count)]
+    t64 = 0.0
+    p64 = 0
+    for b in seq:
+        s = crk.Sim(crk.box_physics(b), leaf_cap=args.leaf_cap, precision=crk.CRK_FP64, stream=stream)
+        s.load(b)
+        stream.synchronize()
+        t1 = time.perf_counter()
+        s.step(b.dt, 2)
+        stream.synchronize()
+        t64 += time.perf_counter() - t1
+        p64 += b.n * 2
+        s.close()
+    return {"requests": count, "of": 2000, "steps_per_request": steps,
+            "p50_ms": round(float(np.percentile(lat, 50)), 3),
+            "p99_ms": round(float(np.percentile(lat, 99)), 3),
+            "queue_p50_ms": round(float(np.percentile(que, 50)), 3),
+            "value": psteps / wall, "unit": UNIT,
+            "arrival_rate_per_s": round(rate, 3), "load": 0.7,
+            "calibration": {"requests": len(calib), "seconds": round(t_cal, 3)},
+            "fp64_sequential": {"value": p64 / t64, "unit": UNIT, "requests": len(seq),
+                                "steps_per_request": 2}}
+
+
+def _rel_l2(x, ref):
+    d = np.linalg.norm(np.asarray(x) - np.asarray(ref))
+    r = np.linalg.norm(np.asarray(ref))
+    return float(d / r) if r > 0 else float(d)
+
+
+def run_clustered(args):
+    """Precision study on the clustered workload (2 x n^3, half uniform and
+    half in 512 Plummer spheres, adaptive h): one force evaluation plus 5 KDK
+    steps in the plain FP64 form and the FP32-mixed form, the mixed form's
+    relative error per output against FP64, both forms' conserved-sum drift,
+    and the FP64 form against the CPU oracle on a seeded sample of particles
+    (the oracle only evaluates the sample and what it depends on)."""
+    import torch
+
+    import oracle
+    from paper_2510_03557_gb300 import crk
+    from paper_2510_03557_gb300 import workloads as wl
+
+    torch.cuda.set_device(0)
+    crk.lib()
+    tg = time.perf_counter()
+    box = wl.clustered_box(args.n, seed=3)
+    t_gen = time.perf_counter() - tg
+    phys = crk.box_physics(box)
+    stream = torch.cuda.Stream()
+    gas = box.species == wl.GAS
+    runs = {}
+    for name, prec in (("fp64", crk.CRK_FP64), ("mixed", crk.CRK_MIXED)):
+        s = crk.Sim(phys, leaf_cap=args.leaf_cap, precision=prec, stream=stream)
+        s.load(box)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        out = s.forces(counts=False)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        mom0, e0, _ = crk.crk_get_sums(s.handle)
+        crk.crk_set_timing(s.handle, True)
+        k0, k1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        k0.record(stream)
+        s.step(box.dt, box.nsteps)
+        k1.record(stream)
+        torch.cuda.synchronize()
+        mom1, e1, nfl = crk.crk_get_sums(s.handle)
+        tim = crk.crk_get_timings(s.handle)
+        calls = max(tim["calls"], 1)
+        pos, vel, u = s.state()
+        pabs = float(np.sum(box.mass[:, None] * np.abs(vel)))
+        runs[name] = dict(out=out, pos=pos, vel=vel, u=u,
+                          force_ms=f0.elapsed_time(f1), step_ms=k0.elapsed_time(k1) / box.nsteps,
+                          momentum_drift=float(np.linalg.norm(np.subtract(mom1, mom0))) / max(pabs, 1e-300),
+                          energy_drift=(e1 - e0) / abs(e0), floor_events=nfl,
+                          breakdown={k: round(tim[k] / calls, 3) for k in
+                                     ("tree_ms", "pairs_ms", "density_ms", "moments_ms", "hydro_ms",
+                                      "gravity_ms", "kdk_ms")},
+                          leaves=int(tim["nleaves"]), leaf_pairs=[int(tim["pairs_hydro"]),
+                                                                  int(tim["pairs_grav"])])
+        s.close()
+    a, b = runs["mixed"], runs["fp64"]
+    err = {"acc": _rel_l2(a["out"]["acc"], b["out"]["acc"]),
+           "dudt": _rel_l2(a["out"]["dudt"][gas], b["out"]["dudt"][gas]),
+           "A": _rel_l2(a["out"]["A"][gas], b["out"]["A"][gas]),
+           "B": _rel_l2(a["out"]["B"][gas], b["out"]["B"][gas]),
+           "gradA": _rel_l2(a["out"]["gradA"][gas], b["out"]["gradA"][gas]),
+           "gradB": _rel_l2(a["out"]["gradB"][gas], b["out"]["gradB"][gas]),
+           "rho": _rel_l2(a["out"]["rho"][gas], b["out"]["rho"][gas]),
+           "pos_after_5_kdk": _rel_l2(a["pos"] - box.pos, b["pos"] - box.pos),
+           "vel_after_5_kdk": _rel_l2(a["vel"], b["vel"]),
+           "u_after_5_kdk": _rel_l2(a["u"][gas], b["u"][gas])}
+    # FP64 form against the oracle on a seeded sample
+    oracle.build()
+    rng = np.random.default_rng(33)
+    idx = np.concatenate([rng.choice(np.flatnonzero(gas), args.sample // 2, replace=False),
+                          rng.choice(np.flatnonzero(~gas), args.sample // 2, replace=False)])
+    op = oracle.make_params(**box.params())
+    to = time.perf_counter()
+    ref = oracle.forces(box.pos, box.vel, box.mass, box.u, box.h, box.species, op, sample=idx)
+    t_or = time.perf_counter() - to
+    gi = idx[gas[idx]]
+    orc = {"acc": _rel_l2(b["out"]["acc"][idx], ref["acc"][idx]),
+           "dudt": _rel_l2(b["out"]["dudt"][gi], ref["dudt"][gi]),
+           "A": _rel_l2(b["out"]["A"][gi], ref["A"][gi]),
+           "B": _rel_l2(b["out"]["B"][gi], ref["B"][gi])}
+    orc_mixed = {"acc": _rel_l2(a["out"]["acc"][idx], ref["acc"][idx]),
+                 "dudt": _rel_l2(a["out"]["dudt"][gi], ref["dudt"][gi]),
+                 "A": _rel_l2(a["out"]["A"][gi], ref["A"][gi]),
+                 "B": _rel_l2(a["out"]["B"][gi], ref["B"][gi])}
+    line = {"metric": METRIC, "value": box.n / (a["step_ms"] / 1e3), "unit": UNIT, "n_gpus": 1,
+            "steps": box.nsteps, "ms_per_step": a["step_ms"], "higher_is_better": True,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"clustered 2x{args.n}^3 precision study (512 Plummer spheres, "
+                                   f"kNN h), 1 force evaluation + {box.nsteps} KDK at dt={box.dt}",
+                       "particles": box.n, "leaf_cap": args.leaf_cap},
+            "fp64_plain": {"value": box.n / (b["step_ms"] / 1e3), "unit": UNIT,
+                           "ms_per_step": b["step_ms"], "force_ms": b["force_ms"],
+                           "breakdown_ms": b["breakdown"], "momentum_drift": b["momentum_drift"],
+                           "energy_drift": b["energy_drift"]},
+            "mixed": {"ms_per_step": a["step_ms"], "force_ms": a["force_ms"],
+                      "breakdown_ms": a["breakdown"], "momentum_drift": a["momentum_drift"],
+                      "energy_drift": a["energy_drift"], "leaves": a["leaves"],
+                      "leaf_pairs": a["leaf_pairs"]},
+            "mixed_vs_fp64_rel_l2": err,
+            "fp64_vs_oracle_rel_l2": orc, "mixed_vs_oracle_rel_l2": orc_mixed,
+            "oracle_sample": {"particles": int(len(idx)), "seconds": round(t_or, 2),
+                              "cores": oracle.max_threads()},
+            "setup_s": round(t_gen, 1)}
+    print(json.dumps(line))
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -149,14 +329,23 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="gaussian", choices=["gaussian", "clustered"],
+                    help="clustered: the precision study (prints its own JSON line)")
+    ap.add_argument("--sample", type=int, default=64, help="oracle sample of the precision study")
     ap.add_argument("--n", type=int, default=128, help="lattice size per species (2 n^3 particles)")
     ap.add_argument("--leaf-cap", type=int, default=128)
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=192,
+                    help="requests of the serving stream to run (0: skip)")
+    ap.add_argument("--serve-leaf-cap", type=int, default=64)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "clustered":
+        run_clustered(args)
         return
 
     import torch
@@ -283,6 +472,10 @@ def main():
                "d2h_bytes_per_step": int(hp.nbytes + hv.nbytes + hu.nbytes), "steps": k_e2e}
         se.close()
 
+    serving = None
+    if args.serve_requests > 0:
+        serving = serve_bench(crk, wl, args, stream)
+
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cb = cpu_baseline()
@@ -307,6 +500,7 @@ def main():
                                                           "gravity": int(tim["pairs_grav"])},
             "breakdown_ms": breakdown,
             "fp64_plain": fp64,
+            "serving": serving,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk,
