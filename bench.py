@@ -147,23 +147,25 @@ def serve_bench(crk, wl, args, stream):
     def collect(tickets, bs):
         return [crk.crk_poll(svc, t, b.n, -1) for t, b in zip(tickets, bs)]
 
-    # calibration: a closed batch, everything submitted at once
-    calib = boxes[:min(32, count)]
-    t0 = time.perf_counter()
-    collect([submit(b) for b in calib], calib)
-    t_cal = time.perf_counter() - t0
-    capacity = len(calib) / t_cal                       # requests/s when saturated
-    rate = 0.7 * capacity
-    arrivals = wl.poisson_arrivals(count, rate, seed=5)
-    tickets = []
-    t0 = time.perf_counter()
-    for a, b in zip(arrivals, boxes):
-        while time.perf_counter() - t0 < a:
-            time.sleep(min(1e-3, max(0.0, a - (time.perf_counter() - t0))))
-        tickets.append(submit(b))
-    res = collect(tickets, boxes)
-    wall = time.perf_counter() - t0
-    crk.crk_service_destroy(svc)
+    try:
+        # calibration: a closed batch, everything submitted at once
+        calib = boxes[:min(32, count)]
+        t0 = time.perf_counter()
+        collect([submit(b) for b in calib], calib)
+        t_cal = time.perf_counter() - t0
+        capacity = len(calib) / t_cal                       # requests/s when saturated
+        rate = 0.7 * capacity
+        arrivals = wl.poisson_arrivals(count, rate, seed=5)
+        tickets = []
+        t0 = time.perf_counter()
+        for a, b in zip(arrivals, boxes):
+            while time.perf_counter() - t0 < a:
+                time.sleep(min(1e-3, max(0.0, a - (time.perf_counter() - t0))))
+            tickets.append(submit(b))
+        res = collect(tickets, boxes)
+        wall = time.perf_counter() - t0
+    finally:
+        crk.crk_service_destroy(svc)
     lat = np.array([r["latency_ns"] for r in res]) / 1e6
     que = np.array([r["queue_ns"] for r in res]) / 1e6
     psteps = sum(b.n for b in boxes) * steps

@@ -829,7 +829,8 @@ int pool_init(crk_sim *s, int max_slots)
     dummy.r_cut = 0.1;
     dummy.r_split = 0.1;
     dummy.gamma = 5.0 / 3.0;
-    s->boxes.assign(max_slots, box_dev(dummy));
+    // slots 0 .. max_slots-1 take jobs; slot max_slots holds retired particles
+    s->boxes.assign((size_t)max_slots + 1, box_dev(dummy));
     for (BoxDev &b : s->boxes) b.active = 0;
     s->n = 0;
     s->n_dead = 0;
@@ -915,7 +916,7 @@ int pool_extract(crk_sim *s, int slot, int64_t n, double *pos, double *vel, doub
     const size_t nn = (size_t)n;
     RET(s->staging.ensure(nn * 7 * 8 + 256));
     double *dp = s->staging.as<double>(), *dv = dp + 3 * nn, *du = dv + 3 * nn;
-    launch_extract_slot(s->sa, s->n, (uint32_t)slot, dp, dv, du, s->st);
+    launch_extract_slot(s->sa, s->n, (uint32_t)slot, n, dp, dv, du, s->st);
     if (pos) CK(cudaMemcpyAsync(pos, dp, nn * 24, cudaMemcpyDeviceToHost, s->st));
     if (vel) CK(cudaMemcpyAsync(vel, dv, nn * 24, cudaMemcpyDeviceToHost, s->st));
     if (u) CK(cudaMemcpyAsync(u, du, nn * 8, cudaMemcpyDeviceToHost, s->st));
@@ -923,10 +924,14 @@ int pool_extract(crk_sim *s, int slot, int64_t n, double *pos, double *vel, doub
     return CRK_OK;
 }
 
-void pool_remove(crk_sim *s, int slot, int64_t n)
+int pool_remove(crk_sim *s, int slot, int64_t n)
 {
+    CK(cudaSetDevice(s->device));
+    launch_retire_slot(s->sa, s->n, (uint32_t)slot, (uint32_t)s->nbox, s->st);
+    CK(cudaGetLastError());
     s->boxes[slot].active = 0;
     s->n_dead += n;
+    return CRK_OK;
 }
 
 int pool_step(crk_sim *s, const double *dt_per_slot)

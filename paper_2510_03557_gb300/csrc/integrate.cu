@@ -299,12 +299,13 @@ __global__ void set_state_k(State s, int64_t n, const double *pos, const double 
 
 // Copies the state of one box slot out in its own load order (id = index
 // within the box).
-__global__ void extract_slot_k(State s, int64_t n, uint32_t slot, double *pos, double *vel,
-                               double *u)
+__global__ void extract_slot_k(State s, int64_t n, uint32_t slot, int64_t n_job, double *pos,
+                               double *vel, double *u)
 {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n || s.slot[k] != slot) return;
     const int64_t o = s.id[k];
+    if (o >= n_job) return;  // not one of the job's particles
     pos[3 * o] = s.x[k];
     pos[3 * o + 1] = s.y[k];
     pos[3 * o + 2] = s.z[k];
@@ -314,7 +315,23 @@ __global__ void extract_slot_k(State s, int64_t n, uint32_t slot, double *pos, d
     u[o] = s.species[k] == CRK_GAS ? s.u[k] : 0.0;
 }
 
+// Moves the particles of a removed slot to the retired slot, whose box stays
+// inactive: the next sort places them last and drops them, and the freed
+// slot can take a new job at once.
+__global__ void retire_slot_k(uint32_t *slot_of, int64_t n, uint32_t from, uint32_t to)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n && slot_of[k] == from) slot_of[k] = to;
+}
+
 }  // namespace
+
+void launch_retire_slot(const State &s, int64_t n, uint32_t from, uint32_t to, cudaStream_t st)
+{
+    if (n <= 0) return;
+    retire_slot_k<<<nblocks(n), kT, 0, st>>>(s.slot, n, from, to);
+    note_launches(1);
+}
 
 void launch_set_state(const State &s, int64_t n, const double *pos, const double *vel,
                       const double *u, cudaStream_t st)
@@ -324,11 +341,11 @@ void launch_set_state(const State &s, int64_t n, const double *pos, const double
     note_launches(1);
 }
 
-void launch_extract_slot(const State &s, int64_t n, uint32_t slot, double *pos, double *vel,
-                         double *u, cudaStream_t st)
+void launch_extract_slot(const State &s, int64_t n, uint32_t slot, int64_t n_job, double *pos,
+                         double *vel, double *u, cudaStream_t st)
 {
     if (n <= 0) return;
-    extract_slot_k<<<nblocks(n), kT, 0, st>>>(s, n, slot, pos, vel, u);
+    extract_slot_k<<<nblocks(n), kT, 0, st>>>(s, n, slot, n_job, pos, vel, u);
     note_launches(1);
 }
 

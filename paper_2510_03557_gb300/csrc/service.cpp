@@ -149,7 +149,8 @@ void worker(crk_service *sv)
                 }
             }
         }
-        for (auto &j : leaving) pool_remove(sv->sim, j->slot, j->n);
+        // a failed retirement launch leaves a CUDA error that the next step reports
+        for (auto &j : leaving) (void)pool_remove(sv->sim, j->slot, j->n);
         {
             std::lock_guard<std::mutex> lk(sv->mu);
             for (auto &j : leaving) {

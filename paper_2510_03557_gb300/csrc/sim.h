@@ -110,7 +110,7 @@ int pool_add(crk_sim *s, int slot, const crk_physics &phys, int64_t n, const dou
              const double *vel, const double *mass, const double *u, const double *h,
              const uint8_t *species);
 int pool_extract(crk_sim *s, int slot, int64_t n, double *pos, double *vel, double *u);
-void pool_remove(crk_sim *s, int slot, int64_t n);
+int pool_remove(crk_sim *s, int slot, int64_t n);
 int pool_step(crk_sim *s, const double *dt_per_slot);
 size_t pool_bytes_per_particle(const crk_sim *s);
 

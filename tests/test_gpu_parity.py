@@ -356,6 +356,26 @@ def test_service_result_is_the_same_alone_and_in_the_mix(crk):
         assert np.array_equal(alone["u"], mixed[i]["u"])
 
 
+def test_service_reuses_freed_slots(crk):
+    """Two slots, six jobs of different sizes and lengths: every freed slot
+    takes the next job while the removed job's particles still sit in the
+    arrays until the next sort.  Each result equals the job run alone."""
+    jobs = [(wl.gaussian_field_box(n, seed=400 + k), steps)
+            for k, (n, steps) in enumerate(((16, 2), (10, 5), (12, 1), (14, 3), (11, 2), (10, 1)))]
+    svc = crk.crk_service_create(8 << 30, 2)
+    try:
+        tickets = [crk.crk_submit(svc, crk.box_physics(b), b.pos, b.vel, b.mass, b.u, b.h,
+                                  b.species, 1e-3, steps) for b, steps in jobs]
+        mixed = [crk.crk_poll(svc, t, b.n, -1) for t, (b, _) in zip(tickets, jobs)]
+    finally:
+        crk.crk_service_destroy(svc)
+    for (b, steps), r in zip(jobs, mixed):
+        alone = _run_service(crk, [b], steps)[0]
+        assert np.array_equal(alone["pos"], r["pos"])
+        assert np.array_equal(alone["vel"], r["vel"])
+        assert np.array_equal(alone["u"], r["u"])
+
+
 def test_service_matches_oracle(crk):
     boxes = _job_boxes()[:3]
     res = _run_service(crk, boxes, 3, precision=0)
