@@ -6,10 +6,12 @@
 // particles; each warp takes one group (lane = target particle i) and runs
 // on its own, without block-wide barriers.  For every neighbour leaf J of the
 // target leaf's pair list the warp
-//   0. skips J when J's box is out of range of the warp's own target box,
-//   1. stages J's contiguous records in warp-private shared memory
-//      (coalesced vector loads; slots past J's end padded with far-away
-//      sentinels, so the test needs no bounds check),
+//   0. skips J when J's box, or one of its 32-particle chunk boxes, is out
+//      of range of the warp's own target box,
+//   1. stages in warp-private shared memory the records of J's particles
+//      that lie in range of the warp's target box, compacted by a ballot
+//      (one candidate per lane; the tile is padded with far-away sentinels
+//      to a multiple of 32, so the test needs no bounds check),
 //   2. tests the staged candidates with a fully unrolled, branch-free loop
 //      into a bitmask (about ten instructions per candidate), and
 //   3. evaluates the pair function of Eq. 1 on the set bits only,
@@ -292,26 +294,119 @@ __device__ __forceinline__ void set_error(int *err, int code, uint32_t id)
     atomicMin(err + 1, (int)id);
 }
 
-// Warp-cooperative staging of leaf J's records, chunks set in cm only.
+// Where a staged candidate sits relative to the target leaf's centre, in
+// FP32, for the per-candidate cut: mixed records are relative to their own
+// leaf's centre and move by the pair frame; FP64 records are absolute.
+struct CandFrame {
+    float fx, fy, fz;          // mixed: pair frame (c_J - c_I)
+    double cx, cy, cz, L, hL;  // FP64: target leaf centre and box
+    bool cull;                 // false: keep every candidate (pair needs per-pair wrap)
+};
+
 template <typename R>
-__device__ __forceinline__ void stage(Vec4<R> *tile, const Vec4<R> *__restrict__ src, uint32_t sJ,
-                                      uint32_t cJ, uint32_t cm, uint32_t lane)
+__device__ __forceinline__ void cand_pos(const Vec4<R> &v, const CandFrame &f, float &x, float &y, float &z)
 {
-    const uint32_t end = (cJ + 31u) & ~31u;
-    for (uint32_t k = lane; k < end; k += 32u) {
-        if (!((cm >> (k / 32u)) & 1u)) continue;
-        Vec4<R> v;
-        if (k < cJ) {
-            v = src[sJ + k];
-        } else {
-            v.x = Real<R>::far;
-            v.y = Real<R>::far;
-            v.z = Real<R>::far;
-            v.w = 0;
-        }
-        tile[k] = v;
+    if (Real<R>::mixed) {
+        x = (float)v.x + f.fx;
+        y = (float)v.y + f.fy;
+        z = (float)v.z + f.fz;
+    } else {
+        x = (float)wrap1((double)v.x - f.cx, f.L, f.hL);
+        y = (float)wrap1((double)v.y - f.cy, f.L, f.hL);
+        z = (float)wrap1((double)v.z - f.cz, f.L, f.hL);
     }
 }
+
+template <typename R>
+__device__ __forceinline__ CandFrame cand_frame(const Leaves &lv, int I, const float4 &fr, double L)
+{
+    CandFrame f;
+    f.fx = fr.x;
+    f.fy = fr.y;
+    f.fz = fr.z;
+    f.cx = lv.cx[I];
+    f.cy = lv.cy[I];
+    f.cz = lv.cz[I];
+    f.L = L;
+    f.hL = 0.5 * L;
+    // one wrap of (x_j - c_I) is exact only when no two points of the two
+    // leaves are L/2 apart on an axis, which the frame's sign certifies
+    f.cull = fr.w >= 0.f;
+    return f;
+}
+
+__device__ __forceinline__ float box_gap2(const WarpBox &b, float x, float y, float z)
+{
+    float gap2 = 0.f, g;
+    g = fabsf(x - b.cx) - b.ex;
+    if (g > 0.f) gap2 += g * g;
+    g = fabsf(y - b.cy) - b.ey;
+    if (g > 0.f) gap2 += g * g;
+    g = fabsf(z - b.cz) - b.ez;
+    if (g > 0.f) gap2 += g * g;
+    return gap2;
+}
+
+// Stages, compacted in J's order, the candidates of leaf J that can reach
+// the warp's target box: candidate k < cJ (in a 32-chunk set in cm) is kept
+// when its distance to the box is below Rc, or below its own radius when
+// PERJ (hydro: 2 h_j from hrec1, whose square also goes to h2j).  Writes
+// tile[0, K) and slot[0, K) (k of each kept candidate), pads the tile to a
+// multiple of 32 with far-away sentinels (h2j 0), and returns K.
+template <typename R, bool PERJ>
+__device__ __forceinline__ uint32_t stage_cull(Vec4<R> *tile, uint8_t *slot, float *h2j,
+                                               const Vec4<R> *__restrict__ src,
+                                               const Vec4<R> *__restrict__ rec1, uint32_t sJ, uint32_t cJ,
+                                               uint32_t cm, const WarpBox &wb, const CandFrame &f, float Rc,
+                                               uint32_t lane)
+{
+    uint32_t K = 0;
+    const uint32_t nch = (cJ + 31u) / 32u;
+    for (uint32_t c = 0; c < nch; ++c) {
+        if (!((cm >> c) & 1u)) continue;
+        const uint32_t k = 32u * c + lane;
+        bool keep = false;
+        Vec4<R> v;
+        float Hj2 = 0.f;
+        if (k < cJ) {
+            v = src[sJ + k];
+            float R2 = Rc * Rc;
+            if (PERJ) {
+                const float Hj = 2.0f * (float)rec1[sJ + k].w;
+                Hj2 = Hj * Hj;
+                const float Rj = Hj * 1.0001f + 1e-6f * (float)f.L;
+                R2 = fmaxf(R2, Rj * Rj);
+            }
+            keep = true;
+            if (f.cull) {
+                float x, y, z;
+                cand_pos(v, f, x, y, z);
+                keep = box_gap2(wb, x, y, z) < R2;
+            }
+        }
+        const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+            const uint32_t pos = K + __popc(bal & ((1u << lane) - 1u));
+            tile[pos] = v;
+            slot[pos] = (uint8_t)k;
+            if (PERJ) h2j[pos] = Hj2;
+        }
+        K += __popc(bal);
+    }
+    const uint32_t end = (K + 31u) & ~31u;
+    if (K + lane < end) {
+        Vec4<R> s;
+        s.x = Real<R>::far;
+        s.y = Real<R>::far;
+        s.z = Real<R>::far;
+        s.w = 0;
+        tile[K + lane] = s;
+        if (PERJ) h2j[K + lane] = 0.f;
+    }
+    return K;
+}
+
+__device__ __forceinline__ uint32_t chunk_mask(uint32_t K) { return K >= 128u ? 0xfu : (1u << ((K + 31u) / 32u)) - 1u; }
 
 // The warp's target group: up to 32 consecutive particles of leaf I.
 struct Group {
@@ -377,6 +472,14 @@ __global__ void records_k(PassArgs a)
     reinterpret_cast<R *>(a.uhat)[k] = (R)uh;
 }
 
+// Shared memory of one warp: the staged tile and the leaf slot of every
+// staged candidate.
+template <typename R, int JMAX>
+constexpr size_t tile_warp_bytes()
+{
+    return JMAX * (sizeof(Vec4<R>) + 1);
+}
+
 // ------------------------------------------------------------- density D
 // rho_i = sum_{j in N_i + {i}} m_j W(r, h_i); V = m/rho; P = (gamma-1) rho u^;
 // c = sqrt(gamma (gamma-1) u^).  Optional: size and hash of N_i.
@@ -388,7 +491,8 @@ __global__ void __launch_bounds__(kBlock) density_k(PassArgs a)
     const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
     const uint32_t gi = blockIdx.x * kWarps + w;
     if (gi >= a.n_ggas) return;
-    R4 *tile = reinterpret_cast<R4 *>(smem) + w * JMAX;
+    R4 *tile = reinterpret_cast<R4 *>(smem + (size_t)w * tile_warp_bytes<R, JMAX>());
+    uint8_t *tslot = reinterpret_cast<uint8_t *>(tile + JMAX);
     const Group G = load_group(a.lv, a.ggas, gi, lane);
     const int I = G.I;
     const uint32_t i = G.i;
@@ -418,12 +522,15 @@ __global__ void __launch_bounds__(kBlock) density_k(PassArgs a)
         const uint32_t cm = chunks_in_range(a.lv, J, cJ, wb, fr, Rc);
         if (cm == 0u) continue;
         __syncwarp();
-        stage(tile, pm, sJ, cJ, cm, lane);
+        const uint32_t K = stage_cull<R, false>(tile, tslot, nullptr, pm, nullptr, sJ, cJ, cm, wb,
+                                                cand_frame<R>(a.lv, I, fr, Ld), Rc, lane);
         __syncwarp();
+        if (K == 0u) continue;
         const Target<R> q = target_in_frame(ri, fr);
         const R gb = Real<R>::mixed ? (R)guard_band((float)H, q.mag) : (R)0;
         uint32_t m[JMAX / 32];
-        test_tile_any<R, JMAX, false>(tile, nullptr, q, L, hL, COUNT ? H2 + gb : H2, G.act ? cm : 0u, m);
+        test_tile_any<R, JMAX, false>(tile, nullptr, q, L, hL, COUNT ? H2 + gb : H2,
+                                      G.act ? chunk_mask(K) : 0u, m);
 #pragma unroll
         for (int ww = 0; ww < JMAX / 32; ++ww) {
             uint32_t bits = m[ww];
@@ -441,11 +548,12 @@ __global__ void __launch_bounds__(kBlock) density_k(PassArgs a)
                 const R om2 = om * om;
                 rho += rj.w * cW * om2 * om2 * om2 * ((R)1 + qq * ((R)6 + qq * (R)(35.0 / 3.0)));
                 if (COUNT) {
+                    const uint32_t jg = sJ + tslot[j];
                     bool in = r2 < H2;
-                    if (Real<R>::mixed && r2 >= H2 - gb) in = exact_lt(a.s, i, sJ + (uint32_t)j, Ld, H2x);
-                    if (in && sJ + (uint32_t)j != i) {
+                    if (Real<R>::mixed && r2 >= H2 - gb) in = exact_lt(a.s, i, jg, Ld, H2x);
+                    if (in && jg != i) {
                         ++nc;
-                        hs += mix64((uint64_t)a.s.id[sJ + j]);
+                        hs += mix64((uint64_t)a.s.id[jg]);
                     }
                 }
             }
@@ -587,7 +695,8 @@ __global__ void __launch_bounds__(kBlock) moments_k(PassArgs a)
     const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
     const uint32_t gi = blockIdx.x * kWarps + w;
     if (gi >= a.n_ggas) return;
-    R4 *tile = reinterpret_cast<R4 *>(smem) + w * JMAX;
+    R4 *tile = reinterpret_cast<R4 *>(smem + (size_t)w * tile_warp_bytes<R, JMAX>());
+    uint8_t *tslot = reinterpret_cast<uint8_t *>(tile + JMAX);
     const Group G = load_group(a.lv, a.ggas, gi, lane);
     const int I = G.I;
     const uint32_t i = G.i;
@@ -617,11 +726,13 @@ __global__ void __launch_bounds__(kBlock) moments_k(PassArgs a)
         const uint32_t cm = chunks_in_range(a.lv, J, cJ, wb, fr, Rc);
         if (cm == 0u) continue;
         __syncwarp();
-        stage(tile, rec0, sJ, cJ, cm, lane);
+        const uint32_t K = stage_cull<R, false>(tile, tslot, nullptr, rec0, nullptr, sJ, cJ, cm, wb,
+                                                cand_frame<R>(a.lv, I, fr, Ld), Rc, lane);
         __syncwarp();
+        if (K == 0u) continue;
         const Target<R> q = target_in_frame(ri, fr);
         uint32_t m[JMAX / 32];
-        test_tile_any<R, JMAX, false>(tile, nullptr, q, L, hL, H2, G.act ? cm : 0u, m);
+        test_tile_any<R, JMAX, false>(tile, nullptr, q, L, hL, H2, G.act ? chunk_mask(K) : 0u, m);
 #pragma unroll
         for (int ww = 0; ww < JMAX / 32; ++ww) {
             uint32_t bits = m[ww];
@@ -713,7 +824,7 @@ __device__ __forceinline__ void corrected_grad(const HState<R> &s, const R x[3],
 template <typename R, int JMAX>
 constexpr size_t hydro_warp_bytes()
 {
-    return 7 * JMAX * sizeof(Vec4<R>) + JMAX * sizeof(float);
+    return 7 * JMAX * sizeof(Vec4<R>) + JMAX * sizeof(float) + JMAX;
 }
 
 // --------------------------------------------------------------- hydro H
@@ -734,6 +845,7 @@ __global__ void __launch_bounds__(kBlock) hydro_k(PassArgs a)
 #pragma unroll
     for (int k = 0; k < 7; ++k) tile[k] = reinterpret_cast<R4 *>(base) + k * JMAX;
     float *h2j = reinterpret_cast<float *>(base + 7 * JMAX * sizeof(R4));
+    uint8_t *tslot = reinterpret_cast<uint8_t *>(h2j + JMAX);
     const Group G = load_group(a.lv, a.ggas, gi, lane);
     const int I = G.I;
     const uint32_t i = G.i;
@@ -770,32 +882,29 @@ __global__ void __launch_bounds__(kBlock) hydro_k(PassArgs a)
         const uint32_t cm = chunks_in_range(a.lv, J, cJ, wb, fr, Rc);
         if (cm == 0u) continue;
         __syncwarp();
-        stage(tile[0], reinterpret_cast<const R4 *>(a.hrec[0]), sJ, cJ, cm, lane);
-        for (uint32_t k = lane; k < cJ; k += 32u) {
-            if (!((cm >> (k / 32u)) & 1u)) continue;
+        const uint32_t K = stage_cull<R, true>(tile[0], tslot, h2j, reinterpret_cast<const R4 *>(a.hrec[0]),
+                                               reinterpret_cast<const R4 *>(a.hrec[1]), sJ, cJ, cm, wb,
+                                               cand_frame<R>(a.lv, I, fr, Ld), Hw * 1.0001f + 1e-6f * (float)Ld,
+                                               lane);
+        __syncwarp();
+        if (K == 0u) continue;
+        for (uint32_t k = lane; k < K; k += 32u) {
+            const uint32_t jg = sJ + tslot[k];
 #pragma unroll
-            for (int r = 1; r < 7; ++r) tile[r][k] = reinterpret_cast<const R4 *>(a.hrec[r])[sJ + k];
-            const float Hj = 2.0f * (float)tile[1][k].w;
-            h2j[k] = Hj * Hj;
+            for (int r = 1; r < 7; ++r) tile[r][k] = reinterpret_cast<const R4 *>(a.hrec[r])[jg];
         }
-        for (uint32_t k = cJ + lane; k < ((cJ + 31u) & ~31u); k += 32u) h2j[k] = 0.f;
         __syncwarp();
         const Target<R> q = target_in_frame(ri0, fr);
         uint32_t m[JMAX / 32];
-        test_tile_any<R, JMAX, true>(tile[0], h2j, q, L, hL, H2i, G.act ? cm : 0u, m);
-        if (J == (uint32_t)I) {
-            // the target itself is slot (i - sJ) of its own leaf
-            const uint32_t self = i - sJ;
-#pragma unroll
-            for (int ww = 0; ww < JMAX / 32; ++ww)
-                if (ww == (int)(self / 32)) m[ww] &= ~(1u << (self % 32));
-        }
+        test_tile_any<R, JMAX, true>(tile[0], h2j, q, L, hL, H2i, G.act ? chunk_mask(K) : 0u, m);
+        const bool same = J == (uint32_t)I;  // the target itself is among the candidates
 #pragma unroll
         for (int ww = 0; ww < JMAX / 32; ++ww) {
             uint32_t bits = m[ww];
             while (bits) {
                 const int j = 32 * ww + __ffs(bits) - 1;
                 bits &= bits - 1;
+                if (same && sJ + tslot[j] == i) continue;
                 HState<R> sj;
                 {
                     R4 r[7];
@@ -875,7 +984,8 @@ __global__ void __launch_bounds__(kBlock) gravity_k(PassArgs a)
     const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
     const uint32_t gi = blockIdx.x * kWarps + w;
     if (gi >= a.n_gall) return;
-    R4 *tile = reinterpret_cast<R4 *>(smem) + w * JMAX;
+    R4 *tile = reinterpret_cast<R4 *>(smem + (size_t)w * tile_warp_bytes<R, JMAX>());
+    uint8_t *tslot = reinterpret_cast<uint8_t *>(tile + JMAX);
     const Group G = load_group(a.lv, a.gall, gi, lane);
     const int I = G.I;
     const uint32_t i = G.i;
@@ -905,30 +1015,29 @@ __global__ void __launch_bounds__(kBlock) gravity_k(PassArgs a)
         const uint32_t cm = chunks_in_range(a.lv, J, cJ, wb, fr, Rc);
         if (cm == 0u) continue;
         __syncwarp();
-        stage(tile, pm, sJ, cJ, cm, lane);
+        const uint32_t K = stage_cull<R, false>(tile, tslot, nullptr, pm, nullptr, sJ, cJ, cm, wb,
+                                                cand_frame<R>(a.lv, I, fr, Ld), Rc, lane);
         __syncwarp();
+        if (K == 0u) continue;
         const Target<R> q = target_in_frame(ri, fr);
         const R gb = Real<R>::mixed ? (R)guard_band((float)rc, q.mag) : (R)0;
         uint32_t m[JMAX / 32];
-        test_tile_any<R, JMAX, false>(tile, nullptr, q, L, hL, rc2 + gb, G.act ? cm : 0u, m);
-        if (J == (uint32_t)I) {
-            const uint32_t self = i - sJ;
-#pragma unroll
-            for (int ww = 0; ww < JMAX / 32; ++ww)
-                if (ww == (int)(self / 32)) m[ww] &= ~(1u << (self % 32));
-        }
+        test_tile_any<R, JMAX, false>(tile, nullptr, q, L, hL, rc2 + gb, G.act ? chunk_mask(K) : 0u, m);
+        const bool same = J == (uint32_t)I;  // the target itself is among the candidates
 #pragma unroll
         for (int ww = 0; ww < JMAX / 32; ++ww) {
             uint32_t bits = m[ww];
             while (bits) {
                 const int j = 32 * ww + __ffs(bits) - 1;
                 bits &= bits - 1;
+                const uint32_t jg = sJ + tslot[j];
+                if (same && jg == i) continue;
                 const R4 rj = tile[j];
                 R dx, dy, dz;
                 const R r2 = q.wrap ? sep2<R, true>(rj, q, L, hL, dx, dy, dz)
                                     : sep2<R, false>(rj, q, L, hL, dx, dy, dz);
                 if (Real<R>::mixed && r2 >= rc2 - gb) {
-                    if (!exact_lt(a.s, i, sJ + (uint32_t)j, Ld, rc2x)) continue;
+                    if (!exact_lt(a.s, i, jg, Ld, rc2x)) continue;
                 }
                 const R r = Real<R>::sqrt_(r2);
                 const R S = split_S<R>(r, inv2rs);
@@ -946,7 +1055,7 @@ __global__ void __launch_bounds__(kBlock) gravity_k(PassArgs a)
                 az += fr_ * dz;
                 if (COUNT) {
                     ++nc;
-                    hs += mix64((uint64_t)a.s.id[sJ + j]);
+                    hs += mix64((uint64_t)a.s.id[jg]);
                 }
             }
         }
@@ -974,7 +1083,7 @@ void launch_warp_kernel(K kernel, uint32_t ngroups, size_t smem, const PassArgs 
 template <typename R, int JMAX>
 void density_dispatch(const PassArgs &a, bool count, cudaStream_t st)
 {
-    const size_t sm = (size_t)kWarps * JMAX * sizeof(Vec4<R>);
+    const size_t sm = (size_t)kWarps * tile_warp_bytes<R, JMAX>();
     if (count) launch_warp_kernel(density_k<R, JMAX, true>, a.n_ggas, sm, a, st);
     else launch_warp_kernel(density_k<R, JMAX, false>, a.n_ggas, sm, a, st);
 }
@@ -982,7 +1091,7 @@ void density_dispatch(const PassArgs &a, bool count, cudaStream_t st)
 template <typename R, int JMAX>
 void gravity_dispatch(const PassArgs &a, bool count, cudaStream_t st)
 {
-    const size_t sm = (size_t)kWarps * JMAX * sizeof(Vec4<R>);
+    const size_t sm = (size_t)kWarps * tile_warp_bytes<R, JMAX>();
     if (count) launch_warp_kernel(gravity_k<R, JMAX, true>, a.n_gall, sm, a, st);
     else launch_warp_kernel(gravity_k<R, JMAX, false>, a.n_gall, sm, a, st);
 }
@@ -990,7 +1099,7 @@ void gravity_dispatch(const PassArgs &a, bool count, cudaStream_t st)
 template <typename R, int JMAX>
 void moments_dispatch(const PassArgs &a, cudaStream_t st)
 {
-    launch_warp_kernel(moments_k<R, JMAX>, a.n_ggas, (size_t)kWarps * JMAX * sizeof(Vec4<R>), a, st);
+    launch_warp_kernel(moments_k<R, JMAX>, a.n_ggas, (size_t)kWarps * tile_warp_bytes<R, JMAX>(), a, st);
 }
 
 template <typename R, int JMAX>
