@@ -212,6 +212,11 @@ PassArgs pass_args(crk_sim *s)
     a.grav_hash = s->gravh.as<uint64_t>();
     a.err = s->err.as<int>();
     a.nfloor = s->nfloor.as<unsigned long long>();
+    a.nl_j = s->nl_j.as<uint32_t>();
+    a.nl_m = s->nl_m.as<uint16_t>();
+    a.nl_row = s->nl_row.as<uint32_t>();
+    a.nl_len = s->nl_len.as<uint32_t>();
+    a.nl_cnt = s->nl_cnt.as<uint32_t>();
     a.ggas = s->grp_gas.as<uint2>();
     a.gall = s->grp_all.as<uint2>();
     a.n_ggas = s->n_ggas;
@@ -365,6 +370,37 @@ int build_tree(crk_sim *s)
     return CRK_OK;
 }
 
+// Sizes the hydro neighbour lists: every gas particle's entry count and
+// every group's row count (count pass), row offsets by a scan, then the
+// list storage (one synchronisation for the total).
+static int size_hydro_lists(crk_sim *s, PassArgs &a, bool want_counts)
+{
+    cudaStream_t st = s->st;
+    if (s->n_ggas == 0) {
+        s->nl_rows = 0;
+        return CRK_OK;
+    }
+    const size_t ng = (size_t)s->n_ggas;
+    RET(s->nl_cnt.ensure((size_t)std::max<int64_t>(s->n, 1) * 4));
+    RET(s->nl_len.ensure(ng * 4));
+    RET(s->nl_row.ensure(ng * 4));
+    a.nl_cnt = s->nl_cnt.as<uint32_t>();
+    a.nl_len = s->nl_len.as<uint32_t>();
+    a.nl_row = s->nl_row.as<uint32_t>();
+    launch_hlist_count(a, s->mixed ? 1 : 0, s->cap, want_counts, st);
+    uint32_t *sc = s->scalars.as<uint32_t>();
+    scan_exclusive_u32(a.nl_len, a.nl_row, s->n_ggas, sc + 5, s->scan_tmp.as<uint32_t>(), st);
+    CK(cudaMemcpyAsync(s->host_scalars + 5, sc + 5, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    s->nl_rows = s->host_scalars[5];
+    const size_t entries = (size_t)std::max<int64_t>(s->nl_rows, 1) * 32u;
+    RET(s->nl_j.ensure(entries * 4));
+    RET(s->nl_m.ensure(entries * 2));
+    a.nl_j = s->nl_j.as<uint32_t>();
+    a.nl_m = s->nl_m.as<uint16_t>();
+    return CRK_OK;
+}
+
 // One step.  kdk = false: a force evaluation at the current state (dt = 0).
 int run_step(crk_sim *s, const double *dt_per_box, bool want_counts)
 {
@@ -395,6 +431,7 @@ int run_step(crk_sim *s, const double *dt_per_box, bool want_counts)
     const int mixed = s->mixed ? 1 : 0;
     mark(s, PH_D, 0);
     launch_records(a, mixed, st);
+    RET(size_hydro_lists(s, a, want_counts));
     launch_density(a, mixed, s->cap, want_counts, st);
     mark(s, PH_D, 1);
     mark(s, PH_M, 0);
@@ -780,7 +817,8 @@ extern "C" int crk_destroy(crk_sim *s)
                     &s->nd_slot, &s->hrow, &s->grow, &s->hcnt, &s->gcnt, &s->hcol, &s->gcol,
                     &s->pm, &s->uhat, &s->acc_h, &s->acc_g, &s->nbrc, &s->nbrh, &s->gravc,
                     &s->gravh, &s->err, &s->nfloor, &s->partial, &s->sums, &s->staging,
-                    &s->in_stage, &s->grp_cnt, &s->grp_off, &s->grp_gas, &s->grp_all, &s->hfr, &s->gfr};
+                    &s->in_stage, &s->grp_cnt, &s->grp_off, &s->grp_gas, &s->grp_all, &s->hfr, &s->gfr,
+                    &s->nl_j, &s->nl_m, &s->nl_row, &s->nl_len, &s->nl_cnt};
     for (DBuf *b : bufs) b->release();
     for (int k = 0; k < 3; ++k) {
         s->lv_u32[k].release();

@@ -92,6 +92,13 @@ struct PassArgs {
     uint64_t *nbr_hash;
     int32_t *grav_count;
     uint64_t *grav_hash;
+    // hydro neighbour lists (written by the density pass): entry k of lane l
+    // of gas group g at [(nl_row[g] + k) * 32 + l]
+    uint32_t *nl_j;          // sorted index of the neighbour
+    uint16_t *nl_m;          // bit 15: r < H_i; bits 0-14: leaf-pair offset in the hydro row
+    uint32_t *nl_row;        // first row of every gas group
+    uint32_t *nl_len;        // rows of every gas group (its longest list)
+    uint32_t *nl_cnt;        // entries of every particle
     const uint2 *ggas;       // warp work items (leaf, first offset) of gas leaves
     const uint2 *gall;       // warp work items of all leaves
     uint32_t n_ggas, n_gall;
@@ -134,6 +141,7 @@ void launch_pair_fill(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, in
 
 // ---- passes (passes.cu) ----
 void launch_records(const PassArgs &a, int mixed, cudaStream_t st);
+void launch_hlist_count(const PassArgs &a, int mixed, int cap, bool count, cudaStream_t st);
 void launch_density(const PassArgs &a, int mixed, int cap, bool count, cudaStream_t st);
 void launch_moments(const PassArgs &a, int mixed, int cap, cudaStream_t st);
 void launch_hydro(const PassArgs &a, int mixed, int cap, cudaStream_t st);

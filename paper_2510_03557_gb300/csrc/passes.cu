@@ -73,6 +73,8 @@ template <> struct Real<float> {
     }
     __device__ static float div(float a, float b) { return __fdividef(a, b); }
     __device__ static float r2(float dx, float dy, float dz) { return fmaf(dz, dz, fmaf(dy, dy, dx * dx)); }
+    __device__ static float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+    __device__ static float add_rn(float a, float b) { return __fadd_rn(a, b); }
 };
 template <> struct Real<double> {
     static constexpr bool mixed = false;
@@ -86,6 +88,8 @@ template <> struct Real<double> {
     {
         return __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
     }
+    __device__ static double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+    __device__ static double add_rn(double a, double b) { return __dadd_rn(a, b); }
 };
 
 template <typename R>
@@ -273,6 +277,33 @@ __device__ __forceinline__ void test_tile_any(const Vec4<R> *tile, const float *
 {
     if (q.wrap) test_tile<R, JMAX, true, PERJ>(tile, thrj, q, L, hL, thr, cm, m);
     else test_tile<R, JMAX, false, PERJ>(tile, thrj, q, L, hL, thr, cm, m);
+}
+
+// The hydro union test over a staged tile in one sweep: bit j of mu[j/32]
+// when r^2 < max(thr, thrj[j]) (r < H_i or r < H_j), bit j of mg[j/32] when
+// r^2 < thr (the gather set r < H_i).
+template <typename R, int JMAX, bool WRAP>
+__device__ __forceinline__ void test_tile_union(const Vec4<R> *tile, const float *thrj, const Target<R> &q, R L,
+                                                R hL, R thr, uint32_t cm, uint32_t (&mu)[JMAX / 32],
+                                                uint32_t (&mg)[JMAX / 32])
+{
+#pragma unroll
+    for (int w = 0; w < JMAX / 32; ++w) {
+        uint32_t bu = 0, bg = 0;
+        mu[w] = 0;
+        mg[w] = 0;
+        if (!((cm >> w) & 1u)) continue;
+#pragma unroll
+        for (int b = 0; b < 32; ++b) {
+            const int j = 32 * w + b;
+            R dx, dy, dz;
+            const R r2 = sep2<R, WRAP>(tile[j], q, L, hL, dx, dy, dz);
+            bu |= (r2 < fmax(thr, (R)thrj[j]) ? 1u : 0u) << b;
+            bg |= (r2 < thr ? 1u : 0u) << b;
+        }
+        mu[w] = bu;
+        mg[w] = bg;
+    }
 }
 
 template <typename R>
@@ -480,19 +511,298 @@ constexpr size_t tile_warp_bytes()
     return JMAX * (sizeof(Vec4<R>) + 1);
 }
 
-// ------------------------------------------------------------- density D
-// rho_i = sum_{j in N_i + {i}} m_j W(r, h_i); V = m/rho; P = (gamma-1) rho u^;
-// c = sqrt(gamma (gamma-1) u^).  Optional: size and hash of N_i.
+// ------------------------------------------------- hydro neighbour lists
+// The density pass tests every candidate pair of the hydro passes once and
+// writes, for every gas particle, the list of its hydro neighbours: the
+// union set r < H_i or r < H_j, the particle itself included.  Entry k of
+// lane l of gas group g sits at row nl_row[g] + k, column l: the lanes of a
+// group read one 128-byte row per step.  The fill stages rows in shared
+// memory and writes each row once all lanes have passed it.  An entry is the neighbour's
+// sorted index and a 16-bit tag: bit 15 set when r < H_i (the gather set of
+// the density and the moments), bits 0-14 the position of the leaf pair in
+// row I of the hydro pair list (its frame).  The moments and hydro passes
+// then walk their lists with every lane busy and no candidate test.
+constexpr uint16_t kGather = 0x8000u;
+constexpr uint32_t kMaxRowOffset = 0x7fffu;
+
+
+template <typename R, int JMAX>
+constexpr size_t hlist_warp_bytes()
+{
+    return JMAX * (sizeof(Vec4<R>) + sizeof(float) + 1);
+}
+
+// Rows of list entries a warp of the fill pass holds in shared memory.
+constexpr uint32_t kRingRows = 32;
+constexpr size_t kRingBytes = kRingRows * 32 * (sizeof(uint32_t) + sizeof(uint16_t));
+
+template <typename R, int JMAX>
+constexpr size_t hfill_warp_bytes()
+{
+    return hlist_warp_bytes<R, JMAX>() + kRingBytes;
+}
+
+// Entries of the fill pass on their way to global memory: a lane puts entry
+// k into ring row k mod kRingRows while k >= base, else writes it directly;
+// rows [base, upto) leave as whole 128-byte (indices) and 64-byte (tags) rows.
+struct ListRing {
+    uint32_t *rj;
+    uint16_t *rt;
+    uint32_t base;
+    size_t e0;       // the lane's entry 0 in global memory
+
+    __device__ __forceinline__ void put(const PassArgs &a, uint32_t k, uint32_t lane, uint32_t j, uint16_t tag)
+    {
+        if (k >= base) {
+            const uint32_t s = (k % kRingRows) * 32u + lane;
+            rj[s] = j;
+            rt[s] = tag;
+        } else {
+            const size_t e = e0 + (size_t)k * 32u;
+            a.nl_j[e] = j;
+            a.nl_m[e] = tag;
+        }
+    }
+    // writes rows [base, upto); a lane's own entries only (k: entries it has put)
+    __device__ __forceinline__ void flush(const PassArgs &a, uint32_t upto, uint32_t k, uint32_t lane)
+    {
+        for (uint32_t r = base; r < upto; ++r) {
+            if (r < k) {
+                const uint32_t s = (r % kRingRows) * 32u + lane;
+                const size_t e = e0 + (size_t)r * 32u;
+                a.nl_j[e] = rj[s];
+                a.nl_m[e] = rt[s];
+            }
+        }
+        base = upto;
+    }
+};
+
+// Target-side thresholds of the hydro neighbour test: r^2 < H_i^2 (plus the
+// guard band when the gather set is counted exactly).
+template <typename R>
+struct HTarget {
+    R H, H2, invH, cW;
+    double H2x;
+};
+
+template <typename R>
+__device__ __forceinline__ HTarget<R> hydro_target(const State &s, uint32_t i)
+{
+    HTarget<R> t;
+    const double H64 = 2.0 * s.h[i];
+    t.H2x = __dmul_rn(H64, H64);
+    t.H = (R)H64;
+    // rounded on its own: the count and fill passes must draw the same sets
+    t.H2 = Real<R>::mixed ? Real<R>::mul_rn(t.H, t.H) : (R)t.H2x;
+    t.invH = Real<R>::rcp(t.H);
+    t.cW = (R)kWn * t.invH * t.invH * t.invH;
+    return t;
+}
+
+// Stages leaf J (row entry p) for the hydro neighbour test of the warp and
+// returns the number of staged candidates (0: none in range).
+template <typename R, int JMAX>
+__device__ __forceinline__ uint32_t hydro_stage(const PassArgs &a, uint32_t p, int I, const WarpBox &wb, float Hw,
+                                                double Ld, Vec4<R> *tile, float *h2j, uint8_t *tslot,
+                                                uint32_t lane, uint32_t &sJ, float4 &fr)
+{
+    const uint32_t J = a.hcol[p];
+    fr = a.hfr[p];
+    const float Rc = fmaxf(Hw, a.lv.hmax[J]) * 1.0001f + 1e-6f * (float)Ld;
+    if (out_of_range(wb, fr, a.lv.ex[J], a.lv.ey[J], a.lv.ez[J], Rc)) return 0u;
+    sJ = a.lv.start[J];
+    const uint32_t cJ = a.lv.count[J];
+    const uint32_t cm = chunks_in_range(a.lv, J, cJ, wb, fr, Rc);
+    if (cm == 0u) return 0u;
+    __syncwarp();
+    const uint32_t K = stage_cull<R, true>(tile, tslot, h2j, reinterpret_cast<const Vec4<R> *>(a.pm),
+                                           reinterpret_cast<const Vec4<R> *>(a.hrec[1]), sJ, cJ, cm, wb,
+                                           cand_frame<R>(a.lv, I, fr, Ld), Hw * 1.0001f + 1e-6f * (float)Ld,
+                                           lane);
+    __syncwarp();
+    return K;
+}
+
+// Size of every gas particle's hydro neighbour list, and the largest of
+// every group (its number of rows).
 template <typename R, int JMAX, bool COUNT>
-__global__ void __launch_bounds__(kBlock) density_k(PassArgs a)
+__global__ void __launch_bounds__(kBlock) hlist_count_k(PassArgs a)
 {
     using R4 = Vec4<R>;
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
     const uint32_t gi = blockIdx.x * kWarps + w;
     if (gi >= a.n_ggas) return;
-    R4 *tile = reinterpret_cast<R4 *>(smem + (size_t)w * tile_warp_bytes<R, JMAX>());
-    uint8_t *tslot = reinterpret_cast<uint8_t *>(tile + JMAX);
+    unsigned char *base = smem + (size_t)w * hlist_warp_bytes<R, JMAX>();
+    R4 *tile = reinterpret_cast<R4 *>(base);
+    float *h2j = reinterpret_cast<float *>(tile + JMAX);
+    uint8_t *tslot = reinterpret_cast<uint8_t *>(h2j + JMAX);
+    const Group G = load_group(a.lv, a.ggas, gi, lane);
+    const int I = G.I;
+    const uint32_t i = G.i;
+    const double Ld = a.boxes[a.lv.slot[I]].L;
+    const R L = (R)Ld, hL = (R)(0.5 * Ld);
+    const R4 ri = reinterpret_cast<const R4 *>(a.pm)[i];
+    const HTarget<R> ht = hydro_target<R>(a.s, i);
+    float px, py, pz;
+    rel_pos(ri, a.lv, I, px, py, pz);
+    const WarpBox wb = warp_box(px, py, pz, G.act);
+    const float Hw = warp_max(G.act ? (float)ht.H : 0.f);
+    uint32_t cnt = 0;
+    for (uint32_t p = a.hrow[I]; p < a.hrow[I + 1]; ++p) {
+        uint32_t sJ;
+        float4 fr;
+        const uint32_t K = hydro_stage<R, JMAX>(a, p, I, wb, Hw, Ld, tile, h2j, tslot, lane, sJ, fr);
+        if (K == 0u) continue;
+        const Target<R> q = target_in_frame(ri, fr);
+        const R gb = (COUNT && Real<R>::mixed) ? (R)guard_band((float)ht.H, q.mag) : (R)0;
+        uint32_t m[JMAX / 32];
+        test_tile_any<R, JMAX, true>(tile, h2j, q, L, hL, Real<R>::add_rn(ht.H2, gb), G.act ? chunk_mask(K) : 0u, m);
+#pragma unroll
+        for (int ww = 0; ww < JMAX / 32; ++ww) cnt += (uint32_t)__popc(m[ww]);
+    }
+    const uint32_t len = __reduce_max_sync(0xffffffffu, cnt);
+    if (lane == 0) a.nl_len[gi] = len;
+    if (G.act) a.nl_cnt[i] = cnt;
+}
+
+// Writes every gas particle's hydro neighbour list (the same sets the count
+// pass counted, from the same staging and test).
+template <typename R, int JMAX, bool COUNT>
+__global__ void __launch_bounds__(kBlock) hlist_fill_k(PassArgs a)
+{
+    using R4 = Vec4<R>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    const uint32_t gi = blockIdx.x * kWarps + w;
+    if (gi >= a.n_ggas) return;
+    unsigned char *base = smem + (size_t)w * hfill_warp_bytes<R, JMAX>();
+    R4 *tile = reinterpret_cast<R4 *>(base);
+    float *h2j = reinterpret_cast<float *>(tile + JMAX);
+    uint8_t *tslot = reinterpret_cast<uint8_t *>(h2j + JMAX);
+    ListRing ring;
+    ring.rj = reinterpret_cast<uint32_t *>(base + hlist_warp_bytes<R, JMAX>());
+    ring.rt = reinterpret_cast<uint16_t *>(ring.rj + kRingRows * 32);
+    ring.base = 0;
+    const Group G = load_group(a.lv, a.ggas, gi, lane);
+    const int I = G.I;
+    const uint32_t i = G.i;
+    const double Ld = a.boxes[a.lv.slot[I]].L;
+    const R L = (R)Ld, hL = (R)(0.5 * Ld);
+    const R4 ri = reinterpret_cast<const R4 *>(a.pm)[i];
+    const HTarget<R> ht = hydro_target<R>(a.s, i);
+    float px, py, pz;
+    rel_pos(ri, a.lv, I, px, py, pz);
+    const WarpBox wb = warp_box(px, py, pz, G.act);
+    const float Hw = warp_max(G.act ? (float)ht.H : 0.f);
+    ring.e0 = (size_t)a.nl_row[gi] * 32u + lane;
+    const uint32_t prow = a.hrow[I];
+    const uint32_t room = G.act ? a.nl_cnt[i] : 0u;  // entries the count pass found
+    uint32_t k = 0;
+    for (uint32_t p = prow; p < a.hrow[I + 1]; ++p) {
+        uint32_t sJ;
+        float4 fr;
+        const uint32_t K = hydro_stage<R, JMAX>(a, p, I, wb, Hw, Ld, tile, h2j, tslot, lane, sJ, fr);
+        if (K == 0u) continue;
+        const Target<R> q = target_in_frame(ri, fr);
+        const R gb = (COUNT && Real<R>::mixed) ? (R)guard_band((float)ht.H, q.mag) : (R)0;
+        const R thr = Real<R>::add_rn(ht.H2, gb);
+        uint32_t mu[JMAX / 32], mg[JMAX / 32];
+        const uint32_t cm = G.act ? chunk_mask(K) : 0u;
+        if (q.wrap) test_tile_union<R, JMAX, true>(tile, h2j, q, L, hL, thr, cm, mu, mg);
+        else test_tile_union<R, JMAX, false>(tile, h2j, q, L, hL, thr, cm, mu, mg);
+        const uint32_t off = p - prow;
+        if (off > kMaxRowOffset && lane == 0) set_error(a.err, CRK_EOVERFLOW, a.s.id[i]);
+        const uint16_t otag = (uint16_t)(off & kMaxRowOffset);
+        uint32_t pop = 0;
+#pragma unroll
+        for (int ww = 0; ww < JMAX / 32; ++ww) pop += (uint32_t)__popc(mu[ww]);
+        // room in the ring for the fastest lane: flush its oldest rows early
+        const uint32_t need = __reduce_max_sync(0xffffffffu, k + pop);
+        if (need > ring.base + kRingRows) ring.flush(a, need - kRingRows, k < room ? k : room, lane);
+#pragma unroll
+        for (int ww = 0; ww < JMAX / 32; ++ww) {
+            uint32_t bits = mu[ww];
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1;
+                if (k < room)
+                    ring.put(a, k, lane, sJ + tslot[32 * ww + b],
+                             (uint16_t)(otag | (((mg[ww] >> b) & 1u) ? kGather : 0u)));
+                ++k;
+            }
+        }
+        // rows every active lane has passed
+        const uint32_t done = __reduce_min_sync(0xffffffffu, G.act ? k : 0xffffffffu);
+        if (done > ring.base) ring.flush(a, done, k < room ? k : room, lane);
+    }
+    ring.flush(a, __reduce_max_sync(0xffffffffu, k), k < room ? k : room, lane);
+    if (G.act && k != room) {
+        // the two passes drew different sets: keep the lists consistent, report
+        a.nl_cnt[i] = k < room ? k : room;
+        set_error(a.err, CRK_EOVERFLOW, a.s.id[i]);
+    }
+}
+
+// Reads a lane's list entries in order, keeping the next two (index, tag)
+// pairs in registers so that their loads overlap the work on earlier pairs.
+struct ListCursor {
+    size_t e0;
+    uint32_t cnt;
+    uint32_t j0, j1;
+    uint16_t tag0, tag1;
+
+    __device__ __forceinline__ ListCursor(const PassArgs &a, uint32_t gi, uint32_t lane, uint32_t n)
+    {
+        e0 = (size_t)a.nl_row[gi] * 32u + lane;
+        cnt = n;
+        j0 = j1 = 0u;
+        tag0 = tag1 = 0;
+        if (cnt > 0u) {
+            j0 = a.nl_j[e0];
+            tag0 = a.nl_m[e0];
+        }
+        if (cnt > 1u) {
+            j1 = a.nl_j[e0 + 32u];
+            tag1 = a.nl_m[e0 + 32u];
+        }
+    }
+    // after entry k - 1 was taken: (j1, tag1) becomes entry k - 1's successor
+    // and entry k is fetched
+    __device__ __forceinline__ void advance(const PassArgs &a, uint32_t k)
+    {
+        j0 = j1;
+        tag0 = tag1;
+        if (k < cnt) {
+            const size_t e = e0 + (size_t)k * 32u;
+            j1 = a.nl_j[e];
+            tag1 = a.nl_m[e];
+        }
+    }
+};
+
+// Separation x_j - x_i of a listed pair: the neighbour's record moved into
+// the target's frame by the leaf-pair frame (FP64: absolute positions).
+template <typename R>
+__device__ __forceinline__ R list_sep2(const Vec4<R> &rj, const Vec4<R> &ri, const float4 &fr, R L, R hL, R &dx,
+                                       R &dy, R &dz)
+{
+    const Target<R> q = target_in_frame(ri, fr);
+    return q.wrap ? sep2<R, true>(rj, q, L, hL, dx, dy, dz) : sep2<R, false>(rj, q, L, hL, dx, dy, dz);
+}
+
+// ------------------------------------------------------------- density D
+// rho_i = sum_{j in N_i + {i}} m_j W(r, h_i); V = m/rho; P = (gamma-1) rho u^;
+// c = sqrt(gamma (gamma-1) u^).  Optional: size and hash of N_i, the FP32
+// decision re-taken in FP64 inside the guard band.
+template <typename R, int JMAX, bool COUNT>
+__global__ void __launch_bounds__(kBlock) density_k(PassArgs a)
+{
+    using R4 = Vec4<R>;
+    const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    const uint32_t gi = blockIdx.x * kWarps + w;
+    if (gi >= a.n_ggas) return;
     const Group G = load_group(a.lv, a.ggas, gi, lane);
     const int I = G.I;
     const uint32_t i = G.i;
@@ -501,61 +811,53 @@ __global__ void __launch_bounds__(kBlock) density_k(PassArgs a)
     const double Ld = bx.L;
     const R L = (R)Ld, hL = (R)(0.5 * Ld);
     const R4 ri = pm[i];
-    const double H64 = 2.0 * a.s.h[i];
-    const double H2x = __dmul_rn(H64, H64);
-    const R H = (R)H64;
-    const R H2 = Real<R>::mixed ? H * H : (R)H2x;
-    const R invH = Real<R>::rcp(H);
-    const R cW = (R)kWn * invH * invH * invH;
-    float px, py, pz;
-    rel_pos(ri, a.lv, I, px, py, pz);
-    const WarpBox wb = warp_box(px, py, pz, G.act);
-    const float Rc = warp_max(G.act ? (float)H : 0.f) * 1.0001f + 1e-6f * (float)Ld;
+    const HTarget<R> ht = hydro_target<R>(a.s, i);
+    const float4 *__restrict__ frow = a.hfr + a.hrow[I];
+    ListCursor cur(a, gi, lane, G.act ? a.nl_cnt[i] : 0u);
     R rho = 0;
     int nc = 0;
     uint64_t hs = 0;
-    for (uint32_t p = a.hrow[I]; p < a.hrow[I + 1]; ++p) {
-        const uint32_t J = a.hcol[p];
-        const float4 fr = a.hfr[p];
-        if (out_of_range(wb, fr, a.lv.ex[J], a.lv.ey[J], a.lv.ez[J], Rc)) continue;
-        const uint32_t sJ = a.lv.start[J], cJ = a.lv.count[J];
-        const uint32_t cm = chunks_in_range(a.lv, J, cJ, wb, fr, Rc);
-        if (cm == 0u) continue;
-        __syncwarp();
-        const uint32_t K = stage_cull<R, false>(tile, tslot, nullptr, pm, nullptr, sJ, cJ, cm, wb,
-                                                cand_frame<R>(a.lv, I, fr, Ld), Rc, lane);
-        __syncwarp();
-        if (K == 0u) continue;
-        const Target<R> q = target_in_frame(ri, fr);
-        const R gb = Real<R>::mixed ? (R)guard_band((float)H, q.mag) : (R)0;
-        uint32_t m[JMAX / 32];
-        test_tile_any<R, JMAX, false>(tile, nullptr, q, L, hL, COUNT ? H2 + gb : H2,
-                                      G.act ? chunk_mask(K) : 0u, m);
-#pragma unroll
-        for (int ww = 0; ww < JMAX / 32; ++ww) {
-            uint32_t bits = m[ww];
-            while (bits) {
-                const int j = 32 * ww + __ffs(bits) - 1;
-                bits &= bits - 1;
-                const R4 rj = tile[j];
-                R dx, dy, dz;
-                const R r2 = q.wrap ? sep2<R, true>(rj, q, L, hL, dx, dy, dz)
-                                    : sep2<R, false>(rj, q, L, hL, dx, dy, dz);
-                const R r = Real<R>::sqrt_(r2);
-                const R qq = r * invH;
-                R om = (R)1 - qq;
-                om = om > (R)0 ? om : (R)0;
-                const R om2 = om * om;
-                rho += rj.w * cW * om2 * om2 * om2 * ((R)1 + qq * ((R)6 + qq * (R)(35.0 / 3.0)));
-                if (COUNT) {
-                    const uint32_t jg = sJ + tslot[j];
-                    bool in = r2 < H2;
-                    if (Real<R>::mixed && r2 >= H2 - gb) in = exact_lt(a.s, i, jg, Ld, H2x);
-                    if (in && jg != i) {
-                        ++nc;
-                        hs += mix64((uint64_t)a.s.id[jg]);
-                    }
-                }
+    R4 rn;
+    float4 fn;
+    uint16_t tn = 0;
+    uint32_t jn = 0;
+    if (cur.cnt > 0u) {
+        tn = cur.tag0;
+        jn = cur.j0;
+        rn = pm[jn];
+        fn = frow[tn & kMaxRowOffset];
+    }
+    for (uint32_t k = 0; k < cur.cnt; ++k) {
+        const R4 rj = rn;
+        const float4 fr = fn;
+        const uint16_t tag = tn;
+        const uint32_t j = jn;
+        if (k + 1u < cur.cnt) {
+            tn = cur.tag1;
+            jn = cur.j1;
+            rn = pm[jn];
+            fn = frow[tn & kMaxRowOffset];
+        }
+        cur.advance(a, k + 2u);
+        if (!(tag & kGather)) continue;
+        R dx, dy, dz;
+        const R r2 = list_sep2(rj, ri, fr, L, hL, dx, dy, dz);
+        const R r = Real<R>::sqrt_(r2);
+        const R qq = r * ht.invH;
+        R om = (R)1 - qq;
+        om = om > (R)0 ? om : (R)0;
+        const R om2 = om * om;
+        rho += rj.w * ht.cW * om2 * om2 * om2 * ((R)1 + qq * ((R)6 + qq * (R)(35.0 / 3.0)));
+        if (COUNT) {
+            bool in = r2 < ht.H2;
+            if (Real<R>::mixed) {
+                const Target<R> q = target_in_frame(ri, fr);
+                const R gb = (R)guard_band((float)ht.H, q.mag);
+                if (r2 >= ht.H2 - gb) in = exact_lt(a.s, i, j, Ld, ht.H2x);
+            }
+            if (in && j != i) {
+                ++nc;
+                hs += mix64((uint64_t)a.s.id[j]);
             }
         }
     }
@@ -691,64 +993,51 @@ template <typename R, int JMAX>
 __global__ void __launch_bounds__(kBlock) moments_k(PassArgs a)
 {
     using R4 = Vec4<R>;
-    extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
     const uint32_t gi = blockIdx.x * kWarps + w;
     if (gi >= a.n_ggas) return;
-    R4 *tile = reinterpret_cast<R4 *>(smem + (size_t)w * tile_warp_bytes<R, JMAX>());
-    uint8_t *tslot = reinterpret_cast<uint8_t *>(tile + JMAX);
     const Group G = load_group(a.lv, a.ggas, gi, lane);
     const int I = G.I;
     const uint32_t i = G.i;
     const R4 *__restrict__ rec0 = reinterpret_cast<const R4 *>(a.hrec[0]);
-    const BoxDev &bx = a.boxes[a.lv.slot[I]];
-    const double Ld = bx.L;
+    const double Ld = a.boxes[a.lv.slot[I]].L;
     const R L = (R)Ld, hL = (R)(0.5 * Ld);
     const R4 ri = rec0[i];
-    const double H64 = 2.0 * a.s.h[i];
-    const R H = (R)H64;
-    const R H2 = Real<R>::mixed ? H * H : (R)__dmul_rn(H64, H64);
+    const R H = (R)(2.0 * a.s.h[i]);
     const R invH = Real<R>::rcp(H);
     const R invH2 = invH * invH;
     const R cW = (R)kWn * invH2 * invH;
     const R cG = (R)kGn * invH2 * invH2 * invH;
-    float px, py, pz;
-    rel_pos(ri, a.lv, I, px, py, pz);
-    const WarpBox wb = warp_box(px, py, pz, G.act);
-    const float Rc = warp_max(G.act ? (float)H : 0.f) * 1.0001f + 1e-6f * (float)Ld;
+    const float4 *__restrict__ frow = a.hfr + a.hrow[I];
+    ListCursor cur(a, gi, lane, G.act ? a.nl_cnt[i] : 0u);
     MomentAcc<R> acc;
     acc.zero();
-    for (uint32_t p = a.hrow[I]; p < a.hrow[I + 1]; ++p) {
-        const uint32_t J = a.hcol[p];
-        const float4 fr = a.hfr[p];
-        if (out_of_range(wb, fr, a.lv.ex[J], a.lv.ey[J], a.lv.ez[J], Rc)) continue;
-        const uint32_t sJ = a.lv.start[J], cJ = a.lv.count[J];
-        const uint32_t cm = chunks_in_range(a.lv, J, cJ, wb, fr, Rc);
-        if (cm == 0u) continue;
-        __syncwarp();
-        const uint32_t K = stage_cull<R, false>(tile, tslot, nullptr, rec0, nullptr, sJ, cJ, cm, wb,
-                                                cand_frame<R>(a.lv, I, fr, Ld), Rc, lane);
-        __syncwarp();
-        if (K == 0u) continue;
-        const Target<R> q = target_in_frame(ri, fr);
-        uint32_t m[JMAX / 32];
-        test_tile_any<R, JMAX, false>(tile, nullptr, q, L, hL, H2, G.act ? chunk_mask(K) : 0u, m);
-#pragma unroll
-        for (int ww = 0; ww < JMAX / 32; ++ww) {
-            uint32_t bits = m[ww];
-            while (bits) {
-                const int j = 32 * ww + __ffs(bits) - 1;
-                bits &= bits - 1;
-                const R4 rj = tile[j];
-                R dx, dy, dz;
-                const R r2 = q.wrap ? sep2<R, true>(rj, q, L, hL, dx, dy, dz)
-                                    : sep2<R, false>(rj, q, L, hL, dx, dy, dz);
-                const R x[3] = {-dx, -dy, -dz};
-                R Wv, g;
-                kernel_wg(Real<R>::sqrt_(r2), invH, cW, cG, Wv, g);
-                acc.add(x, rj.w * Wv, rj.w * g);
-            }
+    // software pipeline: list entries two ahead, the neighbour's record one ahead
+    R4 rn;
+    float4 fn;
+    uint16_t tn = 0;
+    if (cur.cnt > 0u) {
+        tn = cur.tag0;
+        rn = rec0[cur.j0];
+        fn = frow[tn & kMaxRowOffset];
+    }
+    for (uint32_t k = 0; k < cur.cnt; ++k) {
+        const R4 rj = rn;
+        const float4 fr = fn;
+        const uint16_t tag = tn;
+        if (k + 1u < cur.cnt) {
+            tn = cur.tag1;
+            rn = rec0[cur.j1];
+            fn = frow[tn & kMaxRowOffset];
         }
+        cur.advance(a, k + 2u);
+        if (!(tag & kGather)) continue;
+        R dx, dy, dz;
+        const R r2 = list_sep2(rj, ri, fr, L, hL, dx, dy, dz);
+        const R x[3] = {-dx, -dy, -dz};
+        R Wv, g;
+        kernel_wg(Real<R>::sqrt_(r2), invH, cW, cG, Wv, g);
+        acc.add(x, rj.w * Wv, rj.w * g);
     }
     if (!G.act) return;
     double m[40];
@@ -821,31 +1110,20 @@ __device__ __forceinline__ void corrected_grad(const HState<R> &s, const R x[3],
     }
 }
 
-template <typename R, int JMAX>
-constexpr size_t hydro_warp_bytes()
-{
-    return 7 * JMAX * sizeof(Vec4<R>) + JMAX * sizeof(float) + JMAX;
-}
-
 // --------------------------------------------------------------- hydro H
 // Over the hydro pair set (r < H_i or r < H_j, j != i):
 //   F_ij = -1/2 V_i V_j (P_i + P_j + Q_i + Q_j) (dW^R_ij - dW^R_ji)
 //   Q = rho (-alpha c mu + beta mu^2), mu = min(0, h v_ij.x_ij / (r^2 + eps^2 h^2))
 //   m_i a_i = sum F_ij,  m_i du_i = -1/2 sum F_ij . v_ij
+// The pairs are the target's list entries; j's seven records are read
+// through L1/L2 (a group's neighbours are a few leaves).
 template <typename R, int JMAX>
 __global__ void __launch_bounds__(kBlock) hydro_k(PassArgs a)
 {
     using R4 = Vec4<R>;
-    extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
     const uint32_t gi = blockIdx.x * kWarps + w;
     if (gi >= a.n_ggas) return;
-    unsigned char *base = smem + (size_t)w * hydro_warp_bytes<R, JMAX>();
-    R4 *tile[7];
-#pragma unroll
-    for (int k = 0; k < 7; ++k) tile[k] = reinterpret_cast<R4 *>(base) + k * JMAX;
-    float *h2j = reinterpret_cast<float *>(base + 7 * JMAX * sizeof(R4));
-    uint8_t *tslot = reinterpret_cast<uint8_t *>(h2j + JMAX);
     const Group G = load_group(a.lv, a.ggas, gi, lane);
     const int I = G.I;
     const uint32_t i = G.i;
@@ -863,89 +1141,67 @@ __global__ void __launch_bounds__(kBlock) hydro_k(PassArgs a)
         ri0 = r[0];
     }
     const R Hi = (R)2 * si.h;
-    const R H2i = Hi * Hi;
     const R invHi = Real<R>::rcp(Hi);
     const R cWi = (R)kWn * invHi * invHi * invHi;
     const R cGi = (R)kGn * invHi * invHi * invHi * invHi * invHi;
     const R hi2e = eps2 * si.h * si.h;
-    float px, py, pz;
-    rel_pos(ri0, a.lv, I, px, py, pz);
-    const WarpBox wb = warp_box(px, py, pz, G.act);
-    const float Hw = warp_max(G.act ? (float)Hi : 0.f);
+    const float4 *__restrict__ frow = a.hfr + a.hrow[I];
+    ListCursor cur(a, gi, lane, G.act ? a.nl_cnt[i] : 0u);
     R ax = 0, ay = 0, az = 0, du = 0;
-    for (uint32_t p = a.hrow[I]; p < a.hrow[I + 1]; ++p) {
-        const uint32_t J = a.hcol[p];
-        const float4 fr = a.hfr[p];
-        const float Rc = fmaxf(Hw, a.lv.hmax[J]) * 1.0001f + 1e-6f * (float)Ld;
-        if (out_of_range(wb, fr, a.lv.ex[J], a.lv.ey[J], a.lv.ez[J], Rc)) continue;
-        const uint32_t sJ = a.lv.start[J], cJ = a.lv.count[J];
-        const uint32_t cm = chunks_in_range(a.lv, J, cJ, wb, fr, Rc);
-        if (cm == 0u) continue;
-        __syncwarp();
-        const uint32_t K = stage_cull<R, true>(tile[0], tslot, h2j, reinterpret_cast<const R4 *>(a.hrec[0]),
-                                               reinterpret_cast<const R4 *>(a.hrec[1]), sJ, cJ, cm, wb,
-                                               cand_frame<R>(a.lv, I, fr, Ld), Hw * 1.0001f + 1e-6f * (float)Ld,
-                                               lane);
-        __syncwarp();
-        if (K == 0u) continue;
-        for (uint32_t k = lane; k < K; k += 32u) {
-            const uint32_t jg = sJ + tslot[k];
+    // software pipeline: list entries two ahead, the neighbour's records one ahead
+    R4 rn[7];
+    float4 fn;
+    uint32_t jn = 0;
+    if (cur.cnt > 0u) {
+        jn = cur.j0;
+        fn = frow[cur.tag0 & kMaxRowOffset];
 #pragma unroll
-            for (int r = 1; r < 7; ++r) tile[r][k] = reinterpret_cast<const R4 *>(a.hrec[r])[jg];
+        for (int q = 0; q < 7; ++q) rn[q] = reinterpret_cast<const R4 *>(a.hrec[q])[jn];
+    }
+    for (uint32_t k = 0; k < cur.cnt; ++k) {
+        const uint32_t j = jn;
+        const float4 fr = fn;
+        HState<R> sj;
+        unpack_hstate(rn, sj);
+        const R4 rj0 = rn[0];
+        if (k + 1u < cur.cnt) {
+            jn = cur.j1;
+            fn = frow[cur.tag1 & kMaxRowOffset];
+#pragma unroll
+            for (int q = 0; q < 7; ++q) rn[q] = reinterpret_cast<const R4 *>(a.hrec[q])[jn];
         }
-        __syncwarp();
-        const Target<R> q = target_in_frame(ri0, fr);
-        uint32_t m[JMAX / 32];
-        test_tile_any<R, JMAX, true>(tile[0], h2j, q, L, hL, H2i, G.act ? chunk_mask(K) : 0u, m);
-        const bool same = J == (uint32_t)I;  // the target itself is among the candidates
-#pragma unroll
-        for (int ww = 0; ww < JMAX / 32; ++ww) {
-            uint32_t bits = m[ww];
-            while (bits) {
-                const int j = 32 * ww + __ffs(bits) - 1;
-                bits &= bits - 1;
-                if (same && sJ + tslot[j] == i) continue;
-                HState<R> sj;
-                {
-                    R4 r[7];
-#pragma unroll
-                    for (int k = 0; k < 7; ++k) r[k] = tile[k][j];
-                    unpack_hstate(r, sj);
-                }
-                R dx, dy, dz;
-                const R4 rj0 = tile[0][j];
-                const R r2 = q.wrap ? sep2<R, true>(rj0, q, L, hL, dx, dy, dz)
-                                    : sep2<R, false>(rj0, q, L, hL, dx, dy, dz);
-                const R x[3] = {-dx, -dy, -dz};  // x_ij = x_i - x_j
-                const R xm[3] = {dx, dy, dz};    // x_ji
-                const R r = Real<R>::sqrt_(r2);
-                R Wi, gi_, Wj, gj;
-                kernel_wg(r, invHi, cWi, cGi, Wi, gi_);
-                const R invHj = Real<R>::rcp((R)2 * sj.h);
-                const R invHj2 = invHj * invHj;
-                kernel_wg(r, invHj, (R)kWn * invHj2 * invHj, (R)kGn * invHj2 * invHj2 * invHj, Wj, gj);
-                R dWi[3], dWj[3];
-                corrected_grad(si, x, Wi, gi_, dWi);
-                corrected_grad(sj, xm, Wj, gj, dWj);
-                const R vxij = si.vx - sj.vx, vyij = si.vy - sj.vy, vzij = si.vz - sj.vz;
-                const R vdx = vxij * x[0] + vyij * x[1] + vzij * x[2];
-                R Q = 0;
-                if (vdx < (R)0) {
-                    const R mui = Real<R>::div(si.h * vdx, r2 + hi2e);
-                    const R muj = Real<R>::div(sj.h * vdx, r2 + eps2 * sj.h * sj.h);
-                    Q = si.rho * (-alpha * si.c * mui + beta * mui * mui) +
-                        sj.rho * (-alpha * sj.c * muj + beta * muj * muj);
-                }
-                const R pre = (R)(-0.5) * si.V * sj.V * (si.P + sj.P + Q);
-                const R Fx = pre * (dWi[0] - dWj[0]);
-                const R Fy = pre * (dWi[1] - dWj[1]);
-                const R Fz = pre * (dWi[2] - dWj[2]);
-                ax += Fx;
-                ay += Fy;
-                az += Fz;
-                du += Fx * vxij + Fy * vyij + Fz * vzij;
-            }
+        cur.advance(a, k + 2u);
+        if (j == i) continue;
+        R dx, dy, dz;
+        const R r2 = list_sep2(rj0, ri0, fr, L, hL, dx, dy, dz);
+        const R x[3] = {-dx, -dy, -dz};  // x_ij = x_i - x_j
+        const R xm[3] = {dx, dy, dz};    // x_ji
+        const R r = Real<R>::sqrt_(r2);
+        R Wi, gi_, Wj, gj;
+        kernel_wg(r, invHi, cWi, cGi, Wi, gi_);
+        const R invHj = Real<R>::rcp((R)2 * sj.h);
+        const R invHj2 = invHj * invHj;
+        kernel_wg(r, invHj, (R)kWn * invHj2 * invHj, (R)kGn * invHj2 * invHj2 * invHj, Wj, gj);
+        R dWi[3], dWj[3];
+        corrected_grad(si, x, Wi, gi_, dWi);
+        corrected_grad(sj, xm, Wj, gj, dWj);
+        const R vxij = si.vx - sj.vx, vyij = si.vy - sj.vy, vzij = si.vz - sj.vz;
+        const R vdx = vxij * x[0] + vyij * x[1] + vzij * x[2];
+        R Q = 0;
+        if (vdx < (R)0) {
+            const R mui = Real<R>::div(si.h * vdx, r2 + hi2e);
+            const R muj = Real<R>::div(sj.h * vdx, r2 + eps2 * sj.h * sj.h);
+            Q = si.rho * (-alpha * si.c * mui + beta * mui * mui) +
+                sj.rho * (-alpha * sj.c * muj + beta * muj * muj);
         }
+        const R pre = (R)(-0.5) * si.V * sj.V * (si.P + sj.P + Q);
+        const R Fx = pre * (dWi[0] - dWj[0]);
+        const R Fy = pre * (dWi[1] - dWj[1]);
+        const R Fz = pre * (dWi[2] - dWj[2]);
+        ax += Fx;
+        ay += Fy;
+        az += Fz;
+        du += Fx * vxij + Fy * vyij + Fz * vzij;
     }
     if (!G.act) return;
     const R mi = reinterpret_cast<const R4 *>(a.pm)[i].w;
@@ -1081,11 +1337,24 @@ void launch_warp_kernel(K kernel, uint32_t ngroups, size_t smem, const PassArgs 
 }
 
 template <typename R, int JMAX>
+void hlist_count_dispatch(const PassArgs &a, bool count, cudaStream_t st)
+{
+    const size_t sm = (size_t)kWarps * hlist_warp_bytes<R, JMAX>();
+    if (count) launch_warp_kernel(hlist_count_k<R, JMAX, true>, a.n_ggas, sm, a, st);
+    else launch_warp_kernel(hlist_count_k<R, JMAX, false>, a.n_ggas, sm, a, st);
+}
+
+template <typename R, int JMAX>
 void density_dispatch(const PassArgs &a, bool count, cudaStream_t st)
 {
-    const size_t sm = (size_t)kWarps * tile_warp_bytes<R, JMAX>();
-    if (count) launch_warp_kernel(density_k<R, JMAX, true>, a.n_ggas, sm, a, st);
-    else launch_warp_kernel(density_k<R, JMAX, false>, a.n_ggas, sm, a, st);
+    const size_t smf = (size_t)kWarps * hfill_warp_bytes<R, JMAX>();
+    if (count) {
+        launch_warp_kernel(hlist_fill_k<R, JMAX, true>, a.n_ggas, smf, a, st);
+        launch_warp_kernel(density_k<R, JMAX, true>, a.n_ggas, 0, a, st);
+    } else {
+        launch_warp_kernel(hlist_fill_k<R, JMAX, false>, a.n_ggas, smf, a, st);
+        launch_warp_kernel(density_k<R, JMAX, false>, a.n_ggas, 0, a, st);
+    }
 }
 
 template <typename R, int JMAX>
@@ -1099,13 +1368,13 @@ void gravity_dispatch(const PassArgs &a, bool count, cudaStream_t st)
 template <typename R, int JMAX>
 void moments_dispatch(const PassArgs &a, cudaStream_t st)
 {
-    launch_warp_kernel(moments_k<R, JMAX>, a.n_ggas, (size_t)kWarps * tile_warp_bytes<R, JMAX>(), a, st);
+    launch_warp_kernel(moments_k<R, JMAX>, a.n_ggas, 0, a, st);
 }
 
 template <typename R, int JMAX>
 void hydro_dispatch(const PassArgs &a, cudaStream_t st)
 {
-    launch_warp_kernel(hydro_k<R, JMAX>, a.n_ggas, (size_t)kWarps * hydro_warp_bytes<R, JMAX>(), a, st);
+    launch_warp_kernel(hydro_k<R, JMAX>, a.n_ggas, 0, a, st);
 }
 
 }  // namespace
@@ -1131,11 +1400,18 @@ void launch_records(const PassArgs &a, int mixed, cudaStream_t st)
         }                                                                    \
     } while (0)
 
+void launch_hlist_count(const PassArgs &a, int mixed, int cap, bool count, cudaStream_t st)
+{
+    if (a.n_ggas == 0) return;
+    CRK_BY_CAP(hlist_count_dispatch, a, count, st);
+    note_launches(1);
+}
+
 void launch_density(const PassArgs &a, int mixed, int cap, bool count, cudaStream_t st)
 {
     if (a.n_ggas == 0) return;
     CRK_BY_CAP(density_dispatch, a, count, st);
-    note_launches(1);
+    note_launches(2);
 }
 
 void launch_moments(const PassArgs &a, int mixed, int cap, cudaStream_t st)

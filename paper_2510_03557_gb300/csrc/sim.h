@@ -78,6 +78,8 @@ struct crk_sim {
     DBuf hrow, grow, hcnt, gcnt, hcol, gcol, hfr, gfr;
     DBuf pm, hrec[7], uhat, acc_h, acc_g;
     DBuf nbrc, nbrh, gravc, gravh;
+    DBuf nl_j, nl_m, nl_row, nl_len, nl_cnt;  // hydro neighbour lists
+    int64_t nl_rows = 0;
     DBuf err, nfloor, partial, sums;
     DBuf staging, in_stage;
     Leaves lv{};
