@@ -186,13 +186,22 @@ def knn_smoothing_lengths(gas_pos: np.ndarray, k: int = 32, factor: float = 1.2,
     return factor * d[:, k]
 
 
+def _round_down_1sig(x: float) -> float:
+    """x rounded down to one significant decimal digit."""
+    e = math.floor(math.log10(x))
+    return math.floor(x / 10.0 ** e) * 10.0 ** e
+
+
 def clustered_box(n: int = 256, seed: int = 3, nsphere: int = 512, a: float = 0.002,
                   u_sigma: float = 1.0, knn: bool = True) -> Box:
     """2 x n^3 particles; per species half uniform and half in ``nsphere``
     Plummer spheres (scale radius ``a``, truncated at 20a, centres uniform and
     shared by both species, equal split per sphere); v = 0; log-normal gas u
     (median 1, sigma 1); adaptive h from the 32nd-nearest gas neighbour;
-    one force evaluation plus 5 KDK steps at dt = 1e-4."""
+    one force evaluation plus 5 KDK steps.  The step is a Courant bound of the
+    initial state, dt = 0.25 min_gas h / c with c = sqrt(gamma (gamma-1) u),
+    rounded down to one significant digit and at most 1e-4 (2x256^3: 8e-6);
+    a fixed 1e-4 moves the densest core particles by several h per step."""
     rng = np.random.default_rng(seed)
     n3 = n ** 3
     half = n3 // 2
@@ -213,8 +222,11 @@ def clustered_box(n: int = 256, seed: int = 3, nsphere: int = 512, a: float = 0.
         h[n3:] = knn_smoothing_lengths(pos[n3:], 32, 1.2)
     else:
         h[n3:] = 2.0 / n
+    gas = species == GAS
+    c = np.sqrt((5.0 / 3.0) * (2.0 / 3.0) * u[gas])
+    dt = min(1e-4, _round_down_1sig(0.25 * float(np.min(h[gas] / c))))
     box = Box(pos=pos, vel=np.zeros_like(pos), mass=mass, u=u, h=h, species=species,
-              dt=1e-4, nsteps=5, n_lattice=n, name=f"clustered-2x{n}^3")
+              dt=dt, nsteps=5, n_lattice=n, name=f"clustered-2x{n}^3")
     _gravity_scales(n, box)
     return box
 
