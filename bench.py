@@ -317,6 +317,75 @@ def run_clustered(args):
     print(json.dumps(line))
 
 
+def run_batched(args):
+    """The batched workload: 64 independent periodic boxes of 2 n^3 particles,
+    n drawn (seed 2) from {16, 24, 32, 48, 64}, box b from the Gaussian-field
+    generator with seed 1000 + b, all in one handle (one tree and one launch
+    per pass for every box), FP32-mixed, leaf capacity chosen by the library's
+    autotuner.  Beside it the plain FP64 form one box per handle, run one box
+    after another, on the first 8 boxes."""
+    import torch
+
+    from paper_2510_03557_gb300 import crk
+    from paper_2510_03557_gb300 import workloads as wl
+
+    torch.cuda.set_device(0)
+    crk.lib()
+    boxes = wl.batched_boxes(64, seed=2)
+    cat = wl.concat_boxes(boxes)
+    N = int(cat["offsets"][-1])
+    phys = [crk.box_physics(b) for b in boxes]
+    dts = [b.dt for b in boxes]
+    stream = torch.cuda.Stream()
+    sim = crk.Sim(phys[0], leaf_cap=128, precision=crk.CRK_MIXED, stream=stream)
+    crk.crk_load_boxes(sim.handle, [b.n for b in boxes], phys, cat["pos"], cat["vel"], cat["mass"],
+                       cat["u"], cat["h"], cat["species"])
+    sim.n = N
+    best, tune_ms = crk.crk_autotune(sim.handle, (32, 64, 128))
+    crk.crk_step_boxes(sim.handle, dts, args.warmup)
+    crk.crk_set_timing(sim.handle, True)
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clocks:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        crk.crk_step_boxes(sim.handle, dts, args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    tim = crk.crk_get_timings(sim.handle)
+    calls = max(tim["calls"], 1)
+    sim.close()
+    t64 = 0.0
+    p64 = 0
+    for b in boxes[:8]:
+        s = crk.Sim(crk.box_physics(b), leaf_cap=64, precision=crk.CRK_FP64, stream=stream)
+        s.load(b)
+        s.step(b.dt, 1)
+        stream.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        s.step(b.dt, 1)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        t64 += f0.elapsed_time(f1) / 1e3
+        p64 += b.n
+        s.close()
+    line = {"metric": METRIC, "value": N / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "batched: 64 Gaussian-field boxes 2 n^3, n in {16,24,32,48,64} "
+                                   "(seed 2), one handle, FP32-mixed, KDK dt=1e-3",
+                       "particles": N, "boxes": len(boxes), "leaf_cap": best},
+            "autotune_ms": {str(k): round(v, 3) for k, v in tune_ms.items()},
+            "breakdown_ms": {k: round(tim[k] / calls, 4) for k in
+                             ("tree_ms", "pairs_ms", "density_ms", "moments_ms", "hydro_ms",
+                              "gravity_ms", "kdk_ms")},
+            "gpu_launches_per_step": int(tim["launches"]) // max(args.steps, 1),
+            "fp64_one_box_per_launch": {"value": p64 / t64, "unit": UNIT, "boxes": 8, "steps": 1},
+            "clocks": clocks.summary()}
+    print(json.dumps(line))
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -344,8 +413,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="gaussian", choices=["gaussian", "clustered"],
-                    help="clustered: the precision study (prints its own JSON line)")
+    ap.add_argument("--workload", default="gaussian", choices=["gaussian", "clustered", "batched"],
+                    help="clustered: the precision study; batched: 64 boxes in one handle "
+                         "(each prints its own JSON line)")
     ap.add_argument("--sample", type=int, default=64, help="oracle sample of the precision study")
     ap.add_argument("--n", type=int, default=128, help="lattice size per species (2 n^3 particles)")
     ap.add_argument("--leaf-cap", type=int, default=128)
@@ -362,6 +432,9 @@ def main():
         return
     if args.workload == "clustered":
         run_clustered(args)
+        return
+    if args.workload == "batched":
+        run_batched(args)
         return
 
     import torch
@@ -381,15 +454,12 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(v: float) -> float:
-        if dist is None:
-            return v
-        t = torch.tensor([v], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     from paper_2510_03557_gb300 import crk
+    from paper_2510_03557_gb300 import replicas
     from paper_2510_03557_gb300 import workloads as wl
+
+    def max_over_ranks(v: float) -> float:
+        return replicas.max_over_ranks(v, dist, "cuda")
 
     crk.lib()
     box = wl.gaussian_field_box(args.n, seed=1)
@@ -419,9 +489,9 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
-    t_max = max_over_ranks(ms)
+    # every rank steps its own box: all ranks' particles over the slowest rank's time
+    value, t_max = replicas.job_throughput(N * args.steps, ms, dist, "cuda")
     tim = crk.crk_get_timings(sim.handle)
-    value = world * N * args.steps / (t_max / 1e3)
     per_pass_ms = {"density": tim["density_ms"], "moments": tim["moments_ms"],
                    "hydro": tim["hydro_ms"], "gravity": tim["gravity_ms"]}
     calls = max(tim["calls"], 1)

@@ -185,6 +185,19 @@ int crk_get_sums(crk_sim *sim, double momentum[3], double *energy, int64_t *nflo
 /* Number of particles and boxes loaded. */
 int crk_get_size(crk_sim *sim, int64_t *n, int *nbox);
 
+/* Leaf-capacity autotuner.  The paper sizes its base leaves by hand for its
+ * hardware (Sec. IV-B1: a few hundred particles per leaf on MI250X); here the
+ * best capacity depends on the particle distribution.  Runs one force
+ * evaluation of the loaded particles at each candidate capacity caps[k]
+ * (each 32, 64 or 128), timed with CUDA events on the handle's stream after a
+ * warm-up evaluation, keeps the fastest for the handle's later calls and
+ * writes it to *best_cap (optional); ms_out (optional, ncaps entries) gets
+ * each candidate's time in milliseconds.  The particle state is unchanged;
+ * the stored accelerations are those of the chosen capacity.  Synchronises
+ * the stream.  Errors: CRK_EINVAL (bad candidate, no particles), the errors
+ * of crk_forces. */
+int crk_autotune(crk_sim *sim, const int *caps, int ncaps, int *best_cap, double *ms_out);
+
 /* Turns per-phase CUDA-event timing on (1) or off (0) and resets it. */
 int crk_set_timing(crk_sim *sim, int enable);
 int crk_get_timings(crk_sim *sim, crk_timings *out);

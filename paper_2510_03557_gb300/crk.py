@@ -35,7 +35,7 @@ CRK_GAS = 1
 # Every function of the C ABI.
 ABI = ("crk_create", "crk_load", "crk_load_boxes", "crk_forces", "crk_step", "crk_step_boxes",
        "crk_get_state", "crk_set_state", "crk_get_sums", "crk_get_size", "crk_set_timing", "crk_get_timings",
-       "crk_destroy", "crk_service_create", "crk_submit", "crk_poll", "crk_service_destroy",
+       "crk_destroy", "crk_autotune", "crk_service_create", "crk_submit", "crk_poll", "crk_service_destroy",
        "crk_neighbours_noalloc", "crk_last_error")
 CRK_NOALLOC_MAX_N = 262144
 
@@ -275,6 +275,16 @@ def crk_get_timings(sim) -> dict:
 
 def crk_destroy(sim):
     _check(lib().crk_destroy(sim))
+
+
+def crk_autotune(sim, caps=(32, 64, 128)):
+    """Times one force evaluation per leaf capacity, keeps the fastest;
+    returns (best capacity, {capacity: ms})."""
+    arr = (ctypes.c_int * len(caps))(*caps)
+    ms = (ctypes.c_double * len(caps))()
+    best = ctypes.c_int()
+    _check(lib().crk_autotune(sim, arr, ctypes.c_int(len(caps)), ctypes.byref(best), ms))
+    return int(best.value), {c: float(m) for c, m in zip(caps, ms)}
 
 
 def crk_service_create(hbm_budget_bytes: int, max_slots: int, precision=CRK_MIXED, leaf_cap=64,

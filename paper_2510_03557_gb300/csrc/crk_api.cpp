@@ -758,6 +758,52 @@ extern "C" int crk_set_timing(crk_sim *s, int enable)
     return CRK_OK;
 }
 
+extern "C" int crk_autotune(crk_sim *s, const int *caps, int ncaps, int *best_cap, double *ms_out)
+{
+    if (!s || !caps || ncaps < 1) return fail(CRK_EINVAL, "null argument or no candidate");
+    for (int k = 0; k < ncaps; ++k)
+        if (caps[k] != 32 && caps[k] != 64 && caps[k] != 128)
+            return fail(CRK_EINVAL, "leaf capacity candidates must be 32, 64 or 128 (got %d)", caps[k]);
+    CK(cudaSetDevice(s->device));
+    if (s->n == 0) return fail(CRK_EINVAL, "no particles loaded");
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fail(CRK_ECUDA, "event creation failed: %s", cudaGetErrorString(ce));
+    }
+    int best = -1;
+    double best_ms = 0.0;
+    int rc = CRK_OK;
+    for (int k = 0; k < ncaps && rc == CRK_OK; ++k) {
+        s->cap = caps[k];
+        rc = run_step(s, nullptr, false);  // warm-up: buffers grow to this layout
+        if (rc != CRK_OK) break;
+        cudaEventRecord(e0, s->st);
+        rc = run_step(s, nullptr, false);
+        cudaEventRecord(e1, s->st);
+        if (rc != CRK_OK) break;
+        float ms = 0.f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            rc = fail(CRK_ECUDA, "event timing failed");
+            break;
+        }
+        if (ms_out) ms_out[k] = ms;
+        if (best < 0 || ms < best_ms) {
+            best = k;
+            best_ms = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != CRK_OK) return rc;
+    s->cap = caps[best];
+    if (best_cap) *best_cap = caps[best];
+    // the stored accelerations are those of the chosen capacity
+    return run_step(s, nullptr, false);
+}
+
 extern "C" int crk_set_state(crk_sim *s, const double *pos, const double *vel, const double *u,
                              int mem)
 {

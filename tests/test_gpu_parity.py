@@ -310,6 +310,22 @@ def test_batched_boxes_match_each_box_alone(crk):
             compare(part, ref, counts, precision, label=f"box {b}")
 
 
+def test_autotune_keeps_the_fastest_capacity_and_the_forces(crk):
+    box = wl.gaussian_field_box(16, seed=21)
+    op = oracle_params(box)
+    ref = oracle.forces(box.pos, box.vel, box.mass, box.u, box.h, box.species, op)
+    with crk.Sim(crk.box_physics(box), leaf_cap=64, precision=1) as sim:
+        sim.load(box)
+        best, ms = crk.crk_autotune(sim.handle, (32, 64, 128))
+        assert best in (32, 64, 128) and set(ms) == {32, 64, 128}
+        assert all(v > 0 for v in ms.values()) and ms[best] == min(ms.values())
+        out = sim.forces(counts=True)
+        compare(out, ref, oracle_counts(box_dict(box), op), 1, label=f"autotuned cap={best}")
+        with pytest.raises(crk.CrkError) as e:
+            crk.crk_autotune(sim.handle, (48,))
+        assert e.value.code == crk.CRK_EINVAL
+
+
 def test_batched_step_matches_single_box_steps(crk):
     boxes = [wl.gaussian_field_box(n, seed=200 + n) for n in (10, 16)]
     cat = wl.concat_boxes(boxes)
