@@ -186,7 +186,7 @@ int crk_get_sums(crk_sim *sim, double momentum[3], double *energy, int64_t *nflo
 int crk_get_size(crk_sim *sim, int64_t *n, int *nbox);
 
 /* Leaf-capacity autotuner.  The paper sizes its base leaves by hand for its
- * hardware (Sec. IV-B1: a few hundred particles per leaf on MI250X); here the
+ * hardware (Sec. IV-B1: several hundred particles per leaf on MI250X); here the
  * best capacity depends on the particle distribution.  Runs one force
  * evaluation of the loaded particles at each candidate capacity caps[k]
  * (each 32, 64 or 128), timed with CUDA events on the handle's stream after a
