@@ -38,6 +38,27 @@ UNIT = "particles/s"
 # (leaf-pair overlap) are not counted.
 FLOP_PER_PAIR = {"density": 22, "moments": 125, "hydro": 183, "gravity": 41}
 
+# DRAM bytes (read + write) per particle of one launch of each pass, from the
+# one-pass ncu capture summarised in profiles/launches_gaussian_2x128.md
+# (2x128^3 Gaussian field, leaf capacity 128; density = list count + fill +
+# evaluation).  They describe the kernels of the csrc/passes.cu with this
+# SHA-256 only; for any other source the bench reports no traffic.
+TRAFFIC_SOURCE_SHA256 = "f32a10db6e6285cbbee48faa787308c5c79ab49e6ecb1346c956f7e3da5cddb6"
+TRAFFIC_BYTES_PER_PARTICLE = {"gravity": 81.2, "hydro": 997.5, "moments": 955.8, "density": 3546.7}
+
+
+def _traffic(kernel: str, particles: int, leaf_cap: int):
+    import hashlib
+
+    try:
+        with open(os.path.join(ROOT, "paper_2510_03557_gb300", "csrc", "passes.cu"), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+    except OSError:
+        return None
+    if sha != TRAFFIC_SOURCE_SHA256 or leaf_cap != 128 or kernel not in TRAFFIC_BYTES_PER_PARTICLE:
+        return None
+    return round(TRAFFIC_BYTES_PER_PARTICLE[kernel] * particles)
+
 
 def _peaks():
     try:
@@ -577,7 +598,10 @@ def main():
                        "l2": "inputs larger than L2 (~2.5 GB resident state)"},
             "roofline": {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3),
                          "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                         "traffic": None,
+                         "traffic": _traffic(dom, N, args.leaf_cap),
+                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, "
+                                           "2x128^3 capture (profiles/launches_gaussian_2x128.md), "
+                                           "scaled by particles",
                          "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
                                         f"({peak_kind} sm_max_mhz)"},
             "pass_tflops": {k: round(v, 3) for k, v in pass_tflops.items()},
