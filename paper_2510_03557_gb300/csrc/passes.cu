@@ -1232,6 +1232,46 @@ __device__ __forceinline__ R split_S(R r, R inv2rs)
     }
 }
 
+// The pair forces of the K staged candidates of one visit on this lane's
+// target, masked by the gravity predicate: r^2 < r_cut^2 in the pass's
+// precision, re-decided in FP64 inside the mixed form's guard band; the
+// target itself excluded.
+template <typename R, bool WRAP, bool COUNT>
+__device__ __forceinline__ void gravity_tile(const Vec4<R> *tile, const uint8_t *tslot, uint32_t K,
+                                             const Target<R> &q, R L, R hL, R rc2, double rc2x, R gb, R e2,
+                                             R inv2rs, R Gc, bool same, bool act, const State &s, uint32_t i,
+                                             uint32_t sJ, double Ld, R &ax, R &ay, R &az, int &nc, uint64_t &hs)
+{
+#pragma unroll 4
+    for (uint32_t j = 0; j < K; ++j) {
+        const Vec4<R> rj = tile[j];
+        R dx, dy, dz;
+        const R r2 = sep2<R, WRAP>(rj, q, L, hL, dx, dy, dz);
+        bool in = act && r2 < rc2;
+        if (Real<R>::mixed && act && r2 >= rc2 - gb && r2 < rc2 + gb)
+            in = exact_lt(s, i, sJ + tslot[j], Ld, rc2x);  // rare: pairs at the cut
+        if (same && sJ + tslot[j] == i) in = false;
+        const R r = Real<R>::sqrt_(r2);
+        const R S = split_S<R>(r, inv2rs);
+        const R s2 = r2 + e2;
+        R inv3;
+        if (Real<R>::mixed) {
+            const float is = rsqrtf((float)s2);
+            inv3 = (R)(is * is * is);
+        } else {
+            inv3 = (R)1 / (s2 * Real<R>::sqrt_(s2));
+        }
+        const R f = in ? Gc * rj.w * S * inv3 : (R)0;  // a_i += f (x_j - x_i)
+        ax += f * dx;
+        ay += f * dy;
+        az += f * dz;
+        if (COUNT && in) {
+            ++nc;
+            hs += mix64((uint64_t)s.id[sJ + tslot[j]]);
+        }
+    }
+}
+
 template <typename R, int JMAX, bool COUNT>
 __global__ void __launch_bounds__(kBlock) gravity_k(PassArgs a)
 {
@@ -1277,44 +1317,14 @@ __global__ void __launch_bounds__(kBlock) gravity_k(PassArgs a)
         if (K == 0u) continue;
         const Target<R> q = target_in_frame(ri, fr);
         const R gb = Real<R>::mixed ? (R)guard_band((float)rc, q.mag) : (R)0;
-        uint32_t m[JMAX / 32];
-        test_tile_any<R, JMAX, false>(tile, nullptr, q, L, hL, rc2 + gb, G.act ? chunk_mask(K) : 0u, m);
         const bool same = J == (uint32_t)I;  // the target itself is among the candidates
-#pragma unroll
-        for (int ww = 0; ww < JMAX / 32; ++ww) {
-            uint32_t bits = m[ww];
-            while (bits) {
-                const int j = 32 * ww + __ffs(bits) - 1;
-                bits &= bits - 1;
-                const uint32_t jg = sJ + tslot[j];
-                if (same && jg == i) continue;
-                const R4 rj = tile[j];
-                R dx, dy, dz;
-                const R r2 = q.wrap ? sep2<R, true>(rj, q, L, hL, dx, dy, dz)
-                                    : sep2<R, false>(rj, q, L, hL, dx, dy, dz);
-                if (Real<R>::mixed && r2 >= rc2 - gb) {
-                    if (!exact_lt(a.s, i, jg, Ld, rc2x)) continue;
-                }
-                const R r = Real<R>::sqrt_(r2);
-                const R S = split_S<R>(r, inv2rs);
-                const R s2 = r2 + e2;
-                R inv3;
-                if (Real<R>::mixed) {
-                    const float is = rsqrtf((float)s2);
-                    inv3 = (R)(is * is * is);
-                } else {
-                    inv3 = (R)1 / (s2 * Real<R>::sqrt_(s2));
-                }
-                const R fr_ = Gc * rj.w * S * inv3;   // a_i += fr_ (x_j - x_i)
-                ax += fr_ * dx;
-                ay += fr_ * dy;
-                az += fr_ * dz;
-                if (COUNT) {
-                    ++nc;
-                    hs += mix64((uint64_t)a.s.id[jg]);
-                }
-            }
-        }
+        // every staged candidate against every target, branch-free: the pair
+        // force is formed for all and kept where r < r_cut (a select, so that
+        // nothing computed for an out-of-range pair reaches the sums)
+        if (q.wrap) gravity_tile<R, true, COUNT>(tile, tslot, K, q, L, hL, rc2, rc2x, gb, e2, inv2rs, Gc, same,
+                                                 G.act, a.s, i, sJ, Ld, ax, ay, az, nc, hs);
+        else gravity_tile<R, false, COUNT>(tile, tslot, K, q, L, hL, rc2, rc2x, gb, e2, inv2rs, Gc, same,
+                                           G.act, a.s, i, sJ, Ld, ax, ay, az, nc, hs);
     }
     if (!G.act) return;
     R4 o;
