@@ -366,6 +366,17 @@ __device__ __forceinline__ CandFrame cand_frame(const Leaves &lv, int I, const f
     return f;
 }
 
+// Greatest common divisor (Euclid).
+__device__ __forceinline__ uint32_t gcd_u32(uint32_t a, uint32_t b)
+{
+    while (b) {
+        const uint32_t r = a % b;
+        a = b;
+        b = r;
+    }
+    return a;
+}
+
 __device__ __forceinline__ float box_gap2(const WarpBox &b, float x, float y, float z)
 {
     float gap2 = 0.f, g;
@@ -578,6 +589,23 @@ struct ListRing {
     }
 };
 
+// Visit order of a leaf-pair row of n entries: entry (t * stride) mod n at
+// step t, the stride the smallest odd number >= 7 coprime to n.  The row is in
+// Morton order, so consecutive entries lie on one side of the target leaf;
+// striding through it spreads every run of visits over all sides, and the
+// 32 targets of a warp gain neighbours at similar rates.
+struct RowOrder {
+    uint32_t n, stride;
+    __device__ __forceinline__ explicit RowOrder(uint32_t len) : n(len), stride(7u)
+    {
+        while (n > 1u && gcd_u32(stride, n) != 1u) stride += 2u;
+    }
+    __device__ __forceinline__ uint32_t at(uint32_t t) const
+    {
+        return (uint32_t)(((uint64_t)t * stride) % n);
+    }
+};
+
 // Target-side thresholds of the hydro neighbour test: r^2 < H_i^2 (plus the
 // guard band when the gather set is counted exactly).
 template <typename R>
@@ -650,7 +678,9 @@ __global__ void __launch_bounds__(kBlock) hlist_count_k(PassArgs a)
     const WarpBox wb = warp_box(px, py, pz, G.act);
     const float Hw = warp_max(G.act ? (float)ht.H : 0.f);
     uint32_t cnt = 0;
-    for (uint32_t p = a.hrow[I]; p < a.hrow[I + 1]; ++p) {
+    const RowOrder order(a.hrow[I + 1] - a.hrow[I]);
+    for (uint32_t t = 0; t < order.n; ++t) {
+        const uint32_t p = a.hrow[I] + order.at(t);
         uint32_t sJ;
         float4 fr;
         const uint32_t K = hydro_stage<R, JMAX>(a, p, I, wb, Hw, Ld, tile, h2j, tslot, lane, sJ, fr);
@@ -700,7 +730,9 @@ __global__ void __launch_bounds__(kBlock) hlist_fill_k(PassArgs a)
     const uint32_t prow = a.hrow[I];
     const uint32_t room = G.act ? a.nl_cnt[i] : 0u;  // entries the count pass found
     uint32_t k = 0;
-    for (uint32_t p = prow; p < a.hrow[I + 1]; ++p) {
+    const RowOrder order(a.hrow[I + 1] - prow);
+    for (uint32_t t = 0; t < order.n; ++t) {
+        const uint32_t p = prow + order.at(t);
         uint32_t sJ;
         float4 fr;
         const uint32_t K = hydro_stage<R, JMAX>(a, p, I, wb, Hw, Ld, tile, h2j, tslot, lane, sJ, fr);
