@@ -213,7 +213,7 @@ PassArgs pass_args(crk_sim *s)
     a.err = s->err.as<int>();
     a.nfloor = s->nfloor.as<unsigned long long>();
     a.nl_j = s->nl_j.as<uint32_t>();
-    a.nl_m = s->nl_m.as<uint16_t>();
+    a.hsj = s->hsj.as<uint32_t>();
     a.nl_row = s->nl_row.as<uint32_t>();
     a.nl_len = s->nl_len.as<uint32_t>();
     a.nl_cnt = s->nl_cnt.as<uint32_t>();
@@ -361,11 +361,12 @@ int build_tree(crk_sim *s)
     RET(s->hcol.ensure((size_t)std::max<int64_t>(s->npair_h, 1) * 4));
     RET(s->gcol.ensure((size_t)std::max<int64_t>(s->npair_g, 1) * 4));
     RET(s->hfr.ensure((size_t)std::max<int64_t>(s->npair_h, 1) * 16));
+    RET(s->hsj.ensure((size_t)std::max<int64_t>(s->npair_h, 1) * 4));
     RET(s->gfr.ensure((size_t)std::max<int64_t>(s->npair_g, 1) * 16));
     launch_pair_fill(s->nd, s->lv, bd, s->nleaf, 1, s->hrow.as<uint32_t>(), s->hcol.as<uint32_t>(),
-                     s->hfr.as<float4>(), st);
+                     s->hfr.as<float4>(), s->hsj.as<uint32_t>(), st);
     launch_pair_fill(s->nd, s->lv, bd, s->nleaf, 0, s->grow.as<uint32_t>(), s->gcol.as<uint32_t>(),
-                     s->gfr.as<float4>(), st);
+                     s->gfr.as<float4>(), nullptr, st);
     mark(s, PH_PAIRS, 1);
     return CRK_OK;
 }
@@ -395,9 +396,7 @@ static int size_hydro_lists(crk_sim *s, PassArgs &a, bool want_counts)
     s->nl_rows = s->host_scalars[5];
     const size_t entries = (size_t)std::max<int64_t>(s->nl_rows, 1) * 32u;
     RET(s->nl_j.ensure(entries * 4));
-    RET(s->nl_m.ensure(entries * 2));
     a.nl_j = s->nl_j.as<uint32_t>();
-    a.nl_m = s->nl_m.as<uint16_t>();
     return CRK_OK;
 }
 
@@ -864,7 +863,7 @@ extern "C" int crk_destroy(crk_sim *s)
                     &s->pm, &s->uhat, &s->acc_h, &s->acc_g, &s->nbrc, &s->nbrh, &s->gravc,
                     &s->gravh, &s->err, &s->nfloor, &s->partial, &s->sums, &s->staging,
                     &s->in_stage, &s->grp_cnt, &s->grp_off, &s->grp_gas, &s->grp_all, &s->hfr, &s->gfr,
-                    &s->nl_j, &s->nl_m, &s->nl_row, &s->nl_len, &s->nl_cnt};
+                    &s->nl_j, &s->nl_row, &s->nl_len, &s->nl_cnt, &s->hsj};
     for (DBuf *b : bufs) b->release();
     for (int k = 0; k < 3; ++k) {
         s->lv_u32[k].release();

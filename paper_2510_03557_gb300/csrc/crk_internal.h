@@ -83,6 +83,7 @@ struct PassArgs {
     const uint32_t *hrow, *hcol;   // hydro list
     const uint32_t *grow, *gcol;   // gravity list
     const float4 *hfr, *gfr;       // per-entry leaf-pair frames of the two lists
+    const uint32_t *hsj;           // hydro list: first sorted particle of each entry's leaf J
     void *pm;                // R4[n]
     void *hrec[7];           // R4[n] each: hydro records
     void *uhat;              // R[n] predicted u
@@ -93,9 +94,10 @@ struct PassArgs {
     int32_t *grav_count;
     uint64_t *grav_hash;
     // hydro neighbour lists (written by the density pass): entry k of lane l
-    // of gas group g at [(nl_row[g] + k) * 32 + l]
-    uint32_t *nl_j;          // sorted index of the neighbour
-    uint16_t *nl_m;          // bit 15: r < H_i; bits 0-14: leaf-pair offset in the hydro row
+    // of gas group g at [(nl_row[g] + k) * 32 + l]; an entry is bit 31: r < H_i,
+    // bits 7-30: the leaf pair's offset in the target leaf's hydro row,
+    // bits 0-6: the neighbour's slot in its leaf
+    uint32_t *nl_j;
     uint32_t *nl_row;        // first row of every gas group
     uint32_t *nl_len;        // rows of every gas group (its longest list)
     uint32_t *nl_cnt;        // entries of every particle
@@ -137,7 +139,8 @@ void launch_group_fill(const Leaves &lv, int nleaf, int gas_only, const uint32_t
 void launch_pair_count(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, int nleaf,
                        int hydro, uint32_t *counts, cudaStream_t st);
 void launch_pair_fill(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, int nleaf,
-                      int hydro, const uint32_t *row, uint32_t *col, float4 *frame, cudaStream_t st);
+                      int hydro, const uint32_t *row, uint32_t *col, float4 *frame, uint32_t *start,
+                      cudaStream_t st);
 
 // ---- passes (passes.cu) ----
 void launch_records(const PassArgs &a, int mixed, cudaStream_t st);

@@ -528,13 +528,16 @@ constexpr size_t tile_warp_bytes()
 // union set r < H_i or r < H_j, the particle itself included.  Entry k of
 // lane l of gas group g sits at row nl_row[g] + k, column l: the lanes of a
 // group read one 128-byte row per step.  The fill stages rows in shared
-// memory and writes each row once all lanes have passed it.  An entry is the neighbour's
-// sorted index and a 16-bit tag: bit 15 set when r < H_i (the gather set of
-// the density and the moments), bits 0-14 the position of the leaf pair in
-// row I of the hydro pair list (its frame).  The moments and hydro passes
+// memory and writes each row once all lanes have passed it.  An entry is one
+// 32-bit word: bit 31 set when r < H_i (the gather set of the density and the
+// moments), bits 7-30 the position of the leaf pair in row I of the hydro pair
+// list (its frame, and the first particle of leaf J in hsj), bits 0-6 the
+// neighbour's slot in leaf J.  The moments and hydro passes
 // then walk their lists with every lane busy and no candidate test.
-constexpr uint16_t kGather = 0x8000u;
-constexpr uint32_t kMaxRowOffset = 0x7fffu;
+constexpr uint32_t kGather = 0x80000000u;
+constexpr uint32_t kRowShift = 7;
+constexpr uint32_t kMaxRowOffset = 0xffffffu;
+constexpr uint32_t kSlotMask = 0x7fu;
 
 
 template <typename R, int JMAX>
@@ -545,7 +548,7 @@ constexpr size_t hlist_warp_bytes()
 
 // Rows of list entries a warp of the fill pass holds in shared memory.
 constexpr uint32_t kRingRows = 32;
-constexpr size_t kRingBytes = kRingRows * 32 * (sizeof(uint32_t) + sizeof(uint16_t));
+constexpr size_t kRingBytes = kRingRows * 32 * sizeof(uint32_t);
 
 template <typename R, int JMAX>
 constexpr size_t hfill_warp_bytes()
@@ -555,36 +558,22 @@ constexpr size_t hfill_warp_bytes()
 
 // Entries of the fill pass on their way to global memory: a lane puts entry
 // k into ring row k mod kRingRows while k >= base, else writes it directly;
-// rows [base, upto) leave as whole 128-byte (indices) and 64-byte (tags) rows.
+// rows [base, upto) leave as whole 128-byte rows.
 struct ListRing {
     uint32_t *rj;
-    uint16_t *rt;
     uint32_t base;
     size_t e0;       // the lane's entry 0 in global memory
 
-    __device__ __forceinline__ void put(const PassArgs &a, uint32_t k, uint32_t lane, uint32_t j, uint16_t tag)
+    __device__ __forceinline__ void put(const PassArgs &a, uint32_t k, uint32_t lane, uint32_t entry)
     {
-        if (k >= base) {
-            const uint32_t s = (k % kRingRows) * 32u + lane;
-            rj[s] = j;
-            rt[s] = tag;
-        } else {
-            const size_t e = e0 + (size_t)k * 32u;
-            a.nl_j[e] = j;
-            a.nl_m[e] = tag;
-        }
+        if (k >= base) rj[(k % kRingRows) * 32u + lane] = entry;
+        else a.nl_j[e0 + (size_t)k * 32u] = entry;
     }
     // writes rows [base, upto); a lane's own entries only (k: entries it has put)
     __device__ __forceinline__ void flush(const PassArgs &a, uint32_t upto, uint32_t k, uint32_t lane)
     {
-        for (uint32_t r = base; r < upto; ++r) {
-            if (r < k) {
-                const uint32_t s = (r % kRingRows) * 32u + lane;
-                const size_t e = e0 + (size_t)r * 32u;
-                a.nl_j[e] = rj[s];
-                a.nl_m[e] = rt[s];
-            }
-        }
+        for (uint32_t r = base; r < upto; ++r)
+            if (r < k) a.nl_j[e0 + (size_t)r * 32u] = rj[(r % kRingRows) * 32u + lane];
         base = upto;
     }
 };
@@ -713,7 +702,6 @@ __global__ void __launch_bounds__(kBlock) hlist_fill_k(PassArgs a)
     uint8_t *tslot = reinterpret_cast<uint8_t *>(h2j + JMAX);
     ListRing ring;
     ring.rj = reinterpret_cast<uint32_t *>(base + hlist_warp_bytes<R, JMAX>());
-    ring.rt = reinterpret_cast<uint16_t *>(ring.rj + kRingRows * 32);
     ring.base = 0;
     const Group G = load_group(a.lv, a.ggas, gi, lane);
     const int I = G.I;
@@ -746,7 +734,7 @@ __global__ void __launch_bounds__(kBlock) hlist_fill_k(PassArgs a)
         else test_tile_union<R, JMAX, false>(tile, h2j, q, L, hL, thr, cm, mu, mg);
         const uint32_t off = p - prow;
         if (off > kMaxRowOffset && lane == 0) set_error(a.err, CRK_EOVERFLOW, a.s.id[i]);
-        const uint16_t otag = (uint16_t)(off & kMaxRowOffset);
+        const uint32_t otag = (off & kMaxRowOffset) << kRowShift;
         uint32_t pop = 0;
 #pragma unroll
         for (int ww = 0; ww < JMAX / 32; ++ww) pop += (uint32_t)__popc(mu[ww]);
@@ -760,8 +748,7 @@ __global__ void __launch_bounds__(kBlock) hlist_fill_k(PassArgs a)
                 const int b = __ffs(bits) - 1;
                 bits &= bits - 1;
                 if (k < room)
-                    ring.put(a, k, lane, sJ + tslot[32 * ww + b],
-                             (uint16_t)(otag | (((mg[ww] >> b) & 1u) ? kGather : 0u)));
+                    ring.put(a, k, lane, otag | tslot[32 * ww + b] | (((mg[ww] >> b) & 1u) ? kGather : 0u));
                 ++k;
             }
         }
@@ -777,40 +764,47 @@ __global__ void __launch_bounds__(kBlock) hlist_fill_k(PassArgs a)
     }
 }
 
-// Reads a lane's list entries in order, keeping the next two (index, tag)
-// pairs in registers so that their loads overlap the work on earlier pairs.
-struct ListCursor {
+// The neighbour's sorted index and the leaf-pair frame of a list entry.
+__device__ __forceinline__ uint32_t entry_index(const uint32_t *hsj_row, uint32_t e)
+{
+    return hsj_row[(e >> kRowShift) & kMaxRowOffset] + (e & kSlotMask);
+}
+__device__ __forceinline__ float4 entry_frame(const float4 *frow, uint32_t e)
+{
+    return frow[(e >> kRowShift) & kMaxRowOffset];
+}
+
+// Streams a lane's list entries for a consumer that works on entry k while
+// the records of entry k + 1 load: entry k + 1's neighbour index was looked
+// up one step earlier, entry k + 2's lookup and entry k + 3's load are in
+// flight, so that no load is used in the step that issues it.
+struct ListPipe {
     size_t e0;
     uint32_t cnt;
-    uint32_t j0, j1;
-    uint16_t tag0, tag1;
+    uint32_t e1, j1;  // the next entry to take and its neighbour index
+    uint32_t e2, j2;  // the one after, its index looked up
+    uint32_t e3;      // the one after that, loaded
 
-    __device__ __forceinline__ ListCursor(const PassArgs &a, uint32_t gi, uint32_t lane, uint32_t n)
+    // on return (e1, j1) is entry 0
+    __device__ __forceinline__ ListPipe(const PassArgs &a, uint32_t gi, uint32_t lane, uint32_t n,
+                                        const uint32_t *srow)
     {
         e0 = (size_t)a.nl_row[gi] * 32u + lane;
         cnt = n;
-        j0 = j1 = 0u;
-        tag0 = tag1 = 0;
-        if (cnt > 0u) {
-            j0 = a.nl_j[e0];
-            tag0 = a.nl_m[e0];
-        }
-        if (cnt > 1u) {
-            j1 = a.nl_j[e0 + 32u];
-            tag1 = a.nl_m[e0 + 32u];
-        }
+        e1 = cnt > 0u ? a.nl_j[e0] : 0u;
+        e2 = cnt > 1u ? a.nl_j[e0 + 32u] : 0u;
+        e3 = cnt > 2u ? a.nl_j[e0 + 64u] : 0u;
+        j1 = cnt > 0u ? entry_index(srow, e1) : 0u;
+        j2 = cnt > 1u ? entry_index(srow, e2) : 0u;
     }
-    // after entry k - 1 was taken: (j1, tag1) becomes entry k - 1's successor
-    // and entry k is fetched
-    __device__ __forceinline__ void advance(const PassArgs &a, uint32_t k)
+    // entry m, (e1, j1), was taken: (e1, j1) becomes entry m + 1
+    __device__ __forceinline__ void step(const PassArgs &a, const uint32_t *srow, uint32_t m)
     {
-        j0 = j1;
-        tag0 = tag1;
-        if (k < cnt) {
-            const size_t e = e0 + (size_t)k * 32u;
-            j1 = a.nl_j[e];
-            tag1 = a.nl_m[e];
-        }
+        e1 = e2;
+        j1 = j2;
+        e2 = e3;
+        j2 = m + 2u < cnt ? entry_index(srow, e3) : 0u;
+        e3 = m + 3u < cnt ? a.nl_j[e0 + (size_t)(m + 3u) * 32u] : 0u;
     }
 };
 
@@ -845,33 +839,35 @@ __global__ void __launch_bounds__(kBlock) density_k(PassArgs a)
     const R4 ri = pm[i];
     const HTarget<R> ht = hydro_target<R>(a.s, i);
     const float4 *__restrict__ frow = a.hfr + a.hrow[I];
-    ListCursor cur(a, gi, lane, G.act ? a.nl_cnt[i] : 0u);
+    const uint32_t *__restrict__ srow = a.hsj + a.hrow[I];
+    ListPipe pipe(a, gi, lane, G.act ? a.nl_cnt[i] : 0u, srow);
     R rho = 0;
     int nc = 0;
     uint64_t hs = 0;
+    // the neighbour's record and frame one entry ahead
     R4 rn;
     float4 fn;
-    uint16_t tn = 0;
-    uint32_t jn = 0;
-    if (cur.cnt > 0u) {
-        tn = cur.tag0;
-        jn = cur.j0;
+    uint32_t en = 0, jn = 0;
+    if (pipe.cnt > 0u) {
+        en = pipe.e1;
+        jn = pipe.j1;
         rn = pm[jn];
-        fn = frow[tn & kMaxRowOffset];
+        fn = entry_frame(frow, en);
+        pipe.step(a, srow, 0u);
     }
-    for (uint32_t k = 0; k < cur.cnt; ++k) {
+    for (uint32_t k = 0; k < pipe.cnt; ++k) {
         const R4 rj = rn;
         const float4 fr = fn;
-        const uint16_t tag = tn;
+        const uint32_t e = en;
         const uint32_t j = jn;
-        if (k + 1u < cur.cnt) {
-            tn = cur.tag1;
-            jn = cur.j1;
+        if (k + 1u < pipe.cnt) {
+            en = pipe.e1;
+            jn = pipe.j1;
             rn = pm[jn];
-            fn = frow[tn & kMaxRowOffset];
+            fn = entry_frame(frow, en);
+            pipe.step(a, srow, k + 1u);
         }
-        cur.advance(a, k + 2u);
-        if (!(tag & kGather)) continue;
+        if (!(e & kGather)) continue;
         R dx, dy, dz;
         const R r2 = list_sep2(rj, ri, fr, L, hL, dx, dy, dz);
         const R r = Real<R>::sqrt_(r2);
@@ -1041,29 +1037,31 @@ __global__ void __launch_bounds__(kBlock) moments_k(PassArgs a)
     const R cW = (R)kWn * invH2 * invH;
     const R cG = (R)kGn * invH2 * invH2 * invH;
     const float4 *__restrict__ frow = a.hfr + a.hrow[I];
-    ListCursor cur(a, gi, lane, G.act ? a.nl_cnt[i] : 0u);
+    const uint32_t *__restrict__ srow = a.hsj + a.hrow[I];
+    ListPipe pipe(a, gi, lane, G.act ? a.nl_cnt[i] : 0u, srow);
     MomentAcc<R> acc;
     acc.zero();
-    // software pipeline: list entries two ahead, the neighbour's record one ahead
+    // the neighbour's record and frame one entry ahead
     R4 rn;
     float4 fn;
-    uint16_t tn = 0;
-    if (cur.cnt > 0u) {
-        tn = cur.tag0;
-        rn = rec0[cur.j0];
-        fn = frow[tn & kMaxRowOffset];
+    uint32_t en = 0;
+    if (pipe.cnt > 0u) {
+        en = pipe.e1;
+        rn = rec0[pipe.j1];
+        fn = entry_frame(frow, en);
+        pipe.step(a, srow, 0u);
     }
-    for (uint32_t k = 0; k < cur.cnt; ++k) {
+    for (uint32_t k = 0; k < pipe.cnt; ++k) {
         const R4 rj = rn;
         const float4 fr = fn;
-        const uint16_t tag = tn;
-        if (k + 1u < cur.cnt) {
-            tn = cur.tag1;
-            rn = rec0[cur.j1];
-            fn = frow[tn & kMaxRowOffset];
+        const uint32_t e = en;
+        if (k + 1u < pipe.cnt) {
+            en = pipe.e1;
+            rn = rec0[pipe.j1];
+            fn = entry_frame(frow, en);
+            pipe.step(a, srow, k + 1u);
         }
-        cur.advance(a, k + 2u);
-        if (!(tag & kGather)) continue;
+        if (!(e & kGather)) continue;
         R dx, dy, dz;
         const R r2 = list_sep2(rj, ri, fr, L, hL, dx, dy, dz);
         const R x[3] = {-dx, -dy, -dz};
@@ -1178,31 +1176,33 @@ __global__ void __launch_bounds__(kBlock) hydro_k(PassArgs a)
     const R cGi = (R)kGn * invHi * invHi * invHi * invHi * invHi;
     const R hi2e = eps2 * si.h * si.h;
     const float4 *__restrict__ frow = a.hfr + a.hrow[I];
-    ListCursor cur(a, gi, lane, G.act ? a.nl_cnt[i] : 0u);
+    const uint32_t *__restrict__ srow = a.hsj + a.hrow[I];
+    ListPipe pipe(a, gi, lane, G.act ? a.nl_cnt[i] : 0u, srow);
     R ax = 0, ay = 0, az = 0, du = 0;
-    // software pipeline: list entries two ahead, the neighbour's records one ahead
+    // the neighbour's records and frame one entry ahead
     R4 rn[7];
     float4 fn;
     uint32_t jn = 0;
-    if (cur.cnt > 0u) {
-        jn = cur.j0;
-        fn = frow[cur.tag0 & kMaxRowOffset];
+    if (pipe.cnt > 0u) {
+        jn = pipe.j1;
+        fn = entry_frame(frow, pipe.e1);
 #pragma unroll
         for (int q = 0; q < 7; ++q) rn[q] = reinterpret_cast<const R4 *>(a.hrec[q])[jn];
+        pipe.step(a, srow, 0u);
     }
-    for (uint32_t k = 0; k < cur.cnt; ++k) {
+    for (uint32_t k = 0; k < pipe.cnt; ++k) {
         const uint32_t j = jn;
         const float4 fr = fn;
         HState<R> sj;
         unpack_hstate(rn, sj);
         const R4 rj0 = rn[0];
-        if (k + 1u < cur.cnt) {
-            jn = cur.j1;
-            fn = frow[cur.tag1 & kMaxRowOffset];
+        if (k + 1u < pipe.cnt) {
+            jn = pipe.j1;
+            fn = entry_frame(frow, pipe.e1);
 #pragma unroll
             for (int q = 0; q < 7; ++q) rn[q] = reinterpret_cast<const R4 *>(a.hrec[q])[jn];
+            pipe.step(a, srow, k + 1u);
         }
-        cur.advance(a, k + 2u);
         if (j == i) continue;
         R dx, dy, dz;
         const R r2 = list_sep2(rj0, ri0, fr, L, hL, dx, dy, dz);

@@ -75,10 +75,10 @@ struct crk_sim {
     DBuf keys, keys_alt, vals, vals_alt, counts, scan_tmp, flags, flag_scan, scalars;
     DBuf lv_u32[3], lv_sp, lv_c[3], lv_e[3], lv_h, lv_chunk[2];
     DBuf nd_f[7], nd_slot;
-    DBuf hrow, grow, hcnt, gcnt, hcol, gcol, hfr, gfr;
+    DBuf hrow, grow, hcnt, gcnt, hcol, gcol, hfr, gfr, hsj;
     DBuf pm, hrec[7], uhat, acc_h, acc_g;
     DBuf nbrc, nbrh, gravc, gravh;
-    DBuf nl_j, nl_m, nl_row, nl_len, nl_cnt;  // hydro neighbour lists
+    DBuf nl_j, nl_row, nl_len, nl_cnt;  // hydro neighbour lists
     int64_t nl_rows = 0;
     DBuf err, nfloor, partial, sums;
     DBuf staging, in_stage;

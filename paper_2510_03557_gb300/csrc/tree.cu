@@ -445,7 +445,7 @@ __device__ __forceinline__ float4 pair_frame(const Leaves &lv, int I, int J, dou
 template <bool FILL>
 __global__ void pair_walk_k(Nodes nd, Leaves lv, const BoxDev *__restrict__ boxes, int nleaf,
                             int hydro, uint32_t *counts, const uint32_t *__restrict__ row,
-                            uint32_t *col, float4 *frame)
+                            uint32_t *col, float4 *frame, uint32_t *start)
 {
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nleaf) return;
@@ -498,6 +498,7 @@ __global__ void pair_walk_k(Nodes nd, Leaves lv, const BoxDev *__restrict__ boxe
             if (FILL) {
                 col[base + cnt] = (uint32_t)k;
                 frame[base + cnt] = pair_frame(lv, I, k, bx.L);
+                if (start) start[base + cnt] = lv.start[k];
             }
             ++cnt;
         } else {
@@ -745,16 +746,17 @@ void launch_pair_count(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, i
 {
     if (nleaf <= 0) return;
     pair_walk_k<false><<<grid_for(nleaf, 128), 128, 0, st>>>(nd, lv, boxes, nleaf, hydro, counts,
-                                                               nullptr, nullptr, nullptr);
+                                                               nullptr, nullptr, nullptr, nullptr);
     note_launches(1);
 }
 
 void launch_pair_fill(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, int nleaf,
-                      int hydro, const uint32_t *row, uint32_t *col, float4 *frame, cudaStream_t st)
+                      int hydro, const uint32_t *row, uint32_t *col, float4 *frame, uint32_t *start,
+                      cudaStream_t st)
 {
     if (nleaf <= 0) return;
     pair_walk_k<true><<<grid_for(nleaf, 128), 128, 0, st>>>(nd, lv, boxes, nleaf, hydro, nullptr,
-                                                              row, col, frame);
+                                                              row, col, frame, start);
     note_launches(1);
 }
 
