@@ -440,6 +440,8 @@ def main():
     ap.add_argument("--sample", type=int, default=64, help="oracle sample of the precision study")
     ap.add_argument("--n", type=int, default=128, help="lattice size per species (2 n^3 particles)")
     ap.add_argument("--leaf-cap", type=int, default=128)
+    ap.add_argument("--rebuild-every", type=int, default=1,
+                    help="sort into new leaves every this many steps (boxes grow in between)")
     ap.add_argument("--fp64-steps", type=int, default=2,
                     help="KDK steps of the FP64 form (precision study: -1 = as many as the mixed form)")
     ap.add_argument("--no-cpu", action="store_true")
@@ -490,7 +492,8 @@ def main():
     stream = torch.cuda.Stream()
 
     # ---------------- mixed form, device-resident (the headline value)
-    sim = crk.Sim(phys, leaf_cap=args.leaf_cap, precision=crk.CRK_MIXED, stream=stream)
+    sim = crk.Sim(phys, leaf_cap=args.leaf_cap, precision=crk.CRK_MIXED, stream=stream,
+                  rebuild_every=args.rebuild_every)
     sim.load(box)
     counts = sim.forces(counts=True)      # untimed: the true pair counts for the roofline
     gas = box.species == wl.GAS
@@ -594,7 +597,8 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": f"gaussian-field 2x{args.n}^3, FP32-mixed, KDK dt={dt}",
-                       "particles": N, "leaf_cap": args.leaf_cap, "parallelism": f"replicas{world}",
+                       "particles": N, "leaf_cap": args.leaf_cap, "rebuild_every": args.rebuild_every,
+                       "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (~2.5 GB resident state)"},
             "roofline": {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3),
                          "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),

@@ -81,7 +81,13 @@ typedef struct {
     int precision;     /* CRK_FP64 or CRK_MIXED */
     int cm_level;      /* chaining-mesh Morton level b (2^b bins per side); 0 = automatic */
     int flags;         /* reserved, 0 */
-    int reserved[3];
+    int rebuild_every; /* sort particles into new leaves every this many steps (0 or 1: every
+                          step); in between, leaves keep their particles and their bounding
+                          boxes grow with them, and only the boxes, the leaf hierarchy and the
+                          pair lists are recomputed (paper Sec. IV-B1: leaves built once per
+                          long step, boxes grown in the substeps).  Loading or adding or
+                          removing particles always rebuilds. */
+    int reserved[2];
 } crk_params;
 
 /* Outputs of crk_forces.  Every pointer is optional (NULL skips it); all

@@ -55,7 +55,7 @@ class Physics(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("phys", Physics), ("kernel", ctypes.c_int), ("leaf_cap", ctypes.c_int),
                 ("precision", ctypes.c_int), ("cm_level", ctypes.c_int), ("flags", ctypes.c_int),
-                ("reserved", ctypes.c_int * 3)]
+                ("rebuild_every", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
 
 
 class Outputs(ctypes.Structure):
@@ -122,13 +122,14 @@ def physics(box=1.0, G=1.0, gamma=5.0 / 3.0, r_cut=0.1, r_split=0.02, eps_soft=0
 
 
 def params(phys: Physics | None = None, leaf_cap=64, precision=CRK_MIXED, cm_level=0,
-           kernel=CRK_WENDLAND_C4) -> Params:
+           kernel=CRK_WENDLAND_C4, rebuild_every=1) -> Params:
     p = Params()
     p.phys = phys if phys is not None else physics()
     p.kernel = kernel
     p.leaf_cap = leaf_cap
     p.precision = precision
     p.cm_level = cm_level
+    p.rebuild_every = rebuild_every
     return p
 
 
@@ -359,8 +360,9 @@ class Sim:
     """Owns one crk_sim handle (create / load / forces / step / destroy)."""
 
     def __init__(self, phys: Physics | None = None, leaf_cap=64, precision=CRK_MIXED, cm_level=0,
-                 stream=None):
-        self.handle = crk_create(params(phys, leaf_cap, precision, cm_level), stream)
+                 stream=None, rebuild_every=1):
+        self.handle = crk_create(params(phys, leaf_cap, precision, cm_level, rebuild_every=rebuild_every),
+                                 stream)
 
     def load(self, box):
         crk_load(self.handle, box.pos, box.vel, box.mass, box.u, box.h, box.species)

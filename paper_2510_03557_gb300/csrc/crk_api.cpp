@@ -302,30 +302,41 @@ int build_tree(crk_sim *s)
     const int64_t n = s->n;
     cudaStream_t st = s->st;
     mark(s, PH_TREE, 0);
-    launch_morton_keys(s->sa, s->boxes_d.as<BoxDev>(), n, s->slot_bits, s->keys.as<uint64_t>(),
-                       s->vals.as<uint32_t>(), st);
-    uint64_t *ko;
-    uint32_t *vo;
     uint32_t *tmp = s->scan_tmp.as<uint32_t>();
-    radix_sort_u64(s->keys.as<uint64_t>(), s->vals.as<uint32_t>(), s->keys_alt.as<uint64_t>(),
-                   s->vals_alt.as<uint32_t>(), n, s->counts.as<uint32_t>(), tmp, 0, 64, st, &ko, &vo);
-    // particles of removed pool slots carry the largest key and sort last
-    const int64_t nlive = n - s->n_dead;
     uint32_t *sc = s->scalars.as<uint32_t>();
-    launch_leaf_flags(ko, s->slot_bits, s->boxes_d.as<BoxDev>(), nlive, s->cap, s->flags.as<uint32_t>(), st);
-    scan_exclusive_u32(s->flags.as<uint32_t>(), s->flag_scan.as<uint32_t>(), nlive, sc + 0, tmp, st);
-    CK(cudaMemcpyAsync(s->host_scalars, sc, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    s->nleaf = (int)s->host_scalars[0];
-    launch_leaf_setup(s->flags.as<uint32_t>(), s->flag_scan.as<uint32_t>(), nlive, s->nleaf, s->lv, st);
-    // k-d order inside every leaf (on the unsorted state through the sort's
-    // permutation), then one gather of the whole state
-    launch_leaf_kd_order(s->sa, s->lv, s->nleaf, vo, st);
-    launch_permute(s->sa, s->sb, vo, n, st);
-    std::swap(s->sa, s->sb);
-    for (int k = 0; k < 16; ++k) std::swap(s->stA[k], s->stB[k]);
-    s->n = nlive;
-    s->n_dead = 0;
+    // Between rebuilds the leaves keep their particles and their boxes grow
+    // with the particles (paper Sec. IV-B1): no sort, only new bounds, node
+    // boxes and pair lists.  Added or removed particles force a rebuild.
+    const int every = std::max(s->prm.rebuild_every, 1);
+    const bool reuse = s->tree_valid && s->n_dead == 0 && s->since_rebuild + 1 < every;
+    if (reuse) {
+        ++s->since_rebuild;
+    } else {
+        launch_morton_keys(s->sa, s->boxes_d.as<BoxDev>(), n, s->slot_bits, s->keys.as<uint64_t>(),
+                           s->vals.as<uint32_t>(), st);
+        uint64_t *ko;
+        uint32_t *vo;
+        radix_sort_u64(s->keys.as<uint64_t>(), s->vals.as<uint32_t>(), s->keys_alt.as<uint64_t>(),
+                       s->vals_alt.as<uint32_t>(), n, s->counts.as<uint32_t>(), tmp, 0, 64, st, &ko, &vo);
+        // particles of removed pool slots carry the largest key and sort last
+        const int64_t nlive = n - s->n_dead;
+        launch_leaf_flags(ko, s->slot_bits, s->boxes_d.as<BoxDev>(), nlive, s->cap, s->flags.as<uint32_t>(), st);
+        scan_exclusive_u32(s->flags.as<uint32_t>(), s->flag_scan.as<uint32_t>(), nlive, sc + 0, tmp, st);
+        CK(cudaMemcpyAsync(s->host_scalars, sc, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        s->nleaf = (int)s->host_scalars[0];
+        launch_leaf_setup(s->flags.as<uint32_t>(), s->flag_scan.as<uint32_t>(), nlive, s->nleaf, s->lv, st);
+        // k-d order inside every leaf (on the unsorted state through the sort's
+        // permutation), then one gather of the whole state
+        launch_leaf_kd_order(s->sa, s->lv, s->nleaf, vo, st);
+        launch_permute(s->sa, s->sb, vo, n, st);
+        std::swap(s->sa, s->sb);
+        for (int k = 0; k < 16; ++k) std::swap(s->stA[k], s->stB[k]);
+        s->n = nlive;
+        s->n_dead = 0;
+        s->since_rebuild = 0;
+        s->tree_valid = true;
+    }
     launch_leaf_bounds(s->sa, s->boxes_d.as<BoxDev>(), s->lv, s->nleaf, s->mixed ? 1 : 0, s->pm.p,
                        s->nd, st);
     mark(s, PH_TREE, 1);
@@ -491,6 +502,7 @@ int load_impl(crk_sim *s, int nbox, const int64_t *counts, const crk_physics *ph
     CK(cudaSetDevice(s->device));
     RET(reserve(s, n));
     s->n = n;
+    s->tree_valid = false;
     s->nbox = nbox;
     int sb = 0;
     while ((1 << sb) < nbox) ++sb;
@@ -548,6 +560,7 @@ int load_impl(crk_sim *s, int nbox, const int64_t *counts, const crk_physics *ph
     int rc = read_error(s);
     if (rc != CRK_OK) {
         s->n = 0;
+        s->tree_valid = false;
         return rc;
     }
     s->have_forces = false;
@@ -583,6 +596,7 @@ extern "C" int crk_create(const crk_params *params, void *cuda_stream, crk_sim *
         return fail(CRK_EINVAL, "precision must be CRK_FP64 or CRK_MIXED");
     if (params->kernel != CRK_WENDLAND_C4) return fail(CRK_EINVAL, "unsupported kernel");
     if (params->cm_level < 0 || params->cm_level > 10) return fail(CRK_EINVAL, "cm_level in [0, 10]");
+    if (params->rebuild_every < 0) return fail(CRK_EINVAL, "rebuild_every must be >= 0");
     crk_sim *s = new crk_sim();
     s->prm = *params;
     s->mixed = params->precision == CRK_MIXED;
@@ -777,6 +791,7 @@ extern "C" int crk_autotune(crk_sim *s, const int *caps, int ncaps, int *best_ca
     int rc = CRK_OK;
     for (int k = 0; k < ncaps && rc == CRK_OK; ++k) {
         s->cap = caps[k];
+        s->tree_valid = false;  // leaves of another capacity
         rc = run_step(s, nullptr, false);  // warm-up: buffers grow to this layout
         if (rc != CRK_OK) break;
         cudaEventRecord(e0, s->st);
@@ -798,6 +813,7 @@ extern "C" int crk_autotune(crk_sim *s, const int *caps, int ncaps, int *best_ca
     cudaEventDestroy(e1);
     if (rc != CRK_OK) return rc;
     s->cap = caps[best];
+    s->tree_valid = false;
     if (best_cap) *best_cap = caps[best];
     // the stored accelerations are those of the chosen capacity
     return run_step(s, nullptr, false);
@@ -916,6 +932,7 @@ int pool_init(crk_sim *s, int max_slots)
     s->boxes.assign((size_t)max_slots + 1, box_dev(dummy));
     for (BoxDev &b : s->boxes) b.active = 0;
     s->n = 0;
+    s->tree_valid = false;
     s->n_dead = 0;
     RET(reserve(s, 4096));
     RET(upload_boxes(s));
@@ -990,6 +1007,7 @@ int pool_add(crk_sim *s, int slot, const crk_physics &phys, int64_t n, const dou
         return rc;
     }
     s->n = n0 + n;
+    s->tree_valid = false;
     return CRK_OK;
 }
 

@@ -473,17 +473,18 @@ __device__ __forceinline__ Group load_group(const Leaves &lv, const uint2 *group
 
 // Position of a target relative to its leaf centre, in FP32 (for the warp box).
 template <typename R>
-__device__ __forceinline__ void rel_pos(const Vec4<R> &ri, const Leaves &lv, int I, float &x, float &y,
-                                        float &z)
+__device__ __forceinline__ void rel_pos(const Vec4<R> &ri, const Leaves &lv, int I, double L, float &x,
+                                        float &y, float &z)
 {
     if (Real<R>::mixed) {
         x = (float)ri.x;
         y = (float)ri.y;
         z = (float)ri.z;
     } else {
-        x = (float)((double)ri.x - lv.cx[I]);
-        y = (float)((double)ri.y - lv.cy[I]);
-        z = (float)((double)ri.z - lv.cz[I]);
+        // absolute FP64 records; the leaf centre may lie past a periodic face
+        x = (float)wrap1((double)ri.x - lv.cx[I], L, 0.5 * L);
+        y = (float)wrap1((double)ri.y - lv.cy[I], L, 0.5 * L);
+        z = (float)wrap1((double)ri.z - lv.cz[I], L, 0.5 * L);
     }
 }
 
@@ -663,7 +664,7 @@ __global__ void __launch_bounds__(kBlock) hlist_count_k(PassArgs a)
     const R4 ri = reinterpret_cast<const R4 *>(a.pm)[i];
     const HTarget<R> ht = hydro_target<R>(a.s, i);
     float px, py, pz;
-    rel_pos(ri, a.lv, I, px, py, pz);
+    rel_pos(ri, a.lv, I, Ld, px, py, pz);
     const WarpBox wb = warp_box(px, py, pz, G.act);
     const float Hw = warp_max(G.act ? (float)ht.H : 0.f);
     uint32_t cnt = 0;
@@ -711,7 +712,7 @@ __global__ void __launch_bounds__(kBlock) hlist_fill_k(PassArgs a)
     const R4 ri = reinterpret_cast<const R4 *>(a.pm)[i];
     const HTarget<R> ht = hydro_target<R>(a.s, i);
     float px, py, pz;
-    rel_pos(ri, a.lv, I, px, py, pz);
+    rel_pos(ri, a.lv, I, Ld, px, py, pz);
     const WarpBox wb = warp_box(px, py, pz, G.act);
     const float Hw = warp_max(G.act ? (float)ht.H : 0.f);
     ring.e0 = (size_t)a.nl_row[gi] * 32u + lane;
@@ -1329,7 +1330,7 @@ __global__ void __launch_bounds__(kBlock) gravity_k(PassArgs a)
     const R inv2rs = (R)(0.5 / bx.r_split);
     const R Gc = (R)bx.G;
     float px, py, pz;
-    rel_pos(ri, a.lv, I, px, py, pz);
+    rel_pos(ri, a.lv, I, Ld, px, py, pz);
     const WarpBox wb = warp_box(px, py, pz, G.act);
     const float Rc = (float)bx.r_cut * 1.0001f + 1e-6f * (float)Ld;
     R ax = 0, ay = 0, az = 0;

@@ -67,6 +67,8 @@ struct crk_sim {
     bool have_forces = false;
     int64_t n_dead = 0;      // particles of removed pool slots, sorted last and dropped next step
     int64_t cap_n = 0;       // particles the per-particle buffers hold
+    bool tree_valid = false; // leaves describe the current particle set (order and membership)
+    int since_rebuild = 0;   // steps since the last sort
 
     // device memory
     DBuf boxes_d;

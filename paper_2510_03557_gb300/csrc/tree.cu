@@ -311,30 +311,57 @@ __device__ __forceinline__ double wmax(double v)
 // leaf's largest kernel support, the level-0 node, and the position-mass
 // records of its particles (leaf-relative FP32 in the mixed form, absolute
 // FP64 in the plain form).
+// Offset of a coordinate from a leaf's reference particle, wrapped once: a
+// leaf whose particles drifted across a periodic face keeps a compact box
+// (its box may then reach past [0, L); every user wraps differences).
+__device__ __forceinline__ double leaf_offset(double x, double ref, double L)
+{
+    double d = x - ref;
+    if (d >= 0.5 * L) d -= L;
+    else if (d < -0.5 * L) d += L;
+    return d;
+}
+
 template <int MIXED>
-__global__ void leaf_bounds_k(State s, Leaves lv, int nleaf, void *pm, Nodes nd)
+__global__ void leaf_bounds_k(State s, const BoxDev *__restrict__ boxes, Leaves lv, int nleaf, void *pm,
+                              Nodes nd)
 {
     const int w = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const uint32_t lane = lane_id();
     if (w >= nleaf) return;
     const uint32_t s0 = lv.start[w], c = lv.count[w];
+    const double Lb = boxes[s.slot[s0]].L;
+    // positions relative to the leaf's first particle (leaves built from a
+    // Morton cell never straddle a face; leaves kept between rebuilds may);
+    // particle 32 ch + lane of the leaf is this lane's ch-th (c <= 128)
+    const double ref[3] = {s.x[s0], s.y[s0], s.z[s0]};
+    double d[kChunks][3];
     double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
     double hm = 0.0;
-    for (uint32_t t = lane; t < c; t += 32) {
-        uint32_t i = s0 + t;
-        double p[3] = {s.x[i], s.y[i], s.z[i]};
 #pragma unroll
-        for (int a = 0; a < 3; ++a) { lo[a] = fmin(lo[a], p[a]); hi[a] = fmax(hi[a], p[a]); }
-        if (s.species[i] == CRK_GAS) hm = fmax(hm, 2.0 * s.h[i]);
+    for (int ch = 0; ch < kChunks; ++ch) {
+        const uint32_t t = 32u * ch + lane;
+        if (t < c) {
+            const uint32_t i = s0 + t;
+            d[ch][0] = leaf_offset(s.x[i], ref[0], Lb);
+            d[ch][1] = leaf_offset(s.y[i], ref[1], Lb);
+            d[ch][2] = leaf_offset(s.z[i], ref[2], Lb);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) { lo[a] = fmin(lo[a], d[ch][a]); hi[a] = fmax(hi[a], d[ch][a]); }
+            if (s.species[i] == CRK_GAS) hm = fmax(hm, 2.0 * s.h[i]);
+        } else {
+            d[ch][0] = d[ch][1] = d[ch][2] = 0.0;
+        }
     }
-    double cen[3];
+    double cen[3], mid[3];
     float ext[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         lo[a] = wmin(lo[a]);
         hi[a] = wmax(hi[a]);
-        cen[a] = 0.5 * (lo[a] + hi[a]);
-        ext[a] = __double2float_ru(fmax(hi[a] - cen[a], cen[a] - lo[a]));
+        mid[a] = 0.5 * (lo[a] + hi[a]);          // centre relative to the reference
+        cen[a] = ref[a] + mid[a];
+        ext[a] = __double2float_ru(fmax(hi[a] - mid[a], mid[a] - lo[a]));
     }
     hm = wmax(hm);
     if (lane == 0) {
@@ -343,10 +370,10 @@ __global__ void leaf_bounds_k(State s, Leaves lv, int nleaf, void *pm, Nodes nd)
         lv.hmax[w] = __double2float_ru(hm);
         lv.slot[w] = s.slot[s0];
         lv.species[w] = s.species[s0];
-        nd.lox[w] = __double2float_rd(lo[0]); nd.loy[w] = __double2float_rd(lo[1]);
-        nd.loz[w] = __double2float_rd(lo[2]);
-        nd.hix[w] = __double2float_ru(hi[0]); nd.hiy[w] = __double2float_ru(hi[1]);
-        nd.hiz[w] = __double2float_ru(hi[2]);
+        nd.lox[w] = __double2float_rd(ref[0] + lo[0]); nd.loy[w] = __double2float_rd(ref[1] + lo[1]);
+        nd.loz[w] = __double2float_rd(ref[2] + lo[2]);
+        nd.hix[w] = __double2float_ru(ref[0] + hi[0]); nd.hiy[w] = __double2float_ru(ref[1] + hi[1]);
+        nd.hiz[w] = __double2float_ru(ref[2] + hi[2]);
         nd.hmax[w] = __double2float_ru(hm);
         nd.slot[w] = (int32_t)s.slot[s0];
     }
@@ -355,10 +382,8 @@ __global__ void leaf_bounds_k(State s, Leaves lv, int nleaf, void *pm, Nodes nd)
     // inverted box that is never in range.
 #pragma unroll
     for (int ch = 0; ch < kChunks; ++ch) {
-        const uint32_t t = 32u * ch + lane;
-        const bool in = t < c;
-        const uint32_t i = s0 + (in ? t : 0u);
-        const double px = s.x[i] - cen[0], py = s.y[i] - cen[1], pz = s.z[i] - cen[2];
+        const bool in = 32u * ch + lane < c;
+        const double px = d[ch][0] - mid[0], py = d[ch][1] - mid[1], pz = d[ch][2] - mid[2];
         const double lx = wmin(in ? px : DBL_MAX), hx = wmax(in ? px : -DBL_MAX);
         const double ly = wmin(in ? py : DBL_MAX), hy = wmax(in ? py : -DBL_MAX);
         const double lz = wmin(in ? pz : DBL_MAX), hz = wmax(in ? pz : -DBL_MAX);
@@ -371,20 +396,20 @@ __global__ void leaf_bounds_k(State s, Leaves lv, int nleaf, void *pm, Nodes nd)
                 any ? make_float4(__double2float_ru(hx), __double2float_ru(hy), __double2float_ru(hz), 0.f)
                     : make_float4(-1e30f, -1e30f, -1e30f, 0.f);
         }
-    }
-    for (uint32_t t = lane; t < c; t += 32) {
-        uint32_t i = s0 + t;
-        if (MIXED) {
-            float4 r;
-            r.x = (float)(s.x[i] - cen[0]);
-            r.y = (float)(s.y[i] - cen[1]);
-            r.z = (float)(s.z[i] - cen[2]);
-            r.w = (float)s.m[i];
-            reinterpret_cast<float4 *>(pm)[i] = r;
-        } else {
-            Vec4<double> r;
-            r.x = s.x[i]; r.y = s.y[i]; r.z = s.z[i]; r.w = s.m[i];
-            reinterpret_cast<Vec4<double> *>(pm)[i] = r;
+        if (in) {
+            const uint32_t i = s0 + 32u * ch + lane;
+            if (MIXED) {
+                float4 r;
+                r.x = (float)px;
+                r.y = (float)py;
+                r.z = (float)pz;
+                r.w = (float)s.m[i];
+                reinterpret_cast<float4 *>(pm)[i] = r;
+            } else {
+                Vec4<double> r;
+                r.x = s.x[i]; r.y = s.y[i]; r.z = s.z[i]; r.w = s.m[i];
+                reinterpret_cast<Vec4<double> *>(pm)[i] = r;
+            }
         }
     }
 }
@@ -715,11 +740,10 @@ void launch_leaf_setup(const uint32_t *flags, const uint32_t *scan, int64_t n, i
 void launch_leaf_bounds(const State &s, const BoxDev *boxes, Leaves lv, int nleaf, int mixed,
                         void *pm, Nodes nd, cudaStream_t st)
 {
-    (void)boxes;
     if (nleaf <= 0) return;
     unsigned g = grid_for((int64_t)nleaf * 32, kT);
-    if (mixed) leaf_bounds_k<1><<<g, kT, 0, st>>>(s, lv, nleaf, pm, nd);
-    else leaf_bounds_k<0><<<g, kT, 0, st>>>(s, lv, nleaf, pm, nd);
+    if (mixed) leaf_bounds_k<1><<<g, kT, 0, st>>>(s, boxes, lv, nleaf, pm, nd);
+    else leaf_bounds_k<0><<<g, kT, 0, st>>>(s, boxes, lv, nleaf, pm, nd);
     note_launches(1);
 }
 

@@ -310,6 +310,35 @@ def test_batched_boxes_match_each_box_alone(crk):
             compare(part, ref, counts, precision, label=f"box {b}")
 
 
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_leaves_kept_between_rebuilds_match_the_oracle(crk, precision):
+    """Sorting into leaves every 4th step only (the boxes grow in between):
+    6 KDK steps match the oracle's KDK; and a force evaluation on leaves
+    built 3 steps earlier gives the oracle's neighbour sets."""
+    box = wl.gaussian_field_box(16, seed=31)
+    op = oracle_params(box)
+    steps = 6
+    ref = oracle.kdk(box.pos, box.vel, box.mass, box.u, box.h, box.species, op, box.dt, steps)
+    with crk.Sim(crk.box_physics(box), leaf_cap=64, precision=precision, rebuild_every=4) as sim:
+        sim.load(box)
+        sim.step(box.dt, steps)
+        pos, vel, u = sim.state()
+    tol = TOL[precision]
+    assert rel_l2(vel, ref["vel"]) <= tol
+    assert rel_l2(u, ref["u"]) <= tol
+    with crk.Sim(crk.box_physics(box), leaf_cap=64, precision=precision, rebuild_every=10) as sim:
+        sim.load(box)
+        sim.step(box.dt, 3)
+        out = sim.forces(counts=True)  # leaves of the initial evaluation, boxes grown
+        pos, vel, u = sim.state()
+    moved = box_dict(box)
+    moved.update(pos=pos, vel=vel, u=u)
+    cref = oracle_counts(moved, op)
+    for name in ("nbr", "grav"):
+        assert np.array_equal(out[name + "_count"], cref[name][0]), name
+        assert np.array_equal(out[name + "_hash"], cref[name][1]), name
+
+
 def test_autotune_keeps_the_fastest_capacity_and_the_forces(crk):
     box = wl.gaussian_field_box(16, seed=21)
     op = oracle_params(box)
