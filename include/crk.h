@@ -45,6 +45,7 @@ extern "C" {
 #define CRK_EPENDING (-6)   /* crk_poll: the job has not finished yet */
 #define CRK_ETIMEOUT (-7)   /* a bounded wait ran out */
 #define CRK_ENOTFOUND (-8)  /* crk_poll: unknown or already collected ticket */
+#define CRK_ECANCELED (-9)  /* the job was cancelled (crk_service_cancel) */
 
 /* Precision of the pair passes */
 #define CRK_FP64 0          /* every operation in FP64 (the plain form) */
@@ -225,7 +226,9 @@ typedef struct {
     int precision;             /* CRK_MIXED or CRK_FP64 */
     int leaf_cap;              /* 32, 64 or 128 */
     int device;                /* CUDA device ordinal */
-    int reserved[4];
+    int snapshot_every;        /* copy every resident job's state to host memory after every
+                                  this many of its steps (0: never); see crk_service_snapshot */
+    int reserved[3];
 } crk_service_params;
 
 typedef struct {
@@ -234,9 +237,19 @@ typedef struct {
     const double *pos, *vel, *mass, *u, *h;   /* host arrays, copied by crk_submit */
     const uint8_t *species;
     double dt;                 /* KDK step */
-    int nsteps;                /* KDK steps to run */
-    int reserved;
+    int nsteps;                /* KDK steps to run in total */
+    int steps_done;            /* resuming from a snapshot: steps already run, else 0 */
+    const double *acc;         /* resuming: accelerations of the snapshot (3n), else NULL */
+    const double *dudt;        /* resuming: du/dt of the snapshot (n), else NULL */
 } crk_job;
+
+typedef struct {
+    double *pos, *vel, *u;     /* caller-owned host buffers (3n, 3n, n) */
+    double *acc, *dudt;        /* caller-owned host buffers (3n, n) */
+    int64_t n;                 /* written: particles */
+    int steps_done;            /* written: KDK steps the snapshot is taken after */
+    int reserved;
+} crk_job_snapshot;
 
 typedef struct {
     double *pos, *vel, *u;     /* caller-owned host buffers (3n, 3n, n) or NULL */
@@ -261,6 +274,22 @@ int crk_submit(crk_service *service, const crk_job *job, uint64_t *ticket);
 int crk_poll(crk_service *service, uint64_t ticket, crk_job_result *result, int64_t timeout_us);
 /* Stops the service thread after the resident jobs finish and frees it. */
 int crk_service_destroy(crk_service *service);
+/* Checkpointing (the analogue of the paper's checkpoint/restart tier,
+ * Sec. IV-B4, for resident jobs): with snapshot_every = K > 0 the service
+ * copies a job's full dynamic state (positions, velocities, u and the
+ * accelerations and du/dt of its last force evaluation, in the job's particle
+ * order) to host memory after every K of its steps; the device-to-host copy
+ * runs on a side stream beside the next step.  crk_service_snapshot writes the
+ * latest complete snapshot of a resident, finished or cancelled job whose
+ * ticket has not been collected; CRK_EPENDING if none was taken yet.  A job
+ * submitted with that state (steps_done, acc, dudt) skips its initial force
+ * evaluation and continues exactly where the snapshot was taken: its result is
+ * bit-identical to a run without interruption.  Thread-safe. */
+int crk_service_snapshot(crk_service *service, uint64_t ticket, crk_job_snapshot *out);
+/* Cancels every queued and resident job at the next step boundary (they end
+ * with CRK_ECANCELED; their latest snapshots stay readable until collected).
+ * The service keeps running and accepts new jobs.  Thread-safe. */
+int crk_service_cancel(crk_service *service);
 
 /* ------------------------------------------------------------------ */
 /* Allocation-free neighbour sets.                                      */

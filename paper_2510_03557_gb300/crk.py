@@ -24,6 +24,7 @@ CRK_ESINGULAR = -5
 CRK_EPENDING = -6
 CRK_ETIMEOUT = -7
 CRK_ENOTFOUND = -8
+CRK_ECANCELED = -9
 CRK_FP64 = 0
 CRK_MIXED = 1
 CRK_WENDLAND_C4 = 0
@@ -36,6 +37,7 @@ CRK_GAS = 1
 ABI = ("crk_create", "crk_load", "crk_load_boxes", "crk_forces", "crk_step", "crk_step_boxes",
        "crk_get_state", "crk_set_state", "crk_get_sums", "crk_get_size", "crk_set_timing", "crk_get_timings",
        "crk_destroy", "crk_autotune", "crk_service_create", "crk_submit", "crk_poll", "crk_service_destroy",
+       "crk_service_snapshot", "crk_service_cancel",
        "crk_neighbours_noalloc", "crk_last_error")
 CRK_NOALLOC_MAX_N = 262144
 
@@ -77,14 +79,21 @@ class Timings(ctypes.Structure):
 class ServiceParams(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int),
                 ("precision", ctypes.c_int), ("leaf_cap", ctypes.c_int), ("device", ctypes.c_int),
-                ("reserved", ctypes.c_int * 4)]
+                ("snapshot_every", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class Job(ctypes.Structure):
     _fields_ = [("phys", Physics), ("n", ctypes.c_int64), ("pos", ctypes.c_void_p),
                 ("vel", ctypes.c_void_p), ("mass", ctypes.c_void_p), ("u", ctypes.c_void_p),
                 ("h", ctypes.c_void_p), ("species", ctypes.c_void_p), ("dt", ctypes.c_double),
-                ("nsteps", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("nsteps", ctypes.c_int), ("steps_done", ctypes.c_int), ("acc", ctypes.c_void_p),
+                ("dudt", ctypes.c_void_p)]
+
+
+class JobSnapshot(ctypes.Structure):
+    _fields_ = [("pos", ctypes.c_void_p), ("vel", ctypes.c_void_p), ("u", ctypes.c_void_p),
+                ("acc", ctypes.c_void_p), ("dudt", ctypes.c_void_p), ("n", ctypes.c_int64),
+                ("steps_done", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 class JobResult(ctypes.Structure):
@@ -289,19 +298,23 @@ def crk_autotune(sim, caps=(32, 64, 128)):
 
 
 def crk_service_create(hbm_budget_bytes: int, max_slots: int, precision=CRK_MIXED, leaf_cap=64,
-                       device=0) -> ctypes.c_void_p:
+                       device=0, snapshot_every=0) -> ctypes.c_void_p:
     p = ServiceParams()
     p.hbm_budget_bytes = int(hbm_budget_bytes)
     p.max_slots = max_slots
     p.precision = precision
     p.leaf_cap = leaf_cap
     p.device = device
+    p.snapshot_every = snapshot_every
     h = ctypes.c_void_p()
     _check(lib().crk_service_create(ctypes.byref(p), ctypes.byref(h)))
     return h
 
 
-def crk_submit(svc, phys: Physics, pos, vel, mass, u, h, species, dt: float, nsteps: int) -> int:
+def crk_submit(svc, phys: Physics, pos, vel, mass, u, h, species, dt: float, nsteps: int,
+               resume=None) -> int:
+    """Queues a job; `resume` (a snapshot dict from crk_service_snapshot, with
+    the job's original mass, h and species) continues it from that state."""
     j = Job()
     j.phys = phys
     arrs = [np.ascontiguousarray(pos, np.float64), np.ascontiguousarray(vel, np.float64),
@@ -310,6 +323,13 @@ def crk_submit(svc, phys: Physics, pos, vel, mass, u, h, species, dt: float, nst
     j.n = arrs[2].shape[0]
     for name, a in zip(("pos", "vel", "mass", "u", "h", "species"), arrs):
         setattr(j, name, a.ctypes.data_as(ctypes.c_void_p))
+    if resume is not None:
+        acc = np.ascontiguousarray(resume["acc"], np.float64)
+        dudt = np.ascontiguousarray(resume["dudt"], np.float64)
+        arrs += [acc, dudt]
+        j.acc = acc.ctypes.data_as(ctypes.c_void_p)
+        j.dudt = dudt.ctypes.data_as(ctypes.c_void_p)
+        j.steps_done = int(resume["steps_done"])
     j.dt = dt
     j.nsteps = nsteps
     t = ctypes.c_uint64()
@@ -336,6 +356,25 @@ def crk_poll(svc, ticket: int, n: int, timeout_us: int = -1):
 
 def crk_service_destroy(svc):
     _check(lib().crk_service_destroy(svc))
+
+
+def crk_service_snapshot(svc, ticket: int, n: int):
+    """The job's latest complete snapshot (dict), or None if none was taken yet."""
+    s = JobSnapshot()
+    out = dict(pos=np.zeros((n, 3)), vel=np.zeros((n, 3)), u=np.zeros(n), acc=np.zeros((n, 3)),
+               dudt=np.zeros(n))
+    for k, v in out.items():
+        setattr(s, k, v.ctypes.data_as(ctypes.c_void_p))
+    rc = lib().crk_service_snapshot(svc, ctypes.c_uint64(ticket), ctypes.byref(s))
+    if rc == CRK_EPENDING:
+        return None
+    _check(rc)
+    out["steps_done"] = int(s.steps_done)
+    return out
+
+
+def crk_service_cancel(svc):
+    _check(lib().crk_service_cancel(svc))
 
 
 def crk_neighbours_noalloc(n: int, pos, h, species, box: float, count, hash_, stream=None) -> int:

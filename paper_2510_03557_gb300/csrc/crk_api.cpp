@@ -965,7 +965,7 @@ static int pool_grow(crk_sim *s, int64_t need)
 
 int pool_add(crk_sim *s, int slot, const crk_physics &phys, int64_t n, const double *pos,
              const double *vel, const double *mass, const double *u, const double *h,
-             const uint8_t *species)
+             const uint8_t *species, const double *acc, const double *dudt)
 {
     if (slot < 0 || slot >= s->nbox) return fail(CRK_EINVAL, "bad slot %d", slot);
     RET(check_physics(phys));
@@ -982,10 +982,11 @@ int pool_add(crk_sim *s, int slot, const crk_physics &phys, int64_t n, const dou
     s->boxes[slot] = b;
     RET(upload_boxes(s));
     const size_t nn = (size_t)n;
-    RET(s->in_stage.ensure(nn * 9 * sizeof(double) + nn * 5 + 64));
+    RET(s->in_stage.ensure(nn * 13 * sizeof(double) + nn * 5 + 64));
     double *d_pos = s->in_stage.as<double>();
     double *d_vel = d_pos + 3 * nn, *d_mass = d_vel + 3 * nn, *d_u = d_mass + nn, *d_h = d_u + nn;
-    uint32_t *d_slot = (uint32_t *)(d_h + nn);
+    double *d_acc = d_h + nn, *d_du = d_acc + 3 * nn;
+    uint32_t *d_slot = (uint32_t *)(d_du + nn);
     uint8_t *d_sp = (uint8_t *)(d_slot + nn);
     std::vector<uint32_t> slot_of(nn, (uint32_t)slot);
     CK(cudaMemcpyAsync(d_pos, pos, nn * 24, cudaMemcpyHostToDevice, s->st));
@@ -997,6 +998,11 @@ int pool_add(crk_sim *s, int slot, const crk_physics &phys, int64_t n, const dou
     CK(cudaMemcpyAsync(d_slot, slot_of.data(), nn * 4, cudaMemcpyHostToDevice, s->st));
     const State part = shifted(s->sa, n0);
     launch_load_state(part, n, d_pos, d_vel, d_mass, d_u, d_h, d_sp, d_slot, s->st);
+    if (acc && dudt) {
+        CK(cudaMemcpyAsync(d_acc, acc, nn * 24, cudaMemcpyHostToDevice, s->st));
+        CK(cudaMemcpyAsync(d_du, dudt, nn * 8, cudaMemcpyHostToDevice, s->st));
+        launch_set_forces(part, n, d_acc, d_du, s->st);
+    }
     RET(reset_error(s));
     launch_validate(part, s->boxes_d.as<BoxDev>(), n, s->err.as<int>(), s->st);
     CK(cudaGetLastError());
@@ -1017,11 +1023,21 @@ int pool_extract(crk_sim *s, int slot, int64_t n, double *pos, double *vel, doub
     const size_t nn = (size_t)n;
     RET(s->staging.ensure(nn * 7 * 8 + 256));
     double *dp = s->staging.as<double>(), *dv = dp + 3 * nn, *du = dv + 3 * nn;
-    launch_extract_slot(s->sa, s->n, (uint32_t)slot, n, dp, dv, du, s->st);
+    launch_extract_slot(s->sa, s->n, (uint32_t)slot, n, dp, dv, du, nullptr, nullptr, s->st);
     if (pos) CK(cudaMemcpyAsync(pos, dp, nn * 24, cudaMemcpyDeviceToHost, s->st));
     if (vel) CK(cudaMemcpyAsync(vel, dv, nn * 24, cudaMemcpyDeviceToHost, s->st));
     if (u) CK(cudaMemcpyAsync(u, du, nn * 8, cudaMemcpyDeviceToHost, s->st));
     CK(cudaStreamSynchronize(s->st));
+    return CRK_OK;
+}
+
+int pool_snapshot(crk_sim *s, int slot, int64_t n, double *dev)
+{
+    CK(cudaSetDevice(s->device));
+    const size_t nn = (size_t)n;
+    double *dp = dev, *dv = dp + 3 * nn, *du = dv + 3 * nn, *da = du + nn, *dd = da + 3 * nn;
+    launch_extract_slot(s->sa, s->n, (uint32_t)slot, n, dp, dv, du, da, dd, s->st);
+    CK(cudaGetLastError());
     return CRK_OK;
 }
 

@@ -169,7 +169,8 @@ void launch_validate(const State &s, const BoxDev *boxes, int64_t n, int *err, c
 void launch_set_state(const State &s, int64_t n, const double *pos, const double *vel,
                       const double *u, cudaStream_t st);
 void launch_extract_slot(const State &s, int64_t n, uint32_t slot, int64_t n_job, double *pos,
-                         double *vel, double *u, cudaStream_t st);
+                         double *vel, double *u, double *acc, double *du, cudaStream_t st);
+void launch_set_forces(const State &s, int64_t n, const double *acc, const double *du, cudaStream_t st);
 void launch_retire_slot(const State &s, int64_t n, uint32_t from, uint32_t to, cudaStream_t st);
 void launch_load_state(const State &s, int64_t n, const double *pos, const double *vel,
                        const double *mass, const double *u, const double *h,

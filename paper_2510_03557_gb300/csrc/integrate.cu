@@ -300,12 +300,18 @@ __global__ void set_state_k(State s, int64_t n, const double *pos, const double 
 // Copies the state of one box slot out in its own load order (id = index
 // within the box).
 __global__ void extract_slot_k(State s, int64_t n, uint32_t slot, int64_t n_job, double *pos,
-                               double *vel, double *u)
+                               double *vel, double *u, double *acc, double *du)
 {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n || s.slot[k] != slot) return;
     const int64_t o = s.id[k];
     if (o >= n_job) return;  // not one of the job's particles
+    if (acc) {
+        acc[3 * o] = s.ax[k];
+        acc[3 * o + 1] = s.ay[k];
+        acc[3 * o + 2] = s.az[k];
+    }
+    if (du) du[o] = s.du[k];
     pos[3 * o] = s.x[k];
     pos[3 * o + 1] = s.y[k];
     pos[3 * o + 2] = s.z[k];
@@ -313,6 +319,18 @@ __global__ void extract_slot_k(State s, int64_t n, uint32_t slot, int64_t n_job,
     vel[3 * o + 1] = s.vy[k];
     vel[3 * o + 2] = s.vz[k];
     u[o] = s.species[k] == CRK_GAS ? s.u[k] : 0.0;
+}
+
+// The accelerations and du/dt of a force evaluation, set from the caller
+// (a job resumed from a snapshot continues with the forces it had).
+__global__ void set_forces_k(State s, int64_t n, const double *acc, const double *du)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    s.ax[k] = acc[3 * k];
+    s.ay[k] = acc[3 * k + 1];
+    s.az[k] = acc[3 * k + 2];
+    s.du[k] = s.species[k] == CRK_GAS ? du[k] : 0.0;
 }
 
 // Moves the particles of a removed slot to the retired slot, whose box stays
@@ -325,6 +343,13 @@ __global__ void retire_slot_k(uint32_t *slot_of, int64_t n, uint32_t from, uint3
 }
 
 }  // namespace
+
+void launch_set_forces(const State &s, int64_t n, const double *acc, const double *du, cudaStream_t st)
+{
+    if (n <= 0) return;
+    set_forces_k<<<nblocks(n), kT, 0, st>>>(s, n, acc, du);
+    note_launches(1);
+}
 
 void launch_retire_slot(const State &s, int64_t n, uint32_t from, uint32_t to, cudaStream_t st)
 {
@@ -342,10 +367,10 @@ void launch_set_state(const State &s, int64_t n, const double *pos, const double
 }
 
 void launch_extract_slot(const State &s, int64_t n, uint32_t slot, int64_t n_job, double *pos,
-                         double *vel, double *u, cudaStream_t st)
+                         double *vel, double *u, double *acc, double *du, cudaStream_t st)
 {
     if (n <= 0) return;
-    extract_slot_k<<<nblocks(n), kT, 0, st>>>(s, n, slot, n_job, pos, vel, u);
+    extract_slot_k<<<nblocks(n), kT, 0, st>>>(s, n, slot, n_job, pos, vel, u, acc, du);
     note_launches(1);
 }
 

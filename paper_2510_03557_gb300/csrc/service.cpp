@@ -29,17 +29,33 @@ struct Job {
     crk_physics phys{};
     int64_t n = 0;
     std::vector<double> pos, vel, mass, u, h;
+    std::vector<double> acc, du;  // forces to resume with (empty: a fresh job)
     std::vector<uint8_t> sp;
     double dt = 0.0;
     int nsteps = 0;
     int steps_done = 0;
     bool init_done = false;
+    bool cancel = false;
     int slot = -1;
     size_t bytes = 0;
     int status = CRK_OK;
     std::string msg;
     bool done = false;
     clk::time_point t_submit, t_admit, t_done;
+    // snapshot: device staging (11 n doubles), pinned host copy, completion event
+    crk::DBuf snap_dev;
+    double *snap_host = nullptr;
+    cudaEvent_t snap_ev = nullptr;
+    bool snap_inflight = false;
+    int snap_steps = -1;          // steps of the copy in flight or last completed
+    int snap_valid = -1;          // steps of the last completed copy (-1: none)
+
+    ~Job()
+    {
+        snap_dev.release();
+        if (snap_host) cudaFreeHost(snap_host);
+        if (snap_ev) cudaEventDestroy(snap_ev);
+    }
 };
 
 }  // namespace
@@ -48,6 +64,8 @@ struct crk_service {
     crk_service_params prm{};
     crk_sim *sim = nullptr;
     cudaStream_t st = nullptr;
+    cudaStream_t side = nullptr;  // snapshot copies
+    cudaEvent_t stepped = nullptr;
     size_t bpp = 0;
     std::thread th;
     std::mutex mu;
@@ -61,6 +79,36 @@ struct crk_service {
 };
 
 namespace {
+
+// Starts a snapshot of a resident job: extraction on the compute stream,
+// device-to-host copy on the side stream (overlapping the next step).  The
+// previous copy of the job is completed first (its staging is reused).
+// Caller holds sv->mu.
+int start_snapshot(crk_service *sv, Job &j)
+{
+    const size_t words = (size_t)j.n * 11;
+    if (!j.snap_host) {
+        if (cudaMallocHost(&j.snap_host, words * sizeof(double)) != cudaSuccess) {
+            j.snap_host = nullptr;
+            return fail(CRK_ENOMEM, "no pinned memory for a snapshot of %lld particles", (long long)j.n);
+        }
+        CK(cudaEventCreateWithFlags(&j.snap_ev, cudaEventDisableTiming));
+    }
+    if (j.snap_inflight) {
+        CK(cudaEventSynchronize(j.snap_ev));
+        j.snap_valid = j.snap_steps;
+        j.snap_inflight = false;
+    }
+    RET(j.snap_dev.ensure(words * sizeof(double)));
+    RET(pool_snapshot(sv->sim, j.slot, j.n, j.snap_dev.as<double>()));
+    CK(cudaEventRecord(sv->stepped, sv->st));
+    CK(cudaStreamWaitEvent(sv->side, sv->stepped, 0));
+    CK(cudaMemcpyAsync(j.snap_host, j.snap_dev.p, words * sizeof(double), cudaMemcpyDeviceToHost, sv->side));
+    CK(cudaEventRecord(j.snap_ev, sv->side));
+    j.snap_steps = j.steps_done;
+    j.snap_inflight = true;
+    return CRK_OK;
+}
 
 void finish(crk_service *sv, const std::shared_ptr<Job> &j, int status, const char *msg)
 {
@@ -104,9 +152,13 @@ void worker(crk_service *sv)
         }
         std::vector<std::shared_ptr<Job>> published;
         for (auto &j : admitted) {
+            const bool resume = !j->acc.empty();
             int rc = pool_add(sv->sim, j->slot, j->phys, j->n, j->pos.data(), j->vel.data(),
-                              j->mass.data(), j->u.data(), j->h.data(), j->sp.data());
+                              j->mass.data(), j->u.data(), j->h.data(), j->sp.data(),
+                              resume ? j->acc.data() : nullptr, resume ? j->du.data() : nullptr);
             j->t_admit = clk::now();
+            // a resumed job has the forces of its snapshot: no initial evaluation
+            j->init_done = resume;
             if (rc != CRK_OK) {
                 finish(sv, j, rc, crk_last_error());
                 published.push_back(j);
@@ -119,13 +171,35 @@ void worker(crk_service *sv)
                 sv->resident_bytes -= j->bytes;
             }
         }
+        std::vector<std::shared_ptr<Job>> leaving;
+        // Cancelled jobs leave at this step boundary.
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            for (auto &j : sv->slots)
+                if (j && !j->done && j->cancel) {
+                    finish(sv, j, CRK_ECANCELED, "cancelled");
+                    leaving.push_back(j);
+                }
+        }
+        // A resumed job that already ran all its steps only publishes its state.
+        for (auto &j : sv->slots)
+            if (j && !j->done && j->init_done && j->steps_done >= j->nsteps) {
+                std::vector<double> pos((size_t)j->n * 3), vel((size_t)j->n * 3), u((size_t)j->n);
+                int r2 = pool_extract(sv->sim, j->slot, j->n, pos.data(), vel.data(), u.data());
+                j->pos.swap(pos);
+                j->vel.swap(vel);
+                j->u.swap(u);
+                finish(sv, j, r2, r2 == CRK_OK ? nullptr : crk_last_error());
+                leaving.push_back(j);
+            }
         // One batched step for every resident job.
         for (int s = 0; s < sv->prm.max_slots; ++s) {
             auto &j = sv->slots[s];
-            dts[(size_t)s] = (j && j->init_done) ? j->dt : 0.0;
+            dts[(size_t)s] = (j && !j->done && j->init_done) ? j->dt : 0.0;
         }
-        int rc = pool_step(sv->sim, dts.data());
-        std::vector<std::shared_ptr<Job>> leaving;
+        bool any_live = false;
+        for (auto &j : sv->slots) any_live = any_live || (j && !j->done);
+        int rc = any_live ? pool_step(sv->sim, dts.data()) : CRK_OK;
         if (rc != CRK_OK) {
             std::string msg = crk_last_error();
             for (auto &j : sv->slots)
@@ -133,11 +207,21 @@ void worker(crk_service *sv)
                     finish(sv, j, rc, msg.c_str());
                     leaving.push_back(j);
                 }
-        } else {
+        } else if (any_live) {
             for (auto &j : sv->slots) {
                 if (!j || j->done) continue;
                 if (!j->init_done) j->init_done = true;
                 else j->steps_done++;
+                const int every = sv->prm.snapshot_every;
+                if (every > 0 && j->steps_done > 0 && j->steps_done % every == 0) {
+                    std::lock_guard<std::mutex> lk(sv->mu);
+                    int r3 = start_snapshot(sv, *j);
+                    if (r3 != CRK_OK) {
+                        finish(sv, j, r3, crk_last_error());
+                        leaving.push_back(j);
+                        continue;
+                    }
+                }
                 if (j->steps_done >= j->nsteps) {
                     std::vector<double> pos((size_t)j->n * 3), vel((size_t)j->n * 3), u((size_t)j->n);
                     int r2 = pool_extract(sv->sim, j->slot, j->n, pos.data(), vel.data(), u.data());
@@ -180,8 +264,16 @@ extern "C" int crk_service_create(const crk_service_params *params, crk_service 
     p.kernel = CRK_WENDLAND_C4;
     p.leaf_cap = params->leaf_cap ? params->leaf_cap : 64;
     p.precision = params->precision;
+    if (params->snapshot_every < 0) {
+        delete sv;
+        return fail(CRK_EINVAL, "snapshot_every must be >= 0");
+    }
     cudaError_t e = cudaStreamCreateWithFlags(&sv->st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sv->stepped, cudaEventDisableTiming);
     if (e != cudaSuccess) {
+        if (sv->st) cudaStreamDestroy(sv->st);
+        if (sv->side) cudaStreamDestroy(sv->side);
         delete sv;
         return fail(CRK_ECUDA, "stream creation failed: %s", cudaGetErrorString(e));
     }
@@ -190,6 +282,8 @@ extern "C" int crk_service_create(const crk_service_params *params, crk_service 
     if (rc != CRK_OK) {
         if (sv->sim) crk_destroy(sv->sim);
         cudaStreamDestroy(sv->st);
+        cudaStreamDestroy(sv->side);
+        cudaEventDestroy(sv->stepped);
         delete sv;
         return rc;
     }
@@ -206,6 +300,9 @@ extern "C" int crk_submit(crk_service *sv, const crk_job *job, uint64_t *ticket)
     if (job->n <= 0 || !job->pos || !job->vel || !job->mass || !job->u || !job->h || !job->species)
         return fail(CRK_EINVAL, "a job needs n > 0 and every particle array");
     if (job->nsteps < 0 || !(job->dt >= 0.0)) return fail(CRK_EINVAL, "nsteps >= 0 and dt >= 0 required");
+    const bool resume = job->acc != nullptr || job->dudt != nullptr || job->steps_done != 0;
+    if (resume && (!job->acc || !job->dudt || job->steps_done < 0 || job->steps_done > job->nsteps))
+        return fail(CRK_EINVAL, "a resumed job needs acc, dudt and 0 <= steps_done <= nsteps");
     auto j = std::make_shared<Job>();
     j->phys = job->phys;
     j->n = job->n;
@@ -216,9 +313,14 @@ extern "C" int crk_submit(crk_service *sv, const crk_job *job, uint64_t *ticket)
     j->u.assign(job->u, job->u + n);
     j->h.assign(job->h, job->h + n);
     j->sp.assign(job->species, job->species + n);
+    if (resume) {
+        j->acc.assign(job->acc, job->acc + 3 * n);
+        j->du.assign(job->dudt, job->dudt + n);
+        j->steps_done = job->steps_done;
+    }
     j->dt = job->dt;
     j->nsteps = job->nsteps;
-    j->bytes = n * sv->bpp + (64u << 10);
+    j->bytes = n * (sv->bpp + (sv->prm.snapshot_every > 0 ? 11 * sizeof(double) : 0)) + (64u << 10);
     if (j->bytes > sv->prm.hbm_budget_bytes)
         return fail(CRK_EINVAL, "job of %lld particles needs %zu bytes, above the budget of %zu",
                     (long long)job->n, j->bytes, sv->prm.hbm_budget_bytes);
@@ -276,8 +378,56 @@ extern "C" int crk_service_destroy(crk_service *sv)
     sv->cv_work.notify_all();
     if (sv->th.joinable()) sv->th.join();
     sv->cv_done.notify_all();
+    cudaStreamSynchronize(sv->side);
     crk_destroy(sv->sim);
     cudaStreamDestroy(sv->st);
+    cudaStreamDestroy(sv->side);
+    cudaEventDestroy(sv->stepped);
     delete sv;
+    return CRK_OK;
+}
+
+extern "C" int crk_service_snapshot(crk_service *sv, uint64_t ticket, crk_job_snapshot *out)
+{
+    if (!sv || !out) return fail(CRK_EINVAL, "null argument");
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->jobs.find(ticket);
+    if (it == sv->jobs.end()) return fail(CRK_ENOTFOUND, "unknown ticket %llu", (unsigned long long)ticket);
+    Job &j = *it->second;
+    if (j.snap_inflight) {
+        CK(cudaEventSynchronize(j.snap_ev));
+        j.snap_valid = j.snap_steps;
+        j.snap_inflight = false;
+    }
+    if (j.snap_valid < 0) return fail(CRK_EPENDING, "no snapshot of job %llu yet", (unsigned long long)ticket);
+    const size_t n = (size_t)j.n;
+    const double *b = j.snap_host;
+    if (out->pos) std::memcpy(out->pos, b, 3 * n * sizeof(double));
+    if (out->vel) std::memcpy(out->vel, b + 3 * n, 3 * n * sizeof(double));
+    if (out->u) std::memcpy(out->u, b + 6 * n, n * sizeof(double));
+    if (out->acc) std::memcpy(out->acc, b + 7 * n, 3 * n * sizeof(double));
+    if (out->dudt) std::memcpy(out->dudt, b + 10 * n, n * sizeof(double));
+    out->n = j.n;
+    out->steps_done = j.snap_valid;
+    return CRK_OK;
+}
+
+extern "C" int crk_service_cancel(crk_service *sv)
+{
+    if (!sv) return fail(CRK_EINVAL, "null argument");
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        for (auto &j : sv->pending) {
+            j->status = CRK_ECANCELED;
+            j->msg = "cancelled before admission";
+            j->t_admit = j->t_done = clk::now();
+            j->done = true;
+        }
+        sv->pending.clear();
+        for (auto &j : sv->slots)
+            if (j) j->cancel = true;
+    }
+    sv->cv_work.notify_all();
+    sv->cv_done.notify_all();
     return CRK_OK;
 }

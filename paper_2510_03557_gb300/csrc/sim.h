@@ -112,7 +112,10 @@ namespace crk {
 int pool_init(crk_sim *s, int max_slots);
 int pool_add(crk_sim *s, int slot, const crk_physics &phys, int64_t n, const double *pos,
              const double *vel, const double *mass, const double *u, const double *h,
-             const uint8_t *species);
+             const uint8_t *species, const double *acc, const double *dudt);
+// Device copy of a slot's state in load order: pos 3n, vel 3n, u n, acc 3n,
+// du/dt n (11 n doubles at dev), stream-ordered on the handle's stream.
+int pool_snapshot(crk_sim *s, int slot, int64_t n, double *dev);
 int pool_extract(crk_sim *s, int slot, int64_t n, double *pos, double *vel, double *u);
 int pool_remove(crk_sim *s, int slot, int64_t n);
 int pool_step(crk_sim *s, const double *dt_per_slot);

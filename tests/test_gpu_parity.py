@@ -421,6 +421,46 @@ def test_service_reuses_freed_slots(crk):
         assert np.array_equal(alone["u"], r["u"])
 
 
+def test_service_resumes_a_cancelled_job_from_its_snapshot_bit_exactly(crk):
+    """Checkpoint/resume: a job's service is cancelled mid-run (the host-side
+    failure); the job resubmitted to a new service from its last snapshot
+    ends exactly where the run without interruption ends."""
+    import time
+
+    box = wl.gaussian_field_box(12, seed=501)
+    steps = 60
+    ref = _run_service(crk, [box], steps)[0]
+    svc = crk.crk_service_create(8 << 30, 4, snapshot_every=5)
+    try:
+        t = crk.crk_submit(svc, crk.box_physics(box), box.pos, box.vel, box.mass, box.u, box.h,
+                           box.species, box.dt, steps)
+        snap = None
+        deadline = time.time() + 60
+        while time.time() < deadline:
+            snap = crk.crk_service_snapshot(svc, t, box.n)
+            if snap is not None and snap["steps_done"] >= 10:
+                break
+            time.sleep(1e-3)
+        assert snap is not None and snap["steps_done"] % 5 == 0 and 10 <= snap["steps_done"] <= steps
+        crk.crk_service_cancel(svc)
+        try:
+            crk.crk_poll(svc, t, box.n, -1)   # finished just before the cancel, or cancelled
+        except crk.CrkError as e:
+            assert e.code == crk.CRK_ECANCELED
+    finally:
+        crk.crk_service_destroy(svc)
+    svc2 = crk.crk_service_create(8 << 30, 4)
+    try:
+        t2 = crk.crk_submit(svc2, crk.box_physics(box), snap["pos"], snap["vel"], box.mass, snap["u"],
+                            box.h, box.species, box.dt, steps, resume=snap)
+        res = crk.crk_poll(svc2, t2, box.n, -1)
+    finally:
+        crk.crk_service_destroy(svc2)
+    assert np.array_equal(res["pos"], ref["pos"])
+    assert np.array_equal(res["vel"], ref["vel"])
+    assert np.array_equal(res["u"], ref["u"])
+
+
 def test_service_matches_oracle(crk):
     boxes = _job_boxes()[:3]
     res = _run_service(crk, boxes, 3, precision=0)
