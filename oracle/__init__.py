@@ -75,7 +75,7 @@ def lib():
             L.orc_S.argtypes = [d, d]
             for name in ("orc_neighbours", "orc_expand_mask", "orc_density", "orc_moments",
                          "orc_corrections", "orc_hydro", "orc_gravity", "orc_pair_forces",
-                         "orc_crk_identities", "orc_forces", "orc_kdk"):
+                         "orc_crk_identities", "orc_forces", "orc_kdk", "orc_fof"):
                 getattr(L, name).restype = ctypes.c_int
             L.orc_max_threads.restype = ctypes.c_int
             _lib = L
@@ -127,6 +127,22 @@ def neighbours(pos, h, species, params: Params, kind: int):
     if rc:
         raise RuntimeError(f"orc_neighbours failed: {rc}")
     return cnt, hs
+
+
+def fof(pos, species, box: float, b: float, species_mask: int = 1):
+    """Friends-of-friends groups (in situ halo finding, Sec. IV-B3): particles
+    of the species in `species_mask` (bit 0 DM, bit 1 gas) linked when
+    r < b; returns (group int64[N]: the smallest index of the particle's
+    group, -1 for other species; number of groups)."""
+    pos = _f64(pos, (-1, 3))
+    n = pos.shape[0]
+    grp = np.zeros(n, np.int64)
+    ng = ctypes.c_int64()
+    rc = lib().orc_fof(ctypes.c_int64(n), _p(pos), _p(_u8(species)), ctypes.c_double(box),
+                       ctypes.c_double(b), ctypes.c_int(species_mask), _p(grp), ctypes.byref(ng))
+    if rc:
+        raise RuntimeError(f"orc_fof failed: {rc}")
+    return grp, int(ng.value)
 
 
 def expand_mask(pos, h, species, params: Params, mask):

@@ -21,7 +21,10 @@
  *     (built with -ffp-contract=off);
  *   - hydro pair set: r^2 < H_i^2 or r^2 < H_j^2; gravity set: r^2 < r_cut^2;
  *   - split: S(r) = erfc(r / 2 r_s) + r / (sqrt(pi) r_s) exp(-r^2 / 4 r_s^2);
- *   - u floored at u_floor after each kick, floor events counted.
+ *   - u floored at u_floor after each kick, floor events counted;
+ *   friends-of-friends groups (in situ halo finding, Sec. IV-B3): particles
+ *   of the chosen species linked when r^2 < b^2 (the same predicate), groups
+ *   the connected components, each labelled by its smallest index.
  * The neighbour search is a cell list of side >= the largest search radius
  * (or all pairs when the box holds fewer than three such cells); no tree,
  * no leaves, no leaf pairs.  Every per-particle sum runs in a fixed order.
@@ -803,4 +806,66 @@ int orc_max_threads(void)
 #else
     return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------ */
+/* Friends-of-friends groups (in situ halo finding, Sec. IV-B3)        */
+/* ------------------------------------------------------------------ */
+/* Root of x with path halving. */
+static int64_t orc_find(int64_t *par, int64_t x)
+{
+    while (par[x] != x) {
+        par[x] = par[par[x]];
+        x = par[x];
+    }
+    return x;
+}
+
+/* Particles whose species bit is set in species_mask (bit 0: CRK_DM, bit 1:
+ * CRK_GAS) are linked when r^2 < b^2, r^2 formed as for every neighbour set;
+ * groups are the connected components of the links.  group[i] = the smallest
+ * index in i's group, -1 for particles of the other species; *ngroups counts
+ * the groups, singletons included.  Sequential union-find over a cell list;
+ * unions always hang the larger root under the smaller, so a root is the
+ * smallest index of its tree. */
+int orc_fof(int64_t n, const double *pos, const uint8_t *species, double L, double b, int species_mask,
+            int64_t *group, int64_t *ngroups)
+{
+    if (!(b > 0.0) || !(b < 0.5 * L)) return ORC_EINVAL;
+    int64_t *par = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    if (!par) return ORC_ENOMEM;
+    for (int64_t i = 0; i < n; ++i) par[i] = i;
+    orc_cells cl;
+    int rc = orc_cells_build(&cl, n, pos, L, b, 0);
+    if (rc) { free(par); return rc; }
+    const double b2 = b * b;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!((species_mask >> species[i]) & 1)) continue;
+        int64_t cells[27];
+        int nci = orc_cells_around(&cl, pos, i, L, cells);
+        for (int c = 0; c < nci; ++c)
+            for (int64_t q = cl.start[cells[c]]; q < cl.start[cells[c] + 1]; ++q) {
+                int64_t j = cl.idx[q];
+                if (j <= i || !((species_mask >> species[j]) & 1)) continue;
+                double dx[3];
+                if (!(orc_sep(pos, i, j, L, dx) < b2)) continue;
+                int64_t ri = orc_find(par, i), rj = orc_find(par, j);
+                if (ri == rj) continue;
+                if (ri < rj) par[rj] = ri;
+                else par[ri] = rj;
+            }
+    }
+    int64_t ng = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!((species_mask >> species[i]) & 1)) {
+            group[i] = -1;
+            continue;
+        }
+        group[i] = orc_find(par, i);
+        if (group[i] == i) ++ng;
+    }
+    *ngroups = ng;
+    orc_cells_free(&cl);
+    free(par);
+    return ORC_OK;
 }
