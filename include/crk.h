@@ -192,6 +192,21 @@ int crk_get_sums(crk_sim *sim, double momentum[3], double *energy, int64_t *nflo
 /* Number of particles and boxes loaded. */
 int crk_get_size(crk_sim *sim, int64_t *n, int *nbox);
 
+/* Friends-of-friends groups of the loaded particles: the paper's in situ
+ * halo finding on the GPU (Sec. IV-B3), here on the solver's own leaves and
+ * gravity leaf-pair lists.  Particles of the species set in species_mask
+ * (bit 0: CRK_DM, bit 1: CRK_GAS) are linked when r < b, r^2 formed as for
+ * the neighbour sets (FP64, (dx*dx + dy*dy) + dz*dz, dx wrapped once); the
+ * mixed form tests in FP32 and re-decides in FP64 inside the guard band, so
+ * the links are the FP64 links.  Groups are the connected components.
+ * group[i] (caller order, n entries, where mem says) = the smallest original
+ * index in i's group, -1 for particles of the other species; *ngroups =
+ * number of groups, singletons included.  Requires 0 < b <= r_cut of every
+ * box.  Sorts the particles into a new tree for the current state (the state
+ * itself is unchanged).  Synchronises the stream.  Errors: CRK_EINVAL,
+ * CRK_ECUDA, CRK_ETIMEOUT (a bounded retry loop of the union-find ran out). */
+int crk_fof(crk_sim *sim, double b, int species_mask, int64_t *group, int64_t *ngroups, int mem);
+
 /* Leaf-capacity autotuner.  The paper sizes its base leaves by hand for its
  * hardware (Sec. IV-B1: several hundred particles per leaf on MI250X); here the
  * best capacity depends on the particle distribution.  Runs one force

@@ -36,7 +36,7 @@ CRK_GAS = 1
 # Every function of the C ABI.
 ABI = ("crk_create", "crk_load", "crk_load_boxes", "crk_forces", "crk_step", "crk_step_boxes",
        "crk_get_state", "crk_set_state", "crk_get_sums", "crk_get_size", "crk_set_timing", "crk_get_timings",
-       "crk_destroy", "crk_autotune", "crk_service_create", "crk_submit", "crk_poll", "crk_service_destroy",
+       "crk_destroy", "crk_fof", "crk_autotune", "crk_service_create", "crk_submit", "crk_poll", "crk_service_destroy",
        "crk_service_snapshot", "crk_service_cancel",
        "crk_neighbours_noalloc", "crk_last_error")
 CRK_NOALLOC_MAX_N = 262144
@@ -285,6 +285,18 @@ def crk_get_timings(sim) -> dict:
 
 def crk_destroy(sim):
     _check(lib().crk_destroy(sim))
+
+
+def crk_fof(sim, b: float, species_mask: int = 1, n: int | None = None):
+    """Friends-of-friends groups (linking length b, species bits as in
+    crk_fof); returns (group int64[N], number of groups)."""
+    if n is None:
+        n = crk_get_size(sim)[0]
+    grp = np.zeros(n, np.int64)
+    ng = ctypes.c_int64()
+    _check(lib().crk_fof(sim, ctypes.c_double(b), ctypes.c_int(species_mask),
+                         grp.ctypes.data_as(ctypes.c_void_p), ctypes.byref(ng), ctypes.c_int(CRK_MEM_HOST)))
+    return grp, int(ng.value)
 
 
 def crk_autotune(sim, caps=(32, 64, 128)):

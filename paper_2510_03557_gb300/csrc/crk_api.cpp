@@ -282,6 +282,8 @@ int read_error(crk_sim *s)
     const int code = s->host_err[0], idx = s->host_err[1];
     if (code == CRK_ESINGULAR)
         return fail(CRK_ESINGULAR, "second-moment matrix of gas particle %d is singular", idx);
+    if (code == CRK_ETIMEOUT)
+        return fail(CRK_ETIMEOUT, "a bounded retry loop ran out (particle %d)", idx);
     if (code == CRK_EINVAL)
         return fail(CRK_EINVAL, "particle %d is invalid (position outside [0,L), non-finite value, "
                                 "mass <= 0, or gas h with 2h <= 0 or 2h >= L/2)", idx);
@@ -771,6 +773,40 @@ extern "C" int crk_set_timing(crk_sim *s, int enable)
     return CRK_OK;
 }
 
+extern "C" int crk_fof(crk_sim *s, double b, int species_mask, int64_t *group, int64_t *ngroups, int mem)
+{
+    if (!s || !group || !ngroups) return fail(CRK_EINVAL, "null argument");
+    if (species_mask < 1 || species_mask > 3) return fail(CRK_EINVAL, "species_mask must be 1, 2 or 3");
+    if (mem != CRK_MEM_HOST && mem != CRK_MEM_DEVICE) return fail(CRK_EINVAL, "bad mem flag");
+    if (!(b > 0.0)) return fail(CRK_EINVAL, "linking length must be > 0");
+    for (const BoxDev &bx : s->boxes)
+        if (bx.active && !(b <= bx.r_cut)) return fail(CRK_EINVAL, "linking length %g above r_cut %g", b, bx.r_cut);
+    CK(cudaSetDevice(s->device));
+    *ngroups = 0;
+    if (s->n == 0) return CRK_OK;
+    RET(reset_error(s));
+    RET(build_tree(s));
+    const size_t n = (size_t)s->n;
+    RET(s->fof_par.ensure(n * 4 + 8 * 8));
+    uint32_t *par = s->fof_par.as<uint32_t>();
+    unsigned long long *cnt = reinterpret_cast<unsigned long long *>(par + ((n + 1) & ~size_t(1)));
+    int64_t *dst = group;
+    if (mem == CRK_MEM_HOST) {
+        RET(s->staging.ensure(n * 8 + 256));
+        dst = s->staging.as<int64_t>();
+    }
+    CK(cudaMemsetAsync(cnt, 0, 8, s->st));
+    PassArgs a = pass_args(s);
+    launch_fof(a, s->mixed ? 1 : 0, s->cap, par, b, species_mask, dst, cnt, s->st);
+    CK(cudaGetLastError());
+    unsigned long long h_cnt = 0;
+    CK(cudaMemcpyAsync(&h_cnt, cnt, 8, cudaMemcpyDeviceToHost, s->st));
+    if (mem == CRK_MEM_HOST) CK(cudaMemcpyAsync(group, dst, n * 8, cudaMemcpyDeviceToHost, s->st));
+    RET(read_error(s));  // synchronises
+    *ngroups = (int64_t)h_cnt;
+    return CRK_OK;
+}
+
 extern "C" int crk_autotune(crk_sim *s, const int *caps, int ncaps, int *best_cap, double *ms_out)
 {
     if (!s || !caps || ncaps < 1) return fail(CRK_EINVAL, "null argument or no candidate");
@@ -879,7 +915,7 @@ extern "C" int crk_destroy(crk_sim *s)
                     &s->pm, &s->uhat, &s->acc_h, &s->acc_g, &s->nbrc, &s->nbrh, &s->gravc,
                     &s->gravh, &s->err, &s->nfloor, &s->partial, &s->sums, &s->staging,
                     &s->in_stage, &s->grp_cnt, &s->grp_off, &s->grp_gas, &s->grp_all, &s->hfr, &s->gfr,
-                    &s->nl_j, &s->nl_row, &s->nl_len, &s->nl_cnt, &s->hsj};
+                    &s->nl_j, &s->nl_row, &s->nl_len, &s->nl_cnt, &s->hsj, &s->fof_par};
     for (DBuf *b : bufs) b->release();
     for (int k = 0; k < 3; ++k) {
         s->lv_u32[k].release();

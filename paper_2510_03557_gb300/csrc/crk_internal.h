@@ -149,6 +149,8 @@ void launch_density(const PassArgs &a, int mixed, int cap, bool count, cudaStrea
 void launch_moments(const PassArgs &a, int mixed, int cap, cudaStream_t st);
 void launch_hydro(const PassArgs &a, int mixed, int cap, cudaStream_t st);
 void launch_gravity(const PassArgs &a, int mixed, int cap, bool count, cudaStream_t st);
+void launch_fof(const PassArgs &a, int mixed, int cap, uint32_t *par, double b, int mask, int64_t *group,
+                unsigned long long *ngroups, cudaStream_t st);
 
 // ---- integration and outputs (integrate.cu) ----
 void launch_kick_drift(const State &s, const BoxDev *boxes, int64_t n,

@@ -1369,6 +1369,144 @@ __global__ void __launch_bounds__(kBlock) gravity_k(PassArgs a)
     }
 }
 
+// ------------------------------------------------- friends-of-friends groups
+// In situ halo finding (paper Sec. IV-B3) on the solver's own leaves and
+// gravity leaf-pair lists: particles of the selected species are linked when
+// r < b (decided like every neighbour set: FP32 test, FP64 re-decision inside
+// the guard band); groups are the connected components.  Concurrent
+// union-find over the sorted particles: a union hangs the root of larger
+// original index under the root of smaller original index with a
+// compare-and-swap on the root's parent, so the final root of a component is
+// its particle of smallest original index.  Every retry loop is bounded.
+constexpr int kFofRetries = 1 << 22;
+
+__device__ __forceinline__ uint32_t fof_find(uint32_t *par, uint32_t x)
+{
+    volatile uint32_t *vp = par;
+    for (int it = 0; it < kFofRetries; ++it) {
+        const uint32_t p = vp[x];
+        if (p == x) return x;
+        const uint32_t g = vp[p];
+        if (g != p) vp[x] = g;  // path halving: only ever points closer to the root
+        x = p;
+    }
+    return 0xffffffffu;
+}
+
+// false when a bound ran out (the caller reports CRK_ETIMEOUT)
+__device__ __forceinline__ bool fof_union(uint32_t *par, const uint32_t *id, uint32_t a, uint32_t b)
+{
+    for (int it = 0; it < kFofRetries; ++it) {
+        const uint32_t ra = fof_find(par, a), rb = fof_find(par, b);
+        if (ra == 0xffffffffu || rb == 0xffffffffu) return false;
+        if (ra == rb) return true;
+        const bool a_first = id[ra] < id[rb];
+        const uint32_t lo = a_first ? ra : rb, hi = a_first ? rb : ra;
+        if (atomicCAS(&par[hi], hi, lo) == hi) return true;
+    }
+    return false;
+}
+
+__global__ void fof_init_k(uint32_t *par, int64_t n)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) par[k] = (uint32_t)k;
+}
+
+template <typename R, int JMAX>
+__global__ void __launch_bounds__(kBlock) fof_link_k(PassArgs a, uint32_t *par, double b, int mask)
+{
+    using R4 = Vec4<R>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    const uint32_t gi = blockIdx.x * kWarps + w;
+    if (gi >= a.n_gall) return;
+    R4 *tile = reinterpret_cast<R4 *>(smem + (size_t)w * JMAX * (sizeof(R4) + 1));
+    uint8_t *tslot = reinterpret_cast<uint8_t *>(tile + JMAX);
+    const Group G = load_group(a.lv, a.gall, gi, lane);
+    const int I = G.I;
+    if (!((mask >> a.lv.species[I]) & 1)) return;
+    const uint32_t i = G.i;
+    const R4 *__restrict__ pm = reinterpret_cast<const R4 *>(a.pm);
+    const double Ld = a.boxes[a.lv.slot[I]].L;
+    const R L = (R)Ld, hL = (R)(0.5 * Ld);
+    const R4 ri = pm[i];
+    const double b2x = __dmul_rn(b, b);
+    const R bb = (R)b;
+    const R b2 = Real<R>::mixed ? bb * bb : (R)b2x;
+    float px, py, pz;
+    rel_pos(ri, a.lv, I, Ld, px, py, pz);
+    const WarpBox wb = warp_box(px, py, pz, G.act);
+    const float Rc = (float)b * 1.0001f + 1e-6f * (float)Ld;
+    bool ok = true;
+    for (uint32_t p = a.grow[I]; p < a.grow[I + 1]; ++p) {
+        const uint32_t J = a.gcol[p];
+        if (!((mask >> a.lv.species[J]) & 1)) continue;
+        const float4 fr = a.gfr[p];
+        if (out_of_range(wb, fr, a.lv.ex[J], a.lv.ey[J], a.lv.ez[J], Rc)) continue;
+        const uint32_t sJ = a.lv.start[J], cJ = a.lv.count[J];
+        const uint32_t cm = chunks_in_range(a.lv, J, cJ, wb, fr, Rc);
+        if (cm == 0u) continue;
+        __syncwarp();
+        const uint32_t K = stage_cull<R, false>(tile, tslot, nullptr, pm, nullptr, sJ, cJ, cm, wb,
+                                                cand_frame<R>(a.lv, I, fr, Ld), Rc, lane);
+        __syncwarp();
+        if (K == 0u) continue;
+        const Target<R> q = target_in_frame(ri, fr);
+        const R gb = Real<R>::mixed ? (R)guard_band((float)b, q.mag) : (R)0;
+        uint32_t m[JMAX / 32];
+        test_tile_any<R, JMAX, false>(tile, nullptr, q, L, hL, b2 + gb, G.act ? chunk_mask(K) : 0u, m);
+#pragma unroll
+        for (int ww = 0; ww < JMAX / 32; ++ww) {
+            uint32_t bits = m[ww];
+            while (bits) {
+                const int j = 32 * ww + __ffs(bits) - 1;
+                bits &= bits - 1;
+                const uint32_t jg = sJ + tslot[j];
+                if (jg <= i) continue;  // each pair once, from its lower index
+                if (Real<R>::mixed) {
+                    R dx, dy, dz;
+                    const R r2 = q.wrap ? sep2<R, true>(tile[j], q, L, hL, dx, dy, dz)
+                                        : sep2<R, false>(tile[j], q, L, hL, dx, dy, dz);
+                    if (r2 >= b2 - gb && !exact_lt(a.s, i, jg, Ld, b2x)) continue;
+                }
+                ok = fof_union(par, a.s.id, i, jg) && ok;
+            }
+        }
+    }
+    if (!ok) set_error(a.err, CRK_ETIMEOUT, a.s.id[i]);
+}
+
+// group[id] = original index of the root (smallest of the group), -1 for the
+// other species; roots counted.
+__global__ void fof_label_k(State s, uint32_t *par, int64_t n, int mask, int64_t *group,
+                            unsigned long long *ngroups, int *err)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const uint32_t o = s.id[k];
+    if (!((mask >> s.species[k]) & 1)) {
+        group[o] = -1;
+        return;
+    }
+    const uint32_t r = fof_find(par, (uint32_t)k);
+    if (r == 0xffffffffu) {
+        set_error(err, CRK_ETIMEOUT, o);
+        group[o] = -1;
+        return;
+    }
+    group[o] = (int64_t)s.id[r];
+    if (r == (uint32_t)k) atomicAdd(ngroups, 1ull);
+}
+
+template <typename R, int JMAX>
+void fof_dispatch(const PassArgs &a, uint32_t *par, double b, int mask, cudaStream_t st)
+{
+    if (a.n_gall == 0) return;
+    const size_t sm = (size_t)kWarps * JMAX * (sizeof(Vec4<R>) + 1);
+    fof_link_k<R, JMAX><<<(a.n_gall + kWarps - 1) / kWarps, kBlock, sm, st>>>(a, par, b, mask);
+}
+
 inline unsigned nblocks(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 template <typename K>
@@ -1421,6 +1559,24 @@ void hydro_dispatch(const PassArgs &a, cudaStream_t st)
 }
 
 }  // namespace
+
+void launch_fof(const PassArgs &a, int mixed, int cap, uint32_t *par, double b, int mask, int64_t *group,
+                unsigned long long *ngroups, cudaStream_t st)
+{
+    if (a.n <= 0) return;
+    fof_init_k<<<nblocks(a.n, 256), 256, 0, st>>>(par, a.n);
+    if (mixed) {
+        if (cap == 32) fof_dispatch<float, 32>(a, par, b, mask, st);
+        else if (cap == 64) fof_dispatch<float, 64>(a, par, b, mask, st);
+        else fof_dispatch<float, 128>(a, par, b, mask, st);
+    } else {
+        if (cap == 32) fof_dispatch<double, 32>(a, par, b, mask, st);
+        else if (cap == 64) fof_dispatch<double, 64>(a, par, b, mask, st);
+        else fof_dispatch<double, 128>(a, par, b, mask, st);
+    }
+    fof_label_k<<<nblocks(a.n, 256), 256, 0, st>>>(a.s, par, a.n, mask, group, ngroups, a.err);
+    note_launches(3);
+}
 
 void launch_records(const PassArgs &a, int mixed, cudaStream_t st)
 {

@@ -81,6 +81,7 @@ struct crk_sim {
     DBuf pm, hrec[7], uhat, acc_h, acc_g;
     DBuf nbrc, nbrh, gravc, gravh;
     DBuf nl_j, nl_row, nl_len, nl_cnt;  // hydro neighbour lists
+    DBuf fof_par;                       // friends-of-friends parents and group count
     int64_t nl_rows = 0;
     DBuf err, nfloor, partial, sums;
     DBuf staging, in_stage;

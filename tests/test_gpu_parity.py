@@ -503,3 +503,46 @@ def test_service_reports_a_bad_job_and_keeps_serving(crk):
             assert crk.crk_poll(svc, t, b.n, -1) is not None
     finally:
         crk.crk_service_destroy(svc)
+
+
+# ------------------------------------------------------------------ friends-of-friends
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_fof_groups_equal_the_oracle(crk, precision):
+    """Group labels (smallest original index per group) and counts are
+    integers: bit-exact against the oracle, for DM only and all species, at
+    the usual b = 0.2 mean spacings and near percolation."""
+    box = wl.clustered_box(24, seed=41, knn=False)
+    phys = box.params()
+    with crk.Sim(crk.box_physics(box), leaf_cap=64, precision=precision) as sim:
+        sim.load(box)
+        for b_over, mask in ((0.2, 1), (0.2, 3), (0.75, 1)):
+            b = b_over / 24
+            assert b <= phys["r_cut"]
+            grp, ng = crk.crk_fof(sim.handle, b, mask)
+            ref, ref_ng = oracle.fof(box.pos, box.species, phys["box"], b, mask)
+            assert ng == ref_ng, (b_over, mask)
+            assert np.array_equal(grp, ref), (b_over, mask)
+            assert ng < np.count_nonzero(ref >= 0)  # groups really formed
+        with pytest.raises(crk.CrkError) as e:
+            crk.crk_fof(sim.handle, 2 * phys["r_cut"], 1)
+        assert e.value.code == crk.CRK_EINVAL
+
+
+def test_fof_groups_stay_inside_their_box(crk):
+    boxes = [wl.clustered_box(n, seed=60 + n, knn=False) for n in (16, 20)]
+    cat = wl.concat_boxes(boxes)
+    phys = [crk.box_physics(b) for b in boxes]
+    b = 0.2 / 20
+    with crk.Sim(phys[0], precision=1) as sim:
+        crk.crk_load_boxes(sim.handle, [x.n for x in boxes], phys, cat["pos"], cat["vel"], cat["mass"],
+                           cat["u"], cat["h"], cat["species"])
+        sim.n = int(cat["offsets"][-1])
+        grp, ng = crk.crk_fof(sim.handle, b, 1)
+    total = 0
+    for k, bx in enumerate(boxes):
+        lo, hi = cat["offsets"][k], cat["offsets"][k + 1]
+        ref, ref_ng = oracle.fof(bx.pos, bx.species, bx.params()["box"], b, 1)
+        ref = np.where(ref >= 0, ref + lo, -1)
+        assert np.array_equal(grp[lo:hi], ref)
+        total += ref_ng
+    assert ng == total
