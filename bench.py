@@ -534,7 +534,30 @@ def main():
                   ("hydro_ms", tim["hydro_ms"]), ("gravity_ms", tim["gravity_ms"]),
                   ("kdk_ms", tim["kdk_ms"]))}
     launches = int(tim["launches"])
+    # friends-of-friends groups of the dark matter at b = 0.2 mean spacings
+    # (the call sorts a new tree for the current state, then links)
+    torch.cuda.synchronize()
+    t_f = time.perf_counter()
+    _, n_groups = crk.crk_fof(sim.handle, 0.2 / args.n, 1, N)
+    fof = {"ms": round((time.perf_counter() - t_f) * 1e3, 3), "groups": n_groups,
+           "linking_length": 0.2 / args.n, "species": "dm",
+           "note": "host wall time of crk_fof: tree build, links, labels, copy-out"}
     sim.close()
+
+    # ---------------- the same KDK step with the long-range mesh (FP64 PM, n^3 cells)
+    smesh = crk.Sim(phys, leaf_cap=args.leaf_cap, precision=crk.CRK_MIXED, stream=stream,
+                    rebuild_every=args.rebuild_every, pm_grid=args.n)
+    smesh.load(box)
+    smesh.step(dt, 2)
+    crk.crk_set_timing(smesh.handle, True)
+    smesh.step(dt, 3)
+    tmesh = crk.crk_get_timings(smesh.handle)
+    mcalls = max(tmesh["calls"], 1)
+    mesh = {"pm_grid": args.n, "pm_ms": round(tmesh["pm_ms"] / mcalls, 4),
+            "step_ms": round(tmesh["total_ms"] / mcalls, 4),
+            "note": "per KDK step, CUDA events on the handle's stream: deposit, cuFFT forward, "
+                    "Green's function, 3 cuFFT inverse, gather (FP64)"}
+    smesh.close()
 
     # ---------------- FP64 plain form on the same box
     fp64 = None
@@ -614,6 +637,8 @@ def main():
                                                           "gravity": int(tim["pairs_grav"])},
             "breakdown_ms": breakdown,
             "fp64_plain": fp64,
+            "fof": fof,
+            "long_range_mesh": mesh,
             "serving": serving,
             "e2e": e2e,
             "gpu_launches": launches,

@@ -88,13 +88,21 @@ typedef struct {
                           pair lists are recomputed (paper Sec. IV-B1: leaves built once per
                           long step, boxes grown in the substeps).  Loading or adding or
                           removing particles always rebuilds. */
-    int reserved[2];
+    int pm_grid;       /* long-range gravity on an FP64 particle mesh of pm_grid^3 cells (an even
+                          number in [4, 1024]; 0: none, the solver computes the short-range part
+                          alone).  With a mesh, every acceleration the handle computes or steps
+                          with is short-range + long-range, the long-range part the Newtonian
+                          force filtered by the Gaussian split (paper Sec. IV-A: FP64 spectral
+                          particle-mesh solver for the long-range force).  One box per handle
+                          (crk_load, or crk_load_boxes with nbox = 1); not with the service. */
+    int reserved[1];
 } crk_params;
 
 /* Outputs of crk_forces.  Every pointer is optional (NULL skips it); all
  * live where `mem` says.  Sizes in particles N of the loaded set. */
 typedef struct {
-    double *acc;          /* 3N: hydro + short-range gravity acceleration */
+    double *acc;          /* 3N: hydro + short-range gravity acceleration (+ the long-range mesh
+                             part when pm_grid > 0) */
     double *dudt;         /* N: du/dt (0 for DM) */
     double *rho;          /* N: density (0 for DM) */
     double *A;            /* N: CRK correction A (0 for DM) */
@@ -127,6 +135,7 @@ typedef struct {
     int64_t pairs_grav;   /* leaf pairs in the last gravity list (ordered) */
     int64_t nleaves;      /* leaves in the last tree */
     int64_t launches;     /* CUDA kernels the library launched in the timed calls */
+    double pm_ms;         /* long-range mesh gravity (deposit, FFTs, Green's function, gather) */
 } crk_timings;
 
 typedef struct crk_sim crk_sim;
@@ -206,6 +215,19 @@ int crk_get_size(crk_sim *sim, int64_t *n, int *nbox);
  * itself is unchanged).  Synchronises the stream.  Errors: CRK_EINVAL,
  * CRK_ECUDA, CRK_ETIMEOUT (a bounded retry loop of the union-find ran out). */
 int crk_fof(crk_sim *sim, double b, int species_mask, int64_t *group, int64_t *ngroups, int mem);
+
+/* Long-range gravity alone: the mesh acceleration of every particle at the
+ * current positions, acc 3N in load order where `mem` says (paper Sec. IV-A;
+ * the particle-mesh steps, all FP64: cloud-in-cell deposit of the mass
+ * density on the pm_grid^3 mesh of cell d = L / pm_grid with cell centres at
+ * (i + 1/2) d; forward FFT; phi(k) = -4 pi G rho(k) exp(-k^2 r_s^2) /
+ * (k^2 C(k)^2) with phi(0) = 0 and C(k) = prod_a sinc^2(k_a d / 2); a(k) =
+ * -i k phi(k) per axis, zero on that axis's Nyquist plane; inverse FFTs;
+ * cloud-in-cell gather).  The deposit adds in no fixed order, so results
+ * agree with any other evaluation to rounding, not bit for bit.  The state
+ * and the tree are unchanged.  Synchronises the stream.  Errors: CRK_EINVAL
+ * (null handle, pm_grid = 0, bad mem flag), CRK_ENOMEM, CRK_ECUDA. */
+int crk_pm_accel(crk_sim *sim, double *acc, int mem);
 
 /* Leaf-capacity autotuner.  The paper sizes its base leaves by hand for its
  * hardware (Sec. IV-B1: several hundred particles per leaf on MI250X); here the

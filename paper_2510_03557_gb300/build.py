@@ -1,7 +1,7 @@
 """Builds libcrk.so in-tree from the CUDA/C++ sources in csrc/ for sm_103a.
 
 Each translation unit is compiled by nvcc in parallel, then linked into one
-shared library with the CUDA runtime linked statically.
+shared library with the CUDA runtime linked statically and cuFFT dynamically.
 """
 from __future__ import annotations
 
@@ -17,7 +17,7 @@ LIB = os.path.join(OUT, "libcrk.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-diag-suppress", "1444"]
-SOURCES = ["tree.cu", "passes.cu", "integrate.cu", "noalloc.cu", "crk_api.cpp", "service.cpp"]
+SOURCES = ["tree.cu", "passes.cu", "integrate.cu", "pm.cu", "noalloc.cu", "crk_api.cpp", "service.cpp"]
 
 
 def nvcc() -> str:
@@ -53,7 +53,10 @@ def build(force: bool = False) -> str:
         objs = list(ex.map(_compile, srcs))
     if (not os.path.exists(LIB)) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-lpthread"]
+        # cuFFT (the mesh transforms) is linked dynamically from the toolkit
+        cudalib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc()))), "lib64")
+        cmd = [nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs, "-L" + cudalib, "-lcufft",
+               "-Xlinker", "-rpath", "-Xlinker", cudalib, "-lpthread"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

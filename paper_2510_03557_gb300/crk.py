@@ -36,7 +36,7 @@ CRK_GAS = 1
 # Every function of the C ABI.
 ABI = ("crk_create", "crk_load", "crk_load_boxes", "crk_forces", "crk_step", "crk_step_boxes",
        "crk_get_state", "crk_set_state", "crk_get_sums", "crk_get_size", "crk_set_timing", "crk_get_timings",
-       "crk_destroy", "crk_fof", "crk_autotune", "crk_service_create", "crk_submit", "crk_poll", "crk_service_destroy",
+       "crk_destroy", "crk_fof", "crk_pm_accel", "crk_autotune", "crk_service_create", "crk_submit", "crk_poll", "crk_service_destroy",
        "crk_service_snapshot", "crk_service_cancel",
        "crk_neighbours_noalloc", "crk_last_error")
 CRK_NOALLOC_MAX_N = 262144
@@ -57,7 +57,7 @@ class Physics(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("phys", Physics), ("kernel", ctypes.c_int), ("leaf_cap", ctypes.c_int),
                 ("precision", ctypes.c_int), ("cm_level", ctypes.c_int), ("flags", ctypes.c_int),
-                ("rebuild_every", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
+                ("rebuild_every", ctypes.c_int), ("pm_grid", ctypes.c_int), ("reserved", ctypes.c_int)]
 
 
 class Outputs(ctypes.Structure):
@@ -73,7 +73,7 @@ class Timings(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in ("tree_ms", "pairs_ms", "density_ms", "moments_ms",
                                                 "hydro_ms", "gravity_ms", "kdk_ms", "total_ms")] + \
                [(k, ctypes.c_int64) for k in ("calls", "pairs_hydro", "pairs_grav", "nleaves",
-                                               "launches")]
+                                               "launches")] + [("pm_ms", ctypes.c_double)]
 
 
 class ServiceParams(ctypes.Structure):
@@ -131,7 +131,7 @@ def physics(box=1.0, G=1.0, gamma=5.0 / 3.0, r_cut=0.1, r_split=0.02, eps_soft=0
 
 
 def params(phys: Physics | None = None, leaf_cap=64, precision=CRK_MIXED, cm_level=0,
-           kernel=CRK_WENDLAND_C4, rebuild_every=1) -> Params:
+           kernel=CRK_WENDLAND_C4, rebuild_every=1, pm_grid=0) -> Params:
     p = Params()
     p.phys = phys if phys is not None else physics()
     p.kernel = kernel
@@ -139,6 +139,7 @@ def params(phys: Physics | None = None, leaf_cap=64, precision=CRK_MIXED, cm_lev
     p.precision = precision
     p.cm_level = cm_level
     p.rebuild_every = rebuild_every
+    p.pm_grid = pm_grid
     return p
 
 
@@ -299,6 +300,19 @@ def crk_fof(sim, b: float, species_mask: int = 1, n: int | None = None):
     return grp, int(ng.value)
 
 
+def crk_pm_accel(sim, out=None):
+    """Long-range mesh acceleration (N, 3) of the current state, load order
+    (crk_pm_accel).  ``out``: a NumPy array or a CUDA tensor of 3N doubles;
+    a new NumPy array when None."""
+    if out is None:
+        out = np.zeros((crk_get_size(sim)[0], 3))
+    p, mem, keep = _ptr(out, np.float64)
+    if mem == CRK_MEM_HOST and keep is not out:
+        raise TypeError("out must be a contiguous float64 array")
+    _check(lib().crk_pm_accel(sim, p, ctypes.c_int(mem)))
+    return out
+
+
 def crk_autotune(sim, caps=(32, 64, 128)):
     """Times one force evaluation per leaf capacity, keeps the fastest;
     returns (best capacity, {capacity: ms})."""
@@ -411,9 +425,9 @@ class Sim:
     """Owns one crk_sim handle (create / load / forces / step / destroy)."""
 
     def __init__(self, phys: Physics | None = None, leaf_cap=64, precision=CRK_MIXED, cm_level=0,
-                 stream=None, rebuild_every=1):
-        self.handle = crk_create(params(phys, leaf_cap, precision, cm_level, rebuild_every=rebuild_every),
-                                 stream)
+                 stream=None, rebuild_every=1, pm_grid=0):
+        self.handle = crk_create(params(phys, leaf_cap, precision, cm_level, rebuild_every=rebuild_every,
+                                        pm_grid=pm_grid), stream)
 
     def load(self, box):
         crk_load(self.handle, box.pos, box.vel, box.mass, box.u, box.h, box.species)

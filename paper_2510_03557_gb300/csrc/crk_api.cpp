@@ -175,6 +175,7 @@ int reserve(crk_sim *s, int64_t n)
     RET(s->uhat.ensure(nn * rsize(s)));
     RET(s->acc_h.ensure(nn * r4));
     RET(s->acc_g.ensure(nn * r4));
+    if (s->prm.pm_grid > 0) RET(s->acc_pm.ensure(nn * 3 * sizeof(double)));
     RET(s->nbrc.ensure(nn * 4));
     RET(s->nbrh.ensure(nn * 8));
     RET(s->gravc.ensure(nn * 4));
@@ -206,6 +207,7 @@ PassArgs pass_args(crk_sim *s)
     a.uhat = s->uhat.p;
     a.acc_h = s->acc_h.p;
     a.acc_g = s->acc_g.p;
+    a.acc_pm = s->prm.pm_grid > 0 ? s->acc_pm.as<double>() : nullptr;
     a.nbr_count = s->nbrc.as<int32_t>();
     a.nbr_hash = s->nbrh.as<uint64_t>();
     a.grav_count = s->gravc.as<int32_t>();
@@ -433,6 +435,11 @@ int run_step(crk_sim *s, const double *dt_per_box, bool want_counts)
         mark(s, PH_KICK, 1);
     }
     RET(build_tree(s));
+    if (s->prm.pm_grid > 0) {
+        mark(s, PH_PM, 0);
+        RET(pm_accelerations(s, s->acc_pm.as<double>(), false));
+        mark(s, PH_PM, 1);
+    }
     PassArgs a = pass_args(s);
     if (!want_counts) {
         a.nbr_count = nullptr;
@@ -491,6 +498,7 @@ int load_impl(crk_sim *s, int nbox, const int64_t *counts, const crk_physics *ph
               const double *h, const uint8_t *species, int mem)
 {
     if (nbox < 1) return fail(CRK_EINVAL, "nbox must be >= 1");
+    if (nbox > 1 && s->prm.pm_grid > 0) return fail(CRK_EINVAL, "a mesh (pm_grid > 0) needs one box");
     if (mem != CRK_MEM_HOST && mem != CRK_MEM_DEVICE) return fail(CRK_EINVAL, "bad mem flag");
     int64_t n = 0;
     for (int b = 0; b < nbox; ++b) {
@@ -599,6 +607,8 @@ extern "C" int crk_create(const crk_params *params, void *cuda_stream, crk_sim *
     if (params->kernel != CRK_WENDLAND_C4) return fail(CRK_EINVAL, "unsupported kernel");
     if (params->cm_level < 0 || params->cm_level > 10) return fail(CRK_EINVAL, "cm_level in [0, 10]");
     if (params->rebuild_every < 0) return fail(CRK_EINVAL, "rebuild_every must be >= 0");
+    if (params->pm_grid != 0 && (params->pm_grid < 4 || params->pm_grid > 1024 || params->pm_grid % 2))
+        return fail(CRK_EINVAL, "pm_grid must be 0 or an even number in [4, 1024] (got %d)", params->pm_grid);
     crk_sim *s = new crk_sim();
     s->prm = *params;
     s->mixed = params->precision == CRK_MIXED;
@@ -807,6 +817,26 @@ extern "C" int crk_fof(crk_sim *s, double b, int species_mask, int64_t *group, i
     return CRK_OK;
 }
 
+extern "C" int crk_pm_accel(crk_sim *s, double *acc, int mem)
+{
+    if (!s || !acc) return fail(CRK_EINVAL, "null argument");
+    if (mem != CRK_MEM_HOST && mem != CRK_MEM_DEVICE) return fail(CRK_EINVAL, "bad mem flag");
+    if (s->prm.pm_grid <= 0) return fail(CRK_EINVAL, "the handle has no mesh (pm_grid = 0)");
+    if (s->nbox != 1) return fail(CRK_EINVAL, "no box loaded");
+    CK(cudaSetDevice(s->device));
+    const size_t n = (size_t)s->n;
+    double *dst = acc;
+    if (mem == CRK_MEM_HOST) {
+        RET(s->staging.ensure(std::max<size_t>(n, 1) * 3 * sizeof(double)));
+        dst = s->staging.as<double>();
+    }
+    RET(pm_accelerations(s, dst, true));
+    if (mem == CRK_MEM_HOST && n > 0)
+        CK(cudaMemcpyAsync(acc, dst, n * 3 * sizeof(double), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    return CRK_OK;
+}
+
 extern "C" int crk_autotune(crk_sim *s, const int *caps, int ncaps, int *best_cap, double *ms_out)
 {
     if (!s || !caps || ncaps < 1) return fail(CRK_EINVAL, "null argument or no candidate");
@@ -897,6 +927,7 @@ extern "C" int crk_get_timings(crk_sim *s, crk_timings *t)
     t->pairs_grav = s->npair_g;
     t->nleaves = s->nleaf;
     t->launches = s->launches;
+    t->pm_ms = s->acc_ms[PH_PM];
     return CRK_OK;
 }
 
@@ -915,8 +946,9 @@ extern "C" int crk_destroy(crk_sim *s)
                     &s->pm, &s->uhat, &s->acc_h, &s->acc_g, &s->nbrc, &s->nbrh, &s->gravc,
                     &s->gravh, &s->err, &s->nfloor, &s->partial, &s->sums, &s->staging,
                     &s->in_stage, &s->grp_cnt, &s->grp_off, &s->grp_gas, &s->grp_all, &s->hfr, &s->gfr,
-                    &s->nl_j, &s->nl_row, &s->nl_len, &s->nl_cnt, &s->hsj, &s->fof_par};
+                    &s->nl_j, &s->nl_row, &s->nl_len, &s->nl_cnt, &s->hsj, &s->fof_par, &s->acc_pm};
     for (DBuf *b : bufs) b->release();
+    pm_release(s);
     for (int k = 0; k < 3; ++k) {
         s->lv_u32[k].release();
         s->lv_c[k].release();
@@ -954,6 +986,7 @@ size_t pool_bytes_per_particle(const crk_sim *s)
 int pool_init(crk_sim *s, int max_slots)
 {
     if (max_slots < 1) return fail(CRK_EINVAL, "max_slots must be >= 1");
+    if (s->prm.pm_grid > 0) return fail(CRK_EINVAL, "the service takes no mesh (pm_grid must be 0)");
     CK(cudaSetDevice(s->device));
     int sb = 0;
     while ((1 << sb) < max_slots + 1) ++sb;

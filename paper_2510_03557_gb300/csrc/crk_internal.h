@@ -89,6 +89,7 @@ struct PassArgs {
     void *uhat;              // R[n] predicted u
     void *acc_h;             // R4[n]: hydro acceleration, du/dt
     void *acc_g;             // R4[n]: gravity acceleration
+    const double *acc_pm;    // FP64 3n: long-range mesh acceleration (null: no mesh)
     int32_t *nbr_count;      // optional
     uint64_t *nbr_hash;
     int32_t *grav_count;

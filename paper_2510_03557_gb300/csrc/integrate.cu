@@ -74,6 +74,11 @@ __global__ void final_kick_k(PassArgs a, unsigned long long *nfloor)
         ay = (double)g.y;
         az = (double)g.z;
     }
+    if (a.acc_pm) {
+        ax = __dadd_rn(ax, a.acc_pm[3 * k]);
+        ay = __dadd_rn(ay, a.acc_pm[3 * k + 1]);
+        az = __dadd_rn(az, a.acc_pm[3 * k + 2]);
+    }
     a.s.vx[k] = __dadd_rn(a.s.vx[k], __dmul_rn(hdt, ax));
     a.s.vy[k] = __dadd_rn(a.s.vy[k], __dmul_rn(hdt, ay));
     a.s.vz[k] = __dadd_rn(a.s.vz[k], __dmul_rn(hdt, az));
@@ -130,6 +135,11 @@ __global__ void rate_sums_k(PassArgs a, double *partial)
             v[3] += m * ((double)r1.x * (double)hh.x + (double)r1.y * (double)hh.y +
                          (double)r1.z * (double)hh.z + (double)hh.w);
         }
+        if (a.acc_pm) {
+            ax += a.acc_pm[3 * k];
+            ay += a.acc_pm[3 * k + 1];
+            az += a.acc_pm[3 * k + 2];
+        }
         v[0] += m * ax;
         v[1] += m * ay;
         v[2] += m * az;
@@ -182,9 +192,16 @@ __global__ void unpermute_outputs_k(PassArgs a, double *acc, double *dudt, doubl
         r6 = reinterpret_cast<const R4 *>(a.hrec[6])[k];
     }
     if (acc) {
-        acc[3 * (int64_t)o + 0] = (double)hh.x + (double)g.x;
-        acc[3 * (int64_t)o + 1] = (double)hh.y + (double)g.y;
-        acc[3 * (int64_t)o + 2] = (double)hh.z + (double)g.z;
+        double ax = (double)hh.x + (double)g.x, ay = (double)hh.y + (double)g.y,
+               az = (double)hh.z + (double)g.z;
+        if (a.acc_pm) {
+            ax += a.acc_pm[3 * k];
+            ay += a.acc_pm[3 * k + 1];
+            az += a.acc_pm[3 * k + 2];
+        }
+        acc[3 * (int64_t)o + 0] = ax;
+        acc[3 * (int64_t)o + 1] = ay;
+        acc[3 * (int64_t)o + 2] = az;
     }
     if (dudt) dudt[o] = (double)hh.w;
     if (rho) rho[o] = (double)r2.x;

@@ -43,7 +43,7 @@ struct DBuf {
     template <typename T> T *as() const { return static_cast<T *>(p); }
 };
 
-enum Phase { PH_TREE, PH_PAIRS, PH_D, PH_M, PH_H, PH_G, PH_KDK, PH_KICK, PH_N };
+enum Phase { PH_TREE, PH_PAIRS, PH_D, PH_M, PH_H, PH_G, PH_KDK, PH_KICK, PH_PM, PH_N };
 
 }  // namespace crk
 
@@ -82,6 +82,9 @@ struct crk_sim {
     DBuf nbrc, nbrh, gravc, gravh;
     DBuf nl_j, nl_row, nl_len, nl_cnt;  // hydro neighbour lists
     DBuf fof_par;                       // friends-of-friends parents and group count
+    DBuf pm_mesh, pm_modes, acc_pm;     // long-range mesh: density + 3 fields, 4 spectra, FP64 3n
+    int pm_ng = 0;                      // mesh side of the cuFFT plans (0: none)
+    int pm_fwd = 0, pm_inv = 0;         // cuFFT plan handles (real-to-complex, complex-to-real)
     int64_t nl_rows = 0;
     DBuf err, nfloor, partial, sums;
     DBuf staging, in_stage;
@@ -120,6 +123,12 @@ int pool_snapshot(crk_sim *s, int slot, int64_t n, double *dev);
 int pool_extract(crk_sim *s, int slot, int64_t n, double *pos, double *vel, double *u);
 int pool_remove(crk_sim *s, int slot, int64_t n);
 int pool_step(crk_sim *s, const double *dt_per_slot);
+
+// Long-range mesh gravity (pm.cu): FP64 accelerations of the current state
+// into acc (3n doubles, sorted order, or load order when `load_order`), on
+// the handle's stream.  Needs prm.pm_grid > 0 and one box.
+int pm_accelerations(crk_sim *s, double *acc, bool load_order);
+void pm_release(crk_sim *s);
 size_t pool_bytes_per_particle(const crk_sim *s);
 
 }  // namespace crk

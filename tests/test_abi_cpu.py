@@ -74,3 +74,13 @@ def test_binding_rejects_mixed_memory_kinds(libcrk):
     assert libcrk._mem_of(None, libcrk.CRK_MEM_HOST) == libcrk.CRK_MEM_HOST
     p, m, keep = libcrk._ptr(np.zeros(4), np.float64)
     assert m == libcrk.CRK_MEM_HOST and keep.dtype == np.float64
+
+
+@pytest.mark.parametrize("pm_grid", [-2, 2, 7, 2048])
+def test_create_rejects_bad_mesh_sizes_before_touching_the_device(libcrk, pm_grid):
+    """pm_grid is 0 or an even number in [4, 1024]; the check runs before
+    any CUDA call, so it answers here without a GPU."""
+    p = libcrk.params(pm_grid=pm_grid)
+    h = ctypes.c_void_p()
+    rc = libcrk.lib().crk_create(ctypes.byref(p), None, ctypes.byref(h))
+    assert rc == libcrk.CRK_EINVAL and "pm_grid" in libcrk.crk_last_error()
