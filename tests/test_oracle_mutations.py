@@ -51,3 +51,42 @@ def test_pins_catch_planted_mistake(tmp_path, name):
                         "tests/test_oracle_pins.py"], cwd=work, capture_output=True, text=True,
                        timeout=600)
     assert r.returncode == 1, f"mutation {name} survived:\n{r.stdout[-2000:]}"
+
+
+# Mistakes planted in the numpy parts of the oracle, each caught by that
+# module's own pins.
+PY_MUTATIONS = {
+    "pm_filter_half_width": ("pm.py", "np.exp(-k2 * r_s * r_s)", "np.exp(-0.5 * k2 * r_s * r_s)"),
+    "pm_one_window_undone": ("pm.py", "/ (k2 * C * C)", "/ (k2 * C)"),
+    "pm_cells_at_corners": ("pm.py", "s = pos / d - 0.5", "s = pos / d"),
+    "pm_gradient_sign": ("pm.py", "-1j * kd * phi", "1j * kd * phi"),
+    "bins_predictor_as_if_step_ended": ("bins.py", "tau = (2 * (s + 1 - s0) - Lb) * (0.5 * d)",
+                                        "tau = Lb * (0.5 * d)"),
+    "bins_ignore_sync": ("bins.py", "return np.maximum(b, b_sync)", "return b"),
+    "bins_close_every_particle": ("bins.py", "vel = np.where(active[:, None], vel + hdt[:, None] * acc, vel)",
+                                  "vel = vel + hdt[:, None] * acc"),
+    "bins_courant_on_c_squared": ("bins.py", "dc = np.where(hot, (courant * h) / c, np.inf)",
+                                  "dc = np.where(hot, (courant * h) / (c * c), np.inf)"),
+}
+PY_PINS = {"pm.py": "tests/test_oracle_pm.py", "bins.py": "tests/test_oracle_bins.py"}
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(PY_MUTATIONS))
+def test_pins_catch_planted_mistake_in_numpy_oracle(tmp_path, name):
+    fname, before, after = PY_MUTATIONS[name]
+    src = open(os.path.join(ROOT, "oracle", fname)).read()
+    assert src.count(before) == 1, name
+    work = tmp_path / "tree"
+    shutil.copytree(os.path.join(ROOT, "oracle"), work / "oracle",
+                    ignore=shutil.ignore_patterns("_build", "__pycache__"))
+    shutil.copytree(os.path.join(ROOT, "tests"), work / "tests",
+                    ignore=shutil.ignore_patterns("__pycache__"))
+    os.makedirs(work / "paper_2510_03557_gb300")
+    for f in ("__init__.py", "workloads.py"):
+        shutil.copy(os.path.join(ROOT, "paper_2510_03557_gb300", f), work / "paper_2510_03557_gb300" / f)
+    shutil.copy(os.path.join(ROOT, "pytest.ini"), work / "pytest.ini")
+    (work / "oracle" / fname).write_text(src.replace(before, after))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:randomly", PY_PINS[fname]],
+                       cwd=work, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 1, f"mutation {name} survived:\n{r.stdout[-2000:]}"
