@@ -229,6 +229,37 @@ int crk_fof(crk_sim *sim, double b, int species_mask, int64_t *group, int64_t *n
  * (null handle, pm_grid = 0, bad mem flag), CRK_ENOMEM, CRK_ECUDA. */
 int crk_pm_accel(crk_sim *sim, double *acc, int mem);
 
+/* Hierarchical (block) time steps: nlong long steps of dt_long, each cut into
+ * 2^depth substeps (paper Sec. II and IV-B1: particles grouped into
+ * power-of-two timestep bins that follow local conditions; forces evaluated
+ * only for the active leaves of a substep; leaves built once per long step
+ * and their boxes grown in its substeps).  A particle in bin b (0..depth)
+ * takes steps of dt_long / 2^b starting at multiples of its step.  Substep s:
+ * opening kick v += dt_b/2 a, u += dt_b/2 du of the particles whose step
+ * starts at s; drift of all by dt_long / 2^depth; forces at the substep's end
+ * for the particles whose step ends there (every particle's velocity and u
+ * predicted to that time: v + tau a, u + tau du, tau = time since its step
+ * started - dt_b/2); closing kick of those; and a new bin for each: the
+ * shallowest b with dt_long / 2^b <= min(sqrt(2 eta eps_soft / |a|),
+ * courant h / c) (the first term only when eps_soft > 0, the second for gas,
+ * c = sqrt(gamma (gamma - 1) u)), at most depth, and never a bin whose steps
+ * do not start at that time.  Bins at the start of the call come from the
+ * stored rates (a force evaluation first when there are none).  The passes
+ * of a substep run only over the leaves holding an active particle (hydro,
+ * gravity), their hydro neighbour leaves (corrections) and the neighbours of
+ * those (density, lists).  active_counts (optional, host, nlong * 2^depth
+ * entries) gets the number of active particles of every substep.  Every
+ * state update is FP64 with each product and sum rounded on its own.
+ * depth = 0 is crk_step.  Not with a mesh (pm_grid > 0).  Errors: CRK_EINVAL
+ * (dt_long <= 0, depth outside [0, 20], nlong < 0, eta or courant <= 0),
+ * the errors of crk_step. */
+int crk_step_bins(crk_sim *sim, double dt_long, int depth, int nlong, double eta, double courant,
+                  int64_t *active_counts);
+
+/* Timestep bin of every particle (load order, n bytes where `mem` says) as
+ * the last crk_step_bins left it.  Synchronises the stream. */
+int crk_get_bins(crk_sim *sim, uint8_t *bins, int mem);
+
 /* Leaf-capacity autotuner.  The paper sizes its base leaves by hand for its
  * hardware (Sec. IV-B1: several hundred particles per leaf on MI250X); here the
  * best capacity depends on the particle distribution.  Runs one force

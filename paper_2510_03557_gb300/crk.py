@@ -36,7 +36,8 @@ CRK_GAS = 1
 # Every function of the C ABI.
 ABI = ("crk_create", "crk_load", "crk_load_boxes", "crk_forces", "crk_step", "crk_step_boxes",
        "crk_get_state", "crk_set_state", "crk_get_sums", "crk_get_size", "crk_set_timing", "crk_get_timings",
-       "crk_destroy", "crk_fof", "crk_pm_accel", "crk_autotune", "crk_service_create", "crk_submit", "crk_poll", "crk_service_destroy",
+       "crk_destroy", "crk_fof", "crk_pm_accel", "crk_step_bins", "crk_get_bins",
+       "crk_autotune", "crk_service_create", "crk_submit", "crk_poll", "crk_service_destroy",
        "crk_service_snapshot", "crk_service_cancel",
        "crk_neighbours_noalloc", "crk_last_error")
 CRK_NOALLOC_MAX_N = 262144
@@ -310,6 +311,26 @@ def crk_pm_accel(sim, out=None):
     if mem == CRK_MEM_HOST and keep is not out:
         raise TypeError("out must be a contiguous float64 array")
     _check(lib().crk_pm_accel(sim, p, ctypes.c_int(mem)))
+    return out
+
+
+def crk_step_bins(sim, dt_long: float, depth: int, nlong: int = 1, eta: float = 0.025,
+                  courant: float = 0.25):
+    """Hierarchical time steps (crk_step_bins); returns the number of active
+    particles of every substep (int64, nlong * 2^depth)."""
+    counts = np.zeros((max(nlong, 0) << depth) if 0 <= depth <= 20 else 0, np.int64)
+    _check(lib().crk_step_bins(sim, ctypes.c_double(dt_long), ctypes.c_int(depth), ctypes.c_int(nlong),
+                               ctypes.c_double(eta), ctypes.c_double(courant),
+                               counts.ctypes.data_as(ctypes.c_void_p)))
+    return counts
+
+
+def crk_get_bins(sim, n: int | None = None) -> np.ndarray:
+    """Timestep bin of every particle, load order (crk_get_bins)."""
+    if n is None:
+        n = crk_get_size(sim)[0]
+    out = np.zeros(n, np.uint8)
+    _check(lib().crk_get_bins(sim, out.ctypes.data_as(ctypes.c_void_p), ctypes.c_int(CRK_MEM_HOST)))
     return out
 
 

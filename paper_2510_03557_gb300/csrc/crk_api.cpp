@@ -115,6 +115,8 @@ int alloc_state(DBuf *b, State &s, int64_t n)
     s.slot = b[14].as<uint32_t>();
     RET(b[15].ensure(nd * sizeof(uint32_t)));
     s.id = b[15].as<uint32_t>();
+    RET(b[16].ensure(nd));
+    s.bin = b[16].as<uint8_t>();
     return CRK_OK;
 }
 
@@ -223,6 +225,8 @@ PassArgs pass_args(crk_sim *s)
     a.gall = s->grp_all.as<uint2>();
     a.n_ggas = s->n_ggas;
     a.n_gall = s->n_gall;
+    a.bsub = -1;
+    a.lmap = nullptr;
     return a;
 }
 
@@ -300,8 +304,10 @@ int reset_error(crk_sim *s)
     return CRK_OK;
 }
 
-// Tree build (S1) and leaf-pair lists (S2).
-int build_tree(crk_sim *s)
+// Tree build (S1) and leaf-pair lists (S2).  mode 0: sort every
+// rebuild_every-th call; 1: sort now; 2: keep the leaves while they are valid.
+enum { TREE_RULE = 0, TREE_SORT = 1, TREE_KEEP = 2 };
+int build_tree(crk_sim *s, int mode = TREE_RULE)
 {
     const int64_t n = s->n;
     cudaStream_t st = s->st;
@@ -312,7 +318,9 @@ int build_tree(crk_sim *s)
     // with the particles (paper Sec. IV-B1): no sort, only new bounds, node
     // boxes and pair lists.  Added or removed particles force a rebuild.
     const int every = std::max(s->prm.rebuild_every, 1);
-    const bool reuse = s->tree_valid && s->n_dead == 0 && s->since_rebuild + 1 < every;
+    bool reuse = s->tree_valid && s->n_dead == 0 && s->since_rebuild + 1 < every;
+    if (mode == TREE_SORT) reuse = false;
+    else if (mode == TREE_KEEP) reuse = s->tree_valid && s->n_dead == 0;
     if (reuse) {
         ++s->since_rebuild;
     } else {
@@ -335,7 +343,7 @@ int build_tree(crk_sim *s)
         launch_leaf_kd_order(s->sa, s->lv, s->nleaf, vo, st);
         launch_permute(s->sa, s->sb, vo, n, st);
         std::swap(s->sa, s->sb);
-        for (int k = 0; k < 16; ++k) std::swap(s->stA[k], s->stB[k]);
+        for (int k = 0; k < 17; ++k) std::swap(s->stA[k], s->stB[k]);
         s->n = nlive;
         s->n_dead = 0;
         s->since_rebuild = 0;
@@ -392,11 +400,11 @@ int build_tree(crk_sim *s)
 static int size_hydro_lists(crk_sim *s, PassArgs &a, bool want_counts)
 {
     cudaStream_t st = s->st;
-    if (s->n_ggas == 0) {
+    if (a.n_ggas == 0) {
         s->nl_rows = 0;
         return CRK_OK;
     }
-    const size_t ng = (size_t)s->n_ggas;
+    const size_t ng = (size_t)a.n_ggas;
     RET(s->nl_cnt.ensure((size_t)std::max<int64_t>(s->n, 1) * 4));
     RET(s->nl_len.ensure(ng * 4));
     RET(s->nl_row.ensure(ng * 4));
@@ -405,7 +413,7 @@ static int size_hydro_lists(crk_sim *s, PassArgs &a, bool want_counts)
     a.nl_row = s->nl_row.as<uint32_t>();
     launch_hlist_count(a, s->mixed ? 1 : 0, s->cap, want_counts, st);
     uint32_t *sc = s->scalars.as<uint32_t>();
-    scan_exclusive_u32(a.nl_len, a.nl_row, s->n_ggas, sc + 5, s->scan_tmp.as<uint32_t>(), st);
+    scan_exclusive_u32(a.nl_len, a.nl_row, a.n_ggas, sc + 5, s->scan_tmp.as<uint32_t>(), st);
     CK(cudaMemcpyAsync(s->host_scalars + 5, sc + 5, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     s->nl_rows = s->host_scalars[5];
@@ -714,6 +722,172 @@ extern "C" int crk_step_boxes(crk_sim *s, const double *dt, int nsteps)
     return CRK_OK;
 }
 
+// One substep of the hierarchical steps (paper Sec. II and IV-B1): opening
+// kicks and the drift, leaves sorted at the start of the long step and kept
+// (boxes grown) in its other substeps, then the passes over the active part
+// only: forces (hydro, gravity) for the leaves holding a particle whose step
+// ends now, corrections for those and their hydro neighbour leaves, density
+// and lists one ring of leaves further out; closing kicks and new bins.
+static int run_substep(crk_sim *s, int sub, int depth, double dt_long, double eta, double courant,
+                       unsigned long long *nactive)
+{
+    cudaStream_t st = s->st;
+    const double d = std::ldexp(dt_long, -depth);
+    RET(reset_error(s));
+    if (s->timing) cudaEventRecord(s->ev_all[0], st);
+    for (bool &r : s->recorded) r = false;
+    const int64_t launches0 = launches_so_far();
+    mark(s, PH_KICK, 0);
+    launch_kick_drift_bins(s->sa, s->boxes_d.as<BoxDev>(), s->n, sub, depth, d,
+                           s->nfloor.as<unsigned long long>(), st);
+    mark(s, PH_KICK, 1);
+    RET(build_tree(s, sub == 0 ? TREE_SORT : TREE_KEEP));
+    // particles active at t_(sub+1): bin >= depth - trailing_zeros(sub + 1)
+    const int t = sub + 1;
+    int tz = 0;
+    while (!((t >> tz) & 1)) ++tz;
+    const int bmin = depth - tz;
+    const size_t nl = (size_t)std::max(s->nleaf, 1);
+    RET(s->bflag.ensure(3 * nl));
+    uint8_t *fh = s->bflag.as<uint8_t>(), *fm = fh + nl, *fd = fm + nl;
+    launch_leaf_active(s->lv, s->nleaf, s->sa.bin, bmin, fh, st);
+    launch_leaf_expand(s->hrow.as<uint32_t>(), s->hcol.as<uint32_t>(), s->nleaf, fh, fm, st);
+    launch_leaf_expand(s->hrow.as<uint32_t>(), s->hcol.as<uint32_t>(), s->nleaf, fm, fd, st);
+    const size_t ng = (size_t)std::max<uint32_t>(std::max(s->n_ggas, s->n_gall), 1);
+    for (int k = 0; k < 4; ++k) RET(s->bgrp[k].ensure(ng * sizeof(uint2)));
+    for (int k = 0; k < 2; ++k) RET(s->bmap[k].ensure(ng * sizeof(uint32_t)));
+    RET(s->bkeep.ensure(ng * sizeof(uint32_t)));
+    RET(s->bpos.ensure(ng * sizeof(uint32_t)));
+    uint32_t *sc = s->scalars.as<uint32_t>(), *tmp = s->scan_tmp.as<uint32_t>();
+    uint32_t *keep = s->bkeep.as<uint32_t>(), *pos = s->bpos.as<uint32_t>();
+    uint2 *gD = s->bgrp[0].as<uint2>(), *gM = s->bgrp[1].as<uint2>(), *gH = s->bgrp[2].as<uint2>(),
+          *gG = s->bgrp[3].as<uint2>();
+    launch_group_select(s->grp_gas.as<uint2>(), s->n_ggas, fd, keep, pos, sc + 8, tmp, gD, nullptr, st);
+    launch_group_select(s->grp_all.as<uint2>(), s->n_gall, fh, keep, pos, sc + 11, tmp, gG, nullptr, st);
+    CK(cudaMemcpyAsync(s->host_scalars + 8, sc + 8, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(s->host_scalars + 11, sc + 11, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const uint32_t nD = s->host_scalars[8], nG = s->host_scalars[11];
+    // the moments and hydro groups are taken from the density groups, so
+    // that each keeps the list row the density pass wrote for it
+    launch_group_select(gD, nD, fm, keep, pos, sc + 9, tmp, gM, s->bmap[0].as<uint32_t>(), st);
+    launch_group_select(gD, nD, fh, keep, pos, sc + 10, tmp, gH, s->bmap[1].as<uint32_t>(), st);
+    CK(cudaMemcpyAsync(s->host_scalars + 9, sc + 9, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const uint32_t nM = s->host_scalars[9], nH = s->host_scalars[10];
+
+    PassArgs a = pass_args(s);
+    a.nbr_count = nullptr;
+    a.nbr_hash = nullptr;
+    a.grav_count = nullptr;
+    a.grav_hash = nullptr;
+    a.bsub = sub;
+    a.bdepth = depth;
+    a.bd = d;
+    const int mixed = s->mixed ? 1 : 0;
+    PassArgs aD = a, aG = a;
+    aD.ggas = gD;
+    aD.n_ggas = nD;
+    aG.gall = gG;
+    aG.n_gall = nG;
+    mark(s, PH_D, 0);
+    launch_records(a, mixed, st);
+    RET(size_hydro_lists(s, aD, false));
+    PassArgs aM = aD, aH = aD;
+    aM.ggas = gM;
+    aM.n_ggas = nM;
+    aM.lmap = s->bmap[0].as<uint32_t>();
+    aH.ggas = gH;
+    aH.n_ggas = nH;
+    aH.lmap = s->bmap[1].as<uint32_t>();
+    launch_density(aD, mixed, s->cap, false, st);
+    mark(s, PH_D, 1);
+    mark(s, PH_M, 0);
+    launch_moments(aM, mixed, s->cap, st);
+    mark(s, PH_M, 1);
+    mark(s, PH_H, 0);
+    launch_hydro(aH, mixed, s->cap, st);
+    mark(s, PH_H, 1);
+    mark(s, PH_G, 0);
+    launch_gravity(aG, mixed, s->cap, false, st);
+    mark(s, PH_G, 1);
+    mark(s, PH_KDK, 0);
+    launch_close_bins(a, mixed, sub, depth, d, dt_long, eta, courant, bmin, s->nfloor.as<unsigned long long>(),
+                      nactive, st);
+    mark(s, PH_KDK, 1);
+    if (s->timing) cudaEventRecord(s->ev_all[1], st);
+    CK(cudaGetLastError());
+    RET(read_error(s));
+    if (s->timing) {
+        for (int ph = 0; ph < PH_N; ++ph) {
+            if (!s->recorded[ph]) continue;
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, s->ev[ph][0], s->ev[ph][1]) == cudaSuccess) s->acc_ms[ph] += ms;
+            else cudaGetLastError();
+        }
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, s->ev_all[0], s->ev_all[1]) == cudaSuccess) s->total_ms += ms;
+        else cudaGetLastError();
+        s->calls++;
+        s->launches += launches_so_far() - launches0;
+    }
+    return CRK_OK;
+}
+
+extern "C" int crk_step_bins(crk_sim *s, double dt_long, int depth, int nlong, double eta, double courant,
+                             int64_t *active_counts)
+{
+    if (!s) return fail(CRK_EINVAL, "null handle");
+    if (!(dt_long > 0.0) || !std::isfinite(dt_long)) return fail(CRK_EINVAL, "dt_long must be finite and > 0");
+    if (depth < 0 || depth > 20) return fail(CRK_EINVAL, "depth in [0, 20]");
+    if (nlong < 0) return fail(CRK_EINVAL, "nlong must be >= 0");
+    if (!(eta > 0.0) || !(courant > 0.0) || !std::isfinite(eta) || !std::isfinite(courant))
+        return fail(CRK_EINVAL, "eta and courant must be finite and > 0");
+    if (s->prm.pm_grid > 0) return fail(CRK_EINVAL, "hierarchical steps take no mesh (pm_grid must be 0)");
+    CK(cudaSetDevice(s->device));
+    const int nsub = 1 << depth;
+    const size_t ncount = (size_t)nlong * (size_t)nsub;
+    if (s->n == 0) {
+        if (active_counts)
+            for (size_t k = 0; k < ncount; ++k) active_counts[k] = 0;
+        return CRK_OK;
+    }
+    if (!s->have_forces) RET(run_step(s, nullptr, false));
+    // every particle starts the long step with the bin of its stored rates
+    launch_assign_bins(s->sa, s->boxes_d.as<BoxDev>(), s->n, dt_long, depth, eta, courant, s->st);
+    RET(s->bcount.ensure(std::max<size_t>(ncount, 1) * sizeof(unsigned long long)));
+    unsigned long long *cnt = s->bcount.as<unsigned long long>();
+    CK(cudaMemsetAsync(cnt, 0, std::max<size_t>(ncount, 1) * sizeof(unsigned long long), s->st));
+    for (int L = 0; L < nlong; ++L)
+        for (int sub = 0; sub < nsub; ++sub)
+            RET(run_substep(s, sub, depth, dt_long, eta, courant, cnt + (size_t)L * nsub + sub));
+    if (active_counts && ncount > 0) {
+        std::vector<unsigned long long> h(ncount);
+        CK(cudaMemcpyAsync(h.data(), cnt, ncount * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s->st));
+        CK(cudaStreamSynchronize(s->st));
+        for (size_t k = 0; k < ncount; ++k) active_counts[k] = (int64_t)h[k];
+    }
+    return CRK_OK;
+}
+
+extern "C" int crk_get_bins(crk_sim *s, uint8_t *bins, int mem)
+{
+    if (!s || (!bins && s->n > 0)) return fail(CRK_EINVAL, "null argument");
+    if (mem != CRK_MEM_HOST && mem != CRK_MEM_DEVICE) return fail(CRK_EINVAL, "bad mem flag");
+    CK(cudaSetDevice(s->device));
+    const size_t n = (size_t)s->n;
+    if (n == 0) return CRK_OK;
+    if (mem == CRK_MEM_DEVICE) {
+        launch_unpermute_bins(s->sa, s->n, bins, s->st);
+    } else {
+        RET(s->staging.ensure(n));
+        launch_unpermute_bins(s->sa, s->n, s->staging.as<uint8_t>(), s->st);
+        CK(cudaMemcpyAsync(bins, s->staging.p, n, cudaMemcpyDeviceToHost, s->st));
+    }
+    CK(cudaStreamSynchronize(s->st));
+    return CRK_OK;
+}
+
 extern "C" int crk_step(crk_sim *s, double dt, int nsteps)
 {
     if (!s) return fail(CRK_EINVAL, "null handle");
@@ -936,7 +1110,7 @@ extern "C" int crk_destroy(crk_sim *s)
     if (!s) return CRK_OK;
     cudaSetDevice(s->device);
     cudaStreamSynchronize(s->st);
-    for (int k = 0; k < 16; ++k) {
+    for (int k = 0; k < 17; ++k) {
         s->stA[k].release();
         s->stB[k].release();
     }
@@ -946,7 +1120,9 @@ extern "C" int crk_destroy(crk_sim *s)
                     &s->pm, &s->uhat, &s->acc_h, &s->acc_g, &s->nbrc, &s->nbrh, &s->gravc,
                     &s->gravh, &s->err, &s->nfloor, &s->partial, &s->sums, &s->staging,
                     &s->in_stage, &s->grp_cnt, &s->grp_off, &s->grp_gas, &s->grp_all, &s->hfr, &s->gfr,
-                    &s->nl_j, &s->nl_row, &s->nl_len, &s->nl_cnt, &s->hsj, &s->fof_par, &s->acc_pm};
+                    &s->nl_j, &s->nl_row, &s->nl_len, &s->nl_cnt, &s->hsj, &s->fof_par, &s->acc_pm,
+                    &s->bflag, &s->bgrp[0], &s->bgrp[1], &s->bgrp[2], &s->bgrp[3], &s->bmap[0],
+                    &s->bmap[1], &s->bkeep, &s->bpos, &s->bcount};
     for (DBuf *b : bufs) b->release();
     pm_release(s);
     for (int k = 0; k < 3; ++k) {
@@ -1016,7 +1192,7 @@ static State shifted(const State &a, int64_t off)
     b.vx += off; b.vy += off; b.vz += off;
     b.u += off; b.m += off; b.h += off;
     b.ax += off; b.ay += off; b.az += off; b.du += off;
-    b.species += off; b.slot += off; b.id += off;
+    b.species += off; b.slot += off; b.id += off; b.bin += off;
     return b;
 }
 
@@ -1029,6 +1205,7 @@ static int pool_grow(crk_sim *s, int64_t need)
     RET(s->stA[13].ensure_keep((size_t)cap, keep, s->st));
     RET(s->stA[14].ensure_keep((size_t)cap * 4, keep * 4, s->st));
     RET(s->stA[15].ensure_keep((size_t)cap * 4, keep * 4, s->st));
+    RET(s->stA[16].ensure_keep((size_t)cap, keep, s->st));
     return reserve(s, cap);
 }
 

@@ -37,6 +37,7 @@ struct State {
     uint8_t *species;        // CRK_DM or CRK_GAS
     uint32_t *slot;          // box index
     uint32_t *id;            // original (load-order) index
+    uint8_t *bin;            // timestep bin of the hierarchical steps (steps of D_t / 2^bin)
 };
 
 // Leaves: runs of <= leaf_cap consecutive sorted particles of one
@@ -90,6 +91,11 @@ struct PassArgs {
     void *acc_h;             // R4[n]: hydro acceleration, du/dt
     void *acc_g;             // R4[n]: gravity acceleration
     const double *acc_pm;    // FP64 3n: long-range mesh acceleration (null: no mesh)
+    // hierarchical steps: forces at the end of substep bsub (-1: fixed step,
+    // the predictor takes the box's dt/2) of 2^bdepth substeps of length bd
+    int bsub, bdepth;
+    double bd;
+    const uint32_t *lmap;    // list row index of every group of ggas (null: the group's own index)
     int32_t *nbr_count;      // optional
     uint64_t *nbr_hash;
     int32_t *grav_count;
@@ -178,5 +184,20 @@ void launch_retire_slot(const State &s, int64_t n, uint32_t from, uint32_t to, c
 void launch_load_state(const State &s, int64_t n, const double *pos, const double *vel,
                        const double *mass, const double *u, const double *h,
                        const uint8_t *species, const uint32_t *slot_of, cudaStream_t st);
+
+// ---- hierarchical time steps (bins.cu) ----
+void launch_kick_drift_bins(const State &s, const BoxDev *boxes, int64_t n, int sub, int depth, double d,
+                            unsigned long long *nfloor, cudaStream_t st);
+void launch_close_bins(const PassArgs &a, int mixed, int sub, int depth, double d, double dt_long, double eta,
+                       double courant, int b_sync, unsigned long long *nfloor, unsigned long long *nactive,
+                       cudaStream_t st);
+void launch_assign_bins(const State &s, const BoxDev *boxes, int64_t n, double dt_long, int depth, double eta,
+                        double courant, cudaStream_t st);
+void launch_leaf_active(const Leaves &lv, int nleaf, const uint8_t *bin, int bmin, uint8_t *flag, cudaStream_t st);
+void launch_leaf_expand(const uint32_t *row, const uint32_t *col, int nleaf, const uint8_t *in, uint8_t *out,
+                        cudaStream_t st);
+void launch_group_select(const uint2 *groups, uint32_t n, const uint8_t *leaf_flag, uint32_t *keep, uint32_t *pos,
+                         uint32_t *total, uint32_t *tmp, uint2 *out, uint32_t *map, cudaStream_t st);
+void launch_unpermute_bins(const State &s, int64_t n, uint8_t *out, cudaStream_t st);
 
 }  // namespace crk

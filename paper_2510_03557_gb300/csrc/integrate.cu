@@ -269,6 +269,7 @@ __global__ void load_state_k(State s, int64_t n, const double *pos, const double
     s.species[k] = gas ? (uint8_t)CRK_GAS : (uint8_t)CRK_DM;
     s.slot[k] = slot_of[k];
     s.id[k] = (uint32_t)k;
+    s.bin[k] = 0;
 }
 
 // Input checks: positions in [0, L) of the particle's box, finite velocity,

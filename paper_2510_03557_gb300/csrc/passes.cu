@@ -489,15 +489,23 @@ __device__ __forceinline__ void rel_pos(const Vec4<R> &ri, const Leaves &lv, int
 }
 
 // ------------------------------------------------------------- records
-// Predictor values that enter the forces: v^ = v_half + dt/2 a_old,
-// u^ = max(u_half + dt/2 du_old, u_floor) (gas).  hrec1 = (v^, h).
+// Predictor values that enter the forces: v^ = v_half + tau a_old,
+// u^ = max(u_half + tau du_old, u_floor) (gas).  hrec1 = (v^, h).  Fixed
+// steps: tau = dt/2.  Hierarchical steps, forces at the end of substep s of
+// length d: tau = ((s + 1 - s0) - L/2) d for a particle whose steps of L
+// substeps started at s0 (dt/2 for the particles whose step ends now).
 template <typename R>
 __global__ void records_k(PassArgs a)
 {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= a.n) return;
     const BoxDev &bx = a.boxes[a.s.slot[k]];
-    const double hdt = bx.hdt;
+    double hdt = bx.hdt;
+    if (a.bsub >= 0) {
+        const int Lb = 1 << (a.bdepth - (int)a.s.bin[k]);
+        const int s0 = (a.bsub / Lb) * Lb;
+        hdt = __dmul_rn((double)(2 * (a.bsub + 1 - s0) - Lb), 0.5 * a.bd);
+    }
     const double vx = __dadd_rn(a.s.vx[k], __dmul_rn(hdt, a.s.ax[k]));
     const double vy = __dadd_rn(a.s.vy[k], __dmul_rn(hdt, a.s.ay[k]));
     const double vz = __dadd_rn(a.s.vz[k], __dmul_rn(hdt, a.s.az[k]));
@@ -790,7 +798,7 @@ struct ListPipe {
     __device__ __forceinline__ ListPipe(const PassArgs &a, uint32_t gi, uint32_t lane, uint32_t n,
                                         const uint32_t *srow)
     {
-        e0 = (size_t)a.nl_row[gi] * 32u + lane;
+        e0 = (size_t)a.nl_row[a.lmap ? a.lmap[gi] : gi] * 32u + lane;
         cnt = n;
         e1 = cnt > 0u ? a.nl_j[e0] : 0u;
         e2 = cnt > 1u ? a.nl_j[e0 + 32u] : 0u;

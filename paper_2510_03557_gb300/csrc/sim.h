@@ -72,7 +72,7 @@ struct crk_sim {
 
     // device memory
     DBuf boxes_d;
-    DBuf stA[16], stB[16];  // state arrays, double-buffered
+    DBuf stA[17], stB[17];  // state arrays, double-buffered
     State sa{}, sb{};
     DBuf keys, keys_alt, vals, vals_alt, counts, scan_tmp, flags, flag_scan, scalars;
     DBuf lv_u32[3], lv_sp, lv_c[3], lv_e[3], lv_h, lv_chunk[2];
@@ -85,6 +85,10 @@ struct crk_sim {
     DBuf pm_mesh, pm_modes, acc_pm;     // long-range mesh: density + 3 fields, 4 spectra, FP64 3n
     int pm_ng = 0;                      // mesh side of the cuFFT plans (0: none)
     int pm_fwd = 0, pm_inv = 0;         // cuFFT plan handles (real-to-complex, complex-to-real)
+    // hierarchical steps: leaf flags (active, moments, density), the four
+    // selected group lists (density, moments, hydro, gravity), the list rows of
+    // the moments and hydro groups, selection scratch, active counts
+    DBuf bflag, bgrp[4], bmap[2], bkeep, bpos, bcount;
     int64_t nl_rows = 0;
     DBuf err, nfloor, partial, sums;
     DBuf staging, in_stage;

@@ -218,7 +218,7 @@ __global__ void permute_k(State a, State b, const uint32_t *__restrict__ perm, i
     b.vx[k] = a.vx[p]; b.vy[k] = a.vy[p]; b.vz[k] = a.vz[p];
     b.u[k] = a.u[p]; b.m[k] = a.m[p]; b.h[k] = a.h[p];
     b.ax[k] = a.ax[p]; b.ay[k] = a.ay[p]; b.az[k] = a.az[p]; b.du[k] = a.du[p];
-    b.species[k] = a.species[p]; b.slot[k] = a.slot[p]; b.id[k] = a.id[p];
+    b.species[k] = a.species[p]; b.slot[k] = a.slot[p]; b.id[k] = a.id[p]; b.bin[k] = a.bin[p];
 }
 
 // ---------------------------------------------------------------- leaves
