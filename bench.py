@@ -222,6 +222,72 @@ def _rel_l2(x, ref):
     return float(d / r) if r > 0 else float(d)
 
 
+def run_bins(args):
+    """Hierarchical time steps on the clustered workload (2 x n^3, half in
+    512 Plummer spheres, kNN h): one long step of 2^depth substeps of the
+    initial Courant step d, against the fixed-step KDK that advances the same
+    time at step d (what every particle needs when the deepest one needs d).
+    The fixed-step time is measured over a few steps and scaled to 2^depth."""
+    import torch
+
+    from paper_2510_03557_gb300 import crk
+    from paper_2510_03557_gb300 import workloads as wl
+
+    torch.cuda.set_device(0)
+    crk.lib()
+    box = wl.clustered_box(args.n, seed=3)
+    phys = crk.box_physics(box)
+    stream = torch.cuda.Stream()
+    depth = args.bin_depth
+    d = box.dt
+    dt_long = d * (1 << depth)
+    s = crk.Sim(phys, leaf_cap=args.leaf_cap, precision=crk.CRK_MIXED, stream=stream)
+    s.load(box)
+    s.forces(counts=False)
+    crk.crk_set_timing(s.handle, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    with ClockSampler(0) as clocks:
+        e0.record(stream)
+        counts = crk.crk_step_bins(s.handle, dt_long, depth, 1, args.bin_eta, args.bin_courant)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms_bins = e0.elapsed_time(e1)
+    tim = crk.crk_get_timings(s.handle)
+    bins = crk.crk_get_bins(s.handle)
+    s.close()
+    f = crk.Sim(phys, leaf_cap=args.leaf_cap, precision=crk.CRK_MIXED, stream=stream)
+    f.load(box)
+    f.step(d, 1)
+    k = max(1, min(args.steps, 1 << depth))
+    torch.cuda.synchronize()
+    e0.record(stream)
+    f.step(d, k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_fixed = e0.elapsed_time(e1) / k * (1 << depth)
+    f.close()
+    calls = max(tim["calls"], 1)
+    line = {"metric": METRIC, "value": box.n * (1 << depth) / (ms_bins / 1e3), "unit": UNIT, "n_gpus": 1,
+            "steps": 1, "ms_per_step": ms_bins, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"clustered 2x{args.n}^3, hierarchical steps: one long step of "
+                                   f"2^{depth} substeps of d={d} (value: particles x substeps / time)",
+                       "particles": box.n, "leaf_cap": args.leaf_cap, "depth": depth,
+                       "eta": args.bin_eta, "courant": args.bin_courant},
+            "bins": {"long_step_ms": round(ms_bins, 3), "fixed_step_ms_same_time": round(ms_fixed, 3),
+                     "speedup": round(ms_fixed / ms_bins, 3),
+                     "bin_histogram_after": np.bincount(bins, minlength=depth + 1).tolist(),
+                     "active_per_substep": counts.tolist(),
+                     "active_fraction": round(float(counts.sum()) / (box.n * (1 << depth)), 5),
+                     "substep_breakdown_ms": {k2: round(tim[k2] / calls, 4) for k2 in
+                                              ("tree_ms", "pairs_ms", "density_ms", "moments_ms",
+                                               "hydro_ms", "gravity_ms", "kdk_ms")},
+                     "fixed_steps_timed": k},
+            "clocks": clocks.summary()}
+    print(json.dumps(line))
+
+
 def run_clustered(args):
     """Precision study on the clustered workload (2 x n^3, half uniform and
     half in 512 Plummer spheres, adaptive h): one force evaluation plus 5 KDK
@@ -434,7 +500,10 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="gaussian", choices=["gaussian", "clustered", "batched"],
+    ap.add_argument("--bin-depth", type=int, default=5, help="bins workload: substeps 2^depth")
+    ap.add_argument("--bin-eta", type=float, default=0.025)
+    ap.add_argument("--bin-courant", type=float, default=0.25)
+    ap.add_argument("--workload", default="gaussian", choices=["gaussian", "clustered", "batched", "bins"],
                     help="clustered: the precision study; batched: 64 boxes in one handle "
                          "(each prints its own JSON line)")
     ap.add_argument("--sample", type=int, default=64, help="oracle sample of the precision study")
@@ -446,6 +515,7 @@ def main():
                     help="KDK steps of the FP64 form (precision study: -1 = as many as the mixed form)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the FOF and long-range mesh legs")
     ap.add_argument("--serve-requests", type=int, default=192,
                     help="requests of the serving stream to run (0: skip)")
     ap.add_argument("--serve-leaf-cap", type=int, default=64)
@@ -458,6 +528,9 @@ def main():
         return
     if args.workload == "batched":
         run_batched(args)
+        return
+    if args.workload == "bins":
+        run_bins(args)
         return
 
     import torch
@@ -534,30 +607,33 @@ def main():
                   ("hydro_ms", tim["hydro_ms"]), ("gravity_ms", tim["gravity_ms"]),
                   ("kdk_ms", tim["kdk_ms"]))}
     launches = int(tim["launches"])
-    # friends-of-friends groups of the dark matter at b = 0.2 mean spacings
-    # (the call sorts a new tree for the current state, then links)
-    torch.cuda.synchronize()
-    t_f = time.perf_counter()
-    _, n_groups = crk.crk_fof(sim.handle, 0.2 / args.n, 1, N)
-    fof = {"ms": round((time.perf_counter() - t_f) * 1e3, 3), "groups": n_groups,
-           "linking_length": 0.2 / args.n, "species": "dm",
-           "note": "host wall time of crk_fof: tree build, links, labels, copy-out"}
+    fof = mesh = None
+    if not args.no_extras:
+        # friends-of-friends groups of the dark matter at b = 0.2 mean spacings
+        # (the call sorts a new tree for the current state, then links)
+        torch.cuda.synchronize()
+        t_f = time.perf_counter()
+        _, n_groups = crk.crk_fof(sim.handle, 0.2 / args.n, 1, N)
+        fof = {"ms": round((time.perf_counter() - t_f) * 1e3, 3), "groups": n_groups,
+               "linking_length": 0.2 / args.n, "species": "dm",
+               "note": "host wall time of crk_fof: tree build, links, labels, copy-out"}
     sim.close()
 
-    # ---------------- the same KDK step with the long-range mesh (FP64 PM, n^3 cells)
-    smesh = crk.Sim(phys, leaf_cap=args.leaf_cap, precision=crk.CRK_MIXED, stream=stream,
-                    rebuild_every=args.rebuild_every, pm_grid=args.n)
-    smesh.load(box)
-    smesh.step(dt, 2)
-    crk.crk_set_timing(smesh.handle, True)
-    smesh.step(dt, 3)
-    tmesh = crk.crk_get_timings(smesh.handle)
-    mcalls = max(tmesh["calls"], 1)
-    mesh = {"pm_grid": args.n, "pm_ms": round(tmesh["pm_ms"] / mcalls, 4),
-            "step_ms": round(tmesh["total_ms"] / mcalls, 4),
-            "note": "per KDK step, CUDA events on the handle's stream: deposit, cuFFT forward, "
-                    "Green's function, 3 cuFFT inverse, gather (FP64)"}
-    smesh.close()
+    if not args.no_extras:
+        # the same KDK step with the long-range mesh (FP64 PM, n^3 cells)
+        smesh = crk.Sim(phys, leaf_cap=args.leaf_cap, precision=crk.CRK_MIXED, stream=stream,
+                        rebuild_every=args.rebuild_every, pm_grid=args.n)
+        smesh.load(box)
+        smesh.step(dt, 2)
+        crk.crk_set_timing(smesh.handle, True)
+        smesh.step(dt, 3)
+        tmesh = crk.crk_get_timings(smesh.handle)
+        mcalls = max(tmesh["calls"], 1)
+        mesh = {"pm_grid": args.n, "pm_ms": round(tmesh["pm_ms"] / mcalls, 4),
+                "step_ms": round(tmesh["total_ms"] / mcalls, 4),
+                "note": "per KDK step, CUDA events on the handle's stream: deposit, cuFFT forward, "
+                        "Green's function, 3 cuFFT inverse, gather (FP64)"}
+        smesh.close()
 
     # ---------------- FP64 plain form on the same box
     fp64 = None
