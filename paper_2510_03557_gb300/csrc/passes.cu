@@ -50,6 +50,7 @@ constexpr double kGn = -(56.0 / 3.0) * kWn;
 // Abramowitz & Stegun 7.1.26 (Hastings): erfc(x) ~ t P(t) exp(-x^2),
 // t = 1/(1 + p x), |error| <= 1.5e-7 for x >= 0.
 constexpr float kAsP = 0.3275911f;
+constexpr float kLog2e = 1.44269504088896341f;  // log2(e)
 constexpr float kAs1 = 0.254829592f, kAs2 = -0.284496736f, kAs3 = 1.421413741f,
                 kAs4 = -1.453152027f, kAs5 = 1.061405429f;
 constexpr double kTwoOverSqrtPi = 1.12837916709551257390;
@@ -69,6 +70,19 @@ template <> struct Real<float> {
     {
         float y;
         asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y;
+    }
+    __device__ static float rsqrt(float x)
+    {
+        float y;
+        asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y;
+    }
+    // 2^x by the hardware approximation (inputs and results here are normal)
+    __device__ static float exp2(float x)
+    {
+        float y;
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
         return y;
     }
     __device__ static float div(float a, float b) { return __fdividef(a, b); }
@@ -393,14 +407,15 @@ __device__ __forceinline__ float box_gap2(const WarpBox &b, float x, float y, fl
 // the warp's target box: candidate k < cJ (in a 32-chunk set in cm) is kept
 // when its distance to the box is below Rc, or below its own radius when
 // PERJ (hydro: 2 h_j from hrec1, whose square also goes to h2j).  Writes
-// tile[0, K) and slot[0, K) (k of each kept candidate), pads the tile to a
-// multiple of 32 with far-away sentinels (h2j 0), and returns K.
+// tile[0, K) and slot[0, K) (k of each kept candidate), the record's w
+// multiplied by wscale, pads the tile to a multiple of 32 with far-away
+// sentinels (h2j 0), and returns K.
 template <typename R, bool PERJ>
 __device__ __forceinline__ uint32_t stage_cull(Vec4<R> *tile, uint8_t *slot, float *h2j,
                                                const Vec4<R> *__restrict__ src,
                                                const Vec4<R> *__restrict__ rec1, uint32_t sJ, uint32_t cJ,
                                                uint32_t cm, const WarpBox &wb, const CandFrame &f, float Rc,
-                                               uint32_t lane)
+                                               uint32_t lane, R wscale = (R)1)
 {
     uint32_t K = 0;
     const uint32_t nch = (cJ + 31u) / 32u;
@@ -429,6 +444,7 @@ __device__ __forceinline__ uint32_t stage_cull(Vec4<R> *tile, uint8_t *slot, flo
         const uint32_t bal = __ballot_sync(0xffffffffu, keep);
         if (keep) {
             const uint32_t pos = K + __popc(bal & ((1u << lane) - 1u));
+            v.w = wscale * v.w;
             tile[pos] = v;
             slot[pos] = (uint8_t)k;
             if (PERJ) h2j[pos] = Hj2;
@@ -1265,7 +1281,7 @@ __device__ __forceinline__ R split_S(R r, R inv2rs)
         const float u = (float)r * (float)inv2rs;
         const float tt = Real<float>::rcp(fmaf(kAsP, u, 1.0f));
         const float poly = tt * (kAs1 + tt * (kAs2 + tt * (kAs3 + tt * (kAs4 + tt * kAs5))));
-        const float e = __expf(-u * u);
+        const float e = Real<float>::exp2(-u * u * kLog2e);  // exp(-u^2) = 2^(-u^2 log2 e)
         return (R)(e * (poly + (float)kTwoOverSqrtPi * u));
     } else {
         const double u = (double)r * (double)inv2rs;
@@ -1275,8 +1291,13 @@ __device__ __forceinline__ R split_S(R r, R inv2rs)
 
 // The pair forces of the K staged candidates of one visit on this lane's
 // target, masked by the gravity predicate: r^2 < r_cut^2 in the pass's
-// precision, re-decided in FP64 inside the mixed form's guard band; the
-// target itself excluded.
+// precision, re-decided in FP64 inside the mixed form's guard band.  The
+// target itself adds f * (0, 0, 0) = 0 (r^2 + eps^2 is kept above 1e-24 so
+// that f stays finite when eps = 0); only the neighbour count and hash
+// exclude it explicitly.  A lane without a target (act false) computes a
+// duplicate of lane 0's sums that is never stored.
+constexpr float kMinS2 = 1e-24f;
+
 template <typename R, bool WRAP, bool COUNT>
 __device__ __forceinline__ void gravity_tile(const Vec4<R> *tile, const uint8_t *tslot, uint32_t K,
                                              const Target<R> &q, R L, R hL, R rc2, double rc2x, R gb, R e2,
@@ -1288,25 +1309,25 @@ __device__ __forceinline__ void gravity_tile(const Vec4<R> *tile, const uint8_t 
         const Vec4<R> rj = tile[j];
         R dx, dy, dz;
         const R r2 = sep2<R, WRAP>(rj, q, L, hL, dx, dy, dz);
-        bool in = act && r2 < rc2;
-        if (Real<R>::mixed && act && r2 >= rc2 - gb && r2 < rc2 + gb)
+        bool in = r2 < rc2;
+        if (Real<R>::mixed && fabs(r2 - rc2) < gb)
             in = exact_lt(s, i, sJ + tslot[j], Ld, rc2x);  // rare: pairs at the cut
-        if (same && sJ + tslot[j] == i) in = false;
+        if (COUNT && same && sJ + tslot[j] == i) in = false;
         const R r = Real<R>::sqrt_(r2);
         const R S = split_S<R>(r, inv2rs);
-        const R s2 = r2 + e2;
+        const R s2 = fmax(r2 + e2, (R)kMinS2);
         R inv3;
         if (Real<R>::mixed) {
-            const float is = rsqrtf((float)s2);
+            const float is = Real<float>::rsqrt((float)s2);
             inv3 = (R)(is * is * is);
         } else {
             inv3 = (R)1 / (s2 * Real<R>::sqrt_(s2));
         }
-        const R f = in ? Gc * rj.w * S * inv3 : (R)0;  // a_i += f (x_j - x_i)
+        const R f = in ? rj.w * S * inv3 : (R)0;  // a_i += f (x_j - x_i), rj.w = G m_j
         ax += f * dx;
         ay += f * dy;
         az += f * dz;
-        if (COUNT && in) {
+        if (COUNT && in && act) {
             ++nc;
             hs += mix64((uint64_t)s.id[sJ + tslot[j]]);
         }
@@ -1353,7 +1374,7 @@ __global__ void __launch_bounds__(kBlock) gravity_k(PassArgs a)
         if (cm == 0u) continue;
         __syncwarp();
         const uint32_t K = stage_cull<R, false>(tile, tslot, nullptr, pm, nullptr, sJ, cJ, cm, wb,
-                                                cand_frame<R>(a.lv, I, fr, Ld), Rc, lane);
+                                                cand_frame<R>(a.lv, I, fr, Ld), Rc, lane, Gc);
         __syncwarp();
         if (K == 0u) continue;
         const Target<R> q = target_in_frame(ri, fr);
