@@ -182,6 +182,8 @@ int reserve(crk_sim *s, int64_t n)
     RET(s->nbrh.ensure(nn * 8));
     RET(s->gravc.ensure(nn * 4));
     RET(s->gravh.ensure(nn * 8));
+    RET(s->cnt_by_id.ensure(nn * 4));
+    RET(s->nl_retry.ensure(16));
     RET(s->err.ensure(16));
     RET(s->nfloor.ensure(16));
     RET(s->partial.ensure((size_t)sums_blocks(n) * 4 * 8 + 64));
@@ -227,6 +229,8 @@ PassArgs pass_args(crk_sim *s)
     a.n_gall = s->n_gall;
     a.bsub = -1;
     a.lmap = nullptr;
+    a.nl_bound = 0;
+    a.nl_retry = s->nl_retry.as<uint32_t>();
     return a;
 }
 
@@ -394,10 +398,11 @@ int build_tree(crk_sim *s, int mode = TREE_RULE)
     return CRK_OK;
 }
 
-// Sizes the hydro neighbour lists: every gas particle's entry count and
-// every group's row count (count pass), row offsets by a scan, then the
-// list storage (one synchronisation for the total).
-static int size_hydro_lists(crk_sim *s, PassArgs &a, bool want_counts)
+// Sizes the hydro neighbour lists: every group's row count, from a count
+// pass over the candidates, or (use_bounds) from the previous step's list
+// sizes with a margin; row offsets by a scan, then the list storage (one
+// synchronisation for the total).
+static int size_hydro_lists(crk_sim *s, PassArgs &a, bool want_counts, bool use_bounds = false)
 {
     cudaStream_t st = s->st;
     if (a.n_ggas == 0) {
@@ -411,7 +416,13 @@ static int size_hydro_lists(crk_sim *s, PassArgs &a, bool want_counts)
     a.nl_cnt = s->nl_cnt.as<uint32_t>();
     a.nl_len = s->nl_len.as<uint32_t>();
     a.nl_row = s->nl_row.as<uint32_t>();
-    launch_hlist_count(a, s->mixed ? 1 : 0, s->cap, want_counts, st);
+    a.nl_bound = use_bounds ? 1 : 0;
+    if (use_bounds) {
+        launch_hlist_bound(a, s->cnt_by_id.as<uint32_t>(), st);
+        CK(cudaMemsetAsync(a.nl_retry, 0, sizeof(uint32_t), st));
+    } else {
+        launch_hlist_count(a, s->mixed ? 1 : 0, s->cap, want_counts, st);
+    }
     uint32_t *sc = s->scalars.as<uint32_t>();
     scan_exclusive_u32(a.nl_len, a.nl_row, a.n_ggas, sc + 5, s->scan_tmp.as<uint32_t>(), st);
     CK(cudaMemcpyAsync(s->host_scalars + 5, sc + 5, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
@@ -458,8 +469,22 @@ int run_step(crk_sim *s, const double *dt_per_box, bool want_counts)
     const int mixed = s->mixed ? 1 : 0;
     mark(s, PH_D, 0);
     launch_records(a, mixed, st);
-    RET(size_hydro_lists(s, a, want_counts));
-    launch_density(a, mixed, s->cap, want_counts, st);
+    RET(size_hydro_lists(s, a, want_counts, s->cnt_valid && !s->is_pool));
+    launch_hlist_fill(a, mixed, s->cap, want_counts, st);
+    if (a.nl_bound) {
+        // a list outgrew the rows sized from the last step: count and fill again
+        CK(cudaMemcpyAsync(s->host_scalars + 6, a.nl_retry, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (s->host_scalars[6]) {
+            RET(size_hydro_lists(s, a, want_counts, false));
+            launch_hlist_fill(a, mixed, s->cap, want_counts, st);
+        }
+    }
+    launch_density_eval(a, mixed, s->cap, want_counts, st);
+    if (!s->is_pool) {
+        launch_keep_counts(a, s->cnt_by_id.as<uint32_t>(), st);
+        s->cnt_valid = true;
+    }
     mark(s, PH_D, 1);
     mark(s, PH_M, 0);
     launch_moments(a, mixed, s->cap, st);
@@ -521,6 +546,7 @@ int load_impl(crk_sim *s, int nbox, const int64_t *counts, const crk_physics *ph
     RET(reserve(s, n));
     s->n = n;
     s->tree_valid = false;
+    s->cnt_valid = false;
     s->nbox = nbox;
     int sb = 0;
     while ((1 << sb) < nbox) ++sb;
@@ -1122,7 +1148,7 @@ extern "C" int crk_destroy(crk_sim *s)
                     &s->in_stage, &s->grp_cnt, &s->grp_off, &s->grp_gas, &s->grp_all, &s->hfr, &s->gfr,
                     &s->nl_j, &s->nl_row, &s->nl_len, &s->nl_cnt, &s->hsj, &s->fof_par, &s->acc_pm,
                     &s->bflag, &s->bgrp[0], &s->bgrp[1], &s->bgrp[2], &s->bgrp[3], &s->bmap[0],
-                    &s->bmap[1], &s->bkeep, &s->bpos, &s->bcount};
+                    &s->bmap[1], &s->bkeep, &s->bpos, &s->bcount, &s->cnt_by_id, &s->nl_retry};
     for (DBuf *b : bufs) b->release();
     pm_release(s);
     for (int k = 0; k < 3; ++k) {
@@ -1162,6 +1188,8 @@ size_t pool_bytes_per_particle(const crk_sim *s)
 int pool_init(crk_sim *s, int max_slots)
 {
     if (max_slots < 1) return fail(CRK_EINVAL, "max_slots must be >= 1");
+    s->is_pool = true;
+    s->cnt_valid = false;
     if (s->prm.pm_grid > 0) return fail(CRK_EINVAL, "the service takes no mesh (pm_grid must be 0)");
     CK(cudaSetDevice(s->device));
     int sb = 0;

@@ -108,6 +108,11 @@ struct PassArgs {
     uint32_t *nl_row;        // first row of every gas group
     uint32_t *nl_len;        // rows of every gas group (its longest list)
     uint32_t *nl_cnt;        // entries of every particle
+    // list rows sized from the previous step's counts (nl_bound 1): the fill
+    // pass may use all nl_len[g] rows of its group, writes the true counts
+    // and sets *nl_retry when a list does not fit
+    int nl_bound;
+    uint32_t *nl_retry;
     const uint2 *ggas;       // warp work items (leaf, first offset) of gas leaves
     const uint2 *gall;       // warp work items of all leaves
     uint32_t n_ggas, n_gall;
@@ -153,6 +158,10 @@ void launch_pair_fill(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, in
 void launch_records(const PassArgs &a, int mixed, cudaStream_t st);
 void launch_hlist_count(const PassArgs &a, int mixed, int cap, bool count, cudaStream_t st);
 void launch_density(const PassArgs &a, int mixed, int cap, bool count, cudaStream_t st);
+void launch_hlist_fill(const PassArgs &a, int mixed, int cap, bool count, cudaStream_t st);
+void launch_density_eval(const PassArgs &a, int mixed, int cap, bool count, cudaStream_t st);
+void launch_hlist_bound(const PassArgs &a, const uint32_t *cnt_by_id, cudaStream_t st);
+void launch_keep_counts(const PassArgs &a, uint32_t *cnt_by_id, cudaStream_t st);
 void launch_moments(const PassArgs &a, int mixed, int cap, cudaStream_t st);
 void launch_hydro(const PassArgs &a, int mixed, int cap, cudaStream_t st);
 void launch_gravity(const PassArgs &a, int mixed, int cap, bool count, cudaStream_t st);

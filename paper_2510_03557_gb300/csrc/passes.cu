@@ -741,7 +741,9 @@ __global__ void __launch_bounds__(kBlock) hlist_fill_k(PassArgs a)
     const float Hw = warp_max(G.act ? (float)ht.H : 0.f);
     ring.e0 = (size_t)a.nl_row[gi] * 32u + lane;
     const uint32_t prow = a.hrow[I];
-    const uint32_t room = G.act ? a.nl_cnt[i] : 0u;  // entries the count pass found
+    // entries the count pass found, or the group's rows when they were sized
+    // from the previous step
+    const uint32_t room = G.act ? (a.nl_bound ? a.nl_len[gi] : a.nl_cnt[i]) : 0u;
     uint32_t k = 0;
     const RowOrder order(a.hrow[I + 1] - prow);
     for (uint32_t t = 0; t < order.n; ++t) {
@@ -782,11 +784,38 @@ __global__ void __launch_bounds__(kBlock) hlist_fill_k(PassArgs a)
         if (done > ring.base) ring.flush(a, done, k < room ? k : room, lane);
     }
     ring.flush(a, __reduce_max_sync(0xffffffffu, k), k < room ? k : room, lane);
-    if (G.act && k != room) {
+    if (a.nl_bound) {
+        if (G.act) a.nl_cnt[i] = k < room ? k : room;
+        if (G.act && k > room) atomicExch(a.nl_retry, 1u);  // the host sizes the lists again
+    } else if (G.act && k != room) {
         // the two passes drew different sets: keep the lists consistent, report
         a.nl_cnt[i] = k < room ? k : room;
         set_error(a.err, CRK_EOVERFLOW, a.s.id[i]);
     }
+}
+
+// Rows of every gas group from the previous step's list sizes (by original
+// index): the largest of its targets plus max(16, 1/8) for the particles'
+// motion since.  A list that outgrows them makes the fill pass ask for a
+// count pass.
+__global__ void __launch_bounds__(kBlock) hlist_bound_k(PassArgs a, const uint32_t *__restrict__ cnt_by_id)
+{
+    const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    const uint32_t gi = blockIdx.x * kWarps + w;
+    if (gi >= a.n_ggas) return;
+    const Group G = load_group(a.lv, a.ggas, gi, lane);
+    const uint32_t c = __reduce_max_sync(0xffffffffu, G.act ? cnt_by_id[a.s.id[G.i]] : 0u);
+    if (lane == 0) a.nl_len[gi] = c + (c / 8u > 16u ? c / 8u : 16u);
+}
+
+// Every gas target's list size, stored by original index for the next step.
+__global__ void keep_counts_k(PassArgs a, uint32_t *cnt_by_id)
+{
+    const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    const uint32_t gi = blockIdx.x * kWarps + w;
+    if (gi >= a.n_ggas) return;
+    const Group G = load_group(a.lv, a.ggas, gi, lane);
+    if (G.act) cnt_by_id[a.s.id[G.i]] = a.nl_cnt[G.i];
 }
 
 // The neighbour's sorted index and the leaf-pair frame of a list entry.
@@ -1042,8 +1071,15 @@ struct MomentAcc {
     }
 };
 
+// Mixed form: five CTAs per SM (at most 102 registers a thread).  The few
+// registers this spills cost less than the extra warps gain in hiding the
+// list and record loads (4.53 -> 3.78 ms at 2x128^3); the FP64 form keeps
+// its registers.
+template <typename R>
+constexpr int moments_min_blocks() { return Real<R>::mixed ? 5 : 1; }
+
 template <typename R, int JMAX>
-__global__ void __launch_bounds__(kBlock) moments_k(PassArgs a)
+__global__ void __launch_bounds__(kBlock, moments_min_blocks<R>()) moments_k(PassArgs a)
 {
     using R4 = Vec4<R>;
     const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
@@ -1555,6 +1591,21 @@ void hlist_count_dispatch(const PassArgs &a, bool count, cudaStream_t st)
 }
 
 template <typename R, int JMAX>
+void fill_dispatch(const PassArgs &a, bool count, cudaStream_t st)
+{
+    const size_t smf = (size_t)kWarps * hfill_warp_bytes<R, JMAX>();
+    if (count) launch_warp_kernel(hlist_fill_k<R, JMAX, true>, a.n_ggas, smf, a, st);
+    else launch_warp_kernel(hlist_fill_k<R, JMAX, false>, a.n_ggas, smf, a, st);
+}
+
+template <typename R, int JMAX>
+void density_eval_dispatch(const PassArgs &a, bool count, cudaStream_t st)
+{
+    if (count) launch_warp_kernel(density_k<R, JMAX, true>, a.n_ggas, 0, a, st);
+    else launch_warp_kernel(density_k<R, JMAX, false>, a.n_ggas, 0, a, st);
+}
+
+template <typename R, int JMAX>
 void density_dispatch(const PassArgs &a, bool count, cudaStream_t st)
 {
     const size_t smf = (size_t)kWarps * hfill_warp_bytes<R, JMAX>();
@@ -1640,6 +1691,34 @@ void launch_density(const PassArgs &a, int mixed, int cap, bool count, cudaStrea
     if (a.n_ggas == 0) return;
     CRK_BY_CAP(density_dispatch, a, count, st);
     note_launches(2);
+}
+
+void launch_hlist_fill(const PassArgs &a, int mixed, int cap, bool count, cudaStream_t st)
+{
+    if (a.n_ggas == 0) return;
+    CRK_BY_CAP(fill_dispatch, a, count, st);
+    note_launches(1);
+}
+
+void launch_density_eval(const PassArgs &a, int mixed, int cap, bool count, cudaStream_t st)
+{
+    if (a.n_ggas == 0) return;
+    CRK_BY_CAP(density_eval_dispatch, a, count, st);
+    note_launches(1);
+}
+
+void launch_hlist_bound(const PassArgs &a, const uint32_t *cnt_by_id, cudaStream_t st)
+{
+    if (a.n_ggas == 0) return;
+    hlist_bound_k<<<nblocks(a.n_ggas, kWarps), kBlock, 0, st>>>(a, cnt_by_id);
+    note_launches(1);
+}
+
+void launch_keep_counts(const PassArgs &a, uint32_t *cnt_by_id, cudaStream_t st)
+{
+    if (a.n_ggas == 0) return;
+    keep_counts_k<<<nblocks(a.n_ggas, kWarps), kBlock, 0, st>>>(a, cnt_by_id);
+    note_launches(1);
 }
 
 void launch_moments(const PassArgs &a, int mixed, int cap, cudaStream_t st)

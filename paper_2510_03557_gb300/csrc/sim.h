@@ -89,6 +89,11 @@ struct crk_sim {
     // selected group lists (density, moments, hydro, gravity), the list rows of
     // the moments and hydro groups, selection scratch, active counts
     DBuf bflag, bgrp[4], bmap[2], bkeep, bpos, bcount;
+    // every gas particle's hydro list size of the last step, by original
+    // index: the next step sizes its lists from it instead of a count pass
+    DBuf cnt_by_id, nl_retry;
+    bool cnt_valid = false;
+    bool is_pool = false;
     int64_t nl_rows = 0;
     DBuf err, nfloor, partial, sums;
     DBuf staging, in_stage;

@@ -546,3 +546,35 @@ def test_fof_groups_stay_inside_their_box(crk):
         assert np.array_equal(grp[lo:hi], ref)
         total += ref_ng
     assert ng == total
+
+
+# ------------------------------------------- list sizes from the last step
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_lists_sized_from_last_step_equal_counted_lists(crk, precision):
+    """The second force evaluation sizes its hydro lists from the first one's
+    counts (no count pass): the outputs are bit-identical."""
+    box = wl.gaussian_field_box(16, seed=3)
+    with crk.Sim(crk.box_physics(box), precision=precision) as sim:
+        sim.load(box)
+        a = sim.forces(counts=True)
+        b = sim.forces(counts=True)
+    for k in FLOAT_OUTPUTS + ("nbr_count", "nbr_hash", "grav_count", "grav_hash"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_lists_that_outgrow_last_step_sizes_are_counted_again(crk):
+    """Compress the box after a step so every list grows far beyond the
+    margin: the fill pass asks for a count pass and the forces still equal
+    the oracle's at the new positions."""
+    box = wl.jittered_lattice(16, seed=2)
+    with crk.Sim(crk.box_physics(box), precision=0) as sim:
+        sim.load(box)
+        sim.forces(counts=False)
+        pos = 0.5 + 0.75 * (box.pos - 0.5)
+        crk.crk_set_state(sim.handle, pos, box.vel, box.u)
+        out = sim.forces(counts=True)
+    s = dict(box_dict(box), pos=pos)
+    op = oracle_params(box)
+    ref = oracle.forces(pos, box.vel, box.mass, box.u, box.h, box.species, op)
+    assert ref["rc"] == 0
+    compare(out, ref, oracle_counts(s, op), 0, label="compressed")
