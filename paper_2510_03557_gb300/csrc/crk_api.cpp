@@ -359,8 +359,19 @@ int build_tree(crk_sim *s, int mode = TREE_RULE)
     mark(s, PH_PAIRS, 0);
     launch_build_nodes(s->nd, s->nleaf, st);
     const BoxDev *bd = s->boxes_d.as<BoxDev>();
-    launch_pair_count(s->nd, s->lv, bd, s->nleaf, 1, s->hcnt.as<uint32_t>(), st);
-    launch_pair_count(s->nd, s->lv, bd, s->nleaf, 0, s->gcnt.as<uint32_t>(), st);
+    // one walk per list into rows of fixed capacity, packed after the scan;
+    // a leaf with more pairs than that makes both lists walk twice (count, fill)
+    const size_t nls = (size_t)std::max(s->nleaf, 1);
+    RET(s->pscr_col.ensure(nls * (kPairCapH + kPairCapG) * sizeof(uint32_t)));
+    RET(s->pscr_fr.ensure(nls * (kPairCapH + kPairCapG) * sizeof(float4)));
+    RET(s->pscr_st.ensure(nls * kPairCapH * sizeof(uint32_t)));
+    uint32_t *scol_h = s->pscr_col.as<uint32_t>(), *scol_g = scol_h + nls * kPairCapH;
+    float4 *sfr_h = s->pscr_fr.as<float4>(), *sfr_g = sfr_h + nls * kPairCapH;
+    CK(cudaMemsetAsync(sc + 7, 0, sizeof(uint32_t), st));
+    launch_pair_scratch(s->nd, s->lv, bd, s->nleaf, 1, s->hcnt.as<uint32_t>(), kPairCapH, scol_h, sfr_h,
+                        s->pscr_st.as<uint32_t>(), sc + 7, st);
+    launch_pair_scratch(s->nd, s->lv, bd, s->nleaf, 0, s->gcnt.as<uint32_t>(), kPairCapG, scol_g, sfr_g,
+                        nullptr, sc + 7, st);
     scan_exclusive_u32(s->hcnt.as<uint32_t>(), s->hrow.as<uint32_t>(), s->nleaf, sc + 1, tmp, st);
     scan_exclusive_u32(s->gcnt.as<uint32_t>(), s->grow.as<uint32_t>(), s->nleaf, sc + 2, tmp, st);
     // warp work items: gas-leaf groups, then all-leaf groups
@@ -372,8 +383,9 @@ int build_tree(crk_sim *s, int mode = TREE_RULE)
     launch_group_count(s->lv, s->nleaf, 0, gc + nl, st);
     scan_exclusive_u32(gc, go, s->nleaf, sc + 3, tmp, st);
     scan_exclusive_u32(gc + nl, go + nl, s->nleaf, sc + 4, tmp, st);
-    CK(cudaMemcpyAsync(s->host_scalars + 1, sc + 1, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(s->host_scalars + 1, sc + 1, 7 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    const bool pair_overflow = s->host_scalars[7] != 0;
     s->npair_h = s->host_scalars[1];
     s->npair_g = s->host_scalars[2];
     s->n_ggas = s->host_scalars[3];
@@ -390,10 +402,18 @@ int build_tree(crk_sim *s, int mode = TREE_RULE)
     RET(s->hfr.ensure((size_t)std::max<int64_t>(s->npair_h, 1) * 16));
     RET(s->hsj.ensure((size_t)std::max<int64_t>(s->npair_h, 1) * 4));
     RET(s->gfr.ensure((size_t)std::max<int64_t>(s->npair_g, 1) * 16));
-    launch_pair_fill(s->nd, s->lv, bd, s->nleaf, 1, s->hrow.as<uint32_t>(), s->hcol.as<uint32_t>(),
-                     s->hfr.as<float4>(), s->hsj.as<uint32_t>(), st);
-    launch_pair_fill(s->nd, s->lv, bd, s->nleaf, 0, s->grow.as<uint32_t>(), s->gcol.as<uint32_t>(),
-                     s->gfr.as<float4>(), nullptr, st);
+    if (pair_overflow) {
+        launch_pair_fill(s->nd, s->lv, bd, s->nleaf, 1, s->hrow.as<uint32_t>(), s->hcol.as<uint32_t>(),
+                         s->hfr.as<float4>(), s->hsj.as<uint32_t>(), st);
+        launch_pair_fill(s->nd, s->lv, bd, s->nleaf, 0, s->grow.as<uint32_t>(), s->gcol.as<uint32_t>(),
+                         s->gfr.as<float4>(), nullptr, st);
+    } else {
+        launch_pair_compact(s->nleaf, kPairCapH, s->hcnt.as<uint32_t>(), s->hrow.as<uint32_t>(), scol_h, sfr_h,
+                            s->pscr_st.as<uint32_t>(), s->hcol.as<uint32_t>(), s->hfr.as<float4>(),
+                            s->hsj.as<uint32_t>(), st);
+        launch_pair_compact(s->nleaf, kPairCapG, s->gcnt.as<uint32_t>(), s->grow.as<uint32_t>(), scol_g, sfr_g,
+                            nullptr, s->gcol.as<uint32_t>(), s->gfr.as<float4>(), nullptr, st);
+    }
     mark(s, PH_PAIRS, 1);
     return CRK_OK;
 }
@@ -1148,7 +1168,7 @@ extern "C" int crk_destroy(crk_sim *s)
                     &s->in_stage, &s->grp_cnt, &s->grp_off, &s->grp_gas, &s->grp_all, &s->hfr, &s->gfr,
                     &s->nl_j, &s->nl_row, &s->nl_len, &s->nl_cnt, &s->hsj, &s->fof_par, &s->acc_pm,
                     &s->bflag, &s->bgrp[0], &s->bgrp[1], &s->bgrp[2], &s->bgrp[3], &s->bmap[0],
-                    &s->bmap[1], &s->bkeep, &s->bpos, &s->bcount, &s->cnt_by_id, &s->nl_retry};
+                    &s->bmap[1], &s->bkeep, &s->bpos, &s->bcount, &s->cnt_by_id, &s->nl_retry, &s->pscr_col, &s->pscr_fr, &s->pscr_st};
     for (DBuf *b : bufs) b->release();
     pm_release(s);
     for (int k = 0; k < 3; ++k) {

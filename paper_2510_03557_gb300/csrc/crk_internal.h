@@ -150,6 +150,12 @@ void launch_group_fill(const Leaves &lv, int nleaf, int gas_only, const uint32_t
                        cudaStream_t st);
 void launch_pair_count(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, int nleaf,
                        int hydro, uint32_t *counts, cudaStream_t st);
+void launch_pair_scratch(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, int nleaf, int hydro,
+                         uint32_t *counts, uint32_t cap, uint32_t *col, float4 *frame, uint32_t *start,
+                         uint32_t *overflow, cudaStream_t st);
+void launch_pair_compact(int nleaf, uint32_t cap, const uint32_t *counts, const uint32_t *row,
+                         const uint32_t *scol, const float4 *sframe, const uint32_t *sstart, uint32_t *col,
+                         float4 *frame, uint32_t *start, cudaStream_t st);
 void launch_pair_fill(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, int nleaf,
                       int hydro, const uint32_t *row, uint32_t *col, float4 *frame, uint32_t *start,
                       cudaStream_t st);

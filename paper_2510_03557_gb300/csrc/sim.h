@@ -43,6 +43,10 @@ struct DBuf {
     template <typename T> T *as() const { return static_cast<T *>(p); }
 };
 
+// Leaf pairs a leaf's hydro and gravity rows hold before the lists are
+// walked twice (count, then fill).
+constexpr uint32_t kPairCapH = 128, kPairCapG = 256;
+
 enum Phase { PH_TREE, PH_PAIRS, PH_D, PH_M, PH_H, PH_G, PH_KDK, PH_KICK, PH_PM, PH_N };
 
 }  // namespace crk
@@ -92,6 +96,7 @@ struct crk_sim {
     // every gas particle's hydro list size of the last step, by original
     // index: the next step sizes its lists from it instead of a count pass
     DBuf cnt_by_id, nl_retry;
+    DBuf pscr_col, pscr_fr, pscr_st;    // leaf-pair rows of fixed capacity before packing
     bool cnt_valid = false;
     bool is_pool = false;
     int64_t nl_rows = 0;

@@ -306,6 +306,18 @@ __device__ __forceinline__ double wmax(double v)
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
+__device__ __forceinline__ float wminf(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ float wmaxf(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
 
 // One warp per leaf: FP64 bounds, centre, half extents (rounded up), the
 // leaf's largest kernel support, the level-0 node, and the position-mass
@@ -337,7 +349,7 @@ __global__ void leaf_bounds_k(State s, const BoxDev *__restrict__ boxes, Leaves 
     const double ref[3] = {s.x[s0], s.y[s0], s.z[s0]};
     double d[kChunks][3];
     double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
-    double hm = 0.0;
+    float hm = 0.f;  // max 2h, rounded up (rounding is monotonic: the max of the rounded values)
 #pragma unroll
     for (int ch = 0; ch < kChunks; ++ch) {
         const uint32_t t = 32u * ch + lane;
@@ -348,7 +360,7 @@ __global__ void leaf_bounds_k(State s, const BoxDev *__restrict__ boxes, Leaves 
             d[ch][2] = leaf_offset(s.z[i], ref[2], Lb);
 #pragma unroll
             for (int a = 0; a < 3; ++a) { lo[a] = fmin(lo[a], d[ch][a]); hi[a] = fmax(hi[a], d[ch][a]); }
-            if (s.species[i] == CRK_GAS) hm = fmax(hm, 2.0 * s.h[i]);
+            if (s.species[i] == CRK_GAS) hm = fmaxf(hm, __double2float_ru(2.0 * s.h[i]));
         } else {
             d[ch][0] = d[ch][1] = d[ch][2] = 0.0;
         }
@@ -363,38 +375,38 @@ __global__ void leaf_bounds_k(State s, const BoxDev *__restrict__ boxes, Leaves 
         cen[a] = ref[a] + mid[a];
         ext[a] = __double2float_ru(fmax(hi[a] - mid[a], mid[a] - lo[a]));
     }
-    hm = wmax(hm);
+    hm = wmaxf(hm);
     if (lane == 0) {
         lv.cx[w] = cen[0]; lv.cy[w] = cen[1]; lv.cz[w] = cen[2];
         lv.ex[w] = ext[0]; lv.ey[w] = ext[1]; lv.ez[w] = ext[2];
-        lv.hmax[w] = __double2float_ru(hm);
+        lv.hmax[w] = hm;
         lv.slot[w] = s.slot[s0];
         lv.species[w] = s.species[s0];
         nd.lox[w] = __double2float_rd(ref[0] + lo[0]); nd.loy[w] = __double2float_rd(ref[1] + lo[1]);
         nd.loz[w] = __double2float_rd(ref[2] + lo[2]);
         nd.hix[w] = __double2float_ru(ref[0] + hi[0]); nd.hiy[w] = __double2float_ru(ref[1] + hi[1]);
         nd.hiz[w] = __double2float_ru(ref[2] + hi[2]);
-        nd.hmax[w] = __double2float_ru(hm);
+        nd.hmax[w] = hm;
         nd.slot[w] = (int32_t)s.slot[s0];
     }
     // Boxes of the 32-particle chunks (particle t of the leaf is in chunk t/32),
     // relative to the leaf centre, rounded outward; empty chunks get an
-    // inverted box that is never in range.
+    // inverted box that is never in range.  Rounding is monotonic, so the
+    // FP32 minimum of the values rounded down is the FP64 minimum rounded
+    // down (and likewise up for the maximum): the reductions run in FP32.
 #pragma unroll
     for (int ch = 0; ch < kChunks; ++ch) {
         const bool in = 32u * ch + lane < c;
         const double px = d[ch][0] - mid[0], py = d[ch][1] - mid[1], pz = d[ch][2] - mid[2];
-        const double lx = wmin(in ? px : DBL_MAX), hx = wmax(in ? px : -DBL_MAX);
-        const double ly = wmin(in ? py : DBL_MAX), hy = wmax(in ? py : -DBL_MAX);
-        const double lz = wmin(in ? pz : DBL_MAX), hz = wmax(in ? pz : -DBL_MAX);
+        const float lx = wminf(in ? __double2float_rd(px) : FLT_MAX), hx = wmaxf(in ? __double2float_ru(px) : -FLT_MAX);
+        const float ly = wminf(in ? __double2float_rd(py) : FLT_MAX), hy = wmaxf(in ? __double2float_ru(py) : -FLT_MAX);
+        const float lz = wminf(in ? __double2float_rd(pz) : FLT_MAX), hz = wmaxf(in ? __double2float_ru(pz) : -FLT_MAX);
         if (lane == 0) {
             const bool any = 32u * ch < c;
             lv.clo[(size_t)w * kChunks + ch] =
-                any ? make_float4(__double2float_rd(lx), __double2float_rd(ly), __double2float_rd(lz), 0.f)
-                    : make_float4(1e30f, 1e30f, 1e30f, 0.f);
+                any ? make_float4(lx, ly, lz, 0.f) : make_float4(1e30f, 1e30f, 1e30f, 0.f);
             lv.chi[(size_t)w * kChunks + ch] =
-                any ? make_float4(__double2float_ru(hx), __double2float_ru(hy), __double2float_ru(hz), 0.f)
-                    : make_float4(-1e30f, -1e30f, -1e30f, 0.f);
+                any ? make_float4(hx, hy, hz, 0.f) : make_float4(-1e30f, -1e30f, -1e30f, 0.f);
         }
         if (in) {
             const uint32_t i = s0 + 32u * ch + lane;
@@ -467,15 +479,20 @@ __device__ __forceinline__ float4 pair_frame(const Leaves &lv, int I, int J, dou
     return make_float4(s[0], s[1], s[2], mag);
 }
 
-template <bool FILL>
+// MODE 0: count the pairs of every leaf; 1: fill the CSR rows (row from a
+// scan of the counts); 2: count and fill fixed rows of `cap` entries at
+// I * cap (a row that does not fit sets *overflow; the host then walks again
+// in modes 0 and 1).
+template <int MODE>
 __global__ void pair_walk_k(Nodes nd, Leaves lv, const BoxDev *__restrict__ boxes, int nleaf,
                             int hydro, uint32_t *counts, const uint32_t *__restrict__ row,
-                            uint32_t *col, float4 *frame, uint32_t *start)
+                            uint32_t *col, float4 *frame, uint32_t *start, uint32_t cap, uint32_t *overflow)
 {
+    constexpr bool FILL = MODE != 0;
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nleaf) return;
     if (hydro && lv.species[I] != CRK_GAS) {
-        if (!FILL) counts[I] = 0;
+        if (MODE != 1) counts[I] = 0;
         return;
     }
     const int32_t slot = (int32_t)lv.slot[I];
@@ -486,7 +503,7 @@ __global__ void pair_walk_k(Nodes nd, Leaves lv, const BoxDev *__restrict__ boxe
     const float eix = 0.5f * (nd.hix[I] - nd.lox[I]), eiy = 0.5f * (nd.hiy[I] - nd.loy[I]),
                 eiz = 0.5f * (nd.hiz[I] - nd.loz[I]);
     const float RI = hydro ? lv.hmax[I] : (float)bx.r_cut;
-    uint32_t base = FILL ? row[I] : 0u;
+    const size_t base = MODE == 1 ? (size_t)row[I] : MODE == 2 ? (size_t)I * cap : 0u;
     uint32_t cnt = 0;
     int2 stack[96];
     int sp = 0;
@@ -520,7 +537,7 @@ __global__ void pair_walk_k(Nodes nd, Leaves lv, const BoxDev *__restrict__ boxe
             if (gap2 >= Rm * Rm) continue;
         }
         if (l == 0) {
-            if (FILL) {
+            if (FILL && (MODE == 1 || cnt < cap)) {
                 col[base + cnt] = (uint32_t)k;
                 frame[base + cnt] = pair_frame(lv, I, k, bx.L);
                 if (start) start[base + cnt] = lv.start[k];
@@ -532,7 +549,26 @@ __global__ void pair_walk_k(Nodes nd, Leaves lv, const BoxDev *__restrict__ boxe
             stack[sp++] = make_int2(l - 1, 2 * k);
         }
     }
-    if (!FILL) counts[I] = cnt;
+    if (MODE != 1) counts[I] = cnt;
+    if (MODE == 2 && cnt > cap) atomicOr(overflow, 1u);
+}
+
+// The fixed rows of mode 2 packed into CSR rows; one warp per leaf.
+__global__ void pair_compact_k(int nleaf, uint32_t cap, const uint32_t *__restrict__ counts,
+                               const uint32_t *__restrict__ row, const uint32_t *__restrict__ scol,
+                               const float4 *__restrict__ sframe, const uint32_t *__restrict__ sstart,
+                               uint32_t *col, float4 *frame, uint32_t *start)
+{
+    const int I = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const uint32_t lane = lane_id();
+    if (I >= nleaf) return;
+    const uint32_t c = counts[I], r = row[I];
+    const size_t b = (size_t)I * cap;
+    for (uint32_t t = lane; t < c; t += 32u) {
+        col[r + t] = scol[b + t];
+        frame[r + t] = sframe[b + t];
+        if (start) start[r + t] = sstart[b + t];
+    }
 }
 
 // Orders the particles of every leaf so that each run of 32 (the chunks and
@@ -769,8 +805,28 @@ void launch_pair_count(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, i
                        int hydro, uint32_t *counts, cudaStream_t st)
 {
     if (nleaf <= 0) return;
-    pair_walk_k<false><<<grid_for(nleaf, 128), 128, 0, st>>>(nd, lv, boxes, nleaf, hydro, counts,
-                                                               nullptr, nullptr, nullptr, nullptr);
+    pair_walk_k<0><<<grid_for(nleaf, 128), 128, 0, st>>>(nd, lv, boxes, nleaf, hydro, counts,
+                                                           nullptr, nullptr, nullptr, nullptr, 0u, nullptr);
+    note_launches(1);
+}
+
+void launch_pair_scratch(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, int nleaf, int hydro,
+                         uint32_t *counts, uint32_t cap, uint32_t *col, float4 *frame, uint32_t *start,
+                         uint32_t *overflow, cudaStream_t st)
+{
+    if (nleaf <= 0) return;
+    pair_walk_k<2><<<grid_for(nleaf, 128), 128, 0, st>>>(nd, lv, boxes, nleaf, hydro, counts, nullptr, col,
+                                                           frame, start, cap, overflow);
+    note_launches(1);
+}
+
+void launch_pair_compact(int nleaf, uint32_t cap, const uint32_t *counts, const uint32_t *row,
+                         const uint32_t *scol, const float4 *sframe, const uint32_t *sstart, uint32_t *col,
+                         float4 *frame, uint32_t *start, cudaStream_t st)
+{
+    if (nleaf <= 0) return;
+    pair_compact_k<<<grid_for((int64_t)nleaf * 32, kT), kT, 0, st>>>(nleaf, cap, counts, row, scol, sframe,
+                                                                     sstart, col, frame, start);
     note_launches(1);
 }
 
@@ -779,8 +835,8 @@ void launch_pair_fill(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, in
                       cudaStream_t st)
 {
     if (nleaf <= 0) return;
-    pair_walk_k<true><<<grid_for(nleaf, 128), 128, 0, st>>>(nd, lv, boxes, nleaf, hydro, nullptr,
-                                                              row, col, frame, start);
+    pair_walk_k<1><<<grid_for(nleaf, 128), 128, 0, st>>>(nd, lv, boxes, nleaf, hydro, nullptr,
+                                                           row, col, frame, start, 0u, nullptr);
     note_launches(1);
 }
 

@@ -578,3 +578,23 @@ def test_lists_that_outgrow_last_step_sizes_are_counted_again(crk):
     ref = oracle.forces(pos, box.vel, box.mass, box.u, box.h, box.species, op)
     assert ref["rc"] == 0
     compare(out, ref, oracle_counts(s, op), 0, label="compressed")
+
+
+def test_pair_rows_beyond_capacity_walk_twice(crk):
+    """A cut-off of most of the box gives every leaf more gravity leaf pairs
+    than a fixed row holds: the lists are walked again (count, fill) and the
+    gravity sets and forces still equal the oracle's."""
+    box = wl.jittered_lattice(16, seed=5)
+    params = dict(box.params(), r_cut=0.45, r_split=0.1)
+    phys = crk.physics(**params)
+    s = box_dict(box)
+    op = oracle.make_params(**params)
+    ref = oracle.forces(box.pos, box.vel, box.mass, box.u, box.h, box.species, op)
+    assert ref["rc"] == 0
+    with crk.Sim(phys, leaf_cap=32, precision=0) as sim:
+        crk.crk_load(sim.handle, s["pos"], s["vel"], s["mass"], s["u"], s["h"], s["species"])
+        sim.n = box.n
+        out = sim.forces(counts=True)
+        tim = crk.crk_get_timings(sim.handle)
+    assert tim["pairs_grav"] > 256 * tim["nleaves"] // 2   # rows well beyond the fixed capacity
+    compare(out, ref, oracle_counts(s, op), 0, label="wide cut-off")
