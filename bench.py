@@ -40,11 +40,11 @@ FLOP_PER_PAIR = {"density": 22, "moments": 125, "hydro": 183, "gravity": 41}
 
 # DRAM bytes (read + write) per particle of one launch of each pass, from the
 # one-pass ncu capture summarised in profiles/launches_gaussian_2x128.md
-# (2x128^3 Gaussian field, leaf capacity 128; density = list count + fill +
-# evaluation).  They describe the kernels of the csrc/passes.cu with this
+# (2x128^3 Gaussian field, leaf capacity 128; density = list bounds + fill +
+# evaluation + kept counts).  They describe the kernels of the csrc/passes.cu with this
 # SHA-256 only; for any other source the bench reports no traffic.
-TRAFFIC_SOURCE_SHA256 = "f32a10db6e6285cbbee48faa787308c5c79ab49e6ecb1346c956f7e3da5cddb6"
-TRAFFIC_BYTES_PER_PARTICLE = {"gravity": 81.2, "hydro": 997.5, "moments": 955.8, "density": 3546.7}
+TRAFFIC_SOURCE_SHA256 = "8f76f58adf6c0502dc31b5d7f42590ea3c2e9bc11eeada0a7ffe6436509dcb42"
+TRAFFIC_BYTES_PER_PARTICLE = {"gravity": 81.4, "hydro": 701.9, "moments": 690.9, "density": 1677.5}
 
 
 def _traffic(kernel: str, particles: int, leaf_cap: int):

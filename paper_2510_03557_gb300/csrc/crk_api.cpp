@@ -360,18 +360,30 @@ int build_tree(crk_sim *s, int mode = TREE_RULE)
     launch_build_nodes(s->nd, s->nleaf, st);
     const BoxDev *bd = s->boxes_d.as<BoxDev>();
     // one walk per list into rows of fixed capacity, packed after the scan;
-    // a leaf with more pairs than that makes both lists walk twice (count, fill)
+    // a leaf with more pairs than that makes both lists walk twice (count,
+    // fill), and the next 16 builds walk twice from the start
     const size_t nls = (size_t)std::max(s->nleaf, 1);
-    RET(s->pscr_col.ensure(nls * (kPairCapH + kPairCapG) * sizeof(uint32_t)));
-    RET(s->pscr_fr.ensure(nls * (kPairCapH + kPairCapG) * sizeof(float4)));
-    RET(s->pscr_st.ensure(nls * kPairCapH * sizeof(uint32_t)));
-    uint32_t *scol_h = s->pscr_col.as<uint32_t>(), *scol_g = scol_h + nls * kPairCapH;
-    float4 *sfr_h = s->pscr_fr.as<float4>(), *sfr_g = sfr_h + nls * kPairCapH;
+    const bool scratch = s->pair_two_pass_left == 0;
+    uint32_t *scol_h = nullptr, *scol_g = nullptr;
+    float4 *sfr_h = nullptr, *sfr_g = nullptr;
     CK(cudaMemsetAsync(sc + 7, 0, sizeof(uint32_t), st));
-    launch_pair_scratch(s->nd, s->lv, bd, s->nleaf, 1, s->hcnt.as<uint32_t>(), kPairCapH, scol_h, sfr_h,
-                        s->pscr_st.as<uint32_t>(), sc + 7, st);
-    launch_pair_scratch(s->nd, s->lv, bd, s->nleaf, 0, s->gcnt.as<uint32_t>(), kPairCapG, scol_g, sfr_g,
-                        nullptr, sc + 7, st);
+    if (scratch) {
+        RET(s->pscr_col.ensure(nls * (kPairCapH + kPairCapG) * sizeof(uint32_t)));
+        RET(s->pscr_fr.ensure(nls * (kPairCapH + kPairCapG) * sizeof(float4)));
+        RET(s->pscr_st.ensure(nls * kPairCapH * sizeof(uint32_t)));
+        scol_h = s->pscr_col.as<uint32_t>();
+        scol_g = scol_h + nls * kPairCapH;
+        sfr_h = s->pscr_fr.as<float4>();
+        sfr_g = sfr_h + nls * kPairCapH;
+        launch_pair_scratch(s->nd, s->lv, bd, s->nleaf, 1, s->hcnt.as<uint32_t>(), kPairCapH, scol_h, sfr_h,
+                            s->pscr_st.as<uint32_t>(), sc + 7, st);
+        launch_pair_scratch(s->nd, s->lv, bd, s->nleaf, 0, s->gcnt.as<uint32_t>(), kPairCapG, scol_g, sfr_g,
+                            nullptr, sc + 7, st);
+    } else {
+        --s->pair_two_pass_left;
+        launch_pair_count(s->nd, s->lv, bd, s->nleaf, 1, s->hcnt.as<uint32_t>(), st);
+        launch_pair_count(s->nd, s->lv, bd, s->nleaf, 0, s->gcnt.as<uint32_t>(), st);
+    }
     scan_exclusive_u32(s->hcnt.as<uint32_t>(), s->hrow.as<uint32_t>(), s->nleaf, sc + 1, tmp, st);
     scan_exclusive_u32(s->gcnt.as<uint32_t>(), s->grow.as<uint32_t>(), s->nleaf, sc + 2, tmp, st);
     // warp work items: gas-leaf groups, then all-leaf groups
@@ -385,7 +397,8 @@ int build_tree(crk_sim *s, int mode = TREE_RULE)
     scan_exclusive_u32(gc + nl, go + nl, s->nleaf, sc + 4, tmp, st);
     CK(cudaMemcpyAsync(s->host_scalars + 1, sc + 1, 7 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    const bool pair_overflow = s->host_scalars[7] != 0;
+    const bool pair_overflow = !scratch || s->host_scalars[7] != 0;
+    if (scratch && pair_overflow) s->pair_two_pass_left = 16;
     s->npair_h = s->host_scalars[1];
     s->npair_g = s->host_scalars[2];
     s->n_ggas = s->host_scalars[3];
