@@ -63,7 +63,7 @@ extern "C" {
 /* Physics of one periodic box (paper Sec. IV-A; constants are inputs). */
 typedef struct {
     double box;        /* periodic side L */
-    double G;          /* gravitational constant */
+    double G;          /* gravitational constant (>= 0) */
     double gamma;      /* adiabatic index of the ideal-gas closure P = (gamma-1) rho u */
     double r_cut;      /* short-range gravity cut-off radius */
     double r_split;    /* Gaussian long/short split scale r_s */

@@ -240,6 +240,7 @@ int check_physics(const crk_physics &p)
     if (!(p.r_cut > 0.0) || !(p.r_cut < 0.5 * p.box))
         return fail(CRK_EINVAL, "r_cut must satisfy 0 < r_cut < L/2 (got %g, L=%g)", p.r_cut, p.box);
     if (!(p.r_split > 0.0)) return fail(CRK_EINVAL, "r_split must be > 0");
+    if (!(p.G >= 0.0) || !std::isfinite(p.G)) return fail(CRK_EINVAL, "G must be finite and >= 0");
     if (!(p.eps_soft >= 0.0)) return fail(CRK_EINVAL, "eps_soft must be >= 0");
     if (!(p.gamma > 1.0)) return fail(CRK_EINVAL, "gamma must be > 1");
     if (!(p.u_floor >= 0.0)) return fail(CRK_EINVAL, "u_floor must be >= 0");

@@ -51,6 +51,11 @@ constexpr double kGn = -(56.0 / 3.0) * kWn;
 // t = 1/(1 + p x), |error| <= 1.5e-7 for x >= 0.
 constexpr float kAsP = 0.3275911f;
 constexpr float kLog2e = 1.44269504088896341f;  // log2(e)
+// The mixed gravity factor in v = u sqrt(log2 e), so that exp(-u^2) = 2^(-v^2):
+// 1 + p u = 1 + (p / sqrt(log2 e)) v and 2u / sqrt(pi) = (2 / (sqrt(pi) sqrt(log2 e))) v.
+constexpr double kSqrtLog2e = 1.20112240878644981;
+constexpr float kAsPv = (float)(0.3275911 / kSqrtLog2e);
+constexpr float kTwoOverSqrtPiV = (float)(1.12837916709551257390 / kSqrtLog2e);
 constexpr float kAs1 = 0.254829592f, kAs2 = -0.284496736f, kAs3 = 1.421413741f,
                 kAs4 = -1.453152027f, kAs5 = 1.061405429f;
 constexpr double kTwoOverSqrtPi = 1.12837916709551257390;
@@ -83,6 +88,12 @@ template <> struct Real<float> {
     {
         float y;
         asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y;
+    }
+    __device__ static float log2(float x)
+    {
+        float y;
+        asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
         return y;
     }
     __device__ static float div(float a, float b) { return __fdividef(a, b); }
@@ -408,9 +419,9 @@ __device__ __forceinline__ float box_gap2(const WarpBox &b, float x, float y, fl
 // when its distance to the box is below Rc, or below its own radius when
 // PERJ (hydro: 2 h_j from hrec1, whose square also goes to h2j).  Writes
 // tile[0, K) and slot[0, K) (k of each kept candidate), the record's w
-// multiplied by wscale, pads the tile to a multiple of 32 with far-away
-// sentinels (h2j 0), and returns K.
-template <typename R, bool PERJ>
+// multiplied by wscale (LOGW: log2 of that), pads the tile to a multiple of 32
+// with far-away sentinels (h2j 0), and returns K.
+template <typename R, bool PERJ, bool LOGW = false>
 __device__ __forceinline__ uint32_t stage_cull(Vec4<R> *tile, uint8_t *slot, float *h2j,
                                                const Vec4<R> *__restrict__ src,
                                                const Vec4<R> *__restrict__ rec1, uint32_t sJ, uint32_t cJ,
@@ -444,7 +455,7 @@ __device__ __forceinline__ uint32_t stage_cull(Vec4<R> *tile, uint8_t *slot, flo
         const uint32_t bal = __ballot_sync(0xffffffffu, keep);
         if (keep) {
             const uint32_t pos = K + __popc(bal & ((1u << lane) - 1u));
-            v.w = wscale * v.w;
+            v.w = LOGW ? (R)Real<float>::log2((float)(wscale * v.w)) : wscale * v.w;
             tile[pos] = v;
             slot[pos] = (uint8_t)k;
             if (PERJ) h2j[pos] = Hj2;
@@ -1328,38 +1339,45 @@ __device__ __forceinline__ R split_S(R r, R inv2rs)
 // The pair forces of the K staged candidates of one visit on this lane's
 // target, masked by the gravity predicate: r^2 < r_cut^2 in the pass's
 // precision, re-decided in FP64 inside the mixed form's guard band.  The
-// target itself adds f * (0, 0, 0) = 0 (r^2 + eps^2 is kept above 1e-24 so
-// that f stays finite when eps = 0); only the neighbour count and hash
-// exclude it explicitly.  A lane without a target (act false) computes a
-// duplicate of lane 0's sums that is never stored.
+// target itself adds f * (0, 0, 0) = 0 (e2 = max(eps^2, 1e-24) keeps f finite
+// when eps = 0 and leaves every other r^2 + eps^2 unchanged in FP32 and FP64);
+// only the neighbour count and hash exclude it explicitly.  A lane without a
+// target (act false) computes a duplicate of lane 0's sums that is never
+// stored.  Staged w: FP64 G m_j; mixed log2(G m_j), so that
+// G m_j exp(-u^2) = 2^(log2(G m_j) - v^2) in one ex2.
 constexpr float kMinS2 = 1e-24f;
 
 template <typename R, bool WRAP, bool COUNT>
 __device__ __forceinline__ void gravity_tile(const Vec4<R> *tile, const uint8_t *tslot, uint32_t K,
                                              const Target<R> &q, R L, R hL, R rc2, double rc2x, R gb, R e2,
-                                             R inv2rs, R Gc, bool same, bool act, const State &s, uint32_t i,
+                                             R inv2rs, bool same, bool act, const State &s, uint32_t i,
                                              uint32_t sJ, double Ld, R &ax, R &ay, R &az, int &nc, uint64_t &hs)
 {
+    const float kv = (float)inv2rs * (float)kSqrtLog2e;
 #pragma unroll 4
     for (uint32_t j = 0; j < K; ++j) {
         const Vec4<R> rj = tile[j];
         R dx, dy, dz;
         const R r2 = sep2<R, WRAP>(rj, q, L, hL, dx, dy, dz);
-        bool in = r2 < rc2;
-        if (Real<R>::mixed && fabs(r2 - rc2) < gb)
+        const R dr = r2 - rc2;
+        bool in = dr < (R)0;
+        if (Real<R>::mixed && fabs(dr) < gb)
             in = exact_lt(s, i, sJ + tslot[j], Ld, rc2x);  // rare: pairs at the cut
         if (COUNT && same && sJ + tslot[j] == i) in = false;
-        const R r = Real<R>::sqrt_(r2);
-        const R S = split_S<R>(r, inv2rs);
-        const R s2 = fmax(r2 + e2, (R)kMinS2);
-        R inv3;
+        R f;
         if (Real<R>::mixed) {
-            const float is = Real<float>::rsqrt((float)s2);
-            inv3 = (R)(is * is * is);
+            const float v = Real<float>::sqrt_((float)r2) * kv;
+            const float tt = Real<float>::rcp(fmaf(kAsPv, v, 1.0f));
+            const float poly = tt * (kAs1 + tt * (kAs2 + tt * (kAs3 + tt * (kAs4 + tt * kAs5))));
+            const float sw = Real<float>::exp2(fmaf(-v, v, (float)rj.w)) * fmaf(kTwoOverSqrtPiV, v, poly);
+            const float is = Real<float>::rsqrt((float)(r2 + e2));
+            f = (R)(sw * is * is * is);  // G m_j S(r) (r^2 + eps^2)^{-3/2}
         } else {
-            inv3 = (R)1 / (s2 * Real<R>::sqrt_(s2));
+            const R S = split_S<R>(Real<R>::sqrt_(r2), inv2rs);
+            const R s2 = r2 + e2;
+            f = rj.w * S * ((R)1 / (s2 * Real<R>::sqrt_(s2)));  // rj.w = G m_j
         }
-        const R f = in ? rj.w * S * inv3 : (R)0;  // a_i += f (x_j - x_i), rj.w = G m_j
+        f = in ? f : (R)0;  // a_i += f (x_j - x_i)
         ax += f * dx;
         ay += f * dy;
         az += f * dz;
@@ -1391,7 +1409,7 @@ __global__ void __launch_bounds__(kBlock) gravity_k(PassArgs a)
     const double rc2x = __dmul_rn(bx.r_cut, bx.r_cut);
     const R rc = (R)bx.r_cut;
     const R rc2 = Real<R>::mixed ? rc * rc : (R)rc2x;
-    const R e2 = (R)(bx.eps_soft * bx.eps_soft);
+    const R e2 = (R)fmax(bx.eps_soft * bx.eps_soft, (double)kMinS2);
     const R inv2rs = (R)(0.5 / bx.r_split);
     const R Gc = (R)bx.G;
     float px, py, pz;
@@ -1409,8 +1427,8 @@ __global__ void __launch_bounds__(kBlock) gravity_k(PassArgs a)
         const uint32_t cm = chunks_in_range(a.lv, J, cJ, wb, fr, Rc);
         if (cm == 0u) continue;
         __syncwarp();
-        const uint32_t K = stage_cull<R, false>(tile, tslot, nullptr, pm, nullptr, sJ, cJ, cm, wb,
-                                                cand_frame<R>(a.lv, I, fr, Ld), Rc, lane, Gc);
+        const uint32_t K = stage_cull<R, false, Real<R>::mixed>(tile, tslot, nullptr, pm, nullptr, sJ, cJ, cm, wb,
+                                                                cand_frame<R>(a.lv, I, fr, Ld), Rc, lane, Gc);
         __syncwarp();
         if (K == 0u) continue;
         const Target<R> q = target_in_frame(ri, fr);
@@ -1419,9 +1437,9 @@ __global__ void __launch_bounds__(kBlock) gravity_k(PassArgs a)
         // every staged candidate against every target, branch-free: the pair
         // force is formed for all and kept where r < r_cut (a select, so that
         // nothing computed for an out-of-range pair reaches the sums)
-        if (q.wrap) gravity_tile<R, true, COUNT>(tile, tslot, K, q, L, hL, rc2, rc2x, gb, e2, inv2rs, Gc, same,
+        if (q.wrap) gravity_tile<R, true, COUNT>(tile, tslot, K, q, L, hL, rc2, rc2x, gb, e2, inv2rs, same,
                                                  G.act, a.s, i, sJ, Ld, ax, ay, az, nc, hs);
-        else gravity_tile<R, false, COUNT>(tile, tslot, K, q, L, hL, rc2, rc2x, gb, e2, inv2rs, Gc, same,
+        else gravity_tile<R, false, COUNT>(tile, tslot, K, q, L, hL, rc2, rc2x, gb, e2, inv2rs, same,
                                            G.act, a.s, i, sJ, Ld, ax, ay, az, nc, hs);
     }
     if (!G.act) return;
