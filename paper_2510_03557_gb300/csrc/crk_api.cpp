@@ -360,6 +360,14 @@ int build_tree(crk_sim *s, int mode = TREE_RULE)
     mark(s, PH_PAIRS, 0);
     launch_build_nodes(s->nd, s->nleaf, st);
     const BoxDev *bd = s->boxes_d.as<BoxDev>();
+    // hierarchical substeps: only the leaves holding an active particle need
+    // gravity rows (the hydro rows of every gas leaf feed the active sets)
+    const uint8_t *gmask = nullptr;
+    if (s->bins_bmin >= 0) {
+        RET(s->bflag.ensure(3 * (size_t)std::max(s->nleaf, 1)));
+        launch_leaf_active(s->lv, s->nleaf, s->sa.bin, s->bins_bmin, s->bflag.as<uint8_t>(), st);
+        gmask = s->bflag.as<uint8_t>();
+    }
     // one walk per list into rows of fixed capacity, packed after the scan;
     // a leaf with more pairs than that makes both lists walk twice (count,
     // fill), and the next 16 builds walk twice from the start
@@ -379,11 +387,11 @@ int build_tree(crk_sim *s, int mode = TREE_RULE)
         launch_pair_scratch(s->nd, s->lv, bd, s->nleaf, 1, s->hcnt.as<uint32_t>(), kPairCapH, scol_h, sfr_h,
                             s->pscr_st.as<uint32_t>(), sc + 7, st);
         launch_pair_scratch(s->nd, s->lv, bd, s->nleaf, 0, s->gcnt.as<uint32_t>(), kPairCapG, scol_g, sfr_g,
-                            nullptr, sc + 7, st);
+                            nullptr, sc + 7, st, gmask);
     } else {
         --s->pair_two_pass_left;
         launch_pair_count(s->nd, s->lv, bd, s->nleaf, 1, s->hcnt.as<uint32_t>(), st);
-        launch_pair_count(s->nd, s->lv, bd, s->nleaf, 0, s->gcnt.as<uint32_t>(), st);
+        launch_pair_count(s->nd, s->lv, bd, s->nleaf, 0, s->gcnt.as<uint32_t>(), st, gmask);
     }
     scan_exclusive_u32(s->hcnt.as<uint32_t>(), s->hrow.as<uint32_t>(), s->nleaf, sc + 1, tmp, st);
     scan_exclusive_u32(s->gcnt.as<uint32_t>(), s->grow.as<uint32_t>(), s->nleaf, sc + 2, tmp, st);
@@ -420,7 +428,7 @@ int build_tree(crk_sim *s, int mode = TREE_RULE)
         launch_pair_fill(s->nd, s->lv, bd, s->nleaf, 1, s->hrow.as<uint32_t>(), s->hcol.as<uint32_t>(),
                          s->hfr.as<float4>(), s->hsj.as<uint32_t>(), st);
         launch_pair_fill(s->nd, s->lv, bd, s->nleaf, 0, s->grow.as<uint32_t>(), s->gcol.as<uint32_t>(),
-                         s->gfr.as<float4>(), nullptr, st);
+                         s->gfr.as<float4>(), nullptr, st, gmask);
     } else {
         launch_pair_compact(s->nleaf, kPairCapH, s->hcnt.as<uint32_t>(), s->hrow.as<uint32_t>(), scol_h, sfr_h,
                             s->pscr_st.as<uint32_t>(), s->hcol.as<uint32_t>(), s->hfr.as<float4>(),
@@ -468,6 +476,29 @@ static int size_hydro_lists(crk_sim *s, PassArgs &a, bool want_counts, bool use_
     return CRK_OK;
 }
 
+// Lists and density of the gas groups of a: rows sized from the last step's
+// counts when they are known (a list that outgrows them is counted and
+// filled again), the fill, the density evaluation, and the counts kept for
+// the next step.
+static int density_pass(crk_sim *s, PassArgs &a, bool want_counts)
+{
+    cudaStream_t st = s->st;
+    const int mixed = s->mixed ? 1 : 0;
+    RET(size_hydro_lists(s, a, want_counts, s->cnt_valid && !s->is_pool));
+    launch_hlist_fill(a, mixed, s->cap, want_counts, st);
+    if (a.nl_bound) {
+        CK(cudaMemcpyAsync(s->host_scalars + 6, a.nl_retry, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (s->host_scalars[6]) {
+            RET(size_hydro_lists(s, a, want_counts, false));
+            launch_hlist_fill(a, mixed, s->cap, want_counts, st);
+        }
+    }
+    launch_density_eval(a, mixed, s->cap, want_counts, st);
+    if (!s->is_pool) launch_keep_counts(a, s->cnt_by_id.as<uint32_t>(), st);
+    return CRK_OK;
+}
+
 // One step.  kdk = false: a force evaluation at the current state (dt = 0).
 int run_step(crk_sim *s, const double *dt_per_box, bool want_counts)
 {
@@ -503,22 +534,8 @@ int run_step(crk_sim *s, const double *dt_per_box, bool want_counts)
     const int mixed = s->mixed ? 1 : 0;
     mark(s, PH_D, 0);
     launch_records(a, mixed, st);
-    RET(size_hydro_lists(s, a, want_counts, s->cnt_valid && !s->is_pool));
-    launch_hlist_fill(a, mixed, s->cap, want_counts, st);
-    if (a.nl_bound) {
-        // a list outgrew the rows sized from the last step: count and fill again
-        CK(cudaMemcpyAsync(s->host_scalars + 6, a.nl_retry, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        if (s->host_scalars[6]) {
-            RET(size_hydro_lists(s, a, want_counts, false));
-            launch_hlist_fill(a, mixed, s->cap, want_counts, st);
-        }
-    }
-    launch_density_eval(a, mixed, s->cap, want_counts, st);
-    if (!s->is_pool) {
-        launch_keep_counts(a, s->cnt_by_id.as<uint32_t>(), st);
-        s->cnt_valid = true;
-    }
+    RET(density_pass(s, a, want_counts));
+    if (!s->is_pool) s->cnt_valid = true;
     mark(s, PH_D, 1);
     mark(s, PH_M, 0);
     launch_moments(a, mixed, s->cap, st);
@@ -801,16 +818,18 @@ static int run_substep(crk_sim *s, int sub, int depth, double dt_long, double et
     launch_kick_drift_bins(s->sa, s->boxes_d.as<BoxDev>(), s->n, sub, depth, d,
                            s->nfloor.as<unsigned long long>(), st);
     mark(s, PH_KICK, 1);
-    RET(build_tree(s, sub == 0 ? TREE_SORT : TREE_KEEP));
-    // particles active at t_(sub+1): bin >= depth - trailing_zeros(sub + 1)
+    // particles active at t_(sub+1): bin >= depth - trailing_zeros(sub + 1);
+    // the tree build flags their leaves (fh) and gives only those gravity rows
     const int t = sub + 1;
     int tz = 0;
     while (!((t >> tz) & 1)) ++tz;
     const int bmin = depth - tz;
+    s->bins_bmin = bmin;
+    const int rc_tree = build_tree(s, sub == 0 ? TREE_SORT : TREE_KEEP);
+    s->bins_bmin = -1;
+    RET(rc_tree);
     const size_t nl = (size_t)std::max(s->nleaf, 1);
-    RET(s->bflag.ensure(3 * nl));
     uint8_t *fh = s->bflag.as<uint8_t>(), *fm = fh + nl, *fd = fm + nl;
-    launch_leaf_active(s->lv, s->nleaf, s->sa.bin, bmin, fh, st);
     launch_leaf_expand(s->hrow.as<uint32_t>(), s->hcol.as<uint32_t>(), s->nleaf, fh, fm, st);
     launch_leaf_expand(s->hrow.as<uint32_t>(), s->hcol.as<uint32_t>(), s->nleaf, fm, fd, st);
     const size_t ng = (size_t)std::max<uint32_t>(std::max(s->n_ggas, s->n_gall), 1);
@@ -852,7 +871,7 @@ static int run_substep(crk_sim *s, int sub, int depth, double dt_long, double et
     aG.n_gall = nG;
     mark(s, PH_D, 0);
     launch_records(a, mixed, st);
-    RET(size_hydro_lists(s, aD, false));
+    RET(density_pass(s, aD, false));
     PassArgs aM = aD, aH = aD;
     aM.ggas = gM;
     aM.n_ggas = nM;
@@ -860,7 +879,6 @@ static int run_substep(crk_sim *s, int sub, int depth, double dt_long, double et
     aH.ggas = gH;
     aH.n_ggas = nH;
     aH.lmap = s->bmap[1].as<uint32_t>();
-    launch_density(aD, mixed, s->cap, false, st);
     mark(s, PH_D, 1);
     mark(s, PH_M, 0);
     launch_moments(aM, mixed, s->cap, st);

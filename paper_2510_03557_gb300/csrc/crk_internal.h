@@ -148,22 +148,22 @@ void launch_build_nodes(Nodes &nd, int nleaf, cudaStream_t st);
 void launch_group_count(const Leaves &lv, int nleaf, int gas_only, uint32_t *counts, cudaStream_t st);
 void launch_group_fill(const Leaves &lv, int nleaf, int gas_only, const uint32_t *off, uint2 *groups,
                        cudaStream_t st);
+// mask (optional): leaves without a 1 get an empty row
 void launch_pair_count(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, int nleaf,
-                       int hydro, uint32_t *counts, cudaStream_t st);
+                       int hydro, uint32_t *counts, cudaStream_t st, const uint8_t *mask = nullptr);
 void launch_pair_scratch(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, int nleaf, int hydro,
                          uint32_t *counts, uint32_t cap, uint32_t *col, float4 *frame, uint32_t *start,
-                         uint32_t *overflow, cudaStream_t st);
+                         uint32_t *overflow, cudaStream_t st, const uint8_t *mask = nullptr);
 void launch_pair_compact(int nleaf, uint32_t cap, const uint32_t *counts, const uint32_t *row,
                          const uint32_t *scol, const float4 *sframe, const uint32_t *sstart, uint32_t *col,
                          float4 *frame, uint32_t *start, cudaStream_t st);
 void launch_pair_fill(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, int nleaf,
                       int hydro, const uint32_t *row, uint32_t *col, float4 *frame, uint32_t *start,
-                      cudaStream_t st);
+                      cudaStream_t st, const uint8_t *mask = nullptr);
 
 // ---- passes (passes.cu) ----
 void launch_records(const PassArgs &a, int mixed, cudaStream_t st);
 void launch_hlist_count(const PassArgs &a, int mixed, int cap, bool count, cudaStream_t st);
-void launch_density(const PassArgs &a, int mixed, int cap, bool count, cudaStream_t st);
 void launch_hlist_fill(const PassArgs &a, int mixed, int cap, bool count, cudaStream_t st);
 void launch_density_eval(const PassArgs &a, int mixed, int cap, bool count, cudaStream_t st);
 void launch_hlist_bound(const PassArgs &a, const uint32_t *cnt_by_id, cudaStream_t st);

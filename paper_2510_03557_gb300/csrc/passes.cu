@@ -1624,19 +1624,6 @@ void density_eval_dispatch(const PassArgs &a, bool count, cudaStream_t st)
 }
 
 template <typename R, int JMAX>
-void density_dispatch(const PassArgs &a, bool count, cudaStream_t st)
-{
-    const size_t smf = (size_t)kWarps * hfill_warp_bytes<R, JMAX>();
-    if (count) {
-        launch_warp_kernel(hlist_fill_k<R, JMAX, true>, a.n_ggas, smf, a, st);
-        launch_warp_kernel(density_k<R, JMAX, true>, a.n_ggas, 0, a, st);
-    } else {
-        launch_warp_kernel(hlist_fill_k<R, JMAX, false>, a.n_ggas, smf, a, st);
-        launch_warp_kernel(density_k<R, JMAX, false>, a.n_ggas, 0, a, st);
-    }
-}
-
-template <typename R, int JMAX>
 void gravity_dispatch(const PassArgs &a, bool count, cudaStream_t st)
 {
     const size_t sm = (size_t)kWarps * tile_warp_bytes<R, JMAX>();
@@ -1702,13 +1689,6 @@ void launch_hlist_count(const PassArgs &a, int mixed, int cap, bool count, cudaS
     if (a.n_ggas == 0) return;
     CRK_BY_CAP(hlist_count_dispatch, a, count, st);
     note_launches(1);
-}
-
-void launch_density(const PassArgs &a, int mixed, int cap, bool count, cudaStream_t st)
-{
-    if (a.n_ggas == 0) return;
-    CRK_BY_CAP(density_dispatch, a, count, st);
-    note_launches(2);
 }
 
 void launch_hlist_fill(const PassArgs &a, int mixed, int cap, bool count, cudaStream_t st)

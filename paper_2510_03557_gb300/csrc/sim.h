@@ -98,6 +98,7 @@ struct crk_sim {
     DBuf cnt_by_id, nl_retry;
     DBuf pscr_col, pscr_fr, pscr_st;    // leaf-pair rows of fixed capacity before packing
     int pair_two_pass_left = 0;         // builds left that walk the pair lists twice (after an overflow)
+    int bins_bmin = -1;                 // hierarchical substep: smallest active bin (-1: not in a substep)
     bool cnt_valid = false;
     bool is_pool = false;
     int64_t nl_rows = 0;

@@ -486,12 +486,14 @@ __device__ __forceinline__ float4 pair_frame(const Leaves &lv, int I, int J, dou
 template <int MODE>
 __global__ void pair_walk_k(Nodes nd, Leaves lv, const BoxDev *__restrict__ boxes, int nleaf,
                             int hydro, uint32_t *counts, const uint32_t *__restrict__ row,
-                            uint32_t *col, float4 *frame, uint32_t *start, uint32_t cap, uint32_t *overflow)
+                            uint32_t *col, float4 *frame, uint32_t *start, uint32_t cap, uint32_t *overflow,
+                            const uint8_t *__restrict__ mask)
 {
     constexpr bool FILL = MODE != 0;
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nleaf) return;
-    if (hydro && lv.species[I] != CRK_GAS) {
+    // leaves without a row: DM leaves of the hydro list, unmasked leaves
+    if ((hydro && lv.species[I] != CRK_GAS) || (mask && !mask[I])) {
         if (MODE != 1) counts[I] = 0;
         return;
     }
@@ -802,21 +804,21 @@ void launch_build_nodes(Nodes &nd, int nleaf, cudaStream_t st)
 }
 
 void launch_pair_count(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, int nleaf,
-                       int hydro, uint32_t *counts, cudaStream_t st)
+                       int hydro, uint32_t *counts, cudaStream_t st, const uint8_t *mask)
 {
     if (nleaf <= 0) return;
     pair_walk_k<0><<<grid_for(nleaf, 128), 128, 0, st>>>(nd, lv, boxes, nleaf, hydro, counts,
-                                                           nullptr, nullptr, nullptr, nullptr, 0u, nullptr);
+                                                           nullptr, nullptr, nullptr, nullptr, 0u, nullptr, mask);
     note_launches(1);
 }
 
 void launch_pair_scratch(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, int nleaf, int hydro,
                          uint32_t *counts, uint32_t cap, uint32_t *col, float4 *frame, uint32_t *start,
-                         uint32_t *overflow, cudaStream_t st)
+                         uint32_t *overflow, cudaStream_t st, const uint8_t *mask)
 {
     if (nleaf <= 0) return;
     pair_walk_k<2><<<grid_for(nleaf, 128), 128, 0, st>>>(nd, lv, boxes, nleaf, hydro, counts, nullptr, col,
-                                                           frame, start, cap, overflow);
+                                                           frame, start, cap, overflow, mask);
     note_launches(1);
 }
 
@@ -832,11 +834,11 @@ void launch_pair_compact(int nleaf, uint32_t cap, const uint32_t *counts, const 
 
 void launch_pair_fill(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, int nleaf,
                       int hydro, const uint32_t *row, uint32_t *col, float4 *frame, uint32_t *start,
-                      cudaStream_t st)
+                      cudaStream_t st, const uint8_t *mask)
 {
     if (nleaf <= 0) return;
     pair_walk_k<1><<<grid_for(nleaf, 128), 128, 0, st>>>(nd, lv, boxes, nleaf, hydro, nullptr,
-                                                           row, col, frame, start, 0u, nullptr);
+                                                           row, col, frame, start, 0u, nullptr, mask);
     note_launches(1);
 }
 
