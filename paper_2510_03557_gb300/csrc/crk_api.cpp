@@ -331,17 +331,32 @@ int build_tree(crk_sim *s, int mode = TREE_RULE)
     } else {
         launch_morton_keys(s->sa, s->boxes_d.as<BoxDev>(), n, s->slot_bits, s->keys.as<uint64_t>(),
                            s->vals.as<uint32_t>(), st);
+        // One box: sort the key bits down to sort_levels octree levels below
+        // the chaining-mesh bin (the leaves of the last sort used fewer; the
+        // order inside a leaf comes from the k-d pass): 3-5 radix passes
+        // instead of 8.  Several boxes sort every bit, so that a box's leaves
+        // and their order never depend on the other boxes (the service's
+        // alone-equals-in-the-mix guarantee).
+        int first_bit = 0;
+        if (s->slot_bits == 0 && s->nbox == 1)
+            first_bit = std::max(s->boxes[0].cm_shift - 3 * s->sort_levels, 0);
         uint64_t *ko;
         uint32_t *vo;
         radix_sort_u64(s->keys.as<uint64_t>(), s->vals.as<uint32_t>(), s->keys_alt.as<uint64_t>(),
-                       s->vals_alt.as<uint32_t>(), n, s->counts.as<uint32_t>(), tmp, 0, 64, st, &ko, &vo);
+                       s->vals_alt.as<uint32_t>(), n, s->counts.as<uint32_t>(), tmp, first_bit, 64, st, &ko,
+                       &vo);
         // particles of removed pool slots carry the largest key and sort last
         const int64_t nlive = n - s->n_dead;
-        launch_leaf_flags(ko, s->slot_bits, s->boxes_d.as<BoxDev>(), nlive, s->cap, s->flags.as<uint32_t>(), st);
+        CK(cudaMemsetAsync(sc + 12, 0, 2 * sizeof(uint32_t), st));
+        launch_leaf_flags(ko, s->slot_bits, s->boxes_d.as<BoxDev>(), nlive, s->cap, s->flags.as<uint32_t>(),
+                          first_bit, sc + 12, st);
         scan_exclusive_u32(s->flags.as<uint32_t>(), s->flag_scan.as<uint32_t>(), nlive, sc + 0, tmp, st);
-        CK(cudaMemcpyAsync(s->host_scalars, sc, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(s->host_scalars, sc, 14 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         s->nleaf = (int)s->host_scalars[0];
+        // the next sort: two levels below the deepest leaf of this one, or all
+        // levels when a cell had to be cut by count above unsorted levels
+        s->sort_levels = s->host_scalars[13] ? kAllLevels : std::min(kAllLevels, (int)s->host_scalars[12] + 2);
         launch_leaf_setup(s->flags.as<uint32_t>(), s->flag_scan.as<uint32_t>(), nlive, s->nleaf, s->lv, st);
         // k-d order inside every leaf (on the unsorted state through the sort's
         // permutation), then one gather of the whole state

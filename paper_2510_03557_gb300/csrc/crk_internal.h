@@ -137,7 +137,7 @@ void launch_morton_keys(const State &s, const BoxDev *boxes, int64_t n, int slot
 void launch_permute(const State &src, const State &dst, const uint32_t *perm, int64_t n,
                     cudaStream_t st);
 void launch_leaf_flags(const uint64_t *keys, int slot_bits, const BoxDev *boxes, int64_t n,
-                       int cap, uint32_t *flags, cudaStream_t st);
+                       int cap, uint32_t *flags, int first_bit, uint32_t *stats, cudaStream_t st);
 void launch_leaf_kd_order(const State &unsorted, const Leaves &lv, int nleaf, uint32_t *perm,
                           cudaStream_t st);
 void launch_leaf_setup(const uint32_t *flags, const uint32_t *scan, int64_t n, int nleaf,

@@ -46,6 +46,8 @@ struct DBuf {
 // Leaf pairs a leaf's hydro and gravity rows hold before the lists are
 // walked twice (count, then fill).
 constexpr uint32_t kPairCapH = 128, kPairCapG = 256;
+// Octree levels of a 21-bit-per-axis Morton key (all of them).
+constexpr int kAllLevels = 21;
 
 enum Phase { PH_TREE, PH_PAIRS, PH_D, PH_M, PH_H, PH_G, PH_KDK, PH_KICK, PH_PM, PH_N };
 
@@ -99,6 +101,7 @@ struct crk_sim {
     DBuf pscr_col, pscr_fr, pscr_st;    // leaf-pair rows of fixed capacity before packing
     int pair_two_pass_left = 0;         // builds left that walk the pair lists twice (after an overflow)
     int bins_bmin = -1;                 // hierarchical substep: smallest active bin (-1: not in a substep)
+    int sort_levels = crk::kAllLevels;  // octree levels below the bins that the next sort orders
     bool cnt_valid = false;
     bool is_pool = false;
     int64_t nl_rows = 0;

@@ -245,16 +245,23 @@ __device__ __forceinline__ bool cell_fits(const uint64_t *__restrict__ keys, int
 // chaining-mesh bin, that holds at most cap particles of one (box, species).
 // Cells are found per particle by a binary search over the levels (a cell's
 // count only shrinks with depth).  Particles that share even the finest cell
-// are cut by count.  flags[k] = 1 where a leaf starts.
+// are cut by count.  flags[k] = 1 where a leaf starts.  The keys are sorted
+// on their bits from first_bit up only, so levels whose cells need lower bits
+// are not used: a cell at the deepest sorted level that still holds more than
+// cap particles is cut by count.  stats[0] gets the deepest level used,
+// stats[1] is set when such a cut happened above levels that exist.
 __global__ void leaf_flags_k(const uint64_t *__restrict__ keys, int sb,
-                             const BoxDev *__restrict__ boxes, int64_t n, int cap, uint32_t *flags)
+                             const BoxDev *__restrict__ boxes, int64_t n, int cap, uint32_t *flags,
+                             int first_bit, uint32_t *stats)
 {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const uint64_t key = keys[k];
     const uint32_t slot = sb ? (uint32_t)(key >> (64 - sb)) : 0u;
     const int s0 = boxes[slot].cm_shift;     // shift of the chaining-mesh bin
-    const int lmax = s0 / 3;                 // deepest level with a non-negative shift
+    const int lall = s0 / 3;                 // deepest level with a non-negative shift
+    const int lsorted = (s0 - first_bit) / 3;
+    const int lmax = lall < lsorted ? lall : lsorted;
     int la = 0, lb = lmax + 1;
     int64_t lo = 0;
     while (la < lb) {
@@ -265,7 +272,9 @@ __global__ void leaf_flags_k(const uint64_t *__restrict__ keys, int sb,
     if (la <= lmax) {
         cell_fits(keys, n, k, key, s0 - 3 * la, cap, lo);
         flags[k] = (k == lo) ? 1u : 0u;
+        if (k == lo) atomicMax(stats, (uint32_t)la);
     } else {
+        if (k % cap == 0 && lmax < lall) atomicOr(stats + 1, 1u);
         const int s = s0 - 3 * lmax;
         const uint64_t g = key >> s;
         int64_t a = 0, b = k;
@@ -759,10 +768,10 @@ void launch_permute(const State &src, const State &dst, const uint32_t *perm, in
 }
 
 void launch_leaf_flags(const uint64_t *keys, int slot_bits, const BoxDev *boxes, int64_t n,
-                       int cap, uint32_t *flags, cudaStream_t st)
+                       int cap, uint32_t *flags, int first_bit, uint32_t *stats, cudaStream_t st)
 {
     if (n <= 0) return;
-    leaf_flags_k<<<grid_for(n, kT), kT, 0, st>>>(keys, slot_bits, boxes, n, cap, flags);
+    leaf_flags_k<<<grid_for(n, kT), kT, 0, st>>>(keys, slot_bits, boxes, n, cap, flags, first_bit, stats);
     note_launches(1);
 }
 
