@@ -157,16 +157,10 @@ int reserve(crk_sim *s, int64_t n)
     s->lv.clo = s->lv_chunk[0].as<float4>();
     s->lv.chi = s->lv_chunk[1].as<float4>();
     const size_t nnode = 2 * nn + 64;
-    for (int k = 0; k < 7; ++k) RET(s->nd_f[k].ensure(nnode * 4));
+    for (int k = 0; k < 2; ++k) RET(s->nd_f[k].ensure(nnode * sizeof(float4)));
     RET(s->nd_slot.ensure(nnode * 4));
-    s->nd.lox = s->nd_f[0].as<float>();
-    s->nd.loy = s->nd_f[1].as<float>();
-    s->nd.loz = s->nd_f[2].as<float>();
-    s->nd.hix = s->nd_f[3].as<float>();
-    s->nd.hiy = s->nd_f[4].as<float>();
-    s->nd.hiz = s->nd_f[5].as<float>();
-    s->nd.hmax = s->nd_f[6].as<float>();
-    s->nd.slot = s->nd_slot.as<int32_t>();
+    s->nd.lo = s->nd_f[0].as<float4>();
+    s->nd.hi = s->nd_f[1].as<float4>();
     RET(s->hrow.ensure((nn + 1) * 4));
     RET(s->grow.ensure((nn + 1) * 4));
     RET(s->hcnt.ensure((nn + 1) * 4));
@@ -354,6 +348,8 @@ int build_tree(crk_sim *s, int mode = TREE_RULE)
         CK(cudaMemcpyAsync(s->host_scalars, sc, 14 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         s->nleaf = (int)s->host_scalars[0];
+        if (s->nleaf >= (1 << 26))  // the leaf-pair walk packs leaf indices into 26 bits
+            return fail(CRK_EOVERFLOW, "%d leaves: at most 2^26 - 1", s->nleaf);
         // the next sort: two levels below the deepest leaf of this one, or all
         // levels when a cell had to be cut by count above unsorted levels
         s->sort_levels = s->host_scalars[13] ? kAllLevels : std::min(kAllLevels, (int)s->host_scalars[12] + 2);

@@ -57,9 +57,8 @@ constexpr int kChunks = 4;   // chunks of 32 per leaf (leaf capacity <= 128)
 // Implicit binary hierarchy over the leaf array: level l node k covers
 // leaves [k << l, min((k+1) << l, nleaf)).
 struct Nodes {
-    float *lox, *loy, *loz, *hix, *hiy, *hiz;  // conservative FP32 boxes
-    float *hmax;             // max H of gas leaves below (0: no gas)
-    int32_t *slot;           // box slot, -1 when the node spans several boxes
+    float4 *lo;              // conservative FP32 box: lower corner, w = max H of gas leaves below (0: no gas)
+    float4 *hi;              // upper corner, w = box slot as int bits (-1 when the node spans several boxes)
     int levels;
     int64_t level_off[40];   // first node of each level
     int64_t total;

@@ -391,12 +391,10 @@ __global__ void leaf_bounds_k(State s, const BoxDev *__restrict__ boxes, Leaves 
         lv.hmax[w] = hm;
         lv.slot[w] = s.slot[s0];
         lv.species[w] = s.species[s0];
-        nd.lox[w] = __double2float_rd(ref[0] + lo[0]); nd.loy[w] = __double2float_rd(ref[1] + lo[1]);
-        nd.loz[w] = __double2float_rd(ref[2] + lo[2]);
-        nd.hix[w] = __double2float_ru(ref[0] + hi[0]); nd.hiy[w] = __double2float_ru(ref[1] + hi[1]);
-        nd.hiz[w] = __double2float_ru(ref[2] + hi[2]);
-        nd.hmax[w] = hm;
-        nd.slot[w] = (int32_t)s.slot[s0];
+        nd.lo[w] = make_float4(__double2float_rd(ref[0] + lo[0]), __double2float_rd(ref[1] + lo[1]),
+                               __double2float_rd(ref[2] + lo[2]), hm);
+        nd.hi[w] = make_float4(__double2float_ru(ref[0] + hi[0]), __double2float_ru(ref[1] + hi[1]),
+                               __double2float_ru(ref[2] + hi[2]), __int_as_float((int32_t)s.slot[s0]));
     }
     // Boxes of the 32-particle chunks (particle t of the leaf is in chunk t/32),
     // relative to the leaf centre, rounded outward; empty chunks get an
@@ -440,21 +438,17 @@ __global__ void node_level_k(Nodes nd, int64_t oc, int64_t ncld, int64_t op, int
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= npar) return;
     int64_t c0 = oc + 2 * k, c1 = oc + 2 * k + 1;
-    float lox = nd.lox[c0], loy = nd.loy[c0], loz = nd.loz[c0];
-    float hix = nd.hix[c0], hiy = nd.hiy[c0], hiz = nd.hiz[c0];
-    float hm = nd.hmax[c0];
-    int32_t sl = nd.slot[c0];
+    float4 lo = nd.lo[c0], hi = nd.hi[c0];
     if (2 * k + 1 < ncld) {
-        lox = fminf(lox, nd.lox[c1]); loy = fminf(loy, nd.loy[c1]); loz = fminf(loz, nd.loz[c1]);
-        hix = fmaxf(hix, nd.hix[c1]); hiy = fmaxf(hiy, nd.hiy[c1]); hiz = fmaxf(hiz, nd.hiz[c1]);
-        hm = fmaxf(hm, nd.hmax[c1]);
-        if (nd.slot[c1] != sl) sl = -1;
+        const float4 l1 = nd.lo[c1], h1 = nd.hi[c1];
+        lo.x = fminf(lo.x, l1.x); lo.y = fminf(lo.y, l1.y); lo.z = fminf(lo.z, l1.z);
+        lo.w = fmaxf(lo.w, l1.w);  // max H
+        hi.x = fmaxf(hi.x, h1.x); hi.y = fmaxf(hi.y, h1.y); hi.z = fmaxf(hi.z, h1.z);
+        if (__float_as_int(h1.w) != __float_as_int(hi.w)) hi.w = __int_as_float(-1);
     }
     int64_t o = op + k;
-    nd.lox[o] = lox; nd.loy[o] = loy; nd.loz[o] = loz;
-    nd.hix[o] = hix; nd.hiy[o] = hiy; nd.hiz[o] = hiz;
-    nd.hmax[o] = hm;
-    nd.slot[o] = sl;
+    nd.lo[o] = lo;
+    nd.hi[o] = hi;
 }
 
 // Depth-first walk of the leaf hierarchy from leaf I, left child first, so a
@@ -509,41 +503,42 @@ __global__ void pair_walk_k(Nodes nd, Leaves lv, const BoxDev *__restrict__ boxe
     const int32_t slot = (int32_t)lv.slot[I];
     const BoxDev bx = boxes[slot];
     const float L = (float)bx.L, hL = 0.5f * L;
-    const float cix = 0.5f * (nd.lox[I] + nd.hix[I]), ciy = 0.5f * (nd.loy[I] + nd.hiy[I]),
-                ciz = 0.5f * (nd.loz[I] + nd.hiz[I]);
-    const float eix = 0.5f * (nd.hix[I] - nd.lox[I]), eiy = 0.5f * (nd.hiy[I] - nd.loy[I]),
-                eiz = 0.5f * (nd.hiz[I] - nd.loz[I]);
+    const float4 ilo = nd.lo[I], ihi = nd.hi[I];
+    const float cix = 0.5f * (ilo.x + ihi.x), ciy = 0.5f * (ilo.y + ihi.y), ciz = 0.5f * (ilo.z + ihi.z);
+    const float eix = 0.5f * (ihi.x - ilo.x), eiy = 0.5f * (ihi.y - ilo.y), eiz = 0.5f * (ihi.z - ilo.z);
     const float RI = hydro ? lv.hmax[I] : (float)bx.r_cut;
     const size_t base = MODE == 1 ? (size_t)row[I] : MODE == 2 ? (size_t)I * cap : 0u;
     uint32_t cnt = 0;
-    int2 stack[96];
+    // stack entries: level << 26 | index within the level (nleaf < 2^26)
+    uint32_t stack[96];
     int sp = 0;
-    stack[sp++] = make_int2(nd.levels - 1, 0);
+    stack[sp++] = (uint32_t)(nd.levels - 1) << 26;
     while (sp > 0) {
-        int2 e = stack[--sp];
-        const int l = e.x, k = e.y;
+        const uint32_t e = stack[--sp];
+        const int l = (int)(e >> 26), k = (int)(e & 0x3ffffffu);
         const int64_t off = nd.level_off[l] + k;
-        const int32_t ns = nd.slot[off];
+        const float4 nlo = nd.lo[off], nhi = nd.hi[off];
+        const int32_t ns = __float_as_int(nhi.w);
         if (ns != -1 && ns != slot) continue;
-        const float nh = nd.hmax[off];
+        const float nh = nlo.w;
         if (hydro && !(nh > 0.f)) continue;
         if (ns == slot) {
             const float R = hydro ? fmaxf(RI, nh) : RI;
             const float Rm = R * 1.0001f + 1e-5f * L;
             float gap2 = 0.f;
             float d, g;
-            d = 0.5f * (nd.lox[off] + nd.hix[off]) - cix;
+            d = 0.5f * (nlo.x + nhi.x) - cix;
             if (d >= hL) d -= L; else if (d < -hL) d += L;
             // extents summed first: the test is exactly symmetric in (I, J)
-            g = fabsf(d) - (eix + 0.5f * (nd.hix[off] - nd.lox[off]));
+            g = fabsf(d) - (eix + 0.5f * (nhi.x - nlo.x));
             if (g > 0.f) gap2 += g * g;
-            d = 0.5f * (nd.loy[off] + nd.hiy[off]) - ciy;
+            d = 0.5f * (nlo.y + nhi.y) - ciy;
             if (d >= hL) d -= L; else if (d < -hL) d += L;
-            g = fabsf(d) - (eiy + 0.5f * (nd.hiy[off] - nd.loy[off]));
+            g = fabsf(d) - (eiy + 0.5f * (nhi.y - nlo.y));
             if (g > 0.f) gap2 += g * g;
-            d = 0.5f * (nd.loz[off] + nd.hiz[off]) - ciz;
+            d = 0.5f * (nlo.z + nhi.z) - ciz;
             if (d >= hL) d -= L; else if (d < -hL) d += L;
-            g = fabsf(d) - (eiz + 0.5f * (nd.hiz[off] - nd.loz[off]));
+            g = fabsf(d) - (eiz + 0.5f * (nhi.z - nlo.z));
             if (g > 0.f) gap2 += g * g;
             if (gap2 >= Rm * Rm) continue;
         }
@@ -556,8 +551,9 @@ __global__ void pair_walk_k(Nodes nd, Leaves lv, const BoxDev *__restrict__ boxe
             ++cnt;
         } else {
             const int64_t nchild = nd.level_off[l] - nd.level_off[l - 1];
-            if ((int64_t)2 * k + 1 < nchild) stack[sp++] = make_int2(l - 1, 2 * k + 1);
-            stack[sp++] = make_int2(l - 1, 2 * k);
+            const uint32_t lc = (uint32_t)(l - 1) << 26;
+            if ((int64_t)2 * k + 1 < nchild) stack[sp++] = lc | (uint32_t)(2 * k + 1);
+            stack[sp++] = lc | (uint32_t)(2 * k);
         }
     }
     if (MODE != 1) counts[I] = cnt;
