@@ -43,8 +43,8 @@ FLOP_PER_PAIR = {"density": 22, "moments": 125, "hydro": 183, "gravity": 41}
 # (2x128^3 Gaussian field, leaf capacity 128; density = list bounds + fill +
 # evaluation + kept counts).  They describe the kernels of the csrc/passes.cu with this
 # SHA-256 only; for any other source the bench reports no traffic.
-TRAFFIC_SOURCE_SHA256 = "8f76f58adf6c0502dc31b5d7f42590ea3c2e9bc11eeada0a7ffe6436509dcb42"
-TRAFFIC_BYTES_PER_PARTICLE = {"gravity": 81.4, "hydro": 701.9, "moments": 690.9, "density": 1677.5}
+TRAFFIC_SOURCE_SHA256 = "bb16f3ed996cbcd2e53403d4717caa7ddec593b53dfcc65bedb15b7200ef0791"
+TRAFFIC_BYTES_PER_PARTICLE = {"gravity": 81.4, "hydro": 701.3, "moments": 690.8, "density": 1677.8}
 
 
 def _traffic(kernel: str, particles: int, leaf_cap: int):
