@@ -505,7 +505,8 @@ static int density_pass(crk_sim *s, PassArgs &a, bool want_counts)
             launch_hlist_fill(a, mixed, s->cap, want_counts, st);
         }
     }
-    launch_density_eval(a, mixed, s->cap, want_counts, st);
+    // without neighbour counts the fill pass has formed the density already
+    if (want_counts) launch_density_eval(a, mixed, s->cap, want_counts, st);
     if (!s->is_pool) launch_keep_counts(a, s->cnt_by_id.as<uint32_t>(), st);
     return CRK_OK;
 }

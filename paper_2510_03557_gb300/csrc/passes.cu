@@ -722,6 +722,26 @@ __global__ void __launch_bounds__(kBlock) hlist_count_k(PassArgs a)
     if (G.act) a.nl_cnt[i] = cnt;
 }
 
+// V = m/rho, P = (gamma-1) rho u^, c = sqrt(gamma (gamma-1) u^) into the
+// hydro records 0 (position, V) and 2 (rho, P, c).
+template <typename R>
+__device__ __forceinline__ void density_out(const PassArgs &a, uint32_t i, const Vec4<R> &ri, R rho)
+{
+    const BoxDev &bx = a.boxes[a.s.slot[i]];
+    const R uh = reinterpret_cast<const R *>(a.uhat)[i];
+    const R gam = (R)bx.gamma;
+    const R V = Real<R>::div(ri.w, rho);
+    Vec4<R> r0;
+    r0.x = ri.x; r0.y = ri.y; r0.z = ri.z; r0.w = V;
+    reinterpret_cast<Vec4<R> *>(a.hrec[0])[i] = r0;
+    Vec4<R> r2v;
+    r2v.x = rho;
+    r2v.y = (gam - (R)1) * rho * uh;
+    r2v.z = Real<R>::sqrt_(gam * (gam - (R)1) * uh);
+    r2v.w = 0;
+    reinterpret_cast<Vec4<R> *>(a.hrec[2])[i] = r2v;
+}
+
 // Writes every gas particle's hydro neighbour list (the same sets the count
 // pass counted, from the same staging and test).
 template <typename R, int JMAX, bool COUNT>
@@ -756,6 +776,7 @@ __global__ void __launch_bounds__(kBlock) hlist_fill_k(PassArgs a)
     // from the previous step
     const uint32_t room = G.act ? (a.nl_bound ? a.nl_len[gi] : a.nl_cnt[i]) : 0u;
     uint32_t k = 0;
+    R rho = 0;  // without neighbour counts the fill pass also forms the density
     const RowOrder order(a.hrow[I + 1] - prow);
     for (uint32_t t = 0; t < order.n; ++t) {
         const uint32_t p = prow + order.at(t);
@@ -785,9 +806,21 @@ __global__ void __launch_bounds__(kBlock) hlist_fill_k(PassArgs a)
             while (bits) {
                 const int b = __ffs(bits) - 1;
                 bits &= bits - 1;
+                const bool gather = (mg[ww] >> b) & 1u;
                 if (k < room)
-                    ring.put(a, k, lane, otag | tslot[32 * ww + b] | (((mg[ww] >> b) & 1u) ? kGather : 0u));
+                    ring.put(a, k, lane, otag | tslot[32 * ww + b] | (gather ? kGather : 0u));
                 ++k;
+                if (!COUNT && gather) {
+                    // the density sum in list order, as the density pass forms it
+                    const R4 rj = tile[32 * ww + b];
+                    R dx, dy, dz;
+                    const R r2 = q.wrap ? sep2<R, true>(rj, q, L, hL, dx, dy, dz) : sep2<R, false>(rj, q, L, hL, dx, dy, dz);
+                    const R qq = Real<R>::sqrt_(r2) * ht.invH;
+                    R om = (R)1 - qq;
+                    om = om > (R)0 ? om : (R)0;
+                    const R om2 = om * om;
+                    rho += rj.w * ht.cW * om2 * om2 * om2 * ((R)1 + qq * ((R)6 + qq * (R)(35.0 / 3.0)));
+                }
             }
         }
         // rows every active lane has passed
@@ -803,6 +836,7 @@ __global__ void __launch_bounds__(kBlock) hlist_fill_k(PassArgs a)
         a.nl_cnt[i] = k < room ? k : room;
         set_error(a.err, CRK_EOVERFLOW, a.s.id[i]);
     }
+    if (!COUNT && G.act) density_out<R>(a, i, ri, rho);
 }
 
 // Rows of every gas group from the previous step's list sizes (by original
@@ -884,6 +918,7 @@ __device__ __forceinline__ R list_sep2(const Vec4<R> &rj, const Vec4<R> &ri, con
 }
 
 // ------------------------------------------------------------- density D
+
 // rho_i = sum_{j in N_i + {i}} m_j W(r, h_i); V = m/rho; P = (gamma-1) rho u^;
 // c = sqrt(gamma (gamma-1) u^).  Optional: size and hash of N_i, the FP32
 // decision re-taken in FP64 inside the guard band.
@@ -955,18 +990,7 @@ __global__ void __launch_bounds__(kBlock) density_k(PassArgs a)
         }
     }
     if (!G.act) return;
-    const R uh = reinterpret_cast<const R *>(a.uhat)[i];
-    const R gam = (R)bx.gamma;
-    const R V = Real<R>::div(ri.w, rho);
-    R4 r0;
-    r0.x = ri.x; r0.y = ri.y; r0.z = ri.z; r0.w = V;
-    reinterpret_cast<R4 *>(a.hrec[0])[i] = r0;
-    R4 r2v;
-    r2v.x = rho;
-    r2v.y = (gam - (R)1) * rho * uh;
-    r2v.z = Real<R>::sqrt_(gam * (gam - (R)1) * uh);
-    r2v.w = 0;
-    reinterpret_cast<R4 *>(a.hrec[2])[i] = r2v;
+    density_out<R>(a, i, ri, rho);
     if (COUNT) {
         if (a.nbr_count) a.nbr_count[i] = nc;
         if (a.nbr_hash) a.nbr_hash[i] = hs;
