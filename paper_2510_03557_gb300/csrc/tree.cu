@@ -642,7 +642,7 @@ __global__ void kd_order_k(State s, Leaves lv, int nleaf, uint32_t *perm)
     const int L = blockIdx.x * kKdWarps + (int)w;
     if (L >= nleaf) return;
     const uint32_t s0 = lv.start[L], c = lv.count[L];
-    if (c <= 32u) return;
+    if (c <= 1u) return;
     KdScratch &S = scratch[w];
     const uint32_t id0 = perm[s0];
     const double x0 = s.x[id0], y0 = s.y[id0], z0 = s.z[id0];
@@ -655,6 +655,9 @@ __global__ void kd_order_k(State s, Leaves lv, int nleaf, uint32_t *perm)
     }
     __syncwarp();
     const uint32_t g = (c + 31u) / 32u;
+    // every leaf is ordered, small ones too: the order inside a leaf is then a
+    // function of its particles' positions alone, whatever order the sort
+    // left them in (it orders only the key bits the leaves need)
     kd_sort_range(S, 0, c, lane);
     const uint32_t cut = 32u * ((g + 1u) / 2u);
     if (cut > 32u) kd_sort_range(S, 0, cut, lane);

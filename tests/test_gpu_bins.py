@@ -142,3 +142,35 @@ def test_bins_argument_errors(crk):
         with pytest.raises(crk.CrkError) as e:
             crk.crk_step_bins(sim.handle, 1e-3, 2, 1)
         assert e.value.code == crk.CRK_EINVAL
+
+
+def test_batched_boxes_step_as_they_do_alone(crk):
+    """Hierarchical steps of two boxes in one handle: each box ends exactly
+    where it ends alone (boxes never interact, every box sorts all key bits
+    and its active sets, lists and sums are its own)."""
+    b1 = _box()
+    b2 = wl.gaussian_field_box(10, seed=8)
+    b2.vel = b2.vel * 20.0
+    boxes = [b1, b2]
+    cat = lambda k: np.concatenate([getattr(b, k) for b in boxes])
+    with crk.Sim(crk.box_physics(b1), precision=1) as sim:
+        crk.crk_load_boxes(sim.handle, [b.n for b in boxes], [crk.box_physics(b) for b in boxes],
+                           cat("pos"), cat("vel"), cat("mass"), cat("u"), cat("h"), cat("species"))
+        sim.n = b1.n + b2.n
+        crk.crk_step_bins(sim.handle, DT_LONG, DEPTH, 1, ETA, COURANT)
+        pos, vel, u = sim.state()
+        bins = crk.crk_get_bins(sim.handle)
+    off = 0
+    for b in boxes:
+        with crk.Sim(crk.box_physics(b), precision=1) as one:
+            # a one-box batch: the same full sort as the two-box handle
+            crk.crk_load_boxes(one.handle, [b.n], [crk.box_physics(b)], b.pos, b.vel, b.mass, b.u, b.h,
+                               b.species)
+            one.n = b.n
+            crk.crk_step_bins(one.handle, DT_LONG, DEPTH, 1, ETA, COURANT)
+            p1, v1, u1 = one.state()
+            bb = crk.crk_get_bins(one.handle)
+        sl = slice(off, off + b.n)
+        assert np.array_equal(bins[sl], bb)
+        assert np.array_equal(pos[sl], p1) and np.array_equal(vel[sl], v1) and np.array_equal(u[sl], u1)
+        off += b.n
