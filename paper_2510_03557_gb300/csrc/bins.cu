@@ -167,13 +167,15 @@ __global__ void leaf_expand_k(const uint32_t *__restrict__ row, const uint32_t *
     out[I] = f;
 }
 
-// Keep-flags of the work items of a group list (item = (leaf, offset)).
+// Keep-flags of the work items of a group list (item = (leaf, offset)):
+// leaf flagged, and not flagged in exclude (optional).
 __global__ void group_flags_k(const uint2 *__restrict__ groups, uint32_t n, const uint8_t *__restrict__ leaf_flag,
-                              uint32_t *keep)
+                              const uint8_t *__restrict__ exclude, uint32_t *keep)
 {
     const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= n) return;
-    keep[g] = leaf_flag[groups[g].x];
+    const uint32_t L = groups[g].x;
+    keep[g] = leaf_flag[L] && !(exclude && exclude[L]);
 }
 
 // Stable compaction of the kept items; map (optional) gets each kept item's
@@ -242,13 +244,14 @@ void launch_leaf_expand(const uint32_t *row, const uint32_t *col, int nleaf, con
 }
 
 void launch_group_select(const uint2 *groups, uint32_t n, const uint8_t *leaf_flag, uint32_t *keep, uint32_t *pos,
-                         uint32_t *total, uint32_t *tmp, uint2 *out, uint32_t *map, cudaStream_t st)
+                         uint32_t *total, uint32_t *tmp, uint2 *out, uint32_t *map, cudaStream_t st,
+                         const uint8_t *exclude)
 {
     if (n == 0) {
         cudaMemsetAsync(total, 0, sizeof(uint32_t), st);
         return;
     }
-    group_flags_k<<<nblocks(n), kT, 0, st>>>(groups, n, leaf_flag, keep);
+    group_flags_k<<<nblocks(n), kT, 0, st>>>(groups, n, leaf_flag, exclude, keep);
     scan_exclusive_u32(keep, pos, n, total, tmp, st);
     group_compact_k<<<nblocks(n), kT, 0, st>>>(groups, n, keep, pos, out, map);
     note_launches(2);

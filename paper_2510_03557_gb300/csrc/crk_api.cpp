@@ -853,19 +853,21 @@ static int run_substep(crk_sim *s, int sub, int depth, double dt_long, double et
     uint32_t *keep = s->bkeep.as<uint32_t>(), *pos = s->bpos.as<uint32_t>();
     uint2 *gD = s->bgrp[0].as<uint2>(), *gM = s->bgrp[1].as<uint2>(), *gH = s->bgrp[2].as<uint2>(),
           *gG = s->bgrp[3].as<uint2>();
-    launch_group_select(s->grp_gas.as<uint2>(), s->n_ggas, fd, keep, pos, sc + 8, tmp, gD, nullptr, st);
+    // gM: lists and density (the moments groups); gD: the outer ring, density
+    // alone; gG: gravity
+    launch_group_select(s->grp_gas.as<uint2>(), s->n_ggas, fm, keep, pos, sc + 9, tmp, gM, nullptr, st);
+    launch_group_select(s->grp_gas.as<uint2>(), s->n_ggas, fd, keep, pos, sc + 8, tmp, gD, nullptr, st, fm);
     launch_group_select(s->grp_all.as<uint2>(), s->n_gall, fh, keep, pos, sc + 11, tmp, gG, nullptr, st);
-    CK(cudaMemcpyAsync(s->host_scalars + 8, sc + 8, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(s->host_scalars + 8, sc + 8, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(s->host_scalars + 11, sc + 11, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    const uint32_t nD = s->host_scalars[8], nG = s->host_scalars[11];
-    // the moments and hydro groups are taken from the density groups, so
-    // that each keeps the list row the density pass wrote for it
-    launch_group_select(gD, nD, fm, keep, pos, sc + 9, tmp, gM, s->bmap[0].as<uint32_t>(), st);
-    launch_group_select(gD, nD, fh, keep, pos, sc + 10, tmp, gH, s->bmap[1].as<uint32_t>(), st);
-    CK(cudaMemcpyAsync(s->host_scalars + 9, sc + 9, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
+    const uint32_t nD = s->host_scalars[8], nM = s->host_scalars[9], nG = s->host_scalars[11];
+    // the hydro groups are taken from the moments groups, so that each keeps
+    // the list row the fill pass wrote for it
+    launch_group_select(gM, nM, fh, keep, pos, sc + 10, tmp, gH, s->bmap[1].as<uint32_t>(), st);
+    CK(cudaMemcpyAsync(s->host_scalars + 10, sc + 10, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
-    const uint32_t nM = s->host_scalars[9], nH = s->host_scalars[10];
+    const uint32_t nH = s->host_scalars[10];
 
     PassArgs a = pass_args(s);
     a.nbr_count = nullptr;
@@ -876,18 +878,18 @@ static int run_substep(crk_sim *s, int sub, int depth, double dt_long, double et
     a.bdepth = depth;
     a.bd = d;
     const int mixed = s->mixed ? 1 : 0;
-    PassArgs aD = a, aG = a;
+    PassArgs aM = a, aD = a, aG = a;
+    aM.ggas = gM;
+    aM.n_ggas = nM;
     aD.ggas = gD;
     aD.n_ggas = nD;
     aG.gall = gG;
     aG.n_gall = nG;
     mark(s, PH_D, 0);
     launch_records(a, mixed, st);
-    RET(density_pass(s, aD, false));
-    PassArgs aM = aD, aH = aD;
-    aM.ggas = gM;
-    aM.n_ggas = nM;
-    aM.lmap = s->bmap[0].as<uint32_t>();
+    RET(density_pass(s, aM, false));
+    launch_density_only(aD, mixed, s->cap, st);
+    PassArgs aH = aM;
     aH.ggas = gH;
     aH.n_ggas = nH;
     aH.lmap = s->bmap[1].as<uint32_t>();

@@ -165,6 +165,7 @@ void launch_records(const PassArgs &a, int mixed, cudaStream_t st);
 void launch_hlist_count(const PassArgs &a, int mixed, int cap, bool count, cudaStream_t st);
 void launch_hlist_fill(const PassArgs &a, int mixed, int cap, bool count, cudaStream_t st);
 void launch_density_eval(const PassArgs &a, int mixed, int cap, bool count, cudaStream_t st);
+void launch_density_only(const PassArgs &a, int mixed, int cap, cudaStream_t st);
 void launch_hlist_bound(const PassArgs &a, const uint32_t *cnt_by_id, cudaStream_t st);
 void launch_keep_counts(const PassArgs &a, uint32_t *cnt_by_id, cudaStream_t st);
 void launch_moments(const PassArgs &a, int mixed, int cap, cudaStream_t st);
@@ -210,8 +211,10 @@ void launch_assign_bins(const State &s, const BoxDev *boxes, int64_t n, double d
 void launch_leaf_active(const Leaves &lv, int nleaf, const uint8_t *bin, int bmin, uint8_t *flag, cudaStream_t st);
 void launch_leaf_expand(const uint32_t *row, const uint32_t *col, int nleaf, const uint8_t *in, uint8_t *out,
                         cudaStream_t st);
+// items whose leaf has leaf_flag set and, when given, exclude not set
 void launch_group_select(const uint2 *groups, uint32_t n, const uint8_t *leaf_flag, uint32_t *keep, uint32_t *pos,
-                         uint32_t *total, uint32_t *tmp, uint2 *out, uint32_t *map, cudaStream_t st);
+                         uint32_t *total, uint32_t *tmp, uint2 *out, uint32_t *map, cudaStream_t st,
+                         const uint8_t *exclude = nullptr);
 void launch_unpermute_bins(const State &s, int64_t n, uint8_t *out, cudaStream_t st);
 
 }  // namespace crk

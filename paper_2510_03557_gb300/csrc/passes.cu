@@ -839,6 +839,71 @@ __global__ void __launch_bounds__(kBlock) hlist_fill_k(PassArgs a)
     if (!COUNT && G.act) density_out<R>(a, i, ri, rho);
 }
 
+// Density alone (no lists) of gas groups whose particles only feed their
+// neighbours' corrections in a hierarchical substep: the same visits, tests
+// and terms, in the same order, as the fill pass's density sum.
+template <typename R, int JMAX>
+__global__ void __launch_bounds__(kBlock) density_only_k(PassArgs a)
+{
+    using R4 = Vec4<R>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    const uint32_t gi = blockIdx.x * kWarps + w;
+    if (gi >= a.n_ggas) return;
+    R4 *tile = reinterpret_cast<R4 *>(smem + (size_t)w * hlist_warp_bytes<R, JMAX>());
+    uint8_t *tslot = reinterpret_cast<uint8_t *>(reinterpret_cast<float *>(tile + JMAX) + JMAX);
+    const Group G = load_group(a.lv, a.ggas, gi, lane);
+    const int I = G.I;
+    const uint32_t i = G.i;
+    const double Ld = a.boxes[a.lv.slot[I]].L;
+    const R L = (R)Ld, hL = (R)(0.5 * Ld);
+    const R4 *__restrict__ pm = reinterpret_cast<const R4 *>(a.pm);
+    const R4 ri = pm[i];
+    const HTarget<R> ht = hydro_target<R>(a.s, i);
+    float px, py, pz;
+    rel_pos(ri, a.lv, I, Ld, px, py, pz);
+    const WarpBox wb = warp_box(px, py, pz, G.act);
+    const float Hw = warp_max(G.act ? (float)ht.H : 0.f);
+    const float Rc = Hw * 1.0001f + 1e-6f * (float)Ld;
+    R rho = 0;
+    const uint32_t prow = a.hrow[I];
+    const RowOrder order(a.hrow[I + 1] - prow);
+    for (uint32_t t = 0; t < order.n; ++t) {
+        const uint32_t p = prow + order.at(t);
+        const uint32_t J = a.hcol[p];
+        const float4 fr = a.hfr[p];
+        if (out_of_range(wb, fr, a.lv.ex[J], a.lv.ey[J], a.lv.ez[J], Rc)) continue;
+        const uint32_t sJ = a.lv.start[J], cJ = a.lv.count[J];
+        const uint32_t cm = chunks_in_range(a.lv, J, cJ, wb, fr, Rc);
+        if (cm == 0u) continue;
+        __syncwarp();
+        const uint32_t K = stage_cull<R, false>(tile, tslot, nullptr, pm, nullptr, sJ, cJ, cm, wb,
+                                                cand_frame<R>(a.lv, I, fr, Ld), Rc, lane);
+        __syncwarp();
+        if (K == 0u) continue;
+        const Target<R> q = target_in_frame(ri, fr);
+        uint32_t m[JMAX / 32];
+        test_tile_any<R, JMAX, false>(tile, nullptr, q, L, hL, ht.H2, G.act ? chunk_mask(K) : 0u, m);
+#pragma unroll
+        for (int ww = 0; ww < JMAX / 32; ++ww) {
+            uint32_t bits = m[ww];
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1;
+                const R4 rj = tile[32 * ww + b];
+                R dx, dy, dz;
+                const R r2 = q.wrap ? sep2<R, true>(rj, q, L, hL, dx, dy, dz) : sep2<R, false>(rj, q, L, hL, dx, dy, dz);
+                const R qq = Real<R>::sqrt_(r2) * ht.invH;
+                R om = (R)1 - qq;
+                om = om > (R)0 ? om : (R)0;
+                const R om2 = om * om;
+                rho += rj.w * ht.cW * om2 * om2 * om2 * ((R)1 + qq * ((R)6 + qq * (R)(35.0 / 3.0)));
+            }
+        }
+    }
+    if (G.act) density_out<R>(a, i, ri, rho);
+}
+
 // Rows of every gas group from the previous step's list sizes (by original
 // index): the largest of its targets plus max(16, 1/8) for the particles'
 // motion since.  A list that outgrows them makes the fill pass ask for a
@@ -1633,6 +1698,12 @@ void hlist_count_dispatch(const PassArgs &a, bool count, cudaStream_t st)
 }
 
 template <typename R, int JMAX>
+void density_only_dispatch(const PassArgs &a, cudaStream_t st)
+{
+    launch_warp_kernel(density_only_k<R, JMAX>, a.n_ggas, (size_t)kWarps * hlist_warp_bytes<R, JMAX>(), a, st);
+}
+
+template <typename R, int JMAX>
 void fill_dispatch(const PassArgs &a, bool count, cudaStream_t st)
 {
     const size_t smf = (size_t)kWarps * hfill_warp_bytes<R, JMAX>();
@@ -1726,6 +1797,13 @@ void launch_density_eval(const PassArgs &a, int mixed, int cap, bool count, cuda
 {
     if (a.n_ggas == 0) return;
     CRK_BY_CAP(density_eval_dispatch, a, count, st);
+    note_launches(1);
+}
+
+void launch_density_only(const PassArgs &a, int mixed, int cap, cudaStream_t st)
+{
+    if (a.n_ggas == 0) return;
+    CRK_BY_CAP(density_only_dispatch, a, st);
     note_launches(1);
 }
 
