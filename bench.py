@@ -43,8 +43,8 @@ FLOP_PER_PAIR = {"density": 22, "moments": 125, "hydro": 183, "gravity": 41}
 # (2x128^3 Gaussian field, leaf capacity 128; density = list bounds + fill
 # with the density sum + kept counts).  They describe the kernels of the csrc/passes.cu with this
 # SHA-256 only; for any other source the bench reports no traffic.
-TRAFFIC_SOURCE_SHA256 = "81ed9bc29b8de0df90f3193c2491863e2afed7a7f817a7a4f3a1a1250bef0735"
-TRAFFIC_BYTES_PER_PARTICLE = {"gravity": 81.6, "hydro": 701.2, "moments": 690.9, "density": 1082.4}
+TRAFFIC_SOURCE_SHA256 = "1b4c94d85a9a1792ff7dafdf520c440daea9a78edd462a848f773df1d5c0b56c"
+TRAFFIC_BYTES_PER_PARTICLE = {"gravity": 81.6, "hydro": 701.3, "moments": 690.8, "density": 1082.8}
 
 
 def _traffic(kernel: str, particles: int, leaf_cap: int):
