@@ -31,6 +31,12 @@ It prints no formula, so this module fixes the reading:
        long step).
 * Before the first long step with no stored forces every particle gets its
   forces at t = 0 and a bin from the same criterion.
+* With a long-range mesh (pm_grid > 0; Sec. IV-A: the long-range force is
+  integrated with the long PM step, the short-range physics in the substeps):
+  every long step is wrapped in two half kicks v += D_t/2 a_mesh(x), the mesh
+  acceleration of ``oracle.pm`` at the positions of its start and of its end;
+  the substeps and the bin criterion see the short-range and hydro forces
+  only, and the forces stored at the start are recomputed (short-range only).
 
 With depth = 0 this is the fixed-step KDK of ``oracle.kdk``; with every
 particle in the deepest bin it is that KDK at dt = D_t / 2^depth.
@@ -42,6 +48,7 @@ import math
 import numpy as np
 
 from . import forces as _forces
+from . import pm as _pm
 
 
 def _wrap(x: np.ndarray, L: float) -> np.ndarray:
@@ -82,7 +89,7 @@ def new_bins(acc, u, h, gas, params, dt_long: float, depth: int, eta: float, cou
 
 
 def kdk_bins(pos, vel, mass, u, h, species, params, dt_long: float, depth: int, nlong: int,
-             eta: float, courant: float, acc=None, dudt=None, bins=None) -> dict:
+             eta: float, courant: float, acc=None, dudt=None, bins=None, pm_grid: int = 0) -> dict:
     """Run nlong long steps; returns the final pos, vel, u, acc, dudt, bins,
     the floor events and the number of active particles of every substep."""
     pos = np.array(pos, np.float64).reshape(-1, 3)
@@ -97,7 +104,8 @@ def kdk_bins(pos, vel, mass, u, h, species, params, dt_long: float, depth: int, 
     nfloor = 0
     nsub = 1 << depth
     d = math.ldexp(dt_long, -depth)
-    if acc is None:
+    mesh = (lambda x: _pm.accelerations(x, mass, L, pm_grid, params.G, params.r_split)) if pm_grid else None
+    if acc is None or mesh is not None:
         r = _forces(pos, vel, mass, u, h, sp, params)
         if r["rc"]:
             raise RuntimeError(f"oracle forces failed: {r['rc']}")
@@ -109,6 +117,8 @@ def kdk_bins(pos, vel, mass, u, h, species, params, dt_long: float, depth: int, 
         bins = np.asarray(bins, np.int64).copy()
     active_counts = []
     for _ in range(nlong):
+        if mesh is not None:
+            vel = vel + (0.5 * dt_long) * mesh(pos)
         for s in range(nsub):
             Lb = np.left_shift(1, depth - bins)          # substeps per step
             hdt = Lb * (0.5 * d)                          # dt_b / 2, exact
@@ -138,5 +148,7 @@ def kdk_bins(pos, vel, mass, u, h, species, params, dt_long: float, depth: int, 
             b_sync = 0 if t == nsub else depth - ((t & -t).bit_length() - 1)
             nb = new_bins(acc, u, h, gas, params, dt_long, depth, eta, courant, b_sync)
             bins = np.where(active, nb, bins)
+        if mesh is not None:
+            vel = vel + (0.5 * dt_long) * mesh(pos)
     return dict(pos=pos, vel=vel, u=u, acc=acc, dudt=dudt, bins=bins, nfloor=nfloor,
                 active_counts=np.array(active_counts, np.int64))

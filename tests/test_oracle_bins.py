@@ -131,3 +131,37 @@ def test_mixed_bins_converge_at_second_order():
         errs.append(np.linalg.norm(got["vel"] - ref["vel"]))
     ratios = [errs[0] / errs[1], errs[1] / errs[2]]
     assert all(3.2 < q < 5.0 for q in ratios), (errs, ratios)
+
+
+def test_mesh_long_step_is_a_leapfrog_when_nothing_is_near():
+    """Dark matter far apart (no pair within r_cut) feels only the mesh: the
+    long step with its two mesh half kicks and the substeps (bin 0: drifts
+    only) is the textbook leapfrog at dt = D_t with the mesh force."""
+    from oracle import pm
+
+    rng = np.random.default_rng(21)
+    g = np.arange(4) * 0.25 + 0.125
+    pos = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3)
+    pos = pos + rng.uniform(-0.02, 0.02, pos.shape)
+    n = len(pos)
+    vel = rng.normal(0.0, 0.05, (n, 3))
+    mass = rng.uniform(0.5, 1.5, n)
+    zero = np.zeros(n)
+    sp = np.zeros(n, np.uint8)
+    op = oracle.make_params(box=1.0, G=1.0, r_cut=0.05, r_split=0.05, eps_soft=0.001)
+    dt, nlong, ng = 2e-3, 3, 16
+    x, v = pos.copy(), vel.copy()
+    for _ in range(nlong):
+        v = v + (0.5 * dt) * pm.accelerations(x, mass, 1.0, ng, 1.0, 0.05)
+        x = x + dt * v
+        x = np.where(x >= 1.0, x - 1.0, x)
+        x = np.where(x < 0.0, x + 1.0, x)
+        v = v + (0.5 * dt) * pm.accelerations(x, mass, 1.0, ng, 1.0, 0.05)
+    got = ob.kdk_bins(pos, vel, mass, zero, zero, sp, op, dt, 0, nlong, eta=0.025, courant=0.25, pm_grid=ng)
+    assert np.array_equal(got["pos"], x)
+    assert np.array_equal(got["vel"], v)
+    # deeper bins change nothing but the drift, cut into four substeps
+    got = ob.kdk_bins(pos, vel, mass, zero, zero, sp, op, dt, 2, nlong, eta=0.025, courant=0.25, pm_grid=ng)
+    assert np.all(got["bins"] == 0)
+    assert np.allclose(got["pos"], x, rtol=0, atol=1e-14)
+    assert np.allclose(got["vel"], v, rtol=1e-12, atol=0)

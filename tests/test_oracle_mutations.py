@@ -67,6 +67,8 @@ PY_MUTATIONS = {
                                   "vel = vel + hdt[:, None] * acc"),
     "bins_courant_on_c_squared": ("bins.py", "dc = np.where(hot, (courant * h) / c, np.inf)",
                                   "dc = np.where(hot, (courant * h) / (c * c), np.inf)"),
+    "bins_mesh_opening_full_kick": ("bins.py", "            vel = vel + (0.5 * dt_long) * mesh(pos)\n        for s",
+                                    "            vel = vel + dt_long * mesh(pos)\n        for s"),
 }
 PY_PINS = {"pm.py": "tests/test_oracle_pm.py", "bins.py": "tests/test_oracle_bins.py"}
 
