@@ -250,9 +250,15 @@ int crk_pm_accel(crk_sim *sim, double *acc, int mem);
  * those (density, lists).  active_counts (optional, host, nlong * 2^depth
  * entries) gets the number of active particles of every substep.  Every
  * state update is FP64 with each product and sum rounded on its own.
- * depth = 0 is crk_step.  Not with a mesh (pm_grid > 0).  Errors: CRK_EINVAL
- * (dt_long <= 0, depth outside [0, 20], nlong < 0, eta or courant <= 0),
- * the errors of crk_step. */
+ * depth = 0 is crk_step.  With a mesh (pm_grid > 0) the long-range force is
+ * integrated on the long step (Sec. IV-A: the PM force once per PM step, the
+ * short-range physics in the substeps): every long step is wrapped in two half
+ * kicks v += dt_long/2 a_mesh, the mesh acceleration at the positions of its
+ * start and of its end, while the substeps, their stored rates and the bins
+ * see the short-range and hydro forces alone (evaluated afresh at the start of
+ * the call; a later crk_step or crk_forces evaluates the full forces again).
+ * Errors: CRK_EINVAL (dt_long <= 0, depth outside [0, 20], nlong < 0, eta or
+ * courant <= 0), the errors of crk_step. */
 int crk_step_bins(crk_sim *sim, double dt_long, int depth, int nlong, double eta, double courant,
                   int64_t *active_counts);
 

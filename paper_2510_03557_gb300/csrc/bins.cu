@@ -189,6 +189,17 @@ __global__ void group_compact_k(const uint2 *__restrict__ groups, uint32_t n, co
     if (map) map[pos[g]] = g;
 }
 
+// Long-range kick of every particle: v += hdt a_mesh (FP64, each product and
+// sum rounded on its own).
+__global__ void pm_kick_k(State s, const double *__restrict__ acc, int64_t n, double hdt)
+{
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    s.vx[k] = __dadd_rn(s.vx[k], __dmul_rn(hdt, acc[3 * k]));
+    s.vy[k] = __dadd_rn(s.vy[k], __dmul_rn(hdt, acc[3 * k + 1]));
+    s.vz[k] = __dadd_rn(s.vz[k], __dmul_rn(hdt, acc[3 * k + 2]));
+}
+
 __global__ void unpermute_bins_k(State s, int64_t n, uint8_t *out)
 {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -255,6 +266,13 @@ void launch_group_select(const uint2 *groups, uint32_t n, const uint8_t *leaf_fl
     scan_exclusive_u32(keep, pos, n, total, tmp, st);
     group_compact_k<<<nblocks(n), kT, 0, st>>>(groups, n, keep, pos, out, map);
     note_launches(2);
+}
+
+void launch_pm_kick(const State &s, const double *acc, int64_t n, double hdt, cudaStream_t st)
+{
+    if (n <= 0) return;
+    pm_kick_k<<<nblocks(n), kT, 0, st>>>(s, acc, n, hdt);
+    note_launches(1);
 }
 
 void launch_unpermute_bins(const State &s, int64_t n, uint8_t *out, cudaStream_t st)

@@ -205,7 +205,7 @@ PassArgs pass_args(crk_sim *s)
     a.uhat = s->uhat.p;
     a.acc_h = s->acc_h.p;
     a.acc_g = s->acc_g.p;
-    a.acc_pm = s->prm.pm_grid > 0 ? s->acc_pm.as<double>() : nullptr;
+    a.acc_pm = s->prm.pm_grid > 0 && !s->pm_suspend ? s->acc_pm.as<double>() : nullptr;
     a.nbr_count = s->nbrc.as<int32_t>();
     a.nbr_hash = s->nbrh.as<uint64_t>();
     a.grav_count = s->gravc.as<int32_t>();
@@ -531,7 +531,7 @@ int run_step(crk_sim *s, const double *dt_per_box, bool want_counts)
         mark(s, PH_KICK, 1);
     }
     RET(build_tree(s));
-    if (s->prm.pm_grid > 0) {
+    if (s->prm.pm_grid > 0 && !s->pm_suspend) {
         mark(s, PH_PM, 0);
         RET(pm_accelerations(s, s->acc_pm.as<double>(), false));
         mark(s, PH_PM, 1);
@@ -935,7 +935,6 @@ extern "C" int crk_step_bins(crk_sim *s, double dt_long, int depth, int nlong, d
     if (nlong < 0) return fail(CRK_EINVAL, "nlong must be >= 0");
     if (!(eta > 0.0) || !(courant > 0.0) || !std::isfinite(eta) || !std::isfinite(courant))
         return fail(CRK_EINVAL, "eta and courant must be finite and > 0");
-    if (s->prm.pm_grid > 0) return fail(CRK_EINVAL, "hierarchical steps take no mesh (pm_grid must be 0)");
     CK(cudaSetDevice(s->device));
     const int nsub = 1 << depth;
     const size_t ncount = (size_t)nlong * (size_t)nsub;
@@ -944,15 +943,38 @@ extern "C" int crk_step_bins(crk_sim *s, double dt_long, int depth, int nlong, d
             for (size_t k = 0; k < ncount; ++k) active_counts[k] = 0;
         return CRK_OK;
     }
-    if (!s->have_forces) RET(run_step(s, nullptr, false));
-    // every particle starts the long step with the bin of its stored rates
-    launch_assign_bins(s->sa, s->boxes_d.as<BoxDev>(), s->n, dt_long, depth, eta, courant, s->st);
-    RET(s->bcount.ensure(std::max<size_t>(ncount, 1) * sizeof(unsigned long long)));
+    // With a mesh the long-range force kicks on the long step (two half kicks
+    // around it, the mesh at the positions of its start and its end) and the
+    // substeps, their stored rates and the bins see the short-range and hydro
+    // forces alone, so those are evaluated afresh first.
+    const bool mesh = s->prm.pm_grid > 0;
+    s->pm_suspend = mesh;
+    int rc = CRK_OK;
+    if (mesh || !s->have_forces) rc = run_step(s, nullptr, false);
+    if (rc == CRK_OK) rc = s->bcount.ensure(std::max<size_t>(ncount, 1) * sizeof(unsigned long long));
     unsigned long long *cnt = s->bcount.as<unsigned long long>();
-    CK(cudaMemsetAsync(cnt, 0, std::max<size_t>(ncount, 1) * sizeof(unsigned long long), s->st));
-    for (int L = 0; L < nlong; ++L)
-        for (int sub = 0; sub < nsub; ++sub)
-            RET(run_substep(s, sub, depth, dt_long, eta, courant, cnt + (size_t)L * nsub + sub));
+    if (rc == CRK_OK) {
+        // every particle starts the long step with the bin of its stored rates
+        launch_assign_bins(s->sa, s->boxes_d.as<BoxDev>(), s->n, dt_long, depth, eta, courant, s->st);
+        if (cudaMemsetAsync(cnt, 0, std::max<size_t>(ncount, 1) * sizeof(unsigned long long), s->st) != cudaSuccess)
+            rc = fail(CRK_ECUDA, "cudaMemsetAsync failed");
+    }
+    auto mesh_kick = [&]() {
+        int r = pm_accelerations(s, s->acc_pm.as<double>(), false);
+        if (r == CRK_OK) launch_pm_kick(s->sa, s->acc_pm.as<double>(), s->n, 0.5 * dt_long, s->st);
+        return r;
+    };
+    for (int L = 0; L < nlong && rc == CRK_OK; ++L) {
+        if (mesh) rc = mesh_kick();
+        for (int sub = 0; sub < nsub && rc == CRK_OK; ++sub)
+            rc = run_substep(s, sub, depth, dt_long, eta, courant, cnt + (size_t)L * nsub + sub);
+        if (mesh && rc == CRK_OK) rc = mesh_kick();
+    }
+    s->pm_suspend = false;
+    // the stored rates are the short-range part alone: a later fixed step
+    // evaluates the full forces first
+    if (mesh) s->have_forces = false;
+    RET(rc);
     if (active_counts && ncount > 0) {
         std::vector<unsigned long long> h(ncount);
         CK(cudaMemcpyAsync(h.data(), cnt, ncount * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s->st));

@@ -216,5 +216,6 @@ void launch_group_select(const uint2 *groups, uint32_t n, const uint8_t *leaf_fl
                          uint32_t *total, uint32_t *tmp, uint2 *out, uint32_t *map, cudaStream_t st,
                          const uint8_t *exclude = nullptr);
 void launch_unpermute_bins(const State &s, int64_t n, uint8_t *out, cudaStream_t st);
+void launch_pm_kick(const State &s, const double *acc, int64_t n, double hdt, cudaStream_t st);
 
 }  // namespace crk

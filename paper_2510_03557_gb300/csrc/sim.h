@@ -101,6 +101,7 @@ struct crk_sim {
     DBuf pscr_col, pscr_fr, pscr_st;    // leaf-pair rows of fixed capacity before packing
     int pair_two_pass_left = 0;         // builds left that walk the pair lists twice (after an overflow)
     int bins_bmin = -1;                 // hierarchical substep: smallest active bin (-1: not in a substep)
+    bool pm_suspend = false;            // hierarchical steps: forces without the mesh (it kicks on the long step)
     int sort_levels = crk::kAllLevels;  // octree levels below the bins that the next sort orders
     bool cnt_valid = false;
     bool is_pool = false;
