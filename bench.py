@@ -43,8 +43,8 @@ FLOP_PER_PAIR = {"density": 22, "moments": 125, "hydro": 183, "gravity": 41}
 # (2x128^3 Gaussian field, leaf capacity 128; density = list bounds + fill
 # with the density sum + kept counts).  They describe the kernels of the csrc/passes.cu with this
 # SHA-256 only; for any other source the bench reports no traffic.
-TRAFFIC_SOURCE_SHA256 = "1b4c94d85a9a1792ff7dafdf520c440daea9a78edd462a848f773df1d5c0b56c"
-TRAFFIC_BYTES_PER_PARTICLE = {"gravity": 81.6, "hydro": 701.3, "moments": 690.8, "density": 1082.8}
+TRAFFIC_SOURCE_SHA256 = "695550b977dabc80776240b71028b5f1020dafab76880c791a1c4e7e33176915"
+TRAFFIC_BYTES_PER_PARTICLE = {"gravity": 81.3, "hydro": 701.4, "moments": 690.8, "density": 1088.2}
 
 
 def _traffic(kernel: str, particles: int, leaf_cap: int):
@@ -288,6 +288,26 @@ def run_bins(args):
     print(json.dumps(line))
 
 
+def pair_census(tim, pairs, n_gas, n):
+    """Evaluated / algorithmic pairs of the counted evaluation: candidate
+    tests in lane slots (a warp tests its up to 32 targets against every staged
+    candidate) per in-range pair, the hydro list entries per gather pair, and
+    the share of walked list slots that hold an entry."""
+    gather = pairs["density"]                 # ordered gather pairs, self included
+    grav = pairs["gravity"] + n               # each target is also tested against itself
+    r = lambda a, b: round(a / b, 3) if b else None
+    return {"gravity": {"tested_slots": tim["tests_grav"], "target_slots": tim["tests_grav_target"],
+                        "in_range": grav, "tested_per_in_range": r(tim["tests_grav"], grav),
+                        "target_slots_per_in_range": r(tim["tests_grav_target"], grav)},
+            "hydro_fill": {"tested_slots": tim["tests_hydro"], "list_entries": tim["list_entries"],
+                           "gather_pairs": gather, "tested_per_entry": r(tim["tests_hydro"], tim["list_entries"]),
+                           "entries_per_gather_pair": r(tim["list_entries"], gather)},
+            "list_walk": {"slots": tim["list_slots"], "entries": tim["list_entries"],
+                          "entry_share": r(tim["list_entries"], tim["list_slots"])},
+            "note": "lane slots of one counted force evaluation; in-range gravity pairs include each "
+                    "target's self test"}
+
+
 def run_clustered(args):
     """Precision study on the clustered workload (2 x n^3, half uniform and
     half in 512 Plummer spheres, adaptive h): one force evaluation plus 5 KDK
@@ -346,6 +366,24 @@ def run_clustered(args):
                                       "gravity_ms", "kdk_ms")},
                           leaves=int(tim["nleaves"]), leaf_pairs=[int(tim["pairs_hydro"]),
                                                                   int(tim["pairs_grav"])])
+        if name == "mixed" and not args.no_extras:
+            # friends-of-friends halos of the dark matter at b = 0.2 mean
+            # spacings on the clustered state after the KDK steps
+            torch.cuda.synchronize()
+            t_f = time.perf_counter()
+            grp, n_groups = crk.crk_fof(s.handle, 0.2 / args.n, 1, box.n)
+            fof_ms = (time.perf_counter() - t_f) * 1e3
+            _, sizes = np.unique(grp[grp >= 0], return_counts=True)
+            runs[name]["fof"] = {"ms": round(fof_ms, 3), "groups": n_groups,
+                                 "groups_20_or_more": int(np.sum(sizes >= 20)),
+                                 "largest": int(sizes.max()) if len(sizes) else 0,
+                                 "in_groups_20_or_more": round(float(sizes[sizes >= 20].sum()) / max(len(grp[grp >= 0]), 1), 4),
+                                 "linking_length": 0.2 / args.n, "species": "dm",
+                                 "note": "host wall time of crk_fof: tree build, links, labels, copy-out"}
+            cnt = s.forces(counts=True)
+            pc = {"density": int(cnt["nbr_count"][gas].sum()) + int(gas.sum()),
+                  "gravity": int(cnt["grav_count"].sum())}
+            runs[name]["census"] = pair_census(crk.crk_get_timings(s.handle), pc, int(gas.sum()), box.n)
         s.close()
     a, b = runs["mixed"], runs["fp64"]
     err = {"acc": _rel_l2(a["out"]["acc"], b["out"]["acc"]),
@@ -396,6 +434,7 @@ def run_clustered(args):
                       "breakdown_ms": a["breakdown"], "momentum_drift": a["momentum_drift"],
                       "energy_drift": a["energy_drift"], "leaves": a["leaves"],
                       "leaf_pairs": a["leaf_pairs"]},
+            "fof": a.get("fof"), "pair_census_after_kdk": a.get("census"),
             "mixed_vs_fp64_rel_l2": err,
             "fp64_vs_oracle_rel_l2": orc, "mixed_vs_oracle_rel_l2": orc_mixed,
             "oracle_sample": {"particles": int(len(idx)), "seconds": round(t_or, 2),
@@ -574,6 +613,7 @@ def main():
              "moments": int(counts["nbr_count"][gas].sum()) + int(gas.sum()),
              "hydro": int(counts["nbr_count"][gas].sum()),
              "gravity": int(counts["grav_count"].sum())}
+    census = pair_census(crk.crk_get_timings(sim.handle), pairs, int(gas.sum()), N)
     for _ in range(args.warmup):
         sim.step(dt, 1)
     crk.crk_set_timing(sim.handle, True)
@@ -709,6 +749,7 @@ def main():
                                         f"({peak_kind} sm_max_mhz)"},
             "pass_tflops": {k: round(v, 3) for k, v in pass_tflops.items()},
             "pairs_per_step": pairs,
+            "pair_census": census,
             "leaves": int(tim["nleaves"]), "leaf_pairs": {"hydro": int(tim["pairs_hydro"]),
                                                           "gravity": int(tim["pairs_grav"])},
             "breakdown_ms": breakdown,

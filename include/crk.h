@@ -136,6 +136,17 @@ typedef struct {
     int64_t nleaves;      /* leaves in the last tree */
     int64_t launches;     /* CUDA kernels the library launched in the timed calls */
     double pm_ms;         /* long-range mesh gravity (deposit, FFTs, Green's function, gather) */
+    /* Pair-work census of the last force evaluation that counted neighbours
+     * (crk_forces with nbr_count, nbr_hash, grav_count or grav_hash set; all
+     * 0 before one), in lane slots: a warp tests its up to 32 targets against
+     * every candidate it stages, so one staged candidate costs 32 slots
+     * whatever the group's size.  Against the in-range pairs of the counts
+     * these give the evaluated / algorithmic pair ratios. */
+    int64_t tests_hydro;        /* hydro candidate tests of the list fill */
+    int64_t list_entries;       /* hydro list entries written (union set, self included) */
+    int64_t tests_grav;         /* gravity candidate tests (every pair force is formed) */
+    int64_t tests_grav_target;  /* of those, the slots of lanes that have a target */
+    int64_t list_slots;         /* lane slots of the list rows the moments and hydro passes walk */
 } crk_timings;
 
 typedef struct crk_sim crk_sim;

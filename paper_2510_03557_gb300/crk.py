@@ -74,7 +74,9 @@ class Timings(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in ("tree_ms", "pairs_ms", "density_ms", "moments_ms",
                                                 "hydro_ms", "gravity_ms", "kdk_ms", "total_ms")] + \
                [(k, ctypes.c_int64) for k in ("calls", "pairs_hydro", "pairs_grav", "nleaves",
-                                               "launches")] + [("pm_ms", ctypes.c_double)]
+                                               "launches")] + [("pm_ms", ctypes.c_double)] + \
+               [(k, ctypes.c_int64) for k in ("tests_hydro", "list_entries", "tests_grav",
+                                               "tests_grav_target", "list_slots")]
 
 
 class ServiceParams(ctypes.Structure):

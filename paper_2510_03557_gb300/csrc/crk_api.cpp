@@ -178,6 +178,7 @@ int reserve(crk_sim *s, int64_t n)
     RET(s->gravh.ensure(nn * 8));
     RET(s->cnt_by_id.ensure(nn * 4));
     RET(s->nl_retry.ensure(16));
+    RET(s->census.ensure(32));
     RET(s->err.ensure(16));
     RET(s->nfloor.ensure(16));
     RET(s->partial.ensure((size_t)sums_blocks(n) * 4 * 8 + 64));
@@ -496,12 +497,14 @@ static int density_pass(crk_sim *s, PassArgs &a, bool want_counts)
     cudaStream_t st = s->st;
     const int mixed = s->mixed ? 1 : 0;
     RET(size_hydro_lists(s, a, want_counts, s->cnt_valid && !s->is_pool));
+    if (a.census) CK(cudaMemsetAsync(a.census, 0, 2 * sizeof(unsigned long long), st));
     launch_hlist_fill(a, mixed, s->cap, want_counts, st);
     if (a.nl_bound) {
         CK(cudaMemcpyAsync(s->host_scalars + 6, a.nl_retry, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         if (s->host_scalars[6]) {
             RET(size_hydro_lists(s, a, want_counts, false));
+            if (a.census) CK(cudaMemsetAsync(a.census, 0, 2 * sizeof(unsigned long long), st));
             launch_hlist_fill(a, mixed, s->cap, want_counts, st);
         }
     }
@@ -542,6 +545,9 @@ int run_step(crk_sim *s, const double *dt_per_box, bool want_counts)
         a.nbr_hash = nullptr;
         a.grav_count = nullptr;
         a.grav_hash = nullptr;
+    } else {
+        a.census = s->census.as<unsigned long long>();
+        CK(cudaMemsetAsync(a.census, 0, 4 * sizeof(unsigned long long), st));
     }
     const int mixed = s->mixed ? 1 : 0;
     mark(s, PH_D, 0);
@@ -564,6 +570,10 @@ int run_step(crk_sim *s, const double *dt_per_box, bool want_counts)
     if (s->timing) cudaEventRecord(s->ev_all[1], st);
     CK(cudaGetLastError());
     RET(read_error(s));
+    if (a.census) {
+        CK(cudaMemcpy(s->census_h, a.census, sizeof(s->census_h), cudaMemcpyDeviceToHost));
+        s->census_rows = s->nl_rows;
+    }
     if (s->timing) {
         for (int ph = 0; ph < PH_N; ++ph) {
             if (!s->recorded[ph]) continue;
@@ -1216,6 +1226,11 @@ extern "C" int crk_get_timings(crk_sim *s, crk_timings *t)
     t->nleaves = s->nleaf;
     t->launches = s->launches;
     t->pm_ms = s->acc_ms[PH_PM];
+    t->tests_hydro = (int64_t)s->census_h[0];
+    t->list_entries = (int64_t)s->census_h[1];
+    t->tests_grav = (int64_t)s->census_h[2];
+    t->tests_grav_target = (int64_t)s->census_h[3];
+    t->list_slots = 32 * s->census_rows;
     return CRK_OK;
 }
 
@@ -1236,7 +1251,7 @@ extern "C" int crk_destroy(crk_sim *s)
                     &s->in_stage, &s->grp_cnt, &s->grp_off, &s->grp_gas, &s->grp_all, &s->hfr, &s->gfr,
                     &s->nl_j, &s->nl_row, &s->nl_len, &s->nl_cnt, &s->hsj, &s->fof_par, &s->acc_pm,
                     &s->bflag, &s->bgrp[0], &s->bgrp[1], &s->bgrp[2], &s->bgrp[3], &s->bmap[0],
-                    &s->bmap[1], &s->bkeep, &s->bpos, &s->bcount, &s->cnt_by_id, &s->nl_retry, &s->pscr_col, &s->pscr_fr, &s->pscr_st};
+                    &s->bmap[1], &s->bkeep, &s->bpos, &s->bcount, &s->cnt_by_id, &s->nl_retry, &s->census, &s->pscr_col, &s->pscr_fr, &s->pscr_st};
     for (DBuf *b : bufs) b->release();
     pm_release(s);
     for (int k = 0; k < 3; ++k) {

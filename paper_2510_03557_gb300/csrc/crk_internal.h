@@ -117,6 +117,11 @@ struct PassArgs {
     uint32_t n_ggas, n_gall;
     int *err;                // [0] code, [1] smallest original index of a failing particle
     unsigned long long *nfloor;  // floor events of the u predictor
+    // pair-work census of a counted evaluation (null otherwise): [0] lane
+    // slots of the hydro candidate tests (32 x staged candidates per visit),
+    // [1] hydro list entries written, [2] lane slots of the gravity tests,
+    // [3] of those the slots of lanes with a target
+    unsigned long long *census;
 };
 
 // Host-side count of kernel launches (every launcher adds what it launched).

@@ -776,6 +776,7 @@ __global__ void __launch_bounds__(kBlock) hlist_fill_k(PassArgs a)
     // from the previous step
     const uint32_t room = G.act ? (a.nl_bound ? a.nl_len[gi] : a.nl_cnt[i]) : 0u;
     uint32_t k = 0;
+    uint64_t tested = 0;  // staged candidates of the visits (census)
     R rho = 0;  // without neighbour counts the fill pass also forms the density
     const RowOrder order(a.hrow[I + 1] - prow);
     for (uint32_t t = 0; t < order.n; ++t) {
@@ -784,6 +785,7 @@ __global__ void __launch_bounds__(kBlock) hlist_fill_k(PassArgs a)
         float4 fr;
         const uint32_t K = hydro_stage<R, JMAX>(a, p, I, wb, Hw, Ld, tile, h2j, tslot, lane, sJ, fr);
         if (K == 0u) continue;
+        if (COUNT) tested += K;
         const Target<R> q = target_in_frame(ri, fr);
         const R gb = (COUNT && Real<R>::mixed) ? (R)guard_band((float)ht.H, q.mag) : (R)0;
         const R thr = Real<R>::add_rn(ht.H2, gb);
@@ -828,6 +830,13 @@ __global__ void __launch_bounds__(kBlock) hlist_fill_k(PassArgs a)
         if (done > ring.base) ring.flush(a, done, k < room ? k : room, lane);
     }
     ring.flush(a, __reduce_max_sync(0xffffffffu, k), k < room ? k : room, lane);
+    if (COUNT && a.census) {
+        const uint32_t kept = __reduce_add_sync(0xffffffffu, G.act ? (k < room ? k : room) : 0u);
+        if (lane == 0) {
+            atomicAdd(&a.census[0], 32ull * tested);
+            atomicAdd(&a.census[1], (unsigned long long)kept);
+        }
+    }
     if (a.nl_bound) {
         if (G.act) a.nl_cnt[i] = k < room ? k : room;
         if (G.act && k > room) atomicExch(a.nl_retry, 1u);  // the host sizes the lists again
@@ -1507,7 +1516,7 @@ __global__ void __launch_bounds__(kBlock) gravity_k(PassArgs a)
     const float Rc = (float)bx.r_cut * 1.0001f + 1e-6f * (float)Ld;
     R ax = 0, ay = 0, az = 0;
     int nc = 0;
-    uint64_t hs = 0;
+    uint64_t hs = 0, tested = 0;
     for (uint32_t p = a.grow[I]; p < a.grow[I + 1]; ++p) {
         const uint32_t J = a.gcol[p];
         const float4 fr = a.gfr[p];
@@ -1520,6 +1529,7 @@ __global__ void __launch_bounds__(kBlock) gravity_k(PassArgs a)
                                                                 cand_frame<R>(a.lv, I, fr, Ld), Rc, lane, Gc);
         __syncwarp();
         if (K == 0u) continue;
+        if (COUNT) tested += K;
         const Target<R> q = target_in_frame(ri, fr);
         const R gb = Real<R>::mixed ? (R)guard_band((float)rc, q.mag) : (R)0;
         const bool same = J == (uint32_t)I;  // the target itself is among the candidates
@@ -1530,6 +1540,10 @@ __global__ void __launch_bounds__(kBlock) gravity_k(PassArgs a)
                                                  G.act, a.s, i, sJ, Ld, ax, ay, az, nc, hs);
         else gravity_tile<R, false, COUNT>(tile, tslot, K, q, L, hL, rc2, rc2x, gb, e2, inv2rs, same,
                                            G.act, a.s, i, sJ, Ld, ax, ay, az, nc, hs);
+    }
+    if (COUNT && a.census && lane == 0) {
+        atomicAdd(&a.census[2], 32ull * tested);
+        atomicAdd(&a.census[3], (unsigned long long)G.cnt * tested);
     }
     if (!G.act) return;
     R4 o;

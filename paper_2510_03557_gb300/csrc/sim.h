@@ -98,6 +98,10 @@ struct crk_sim {
     // every gas particle's hydro list size of the last step, by original
     // index: the next step sizes its lists from it instead of a count pass
     DBuf cnt_by_id, nl_retry;
+    // pair-work census of the last counted force evaluation (see PassArgs)
+    DBuf census;
+    uint64_t census_h[4] = {};
+    int64_t census_rows = 0;
     DBuf pscr_col, pscr_fr, pscr_st;    // leaf-pair rows of fixed capacity before packing
     int pair_two_pass_left = 0;         // builds left that walk the pair lists twice (after an overflow)
     int bins_bmin = -1;                 // hierarchical substep: smallest active bin (-1: not in a substep)

@@ -598,3 +598,55 @@ def test_pair_rows_beyond_capacity_walk_twice(crk):
         tim = crk.crk_get_timings(sim.handle)
     assert tim["pairs_grav"] > 256 * tim["nleaves"] // 2   # rows well beyond the fixed capacity
     compare(out, ref, oracle_counts(s, op), 0, label="wide cut-off")
+
+
+# ------------------------------------------------------- pair-work census
+def test_pair_census_of_one_leaf_is_exact(crk):
+    """20 gas particles in one chaining-mesh cell, all within every cut-off:
+    one leaf, one warp group of 20 targets, one visit that stages all 20
+    candidates.  The census is then 32 x 20 lane slots per test pass, 20 x 20
+    slots of lanes with a target, 400 list entries in 20 rows."""
+    rng = np.random.default_rng(5)
+    n = 20
+    pos = 0.3125 + rng.uniform(-0.01, 0.01, (n, 3))
+    phys = crk.physics(box=1.0, G=1.0, r_cut=0.1, r_split=0.02, eps_soft=0.001)
+    with crk.Sim(phys, leaf_cap=32, precision=1) as sim:
+        crk.crk_load(sim.handle, pos, np.zeros((n, 3)), np.full(n, 1e-3), np.ones(n), np.full(n, 0.03),
+                     np.ones(n, np.uint8))
+        sim.n = n
+        t0 = crk.crk_get_timings(sim.handle)
+        out = sim.forces(counts=True)
+        t = crk.crk_get_timings(sim.handle)
+    assert all(t0[k] == 0 for k in ("tests_hydro", "list_entries", "tests_grav", "tests_grav_target",
+                                   "list_slots"))
+    assert t["nleaves"] == 1
+    assert np.all(out["nbr_count"] == n - 1) and np.all(out["grav_count"] == n - 1)
+    assert (t["tests_hydro"], t["list_entries"], t["list_slots"]) == (32 * n, n * n, 32 * n)
+    assert (t["tests_grav"], t["tests_grav_target"]) == (32 * n, n * n)
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_pair_census_bounds_the_in_range_pairs(crk, precision):
+    """Every in-range pair is tested once and written once: the tests cover
+    the neighbour counts, the list entries hold at least the gather sets,
+    the walked slots hold the entries; two counted evaluations test and write
+    the same (the second one's rows are sized from the first one's counts
+    with a margin, so it walks at least as many slots)."""
+    box = wl.gaussian_field_box(16, seed=3)
+    gas = box.species == wl.GAS
+    with crk.Sim(crk.box_physics(box), precision=precision) as sim:
+        sim.load(box)
+        out = sim.forces(counts=True)
+        t = crk.crk_get_timings(sim.handle)
+        sim.forces(counts=True)
+        t2 = crk.crk_get_timings(sim.handle)
+    for k in ("tests_hydro", "list_entries", "tests_grav", "tests_grav_target"):
+        assert t[k] == t2[k], k
+    assert t2["list_slots"] >= t["list_slots"]
+    gather = int(out["nbr_count"][gas].sum()) + int(gas.sum())    # self included
+    grav = int(out["grav_count"].sum())
+    assert t["list_entries"] >= gather
+    assert t["tests_hydro"] >= t["list_entries"] and t["tests_hydro"] % 32 == 0
+    assert t["list_slots"] >= t["list_entries"] and t["list_slots"] % 32 == 0
+    assert t["tests_grav"] >= t["tests_grav_target"] >= grav + box.n
+    assert t["tests_grav"] % 32 == 0
