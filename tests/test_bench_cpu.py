@@ -1,0 +1,65 @@
+"""Host logic of ``bench.py`` (no GPU): the FP32 peak, the clock-record
+summary, the pair census ratios and the traffic table's source guard."""
+import hashlib
+import os
+
+import pytest
+
+import bench
+
+
+def test_fp32_peak_is_sms_times_lanes_times_fma_times_clock():
+    assert bench.fp32_peak_tflops(2070.0) == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
+    assert bench.fp32_peak_tflops(1000.0) == pytest.approx(38.912)
+
+
+def _sampler(rows):
+    s = bench.ClockSampler(0)
+    s.samples = [r.split(",") for r in rows]
+    return s
+
+
+def test_clock_summary_median_max_and_reasons():
+    idle = "Not Active"
+    rows = [f"0, {mhz}, 2070, 900.0, 0x0, {idle}, {idle}, {idle}, {cap}"
+            for mhz, cap in ((2070, idle), (2055, "Active"), (2070, idle))]
+    out = _sampler(rows).summary()
+    assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"] and out["samples"] == 3
+    hot = _sampler([f"0, 1500, 2070, 1400.0, 0x0, Active, {idle}, Active, {idle}"]).summary()
+    assert hot["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+
+
+def test_clock_summary_without_samples_says_so():
+    s = bench.ClockSampler(0)
+    s.samples = []
+    assert s.summary()["reasons"] == ["unsampled"]
+
+
+def test_pair_census_ratios():
+    tim = {"tests_grav": 3200, "tests_grav_target": 2000, "tests_hydro": 640, "list_entries": 200,
+           "list_slots": 320}
+    pairs = {"density": 190, "gravity": 300}
+    c = bench.pair_census(tim, pairs, n_gas=10, n=20)
+    # each of the 20 targets is also tested against itself
+    assert c["gravity"]["in_range"] == 320
+    assert c["gravity"]["tested_per_in_range"] == 10.0
+    assert c["gravity"]["target_slots_per_in_range"] == 6.25
+    assert c["hydro_fill"]["tested_per_entry"] == 3.2
+    assert c["hydro_fill"]["entries_per_gather_pair"] == pytest.approx(1.053, abs=1e-3)
+    assert c["list_walk"]["entry_share"] == 0.625
+    empty = bench.pair_census({k: 0 for k in tim}, {"density": 0, "gravity": 0}, 0, 0)
+    assert empty["gravity"]["tested_per_in_range"] is None
+
+
+def test_traffic_only_for_the_captured_source_and_capacity():
+    assert bench._traffic("gravity", 1000, 64) is None
+    assert bench._traffic("tree", 1000, 128) is None
+    path = os.path.join(bench.ROOT, "paper_2510_03557_gb300", "csrc", "passes.cu")
+    with open(path, "rb") as f:
+        same = hashlib.sha256(f.read()).hexdigest() == bench.TRAFFIC_SOURCE_SHA256
+    t = bench._traffic("gravity", 1000, 128)
+    if same:
+        assert t == round(bench.TRAFFIC_BYTES_PER_PARTICLE["gravity"] * 1000)
+    else:
+        assert t is None
