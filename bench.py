@@ -37,6 +37,9 @@ UNIT = "particles/s"
 # 2, add/mul = 1, sqrt/rsqrt/exp/reciprocal = 1).  Pairs outside the support
 # (leaf-pair overlap) are not counted.
 FLOP_PER_PAIR = {"density": 22, "moments": 125, "hydro": 183, "gravity": 41}
+# GB300's FP64 rate (vector and tensor alike are far below its FP32 rate); a
+# nominal figure, the denominator of the plain FP64 form's algorithmic rates.
+FP64_NOMINAL_TFLOPS = 1.25
 
 # DRAM bytes (read + write) per particle of one launch of each pass, from the
 # one-pass ncu capture summarised in profiles/launches_gaussian_2x128.md
@@ -286,6 +289,21 @@ def run_bins(args):
                      "fixed_steps_timed": k},
             "clocks": clocks.summary()}
     print(json.dumps(line))
+
+
+def fp64_pass_rates(tim, pairs):
+    """Per-phase times of the timed FP64 steps and each pair pass's
+    algorithmic rate, also as a share of the nominal FP64 rate."""
+    calls = max(tim["calls"], 1)
+    rates = {k: pairs[k] * FLOP_PER_PAIR[k] / (tim[k + "_ms"] / calls / 1e3) / 1e12
+             for k in ("density", "moments", "hydro", "gravity") if tim[k + "_ms"] > 0}
+    return {"breakdown_ms": {k: round(tim[k] / calls, 3) for k in
+                             ("tree_ms", "pairs_ms", "density_ms", "moments_ms", "hydro_ms",
+                              "gravity_ms", "kdk_ms")},
+            "pass_tflops": {k: round(v, 4) for k, v in rates.items()},
+            "pass_of_fp64_peak": {k: round(v / FP64_NOMINAL_TFLOPS, 4) for k, v in rates.items()},
+            "fp64_peak": {"value": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                          "source": "nominal GB300 FP64 rate, not measured"}}
 
 
 def pair_census(tim, pairs, n_gas, n):
@@ -681,6 +699,7 @@ def main():
         s64 = crk.Sim(phys, leaf_cap=args.leaf_cap, precision=crk.CRK_FP64, stream=stream)
         s64.load(box)
         s64.step(dt, 1)
+        crk.crk_set_timing(s64.handle, True)
         barrier()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
@@ -691,6 +710,8 @@ def main():
         t64 = max_over_ranks(f0.elapsed_time(f1))
         fp64 = {"value": world * N * args.fp64_steps / (t64 / 1e3), "unit": UNIT,
                 "ms_per_step": t64 / args.fp64_steps, "steps": args.fp64_steps, "dtype": "f64"}
+        # the same pair sets as the mixed form (both decide them in FP64)
+        fp64.update(fp64_pass_rates(crk.crk_get_timings(s64.handle), pairs))
         s64.close()
 
     # ---------------- end to end through the public API with host buffers

@@ -63,3 +63,15 @@ def test_traffic_only_for_the_captured_source_and_capacity():
         assert t == round(bench.TRAFFIC_BYTES_PER_PARTICLE["gravity"] * 1000)
     else:
         assert t is None
+
+
+def test_fp64_pass_rates():
+    tim = {"calls": 2, "tree_ms": 2.0, "pairs_ms": 4.0, "density_ms": 20.0, "moments_ms": 0.0,
+           "hydro_ms": 200.0, "gravity_ms": 100.0, "kdk_ms": 1.0}
+    pairs = {"density": 1_000_000, "moments": 1_000_000, "hydro": 2_000_000, "gravity": 5_000_000}
+    r = bench.fp64_pass_rates(tim, pairs)
+    assert r["breakdown_ms"]["hydro_ms"] == 100.0 and r["breakdown_ms"]["tree_ms"] == 1.0
+    # 2e6 pairs x 183 flop in 0.1 s
+    assert r["pass_tflops"]["hydro"] == pytest.approx(2e6 * 183 / 0.1 / 1e12, abs=1e-4)  # 4 decimals
+    assert "moments" not in r["pass_tflops"]          # untimed phase: no rate
+    assert r["pass_of_fp64_peak"]["gravity"] == pytest.approx(5e6 * 41 / 0.05 / 1e12 / 1.25, abs=1e-4)
