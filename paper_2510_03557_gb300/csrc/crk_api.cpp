@@ -570,7 +570,7 @@ int run_step(crk_sim *s, const double *dt_per_box, bool want_counts)
     if (s->timing) cudaEventRecord(s->ev_all[1], st);
     CK(cudaGetLastError());
     RET(read_error(s));
-    if (a.census) {
+    if (a.census) {  // read_error has synchronised the stream: the counters are final
         CK(cudaMemcpy(s->census_h, a.census, sizeof(s->census_h), cudaMemcpyDeviceToHost));
         s->census_rows = s->nl_rows;
     }
