@@ -47,23 +47,44 @@ def test_error_message_is_available_without_gpu(libcrk):
     assert isinstance(libcrk.crk_last_error(), str)
 
 
+STRUCTS = (("crk_physics", "Physics"), ("crk_params", "Params"), ("crk_outputs", "Outputs"),
+           ("crk_timings", "Timings"), ("crk_service_params", "ServiceParams"), ("crk_job", "Job"),
+           ("crk_job_snapshot", "JobSnapshot"), ("crk_job_result", "JobResult"))
+
+
 def test_struct_layouts_match_header(libcrk, tmp_path):
-    prog = tmp_path / "sizes.c"
-    prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "crk.h"\n'
-                    "int main(void){printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\","
-                    "sizeof(crk_physics), sizeof(crk_params), sizeof(crk_outputs),"
-                    "sizeof(crk_timings), sizeof(crk_service_params), sizeof(crk_job),"
-                    "sizeof(crk_job_result), offsetof(crk_outputs, momentum_rate),"
-                    "offsetof(crk_job, dt));return 0;}\n")
-    exe = tmp_path / "sizes"
+    """Every field of every binding structure exists in the header's struct
+    under the same name, at the same offset and with the same size, and the
+    structs have the same size: gcc's layout of the header against ctypes'."""
+    lines = []
+    for cname, pyname in STRUCTS:
+        lines.append(f'printf("{cname} sizeof %zu\\n", sizeof({cname}));')
+        for f in getattr(libcrk, pyname)._fields_:
+            lines.append(f'printf("{cname} {f[0]} %zu %zu\\n", offsetof({cname}, {f[0]}), '
+                         f"sizeof((({cname} *)0)->{f[0]}));")
+    prog = tmp_path / "layout.c"
+    prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "crk.h"\nint main(void){\n'
+                    + "\n".join(lines) + "\nreturn 0;}\n")
+    exe = tmp_path / "layout"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
-    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True,
-                                          check=True).stdout.split()]
-    c = libcrk
-    want = [ctypes.sizeof(c.Physics), ctypes.sizeof(c.Params), ctypes.sizeof(c.Outputs),
-            ctypes.sizeof(c.Timings), ctypes.sizeof(c.ServiceParams), ctypes.sizeof(c.Job),
-            ctypes.sizeof(c.JobResult), c.Outputs.momentum_rate.offset, c.Job.dt.offset]
+    got = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines()
+    want = []
+    for cname, pyname in STRUCTS:
+        cls = getattr(libcrk, pyname)
+        want.append(f"{cname} sizeof {ctypes.sizeof(cls)}")
+        for f in cls._fields_:
+            d = getattr(cls, f[0])
+            want.append(f"{cname} {f[0]} {d.offset} {d.size}")
     assert got == want
+
+
+def test_binding_has_every_header_struct_field(libcrk):
+    """No header field is missing from the binding (names in order)."""
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    for cname, pyname in STRUCTS:
+        body = re.search(r"typedef struct \{([^{}]*)\}\s*" + cname + r"\s*;", src).group(1)
+        names = re.findall(r"(\w+)\s*(?:\[[^\]]*\])?\s*[,;]", body)
+        assert names == [f[0] for f in getattr(libcrk, pyname)._fields_], cname
 
 
 def test_binding_rejects_mixed_memory_kinds(libcrk):
