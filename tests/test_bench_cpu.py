@@ -75,3 +75,26 @@ def test_fp64_pass_rates():
     assert r["pass_tflops"]["hydro"] == pytest.approx(2e6 * 183 / 0.1 / 1e12, abs=1e-4)  # 4 decimals
     assert "moments" not in r["pass_tflops"]          # untimed phase: no rate
     assert r["pass_of_fp64_peak"]["gravity"] == pytest.approx(5e6 * 41 / 0.05 / 1e12 / 1.25, abs=1e-4)
+
+
+def test_reference_arm_line(tmp_path):
+    """``--impl reference`` times the oracle on a bounded sample and reports
+    the headline arm's config, metric and unit, with zero transfer bytes."""
+    import argparse
+    import json
+    import subprocess
+    import sys
+
+    out = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference",
+                          "--steps", "1", "--warmup", "0"], capture_output=True, text=True, check=True,
+                         cwd=bench.ROOT, timeout=600).stdout.strip().splitlines()
+    line = json.loads(out[-1])
+    args = argparse.Namespace(n=128, leaf_cap=128, rebuild_every=1)
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
+    assert line["config"] == bench.headline_config(args, 1)
+    assert line["higher_is_better"] is True and line["value"] > 0
+    cb = line["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and "2x40^3" in cb["sample"]
+    assert cb["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
