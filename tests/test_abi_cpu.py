@@ -105,3 +105,26 @@ def test_create_rejects_bad_mesh_sizes_before_touching_the_device(libcrk, pm_gri
     h = ctypes.c_void_p()
     rc = libcrk.lib().crk_create(ctypes.byref(p), None, ctypes.byref(h))
     assert rc == libcrk.CRK_EINVAL and "pm_grid" in libcrk.crk_last_error()
+
+
+@pytest.mark.parametrize("field,value,word", [("leaf_cap", 48, "leaf_cap"), ("precision", 2, "precision"),
+                                              ("kernel", 1, "kernel"), ("cm_level", 11, "cm_level"),
+                                              ("cm_level", -1, "cm_level"),
+                                              ("rebuild_every", -1, "rebuild_every")])
+def test_create_rejects_bad_params_before_touching_the_device(libcrk, field, value, word):
+    """Every create-time parameter is checked before the first CUDA call."""
+    p = libcrk.params()
+    setattr(p, field, value)
+    h = ctypes.c_void_p()
+    rc = libcrk.lib().crk_create(ctypes.byref(p), None, ctypes.byref(h))
+    assert rc == libcrk.CRK_EINVAL and word in libcrk.crk_last_error()
+
+
+def test_null_arguments_are_rejected_without_a_device(libcrk):
+    L = libcrk.lib()
+    h = ctypes.c_void_p()
+    assert L.crk_create(None, None, ctypes.byref(h)) == libcrk.CRK_EINVAL
+    p = libcrk.params()
+    assert L.crk_create(ctypes.byref(p), None, None) == libcrk.CRK_EINVAL
+    assert L.crk_get_timings(None, None) == libcrk.CRK_EINVAL
+    assert L.crk_destroy(None) == libcrk.CRK_OK
