@@ -257,6 +257,7 @@ extern "C" int crk_service_create(const crk_service_params *params, crk_service 
     if (params->max_slots < 1 || params->max_slots > 65535)
         return fail(CRK_EINVAL, "max_slots must be in [1, 65535]");
     if (params->hbm_budget_bytes == 0) return fail(CRK_EINVAL, "hbm_budget_bytes must be > 0");
+    if (params->snapshot_every < 0) return fail(CRK_EINVAL, "snapshot_every must be >= 0");
     CK(cudaSetDevice(params->device));
     auto *sv = new crk_service();
     sv->prm = *params;
@@ -264,10 +265,6 @@ extern "C" int crk_service_create(const crk_service_params *params, crk_service 
     p.kernel = CRK_WENDLAND_C4;
     p.leaf_cap = params->leaf_cap ? params->leaf_cap : 64;
     p.precision = params->precision;
-    if (params->snapshot_every < 0) {
-        delete sv;
-        return fail(CRK_EINVAL, "snapshot_every must be >= 0");
-    }
     cudaError_t e = cudaStreamCreateWithFlags(&sv->st, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->side, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sv->stepped, cudaEventDisableTiming);

@@ -128,3 +128,26 @@ def test_null_arguments_are_rejected_without_a_device(libcrk):
     assert L.crk_create(ctypes.byref(p), None, None) == libcrk.CRK_EINVAL
     assert L.crk_get_timings(None, None) == libcrk.CRK_EINVAL
     assert L.crk_destroy(None) == libcrk.CRK_OK
+
+
+@pytest.mark.parametrize("kw,word", [(dict(max_slots=0), "max_slots"), (dict(max_slots=70000), "max_slots"),
+                                     (dict(hbm_budget_bytes=0), "hbm_budget_bytes"),
+                                     (dict(snapshot_every=-1), "snapshot_every")])
+def test_service_create_rejects_bad_params_before_touching_the_device(libcrk, kw, word):
+    args = dict(hbm_budget_bytes=1 << 30, max_slots=4)
+    args.update(kw)
+    with pytest.raises(libcrk.CrkError) as e:
+        libcrk.crk_service_create(**args)
+    assert e.value.code == libcrk.CRK_EINVAL and word in str(e.value)
+
+
+def test_noalloc_argument_checks_without_a_device(libcrk):
+    """The allocation-free entry point answers bad sizes, a bad box and null
+    arrays (and n = 0) before any CUDA call."""
+    f = libcrk.lib().crk_neighbours_noalloc
+    i64, dbl = ctypes.c_int64, ctypes.c_double
+    assert f(i64(-1), None, None, None, dbl(1.0), None, None, None) == libcrk.CRK_EINVAL
+    assert f(i64(libcrk.CRK_NOALLOC_MAX_N + 1), None, None, None, dbl(1.0), None, None, None) == libcrk.CRK_EINVAL
+    assert f(i64(8), None, None, None, dbl(0.0), None, None, None) == libcrk.CRK_EINVAL
+    assert f(i64(8), None, None, None, dbl(1.0), None, None, None) == libcrk.CRK_EINVAL
+    assert f(i64(0), None, None, None, dbl(1.0), None, None, None) == libcrk.CRK_OK
