@@ -28,6 +28,10 @@ MUTATIONS = {
     "m2_packing_index": ("static const int ORC_SYM_B[6] = {0, 1, 2, 1, 2, 2};",
                          "static const int ORC_SYM_B[6] = {0, 1, 2, 1, 1, 2};"),
     "gravity_drops_softening": ("double s2 = r2 + e2;", "double s2 = r2;"),
+    "kdk_predictor_drops_half_kick": ("for (int64_t i = 0; i < 3 * n; ++i) vp[i] = vel[i] + hdt * acc[i];",
+                                      "for (int64_t i = 0; i < 3 * n; ++i) vp[i] = vel[i];"),
+    "kdk_energy_predictor_drops_half_kick": ("for (int64_t i = 0; i < n; ++i) up[i] = u[i] + hdt * dudt[i];",
+                                             "for (int64_t i = 0; i < n; ++i) up[i] = u[i];"),
 }
 
 

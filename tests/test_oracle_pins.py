@@ -404,6 +404,31 @@ def test_kdk_conserves_momentum(oracle_lib):
     assert np.all(out["pos"] >= 0) and np.all(out["pos"] < 1)
 
 
+def test_kdk_converges_at_second_order(oracle_lib):
+    """A compressing gas blob with a hot core (viscosity active, forces that
+    depend on the predicted velocities and energies) against a run at
+    dt / 256: halving dt divides the velocity error by about 4.  A predictor
+    that left out the half kick with the old rates (forces at the half-step
+    velocities) would make the scheme first order."""
+    rng = np.random.default_rng(11)
+    g = (np.arange(6) - 2.5) * 0.02
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    pos = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1) + 0.5
+    r = np.linalg.norm(pos - 0.5, axis=1)
+    u = np.where(r < 0.035, 40.0, 1.0)
+    pos = pos + rng.uniform(-0.002, 0.002, pos.shape)
+    n = len(pos)
+    vel = -3.0 * (pos - 0.5)
+    mass, h, sp = np.full(n, 1e-5), np.full(n, 0.025), np.ones(n, np.uint8)
+    p = oracle_lib.make_params(box=1.0, G=0.0, r_cut=0.1, r_split=0.02, eps_soft=0.0)
+    T = 4e-3
+    ref = oracle_lib.kdk(pos, vel, mass, u, h, sp, p, T / 1024, 1024)
+    errs = [np.linalg.norm(oracle_lib.kdk(pos, vel, mass, u, h, sp, p, T / k, k)["vel"] - ref["vel"])
+            for k in (4, 8, 16)]
+    ratios = [errs[0] / errs[1], errs[1] / errs[2]]
+    assert all(3.2 < q < 5.0 for q in ratios), (errs, ratios)
+
+
 def test_sampled_outputs_equal_full_outputs(oracle_lib):
     box = wl.jittered_lattice(10, seed=1)
     p = _params(oracle_lib, box)
