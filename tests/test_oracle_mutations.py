@@ -28,6 +28,9 @@ MUTATIONS = {
     "m2_packing_index": ("static const int ORC_SYM_B[6] = {0, 1, 2, 1, 2, 2};",
                          "static const int ORC_SYM_B[6] = {0, 1, 2, 1, 1, 2};"),
     "gravity_drops_softening": ("double s2 = r2 + e2;", "double s2 = r2;"),
+    "viscosity_clamp_inverted": ("if (mu > 0.0) mu = 0.0;", "if (mu < 0.0) mu = 0.0;"),
+    "viscosity_linear_term_sign": ("return rho * (-p->av_alpha * c * mu + p->av_beta * mu * mu);",
+                                   "return rho * (p->av_alpha * c * mu + p->av_beta * mu * mu);"),
     "kdk_predictor_drops_half_kick": ("for (int64_t i = 0; i < 3 * n; ++i) vp[i] = vel[i] + hdt * acc[i];",
                                       "for (int64_t i = 0; i < 3 * n; ++i) vp[i] = vel[i];"),
     "kdk_energy_predictor_drops_half_kick": ("for (int64_t i = 0; i < n; ++i) up[i] = u[i] + hdt * dudt[i];",

@@ -404,6 +404,36 @@ def test_kdk_conserves_momentum(oracle_lib):
     assert np.all(out["pos"] >= 0) and np.all(out["pos"] < 1)
 
 
+def test_viscosity_only_heats_and_only_between_approaching_pairs(oracle_lib):
+    """With zero pressure and the plain kernel (A = 1, B = 0) the hydro
+    force is the artificial viscosity alone: a pair that recedes feels
+    nothing, and every particle's du/dt is >= 0 in any velocity field (the
+    viscosity turns kinetic energy into heat, never back)."""
+    rng = np.random.default_rng(12)
+    N = 300
+    pos = 0.5 + rng.uniform(-0.2, 0.2, size=(N, 3))
+    sp = np.ones(N, np.uint8)
+    h = np.full(N, 0.05)
+    mass = np.full(N, 1.0 / N)
+    p = oracle_lib.make_params(box=1.0, r_cut=0.1, av_alpha=1.0, av_beta=2.0)
+    rho, V, _, _ = oracle_lib.density(pos, mass, np.ones(N), h, sp, p)
+    P = np.zeros(N)
+    c = rng.uniform(0.5, 2.0, N)
+    args = (np.ones(N), np.zeros((N, 3)), np.zeros((N, 3)), np.zeros((N, 3, 3)), p)
+    # receding everywhere: no force, no heating
+    acc, dudt = oracle_lib.hydro(pos, 2.0 * (pos - 0.5), mass, h, sp, rho, V, P, c, *args)
+    assert np.all(acc == 0.0) and np.all(dudt == 0.0)
+    # approaching everywhere: repulsion and heating of every particle with a neighbour
+    acc, dudt = oracle_lib.hydro(pos, -2.0 * (pos - 0.5), mass, h, sp, rho, V, P, c, *args)
+    assert np.all(dudt >= 0.0) and np.sum(dudt > 0.0) > 0.9 * N
+    assert np.sum((pos - 0.5) * acc) > 0.0
+    # any velocity field: heating only
+    for seed in range(3):
+        vel = np.random.default_rng(seed).standard_normal((N, 3))
+        acc, dudt = oracle_lib.hydro(pos, vel, mass, h, sp, rho, V, P, c, *args)
+        assert np.all(dudt >= -1e-14 * np.abs(dudt).max()) and dudt.sum() > 0.0
+
+
 def test_kdk_converges_at_second_order(oracle_lib):
     """A compressing gas blob with a hot core (viscosity active, forces that
     depend on the predicted velocities and energies) against a run at
