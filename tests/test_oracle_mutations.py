@@ -31,6 +31,8 @@ MUTATIONS = {
     "viscosity_clamp_inverted": ("if (mu > 0.0) mu = 0.0;", "if (mu < 0.0) mu = 0.0;"),
     "viscosity_linear_term_sign": ("return rho * (-p->av_alpha * c * mu + p->av_beta * mu * mu);",
                                    "return rho * (p->av_alpha * c * mu + p->av_beta * mu * mu);"),
+    "kdk_half_drift": ("pos[i] = orc_wrap_pos(pos[i] + dt * vel[i], p->L);",
+                       "pos[i] = orc_wrap_pos(pos[i] + hdt * vel[i], p->L);"),
     "kdk_predictor_drops_half_kick": ("for (int64_t i = 0; i < 3 * n; ++i) vp[i] = vel[i] + hdt * acc[i];",
                                       "for (int64_t i = 0; i < 3 * n; ++i) vp[i] = vel[i];"),
     "kdk_energy_predictor_drops_half_kick": ("for (int64_t i = 0; i < n; ++i) up[i] = u[i] + hdt * dudt[i];",

@@ -434,6 +434,22 @@ def test_viscosity_only_heats_and_only_between_approaching_pairs(oracle_lib):
         assert np.all(dudt >= -1e-14 * np.abs(dudt).max()) and dudt.sum() > 0.0
 
 
+def test_kdk_moves_free_particles_in_straight_lines(oracle_lib):
+    """Dark matter with G = 0 feels no force: after k steps of dt every
+    particle sits at x0 + k dt v, wrapped into the box, with v unchanged."""
+    rng = np.random.default_rng(13)
+    n = 50
+    pos = rng.uniform(0, 1, (n, 3))
+    vel = rng.standard_normal((n, 3))
+    z = np.zeros(n)
+    p = oracle_lib.make_params(box=1.0, G=0.0, r_cut=0.1, r_split=0.02, eps_soft=0.0)
+    out = oracle_lib.kdk(pos, vel, np.ones(n), z, z, np.zeros(n, np.uint8), p, 0.01, 7)
+    assert np.array_equal(out["vel"], vel) and np.all(out["acc"] == 0.0)
+    want = np.mod(pos + 0.07 * vel, 1.0)
+    d = (out["pos"] - want + 0.5) % 1.0 - 0.5
+    assert np.max(np.abs(d)) < 1e-14
+
+
 def test_kdk_converges_at_second_order(oracle_lib):
     """A compressing gas blob with a hot core (viscosity active, forces that
     depend on the predicted velocities and energies) against a run at
