@@ -31,6 +31,14 @@ MUTATIONS = {
     "viscosity_clamp_inverted": ("if (mu > 0.0) mu = 0.0;", "if (mu < 0.0) mu = 0.0;"),
     "viscosity_linear_term_sign": ("return rho * (-p->av_alpha * c * mu + p->av_beta * mu * mu);",
                                    "return rho * (p->av_alpha * c * mu + p->av_beta * mu * mu);"),
+    # the friends-of-friends labels, caught by their own pins
+    "fof_non_strict_link": ("if (!(orc_sep(pos, i, j, L, dx) < b2)) continue;",
+                            "if (!(orc_sep(pos, i, j, L, dx) <= b2)) continue;", "tests/test_oracle_fof.py"),
+    "fof_ignores_species_of_j": ("if (j <= i || !((species_mask >> species[j]) & 1)) continue;",
+                                 "if (j <= i) continue;", "tests/test_oracle_fof.py"),
+    "fof_labels_by_largest_root": ("if (ri < rj) par[rj] = ri;\n                else par[ri] = rj;",
+                                   "if (ri < rj) par[ri] = rj;\n                else par[rj] = ri;",
+                                   "tests/test_oracle_fof.py"),
     "kdk_half_drift": ("pos[i] = orc_wrap_pos(pos[i] + dt * vel[i], p->L);",
                        "pos[i] = orc_wrap_pos(pos[i] + hdt * vel[i], p->L);"),
     "kdk_predictor_drops_half_kick": ("for (int64_t i = 0; i < 3 * n; ++i) vp[i] = vel[i] + hdt * acc[i];",
@@ -43,9 +51,9 @@ MUTATIONS = {
 @pytest.mark.slow
 @pytest.mark.parametrize("name", sorted(MUTATIONS))
 def test_pins_catch_planted_mistake(tmp_path, name):
-    before, after = MUTATIONS[name]
+    before, after, *pins = MUTATIONS[name]
     src = open(os.path.join(ROOT, "oracle", "crk_oracle.c")).read()
-    assert before in src, name
+    assert src.count(before) == 1, name
     work = tmp_path / "tree"
     shutil.copytree(os.path.join(ROOT, "oracle"), work / "oracle",
                     ignore=shutil.ignore_patterns("_build", "__pycache__"))
@@ -57,8 +65,8 @@ def test_pins_catch_planted_mistake(tmp_path, name):
     shutil.copy(os.path.join(ROOT, "pytest.ini"), work / "pytest.ini")
     (work / "oracle" / "crk_oracle.c").write_text(src.replace(before, after))
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:randomly",
-                        "tests/test_oracle_pins.py"], cwd=work, capture_output=True, text=True,
-                       timeout=600)
+                        pins[0] if pins else "tests/test_oracle_pins.py"], cwd=work, capture_output=True,
+                       text=True, timeout=600)
     assert r.returncode == 1, f"mutation {name} survived:\n{r.stdout[-2000:]}"
 
 
