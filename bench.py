@@ -83,18 +83,26 @@ class ClockSampler:
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, device: int):
+    def __init__(self, device: int, cmd=None):
         self.device = device
         self.proc = None
+        self.cmd = cmd or ["nvidia-smi", "-i", str(device), f"--query-gpu={self.FIELDS}",
+                           "--format=csv,noheader,nounits", "-lms", "100"]
 
     def __enter__(self):
+        import select
+
         try:
-            self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
-                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.proc = subprocess.Popen(self.cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
         except OSError:
             self.proc = None
+            return self
+        # wait (at most 5 s) until the sampler runs, so that the timed region
+        # is sampled from its start; the first record precedes it and is dropped
+        ready, _, _ = select.select([self.proc.stdout], [], [], 5.0)
+        if ready:
+            self.proc.stdout.readline()
         return self
 
     def __exit__(self, *exc):

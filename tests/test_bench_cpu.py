@@ -98,3 +98,27 @@ def test_reference_arm_line(tmp_path):
     assert cb["value"] == line["value"]
     assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
+
+
+def test_clock_sampler_records_the_region_after_its_first_sample():
+    """The sampler waits for its first record, drops it, and keeps what the
+    sampling command prints while the region runs (a stand-in command here)."""
+    import sys
+    import time
+
+    line = "0, 2070, 2070, 900.0, 0x0, Not Active, Not Active, Not Active, Not Active"
+    prog = ("import sys, time\n"
+            "print('0, 1, 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active', flush=True)\n"
+            "time.sleep(0.3)\n"
+            f"for _ in range(3): print({line!r}, flush=True); time.sleep(0.05)\n"
+            "time.sleep(30)\n")
+    with bench.ClockSampler(0, cmd=[sys.executable, "-c", prog]) as s:
+        time.sleep(0.8)
+    out = s.summary()
+    assert out["samples"] == 3 and out["sm_mhz"] == 2070.0 and out["reasons"] == []
+
+
+def test_clock_sampler_without_the_tool():
+    with bench.ClockSampler(0, cmd=["/nonexistent/sampler"]) as s:
+        pass
+    assert s.summary()["reasons"] == ["unsampled"]
