@@ -151,3 +151,30 @@ def test_noalloc_argument_checks_without_a_device(libcrk):
     assert f(i64(8), None, None, None, dbl(0.0), None, None, None) == libcrk.CRK_EINVAL
     assert f(i64(8), None, None, None, dbl(1.0), None, None, None) == libcrk.CRK_EINVAL
     assert f(i64(0), None, None, None, dbl(1.0), None, None, None) == libcrk.CRK_OK
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path, monkeypatch):
+    """There is no CPU fallback: with libcrk.so missing the binding raises
+    instead of computing anything."""
+    from paper_2510_03557_gb300 import crk
+
+    monkeypatch.setattr(crk, "_lib", None)
+    monkeypatch.setattr(crk, "LIB_PATH", str(tmp_path / "missing" / "libcrk.so"))
+    with pytest.raises(ImportError):
+        crk.lib()
+    with pytest.raises(ImportError):
+        crk.crk_create(crk.params())
+
+
+def test_product_package_never_imports_the_oracle():
+    """Only the tests, the smoke check and the bench's CPU legs may use the
+    oracle: no module of the package names it."""
+    pkg = os.path.join(ROOT, "paper_2510_03557_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        if "_build" in dirpath or "__pycache__" in dirpath:
+            continue
+        for f in files:
+            if f.endswith((".py", ".cu", ".cpp", ".h")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", src, flags=re.M), f
+                assert "crk_oracle" not in src and "orc_" not in src, f
