@@ -178,3 +178,14 @@ def test_product_package_never_imports_the_oracle():
                 src = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle\b", src, flags=re.M), f
                 assert "crk_oracle" not in src and "orc_" not in src, f
+
+
+def test_oracle_never_uses_the_cuda_path():
+    """The oracle shares no code with the CUDA path: it imports nothing of the
+    package and loads none of its libraries."""
+    odir = os.path.join(ROOT, "oracle")
+    for f in os.listdir(odir):
+        if f.endswith((".py", ".c", ".h")):
+            src = open(os.path.join(odir, f)).read()
+            assert "paper_2510_03557_gb300" not in src, f
+            assert not re.search(r"libcrk\.so|crk_api|passes\.cu", src), f
