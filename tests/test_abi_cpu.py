@@ -189,3 +189,10 @@ def test_oracle_never_uses_the_cuda_path():
             src = open(os.path.join(odir, f)).read()
             assert "paper_2510_03557_gb300" not in src, f
             assert not re.search(r"libcrk\.so|crk_api|passes\.cu", src), f
+
+
+def test_build_compiles_every_source_for_sm_103a_only():
+    srcs = {f for f in os.listdir(build_mod.CSRC) if f.endswith((".cu", ".cpp"))}
+    assert srcs == set(build_mod.SOURCES)
+    assert build_mod.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+    assert "-lineinfo" in build_mod.FLAGS and "-O3" in build_mod.FLAGS
