@@ -290,6 +290,40 @@ int crk_get_bins(crk_sim *sim, uint8_t *bins, int mem);
  * of crk_forces. */
 int crk_autotune(crk_sim *sim, const int *caps, int ncaps, int *best_cap, double *ms_out);
 
+/* Leaves and leaf-pair lists of the handle's last tree (paper Sec. IV-B1:
+ * base leaves of the spatial tree and the leaf-pair interaction lists), for
+ * inspection and tests.  The sizes are written always; every array pointer
+ * is an optional caller-owned HOST buffer (NULL skips it), so a first call
+ * with NULL arrays gets the sizes.  Particles are in the tree's sorted order:
+ * leaf L holds sorted positions leaf_start[L] .. leaf_start[L] +
+ * leaf_count[L] - 1, all of one box and one species; order[k] is the
+ * original (load-order) index of sorted position k.  A leaf's box is
+ * leaf_centre +- leaf_half per axis (periodic: a particle lies in it when its
+ * minimum-image offset from the centre is within the half extent).  Row L of
+ * a list (CSR: the entries row[L] .. row[L+1] - 1 of col) holds the leaves
+ * whose boxes lie within reach of leaf L's (hydro: gas leaves within the
+ * larger of the two leaves' max 2h; gravity: all leaves within r_cut), L
+ * itself included, in ascending order.  Errors: CRK_EINVAL (null handle or
+ * sizes, no tree yet: call crk_forces or crk_step first), CRK_ECUDA.
+ * Synchronises the stream. */
+typedef struct {
+    int64_t n;              /* written: particles */
+    int64_t nleaf;          /* written: leaves */
+    int64_t npair_hydro;    /* written: entries of the hydro list */
+    int64_t npair_grav;     /* written: entries of the gravity list */
+    int64_t *order;         /* n */
+    uint32_t *leaf_start;   /* nleaf */
+    uint32_t *leaf_count;   /* nleaf */
+    uint8_t *leaf_species;  /* nleaf: CRK_DM or CRK_GAS */
+    double *leaf_centre;    /* 3 nleaf (x, y, z per leaf) */
+    float *leaf_half;       /* 3 nleaf: half extents, rounded up */
+    uint32_t *hydro_row;    /* nleaf + 1 */
+    uint32_t *hydro_col;    /* npair_hydro */
+    uint32_t *grav_row;     /* nleaf + 1 */
+    uint32_t *grav_col;     /* npair_grav */
+} crk_tree;
+int crk_get_tree(crk_sim *sim, crk_tree *out);
+
 /* Turns per-phase CUDA-event timing on (1) or off (0) and resets it. */
 int crk_set_timing(crk_sim *sim, int enable);
 int crk_get_timings(crk_sim *sim, crk_timings *out);
@@ -299,21 +333,27 @@ int crk_destroy(crk_sim *sim);
 
 /* ------------------------------------------------------------------ */
 /* Service: continuous batching of many small-box force-and-KDK jobs.   */
-/* A host thread admits submitted jobs while slots and the HBM budget    */
-/* allow, keeps every admitted job's particles and tree resident in one  */
-/* batched device state, advances all resident jobs one KDK step per     */
-/* batched launch sequence, and publishes each job when its steps are    */
-/* done; new jobs join at the next step boundary.                       */
+/* Jobs are sorted by particle count into size classes.  Each class has  */
+/* its own host thread, CUDA stream and batched device state: it admits  */
+/* its submitted jobs (FIFO) while slots and the shared HBM budget allow,*/
+/* keeps every admitted job's particles and tree resident, advances all  */
+/* its resident jobs one KDK step per batched launch sequence, and       */
+/* publishes each job when its steps are done; new jobs join at the next */
+/* step boundary.  The classes step side by side on the device, so a     */
+/* small job does not wait for the largest boxes.                        */
 /* ------------------------------------------------------------------ */
 typedef struct {
-    size_t hbm_budget_bytes;   /* admission limit on the device memory of resident jobs */
-    int max_slots;             /* at most this many resident jobs */
+    size_t hbm_budget_bytes;   /* admission limit on the device memory of all resident jobs */
+    int max_slots;             /* at most this many resident jobs per size class */
     int precision;             /* CRK_MIXED or CRK_FP64 */
     int leaf_cap;              /* 32, 64 or 128 */
     int device;                /* CUDA device ordinal */
     int snapshot_every;        /* copy every resident job's state to host memory after every
                                   this many of its steps (0: never); see crk_service_snapshot */
-    int reserved[3];
+    int size_classes;          /* number of size classes K in [1, 8] (0: 3).  A job of n particles
+                                  goes to class k, the first with n < 8192 * 8^(k+1), or to the
+                                  last class (K = 3: n < 65,536; n < 524,288; the rest) */
+    int reserved[2];
 } crk_service_params;
 
 typedef struct {
@@ -347,11 +387,15 @@ typedef struct {
 
 typedef struct crk_service crk_service;
 
-/* Creates the service and starts its host thread on params->device.
- * Errors: CRK_EINVAL, CRK_ENOMEM, CRK_ECUDA. */
+/* Creates the service and starts its host threads (one per size class) on
+ * params->device.  Errors: CRK_EINVAL, CRK_ENOMEM, CRK_ECUDA. */
 int crk_service_create(const crk_service_params *params, crk_service **out);
-/* Copies the job's arrays and enqueues it; *ticket identifies it.  Errors:
- * CRK_EINVAL (bad job, or a job that alone exceeds the budget). Thread-safe. */
+/* Copies the job's arrays and enqueues it in its size class; *ticket
+ * identifies it.  With snapshot_every > 0 the pinned host buffer of the
+ * job's snapshots is allocated here, on the submitting thread (its current
+ * device is restored), and the device staging at admission, so the serving
+ * loop allocates nothing per step.  Errors: CRK_EINVAL (bad job, or a job
+ * that alone exceeds the budget), CRK_ENOMEM.  Thread-safe. */
 int crk_submit(crk_service *service, const crk_job *job, uint64_t *ticket);
 /* Waits up to timeout_us (0 = do not wait, < 0 = forever) for the job;
  * CRK_EPENDING if still running, CRK_ENOTFOUND for an unknown ticket.  On
@@ -401,6 +445,13 @@ int crk_service_cancel(crk_service *service);
  * device before any stream capture.  All calls share the one array and it
  * keeps the last call's contents, so calls whose GPU work overlaps (on
  * different streams or threads) race: order them on one stream.
+ *
+ * Invalid particle values are reported in the outputs, since the call does
+ * not wait for the GPU: a particle with a coordinate outside [0, box) (or
+ * not finite) gets count -1 and hash 0 and belongs to no other particle's
+ * set; a gas particle whose h is not finite, negative, or has 2h >= box/2
+ * (where one periodic wrap is no longer the minimum image) gets count -1 and
+ * hash 0 while still counting in the sets of the others.
  *
  * Errors (returned; crk_last_error() is not updated by this call):
  * CRK_EINVAL for n < 0, n > CRK_NOALLOC_MAX_N, box <= 0 or a NULL pointer

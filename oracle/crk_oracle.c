@@ -148,9 +148,14 @@ static int orc_cell_of(double x, double L, int nc)
     return c;
 }
 
+/* Cells at least R (1 + 1e-9) wide: a cell index is rounded, so with cells
+ * exactly R wide a pair with r just below R could land two cells apart; the
+ * margin keeps every pair with r < R in neighbouring cells. */
 static int orc_cells_build(orc_cells *cl, int64_t n, const double *pos, double L, double R, int brute)
 {
-    int nc = (R > 0.0) ? (int)floor(L / R) : 1;
+    double Rm = R * (1.0 + 1e-9);
+    int nc = (R > 0.0) ? (int)floor(L / Rm) : 1;
+    while (nc > 1 && L / (double)nc < Rm) --nc;
     if (brute || nc < 3) nc = 1;
     if (nc > 1024) nc = 1024;
     int64_t ncell = (int64_t)nc * nc * nc;

@@ -39,7 +39,7 @@ ABI = ("crk_create", "crk_load", "crk_load_boxes", "crk_forces", "crk_step", "cr
        "crk_destroy", "crk_fof", "crk_pm_accel", "crk_step_bins", "crk_get_bins",
        "crk_autotune", "crk_service_create", "crk_submit", "crk_poll", "crk_service_destroy",
        "crk_service_snapshot", "crk_service_cancel",
-       "crk_neighbours_noalloc", "crk_last_error")
+       "crk_neighbours_noalloc", "crk_get_tree", "crk_last_error")
 CRK_NOALLOC_MAX_N = 262144
 
 
@@ -79,10 +79,18 @@ class Timings(ctypes.Structure):
                                                "tests_grav_target", "list_slots")]
 
 
+class Tree(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("n", "nleaf", "npair_hydro", "npair_grav")] + \
+               [(k, ctypes.c_void_p) for k in ("order", "leaf_start", "leaf_count", "leaf_species",
+                                                "leaf_centre", "leaf_half", "hydro_row", "hydro_col",
+                                                "grav_row", "grav_col")]
+
+
 class ServiceParams(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int),
                 ("precision", ctypes.c_int), ("leaf_cap", ctypes.c_int), ("device", ctypes.c_int),
-                ("snapshot_every", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("snapshot_every", ctypes.c_int), ("size_classes", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 class Job(ctypes.Structure):
@@ -287,6 +295,25 @@ def crk_get_timings(sim) -> dict:
     return {k: getattr(t, k) for k, _ in Timings._fields_}
 
 
+def crk_get_tree(sim) -> dict:
+    """Leaves and leaf-pair lists of the handle's last tree, as host arrays:
+    order (original index of each sorted position), leaf_start, leaf_count,
+    leaf_species, leaf_centre (nleaf x 3), leaf_half (nleaf x 3), and the CSR
+    lists hydro_row/hydro_col, grav_row/grav_col."""
+    t = Tree()
+    _check(lib().crk_get_tree(sim, ctypes.byref(t)))
+    n, nl = int(t.n), int(t.nleaf)
+    out = {"order": np.zeros(n, np.int64), "leaf_start": np.zeros(nl, np.uint32),
+           "leaf_count": np.zeros(nl, np.uint32), "leaf_species": np.zeros(nl, np.uint8),
+           "leaf_centre": np.zeros((nl, 3)), "leaf_half": np.zeros((nl, 3), np.float32),
+           "hydro_row": np.zeros(nl + 1, np.uint32), "hydro_col": np.zeros(int(t.npair_hydro), np.uint32),
+           "grav_row": np.zeros(nl + 1, np.uint32), "grav_col": np.zeros(int(t.npair_grav), np.uint32)}
+    for k, v in out.items():
+        setattr(t, k, v.ctypes.data if v.size else None)
+    _check(lib().crk_get_tree(sim, ctypes.byref(t)))
+    return out
+
+
 def crk_destroy(sim):
     _check(lib().crk_destroy(sim))
 
@@ -347,8 +374,9 @@ def crk_autotune(sim, caps=(32, 64, 128)):
 
 
 def crk_service_create(hbm_budget_bytes: int, max_slots: int, precision=CRK_MIXED, leaf_cap=64,
-                       device=0, snapshot_every=0) -> ctypes.c_void_p:
+                       device=0, snapshot_every=0, size_classes=0) -> ctypes.c_void_p:
     p = ServiceParams()
+    p.size_classes = size_classes
     p.hbm_budget_bytes = int(hbm_budget_bytes)
     p.max_slots = max_slots
     p.precision = precision

@@ -1234,6 +1234,53 @@ extern "C" int crk_get_timings(crk_sim *s, crk_timings *t)
     return CRK_OK;
 }
 
+extern "C" int crk_get_tree(crk_sim *s, crk_tree *t)
+{
+    if (!s || !t) return fail(CRK_EINVAL, "null argument");
+    if (!s->tree_valid || (s->n > 0 && s->nleaf == 0))
+        return fail(CRK_EINVAL, "no tree: call crk_forces or crk_step first");
+    t->n = s->n;
+    t->nleaf = s->nleaf;
+    t->npair_hydro = s->npair_h;
+    t->npair_grav = s->npair_g;
+    const size_t nl = (size_t)s->nleaf;
+    if (nl == 0) return CRK_OK;
+    CK(cudaStreamSynchronize(s->st));
+    auto get = [&](void *dst, const void *src, size_t bytes) -> int {
+        if (dst && bytes) CK(cudaMemcpy(dst, src, bytes, cudaMemcpyDeviceToHost));
+        return CRK_OK;
+    };
+    if (t->order && s->n > 0) {
+        std::vector<uint32_t> id((size_t)s->n);
+        RET(get(id.data(), s->sa.id, id.size() * sizeof(uint32_t)));
+        for (size_t k = 0; k < id.size(); ++k) t->order[k] = (int64_t)id[k];
+    }
+    RET(get(t->leaf_start, s->lv.start, nl * sizeof(uint32_t)));
+    RET(get(t->leaf_count, s->lv.count, nl * sizeof(uint32_t)));
+    RET(get(t->leaf_species, s->lv.species, nl));
+    if (t->leaf_centre && nl) {
+        std::vector<double> c(3 * nl);
+        RET(get(c.data(), s->lv.cx, nl * sizeof(double)));
+        RET(get(c.data() + nl, s->lv.cy, nl * sizeof(double)));
+        RET(get(c.data() + 2 * nl, s->lv.cz, nl * sizeof(double)));
+        for (size_t L = 0; L < nl; ++L)
+            for (int a = 0; a < 3; ++a) t->leaf_centre[3 * L + a] = c[a * nl + L];
+    }
+    if (t->leaf_half && nl) {
+        std::vector<float> e(3 * nl);
+        RET(get(e.data(), s->lv.ex, nl * sizeof(float)));
+        RET(get(e.data() + nl, s->lv.ey, nl * sizeof(float)));
+        RET(get(e.data() + 2 * nl, s->lv.ez, nl * sizeof(float)));
+        for (size_t L = 0; L < nl; ++L)
+            for (int a = 0; a < 3; ++a) t->leaf_half[3 * L + a] = e[a * nl + L];
+    }
+    RET(get(t->hydro_row, s->hrow.p, (nl + 1) * sizeof(uint32_t)));
+    RET(get(t->hydro_col, s->hcol.p, (size_t)s->npair_h * sizeof(uint32_t)));
+    RET(get(t->grav_row, s->grow.p, (nl + 1) * sizeof(uint32_t)));
+    RET(get(t->grav_col, s->gcol.p, (size_t)s->npair_g * sizeof(uint32_t)));
+    return CRK_OK;
+}
+
 extern "C" int crk_destroy(crk_sim *s)
 {
     if (!s) return CRK_OK;

@@ -129,6 +129,11 @@ void note_launches(int k);
 int64_t launches_so_far();
 
 // ---- scan / sort / tree (tree.cu) ----
+// Items per tile of the scan and radix-sort kernels, and the scratch words
+// those need for n items (a caller sizing fixed scratch uses these too).
+constexpr int64_t kSortTile = 4096;
+constexpr size_t radix_count_words_for(int64_t n) { return (size_t)256 * (size_t)((n + kSortTile - 1) / kSortTile); }
+constexpr size_t scan_tmp_words_for(int64_t n) { return (size_t)((n + kSortTile - 1) / kSortTile) + 1; }
 void scan_exclusive_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *total,
                         uint32_t *tmp, cudaStream_t st);
 size_t scan_tmp_words(int64_t n);

@@ -26,10 +26,14 @@ constexpr size_t align_up(size_t b) { return (b + kAlign - 1) / kAlign * kAlign;
 // Layout of the scratch array for kMaxN particles.
 constexpr size_t kKeysBytes = align_up(kMaxN * sizeof(uint64_t));
 constexpr size_t kValsBytes = align_up(kMaxN * sizeof(uint32_t));
-constexpr size_t kCountWords = 256 * ((kMaxN + 4095) / 4096);
+// the radix sort's histogram words for kMaxN keys, and the scan scratch of
+// its scans over those words (sized by the sort's own formulas)
+constexpr size_t kCountWords = radix_count_words_for(kMaxN);
 constexpr size_t kCountBytes = align_up(kCountWords * sizeof(uint32_t));
-constexpr size_t kScanWords = (kCountWords + 4095) / 4096 + 1 + (kMaxN + 4095) / 4096 + 1 + 8;
+constexpr size_t kScanWords = scan_tmp_words_for((int64_t)kCountWords) + 8;
 constexpr size_t kScanBytes = align_up(kScanWords * sizeof(uint32_t));
+static_assert(kCountWords >= radix_count_words_for(kMaxN), "histogram area too small");
+static_assert(kScanWords >= scan_tmp_words_for((int64_t)kCountWords), "scan area too small");
 constexpr size_t kParamBytes = kAlign;  // [0] max 2h bits (u64), [8] cells per side (int)
 constexpr size_t kOffKeys = 0;
 constexpr size_t kOffKeysAlt = kOffKeys + kKeysBytes;
@@ -57,24 +61,40 @@ __device__ __forceinline__ uint64_t mix64(uint64_t x)
     return z ^ (z >> 31);
 }
 
+// A particle takes part only when its position lies in [0, box) on every
+// axis; a gas particle has a set of its own only when 0 <= 2h < box/2 (the
+// minimum image of one wrap is then exact).  Anything else, NaN included,
+// fails these comparisons.
+__device__ __forceinline__ bool pos_ok(const double *pos, int64_t k, double box)
+{
+    const double x = pos[3 * k], y = pos[3 * k + 1], z = pos[3 * k + 2];
+    return x >= 0.0 && x < box && y >= 0.0 && y < box && z >= 0.0 && z < box;
+}
+
+__device__ __forceinline__ bool h_ok(double h, double box) { return h >= 0.0 && 2.0 * h < 0.5 * box; }
+
 __global__ void hmax_k(int64_t n, const double *__restrict__ h, const uint8_t *__restrict__ sp,
-                       unsigned long long *hbits)
+                       double box, unsigned long long *hbits)
 {
     double m = 0.0;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x)
-        if (sp[k] == CRK_GAS) m = fmax(m, 2.0 * h[k]);
+        if (sp[k] == CRK_GAS && h_ok(h[k], box)) m = fmax(m, 2.0 * h[k]);
     for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
     // non-negative doubles order like their bit patterns
     if ((threadIdx.x & 31) == 0) atomicMax(hbits, (unsigned long long)__double_as_longlong(m));
 }
 
-// Cells per side: the largest count whose cell side is >= the largest
-// support; fewer than three cells per side fall back to one cell.
+// Cells per side: the largest count whose cell side exceeds the largest
+// support by a relative margin of 1e-9, so that the rounding of a cell index
+// (a few ulps) never puts a pair with r < H two cells apart; fewer than three
+// cells per side fall back to one cell.
 __global__ void cells_k(double box, unsigned char *param)
 {
     const double H = __longlong_as_double((long long)*reinterpret_cast<unsigned long long *>(param));
-    int nc = H > 0.0 ? (int)floor(box / H) : 1;
+    const double Hm = H * (1.0 + 1e-9);
+    int nc = H > 0.0 ? (int)floor(box / Hm) : 1;
+    while (nc > 1 && box / (double)nc < Hm) --nc;
     if (nc < 3) nc = 1;
     if (nc > 1024) nc = 1024;
     *reinterpret_cast<int *>(param + 8) = nc;
@@ -110,7 +130,9 @@ __device__ __forceinline__ int64_t lower_bound(const uint64_t *keys, int64_t n, 
 }
 
 // One thread per particle: the gather set {gas j != i : r^2 < (2h_i)^2} with
-// the predicate's exact FP64 expression (one wrap, no contraction).
+// the predicate's exact FP64 expression (one wrap, no contraction).  A
+// particle that fails pos_ok, or a gas particle that fails h_ok, gets count
+// -1 and hash 0; a particle that fails pos_ok is in no other set.
 __global__ void gather_k(int64_t n, const double *__restrict__ pos, const double *__restrict__ h,
                          const uint8_t *__restrict__ sp, double box, const unsigned char *param,
                          const uint64_t *__restrict__ keys, const uint32_t *__restrict__ vals,
@@ -120,6 +142,11 @@ __global__ void gather_k(int64_t n, const double *__restrict__ pos, const double
     if (i >= n) return;
     int32_t cnt = 0;
     uint64_t hs = 0;
+    if (!pos_ok(pos, i, box) || (sp[i] == CRK_GAS && !h_ok(h[i], box))) {
+        count[i] = -1;
+        hash[i] = 0;
+        return;
+    }
     if (sp[i] == CRK_GAS) {
         const int nc = *reinterpret_cast<const int *>(param + 8);
         const double hL = 0.5 * box;
@@ -135,7 +162,7 @@ __global__ void gather_k(int64_t n, const double *__restrict__ pos, const double
                     const uint64_t key = ((uint64_t)z * nc + y) * nc + x;
                     for (int64_t k = lower_bound(keys, n, key); k < n && keys[k] == key; ++k) {
                         const uint32_t j = vals[k];
-                        if ((int64_t)j == i || sp[j] != CRK_GAS) continue;
+                        if ((int64_t)j == i || sp[j] != CRK_GAS || !pos_ok(pos, j, box)) continue;
                         double ex = pos[3 * (int64_t)j] - xi, ey = pos[3 * (int64_t)j + 1] - yi,
                                ez = pos[3 * (int64_t)j + 2] - zi;
                         if (ex >= hL) ex -= box; else if (ex < -hL) ex += box;
@@ -206,7 +233,8 @@ extern "C" int crk_neighbours_noalloc(int64_t n, const double *pos, const double
         return CRK_ECUDA;
     }
     const unsigned nb = (unsigned)((n + kT - 1) / kT);
-    hmax_k<<<nb < 304u ? nb : 304u, kT, 0, st>>>(n, h, species, reinterpret_cast<unsigned long long *>(param));
+    hmax_k<<<nb < 304u ? nb : 304u, kT, 0, st>>>(n, h, species, box,
+                                                 reinterpret_cast<unsigned long long *>(param));
     cells_k<<<1, 1, 0, st>>>(box, param);
     cell_keys_k<<<nb, kT, 0, st>>>(n, pos, box, param, keys, vals);
     uint64_t *ko;
@@ -214,7 +242,7 @@ extern "C" int crk_neighbours_noalloc(int64_t n, const double *pos, const double
     // cell ids are below 2^30: four 8-bit passes, ending back in keys / vals
     radix_sort_u64(keys, vals, keys_alt, vals_alt, n, counts, scan, 0, 32, st, &ko, &vo);
     gather_k<<<nb, kT, 0, st>>>(n, pos, h, species, box, param, ko, vo, count, hash);
-    note_launches(4);
+    note_launches(4);  // hmax, cells, keys, gather (the sort counts its own launches)
     if (cudaGetLastError() != cudaSuccess) return CRK_ECUDA;
     return CRK_OK;
 }

@@ -1,12 +1,19 @@
 // Continuous-batching service for many small-box force-and-KDK jobs (the
-// shape of an emulator campaign).  One host thread owns a pool handle whose
-// box slots hold the resident jobs' particles and trees on the device; each
-// iteration it admits queued jobs into free slots while the HBM budget
-// allows, advances every resident job by one KDK step in the same batched
-// launches (a newly admitted job's first step is its initial force
-// evaluation, dt = 0), and publishes jobs whose steps are done.  The
-// paper's GPU-resident design (Sec. IV-A: data stays on the device for the
-// whole PM step) applied across jobs instead of across substeps.
+// shape of an emulator campaign).  Jobs are sorted by size into classes
+// (lanes); each lane owns a pool handle whose box slots hold its resident
+// jobs' particles and trees on the device, its own CUDA stream and its own
+// host thread.  Every iteration a lane admits queued jobs of its class into
+// free slots while the shared HBM budget allows, advances all its resident
+// jobs by one KDK step in the same batched launches (a newly admitted job's
+// first step is its initial force evaluation, dt = 0), and publishes the jobs
+// whose steps are done.  The lanes run side by side on the device, so a small
+// job's step never waits for the largest box in the service.  The paper's
+// GPU-resident design (Sec. IV-A: data stays on the device for the whole PM
+// step) applied across jobs instead of across substeps.
+//
+// Locking: one mutex guards the ticket table, the queues, the slots, the
+// budget and every job field that crk_poll or crk_service_snapshot reads;
+// a job's final state and status are written under it before `done` is set.
 #include "sim.h"
 
 #include <chrono>
@@ -24,10 +31,19 @@ namespace {
 
 using clk = std::chrono::steady_clock;
 
+// Size classes: a job of n particles goes to the first lane whose upper
+// bound exceeds n; lane k < K-1 takes n < 8192 * 8^(k+1) (65,536, 524,288,
+// ...: one class per factor 8, a factor 2 in the lattice side n^(1/3)).
+constexpr int kDefaultClasses = 3;
+constexpr int kMaxClasses = 8;
+
+int64_t class_bound(int k) { return (int64_t)8192 << (3 * (k + 1)); }
+
 struct Job {
     uint64_t ticket = 0;
     crk_physics phys{};
     int64_t n = 0;
+    int lane = 0;
     std::vector<double> pos, vel, mass, u, h;
     std::vector<double> acc, du;  // forces to resume with (empty: a fresh job)
     std::vector<uint8_t> sp;
@@ -42,7 +58,8 @@ struct Job {
     std::string msg;
     bool done = false;
     clk::time_point t_submit, t_admit, t_done;
-    // snapshot: device staging (11 n doubles), pinned host copy, completion event
+    // snapshot: device staging (11 n doubles, allocated at admission), pinned
+    // host copy (allocated at submission), completion event
     crk::DBuf snap_dev;
     double *snap_host = nullptr;
     cudaEvent_t snap_ev = nullptr;
@@ -58,20 +75,26 @@ struct Job {
     }
 };
 
-}  // namespace
-
-struct crk_service {
-    crk_service_params prm{};
+struct Lane {
+    int index = 0;
     crk_sim *sim = nullptr;
     cudaStream_t st = nullptr;
     cudaStream_t side = nullptr;  // snapshot copies
     cudaEvent_t stepped = nullptr;
-    size_t bpp = 0;
     std::thread th;
-    std::mutex mu;
-    std::condition_variable cv_work, cv_done;
+    std::condition_variable cv_work;
     std::deque<std::shared_ptr<Job>> pending;
     std::vector<std::shared_ptr<Job>> slots;
+};
+
+}  // namespace
+
+struct crk_service {
+    crk_service_params prm{};
+    size_t bpp = 0;
+    std::mutex mu;
+    std::condition_variable cv_done;
+    std::vector<std::unique_ptr<Lane>> lanes;
     std::unordered_map<uint64_t, std::shared_ptr<Job>> jobs;
     uint64_t next_ticket = 1;
     size_t resident_bytes = 0;
@@ -80,37 +103,8 @@ struct crk_service {
 
 namespace {
 
-// Starts a snapshot of a resident job: extraction on the compute stream,
-// device-to-host copy on the side stream (overlapping the next step).  The
-// previous copy of the job is completed first (its staging is reused).
-// Caller holds sv->mu.
-int start_snapshot(crk_service *sv, Job &j)
-{
-    const size_t words = (size_t)j.n * 11;
-    if (!j.snap_host) {
-        if (cudaMallocHost(&j.snap_host, words * sizeof(double)) != cudaSuccess) {
-            j.snap_host = nullptr;
-            return fail(CRK_ENOMEM, "no pinned memory for a snapshot of %lld particles", (long long)j.n);
-        }
-        CK(cudaEventCreateWithFlags(&j.snap_ev, cudaEventDisableTiming));
-    }
-    if (j.snap_inflight) {
-        CK(cudaEventSynchronize(j.snap_ev));
-        j.snap_valid = j.snap_steps;
-        j.snap_inflight = false;
-    }
-    RET(j.snap_dev.ensure(words * sizeof(double)));
-    RET(pool_snapshot(sv->sim, j.slot, j.n, j.snap_dev.as<double>()));
-    CK(cudaEventRecord(sv->stepped, sv->st));
-    CK(cudaStreamWaitEvent(sv->side, sv->stepped, 0));
-    CK(cudaMemcpyAsync(j.snap_host, j.snap_dev.p, words * sizeof(double), cudaMemcpyDeviceToHost, sv->side));
-    CK(cudaEventRecord(j.snap_ev, sv->side));
-    j.snap_steps = j.steps_done;
-    j.snap_inflight = true;
-    return CRK_OK;
-}
-
-void finish(crk_service *sv, const std::shared_ptr<Job> &j, int status, const char *msg)
+// Marks a job finished.  Caller holds sv->mu.
+void finish_locked(const std::shared_ptr<Job> &j, int status, const char *msg)
 {
     j->status = status;
     if (msg) j->msg = msg;
@@ -118,7 +112,58 @@ void finish(crk_service *sv, const std::shared_ptr<Job> &j, int status, const ch
     j->done = true;
 }
 
-void worker(crk_service *sv)
+// Starts a snapshot of a resident job: extraction on the lane's stream,
+// device-to-host copy on its side stream (overlapping the next step).  The
+// previous copy of the job is completed first (its staging is reused).
+// Both buffers exist already.  Caller holds sv->mu.
+int start_snapshot(Lane &ln, Job &j)
+{
+    const size_t words = (size_t)j.n * 11;
+    if (j.snap_inflight) {
+        CK(cudaEventSynchronize(j.snap_ev));
+        j.snap_valid = j.snap_steps;
+        j.snap_inflight = false;
+    }
+    RET(pool_snapshot(ln.sim, j.slot, j.n, j.snap_dev.as<double>()));
+    CK(cudaEventRecord(ln.stepped, ln.st));
+    CK(cudaStreamWaitEvent(ln.side, ln.stepped, 0));
+    CK(cudaMemcpyAsync(j.snap_host, j.snap_dev.p, words * sizeof(double), cudaMemcpyDeviceToHost, ln.side));
+    CK(cudaEventRecord(j.snap_ev, ln.side));
+    j.snap_steps = j.steps_done;
+    j.snap_inflight = true;
+    return CRK_OK;
+}
+
+// Final state of a job, copied out of its slot without the lock, then
+// published under it.
+struct Extracted {
+    std::vector<double> pos, vel, u;
+    int rc = CRK_OK;
+    std::string msg;
+};
+
+Extracted extract(Lane &ln, const Job &j)
+{
+    Extracted e;
+    e.pos.resize((size_t)j.n * 3);
+    e.vel.resize((size_t)j.n * 3);
+    e.u.resize((size_t)j.n);
+    e.rc = pool_extract(ln.sim, j.slot, j.n, e.pos.data(), e.vel.data(), e.u.data());
+    if (e.rc != CRK_OK) e.msg = crk_last_error();
+    return e;
+}
+
+void publish_locked(const std::shared_ptr<Job> &j, Extracted &e)
+{
+    if (e.rc == CRK_OK) {
+        j->pos.swap(e.pos);
+        j->vel.swap(e.vel);
+        j->u.swap(e.u);
+    }
+    finish_locked(j, e.rc, e.rc == CRK_OK ? nullptr : e.msg.c_str());
+}
+
+void worker(crk_service *sv, Lane *ln)
 {
     cudaSetDevice(sv->prm.device);
     std::vector<double> dts((size_t)sv->prm.max_slots, 0.0);
@@ -126,127 +171,152 @@ void worker(crk_service *sv)
         std::vector<std::shared_ptr<Job>> admitted;
         {
             std::unique_lock<std::mutex> lk(sv->mu);
-            // FIFO admission while a slot and the budget allow.
-            while (!sv->pending.empty()) {
-                auto &j = sv->pending.front();
+            // FIFO admission of this class while a slot and the budget allow.
+            while (!ln->pending.empty()) {
+                auto &j = ln->pending.front();
                 int free_slot = -1;
                 for (int s = 0; s < sv->prm.max_slots; ++s)
-                    if (!sv->slots[s]) {
+                    if (!ln->slots[s]) {
                         free_slot = s;
                         break;
                     }
                 if (free_slot < 0 || sv->resident_bytes + j->bytes > sv->prm.hbm_budget_bytes) break;
                 j->slot = free_slot;
-                sv->slots[free_slot] = j;
+                ln->slots[free_slot] = j;
                 sv->resident_bytes += j->bytes;
                 admitted.push_back(j);
-                sv->pending.pop_front();
+                ln->pending.pop_front();
             }
             bool any = false;
-            for (auto &p : sv->slots) any = any || (p != nullptr);
+            for (auto &p : ln->slots) any = any || (p != nullptr);
             if (!any) {
                 if (sv->stop) break;
-                sv->cv_work.wait(lk);
+                ln->cv_work.wait(lk);
                 continue;
             }
         }
-        std::vector<std::shared_ptr<Job>> published;
+        std::vector<std::shared_ptr<Job>> leaving;
         for (auto &j : admitted) {
             const bool resume = !j->acc.empty();
-            int rc = pool_add(sv->sim, j->slot, j->phys, j->n, j->pos.data(), j->vel.data(),
-                              j->mass.data(), j->u.data(), j->h.data(), j->sp.data(),
-                              resume ? j->acc.data() : nullptr, resume ? j->du.data() : nullptr);
+            int rc = CRK_OK;
+            if (sv->prm.snapshot_every > 0) rc = j->snap_dev.ensure((size_t)j->n * 11 * sizeof(double));
+            if (rc == CRK_OK)
+                rc = pool_add(ln->sim, j->slot, j->phys, j->n, j->pos.data(), j->vel.data(), j->mass.data(),
+                              j->u.data(), j->h.data(), j->sp.data(), resume ? j->acc.data() : nullptr,
+                              resume ? j->du.data() : nullptr);
+            std::lock_guard<std::mutex> lk(sv->mu);
             j->t_admit = clk::now();
             // a resumed job has the forces of its snapshot: no initial evaluation
             j->init_done = resume;
             if (rc != CRK_OK) {
-                finish(sv, j, rc, crk_last_error());
-                published.push_back(j);
-            }
-        }
-        {
-            std::lock_guard<std::mutex> lk(sv->mu);
-            for (auto &j : published) {
-                sv->slots[j->slot] = nullptr;
+                finish_locked(j, rc, crk_last_error());
+                ln->slots[j->slot] = nullptr;
                 sv->resident_bytes -= j->bytes;
             }
         }
-        std::vector<std::shared_ptr<Job>> leaving;
+        bool notify = false;
         // Cancelled jobs leave at this step boundary.
         {
             std::lock_guard<std::mutex> lk(sv->mu);
-            for (auto &j : sv->slots)
+            for (auto &j : ln->slots)
                 if (j && !j->done && j->cancel) {
-                    finish(sv, j, CRK_ECANCELED, "cancelled");
+                    finish_locked(j, CRK_ECANCELED, "cancelled");
                     leaving.push_back(j);
                 }
         }
         // A resumed job that already ran all its steps only publishes its state.
-        for (auto &j : sv->slots)
-            if (j && !j->done && j->init_done && j->steps_done >= j->nsteps) {
-                std::vector<double> pos((size_t)j->n * 3), vel((size_t)j->n * 3), u((size_t)j->n);
-                int r2 = pool_extract(sv->sim, j->slot, j->n, pos.data(), vel.data(), u.data());
-                j->pos.swap(pos);
-                j->vel.swap(vel);
-                j->u.swap(u);
-                finish(sv, j, r2, r2 == CRK_OK ? nullptr : crk_last_error());
-                leaving.push_back(j);
+        for (auto &j : ln->slots) {
+            if (!j) continue;
+            bool ready;
+            {
+                std::lock_guard<std::mutex> lk(sv->mu);
+                ready = !j->done && j->init_done && j->steps_done >= j->nsteps;
             }
-        // One batched step for every resident job.
-        for (int s = 0; s < sv->prm.max_slots; ++s) {
-            auto &j = sv->slots[s];
-            dts[(size_t)s] = (j && !j->done && j->init_done) ? j->dt : 0.0;
+            if (!ready) continue;
+            Extracted e = extract(*ln, *j);
+            std::lock_guard<std::mutex> lk(sv->mu);
+            publish_locked(j, e);
+            leaving.push_back(j);
         }
+        // One batched step for every live resident job of the lane.
         bool any_live = false;
-        for (auto &j : sv->slots) any_live = any_live || (j && !j->done);
-        int rc = any_live ? pool_step(sv->sim, dts.data()) : CRK_OK;
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            for (int s = 0; s < sv->prm.max_slots; ++s) {
+                auto &j = ln->slots[s];
+                const bool live = j && !j->done;
+                dts[(size_t)s] = (live && j->init_done) ? j->dt : 0.0;
+                any_live = any_live || live;
+            }
+        }
+        int rc = any_live ? pool_step(ln->sim, dts.data()) : CRK_OK;
         if (rc != CRK_OK) {
             std::string msg = crk_last_error();
-            for (auto &j : sv->slots)
+            std::lock_guard<std::mutex> lk(sv->mu);
+            for (auto &j : ln->slots)
                 if (j && !j->done) {
-                    finish(sv, j, rc, msg.c_str());
+                    finish_locked(j, rc, msg.c_str());
                     leaving.push_back(j);
                 }
         } else if (any_live) {
-            for (auto &j : sv->slots) {
-                if (!j || j->done) continue;
-                if (!j->init_done) j->init_done = true;
-                else j->steps_done++;
-                const int every = sv->prm.snapshot_every;
-                if (every > 0 && j->steps_done > 0 && j->steps_done % every == 0) {
+            for (auto &j : ln->slots) {
+                bool finished;
+                {
                     std::lock_guard<std::mutex> lk(sv->mu);
-                    int r3 = start_snapshot(sv, *j);
-                    if (r3 != CRK_OK) {
-                        finish(sv, j, r3, crk_last_error());
-                        leaving.push_back(j);
-                        continue;
+                    if (!j || j->done) continue;
+                    if (!j->init_done) j->init_done = true;
+                    else j->steps_done++;
+                    const int every = sv->prm.snapshot_every;
+                    if (every > 0 && j->steps_done > 0 && j->steps_done % every == 0) {
+                        int r3 = start_snapshot(*ln, *j);
+                        if (r3 != CRK_OK) {
+                            finish_locked(j, r3, crk_last_error());
+                            leaving.push_back(j);
+                            continue;
+                        }
                     }
+                    finished = j->steps_done >= j->nsteps;
                 }
-                if (j->steps_done >= j->nsteps) {
-                    std::vector<double> pos((size_t)j->n * 3), vel((size_t)j->n * 3), u((size_t)j->n);
-                    int r2 = pool_extract(sv->sim, j->slot, j->n, pos.data(), vel.data(), u.data());
-                    j->pos.swap(pos);
-                    j->vel.swap(vel);
-                    j->u.swap(u);
-                    finish(sv, j, r2, r2 == CRK_OK ? nullptr : crk_last_error());
+                if (finished) {
+                    Extracted e = extract(*ln, *j);
+                    std::lock_guard<std::mutex> lk(sv->mu);
+                    publish_locked(j, e);
                     leaving.push_back(j);
                 }
             }
         }
         // a failed retirement launch leaves a CUDA error that the next step reports
-        for (auto &j : leaving) (void)pool_remove(sv->sim, j->slot, j->n);
+        for (auto &j : leaving) (void)pool_remove(ln->sim, j->slot, j->n);
         {
             std::lock_guard<std::mutex> lk(sv->mu);
             for (auto &j : leaving) {
-                sv->slots[j->slot] = nullptr;
+                ln->slots[j->slot] = nullptr;
                 sv->resident_bytes -= j->bytes;
                 j->mass.clear();
                 j->h.clear();
                 j->sp.clear();
             }
+            notify = !leaving.empty() || !admitted.empty();
         }
-        if (!leaving.empty() || !published.empty()) sv->cv_done.notify_all();
+        if (notify) {
+            sv->cv_done.notify_all();
+            // freed budget may let another lane admit its queue head
+            for (auto &other : sv->lanes)
+                if (other.get() != ln) other->cv_work.notify_one();
+        }
     }
+}
+
+void destroy_lane(Lane &ln)
+{
+    if (ln.side) cudaStreamSynchronize(ln.side);
+    if (ln.sim) crk_destroy(ln.sim);
+    if (ln.st) cudaStreamDestroy(ln.st);
+    if (ln.side) cudaStreamDestroy(ln.side);
+    if (ln.stepped) cudaEventDestroy(ln.stepped);
+    ln.sim = nullptr;
+    ln.st = ln.side = nullptr;
+    ln.stepped = nullptr;
 }
 
 }  // namespace
@@ -258,35 +328,36 @@ extern "C" int crk_service_create(const crk_service_params *params, crk_service 
         return fail(CRK_EINVAL, "max_slots must be in [1, 65535]");
     if (params->hbm_budget_bytes == 0) return fail(CRK_EINVAL, "hbm_budget_bytes must be > 0");
     if (params->snapshot_every < 0) return fail(CRK_EINVAL, "snapshot_every must be >= 0");
+    if (params->size_classes < 0 || params->size_classes > kMaxClasses)
+        return fail(CRK_EINVAL, "size_classes must be in [0, %d]", kMaxClasses);
     CK(cudaSetDevice(params->device));
     auto *sv = new crk_service();
     sv->prm = *params;
+    if (sv->prm.size_classes == 0) sv->prm.size_classes = kDefaultClasses;
     crk_params p{};
     p.kernel = CRK_WENDLAND_C4;
     p.leaf_cap = params->leaf_cap ? params->leaf_cap : 64;
     p.precision = params->precision;
-    cudaError_t e = cudaStreamCreateWithFlags(&sv->st, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&sv->side, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sv->stepped, cudaEventDisableTiming);
-    if (e != cudaSuccess) {
-        if (sv->st) cudaStreamDestroy(sv->st);
-        if (sv->side) cudaStreamDestroy(sv->side);
-        delete sv;
-        return fail(CRK_ECUDA, "stream creation failed: %s", cudaGetErrorString(e));
+    int rc = CRK_OK;
+    for (int k = 0; k < sv->prm.size_classes && rc == CRK_OK; ++k) {
+        auto ln = std::make_unique<Lane>();
+        ln->index = k;
+        cudaError_t e = cudaStreamCreateWithFlags(&ln->st, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ln->side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ln->stepped, cudaEventDisableTiming);
+        if (e != cudaSuccess) rc = fail(CRK_ECUDA, "stream creation failed: %s", cudaGetErrorString(e));
+        if (rc == CRK_OK) rc = crk_create(&p, ln->st, &ln->sim);
+        if (rc == CRK_OK) rc = pool_init(ln->sim, params->max_slots);
+        ln->slots.assign((size_t)params->max_slots, nullptr);
+        sv->lanes.push_back(std::move(ln));
     }
-    int rc = crk_create(&p, sv->st, &sv->sim);
-    if (rc == CRK_OK) rc = pool_init(sv->sim, params->max_slots);
     if (rc != CRK_OK) {
-        if (sv->sim) crk_destroy(sv->sim);
-        cudaStreamDestroy(sv->st);
-        cudaStreamDestroy(sv->side);
-        cudaEventDestroy(sv->stepped);
+        for (auto &ln : sv->lanes) destroy_lane(*ln);
         delete sv;
         return rc;
     }
-    sv->bpp = pool_bytes_per_particle(sv->sim);
-    sv->slots.assign((size_t)params->max_slots, nullptr);
-    sv->th = std::thread(worker, sv);
+    sv->bpp = pool_bytes_per_particle(sv->lanes[0]->sim);
+    for (auto &ln : sv->lanes) ln->th = std::thread(worker, sv, ln.get());
     *out = sv;
     return CRK_OK;
 }
@@ -304,6 +375,13 @@ extern "C" int crk_submit(crk_service *sv, const crk_job *job, uint64_t *ticket)
     j->phys = job->phys;
     j->n = job->n;
     const size_t n = (size_t)job->n;
+    j->bytes = n * (sv->bpp + (sv->prm.snapshot_every > 0 ? 11 * sizeof(double) : 0)) + (64u << 10);
+    if (j->bytes > sv->prm.hbm_budget_bytes)
+        return fail(CRK_EINVAL, "job of %lld particles needs %zu bytes, above the budget of %zu",
+                    (long long)job->n, j->bytes, sv->prm.hbm_budget_bytes);
+    int lane = 0;
+    while (lane + 1 < sv->prm.size_classes && job->n >= class_bound(lane)) ++lane;
+    j->lane = lane;
     j->pos.assign(job->pos, job->pos + 3 * n);
     j->vel.assign(job->vel, job->vel + 3 * n);
     j->mass.assign(job->mass, job->mass + n);
@@ -317,18 +395,30 @@ extern "C" int crk_submit(crk_service *sv, const crk_job *job, uint64_t *ticket)
     }
     j->dt = job->dt;
     j->nsteps = job->nsteps;
-    j->bytes = n * (sv->bpp + (sv->prm.snapshot_every > 0 ? 11 * sizeof(double) : 0)) + (64u << 10);
-    if (j->bytes > sv->prm.hbm_budget_bytes)
-        return fail(CRK_EINVAL, "job of %lld particles needs %zu bytes, above the budget of %zu",
-                    (long long)job->n, j->bytes, sv->prm.hbm_budget_bytes);
+    if (sv->prm.snapshot_every > 0) {
+        // the pinned host copy of the job's snapshots, on the service's device
+        // (the caller's current device is restored)
+        int prev = 0;
+        cudaGetDevice(&prev);
+        cudaSetDevice(sv->prm.device);
+        cudaError_t e = cudaMallocHost(&j->snap_host, n * 11 * sizeof(double));
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&j->snap_ev, cudaEventDisableTiming);
+        cudaSetDevice(prev);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(CRK_ENOMEM, "no pinned memory or event for the snapshots of %lld particles",
+                        (long long)job->n);
+        }
+    }
     j->t_submit = clk::now();
+    Lane *ln = sv->lanes[(size_t)lane].get();
     {
         std::lock_guard<std::mutex> lk(sv->mu);
         j->ticket = sv->next_ticket++;
         sv->jobs[j->ticket] = j;
-        sv->pending.push_back(j);
+        ln->pending.push_back(j);
     }
-    sv->cv_work.notify_one();
+    ln->cv_work.notify_one();
     *ticket = j->ticket;
     return CRK_OK;
 }
@@ -345,6 +435,8 @@ extern "C" int crk_poll(crk_service *sv, uint64_t ticket, crk_job_result *res, i
     else if (timeout_us > 0) sv->cv_done.wait_for(lk, std::chrono::microseconds(timeout_us), ready);
     if (!j->done) return fail(CRK_EPENDING, "job %llu has not finished", (unsigned long long)ticket);
     sv->jobs.erase(it);
+    // everything below was written under the mutex before done was set, and
+    // the worker no longer touches a finished job's result
     lk.unlock();
     res->n = j->n;
     res->status = j->status;
@@ -365,21 +457,19 @@ extern "C" int crk_service_destroy(crk_service *sv)
         std::lock_guard<std::mutex> lk(sv->mu);
         sv->stop = true;
         // queued jobs that never started are cancelled
-        for (auto &j : sv->pending) {
-            j->status = CRK_EINVAL;
-            j->msg = "service destroyed before the job was admitted";
-            j->done = true;
+        for (auto &ln : sv->lanes) {
+            for (auto &j : ln->pending) {
+                j->t_admit = clk::now();
+                finish_locked(j, CRK_EINVAL, "service destroyed before the job was admitted");
+            }
+            ln->pending.clear();
         }
-        sv->pending.clear();
     }
-    sv->cv_work.notify_all();
-    if (sv->th.joinable()) sv->th.join();
+    for (auto &ln : sv->lanes) ln->cv_work.notify_all();
+    for (auto &ln : sv->lanes)
+        if (ln->th.joinable()) ln->th.join();
     sv->cv_done.notify_all();
-    cudaStreamSynchronize(sv->side);
-    crk_destroy(sv->sim);
-    cudaStreamDestroy(sv->st);
-    cudaStreamDestroy(sv->side);
-    cudaEventDestroy(sv->stepped);
+    for (auto &ln : sv->lanes) destroy_lane(*ln);
     delete sv;
     return CRK_OK;
 }
@@ -414,17 +504,17 @@ extern "C" int crk_service_cancel(crk_service *sv)
     if (!sv) return fail(CRK_EINVAL, "null argument");
     {
         std::lock_guard<std::mutex> lk(sv->mu);
-        for (auto &j : sv->pending) {
-            j->status = CRK_ECANCELED;
-            j->msg = "cancelled before admission";
-            j->t_admit = j->t_done = clk::now();
-            j->done = true;
+        for (auto &ln : sv->lanes) {
+            for (auto &j : ln->pending) {
+                j->t_admit = clk::now();
+                finish_locked(j, CRK_ECANCELED, "cancelled before admission");
+            }
+            ln->pending.clear();
+            for (auto &j : ln->slots)
+                if (j) j->cancel = true;
         }
-        sv->pending.clear();
-        for (auto &j : sv->slots)
-            if (j) j->cancel = true;
     }
-    sv->cv_work.notify_all();
+    for (auto &ln : sv->lanes) ln->cv_work.notify_all();
     sv->cv_done.notify_all();
     return CRK_OK;
 }

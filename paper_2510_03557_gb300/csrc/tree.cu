@@ -18,6 +18,7 @@ namespace {
 constexpr int kT = 256;            // threads per block for flat kernels
 constexpr int kItems = 16;         // items per thread in scan / sort tiles
 constexpr int kTile = kT * kItems; // 4096
+static_assert(kTile == kSortTile, "scratch sizing of the scan and sort tiles");
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
 
@@ -711,7 +712,7 @@ void launch_group_fill(const Leaves &lv, int nleaf, int gas_only, const uint32_t
     note_launches(1);
 }
 
-size_t scan_tmp_words(int64_t n) { return (size_t)((n + kTile - 1) / kTile) + 1; }
+size_t scan_tmp_words(int64_t n) { return scan_tmp_words_for(n); }
 
 void scan_exclusive_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *total,
                         uint32_t *tmp, cudaStream_t st)
@@ -727,7 +728,7 @@ void scan_exclusive_u32(const uint32_t *in, uint32_t *out, int64_t n, uint32_t *
     note_launches(3);
 }
 
-size_t radix_count_words(int64_t n) { return (size_t)256 * (size_t)((n + kTile - 1) / kTile); }
+size_t radix_count_words(int64_t n) { return radix_count_words_for(n); }
 
 void radix_sort_u64(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
                     int64_t n, uint32_t *counts, uint32_t *scan_tmp, int first_bit, int end_bit,

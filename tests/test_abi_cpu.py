@@ -49,7 +49,7 @@ def test_error_message_is_available_without_gpu(libcrk):
 
 STRUCTS = (("crk_physics", "Physics"), ("crk_params", "Params"), ("crk_outputs", "Outputs"),
            ("crk_timings", "Timings"), ("crk_service_params", "ServiceParams"), ("crk_job", "Job"),
-           ("crk_job_snapshot", "JobSnapshot"), ("crk_job_result", "JobResult"))
+           ("crk_job_snapshot", "JobSnapshot"), ("crk_job_result", "JobResult"), ("crk_tree", "Tree"))
 
 
 def test_struct_layouts_match_header(libcrk, tmp_path):
@@ -127,12 +127,15 @@ def test_null_arguments_are_rejected_without_a_device(libcrk):
     p = libcrk.params()
     assert L.crk_create(ctypes.byref(p), None, None) == libcrk.CRK_EINVAL
     assert L.crk_get_timings(None, None) == libcrk.CRK_EINVAL
+    assert L.crk_get_tree(None, None) == libcrk.CRK_EINVAL
     assert L.crk_destroy(None) == libcrk.CRK_OK
 
 
 @pytest.mark.parametrize("kw,word", [(dict(max_slots=0), "max_slots"), (dict(max_slots=70000), "max_slots"),
                                      (dict(hbm_budget_bytes=0), "hbm_budget_bytes"),
-                                     (dict(snapshot_every=-1), "snapshot_every")])
+                                     (dict(snapshot_every=-1), "snapshot_every"),
+                                     (dict(size_classes=-1), "size_classes"),
+                                     (dict(size_classes=9), "size_classes")])
 def test_service_create_rejects_bad_params_before_touching_the_device(libcrk, kw, word):
     args = dict(hbm_budget_bytes=1 << 30, max_slots=4)
     args.update(kw)

@@ -126,6 +126,34 @@ def test_neighbour_sets_match_independent_brute_force(oracle_lib, brute):
         assert np.array_equal(hs, exp_hash)
 
 
+@pytest.mark.parametrize("r_cut", [0.2, 0.25])
+def test_cell_list_finds_pairs_across_faces_of_whole_number_cells(oracle_lib, r_cut):
+    """box / support a whole number (5 and 4 cells of exactly the support):
+    pairs just inside the support straddling the cell faces on each axis are
+    found by the cell list as by brute force and by numpy."""
+    rng = np.random.default_rng(12)
+    pts = [rng.uniform(0, 1, size=(300, 3))]
+    k_max = int(round(1.0 / r_cut))
+    for k in range(1, k_max + 1):
+        for axis in range(3):
+            a = rng.uniform(0.05, 0.95, 3)
+            a[axis] = (r_cut * k - 1e-12) % 1.0
+            b = a.copy()
+            b[axis] = (a[axis] + r_cut - 3e-12) % 1.0
+            pts.append(np.stack([a, b]))
+    pos = np.concatenate(pts)
+    pos[pos >= 1.0] = 0.0
+    n = len(pos)
+    sp = np.ones(n, np.uint8)
+    h = np.full(n, 0.5 * r_cut)
+    sets = _numpy_brute_sets(pos, h, sp, 1.0, r_cut)
+    for brute in (False, True):
+        p = oracle_lib.make_params(box=1.0, r_cut=r_cut, brute=brute)
+        for kind in (0, 2):
+            cnt, _ = oracle_lib.neighbours(pos, h, sp, p, kind)
+            assert np.array_equal(cnt, sets[kind].sum(1).astype(np.int32)), (brute, kind)
+
+
 # --------------------------------------------------------------- density
 def test_lattice_density_equals_mean_density(oracle_lib):
     """On a perfect lattice the kernel estimate of the density equals the
