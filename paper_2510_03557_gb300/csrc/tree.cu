@@ -242,15 +242,60 @@ __device__ __forceinline__ bool cell_fits(const uint64_t *__restrict__ keys, int
     return !(lo + cap < n && (keys[lo + cap] >> s) == p);
 }
 
-// Leaves are octree cells: the coarsest Morton cell, at or below the box's
-// chaining-mesh bin, that holds at most cap particles of one (box, species).
-// Cells are found per particle by a binary search over the levels (a cell's
-// count only shrinks with depth).  Particles that share even the finest cell
-// are cut by count.  flags[k] = 1 where a leaf starts.  The keys are sorted
-// on their bits from first_bit up only, so levels whose cells need lower bits
-// are not used: a cell at the deepest sorted level that still holds more than
-// cap particles is cut by count.  stats[0] gets the deepest level used,
-// stats[1] is set when such a cut happened above levels that exist.
+// First index in [a, b) whose key prefix (key >> s) is >= p (keys sorted).
+__device__ __forceinline__ int64_t prefix_lower_bound(const uint64_t *__restrict__ keys, int64_t a, int64_t b,
+                                                      int s, uint64_t p)
+{
+    while (a < b) {
+        const int64_t mid = (a + b) >> 1;
+        if ((keys[mid] >> s) < p) a = mid + 1;
+        else b = mid;
+    }
+    return a;
+}
+
+// Leaf cells are packed with their siblings: the children of one octree
+// cell that is too large to be a leaf are taken in Morton order, and runs of
+// consecutive children that each fit (at most cap particles) are packed
+// greedily into leaves of at most cap particles; a child that does not fit
+// (it is cut into deeper leaves) ends a run.  True when the leaf cell of
+// particle k (its first particle, at shift s, parent at shift s + 3, cell
+// range [lo, hi)) starts a new leaf.  Every probe stays inside the parent's
+// range, which lies in [0, hi].
+__device__ bool starts_packed_leaf(const uint64_t *__restrict__ keys, int64_t lo, int64_t hi, uint64_t key, int s,
+                                   int cap)
+{
+    const uint64_t parent = key >> (s + 3);
+    const uint32_t own = (uint32_t)((key >> s) & 7u);
+    int64_t c0 = prefix_lower_bound(keys, 0, lo, s + 3, parent);   // the parent's first particle
+    uint32_t acc = 0;
+    bool start = true;
+    for (uint32_t c = 0; c <= own; ++c) {
+        const int64_t c1 = c == own ? hi : prefix_lower_bound(keys, c0, lo, s, (parent << 3) | (c + 1));
+        const uint32_t cnt = (uint32_t)(c1 - c0);
+        c0 = c1;
+        if (cnt == 0) continue;
+        if (cnt > (uint32_t)cap) {
+            acc = 0;
+            continue;
+        }
+        start = acc == 0 || acc + cnt > (uint32_t)cap;
+        acc = start ? cnt : acc + cnt;
+    }
+    return start;
+}
+
+// Leaves: the coarsest Morton cells, at or below the box's chaining-mesh
+// bin, that hold at most cap particles of one (box, species), packed with
+// their small siblings (starts_packed_leaf), so that leaves are compact runs
+// of Morton order that rarely fall far below cap.  Cells are found per
+// particle by a binary search over the levels (a cell's count only shrinks
+// with depth).  Particles that share even the finest cell are cut by count.
+// flags[k] = 1 where a leaf starts.  The keys are sorted on their bits from
+// first_bit up only, so levels whose cells need lower bits are not used: a
+// cell at the deepest sorted level that still holds more than cap particles
+// is cut by count.  stats[0] gets the deepest level used, stats[1] is set
+// when such a cut happened above levels that exist.
 __global__ void leaf_flags_k(const uint64_t *__restrict__ keys, int sb,
                              const BoxDev *__restrict__ boxes, int64_t n, int cap, uint32_t *flags,
                              int first_bit, uint32_t *stats)
@@ -271,9 +316,19 @@ __global__ void leaf_flags_k(const uint64_t *__restrict__ keys, int sb,
         else la = mid + 1;
     }
     if (la <= lmax) {
-        cell_fits(keys, n, k, key, s0 - 3 * la, cap, lo);
-        flags[k] = (k == lo) ? 1u : 0u;
-        if (k == lo) atomicMax(stats, (uint32_t)la);
+        const int s = s0 - 3 * la;
+        cell_fits(keys, n, k, key, s, cap, lo);
+        uint32_t f = 0u;
+        if (k == lo) {
+            atomicMax(stats, (uint32_t)la);
+            f = 1u;
+            if (la >= 1) {
+                // the cell's end: it holds at most cap particles
+                const int64_t hi = prefix_lower_bound(keys, k, k + cap < n ? k + cap + 1 : n, s, (key >> s) + 1);
+                f = starts_packed_leaf(keys, lo, hi, key, s, cap) ? 1u : 0u;
+            }
+        }
+        flags[k] = f;
     } else {
         if (k % cap == 0 && lmax < lall) atomicOr(stats + 1, 1u);
         const int s = s0 - 3 * lmax;

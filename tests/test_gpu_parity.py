@@ -252,10 +252,11 @@ def test_clustered_2x64_matches_oracle(crk, precision, nsphere):
         assert sets["grav"][0].max() > 20000     # the dense cores are really reached
 
 
-def _clustered_smooth_h(seed, n_gas=2500, n_dm=1500):
+def _clustered_smooth_h(seed, n_gas=2500, n_dm=1500, h0=0.09):
     """Half uniform, half in a Gaussian clump, species shuffled, gas h from a
-    smooth field 0.09 + 0.04 sin(5x) cos(3y) (so the uniform half's smallest
-    supports hold only a few neighbours: badly conditioned m2 there)."""
+    smooth field h0 + 0.04 sin(5x) cos(3y).  With h0 = 0.09 the uniform
+    half's smallest supports hold only a few neighbours, and some gas
+    particle's second-moment matrix is singular."""
     rng = np.random.default_rng(seed)
     g1 = rng.uniform(0, 1, size=(n_gas // 2, 3))
     g2 = (0.5 + 0.05 * rng.standard_normal((n_gas - n_gas // 2, 3))) % 1.0
@@ -268,18 +269,36 @@ def _clustered_smooth_h(seed, n_gas=2500, n_dm=1500):
     perm = rng.permutation(N)
     pos, sp = pos[perm], sp[perm]
     mass = np.where(sp == 1, 1.0 / n_gas, 2.0 / n_dm) * rng.uniform(0.8, 1.2, size=N)
-    h = np.where(sp == 1, 0.09 + 0.04 * np.sin(5.0 * pos[:, 0]) * np.cos(3.0 * pos[:, 1]), 0.0)
+    h = np.where(sp == 1, h0 + 0.04 * np.sin(5.0 * pos[:, 0]) * np.cos(3.0 * pos[:, 1]), 0.0)
     u = np.where(sp == 1, np.exp(rng.normal(0, 0.5, size=N)), 0.0)
     vel = 0.2 * rng.standard_normal((N, 3))
     return dict(pos=pos, vel=vel, mass=mass, u=u, h=h, species=sp)
 
 
+@pytest.mark.parametrize("seed", [53, 149])
+@pytest.mark.parametrize("leaf_cap", [32, 128])
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
+def test_smooth_field_h_singular_inputs_are_reported(crk, precision, leaf_cap, seed):
+    """The smooth-h inputs with h0 = 0.09 leave gas particles in the uniform
+    half with no or one neighbour, whose m2 is singular: the oracle reports
+    CRK_ESINGULAR, and so does each GPU form (never a NaN result)."""
+    s = _clustered_smooth_h(seed=seed)
+    phys = dict(box=1.0, G=1.0, gamma=5.0 / 3.0, r_cut=0.12, r_split=0.12 / 4.5, eps_soft=1e-3)
+    op = oracle.make_params(**phys)
+    ref = oracle.forces(s["pos"], s["vel"], s["mass"], s["u"], s["h"], s["species"], op)
+    assert ref["rc"] == crk.CRK_ESINGULAR
+    with pytest.raises(crk.CrkError) as e:
+        run_gpu(crk, s, crk.physics(**phys), precision, leaf_cap=leaf_cap)
+    assert e.value.code == crk.CRK_ESINGULAR
+
+
 @pytest.mark.parametrize("leaf_cap", [32, 64, 128])
 @pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "mixed"])
 def test_smooth_field_h_matches_oracle(crk, precision, leaf_cap):
-    """Smoothly varying h (not kNN h): gather sets from a handful of
-    neighbours in the uniform half to about a thousand in the clump."""
-    s = _clustered_smooth_h(seed=21 + leaf_cap)
+    """Smoothly varying h (not kNN h), raised to h0 = 0.12 so every m2 is
+    invertible: gather sets from about twenty neighbours in the uniform half
+    to about a thousand in the clump."""
+    s = _clustered_smooth_h(seed=21 + leaf_cap, h0=0.12)
     phys = dict(box=1.0, G=1.0, gamma=5.0 / 3.0, r_cut=0.12, r_split=0.12 / 4.5, eps_soft=1e-3)
     op = oracle.make_params(**phys)
     ref = oracle.forces(s["pos"], s["vel"], s["mass"], s["u"], s["h"], s["species"], op)
