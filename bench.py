@@ -3,9 +3,13 @@
 One step = one pass of the whole hot path on one batch of particles: first
 half kick and drift, Morton keys, radix sort, permutation, leaves, leaf
 hierarchy, leaf-pair lists, density, moments + corrections, hydro, gravity,
-second half kick.  Workload: the 2 x 128^3 Gaussian-random-field box
-(P(k) ~ k^-2, 0.3-cell rms displacement, ~270 gas neighbours), FP32-mixed
-form, inputs resident in HBM (about 2.5 GB of state, far larger than L2).
+second half kick.  Headline workload: the clustered 2 x 256^3 box (33.5 M
+particles; per species half uniform, half in 512 Plummer spheres of scale
+radius 0.002, adaptive h from the 32nd-nearest gas neighbour), FP32-mixed
+form, KDK at the box's Courant step, inputs resident in HBM (about 20 GB of
+state, far larger than L2).  Beside it on the same box: the plain FP64 form,
+the end-to-end rate through the C ABI with host buffers, the oracle on a
+sample, and the 2 x 128^3 Gaussian-field box as a secondary field.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -34,20 +38,22 @@ UNIT = "particles/s"
 
 # Algorithmic FP32 operations of one in-range pair, counted from the kernels'
 # pair bodies in csrc/passes.cu with the paper's convention (Sec. VI-B: FMA =
-# 2, add/mul = 1, sqrt/rsqrt/exp/reciprocal = 1).  Pairs outside the support
-# (leaf-pair overlap) are not counted.
+# 2, add/mul = 1, sqrt/rsqrt/exp/reciprocal = 1).  Units: density and moments
+# per ordered gather pair (self included: each target sums its own set, by
+# definition); hydro and gravity per UNORDERED pair (the method's force is
+# one evaluation per pair, F_ji = -F_ij; the gather kernels form it from both
+# sides, and that second evaluation is not counted as work).  Pairs outside
+# the support (leaf-pair overlap) are not counted either.
 FLOP_PER_PAIR = {"density": 22, "moments": 125, "hydro": 183, "gravity": 41}
-# GB300's FP64 rate (vector and tensor alike are far below its FP32 rate); a
-# nominal figure, the denominator of the plain FP64 form's algorithmic rates.
-FP64_NOMINAL_TFLOPS = 1.25
 
-# DRAM bytes (read + write) per particle of one launch of each pass, from the
-# one-pass ncu capture summarised in profiles/launches_gaussian_2x128.md
-# (2x128^3 Gaussian field, leaf capacity 128; density = list bounds + fill
-# with the density sum + kept counts).  They describe the kernels of the csrc/passes.cu with this
-# SHA-256 only; for any other source the bench reports no traffic.
-TRAFFIC_SOURCE_SHA256 = "695550b977dabc80776240b71028b5f1020dafab76880c791a1c4e7e33176915"
-TRAFFIC_BYTES_PER_PARTICLE = {"gravity": 81.3, "hydro": 701.4, "moments": 690.8, "density": 1088.2}
+# DRAM bytes (read + write) per particle of one launch of the gravity pass,
+# from an ncu capture of gravity_k on the clustered generator at 2 x 64^3
+# with 8 dense cores (32,768 particles per core, as in the 2 x 256^3 box),
+# leaf capacity 128, scaled to the launch by the particles it processes.  They
+# describe the kernels of the csrc/passes.cu with this SHA-256 only; for any
+# other source the bench reports no traffic.
+TRAFFIC_SOURCE_SHA256 = ""
+TRAFFIC_BYTES_PER_PARTICLE = {}
 
 
 def _traffic(kernel: str, particles: int, leaf_cap: int):
@@ -71,9 +77,23 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def fp32_peak_tflops(sm_mhz: float) -> float:
-    """152 SMs x 128 FP32 lanes x 2 flop (FMA) x SM clock."""
-    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+def fp32_peak_tflops(sm_mhz: float, sms: int = 152) -> float:
+    """SMs x 128 FP32 lanes x 2 flop (FMA) x SM clock (GB300: 152 SMs)."""
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+def algorithmic_pairs(counts, gas, list_entries=None):
+    """Pair counts of one force evaluation in the units of FLOP_PER_PAIR:
+    density and moments over ordered gather pairs with self, hydro over
+    unordered union pairs (r < max(2h_i, 2h_j); from the list entries of the
+    counted evaluation, which hold every target's union set and itself, else
+    from the gather sets, which equal the union sets when h is uniform),
+    gravity over unordered pairs within r_cut."""
+    n_gas = int(gas.sum())
+    gather = int(counts["nbr_count"][gas].sum())
+    union_ordered = (int(list_entries) - n_gas) if list_entries else gather
+    return {"density": gather + n_gas, "moments": gather + n_gas, "hydro": union_ordered // 2,
+            "gravity": int(counts["grav_count"].sum()) // 2}
 
 
 class ClockSampler:
@@ -132,99 +152,124 @@ class ClockSampler:
                 "samples": len(self.samples)}
 
 
-def cpu_baseline(n: int = 80):
-    """The CPU oracle as it stands, on a bounded sample of the same workload:
-    one force evaluation plus one KDK step of a 2 x n^3 box from the same
-    generator (same density, neighbour counts and h in spacing units)."""
+def oracle_sample(box, size: int, seed: int = 7):
+    """The CPU oracle as it stands on a bounded sample of a box: the forces of
+    `size` seeded random particles (both species in proportion), with every
+    quantity they depend on (the densities, moments and corrections of their
+    neighbours and of those neighbours' neighbours) evaluated too, over the
+    whole box's particles.  Returns the timing and the sampled outputs."""
     import oracle
-    from paper_2510_03557_gb300 import workloads as wl
 
     oracle.build()
-    box = wl.gaussian_field_box(n, seed=1)
+    rng = np.random.default_rng(seed)
+    idx = np.sort(rng.choice(box.n, size=min(size, box.n), replace=False))
     op = oracle.make_params(**box.params())
     t0 = time.perf_counter()
-    ref = oracle.forces(box.pos, box.vel, box.mass, box.u, box.h, box.species, op)
-    t1 = time.perf_counter()
-    oracle.kdk(box.pos, box.vel, box.mass, box.u, box.h, box.species, op, box.dt, 1,
-               acc=ref["acc"], dudt=ref["dudt"])
-    t2 = time.perf_counter()
-    step_s = t2 - t1  # one KDK step = one force evaluation plus kicks and drift
-    return {"value": box.n / step_s, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
-            "sample": f"one KDK step of a 2x{n}^3 box from the same generator (N={box.n}), "
-                      f"force evaluation {t1 - t0:.2f} s"}
+    ref = oracle.forces(box.pos, box.vel, box.mass, box.u, box.h, box.species, op, sample=idx)
+    secs = time.perf_counter() - t0
+    return idx, ref, secs
 
 
-def serve_bench(crk, wl, args, stream):
-    """The serving workload on a bounded sample: the first ``count`` requests
-    of the 2,000-request stream (n log-uniform in [16, 128], 20 KDK steps at
-    dt = 1e-3, FP32-mixed, 150 GB budget).  A closed-loop calibration batch
-    fixes the saturated throughput; Poisson arrivals are then issued at 70% of
-    it and the service reports each request's submit-to-completion latency.
-    Beside it, sequential plain-FP64 solves (one handle per request, one box
-    per launch) of a few of the same requests give the FP64 rate."""
+def cpu_baseline(box, size: int, label: str):
+    """particles/s of the oracle on a sample of the box (sampled particles
+    over the time of their force evaluation, which is the bulk of a step);
+    also returns the oracle's sampled outputs for the parity check."""
+    import oracle
+
+    idx, ref, secs = oracle_sample(box, size)
+    return ({"value": len(idx) / secs, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+             "sample": f"forces of {len(idx)} seeded random particles of the {label} box with everything "
+                       f"they depend on (neighbour densities, moments, corrections), {secs:.1f} s"},
+            idx, ref)
+
+
+def serve_bench(crk, wl, args):
+    """The serving workload: the first `count` requests of the 2,000-request
+    stream (n log-uniform in [16, 128], 20 KDK steps at dt = 1e-3, FP32-mixed,
+    150 GB budget, size classes of the service).  A closed-loop calibration
+    batch fixes the saturated throughput; Poisson arrivals are then issued at
+    70% of it and the service reports each request's submit-to-completion
+    latency.  Request boxes are generated on host threads ahead of their
+    arrival (the stream holds ~1.3 G particles in all, too many to generate
+    up front).  Submission stops once --serve-seconds have passed; the line
+    says how many requests ran.  Beside it, sequential plain-FP64 solves (one
+    handle per request, one box per launch, the same 20 KDK steps) of a few of
+    the requests give the FP64 rate."""
     import concurrent.futures as cf
 
     count = args.serve_requests
     reqs = wl.serving_requests(2000)[:count]
-    with cf.ThreadPoolExecutor(8) as ex:
-        boxes = list(ex.map(lambda r: wl.gaussian_field_box(r[0], seed=r[1]), reqs))
     steps = 20
     svc = crk.crk_service_create(150 * 10**9, max_slots=64, precision=crk.CRK_MIXED,
                                  leaf_cap=args.serve_leaf_cap)
+    gen = lambda r: wl.gaussian_field_box(r[0], seed=r[1])
+    ex = cf.ThreadPoolExecutor(12)
 
     def submit(b):
         return crk.crk_submit(svc, crk.box_physics(b), b.pos, b.vel, b.mass, b.u, b.h, b.species,
                               b.dt, steps)
 
-    def collect(tickets, bs):
-        return [crk.crk_poll(svc, t, b.n, -1) for t, b in zip(tickets, bs)]
-
     try:
-        # calibration: a closed batch, everything submitted at once
-        calib = boxes[:min(32, count)]
+        # calibration: a closed batch of the first requests, all submitted at once
+        ncal = min(32, count)
+        calib = list(ex.map(gen, reqs[:ncal]))
         t0 = time.perf_counter()
-        collect([submit(b) for b in calib], calib)
+        tk = [submit(b) for b in calib]
+        for t, b in zip(tk, calib):
+            crk.crk_poll(svc, t, b.n, -1)
         t_cal = time.perf_counter() - t0
-        capacity = len(calib) / t_cal                       # requests/s when saturated
+        capacity = ncal / t_cal                       # requests/s when saturated
         rate = 0.7 * capacity
         arrivals = wl.poisson_arrivals(count, rate, seed=5)
-        tickets = []
+        futs = [ex.submit(gen, r) for r in reqs]      # generated in order, ahead of arrival
+        tickets, sizes, late = [], [], 0
         t0 = time.perf_counter()
-        for a, b in zip(arrivals, boxes):
+        for a, f in zip(arrivals, futs):
+            if time.perf_counter() - t0 > args.serve_seconds:
+                break
             while time.perf_counter() - t0 < a:
                 time.sleep(min(1e-3, max(0.0, a - (time.perf_counter() - t0))))
+            b = f.result()
+            late += (time.perf_counter() - t0) > a + 0.05
             tickets.append(submit(b))
-        res = collect(tickets, boxes)
+            sizes.append(b.n)
+        for f in futs[len(tickets):]:
+            f.cancel()
+        res = [crk.crk_poll(svc, t, n, -1) for t, n in zip(tickets, sizes)]
         wall = time.perf_counter() - t0
     finally:
         crk.crk_service_destroy(svc)
+        ex.shutdown(wait=True, cancel_futures=True)
     lat = np.array([r["latency_ns"] for r in res]) / 1e6
     que = np.array([r["queue_ns"] for r in res]) / 1e6
-    psteps = sum(b.n for b in boxes) * steps
+    psteps = sum(sizes) * steps
 
-    # sequential plain FP64: one request at a time, 2 steps each, on a few requests
-    seq = boxes[:min(6, count)]
+    # sequential plain FP64, one request at a time, the same 20 KDK steps
+    seq = [gen(r) for r in reqs[:min(args.serve_fp64, count)]]
     t64 = 0.0
     p64 = 0
     for b in seq:
-        s = crk.Sim(crk.box_physics(b), leaf_cap=args.leaf_cap, precision=crk.CRK_FP64, stream=stream)
+        s = crk.Sim(crk.box_physics(b), leaf_cap=64, precision=crk.CRK_FP64)
         s.load(b)
-        stream.synchronize()
         t1 = time.perf_counter()
-        s.step(b.dt, 2)
-        stream.synchronize()
+        s.step(b.dt, steps)
+        s.state()
         t64 += time.perf_counter() - t1
-        p64 += b.n * 2
+        p64 += b.n * steps
         s.close()
-    return {"requests": count, "of": 2000, "steps_per_request": steps,
+    small = np.array(sizes) < 65536
+    return {"requests": len(res), "of": 2000, "steps_per_request": steps,
             "p50_ms": round(float(np.percentile(lat, 50)), 3),
             "p99_ms": round(float(np.percentile(lat, 99)), 3),
+            "p99_over_p50": round(float(np.percentile(lat, 99) / np.percentile(lat, 50)), 3),
+            "p50_ms_small_jobs": round(float(np.percentile(lat[small], 50)), 3) if small.any() else None,
             "queue_p50_ms": round(float(np.percentile(que, 50)), 3),
-            "value": psteps / wall, "unit": UNIT,
-            "arrival_rate_per_s": round(rate, 3), "load": 0.7,
-            "calibration": {"requests": len(calib), "seconds": round(t_cal, 3)},
-            "fp64_sequential": {"value": p64 / t64, "unit": UNIT, "requests": len(seq),
-                                "steps_per_request": 2}}
+            "value": psteps / wall, "unit": UNIT, "wall_s": round(wall, 2),
+            "arrival_rate_per_s": round(rate, 3), "load": 0.7, "late_submissions": int(late),
+            "calibration": {"requests": ncal, "seconds": round(t_cal, 3)},
+            "size_classes": "3 (below 65,536 particles; below 524,288; the rest)",
+            "fp64_sequential": {"value": p64 / t64 if t64 else None, "unit": UNIT, "requests": len(seq),
+                                "steps_per_request": steps}}
 
 
 def _rel_l2(x, ref):
@@ -299,9 +344,9 @@ def run_bins(args):
     print(json.dumps(line))
 
 
-def fp64_pass_rates(tim, pairs):
-    """Per-phase times of the timed FP64 steps and each pair pass's
-    algorithmic rate, also as a share of the nominal FP64 rate."""
+def fp64_pass_rates(tim, pairs, peak_tflops: float, peak_source: str):
+    """Per-phase times of the timed FP64 evaluations and each pair pass's
+    algorithmic rate, also as a share of the measured FP64 FMA rate."""
     calls = max(tim["calls"], 1)
     rates = {k: pairs[k] * FLOP_PER_PAIR[k] / (tim[k + "_ms"] / calls / 1e3) / 1e12
              for k in ("density", "moments", "hydro", "gravity") if tim[k + "_ms"] > 0}
@@ -309,32 +354,32 @@ def fp64_pass_rates(tim, pairs):
                              ("tree_ms", "pairs_ms", "density_ms", "moments_ms", "hydro_ms",
                               "gravity_ms", "kdk_ms")},
             "pass_tflops": {k: round(v, 4) for k, v in rates.items()},
-            "pass_of_fp64_peak": {k: round(v / FP64_NOMINAL_TFLOPS, 4) for k, v in rates.items()},
-            "fp64_peak": {"value": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                          "source": "nominal GB300 FP64 rate, not measured"}}
+            "pass_of_fp64_peak": {k: round(v / peak_tflops, 4) for k, v in rates.items()},
+            "fp64_peak": {"value": round(peak_tflops, 4), "unit": "TFLOP/s", "source": peak_source}}
 
 
-def pair_census(tim, pairs, n_gas, n):
+def pair_census(tim, gather_pairs: int, grav_ordered: int, n: int):
     """Evaluated / algorithmic pairs of the counted evaluation: candidate
     tests in lane slots (a warp tests its up to 32 targets against every staged
-    candidate) per in-range pair, the hydro list entries per gather pair, and
-    the share of walked list slots that hold an entry."""
-    gather = pairs["density"]                 # ordered gather pairs, self included
-    grav = pairs["gravity"] + n               # each target is also tested against itself
+    candidate) per in-range ordered pair, the hydro list entries per gather
+    pair (self included), and the share of walked list slots that hold an
+    entry."""
+    grav = grav_ordered + n                   # each target is also tested against itself
     r = lambda a, b: round(a / b, 3) if b else None
     return {"gravity": {"tested_slots": tim["tests_grav"], "target_slots": tim["tests_grav_target"],
                         "in_range": grav, "tested_per_in_range": r(tim["tests_grav"], grav),
                         "target_slots_per_in_range": r(tim["tests_grav_target"], grav)},
             "hydro_fill": {"tested_slots": tim["tests_hydro"], "list_entries": tim["list_entries"],
-                           "gather_pairs": gather, "tested_per_entry": r(tim["tests_hydro"], tim["list_entries"]),
-                           "entries_per_gather_pair": r(tim["list_entries"], gather)},
+                           "gather_pairs": gather_pairs,
+                           "tested_per_entry": r(tim["tests_hydro"], tim["list_entries"]),
+                           "entries_per_gather_pair": r(tim["list_entries"], gather_pairs)},
             "list_walk": {"slots": tim["list_slots"], "entries": tim["list_entries"],
                           "entry_share": r(tim["list_entries"], tim["list_slots"])},
-            "note": "lane slots of one counted force evaluation; in-range gravity pairs include each "
-                    "target's self test"}
+            "note": "lane slots of one counted force evaluation; in-range gravity pairs are ordered and "
+                    "include each target's self test"}
 
 
-def run_clustered(args):
+def run_precision(args):
     """Precision study on the clustered workload (2 x n^3, half uniform and
     half in 512 Plummer spheres, adaptive h): one force evaluation plus 5 KDK
     steps in the plain FP64 form and the FP32-mixed form, the mixed form's
@@ -407,9 +452,9 @@ def run_clustered(args):
                                  "linking_length": 0.2 / args.n, "species": "dm",
                                  "note": "host wall time of crk_fof: tree build, links, labels, copy-out"}
             cnt = s.forces(counts=True)
-            pc = {"density": int(cnt["nbr_count"][gas].sum()) + int(gas.sum()),
-                  "gravity": int(cnt["grav_count"].sum())}
-            runs[name]["census"] = pair_census(crk.crk_get_timings(s.handle), pc, int(gas.sum()), box.n)
+            runs[name]["census"] = pair_census(crk.crk_get_timings(s.handle),
+                                               int(cnt["nbr_count"][gas].sum()) + int(gas.sum()),
+                                               int(cnt["grav_count"].sum()), box.n)
         s.close()
     a, b = runs["mixed"], runs["fp64"]
     err = {"acc": _rel_l2(a["out"]["acc"], b["out"]["acc"]),
@@ -539,34 +584,127 @@ def run_batched(args):
 
 
 def headline_config(args, world: int) -> dict:
-    """The headline workload's config: the 2 x n^3 Gaussian-field box of the
-    generator (dt 1e-3), as both arms report it."""
+    """The headline workload's config, as both arms report it: the clustered
+    2 x n^3 box of the generator (seed 3), KDK at the box's Courant step."""
     n = 2 * args.n ** 3
-    return {"workload": f"gaussian-field 2x{args.n}^3, FP32-mixed, KDK dt=0.001",
+    return {"workload": f"clustered 2x{args.n}^3 (half uniform, half in 512 Plummer spheres of scale 0.002, "
+                        f"kNN h), FP32-mixed, KDK steps at the box's Courant dt",
             "particles": n, "leaf_cap": args.leaf_cap, "rebuild_every": args.rebuild_every,
             "parallelism": f"replicas{world}",
             "l2": f"inputs larger than L2 (~{n * 600 / 1e9:.1f} GB resident state)"}
 
 
 def run_reference(args):
+    """The reference arm: the oracle as it stands, on the host cores, on a
+    bounded sample of the headline workload each step (the forces of
+    --cpu-sample seeded random particles of the same box with everything they
+    depend on), on the headline's config, metric and unit.  Under torchrun
+    only rank 0 runs; the other ranks exit without work."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    from paper_2510_03557_gb300 import workloads as wl
+
+    box = wl.clustered_box(args.n, seed=3)
+    label = f"clustered 2x{args.n}^3"
     steps = []
     cb = None
     for _ in range(args.warmup):
-        cpu_baseline(40)
+        cpu_baseline(box, args.cpu_sample, label)
     for _ in range(args.steps):
-        cb = cpu_baseline(40)
+        cb, _, _ = cpu_baseline(box, args.cpu_sample, label)
         steps.append(cb["value"])
-    value = statistics.median(steps)
+    value = statistics.median(steps) if steps else 0.0
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": headline_config(args, args.gpus),
-            "cpu_baseline": dict(cb, value=value),
+            "cpu_baseline": dict(cb or {}, value=value),
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def run_gaussian(crk, wl, args, stream, timed_steps: int):
+    """The 2 x 128^3 Gaussian-field box (P(k) ~ k^-2, 0.3-cell rms
+    displacement, ~270 gas neighbours), the same mixed KDK steps: a
+    secondary field of the headline line (and, with --workload gaussian, a
+    line of its own)."""
+    import torch
+
+    box = wl.gaussian_field_box(args.gauss_n, seed=1)
+    gas = box.species == wl.GAS
+    sim = crk.Sim(crk.box_physics(box), leaf_cap=args.leaf_cap, precision=crk.CRK_MIXED, stream=stream,
+                  rebuild_every=args.rebuild_every)
+    sim.load(box)
+    counts = sim.forces(counts=True)
+    tim0 = crk.crk_get_timings(sim.handle)
+    pairs = algorithmic_pairs(counts, gas, tim0["list_entries"])
+    for _ in range(3):
+        sim.step(box.dt, 1)
+    crk.crk_set_timing(sim.handle, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sim.step(box.dt, timed_steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / timed_steps
+    tim = crk.crk_get_timings(sim.handle)
+    calls = max(tim["calls"], 1)
+    out = {"workload": f"gaussian-field 2x{args.gauss_n}^3, FP32-mixed, KDK dt={box.dt}", "particles": box.n,
+           "value": box.n / (ms / 1e3), "unit": UNIT, "ms_per_step": round(ms, 4), "steps": timed_steps,
+           "breakdown_ms": {k: round(tim[k] / calls, 4) for k in
+                            ("tree_ms", "pairs_ms", "density_ms", "moments_ms", "hydro_ms", "gravity_ms",
+                             "kdk_ms")},
+           "pass_tflops": {k: round(pairs[k] * FLOP_PER_PAIR[k] / (tim[k + "_ms"] / calls / 1e3) / 1e12, 3)
+                           for k in ("density", "moments", "hydro", "gravity")},
+           "pairs_per_step": pairs,
+           "pair_census": pair_census(tim0, pairs["density"], int(counts["grav_count"].sum()), box.n),
+           "leaves": int(tim["nleaves"])}
+    fof = None
+    if not args.no_extras:
+        torch.cuda.synchronize()
+        t_f = time.perf_counter()
+        _, n_groups = crk.crk_fof(sim.handle, 0.2 / args.gauss_n, 1, box.n)
+        fof = {"ms": round((time.perf_counter() - t_f) * 1e3, 3), "groups": n_groups,
+               "linking_length": 0.2 / args.gauss_n, "species": "dm",
+               "note": "host wall time of crk_fof: tree build, links, labels, copy-out"}
+    sim.close()
+    mesh = None
+    if not args.no_extras:
+        # the same KDK step with the long-range mesh (FP64 PM, n^3 cells)
+        smesh = crk.Sim(crk.box_physics(box), leaf_cap=args.leaf_cap, precision=crk.CRK_MIXED, stream=stream,
+                        rebuild_every=args.rebuild_every, pm_grid=args.gauss_n)
+        smesh.load(box)
+        smesh.step(box.dt, 2)
+        crk.crk_set_timing(smesh.handle, True)
+        smesh.step(box.dt, 3)
+        tmesh = crk.crk_get_timings(smesh.handle)
+        mcalls = max(tmesh["calls"], 1)
+        mesh = {"pm_grid": args.gauss_n, "pm_ms": round(tmesh["pm_ms"] / mcalls, 4),
+                "step_ms": round(tmesh["total_ms"] / mcalls, 4),
+                "note": "per KDK step, CUDA events on the handle's stream: deposit, cuFFT forward, "
+                        "Green's function, 3 cuFFT inverse, gather (FP64)"}
+        smesh.close()
+    out["fof"] = fof
+    out["long_range_mesh"] = mesh
+    return out
+
+
+def parity_on_sample(out, ref, idx, gas):
+    """Relative L2 and the worst particle's relative error of a GPU form's
+    outputs against the oracle on the sampled particles."""
+    gi = idx[gas[idx]]
+    res = {}
+    for k, ok, sel in (("acc", "acc", idx), ("dudt", "dudt", gi), ("rho", "rho", gi), ("A", "A", gi),
+                       ("B", "B", gi), ("gradA", "dA", gi), ("gradB", "dB", gi)):
+        a = np.asarray(out[k][sel], np.float64).reshape(len(sel), -1)
+        b = np.asarray(ref[ok][sel], np.float64).reshape(len(sel), -1)
+        nb = np.linalg.norm(b, axis=1)
+        floor = 1e-6 * float(np.sqrt(np.mean(nb * nb))) if len(nb) else 0.0
+        per = np.linalg.norm(a - b, axis=1) / np.maximum(nb + floor, 1e-300)
+        res[k] = {"rel_l2": _rel_l2(a, b), "worst_particle": float(per.max()) if len(per) else 0.0}
+    return res
 
 
 def main():
@@ -575,31 +713,42 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="headline",
+                    choices=["headline", "gaussian", "precision", "batched", "bins"],
+                    help="headline: the clustered 2 x n^3 line; gaussian: the 2 x 128^3 box alone; "
+                         "precision: FP64 and mixed KDK on the clustered box with per-output errors; "
+                         "batched: 64 boxes in one handle; bins: hierarchical steps (each prints its own line)")
     ap.add_argument("--bin-depth", type=int, default=5, help="bins workload: substeps 2^depth")
     ap.add_argument("--bin-eta", type=float, default=0.025)
     ap.add_argument("--bin-courant", type=float, default=0.25)
-    ap.add_argument("--workload", default="gaussian", choices=["gaussian", "clustered", "batched", "bins"],
-                    help="clustered: the precision study; batched: 64 boxes in one handle "
-                         "(each prints its own JSON line)")
     ap.add_argument("--sample", type=int, default=64, help="oracle sample of the precision study")
-    ap.add_argument("--n", type=int, default=128, help="lattice size per species (2 n^3 particles)")
+    ap.add_argument("--n", type=int, default=256, help="clustered box: lattice size per species (2 n^3)")
+    ap.add_argument("--gauss-n", type=int, default=128, help="Gaussian-field box: 2 n^3 particles")
     ap.add_argument("--leaf-cap", type=int, default=128)
     ap.add_argument("--rebuild-every", type=int, default=1,
                     help="sort into new leaves every this many steps (boxes grow in between)")
+    ap.add_argument("--fp64-evals", type=int, default=1,
+                    help="timed FP64 force evaluations on the headline box (0: skip the FP64 form)")
     ap.add_argument("--fp64-steps", type=int, default=2,
-                    help="KDK steps of the FP64 form (precision study: -1 = as many as the mixed form)")
+                    help="precision workload: KDK steps of the FP64 form (-1 = as many as the mixed form)")
+    ap.add_argument("--cpu-sample", type=int, default=4096,
+                    help="particles of the oracle's sample (cpu_baseline and the reference arm)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-gaussian", action="store_true", help="skip the 2 x 128^3 secondary field")
     ap.add_argument("--no-extras", action="store_true", help="skip the FOF and long-range mesh legs")
-    ap.add_argument("--serve-requests", type=int, default=192,
+    ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests of the serving stream to run (0: skip)")
+    ap.add_argument("--serve-seconds", type=float, default=240.0,
+                    help="stop submitting serving requests after this many seconds")
+    ap.add_argument("--serve-fp64", type=int, default=4, help="requests solved one by one in plain FP64")
     ap.add_argument("--serve-leaf-cap", type=int, default=64)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
         return
-    if args.workload == "clustered":
-        run_clustered(args)
+    if args.workload == "precision":
+        run_precision(args)
         return
     if args.workload == "batched":
         run_batched(args)
@@ -633,23 +782,42 @@ def main():
         return replicas.max_over_ranks(v, dist, "cuda")
 
     crk.lib()
-    box = wl.gaussian_field_box(args.n, seed=1)
+    stream = torch.cuda.Stream()
+    if args.workload == "gaussian":
+        g = run_gaussian(crk, wl, args, stream, args.steps)
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": g["value"], "unit": UNIT, "n_gpus": world,
+                              "steps": args.steps, "ms_per_step": g["ms_per_step"], "higher_is_better": True,
+                              "dtype": "f32", "data": "synthetic", "config": {"workload": g["workload"]},
+                              "gaussian": g}))
+        return
+
+    legs = {}
+    t_leg = time.perf_counter()
+
+    def leg(name):
+        nonlocal t_leg
+        now = time.perf_counter()
+        legs[name] = round(now - t_leg, 1)
+        t_leg = now
+
+    box = wl.clustered_box(args.n, seed=3)
+    leg("setup")
+    t_gen = legs["setup"]
     N = box.n
     dt = box.dt
     phys = crk.box_physics(box)
-    stream = torch.cuda.Stream()
+    gas = box.species == wl.GAS
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
 
     # ---------------- mixed form, device-resident (the headline value)
     sim = crk.Sim(phys, leaf_cap=args.leaf_cap, precision=crk.CRK_MIXED, stream=stream,
                   rebuild_every=args.rebuild_every)
     sim.load(box)
     counts = sim.forces(counts=True)      # untimed: the true pair counts for the roofline
-    gas = box.species == wl.GAS
-    pairs = {"density": int(counts["nbr_count"][gas].sum()) + int(gas.sum()),
-             "moments": int(counts["nbr_count"][gas].sum()) + int(gas.sum()),
-             "hydro": int(counts["nbr_count"][gas].sum()),
-             "gravity": int(counts["grav_count"].sum())}
-    census = pair_census(crk.crk_get_timings(sim.handle), pairs, int(gas.sum()), N)
+    tim0 = crk.crk_get_timings(sim.handle)
+    pairs = algorithmic_pairs(counts, gas, tim0["list_entries"])
+    census = pair_census(tim0, pairs["density"], int(counts["grav_count"].sum()), N)
     for _ in range(args.warmup):
         sim.step(dt, 1)
     crk.crk_set_timing(sim.handle, True)
@@ -673,7 +841,9 @@ def main():
     clk = clocks.summary()
     peaks, peak_kind = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = fp32_peak_tflops(sm_max)
+    peak = fp32_peak_tflops(sm_max, sms)
+    fma32 = crk.crk_fma_peak(crk.CRK_MIXED, stream)
+    fma64 = crk.crk_fma_peak(crk.CRK_FP64, stream)
     achieved = pairs[dom] * FLOP_PER_PAIR[dom] / (dom_ms / 1e3) / 1e12
     pass_tflops = {k: pairs[k] * FLOP_PER_PAIR[k] / (per_pass_ms[k] / calls / 1e3) / 1e12
                    for k in per_pass_ms}
@@ -683,54 +853,55 @@ def main():
                   ("hydro_ms", tim["hydro_ms"]), ("gravity_ms", tim["gravity_ms"]),
                   ("kdk_ms", tim["kdk_ms"]))}
     launches = int(tim["launches"])
-    fof = mesh = None
+    fof = None
     if not args.no_extras:
-        # friends-of-friends groups of the dark matter at b = 0.2 mean spacings
-        # (the call sorts a new tree for the current state, then links)
+        # friends-of-friends halos of the dark matter at b = 0.2 mean spacings
+        # on the clustered state after the steps (a new tree, then links)
         torch.cuda.synchronize()
         t_f = time.perf_counter()
-        _, n_groups = crk.crk_fof(sim.handle, 0.2 / args.n, 1, N)
+        grp, n_groups = crk.crk_fof(sim.handle, 0.2 / args.n, 1, N)
+        _, sizes = np.unique(grp[grp >= 0], return_counts=True)
         fof = {"ms": round((time.perf_counter() - t_f) * 1e3, 3), "groups": n_groups,
+               "groups_20_or_more": int(np.sum(sizes >= 20)), "largest": int(sizes.max()) if len(sizes) else 0,
                "linking_length": 0.2 / args.n, "species": "dm",
                "note": "host wall time of crk_fof: tree build, links, labels, copy-out"}
     sim.close()
+    leg("mixed")
 
-    if not args.no_extras:
-        # the same KDK step with the long-range mesh (FP64 PM, n^3 cells)
-        smesh = crk.Sim(phys, leaf_cap=args.leaf_cap, precision=crk.CRK_MIXED, stream=stream,
-                        rebuild_every=args.rebuild_every, pm_grid=args.n)
-        smesh.load(box)
-        smesh.step(dt, 2)
-        crk.crk_set_timing(smesh.handle, True)
-        smesh.step(dt, 3)
-        tmesh = crk.crk_get_timings(smesh.handle)
-        mcalls = max(tmesh["calls"], 1)
-        mesh = {"pm_grid": args.n, "pm_ms": round(tmesh["pm_ms"] / mcalls, 4),
-                "step_ms": round(tmesh["total_ms"] / mcalls, 4),
-                "note": "per KDK step, CUDA events on the handle's stream: deposit, cuFFT forward, "
-                        "Green's function, 3 cuFFT inverse, gather (FP64)"}
-        smesh.close()
-
-    # ---------------- FP64 plain form on the same box
+    # ---------------- FP64 plain form on the same box, the same state
     fp64 = None
-    if args.fp64_steps > 0:
+    out64 = None
+    if args.fp64_evals > 0:
         s64 = crk.Sim(phys, leaf_cap=args.leaf_cap, precision=crk.CRK_FP64, stream=stream)
         s64.load(box)
-        s64.step(dt, 1)
         crk.crk_set_timing(s64.handle, True)
         barrier()
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
         f0.record(stream)
-        s64.step(dt, args.fp64_steps)
+        for _ in range(args.fp64_evals):
+            out64 = s64.forces(counts=False)
         f1.record(stream)
         torch.cuda.synchronize()
-        t64 = max_over_ranks(f0.elapsed_time(f1))
-        fp64 = {"value": world * N * args.fp64_steps / (t64 / 1e3), "unit": UNIT,
-                "ms_per_step": t64 / args.fp64_steps, "steps": args.fp64_steps, "dtype": "f64"}
-        # the same pair sets as the mixed form (both decide them in FP64)
-        fp64.update(fp64_pass_rates(crk.crk_get_timings(s64.handle), pairs))
+        t64 = max_over_ranks(f0.elapsed_time(f1)) / args.fp64_evals   # includes the copy-out
+        tim64 = crk.crk_get_timings(s64.handle)
+        dev64 = tim64["total_ms"] / max(tim64["calls"], 1)
+        fp64 = {"value": world * N / (dev64 / 1e3), "unit": UNIT, "ms_per_force_evaluation": round(dev64, 2),
+                "wall_ms_with_copy_out": round(t64, 2), "evaluations": args.fp64_evals, "dtype": "f64",
+                "rate_from": "device time of a force evaluation (tree, lists, D, M, C, H, G); a KDK step adds "
+                             "only its FP64 kicks and drift (kdk_ms of the mixed form)",
+                "mixed_over_fp64": round(value / (world * N / (dev64 / 1e3)), 2)}
+        fp64.update(fp64_pass_rates(tim64, pairs, fma64, "crk_fma_peak: FP64 FMA chains on this device"))
         s64.close()
+        leg("fp64")
+    precision = None
+    if out64 is not None:
+        # the mixed form against the FP64 form at the loaded state (both forms'
+        # first force evaluation), relative L2 per output over every particle
+        precision = {k: _rel_l2(counts[k][sel], out64[k][sel]) for k, sel in
+                     (("acc", slice(None)), ("dudt", gas), ("rho", gas), ("A", gas), ("B", gas),
+                      ("gradA", gas), ("gradB", gas))}
+        del out64
 
     # ---------------- end to end through the public API with host buffers
     e2e = None
@@ -741,7 +912,7 @@ def main():
         pin = lambda shape: torch.empty(shape, dtype=torch.float64).pin_memory().numpy()
         hp, hv, hu = pin((N, 3)), pin((N, 3)), pin(N)
         crk.crk_get_state(se.handle, hp, hv, hu)
-        k_e2e = max(2, min(args.steps, 5))
+        k_e2e = max(2, min(args.steps, 3))
         barrier()
         t0 = time.perf_counter()
         g0 = torch.cuda.Event(enable_timing=True)
@@ -759,14 +930,26 @@ def main():
                "h2d_bytes_per_step": int(hp.nbytes + hv.nbytes + hu.nbytes),
                "d2h_bytes_per_step": int(hp.nbytes + hv.nbytes + hu.nbytes), "steps": k_e2e}
         se.close()
+        del hp, hv, hu
+        leg("e2e")
+
+    gaussian = None
+    if not args.no_gaussian:
+        gaussian = run_gaussian(crk, wl, args, stream, max(2, min(args.steps, 10)))
+        leg("gaussian")
 
     serving = None
     if args.serve_requests > 0:
-        serving = serve_bench(crk, wl, args, stream)
+        serving = serve_bench(crk, wl, args)
+        leg("serving")
 
     cb = None
+    sample_parity = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cb = cpu_baseline()
+        cb, idx, ref = cpu_baseline(box, args.cpu_sample, f"clustered 2x{args.n}^3")
+        sample_parity = {"particles": int(len(idx)), "mixed": parity_on_sample(counts, ref, idx, gas),
+                         "oracle_rc": int(ref["rc"])}
+        leg("cpu_baseline")
 
     if rank == 0:
         line = {
@@ -778,25 +961,34 @@ def main():
             "roofline": {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3),
                          "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
                          "traffic": _traffic(dom, N, args.leaf_cap),
-                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, "
-                                           "2x128^3 capture (profiles/launches_gaussian_2x128.md), "
-                                           "scaled by particles",
-                         "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
-                                        f"({peak_kind} sm_max_mhz)"},
+                         "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on "
+                                           "the clustered generator at 2x64^3 with 8 dense cores, scaled by "
+                                           "particles (null when the kernel source differs from the captured one)",
+                         "work": f"{FLOP_PER_PAIR[dom]} flop per "
+                                 f"{'unordered' if dom in ('hydro', 'gravity') else 'ordered'} in-range pair",
+                         "peak_source": f"{sms} SMs (device query) x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
+                                        f"({peak_kind} sm_max_mhz)",
+                         "fma_probe_tflops": {"fp32": round(fma32, 3), "fp64": round(fma64, 4)}},
             "pass_tflops": {k: round(v, 3) for k, v in pass_tflops.items()},
+            "pass_of_fp32_peak": {k: round(v / peak, 4) for k, v in pass_tflops.items()},
             "pairs_per_step": pairs,
             "pair_census": census,
             "leaves": int(tim["nleaves"]), "leaf_pairs": {"hydro": int(tim["pairs_hydro"]),
                                                           "gravity": int(tim["pairs_grav"])},
             "breakdown_ms": breakdown,
+            "dt": dt,
+            "setup_s": round(t_gen, 1),
             "fp64_plain": fp64,
+            "mixed_vs_fp64_rel_l2": precision,
+            "oracle_sample_parity": sample_parity,
             "fof": fof,
-            "long_range_mesh": mesh,
+            "gaussian_2x128": gaussian,
             "serving": serving,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk,
             "cpu_baseline": cb,
+            "leg_wall_s": legs,
         }
         print(json.dumps(line))
     if dist is not None:

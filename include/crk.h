@@ -324,6 +324,15 @@ typedef struct {
 } crk_tree;
 int crk_get_tree(crk_sim *sim, crk_tree *out);
 
+/* Measured fused-multiply-add throughput of the current device, the
+ * denominator of the pair passes' roofline fractions: precision CRK_MIXED
+ * times FP32 FMA chains, CRK_FP64 FP64 FMA chains (8 independent chains per
+ * thread, every SM filled with resident blocks, a warm-up launch, then 3
+ * launches timed with CUDA events on cuda_stream, a cudaStream_t or NULL);
+ * *tflops = 2 flop per FMA / time, in TFLOP/s.  Synchronises the stream.
+ * Errors: CRK_EINVAL (bad precision, null tflops), CRK_ECUDA. */
+int crk_fma_peak(int precision, double *tflops, void *cuda_stream);
+
 /* Turns per-phase CUDA-event timing on (1) or off (0) and resets it. */
 int crk_set_timing(crk_sim *sim, int enable);
 int crk_get_timings(crk_sim *sim, crk_timings *out);

@@ -17,7 +17,8 @@ LIB = os.path.join(OUT, "libcrk.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-diag-suppress", "1444"]
-SOURCES = ["tree.cu", "passes.cu", "integrate.cu", "pm.cu", "bins.cu", "noalloc.cu", "crk_api.cpp", "service.cpp"]
+SOURCES = ["tree.cu", "passes.cu", "integrate.cu", "pm.cu", "bins.cu", "noalloc.cu", "probe.cu", "crk_api.cpp",
+           "service.cpp"]
 
 
 def nvcc() -> str:

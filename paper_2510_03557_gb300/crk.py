@@ -39,7 +39,7 @@ ABI = ("crk_create", "crk_load", "crk_load_boxes", "crk_forces", "crk_step", "cr
        "crk_destroy", "crk_fof", "crk_pm_accel", "crk_step_bins", "crk_get_bins",
        "crk_autotune", "crk_service_create", "crk_submit", "crk_poll", "crk_service_destroy",
        "crk_service_snapshot", "crk_service_cancel",
-       "crk_neighbours_noalloc", "crk_get_tree", "crk_last_error")
+       "crk_neighbours_noalloc", "crk_get_tree", "crk_fma_peak", "crk_last_error")
 CRK_NOALLOC_MAX_N = 262144
 
 
@@ -312,6 +312,14 @@ def crk_get_tree(sim) -> dict:
         setattr(t, k, v.ctypes.data if v.size else None)
     _check(lib().crk_get_tree(sim, ctypes.byref(t)))
     return out
+
+
+def crk_fma_peak(precision: int, stream=None) -> float:
+    """Measured FMA throughput of the current device in TFLOP/s (FP32 for
+    CRK_MIXED, FP64 for CRK_FP64)."""
+    out = ctypes.c_double()
+    _check(lib().crk_fma_peak(ctypes.c_int(precision), ctypes.byref(out), _stream_handle(stream)))
+    return float(out.value)
 
 
 def crk_destroy(sim):

@@ -11,6 +11,21 @@ import bench
 def test_fp32_peak_is_sms_times_lanes_times_fma_times_clock():
     assert bench.fp32_peak_tflops(2070.0) == pytest.approx(152 * 128 * 2 * 2.07e9 / 1e12)
     assert bench.fp32_peak_tflops(1000.0) == pytest.approx(38.912)
+    assert bench.fp32_peak_tflops(1000.0, sms=76) == pytest.approx(38.912 / 2)
+
+
+def test_algorithmic_pairs_count_forces_per_unordered_pair():
+    """Density and moments per ordered gather pair with self; hydro per
+    unordered union pair (from the list entries, which include each gas
+    target itself); gravity per unordered pair."""
+    import numpy as np
+
+    gas = np.array([True, True, False, True])
+    counts = {"nbr_count": np.array([4, 6, 0, 2]), "grav_count": np.array([10, 12, 8, 6])}
+    p = bench.algorithmic_pairs(counts, gas, list_entries=3 + 20)
+    assert p == {"density": 15, "moments": 15, "hydro": 10, "gravity": 18}
+    # without list entries the gather sets stand in for the union sets
+    assert bench.algorithmic_pairs(counts, gas)["hydro"] == 6
 
 
 def _sampler(rows):
@@ -39,8 +54,7 @@ def test_clock_summary_without_samples_says_so():
 def test_pair_census_ratios():
     tim = {"tests_grav": 3200, "tests_grav_target": 2000, "tests_hydro": 640, "list_entries": 200,
            "list_slots": 320}
-    pairs = {"density": 190, "gravity": 300}
-    c = bench.pair_census(tim, pairs, n_gas=10, n=20)
+    c = bench.pair_census(tim, 190, 300, n=20)
     # each of the 20 targets is also tested against itself
     assert c["gravity"]["in_range"] == 320
     assert c["gravity"]["tested_per_in_range"] == 10.0
@@ -48,7 +62,7 @@ def test_pair_census_ratios():
     assert c["hydro_fill"]["tested_per_entry"] == 3.2
     assert c["hydro_fill"]["entries_per_gather_pair"] == pytest.approx(1.053, abs=1e-3)
     assert c["list_walk"]["entry_share"] == 0.625
-    empty = bench.pair_census({k: 0 for k in tim}, {"density": 0, "gravity": 0}, 0, 0)
+    empty = bench.pair_census({k: 0 for k in tim}, 0, 0, 0)
     assert empty["gravity"]["tested_per_in_range"] is None
 
 
@@ -69,12 +83,13 @@ def test_fp64_pass_rates():
     tim = {"calls": 2, "tree_ms": 2.0, "pairs_ms": 4.0, "density_ms": 20.0, "moments_ms": 0.0,
            "hydro_ms": 200.0, "gravity_ms": 100.0, "kdk_ms": 1.0}
     pairs = {"density": 1_000_000, "moments": 1_000_000, "hydro": 2_000_000, "gravity": 5_000_000}
-    r = bench.fp64_pass_rates(tim, pairs)
+    r = bench.fp64_pass_rates(tim, pairs, 1.1, "probe")
     assert r["breakdown_ms"]["hydro_ms"] == 100.0 and r["breakdown_ms"]["tree_ms"] == 1.0
     # 2e6 pairs x 183 flop in 0.1 s
     assert r["pass_tflops"]["hydro"] == pytest.approx(2e6 * 183 / 0.1 / 1e12, abs=1e-4)  # 4 decimals
     assert "moments" not in r["pass_tflops"]          # untimed phase: no rate
-    assert r["pass_of_fp64_peak"]["gravity"] == pytest.approx(5e6 * 41 / 0.05 / 1e12 / 1.25, abs=1e-4)
+    assert r["pass_of_fp64_peak"]["gravity"] == pytest.approx(5e6 * 41 / 0.05 / 1e12 / 1.1, abs=1e-4)
+    assert r["fp64_peak"] == {"value": 1.1, "unit": "TFLOP/s", "source": "probe"}
 
 
 def test_reference_arm_line(tmp_path):
@@ -86,15 +101,17 @@ def test_reference_arm_line(tmp_path):
     import sys
 
     out = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference",
-                          "--steps", "1", "--warmup", "0"], capture_output=True, text=True, check=True,
+                          "--steps", "1", "--warmup", "0", "--n", "32", "--cpu-sample", "64"],
+                         capture_output=True, text=True, check=True,
                          cwd=bench.ROOT, timeout=600).stdout.strip().splitlines()
     line = json.loads(out[-1])
-    args = argparse.Namespace(n=128, leaf_cap=128, rebuild_every=1)
+    args = argparse.Namespace(n=32, leaf_cap=128, rebuild_every=1)
     assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
     assert line["config"] == bench.headline_config(args, 1)
+    assert "clustered 2x32^3" in line["config"]["workload"]
     assert line["higher_is_better"] is True and line["value"] > 0
     cb = line["cpu_baseline"]
-    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and "2x40^3" in cb["sample"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and "64 seeded random particles" in cb["sample"]
     assert cb["value"] == line["value"]
     assert line["e2e"] == {"value": line["value"], "unit": bench.UNIT, "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
