@@ -201,7 +201,7 @@ def serve_bench(crk, wl, args):
     reqs = wl.serving_requests(2000)[:count]
     steps = 20
     svc = crk.crk_service_create(150 * 10**9, max_slots=64, precision=crk.CRK_MIXED,
-                                 leaf_cap=args.serve_leaf_cap)
+                                 leaf_cap=args.serve_leaf_cap, lane_priority=args.serve_priority)
     gen = lambda r: wl.gaussian_field_box(r[0], seed=r[1])
     ex = cf.ThreadPoolExecutor(12)
 
@@ -268,6 +268,7 @@ def serve_bench(crk, wl, args):
             "arrival_rate_per_s": round(rate, 3), "load": 0.7, "late_submissions": int(late),
             "calibration": {"requests": ncal, "seconds": round(t_cal, 3)},
             "size_classes": "3 (below 65,536 particles; below 524,288; the rest)",
+            "lane_priority": args.serve_priority,
             "fp64_sequential": {"value": p64 / t64 if t64 else None, "unit": UNIT, "requests": len(seq),
                                 "steps_per_request": steps}}
 
@@ -598,7 +599,8 @@ def run_reference(args):
     """The reference arm: the oracle as it stands, on the host cores, on a
     bounded sample of the headline workload each step (the forces of
     --cpu-sample seeded random particles of the same box with everything they
-    depend on), on the headline's config, metric and unit.  Under torchrun
+    depend on; --ref-sample particles), on the headline's config, metric and
+    unit.  Under torchrun
     only rank 0 runs; the other ranks exit without work."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -610,9 +612,9 @@ def run_reference(args):
     steps = []
     cb = None
     for _ in range(args.warmup):
-        cpu_baseline(box, args.cpu_sample, label)
+        cpu_baseline(box, args.ref_sample, label)
     for _ in range(args.steps):
-        cb, _, _ = cpu_baseline(box, args.cpu_sample, label)
+        cb, _, _ = cpu_baseline(box, args.ref_sample, label)
         steps.append(cb["value"])
     value = statistics.median(steps) if steps else 0.0
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
@@ -731,8 +733,10 @@ def main():
                     help="timed FP64 force evaluations on the headline box (0: skip the FP64 form)")
     ap.add_argument("--fp64-steps", type=int, default=2,
                     help="precision workload: KDK steps of the FP64 form (-1 = as many as the mixed form)")
-    ap.add_argument("--cpu-sample", type=int, default=4096,
-                    help="particles of the oracle's sample (cpu_baseline and the reference arm)")
+    ap.add_argument("--cpu-sample", type=int, default=256,
+                    help="particles of the oracle's sample in cpu_baseline")
+    ap.add_argument("--ref-sample", type=int, default=32,
+                    help="particles of the oracle's sample in each step of the reference arm")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-gaussian", action="store_true", help="skip the 2 x 128^3 secondary field")
@@ -743,6 +747,8 @@ def main():
                     help="stop submitting serving requests after this many seconds")
     ap.add_argument("--serve-fp64", type=int, default=4, help="requests solved one by one in plain FP64")
     ap.add_argument("--serve-leaf-cap", type=int, default=64)
+    ap.add_argument("--serve-priority", type=int, default=1, choices=[-1, 0, 1],
+                    help="service lane_priority: 1 larger size classes first")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

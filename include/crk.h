@@ -57,6 +57,16 @@ extern "C" {
 #define CRK_MEM_HOST 0
 #define CRK_MEM_DEVICE 1
 
+/* crk_params.flags */
+#define CRK_FLAG_DETERMINISTIC 1  /* mixed form: gravity by the gather kernel, every sum in a fixed
+                                     order, so results are bit-reproducible run to run and a box
+                                     gives the same bits alone or batched; without it the mixed
+                                     form evaluates each gravity pair once and adds the partial sums
+                                     with atomics (about twice the pair throughput, results equal
+                                     to rounding).  The FP64 form, counted evaluations (neighbour
+                                     counts or hashes asked for), hierarchical substeps and the
+                                     service always use the gather kernel. */
+
 #define CRK_DM 0
 #define CRK_GAS 1
 
@@ -81,7 +91,7 @@ typedef struct {
     int leaf_cap;      /* leaf capacity C: 32, 64 or 128 particles */
     int precision;     /* CRK_FP64 or CRK_MIXED */
     int cm_level;      /* chaining-mesh Morton level b (2^b bins per side); 0 = automatic */
-    int flags;         /* reserved, 0 */
+    int flags;         /* CRK_FLAG_* bits (0: none) */
     int rebuild_every; /* sort particles into new leaves every this many steps (0 or 1: every
                           step); in between, leaves keep their particles and their bounding
                           boxes grow with them, and only the boxes, the leaf hierarchy and the
@@ -362,7 +372,10 @@ typedef struct {
     int size_classes;          /* number of size classes K in [1, 8] (0: 3).  A job of n particles
                                   goes to class k, the first with n < 8192 * 8^(k+1), or to the
                                   last class (K = 3: n < 65,536; n < 524,288; the rest) */
-    int reserved[2];
+    int lane_priority;         /* CUDA stream priorities of the classes: 0 all equal; 1 larger classes
+                                  higher (their blocks go first when SMs free up, which shortens the
+                                  latency tail of the large jobs); -1 smaller classes higher */
+    int reserved[1];
 } crk_service_params;
 
 typedef struct {

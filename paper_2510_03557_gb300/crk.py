@@ -30,6 +30,7 @@ CRK_MIXED = 1
 CRK_WENDLAND_C4 = 0
 CRK_MEM_HOST = 0
 CRK_MEM_DEVICE = 1
+CRK_FLAG_DETERMINISTIC = 1
 CRK_DM = 0
 CRK_GAS = 1
 
@@ -90,7 +91,7 @@ class ServiceParams(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_slots", ctypes.c_int),
                 ("precision", ctypes.c_int), ("leaf_cap", ctypes.c_int), ("device", ctypes.c_int),
                 ("snapshot_every", ctypes.c_int), ("size_classes", ctypes.c_int),
-                ("reserved", ctypes.c_int * 2)]
+                ("lane_priority", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
 
 class Job(ctypes.Structure):
@@ -142,10 +143,11 @@ def physics(box=1.0, G=1.0, gamma=5.0 / 3.0, r_cut=0.1, r_split=0.02, eps_soft=0
 
 
 def params(phys: Physics | None = None, leaf_cap=64, precision=CRK_MIXED, cm_level=0,
-           kernel=CRK_WENDLAND_C4, rebuild_every=1, pm_grid=0) -> Params:
+           kernel=CRK_WENDLAND_C4, rebuild_every=1, pm_grid=0, flags=0) -> Params:
     p = Params()
     p.phys = phys if phys is not None else physics()
     p.kernel = kernel
+    p.flags = flags
     p.leaf_cap = leaf_cap
     p.precision = precision
     p.cm_level = cm_level
@@ -382,9 +384,10 @@ def crk_autotune(sim, caps=(32, 64, 128)):
 
 
 def crk_service_create(hbm_budget_bytes: int, max_slots: int, precision=CRK_MIXED, leaf_cap=64,
-                       device=0, snapshot_every=0, size_classes=0) -> ctypes.c_void_p:
+                       device=0, snapshot_every=0, size_classes=0, lane_priority=0) -> ctypes.c_void_p:
     p = ServiceParams()
     p.size_classes = size_classes
+    p.lane_priority = lane_priority
     p.hbm_budget_bytes = int(hbm_budget_bytes)
     p.max_slots = max_slots
     p.precision = precision
@@ -484,9 +487,9 @@ class Sim:
     """Owns one crk_sim handle (create / load / forces / step / destroy)."""
 
     def __init__(self, phys: Physics | None = None, leaf_cap=64, precision=CRK_MIXED, cm_level=0,
-                 stream=None, rebuild_every=1, pm_grid=0):
+                 stream=None, rebuild_every=1, pm_grid=0, flags=0):
         self.handle = crk_create(params(phys, leaf_cap, precision, cm_level, rebuild_every=rebuild_every,
-                                        pm_grid=pm_grid), stream)
+                                        pm_grid=pm_grid, flags=flags), stream)
 
     def load(self, box):
         crk_load(self.handle, box.pos, box.vel, box.mass, box.u, box.h, box.species)

@@ -226,6 +226,10 @@ PassArgs pass_args(crk_sim *s)
     a.lmap = nullptr;
     a.nl_bound = 0;
     a.nl_retry = s->nl_retry.as<uint32_t>();
+    // each gravity pair once (atomics) unless fixed-order sums are needed:
+    // the deterministic flag, the service's pool, a hierarchical substep
+    // (rows only for active leaves, so a pair may be seen from one side only)
+    a.grav_once = s->mixed && !(s->prm.flags & CRK_FLAG_DETERMINISTIC) && !s->is_pool && s->bins_bmin < 0;
     return a;
 }
 
@@ -714,6 +718,7 @@ extern "C" int crk_create(const crk_params *params, void *cuda_stream, crk_sim *
     if (params->kernel != CRK_WENDLAND_C4) return fail(CRK_EINVAL, "unsupported kernel");
     if (params->cm_level < 0 || params->cm_level > 10) return fail(CRK_EINVAL, "cm_level in [0, 10]");
     if (params->rebuild_every < 0) return fail(CRK_EINVAL, "rebuild_every must be >= 0");
+    if (params->flags & ~CRK_FLAG_DETERMINISTIC) return fail(CRK_EINVAL, "unknown flags bits 0x%x", params->flags);
     if (params->pm_grid != 0 && (params->pm_grid < 4 || params->pm_grid > 1024 || params->pm_grid % 2))
         return fail(CRK_EINVAL, "pm_grid must be 0 or an even number in [4, 1024] (got %d)", params->pm_grid);
     crk_sim *s = new crk_sim();

@@ -117,6 +117,9 @@ struct PassArgs {
     uint32_t n_ggas, n_gall;
     int *err;                // [0] code, [1] smallest original index of a failing particle
     unsigned long long *nfloor;  // floor events of the u predictor
+    // gravity of the mixed form with each unordered pair evaluated once and
+    // the sums added by atomics (1), or the deterministic gather (0)
+    int grav_once;
     // pair-work census of a counted evaluation (null otherwise): [0] lane
     // slots of the hydro candidate tests (32 x staged candidates per visit),
     // [1] hydro list entries written, [2] lane slots of the gravity tests,

@@ -1555,6 +1555,140 @@ __global__ void __launch_bounds__(kBlock) gravity_k(PassArgs a)
     }
 }
 
+// ------------------------------------------- gravity, each pair evaluated once
+// The mixed form's short-range gravity with every unordered pair evaluated
+// once (paper Sec. IV-B2, Eq. 1-2 and Algorithm 1: warp splitting, partial
+// sums exchanged by shuffles, register accumulation, atomics per leaf
+// output).  The warp of a target group of leaf I visits only the neighbour
+// leaves J >= I of its row; inside leaf I a pair is done by its
+// lower-indexed particle.  The staged candidates of a visit are taken in
+// chunks of 32 on a diagonal: at step k lane l pairs its target with
+// candidate (l + k) mod 32 of the chunk, so the 32 lanes meet 32 different
+// candidates; the candidate's partial sum -sum_i G m_i S(r)/(r^2+eps^2)^{3/2}
+// x_ij travels with it from lane to lane by three shuffles a step and, after
+// 32 steps, is back in lane l = its own slot, which adds it to the
+// candidate's acceleration with one float4 atomic (skipped when no pair was
+// in range).  The target's own sum stays in registers and is added once at
+// the end.  The candidate test, the guard-band re-decision in FP64 and the
+// pair force are those of gravity_k; the summation order of the atomics is
+// not fixed, so results agree with the gather form to rounding, not bit for
+// bit.  Staged w: G m_j.
+template <bool WRAP>
+__device__ __forceinline__ void gravity_sym_tile(const Vec4<float> *tile, const uint8_t *tslot, uint32_t K,
+                                                 const Target<float> &q, float L, float hL, float rc2, double rc2x,
+                                                 float gb, float e2, float kv, float Gmi, bool same, bool act,
+                                                 const State &s, uint32_t i, uint32_t sJ, double Ld, uint32_t lane,
+                                                 float &ax, float &ay, float &az, float4 *__restrict__ acc)
+{
+    const uint32_t src = (lane + 1u) & 31u;
+    for (uint32_t c0 = 0; c0 < K; c0 += 32u) {
+        const Vec4<float> *chunk = tile + c0;
+        const uint8_t *cslot = tslot + c0;
+        float bx = 0.f, by = 0.f, bz = 0.f;
+        uint32_t jj = lane;
+#pragma unroll 4
+        for (int k = 0; k < 32; ++k) {
+            const Vec4<float> rj = chunk[jj];
+            float dx, dy, dz;
+            const float r2 = sep2<float, WRAP>(rj, q, L, hL, dx, dy, dz);
+            const float dr = r2 - rc2;
+            bool in = dr < 0.f;
+            if (fabsf(dr) < gb) in = exact_lt(s, i, sJ + cslot[jj], Ld, rc2x);  // rare: pairs at the cut
+            if (same) in = in && (sJ + cslot[jj] > i);  // one leaf: the lower index does the pair
+            in = in && act;
+            const float v = Real<float>::sqrt_(r2) * kv;
+            const float tt = Real<float>::rcp(fmaf(kAsPv, v, 1.0f));
+            const float poly = tt * (kAs1 + tt * (kAs2 + tt * (kAs3 + tt * (kAs4 + tt * kAs5))));
+            const float sw = Real<float>::exp2(-v * v) * fmaf(kTwoOverSqrtPiV, v, poly);  // S(r)
+            const float is = Real<float>::rsqrt(r2 + e2);
+            float f = sw * is * is * is;  // S(r) (r^2 + eps^2)^{-3/2}
+            f = in ? f : 0.f;
+            const float fi = f * rj.w, fj = f * Gmi;
+            ax = fmaf(fi, dx, ax);
+            ay = fmaf(fi, dy, ay);
+            az = fmaf(fi, dz, az);
+            bx = fmaf(-fj, dx, bx);
+            by = fmaf(-fj, dy, by);
+            bz = fmaf(-fj, dz, bz);
+            // hand the candidate's partial to the lane that meets it next
+            bx = __shfl_sync(0xffffffffu, bx, src);
+            by = __shfl_sync(0xffffffffu, by, src);
+            bz = __shfl_sync(0xffffffffu, bz, src);
+            jj = (jj + 1u) & 31u;
+        }
+        // after 32 shifts the partial of candidate c0 + lane is in lane
+        if (c0 + lane < K && (bx != 0.f || by != 0.f || bz != 0.f))
+            atomicAdd(acc + (sJ + cslot[lane]), make_float4(bx, by, bz, 0.f));
+    }
+}
+
+template <int JMAX>
+__global__ void __launch_bounds__(kBlock) gravity_sym_k(PassArgs a)
+{
+    using R4 = Vec4<float>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    const uint32_t gi = blockIdx.x * kWarps + w;
+    if (gi >= a.n_gall) return;
+    R4 *tile = reinterpret_cast<R4 *>(smem + (size_t)w * tile_warp_bytes<float, JMAX>());
+    uint8_t *tslot = reinterpret_cast<uint8_t *>(tile + JMAX);
+    const Group G = load_group(a.lv, a.gall, gi, lane);
+    const int I = G.I;
+    const uint32_t i = G.i;
+    const R4 *__restrict__ pm = reinterpret_cast<const R4 *>(a.pm);
+    float4 *__restrict__ acc = reinterpret_cast<float4 *>(a.acc_g);
+    const BoxDev &bx = a.boxes[a.lv.slot[I]];
+    const double Ld = bx.L;
+    const float L = (float)Ld, hL = (float)(0.5 * Ld);
+    const R4 ri = pm[i];
+    const double rc2x = __dmul_rn(bx.r_cut, bx.r_cut);
+    const float rc = (float)bx.r_cut;
+    const float rc2 = rc * rc;
+    const float e2 = (float)fmax(bx.eps_soft * bx.eps_soft, (double)kMinS2);
+    const float Gc = (float)bx.G;
+    const float kv = (float)(0.5 / bx.r_split) * (float)kSqrtLog2e;
+    const float Gmi = Gc * ri.w;
+    float px, py, pz;
+    rel_pos(ri, a.lv, I, Ld, px, py, pz);
+    const WarpBox wb = warp_box(px, py, pz, G.act);
+    const float Rc = (float)bx.r_cut * 1.0001f + 1e-6f * (float)Ld;
+    float ax = 0.f, ay = 0.f, az = 0.f;
+    // the row is ascending: start at the first J >= I
+    uint32_t p0 = a.grow[I], p1 = a.grow[I + 1];
+    {
+        uint32_t lo = p0, hi = p1;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (a.gcol[mid] < (uint32_t)I) lo = mid + 1;
+            else hi = mid;
+        }
+        p0 = lo;
+    }
+    for (uint32_t p = p0; p < p1; ++p) {
+        const uint32_t J = a.gcol[p];
+        const float4 fr = a.gfr[p];
+        if (out_of_range(wb, fr, a.lv.ex[J], a.lv.ey[J], a.lv.ez[J], Rc)) continue;
+        const uint32_t sJ = a.lv.start[J], cJ = a.lv.count[J];
+        const uint32_t cm = chunks_in_range(a.lv, J, cJ, wb, fr, Rc);
+        if (cm == 0u) continue;
+        __syncwarp();
+        const uint32_t K = stage_cull<float, false, false>(tile, tslot, nullptr, pm, nullptr, sJ, cJ, cm, wb,
+                                                           cand_frame<float>(a.lv, I, fr, Ld), Rc, lane, Gc);
+        __syncwarp();
+        if (K == 0u) continue;
+        const Target<float> q = target_in_frame(ri, fr);
+        const float gb = guard_band(rc, q.mag);
+        const bool same = J == (uint32_t)I;
+        if (q.wrap)
+            gravity_sym_tile<true>(tile, tslot, K, q, L, hL, rc2, rc2x, gb, e2, kv, Gmi, same, G.act, a.s, i, sJ,
+                                   Ld, lane, ax, ay, az, acc);
+        else
+            gravity_sym_tile<false>(tile, tslot, K, q, L, hL, rc2, rc2x, gb, e2, kv, Gmi, same, G.act, a.s, i, sJ,
+                                    Ld, lane, ax, ay, az, acc);
+    }
+    if (G.act) atomicAdd(acc + i, make_float4(ax, ay, az, 0.f));
+}
+
 // ------------------------------------------------- friends-of-friends groups
 // In situ halo finding (paper Sec. IV-B3) on the solver's own leaves and
 // gravity leaf-pair lists: particles of the selected species are linked when
@@ -1852,6 +1986,18 @@ void launch_hydro(const PassArgs &a, int mixed, int cap, cudaStream_t st)
 void launch_gravity(const PassArgs &a, int mixed, int cap, bool count, cudaStream_t st)
 {
     if (a.n_gall == 0) return;
+    if (mixed && !count && a.grav_once) {
+        // every contribution is added: the accelerations start from zero
+        cudaMemsetAsync(a.acc_g, 0, (size_t)a.n * sizeof(float4), st);
+        if (cap == 32)
+            launch_warp_kernel(gravity_sym_k<32>, a.n_gall, (size_t)kWarps * tile_warp_bytes<float, 32>(), a, st);
+        else if (cap == 64)
+            launch_warp_kernel(gravity_sym_k<64>, a.n_gall, (size_t)kWarps * tile_warp_bytes<float, 64>(), a, st);
+        else
+            launch_warp_kernel(gravity_sym_k<128>, a.n_gall, (size_t)kWarps * tile_warp_bytes<float, 128>(), a, st);
+        note_launches(1);
+        return;
+    }
     CRK_BY_CAP(gravity_dispatch, a, count, st);
     note_launches(1);
 }

@@ -330,6 +330,8 @@ extern "C" int crk_service_create(const crk_service_params *params, crk_service 
     if (params->snapshot_every < 0) return fail(CRK_EINVAL, "snapshot_every must be >= 0");
     if (params->size_classes < 0 || params->size_classes > kMaxClasses)
         return fail(CRK_EINVAL, "size_classes must be in [0, %d]", kMaxClasses);
+    if (params->lane_priority < -1 || params->lane_priority > 1)
+        return fail(CRK_EINVAL, "lane_priority must be -1, 0 or 1");
     CK(cudaSetDevice(params->device));
     auto *sv = new crk_service();
     sv->prm = *params;
@@ -339,10 +341,22 @@ extern "C" int crk_service_create(const crk_service_params *params, crk_service 
     p.leaf_cap = params->leaf_cap ? params->leaf_cap : 64;
     p.precision = params->precision;
     int rc = CRK_OK;
-    for (int k = 0; k < sv->prm.size_classes && rc == CRK_OK; ++k) {
+    // stream priorities: lower numbers run first; greatest <= least
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+        cudaGetLastError();
+        least = greatest = 0;
+    }
+    const int K = sv->prm.size_classes;
+    for (int k = 0; k < K && rc == CRK_OK; ++k) {
         auto ln = std::make_unique<Lane>();
         ln->index = k;
-        cudaError_t e = cudaStreamCreateWithFlags(&ln->st, cudaStreamNonBlocking);
+        int prio = least;
+        if (sv->prm.lane_priority != 0 && K > 1) {
+            const int rank = sv->prm.lane_priority > 0 ? k : K - 1 - k;   // 0 = lowest priority
+            prio = least - (int)((long)(least - greatest) * rank / (K - 1));
+        }
+        cudaError_t e = cudaStreamCreateWithPriority(&ln->st, cudaStreamNonBlocking, prio);
         if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&ln->side, cudaStreamNonBlocking);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ln->stepped, cudaEventDisableTiming);
         if (e != cudaSuccess) rc = fail(CRK_ECUDA, "stream creation failed: %s", cudaGetErrorString(e));

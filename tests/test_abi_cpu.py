@@ -110,7 +110,8 @@ def test_create_rejects_bad_mesh_sizes_before_touching_the_device(libcrk, pm_gri
 @pytest.mark.parametrize("field,value,word", [("leaf_cap", 48, "leaf_cap"), ("precision", 2, "precision"),
                                               ("kernel", 1, "kernel"), ("cm_level", 11, "cm_level"),
                                               ("cm_level", -1, "cm_level"),
-                                              ("rebuild_every", -1, "rebuild_every")])
+                                              ("rebuild_every", -1, "rebuild_every"),
+                                              ("flags", 2, "flags")])
 def test_create_rejects_bad_params_before_touching_the_device(libcrk, field, value, word):
     """Every create-time parameter is checked before the first CUDA call."""
     p = libcrk.params()
@@ -135,7 +136,8 @@ def test_null_arguments_are_rejected_without_a_device(libcrk):
                                      (dict(hbm_budget_bytes=0), "hbm_budget_bytes"),
                                      (dict(snapshot_every=-1), "snapshot_every"),
                                      (dict(size_classes=-1), "size_classes"),
-                                     (dict(size_classes=9), "size_classes")])
+                                     (dict(size_classes=9), "size_classes"),
+                                     (dict(lane_priority=2), "lane_priority")])
 def test_service_create_rejects_bad_params_before_touching_the_device(libcrk, kw, word):
     args = dict(hbm_budget_bytes=1 << 30, max_slots=4)
     args.update(kw)

@@ -101,7 +101,7 @@ def test_reference_arm_line(tmp_path):
     import sys
 
     out = subprocess.run([sys.executable, os.path.join(bench.ROOT, "bench.py"), "--impl", "reference",
-                          "--steps", "1", "--warmup", "0", "--n", "32", "--cpu-sample", "64"],
+                          "--steps", "1", "--warmup", "0", "--n", "32", "--ref-sample", "64"],
                          capture_output=True, text=True, check=True,
                          cwd=bench.ROOT, timeout=600).stdout.strip().splitlines()
     line = json.loads(out[-1])

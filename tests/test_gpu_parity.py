@@ -46,8 +46,8 @@ def oracle_params(box_like, **kw):
     return oracle.make_params(**d)
 
 
-def run_gpu(crk, s, phys, precision, leaf_cap=64, counts=True):
-    with crk.Sim(phys, leaf_cap=leaf_cap, precision=precision) as sim:
+def run_gpu(crk, s, phys, precision, leaf_cap=64, counts=True, flags=0):
+    with crk.Sim(phys, leaf_cap=leaf_cap, precision=precision, flags=flags) as sim:
         crk.crk_load(sim.handle, s["pos"], s["vel"], s["mass"], s["u"], s["h"], s["species"])
         sim.n = len(s["mass"])
         return sim.forces(counts=counts)
@@ -250,6 +250,35 @@ def test_clustered_2x64_matches_oracle(crk, precision, nsphere):
     compare(out, ref, sets, precision, sample=sample, label=f"clustered 2x64^3 nsphere={nsphere}")
     if nsphere == 8:
         assert sets["grav"][0].max() > 20000     # the dense cores are really reached
+    if precision == 1:
+        # the force-only evaluation of the mixed form: gravity with each pair
+        # evaluated once and the partial sums added by atomics
+        once = run_gpu(crk, box_dict(box), crk.box_physics(box), 1, leaf_cap=128, counts=False)
+        compare(once, ref, {}, 1, sample=sample, label=f"clustered 2x64^3 nsphere={nsphere}, pairs once")
+        assert rel_l2(once["acc"], out["acc"]) <= TOL[1]
+
+
+@pytest.mark.parametrize("leaf_cap", [32, 64, 128])
+def test_gravity_pairs_once_matches_the_gather_form(crk, leaf_cap):
+    """Mixed form: gravity with each unordered pair evaluated once (atomics)
+    against the deterministic gather form and the oracle on the clustered
+    inputs with periodic wraps; the deterministic flag gives bit-identical
+    repeated evaluations, the default agrees with it to rounding and keeps
+    the total momentum rate at roundoff."""
+    s = _clustered(seed=91)
+    phys = dict(box=1.0, G=1.0, gamma=5.0 / 3.0, r_cut=0.12, r_split=0.12 / 4.5, eps_soft=1e-3)
+    op = oracle.make_params(**phys)
+    ref = oracle.forces(s["pos"], s["vel"], s["mass"], s["u"], s["h"], s["species"], op)
+    assert ref["rc"] == 0
+    det = crk.CRK_FLAG_DETERMINISTIC
+    d1 = run_gpu(crk, s, crk.physics(**phys), 1, leaf_cap=leaf_cap, counts=False, flags=det)
+    d2 = run_gpu(crk, s, crk.physics(**phys), 1, leaf_cap=leaf_cap, counts=False, flags=det)
+    assert np.array_equal(d1["acc"], d2["acc"])
+    once = run_gpu(crk, s, crk.physics(**phys), 1, leaf_cap=leaf_cap, counts=False)
+    compare(once, ref, {}, 1, label=f"pairs once cap={leaf_cap}")
+    assert rel_l2(once["acc"], d1["acc"]) <= 1e-5
+    ma = s["mass"][:, None] * once["acc"]
+    assert np.abs(once["momentum_rate"]).max() / np.abs(ma).sum() < 1e-5
 
 
 def _clustered_smooth_h(seed, n_gas=2500, n_dm=1500, h0=0.09):

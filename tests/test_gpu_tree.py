@@ -108,7 +108,7 @@ def _check_tree(crk, sim, s, r_cut, cap, label):
     return t
 
 
-def _clustered_small(seed, n_gas=2400, n_dm=1600):
+def _clustered_small(seed, n_gas=6000, n_dm=2000):
     rng = np.random.default_rng(seed)
     g = np.concatenate([rng.uniform(0, 1, size=(n_gas // 2, 3)),
                         (0.02 + 0.04 * rng.standard_normal((n_gas - n_gas // 2, 3))) % 1.0])
