@@ -590,7 +590,9 @@ def headline_config(args, world: int) -> dict:
     n = 2 * args.n ** 3
     return {"workload": f"clustered 2x{args.n}^3 (half uniform, half in 512 Plummer spheres of scale 0.002, "
                         f"kNN h), FP32-mixed, KDK steps at the box's Courant dt",
-            "particles": n, "leaf_cap": args.leaf_cap, "rebuild_every": args.rebuild_every,
+            "particles": n,
+            "leaf_cap": "autotuned over (64, 128) with the gravity form" if args.autotune else args.leaf_cap,
+            "rebuild_every": args.rebuild_every,
             "parallelism": f"replicas{world}",
             "l2": f"inputs larger than L2 (~{n * 600 / 1e9:.1f} GB resident state)"}
 
@@ -727,6 +729,8 @@ def main():
     ap.add_argument("--n", type=int, default=256, help="clustered box: lattice size per species (2 n^3)")
     ap.add_argument("--gauss-n", type=int, default=128, help="Gaussian-field box: 2 n^3 particles")
     ap.add_argument("--leaf-cap", type=int, default=128)
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="headline: keep --leaf-cap and the gather gravity instead of the library's autotuner")
     ap.add_argument("--rebuild-every", type=int, default=1,
                     help="sort into new leaves every this many steps (boxes grow in between)")
     ap.add_argument("--fp64-evals", type=int, default=1,
@@ -820,6 +824,14 @@ def main():
     sim = crk.Sim(phys, leaf_cap=args.leaf_cap, precision=crk.CRK_MIXED, stream=stream,
                   rebuild_every=args.rebuild_every)
     sim.load(box)
+    tune = None
+    cap = args.leaf_cap
+    if args.autotune:
+        # the library's autotuner: leaf capacity x gravity pair decomposition
+        cap, form, grid = crk.crk_autotune_ex(sim.handle, (64, 128))
+        names = {crk.CRK_GRAVITY_GATHER: "gather", crk.CRK_GRAVITY_PAIRS_ONCE: "pairs_once"}
+        tune = {"leaf_cap": cap, "gravity_form": names[form],
+                "force_evaluation_ms": {f"{c}/{names[f]}": round(v, 2) for (c, f), v in grid.items()}}
     counts = sim.forces(counts=True)      # untimed: the true pair counts for the roofline
     tim0 = crk.crk_get_timings(sim.handle)
     pairs = algorithmic_pairs(counts, gas, tim0["list_entries"])
@@ -878,7 +890,7 @@ def main():
     fp64 = None
     out64 = None
     if args.fp64_evals > 0:
-        s64 = crk.Sim(phys, leaf_cap=args.leaf_cap, precision=crk.CRK_FP64, stream=stream)
+        s64 = crk.Sim(phys, leaf_cap=cap, precision=crk.CRK_FP64, stream=stream)
         s64.load(box)
         crk.crk_set_timing(s64.handle, True)
         barrier()
@@ -912,7 +924,8 @@ def main():
     # ---------------- end to end through the public API with host buffers
     e2e = None
     if not args.no_e2e:
-        se = crk.Sim(phys, leaf_cap=args.leaf_cap, precision=crk.CRK_MIXED, stream=stream)
+        se = crk.Sim(phys, leaf_cap=cap, precision=crk.CRK_MIXED, stream=stream,
+                     flags=crk.CRK_FLAG_GRAVITY_PAIRS_ONCE if tune and tune["gravity_form"] == "pairs_once" else 0)
         se.load(box)
         se.step(dt, 1)
         pin = lambda shape: torch.empty(shape, dtype=torch.float64).pin_memory().numpy()
@@ -966,10 +979,11 @@ def main():
             "config": headline_config(args, world),
             "roofline": {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3),
                          "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                         "traffic": _traffic(dom, N, args.leaf_cap),
+                         "traffic": _traffic(dom, N, cap),
                          "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on "
                                            "the clustered generator at 2x64^3 with 8 dense cores, scaled by "
-                                           "particles (null when the kernel source differs from the captured one)",
+                                           "particles (null when the kernel source or leaf capacity differs from "
+                                           "the captured one)",
                          "work": f"{FLOP_PER_PAIR[dom]} flop per "
                                  f"{'unordered' if dom in ('hydro', 'gravity') else 'ordered'} in-range pair",
                          "peak_source": f"{sms} SMs (device query) x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
@@ -982,6 +996,7 @@ def main():
             "leaves": int(tim["nleaves"]), "leaf_pairs": {"hydro": int(tim["pairs_hydro"]),
                                                           "gravity": int(tim["pairs_grav"])},
             "breakdown_ms": breakdown,
+            "autotune": tune,
             "dt": dt,
             "setup_s": round(t_gen, 1),
             "fp64_plain": fp64,

@@ -58,14 +58,22 @@ extern "C" {
 #define CRK_MEM_DEVICE 1
 
 /* crk_params.flags */
-#define CRK_FLAG_DETERMINISTIC 1  /* mixed form: gravity by the gather kernel, every sum in a fixed
-                                     order, so results are bit-reproducible run to run and a box
-                                     gives the same bits alone or batched; without it the mixed
-                                     form evaluates each gravity pair once and adds the partial sums
-                                     with atomics (about twice the pair throughput, results equal
-                                     to rounding).  The FP64 form, counted evaluations (neighbour
-                                     counts or hashes asked for), hierarchical substeps and the
-                                     service always use the gather kernel. */
+#define CRK_FLAG_GRAVITY_PAIRS_ONCE 2  /* mixed form: short-range gravity with each unordered pair
+                                          evaluated once (warp splitting, paper Sec. IV-B2 and
+                                          Algorithm 1): partial sums passed between lanes by shuffles
+                                          and added with atomics, so results agree with the default
+                                          gather form to rounding but are not bit-reproducible run to
+                                          run.  Without it every target sums its own pairs in a fixed
+                                          order (bit-reproducible; a box gives the same bits alone or
+                                          batched).  The FP64 form, counted evaluations (neighbour
+                                          counts or hashes asked for), hierarchical substeps and the
+                                          service always use the gather form. */
+
+/* Gravity pair decompositions (crk_autotune_ex) */
+#define CRK_GRAVITY_GATHER 0       /* each target sums its own pairs (32 threads per visit of a
+                                      target group to a neighbour leaf, one per target) */
+#define CRK_GRAVITY_PAIRS_ONCE 1   /* each pair once (32 threads per visit, one pair per thread per
+                                      step, both sides updated) */
 
 #define CRK_DM 0
 #define CRK_GAS 1
@@ -299,6 +307,19 @@ int crk_get_bins(crk_sim *sim, uint8_t *bins, int mem);
  * the stream.  Errors: CRK_EINVAL (bad candidate, no particles), the errors
  * of crk_forces. */
 int crk_autotune(crk_sim *sim, const int *caps, int ncaps, int *best_cap, double *ms_out);
+
+/* The autotuner over two axes: leaf capacity (caps, as crk_autotune) and
+ * the gravity pair decomposition of the mixed form (forms: CRK_GRAVITY_GATHER
+ * or CRK_GRAVITY_PAIRS_ONCE; the FP64 form and the service run the gather
+ * form whatever is chosen).  Times one force evaluation at every pair of
+ * candidates (after a warm-up one), keeps the fastest for the handle's later
+ * calls (its leaf capacity and its CRK_FLAG_GRAVITY_PAIRS_ONCE bit) and
+ * writes it to *best_cap / *best_form (optional); ms_out (optional, ncaps x
+ * nforms entries) gets the time of caps[k] with forms[f] at ms_out[k * nforms
+ * + f].  Synchronises the stream.  Errors: CRK_EINVAL (bad candidate, no
+ * particles), the errors of crk_forces. */
+int crk_autotune_ex(crk_sim *sim, const int *caps, int ncaps, const int *forms, int nforms, int *best_cap,
+                    int *best_form, double *ms_out);
 
 /* Leaves and leaf-pair lists of the handle's last tree (paper Sec. IV-B1:
  * base leaves of the spatial tree and the leaf-pair interaction lists), for

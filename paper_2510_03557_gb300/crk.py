@@ -30,7 +30,9 @@ CRK_MIXED = 1
 CRK_WENDLAND_C4 = 0
 CRK_MEM_HOST = 0
 CRK_MEM_DEVICE = 1
-CRK_FLAG_DETERMINISTIC = 1
+CRK_FLAG_GRAVITY_PAIRS_ONCE = 2
+CRK_GRAVITY_GATHER = 0
+CRK_GRAVITY_PAIRS_ONCE = 1
 CRK_DM = 0
 CRK_GAS = 1
 
@@ -38,7 +40,7 @@ CRK_GAS = 1
 ABI = ("crk_create", "crk_load", "crk_load_boxes", "crk_forces", "crk_step", "crk_step_boxes",
        "crk_get_state", "crk_set_state", "crk_get_sums", "crk_get_size", "crk_set_timing", "crk_get_timings",
        "crk_destroy", "crk_fof", "crk_pm_accel", "crk_step_bins", "crk_get_bins",
-       "crk_autotune", "crk_service_create", "crk_submit", "crk_poll", "crk_service_destroy",
+       "crk_autotune", "crk_autotune_ex", "crk_service_create", "crk_submit", "crk_poll", "crk_service_destroy",
        "crk_service_snapshot", "crk_service_cancel",
        "crk_neighbours_noalloc", "crk_get_tree", "crk_fma_peak", "crk_last_error")
 CRK_NOALLOC_MAX_N = 262144
@@ -381,6 +383,19 @@ def crk_autotune(sim, caps=(32, 64, 128)):
     best = ctypes.c_int()
     _check(lib().crk_autotune(sim, arr, ctypes.c_int(len(caps)), ctypes.byref(best), ms))
     return int(best.value), {c: float(m) for c, m in zip(caps, ms)}
+
+
+def crk_autotune_ex(sim, caps=(32, 64, 128), forms=(CRK_GRAVITY_GATHER, CRK_GRAVITY_PAIRS_ONCE)):
+    """Times one force evaluation per (leaf capacity, gravity form), keeps the
+    fastest; returns (best capacity, best form, {(capacity, form): ms})."""
+    ca = (ctypes.c_int * len(caps))(*caps)
+    fa = (ctypes.c_int * len(forms))(*forms)
+    ms = (ctypes.c_double * (len(caps) * len(forms)))()
+    bc, bf = ctypes.c_int(), ctypes.c_int()
+    _check(lib().crk_autotune_ex(sim, ca, ctypes.c_int(len(caps)), fa, ctypes.c_int(len(forms)), ctypes.byref(bc),
+                                 ctypes.byref(bf), ms))
+    grid = {(c, f): float(ms[k * len(forms) + j]) for k, c in enumerate(caps) for j, f in enumerate(forms)}
+    return int(bc.value), int(bf.value), grid
 
 
 def crk_service_create(hbm_budget_bytes: int, max_slots: int, precision=CRK_MIXED, leaf_cap=64,

@@ -226,10 +226,10 @@ PassArgs pass_args(crk_sim *s)
     a.lmap = nullptr;
     a.nl_bound = 0;
     a.nl_retry = s->nl_retry.as<uint32_t>();
-    // each gravity pair once (atomics) unless fixed-order sums are needed:
-    // the deterministic flag, the service's pool, a hierarchical substep
+    // each gravity pair once (atomics) when the handle asks for it, except in
+    // the service's pool (fixed-order sums) and in a hierarchical substep
     // (rows only for active leaves, so a pair may be seen from one side only)
-    a.grav_once = s->mixed && !(s->prm.flags & CRK_FLAG_DETERMINISTIC) && !s->is_pool && s->bins_bmin < 0;
+    a.grav_once = s->mixed && (s->prm.flags & CRK_FLAG_GRAVITY_PAIRS_ONCE) && !s->is_pool && s->bins_bmin < 0;
     return a;
 }
 
@@ -718,7 +718,8 @@ extern "C" int crk_create(const crk_params *params, void *cuda_stream, crk_sim *
     if (params->kernel != CRK_WENDLAND_C4) return fail(CRK_EINVAL, "unsupported kernel");
     if (params->cm_level < 0 || params->cm_level > 10) return fail(CRK_EINVAL, "cm_level in [0, 10]");
     if (params->rebuild_every < 0) return fail(CRK_EINVAL, "rebuild_every must be >= 0");
-    if (params->flags & ~CRK_FLAG_DETERMINISTIC) return fail(CRK_EINVAL, "unknown flags bits 0x%x", params->flags);
+    if (params->flags & ~CRK_FLAG_GRAVITY_PAIRS_ONCE)
+        return fail(CRK_EINVAL, "unknown flags bits 0x%x", params->flags);
     if (params->pm_grid != 0 && (params->pm_grid < 4 || params->pm_grid > 1024 || params->pm_grid % 2))
         return fail(CRK_EINVAL, "pm_grid must be 0 or an even number in [4, 1024] (got %d)", params->pm_grid);
     crk_sim *s = new crk_sim();
@@ -889,6 +890,9 @@ static int run_substep(crk_sim *s, int sub, int depth, double dt_long, double et
     a.nbr_hash = nullptr;
     a.grav_count = nullptr;
     a.grav_hash = nullptr;
+    // gravity rows exist only for the active leaves: a pair must be seen from
+    // its own target's side, so the gather form
+    a.grav_once = 0;
     a.bsub = sub;
     a.bdepth = depth;
     a.bd = d;
@@ -1140,12 +1144,19 @@ extern "C" int crk_pm_accel(crk_sim *s, double *acc, int mem)
     return CRK_OK;
 }
 
-extern "C" int crk_autotune(crk_sim *s, const int *caps, int ncaps, int *best_cap, double *ms_out)
+// Times one force evaluation (after a warm-up one) at every (capacity,
+// gravity form) candidate and keeps the fastest.
+static int autotune_grid(crk_sim *s, const int *caps, int ncaps, const int *forms, int nforms, int *best_cap,
+                         int *best_form, double *ms_out)
 {
-    if (!s || !caps || ncaps < 1) return fail(CRK_EINVAL, "null argument or no candidate");
+    if (!s || !caps || ncaps < 1 || !forms || nforms < 1) return fail(CRK_EINVAL, "null argument or no candidate");
     for (int k = 0; k < ncaps; ++k)
         if (caps[k] != 32 && caps[k] != 64 && caps[k] != 128)
             return fail(CRK_EINVAL, "leaf capacity candidates must be 32, 64 or 128 (got %d)", caps[k]);
+    for (int f = 0; f < nforms; ++f)
+        if (forms[f] != CRK_GRAVITY_GATHER && forms[f] != CRK_GRAVITY_PAIRS_ONCE)
+            return fail(CRK_EINVAL, "gravity form candidates must be CRK_GRAVITY_GATHER or "
+                                    "CRK_GRAVITY_PAIRS_ONCE (got %d)", forms[f]);
     CK(cudaSetDevice(s->device));
     if (s->n == 0) return fail(CRK_EINVAL, "no particles loaded");
     cudaEvent_t e0, e1;
@@ -1155,37 +1166,57 @@ extern "C" int crk_autotune(crk_sim *s, const int *caps, int ncaps, int *best_ca
         cudaEventDestroy(e0);
         return fail(CRK_ECUDA, "event creation failed: %s", cudaGetErrorString(ce));
     }
+    const int flags0 = s->prm.flags & ~CRK_FLAG_GRAVITY_PAIRS_ONCE;
     int best = -1;
     double best_ms = 0.0;
     int rc = CRK_OK;
     for (int k = 0; k < ncaps && rc == CRK_OK; ++k) {
         s->cap = caps[k];
         s->tree_valid = false;  // leaves of another capacity
-        rc = run_step(s, nullptr, false);  // warm-up: buffers grow to this layout
-        if (rc != CRK_OK) break;
-        cudaEventRecord(e0, s->st);
-        rc = run_step(s, nullptr, false);
-        cudaEventRecord(e1, s->st);
-        if (rc != CRK_OK) break;
-        float ms = 0.f;
-        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-            rc = fail(CRK_ECUDA, "event timing failed");
-            break;
-        }
-        if (ms_out) ms_out[k] = ms;
-        if (best < 0 || ms < best_ms) {
-            best = k;
-            best_ms = ms;
+        for (int f = 0; f < nforms && rc == CRK_OK; ++f) {
+            s->prm.flags = flags0 | (forms[f] == CRK_GRAVITY_PAIRS_ONCE ? CRK_FLAG_GRAVITY_PAIRS_ONCE : 0);
+            rc = run_step(s, nullptr, false);  // warm-up: buffers grow to this layout
+            if (rc != CRK_OK) break;
+            cudaEventRecord(e0, s->st);
+            rc = run_step(s, nullptr, false);
+            cudaEventRecord(e1, s->st);
+            if (rc != CRK_OK) break;
+            float ms = 0.f;
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                rc = fail(CRK_ECUDA, "event timing failed");
+                break;
+            }
+            if (ms_out) ms_out[k * nforms + f] = ms;
+            if (best < 0 || ms < best_ms) {
+                best = k * nforms + f;
+                best_ms = ms;
+            }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != CRK_OK) return rc;
-    s->cap = caps[best];
+    const int bc = caps[best / nforms], bf = forms[best % nforms];
+    s->cap = bc;
+    s->prm.flags = flags0 | (bf == CRK_GRAVITY_PAIRS_ONCE ? CRK_FLAG_GRAVITY_PAIRS_ONCE : 0);
     s->tree_valid = false;
-    if (best_cap) *best_cap = caps[best];
-    // the stored accelerations are those of the chosen capacity
+    if (best_cap) *best_cap = bc;
+    if (best_form) *best_form = bf;
+    // the stored accelerations are those of the chosen configuration
     return run_step(s, nullptr, false);
+}
+
+extern "C" int crk_autotune(crk_sim *s, const int *caps, int ncaps, int *best_cap, double *ms_out)
+{
+    if (!s) return fail(CRK_EINVAL, "null handle");
+    const int form = (s->prm.flags & CRK_FLAG_GRAVITY_PAIRS_ONCE) ? CRK_GRAVITY_PAIRS_ONCE : CRK_GRAVITY_GATHER;
+    return autotune_grid(s, caps, ncaps, &form, 1, best_cap, nullptr, ms_out);
+}
+
+extern "C" int crk_autotune_ex(crk_sim *s, const int *caps, int ncaps, const int *forms, int nforms, int *best_cap,
+                               int *best_form, double *ms_out)
+{
+    return autotune_grid(s, caps, ncaps, forms, nforms, best_cap, best_form, ms_out);
 }
 
 extern "C" int crk_set_state(crk_sim *s, const double *pos, const double *vel, const double *u,

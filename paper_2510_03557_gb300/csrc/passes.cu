@@ -1573,12 +1573,12 @@ __global__ void __launch_bounds__(kBlock) gravity_k(PassArgs a)
 // pair force are those of gravity_k; the summation order of the atomics is
 // not fixed, so results agree with the gather form to rounding, not bit for
 // bit.  Staged w: G m_j.
-template <bool WRAP>
-__device__ __forceinline__ void gravity_sym_tile(const Vec4<float> *tile, const uint8_t *tslot, uint32_t K,
-                                                 const Target<float> &q, float L, float hL, float rc2, double rc2x,
-                                                 float gb, float e2, float kv, float Gmi, bool same, bool act,
-                                                 const State &s, uint32_t i, uint32_t sJ, double Ld, uint32_t lane,
-                                                 float &ax, float &ay, float &az, float4 *__restrict__ acc)
+template <bool WRAP, bool SAME>
+__device__ __forceinline__ void gravity_sym_tile(const PassArgs &a, const Vec4<float> *tile, const uint8_t *tslot,
+                                                 uint32_t K, const Target<float> &q, float L, float hL, float rc2,
+                                                 float gb, float e2, float kv, float Gmi, bool act, uint32_t i,
+                                                 uint32_t sJ, uint32_t lane, float &ax, float &ay, float &az,
+                                                 float4 *__restrict__ acc)
 {
     const uint32_t src = (lane + 1u) & 31u;
     for (uint32_t c0 = 0; c0 < K; c0 += 32u) {
@@ -1593,8 +1593,13 @@ __device__ __forceinline__ void gravity_sym_tile(const Vec4<float> *tile, const 
             const float r2 = sep2<float, WRAP>(rj, q, L, hL, dx, dy, dz);
             const float dr = r2 - rc2;
             bool in = dr < 0.f;
-            if (fabsf(dr) < gb) in = exact_lt(s, i, sJ + cslot[jj], Ld, rc2x);  // rare: pairs at the cut
-            if (same) in = in && (sJ + cslot[jj] > i);  // one leaf: the lower index does the pair
+            if (fabsf(dr) < gb) {
+                // rare: a pair at the cut, re-decided in FP64 (arguments read
+                // from the kernel's parameters, not held in registers)
+                const BoxDev &bxd = a.boxes[a.s.slot[i]];
+                in = exact_lt(a.s, i, sJ + cslot[jj], bxd.L, __dmul_rn(bxd.r_cut, bxd.r_cut));
+            }
+            if (SAME) in = in && (sJ + cslot[jj] > i);  // one leaf: the lower index does the pair
             in = in && act;
             const float v = Real<float>::sqrt_(r2) * kv;
             const float tt = Real<float>::rcp(fmaf(kAsPv, v, 1.0f));
@@ -1623,7 +1628,7 @@ __device__ __forceinline__ void gravity_sym_tile(const Vec4<float> *tile, const 
 }
 
 template <int JMAX>
-__global__ void __launch_bounds__(kBlock) gravity_sym_k(PassArgs a)
+__global__ void __launch_bounds__(kBlock) gravity_sym_k(const __grid_constant__ PassArgs a)
 {
     using R4 = Vec4<float>;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1641,7 +1646,6 @@ __global__ void __launch_bounds__(kBlock) gravity_sym_k(PassArgs a)
     const double Ld = bx.L;
     const float L = (float)Ld, hL = (float)(0.5 * Ld);
     const R4 ri = pm[i];
-    const double rc2x = __dmul_rn(bx.r_cut, bx.r_cut);
     const float rc = (float)bx.r_cut;
     const float rc2 = rc * rc;
     const float e2 = (float)fmax(bx.eps_soft * bx.eps_soft, (double)kMinS2);
@@ -1678,13 +1682,21 @@ __global__ void __launch_bounds__(kBlock) gravity_sym_k(PassArgs a)
         if (K == 0u) continue;
         const Target<float> q = target_in_frame(ri, fr);
         const float gb = guard_band(rc, q.mag);
-        const bool same = J == (uint32_t)I;
-        if (q.wrap)
-            gravity_sym_tile<true>(tile, tslot, K, q, L, hL, rc2, rc2x, gb, e2, kv, Gmi, same, G.act, a.s, i, sJ,
-                                   Ld, lane, ax, ay, az, acc);
-        else
-            gravity_sym_tile<false>(tile, tslot, K, q, L, hL, rc2, rc2x, gb, e2, kv, Gmi, same, G.act, a.s, i, sJ,
-                                    Ld, lane, ax, ay, az, acc);
+        if (J == (uint32_t)I) {
+            if (q.wrap)
+                gravity_sym_tile<true, true>(a, tile, tslot, K, q, L, hL, rc2, gb, e2, kv, Gmi, G.act, i, sJ, lane,
+                                             ax, ay, az, acc);
+            else
+                gravity_sym_tile<false, true>(a, tile, tslot, K, q, L, hL, rc2, gb, e2, kv, Gmi, G.act, i, sJ, lane,
+                                              ax, ay, az, acc);
+        } else {
+            if (q.wrap)
+                gravity_sym_tile<true, false>(a, tile, tslot, K, q, L, hL, rc2, gb, e2, kv, Gmi, G.act, i, sJ, lane,
+                                              ax, ay, az, acc);
+            else
+                gravity_sym_tile<false, false>(a, tile, tslot, K, q, L, hL, rc2, gb, e2, kv, Gmi, G.act, i, sJ,
+                                               lane, ax, ay, az, acc);
+        }
     }
     if (G.act) atomicAdd(acc + i, make_float4(ax, ay, az, 0.f));
 }

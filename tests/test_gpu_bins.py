@@ -89,9 +89,7 @@ def test_bins_mixed_match_oracle(crk, reference):
 
 def test_depth_zero_is_crk_step(crk):
     box = _box()
-    det = crk.CRK_FLAG_DETERMINISTIC   # fixed-order gravity sums in both handles
-    with crk.Sim(crk.box_physics(box), precision=1, flags=det) as a, \
-            crk.Sim(crk.box_physics(box), precision=1, flags=det) as b:
+    with crk.Sim(crk.box_physics(box), precision=1) as a, crk.Sim(crk.box_physics(box), precision=1) as b:
         a.load(box)
         b.load(box)
         counts = crk.crk_step_bins(a.handle, 1e-3, 0, 3, ETA, COURANT)
@@ -150,8 +148,7 @@ def test_batched_boxes_step_as_they_do_alone(crk):
     b2.vel = b2.vel * 20.0
     boxes = [b1, b2]
     cat = lambda k: np.concatenate([getattr(b, k) for b in boxes])
-    det = crk.CRK_FLAG_DETERMINISTIC   # fixed-order gravity sums in the first force evaluation too
-    with crk.Sim(crk.box_physics(b1), precision=1, flags=det) as sim:
+    with crk.Sim(crk.box_physics(b1), precision=1) as sim:
         crk.crk_load_boxes(sim.handle, [b.n for b in boxes], [crk.box_physics(b) for b in boxes],
                            cat("pos"), cat("vel"), cat("mass"), cat("u"), cat("h"), cat("species"))
         sim.n = b1.n + b2.n
@@ -160,7 +157,7 @@ def test_batched_boxes_step_as_they_do_alone(crk):
         bins = crk.crk_get_bins(sim.handle)
     off = 0
     for b in boxes:
-        with crk.Sim(crk.box_physics(b), precision=1, flags=det) as one:
+        with crk.Sim(crk.box_physics(b), precision=1) as one:
             # a one-box batch: the same full sort as the two-box handle
             crk.crk_load_boxes(one.handle, [b.n], [crk.box_physics(b)], b.pos, b.vel, b.mass, b.u, b.h,
                                b.species)

@@ -251,9 +251,10 @@ def test_clustered_2x64_matches_oracle(crk, precision, nsphere):
     if nsphere == 8:
         assert sets["grav"][0].max() > 20000     # the dense cores are really reached
     if precision == 1:
-        # the force-only evaluation of the mixed form: gravity with each pair
-        # evaluated once and the partial sums added by atomics
-        once = run_gpu(crk, box_dict(box), crk.box_physics(box), 1, leaf_cap=128, counts=False)
+        # the mixed form with gravity pairs evaluated once, the partial sums
+        # added by atomics (a force-only evaluation: counted ones gather)
+        once = run_gpu(crk, box_dict(box), crk.box_physics(box), 1, leaf_cap=128, counts=False,
+                       flags=crk.CRK_FLAG_GRAVITY_PAIRS_ONCE)
         compare(once, ref, {}, 1, sample=sample, label=f"clustered 2x64^3 nsphere={nsphere}, pairs once")
         assert rel_l2(once["acc"], out["acc"]) <= TOL[1]
 
@@ -261,20 +262,20 @@ def test_clustered_2x64_matches_oracle(crk, precision, nsphere):
 @pytest.mark.parametrize("leaf_cap", [32, 64, 128])
 def test_gravity_pairs_once_matches_the_gather_form(crk, leaf_cap):
     """Mixed form: gravity with each unordered pair evaluated once (atomics)
-    against the deterministic gather form and the oracle on the clustered
-    inputs with periodic wraps; the deterministic flag gives bit-identical
-    repeated evaluations, the default agrees with it to rounding and keeps
-    the total momentum rate at roundoff."""
+    against the default gather form and the oracle on the clustered inputs
+    with periodic wraps; the gather form gives bit-identical repeated
+    evaluations, the pairs-once form agrees with it to rounding and keeps the
+    total momentum rate at roundoff."""
     s = _clustered(seed=91)
     phys = dict(box=1.0, G=1.0, gamma=5.0 / 3.0, r_cut=0.12, r_split=0.12 / 4.5, eps_soft=1e-3)
     op = oracle.make_params(**phys)
     ref = oracle.forces(s["pos"], s["vel"], s["mass"], s["u"], s["h"], s["species"], op)
     assert ref["rc"] == 0
-    det = crk.CRK_FLAG_DETERMINISTIC
-    d1 = run_gpu(crk, s, crk.physics(**phys), 1, leaf_cap=leaf_cap, counts=False, flags=det)
-    d2 = run_gpu(crk, s, crk.physics(**phys), 1, leaf_cap=leaf_cap, counts=False, flags=det)
+    d1 = run_gpu(crk, s, crk.physics(**phys), 1, leaf_cap=leaf_cap, counts=False)
+    d2 = run_gpu(crk, s, crk.physics(**phys), 1, leaf_cap=leaf_cap, counts=False)
     assert np.array_equal(d1["acc"], d2["acc"])
-    once = run_gpu(crk, s, crk.physics(**phys), 1, leaf_cap=leaf_cap, counts=False)
+    once = run_gpu(crk, s, crk.physics(**phys), 1, leaf_cap=leaf_cap, counts=False,
+                   flags=crk.CRK_FLAG_GRAVITY_PAIRS_ONCE)
     compare(once, ref, {}, 1, label=f"pairs once cap={leaf_cap}")
     assert rel_l2(once["acc"], d1["acc"]) <= 1e-5
     ma = s["mass"][:, None] * once["acc"]
@@ -506,6 +507,25 @@ def test_leaves_kept_between_rebuilds_match_the_oracle(crk, precision):
     for name in ("nbr", "grav"):
         assert np.array_equal(out[name + "_count"], cref[name][0]), name
         assert np.array_equal(out[name + "_hash"], cref[name][1]), name
+
+
+def test_autotune_over_capacity_and_gravity_form(crk):
+    """The two-axis autotuner times every (capacity, gravity form) pair,
+    keeps the fastest, and the forces of the chosen configuration equal the
+    oracle's."""
+    box = wl.gaussian_field_box(16, seed=22)
+    op = oracle_params(box)
+    ref = oracle.forces(box.pos, box.vel, box.mass, box.u, box.h, box.species, op)
+    with crk.Sim(crk.box_physics(box), leaf_cap=64, precision=1) as sim:
+        sim.load(box)
+        cap, form, grid = crk.crk_autotune_ex(sim.handle, (32, 128))
+        assert set(grid) == {(32, 0), (32, 1), (128, 0), (128, 1)} and all(v > 0 for v in grid.values())
+        assert grid[(cap, form)] == min(grid.values())
+        out = sim.forces(counts=False)
+        compare(out, ref, {}, 1, label=f"autotuned cap={cap} form={form}")
+        with pytest.raises(crk.CrkError) as e:
+            crk.crk_autotune_ex(sim.handle, (64,), (2,))
+        assert e.value.code == crk.CRK_EINVAL
 
 
 def test_autotune_keeps_the_fastest_capacity_and_the_forces(crk):
