@@ -69,6 +69,8 @@ extern "C" {
                                           counts or hashes asked for), hierarchical substeps and the
                                           service always use the gather form. */
 
+#define CRK_FLAG_NO_GRAPH 4            /* run every step host-sized (see crk_step): no CUDA graph */
+
 /* Gravity pair decompositions (crk_autotune_ex) */
 #define CRK_GRAVITY_GATHER 0       /* each target sums its own pairs (32 threads per visit of a
                                       target group to a neighbour leaf, one per target) */
@@ -165,6 +167,16 @@ typedef struct {
     int64_t tests_grav;         /* gravity candidate tests (every pair force is formed) */
     int64_t tests_grav_target;  /* of those, the slots of lanes that have a target */
     int64_t list_slots;         /* lane slots of the list rows the moments and hydro passes walk */
+    /* Step counters since the last crk_set_timing (whether timing is on or
+     * not): KDK steps run, of those the steps replayed from a CUDA graph,
+     * host synchronisations inside host-sized steps and force evaluations
+     * (a replayed step has none; a crk_step call that replays graphs
+     * synchronises once at its end), and batches of replayed steps that
+     * overflowed a capacity and ran again host-sized. */
+    int64_t steps;
+    int64_t graph_steps;
+    int64_t host_syncs;
+    int64_t graph_overflows;
 } crk_timings;
 
 typedef struct crk_sim crk_sim;
@@ -204,7 +216,18 @@ int crk_forces(crk_sim *sim, crk_outputs *out);
  *   forces at (x, v + dt/2 a_old, u + dt/2 du_old);
  *   v += dt/2 a; u += dt/2 du    (gas u floored at u_floor each time).
  * If no forces exist yet, one force evaluation at the loaded state comes
- * first.  State stays on the device.  Errors as crk_forces. */
+ * first.  State stays on the device.
+ * With nsteps >= 3 (and no mesh, rebuild_every <= 1, timing off, not
+ * CRK_FLAG_NO_GRAPH) the first step runs host-sized and the others as
+ * replays of a CUDA graph of two steps (paper Sec. IV-A: the data stay on
+ * the GPU for the whole step; here no size reaches the host either): every
+ * leaf, pair, target-group and list count stays on the device against
+ * capacities taken from the first step with a margin, and the pair passes
+ * are persistent launches that drain a device work queue of (leaf, target
+ * group) items of every box.  The call synchronises once at its end; if a
+ * capacity was exceeded, the state of the replays' start is restored and
+ * those steps run again host-sized (results are the same either way).
+ * Errors as crk_forces. */
 int crk_step(crk_sim *sim, double dt, int nsteps);
 
 /* As crk_step with a per-box step size (dt: host array of nbox values). */
@@ -364,7 +387,9 @@ int crk_get_tree(crk_sim *sim, crk_tree *out);
  * Errors: CRK_EINVAL (bad precision, null tflops), CRK_ECUDA. */
 int crk_fma_peak(int precision, double *tflops, void *cuda_stream);
 
-/* Turns per-phase CUDA-event timing on (1) or off (0) and resets it. */
+/* Turns per-phase CUDA-event timing on (1) or off (0) and resets it and the
+ * step counters.  With timing on every step runs host-sized (the phase
+ * events are read back per step). */
 int crk_set_timing(crk_sim *sim, int enable);
 int crk_get_timings(crk_sim *sim, crk_timings *out);
 

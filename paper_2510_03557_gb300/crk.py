@@ -31,6 +31,7 @@ CRK_WENDLAND_C4 = 0
 CRK_MEM_HOST = 0
 CRK_MEM_DEVICE = 1
 CRK_FLAG_GRAVITY_PAIRS_ONCE = 2
+CRK_FLAG_NO_GRAPH = 4
 CRK_GRAVITY_GATHER = 0
 CRK_GRAVITY_PAIRS_ONCE = 1
 CRK_DM = 0
@@ -79,7 +80,8 @@ class Timings(ctypes.Structure):
                [(k, ctypes.c_int64) for k in ("calls", "pairs_hydro", "pairs_grav", "nleaves",
                                                "launches")] + [("pm_ms", ctypes.c_double)] + \
                [(k, ctypes.c_int64) for k in ("tests_hydro", "list_entries", "tests_grav",
-                                               "tests_grav_target", "list_slots")]
+                                               "tests_grav_target", "list_slots", "steps", "graph_steps",
+                                               "host_syncs", "graph_overflows")]
 
 
 class Tree(ctypes.Structure):

@@ -196,8 +196,10 @@ PassArgs pass_args(crk_sim *s)
     a.s = s->sa;
     a.lv = s->lv;
     a.hrow = s->hrow.as<uint32_t>();
+    a.hend = a.hrow ? a.hrow + 1 : nullptr;
     a.hcol = s->hcol.as<uint32_t>();
     a.grow = s->grow.as<uint32_t>();
+    a.gend = a.grow ? a.grow + 1 : nullptr;
     a.gcol = s->gcol.as<uint32_t>();
     a.hfr = s->hfr.as<float4>();
     a.gfr = s->gfr.as<float4>();
@@ -285,10 +287,18 @@ int upload_boxes(crk_sim *s)
     return CRK_OK;
 }
 
+// A host synchronisation inside a step (counted: a step captured as a graph
+// has none).
+#define HOST_SYNC(s)                         \
+    do {                                     \
+        ++(s)->host_syncs;                   \
+        CK(cudaStreamSynchronize((s)->st));  \
+    } while (0)
+
 int read_error(crk_sim *s)
 {
     CK(cudaMemcpyAsync(s->host_err, s->err.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, s->st));
-    CK(cudaStreamSynchronize(s->st));
+    HOST_SYNC(s);
     const int code = s->host_err[0], idx = s->host_err[1];
     if (code == CRK_ESINGULAR)
         return fail(CRK_ESINGULAR, "second-moment matrix of gas particle %d is singular", idx);
@@ -351,7 +361,7 @@ int build_tree(crk_sim *s, int mode = TREE_RULE)
                           first_bit, sc + 12, st);
         scan_exclusive_u32(s->flags.as<uint32_t>(), s->flag_scan.as<uint32_t>(), nlive, sc + 0, tmp, st);
         CK(cudaMemcpyAsync(s->host_scalars, sc, 14 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
+        HOST_SYNC(s);
         s->nleaf = (int)s->host_scalars[0];
         if (s->nleaf >= (1 << 26))  // the leaf-pair walk packs leaf indices into 26 bits
             return fail(CRK_EOVERFLOW, "%d leaves: at most 2^26 - 1", s->nleaf);
@@ -421,7 +431,7 @@ int build_tree(crk_sim *s, int mode = TREE_RULE)
     scan_exclusive_u32(gc, go, s->nleaf, sc + 3, tmp, st);
     scan_exclusive_u32(gc + nl, go + nl, s->nleaf, sc + 4, tmp, st);
     CK(cudaMemcpyAsync(s->host_scalars + 1, sc + 1, 7 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    HOST_SYNC(s);
     const bool pair_overflow = !scratch || s->host_scalars[7] != 0;
     if (scratch && pair_overflow) s->pair_two_pass_left = 16;
     s->npair_h = s->host_scalars[1];
@@ -484,7 +494,7 @@ static int size_hydro_lists(crk_sim *s, PassArgs &a, bool want_counts, bool use_
     uint32_t *sc = s->scalars.as<uint32_t>();
     scan_exclusive_u32(a.nl_len, a.nl_row, a.n_ggas, sc + 5, s->scan_tmp.as<uint32_t>(), st);
     CK(cudaMemcpyAsync(s->host_scalars + 5, sc + 5, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    HOST_SYNC(s);
     s->nl_rows = s->host_scalars[5];
     const size_t entries = (size_t)std::max<int64_t>(s->nl_rows, 1) * 32u;
     RET(s->nl_j.ensure(entries * 4));
@@ -505,7 +515,7 @@ static int density_pass(crk_sim *s, PassArgs &a, bool want_counts)
     launch_hlist_fill(a, mixed, s->cap, want_counts, st);
     if (a.nl_bound) {
         CK(cudaMemcpyAsync(s->host_scalars + 6, a.nl_retry, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
+        HOST_SYNC(s);
         if (s->host_scalars[6]) {
             RET(size_hydro_lists(s, a, want_counts, false));
             if (a.census) CK(cudaMemsetAsync(a.census, 0, 2 * sizeof(unsigned long long), st));
@@ -592,6 +602,7 @@ int run_step(crk_sim *s, const double *dt_per_box, bool want_counts)
         s->launches += launches_so_far() - launches0;
     }
     s->have_forces = true;
+    if (dt_per_box) ++s->steps_run;
     return CRK_OK;
 }
 
@@ -718,7 +729,7 @@ extern "C" int crk_create(const crk_params *params, void *cuda_stream, crk_sim *
     if (params->kernel != CRK_WENDLAND_C4) return fail(CRK_EINVAL, "unsupported kernel");
     if (params->cm_level < 0 || params->cm_level > 10) return fail(CRK_EINVAL, "cm_level in [0, 10]");
     if (params->rebuild_every < 0) return fail(CRK_EINVAL, "rebuild_every must be >= 0");
-    if (params->flags & ~CRK_FLAG_GRAVITY_PAIRS_ONCE)
+    if (params->flags & ~(CRK_FLAG_GRAVITY_PAIRS_ONCE | CRK_FLAG_NO_GRAPH))
         return fail(CRK_EINVAL, "unknown flags bits 0x%x", params->flags);
     if (params->pm_grid != 0 && (params->pm_grid < 4 || params->pm_grid > 1024 || params->pm_grid % 2))
         return fail(CRK_EINVAL, "pm_grid must be 0 or an even number in [4, 1024] (got %d)", params->pm_grid);
@@ -814,6 +825,249 @@ extern "C" int crk_forces(crk_sim *s, crk_outputs *out)
     return CRK_OK;
 }
 
+// ------------------------------------------------------- graph-captured steps
+// A KDK step with every size kept on the device: leaves, leaf pairs, target
+// groups and list rows are counted by scans into the device sizes block and
+// every launch after them is sized by a capacity fixed on the host (from the
+// last host-sized step, with a margin) and reads the true count on the
+// device; the pass kernels are persistent launches that drain a device work
+// queue of (leaf, target group) items of every box.  Leaf-pair rows stay in
+// the fixed-capacity rows the walk fills (no packing), hydro list rows are
+// sized from the last step's counts.  Nothing is read back, so the step can
+// be captured into a CUDA graph; an overflow of a capacity is recorded on the
+// device (and zeroes the counts the rest of the step launches over).
+static int run_step_ds(crk_sim *s)
+{
+    cudaStream_t st = s->st;
+    const int64_t n = s->n;
+    const int mixed = s->mixed ? 1 : 0;
+    const BoxDev *bd = s->boxes_d.as<BoxDev>();
+    uint32_t *dz = s->dz.as<uint32_t>();
+    uint32_t *tmp = s->scan_tmp.as<uint32_t>();
+    const int capL = s->ds_cap_leaf;
+    const size_t nl = (size_t)capL;
+    const uint32_t capI = s->ds_cap_items;
+    CK(cudaMemsetAsync(dz + DZ_QUEUE, 0, kQueueSlots * sizeof(uint32_t), st));
+    CK(cudaMemsetAsync(dz + DZ_PAIR_OVF, 0, sizeof(uint32_t), st));
+    launch_kick_drift(s->sa, bd, n, s->nfloor.as<unsigned long long>(), st);
+    // S1: keys, sort (the bits the last host-sized sort chose), leaves
+    launch_morton_keys(s->sa, bd, n, s->slot_bits, s->keys.as<uint64_t>(), s->vals.as<uint32_t>(), st);
+    int first_bit = 0;
+    if (s->slot_bits == 0 && s->nbox == 1) first_bit = std::max(s->boxes[0].cm_shift - 3 * s->sort_levels, 0);
+    uint64_t *ko;
+    uint32_t *vo;
+    radix_sort_u64(s->keys.as<uint64_t>(), s->vals.as<uint32_t>(), s->keys_alt.as<uint64_t>(),
+                   s->vals_alt.as<uint32_t>(), n, s->counts.as<uint32_t>(), tmp, first_bit, 64, st, &ko, &vo);
+    launch_leaf_flags(ko, s->slot_bits, bd, n, s->cap, s->flags.as<uint32_t>(), first_bit, dz + DZ_STATS, st);
+    scan_exclusive_u32(s->flags.as<uint32_t>(), s->flag_scan.as<uint32_t>(), n, dz + DZ_NLEAF_RAW, tmp, st);
+    launch_ds_check(dz, 0, (uint32_t)capL, nullptr, st);
+    const uint32_t *nld = dz + DZ_NLEAF;
+    launch_leaf_setup(s->flags.as<uint32_t>(), s->flag_scan.as<uint32_t>(), n, capL, s->lv, st, nld);
+    launch_leaf_kd_order(s->sa, s->lv, capL, vo, st, nld);
+    launch_permute(s->sa, s->sb, vo, n, st);
+    std::swap(s->sa, s->sb);
+    for (int k = 0; k < 17; ++k) std::swap(s->stA[k], s->stB[k]);
+    launch_leaf_bounds(s->sa, bd, s->lv, capL, mixed, s->pm.p, s->nd, st, nld);
+    // S2: hierarchy over the capacity, pair rows of fixed capacity, groups
+    Nodes nd = s->nd;
+    launch_build_nodes(nd, capL, st);
+    uint32_t *scol_h = s->pscr_col.as<uint32_t>(), *scol_g = scol_h + nl * kPairCapH;
+    float4 *sfr_h = s->pscr_fr.as<float4>(), *sfr_g = sfr_h + nl * kPairCapH;
+    launch_pair_scratch(nd, s->lv, bd, capL, 1, s->hcnt.as<uint32_t>(), kPairCapH, scol_h, sfr_h,
+                        s->pscr_st.as<uint32_t>(), dz + DZ_PAIR_OVF, st, nullptr, nld);
+    launch_pair_scratch(nd, s->lv, bd, capL, 0, s->gcnt.as<uint32_t>(), kPairCapG, scol_g, sfr_g, nullptr,
+                        dz + DZ_PAIR_OVF, st, nullptr, nld);
+    launch_ds_check(dz, 1, 0u, nullptr, st);
+    uint32_t *hb = s->ds_row[0].as<uint32_t>(), *he = s->ds_row[1].as<uint32_t>();
+    uint32_t *gb = s->ds_row[2].as<uint32_t>(), *ge = s->ds_row[3].as<uint32_t>();
+    launch_fixed_rows(s->hcnt.as<uint32_t>(), capL, kPairCapH, hb, he, st);
+    launch_fixed_rows(s->gcnt.as<uint32_t>(), capL, kPairCapG, gb, ge, st);
+    uint32_t *gc = s->grp_cnt.as<uint32_t>(), *go = s->grp_off.as<uint32_t>();
+    launch_group_count(s->lv, capL, 1, gc, st, nld);
+    launch_group_count(s->lv, capL, 0, gc + nl, st, nld);
+    scan_exclusive_u32(gc, go, capL, dz + DZ_GGAS, tmp, st);
+    scan_exclusive_u32(gc + nl, go + nl, capL, dz + DZ_GALL, tmp, st);
+    launch_ds_check(dz, 2, 0u, nullptr, st);
+    launch_group_fill(s->lv, capL, 1, go, s->grp_gas.as<uint2>(), st, nld);
+    launch_group_fill(s->lv, capL, 0, go + nl, s->grp_all.as<uint2>(), st, nld);
+    // the passes over device work queues
+    PassArgs a = pass_args(s);
+    a.nleaf = capL;
+    a.hrow = hb;
+    a.hend = he;
+    a.hcol = scol_h;
+    a.hfr = sfr_h;
+    a.hsj = s->pscr_st.as<uint32_t>();
+    a.grow = gb;
+    a.gend = ge;
+    a.gcol = scol_g;
+    a.gfr = sfr_g;
+    a.n_ggas = capI;
+    a.n_gall = capI;
+    a.ggas_dev = dz + DZ_GGAS;
+    a.gall_dev = dz + DZ_GALL;
+    a.queue = dz + DZ_QUEUE;
+    a.nbr_count = nullptr;
+    a.nbr_hash = nullptr;
+    a.grav_count = nullptr;
+    a.grav_hash = nullptr;
+    a.nl_cnt = s->nl_cnt.as<uint32_t>();
+    a.nl_len = s->nl_len.as<uint32_t>();
+    a.nl_row = s->nl_row.as<uint32_t>();
+    a.nl_j = s->nl_j.as<uint32_t>();
+    a.nl_bound = 1;
+    launch_records(a, mixed, st);
+    // S3: lists (rows from the last step's counts) with the density in the fill
+    CK(cudaMemsetAsync(a.nl_len, 0, (size_t)capI * sizeof(uint32_t), st));
+    CK(cudaMemsetAsync(a.nl_retry, 0, sizeof(uint32_t), st));
+    launch_hlist_bound(a, s->cnt_by_id.as<uint32_t>(), st);
+    scan_exclusive_u32(a.nl_len, a.nl_row, capI, dz + DZ_ROWS, tmp, st);
+    launch_ds_check(dz, 3, s->ds_cap_rows, nullptr, st);
+    launch_hlist_fill(a, mixed, s->cap, false, st);
+    launch_ds_check(dz, 4, 0u, a.nl_retry, st);
+    launch_keep_counts(a, s->cnt_by_id.as<uint32_t>(), st);
+    // S4-S8
+    launch_moments(a, mixed, s->cap, st);
+    launch_hydro(a, mixed, s->cap, st);
+    launch_gravity(a, mixed, s->cap, false, st);
+    launch_final_kick(a, mixed, s->nfloor.as<unsigned long long>(), st);
+    return CRK_OK;
+}
+
+// Steps a handle can run as graph replays: the handle's own particles on a
+// stream of its own, every leaf sorted every step, no mesh, no service pool.
+static bool graph_eligible(const crk_sim *s)
+{
+    return !(s->prm.flags & CRK_FLAG_NO_GRAPH) && !s->timing && s->prm.pm_grid == 0 && !s->is_pool &&
+           s->prm.rebuild_every <= 1 && s->n > 0 && s->n_dead == 0 && s->nleaf > 0;
+}
+
+// Capacities of the device-sized step from the last host-sized step, and
+// every buffer it uses grown to them (before a capture: no allocation may
+// happen inside one).
+static int ds_prepare(crk_sim *s)
+{
+    const int64_t n = s->n;
+    const double m = s->ds_margin;
+    s->ds_cap_leaf = (int)std::min<int64_t>(n, (int64_t)(m * s->nleaf) + 1024);
+    s->ds_cap_items = (uint32_t)std::min<int64_t>((int64_t)4 * s->ds_cap_leaf, s->ds_cap_leaf + n / 32 + 64);
+    s->ds_cap_rows = (uint32_t)std::max<int64_t>((int64_t)(m * s->nl_rows) + 1024, 1024);
+    const size_t nl = (size_t)s->ds_cap_leaf, ni = s->ds_cap_items;
+    RET(s->dz.ensure(DZ_WORDS * sizeof(uint32_t)));
+    for (int k = 0; k < 4; ++k) RET(s->ds_row[k].ensure(nl * sizeof(uint32_t)));
+    RET(s->pscr_col.ensure(nl * (kPairCapH + kPairCapG) * sizeof(uint32_t)));
+    RET(s->pscr_fr.ensure(nl * (kPairCapH + kPairCapG) * sizeof(float4)));
+    RET(s->pscr_st.ensure(nl * kPairCapH * sizeof(uint32_t)));
+    RET(s->grp_cnt.ensure(nl * 4 * 2));
+    RET(s->grp_off.ensure(nl * 4 * 2));
+    RET(s->grp_gas.ensure(ni * sizeof(uint2)));
+    RET(s->grp_all.ensure(ni * sizeof(uint2)));
+    RET(s->nl_cnt.ensure((size_t)std::max<int64_t>(n, 1) * 4));
+    RET(s->nl_len.ensure(ni * 4));
+    RET(s->nl_row.ensure(ni * 4));
+    RET(s->nl_j.ensure((size_t)s->ds_cap_rows * 32u * 4u));
+    const size_t words = (size_t)n;
+    RET(s->ds_snap.ensure(words * (13 * sizeof(double) + 1 + 4 + 4 + 1)));
+    if (!s->cap_st) CK(cudaStreamCreateWithFlags(&s->cap_st, cudaStreamNonBlocking));
+    return CRK_OK;
+}
+
+// Two device-sized steps captured into the handle's graph (the state buffers
+// swap at each sort, so two steps bring them back).  The capture runs on a
+// stream of the library's own, so that handles on the legacy default stream
+// can replay graphs too.
+static int ds_capture(crk_sim *s)
+{
+    if (s->graph) {
+        cudaGraphExecDestroy(s->graph);
+        s->graph = nullptr;
+    }
+    cudaStream_t user = s->st;
+    s->st = s->cap_st;
+    const int64_t l0 = launches_so_far();
+    cudaError_t e = cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal);
+    int rc = e == cudaSuccess ? CRK_OK : fail(CRK_ECUDA, "stream capture failed: %s", cudaGetErrorString(e));
+    if (rc == CRK_OK) rc = run_step_ds(s);
+    if (rc == CRK_OK) rc = run_step_ds(s);
+    cudaGraph_t g = nullptr;
+    if (e == cudaSuccess) {
+        cudaError_t e2 = cudaStreamEndCapture(s->st, &g);
+        if (rc == CRK_OK && e2 != cudaSuccess)
+            rc = fail(CRK_ECUDA, "stream capture failed: %s", cudaGetErrorString(e2));
+    }
+    s->st = user;
+    if (rc == CRK_OK) {
+        e = cudaGraphInstantiate(&s->graph, g, 0);
+        if (e != cudaSuccess) {
+            s->graph = nullptr;
+            rc = fail(CRK_ECUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+        }
+    }
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    s->graph_launch_nodes = (launches_so_far() - l0) / 2;
+    return rc;
+}
+
+// Copies the state arrays (sorted order) to or from the batch snapshot.
+static int ds_snapshot(crk_sim *s, bool save)
+{
+    const size_t n = (size_t)s->n;
+    char *p = s->ds_snap.as<char>();
+    double *dp[13] = {s->sa.x, s->sa.y, s->sa.z, s->sa.vx, s->sa.vy, s->sa.vz, s->sa.u, s->sa.m, s->sa.h,
+                      s->sa.ax, s->sa.ay, s->sa.az, s->sa.du};
+    auto cp = [&](void *dev, size_t bytes) -> int {
+        CK(cudaMemcpyAsync(save ? (void *)p : dev, save ? dev : (void *)p, bytes, cudaMemcpyDeviceToDevice, s->st));
+        p += bytes;
+        return CRK_OK;
+    };
+    for (double *d : dp) RET(cp(d, n * sizeof(double)));
+    RET(cp(s->sa.species, n));
+    RET(cp(s->sa.slot, n * 4));
+    RET(cp(s->sa.id, n * 4));
+    RET(cp(s->sa.bin, n));
+    return CRK_OK;
+}
+
+// nsteps KDK steps after the first ones: pairs of steps replayed from the
+// captured graph, with one host synchronisation per call to read the
+// overflow bits and the error word.  After an overflow the state of the
+// batch start is restored, the capacities grow and the steps run host-sized.
+static int step_graph(crk_sim *s, const double *dt, int nsteps)
+{
+    const int pairs = nsteps / 2;
+    // the step sizes every replay uses live in the device box table
+    for (int b = 0; b < s->nbox; ++b) {
+        s->boxes[b].dt = dt[b];
+        s->boxes[b].hdt = 0.5 * dt[b];
+    }
+    RET(upload_boxes(s));
+    RET(ds_prepare(s));
+    RET(ds_capture(s));
+    RET(reset_error(s));
+    RET(ds_snapshot(s, true));
+    CK(cudaMemsetAsync(s->dz.p, 0, DZ_WORDS * sizeof(uint32_t), s->st));
+    for (int k = 0; k < pairs; ++k) CK(cudaGraphLaunch(s->graph, s->st));
+    note_launches((int)(2 * pairs * s->graph_launch_nodes));
+    uint32_t ovf = 0;
+    CK(cudaMemcpyAsync(s->host_scalars + 15, s->dz.as<uint32_t>() + DZ_OVF, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                       s->st));
+    RET(read_error(s));
+    ovf = s->host_scalars[15];
+    s->tree_valid = false;  // the host's leaf and list sizes are those of the last host-sized step
+    if (ovf == 0) {
+        s->graph_steps += 2 * pairs;
+        s->steps_run += 2 * pairs;
+    } else {
+        ++s->graph_overflows;
+        s->ds_margin *= 1.5;
+        RET(ds_snapshot(s, false));
+        for (int k = 0; k < 2 * pairs; ++k) RET(run_step(s, dt, false));
+    }
+    for (int k = 2 * pairs; k < nsteps; ++k) RET(run_step(s, dt, false));
+    return CRK_OK;
+}
+
 extern "C" int crk_step_boxes(crk_sim *s, const double *dt, int nsteps)
 {
     if (!s || !dt) return fail(CRK_EINVAL, "null argument");
@@ -823,6 +1077,12 @@ extern "C" int crk_step_boxes(crk_sim *s, const double *dt, int nsteps)
     CK(cudaSetDevice(s->device));
     if (s->n == 0) return CRK_OK;
     if (!s->have_forces) RET(run_step(s, nullptr, false));
+    // the first step host-sized (it sizes the capacities), the rest replayed
+    if (nsteps >= 3 && graph_eligible(s)) {
+        RET(run_step(s, dt, false));
+        if (graph_eligible(s)) return step_graph(s, dt, nsteps - 1);
+        nsteps -= 1;
+    }
     for (int k = 0; k < nsteps; ++k) RET(run_step(s, dt, false));
     return CRK_OK;
 }
@@ -876,13 +1136,13 @@ static int run_substep(crk_sim *s, int sub, int depth, double dt_long, double et
     launch_group_select(s->grp_all.as<uint2>(), s->n_gall, fh, keep, pos, sc + 11, tmp, gG, nullptr, st);
     CK(cudaMemcpyAsync(s->host_scalars + 8, sc + 8, 2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(s->host_scalars + 11, sc + 11, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    HOST_SYNC(s);
     const uint32_t nD = s->host_scalars[8], nM = s->host_scalars[9], nG = s->host_scalars[11];
     // the hydro groups are taken from the moments groups, so that each keeps
     // the list row the fill pass wrote for it
     launch_group_select(gM, nM, fh, keep, pos, sc + 10, tmp, gH, s->bmap[1].as<uint32_t>(), st);
     CK(cudaMemcpyAsync(s->host_scalars + 10, sc + 10, sizeof(uint32_t), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    HOST_SYNC(s);
     const uint32_t nH = s->host_scalars[10];
 
     PassArgs a = pass_args(s);
@@ -1087,6 +1347,7 @@ extern "C" int crk_set_timing(crk_sim *s, int enable)
     s->total_ms = 0;
     s->calls = 0;
     s->launches = 0;
+    s->host_syncs = s->steps_run = s->graph_steps = s->graph_overflows = 0;
     return CRK_OK;
 }
 
@@ -1267,6 +1528,10 @@ extern "C" int crk_get_timings(crk_sim *s, crk_timings *t)
     t->tests_grav = (int64_t)s->census_h[2];
     t->tests_grav_target = (int64_t)s->census_h[3];
     t->list_slots = 32 * s->census_rows;
+    t->steps = s->steps_run;
+    t->graph_steps = s->graph_steps;
+    t->host_syncs = s->host_syncs;
+    t->graph_overflows = s->graph_overflows;
     return CRK_OK;
 }
 
@@ -1334,7 +1599,8 @@ extern "C" int crk_destroy(crk_sim *s)
                     &s->in_stage, &s->grp_cnt, &s->grp_off, &s->grp_gas, &s->grp_all, &s->hfr, &s->gfr,
                     &s->nl_j, &s->nl_row, &s->nl_len, &s->nl_cnt, &s->hsj, &s->fof_par, &s->acc_pm,
                     &s->bflag, &s->bgrp[0], &s->bgrp[1], &s->bgrp[2], &s->bgrp[3], &s->bmap[0],
-                    &s->bmap[1], &s->bkeep, &s->bpos, &s->bcount, &s->cnt_by_id, &s->nl_retry, &s->census, &s->pscr_col, &s->pscr_fr, &s->pscr_st};
+                    &s->bmap[1], &s->bkeep, &s->bpos, &s->bcount, &s->cnt_by_id, &s->nl_retry, &s->census, &s->pscr_col, &s->pscr_fr, &s->pscr_st,
+                    &s->dz, &s->ds_row[0], &s->ds_row[1], &s->ds_row[2], &s->ds_row[3], &s->ds_snap};
     for (DBuf *b : bufs) b->release();
     pm_release(s);
     for (int k = 0; k < 3; ++k) {
@@ -1352,6 +1618,8 @@ extern "C" int crk_destroy(crk_sim *s)
             if (s->ev[ph][w]) cudaEventDestroy(s->ev[ph][w]);
     if (s->ev_all[0]) cudaEventDestroy(s->ev_all[0]);
     if (s->ev_all[1]) cudaEventDestroy(s->ev_all[1]);
+    if (s->graph) cudaGraphExecDestroy(s->graph);
+    if (s->cap_st) cudaStreamDestroy(s->cap_st);
     if (s->host_scalars) cudaFreeHost(s->host_scalars);
     if (s->host_err) cudaFreeHost(s->host_err);
     delete s;

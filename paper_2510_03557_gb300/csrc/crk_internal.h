@@ -80,8 +80,10 @@ struct PassArgs {
     const BoxDev *boxes;
     State s;
     Leaves lv;
-    const uint32_t *hrow, *hcol;   // hydro list
-    const uint32_t *grow, *gcol;   // gravity list
+    // leaf-pair lists: row I of a list holds entries [row[I], end[I]) of its
+    // columns (CSR: end = row + 1; rows of fixed capacity: end = row + count)
+    const uint32_t *hrow, *hend, *hcol;   // hydro list
+    const uint32_t *grow, *gend, *gcol;   // gravity list
     const float4 *hfr, *gfr;       // per-entry leaf-pair frames of the two lists
     const uint32_t *hsj;           // hydro list: first sorted particle of each entry's leaf J
     void *pm;                // R4[n]
@@ -115,6 +117,10 @@ struct PassArgs {
     const uint2 *ggas;       // warp work items (leaf, first offset) of gas leaves
     const uint2 *gall;       // warp work items of all leaves
     uint32_t n_ggas, n_gall;
+    // device-side item counts (null: n_ggas / n_gall above) and the work-queue
+    // counters of the persistent pass launches (null: one warp per item)
+    const uint32_t *ggas_dev, *gall_dev;
+    uint32_t *queue;
     int *err;                // [0] code, [1] smallest original index of a failing particle
     unsigned long long *nfloor;  // floor events of the u predictor
     // gravity of the mixed form with each unordered pair evaluated once and
@@ -150,22 +156,27 @@ void launch_permute(const State &src, const State &dst, const uint32_t *perm, in
                     cudaStream_t st);
 void launch_leaf_flags(const uint64_t *keys, int slot_bits, const BoxDev *boxes, int64_t n,
                        int cap, uint32_t *flags, int first_bit, uint32_t *stats, cudaStream_t st);
+// nl_dev (optional): the leaf count on the device, nleaf then being the
+// capacity of the leaf arrays (the launch size); slots beyond the count are
+// left empty (no particles, an inverted box, no rows, no groups).
 void launch_leaf_kd_order(const State &unsorted, const Leaves &lv, int nleaf, uint32_t *perm,
-                          cudaStream_t st);
+                          cudaStream_t st, const uint32_t *nl_dev = nullptr);
 void launch_leaf_setup(const uint32_t *flags, const uint32_t *scan, int64_t n, int nleaf,
-                       Leaves lv, cudaStream_t st);
+                       Leaves lv, cudaStream_t st, const uint32_t *nl_dev = nullptr);
 void launch_leaf_bounds(const State &s, const BoxDev *boxes, Leaves lv, int nleaf, int mixed,
-                        void *pm, Nodes nd, cudaStream_t st);
+                        void *pm, Nodes nd, cudaStream_t st, const uint32_t *nl_dev = nullptr);
 void launch_build_nodes(Nodes &nd, int nleaf, cudaStream_t st);
-void launch_group_count(const Leaves &lv, int nleaf, int gas_only, uint32_t *counts, cudaStream_t st);
+void launch_group_count(const Leaves &lv, int nleaf, int gas_only, uint32_t *counts, cudaStream_t st,
+                        const uint32_t *nl_dev = nullptr);
 void launch_group_fill(const Leaves &lv, int nleaf, int gas_only, const uint32_t *off, uint2 *groups,
-                       cudaStream_t st);
+                       cudaStream_t st, const uint32_t *nl_dev = nullptr);
 // mask (optional): leaves without a 1 get an empty row
 void launch_pair_count(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, int nleaf,
                        int hydro, uint32_t *counts, cudaStream_t st, const uint8_t *mask = nullptr);
 void launch_pair_scratch(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, int nleaf, int hydro,
                          uint32_t *counts, uint32_t cap, uint32_t *col, float4 *frame, uint32_t *start,
-                         uint32_t *overflow, cudaStream_t st, const uint8_t *mask = nullptr);
+                         uint32_t *overflow, cudaStream_t st, const uint8_t *mask = nullptr,
+                         const uint32_t *nl_dev = nullptr);
 void launch_pair_compact(int nleaf, uint32_t cap, const uint32_t *counts, const uint32_t *row,
                          const uint32_t *scol, const float4 *sframe, const uint32_t *sstart, uint32_t *col,
                          float4 *frame, uint32_t *start, cudaStream_t st);
@@ -212,6 +223,35 @@ void launch_retire_slot(const State &s, int64_t n, uint32_t from, uint32_t to, c
 void launch_load_state(const State &s, int64_t n, const double *pos, const double *vel,
                        const double *mass, const double *u, const double *h,
                        const uint8_t *species, const uint32_t *slot_of, cudaStream_t st);
+
+// ---- steps sized on the device (integrate.cu) ----
+// Words of the device sizes block of a step whose sizes never reach the host
+// (the CUDA-graph step): counts written by scans, the overflow bits, and the
+// work-queue counters of the persistent pass launches.
+enum DevSize {
+    DZ_NLEAF_RAW = 0,   // leaves the sort made
+    DZ_NLEAF = 1,       // leaves the step uses (0 after an overflow)
+    DZ_GGAS = 2,        // gas target groups (0 after an overflow)
+    DZ_GALL = 3,        // all target groups (0 after an overflow)
+    DZ_ROWS = 4,        // hydro list rows the groups need
+    DZ_OVF = 5,         // overflow bits: 1 leaves, 2 pair rows, 4 list rows, 8 a list outgrew its rows
+    DZ_PAIR_OVF = 6,    // set by the pair walk when a leaf has more pairs than a row holds
+    DZ_STATS = 7,       // 2 words: statistics of the leaf cut (unused here)
+    DZ_QUEUE = 16,      // kQueueSlots words: work-queue heads
+    DZ_WORDS = 48
+};
+constexpr int kQueueSlots = 16;
+// stage 0 after the leaf scan (cap: leaf capacity), 1 after the pair walk,
+// 2 after the group scans, 3 after the list-row scan (cap: row capacity), 4
+// after the list fill (flag: the fill's retry word).  An overflow zeroes the
+// counts the rest of the step launches over, so that it touches nothing
+// beyond its buffers; the host then restores the state and steps again with
+// larger buffers.
+void launch_ds_check(uint32_t *dz, int stage, uint32_t cap, const uint32_t *flag, cudaStream_t st);
+// Row begin and end of leaves in rows of fixed capacity: beg = L * cap, end =
+// beg + min(count, cap), for L < nleaf (the capacity of the leaf arrays).
+void launch_fixed_rows(const uint32_t *counts, int nleaf, uint32_t cap, uint32_t *beg, uint32_t *end,
+                       cudaStream_t st);
 
 // ---- hierarchical time steps (bins.cu) ----
 void launch_kick_drift_bins(const State &s, const BoxDev *boxes, int64_t n, int sub, int depth, double d,

@@ -360,7 +360,47 @@ __global__ void retire_slot_k(uint32_t *slot_of, int64_t n, uint32_t from, uint3
     if (k < n && slot_of[k] == from) slot_of[k] = to;
 }
 
+__global__ void ds_check_k(uint32_t *dz, int stage, uint32_t cap, const uint32_t *flag)
+{
+    uint32_t ovf = dz[DZ_OVF];
+    if (stage == 0 && dz[DZ_NLEAF_RAW] > cap) ovf |= 1u;
+    if (stage == 1 && dz[DZ_PAIR_OVF]) ovf |= 2u;
+    if (stage == 3 && dz[DZ_ROWS] > cap) ovf |= 4u;
+    if (stage == 4 && flag && *flag) ovf |= 8u;
+    dz[DZ_OVF] = ovf;
+    if (stage == 0) dz[DZ_NLEAF] = ovf ? 0u : dz[DZ_NLEAF_RAW];
+    if (ovf) {
+        dz[DZ_NLEAF] = 0u;
+        dz[DZ_GGAS] = 0u;
+        dz[DZ_GALL] = 0u;
+    }
+}
+
+__global__ void fixed_rows_k(const uint32_t *__restrict__ counts, int nleaf, uint32_t cap, uint32_t *beg,
+                             uint32_t *end)
+{
+    const int L = blockIdx.x * blockDim.x + threadIdx.x;
+    if (L >= nleaf) return;
+    const uint32_t c = counts[L];
+    beg[L] = (uint32_t)L * cap;
+    end[L] = (uint32_t)L * cap + (c < cap ? c : cap);
+}
+
 }  // namespace
+
+void launch_ds_check(uint32_t *dz, int stage, uint32_t cap, const uint32_t *flag, cudaStream_t st)
+{
+    ds_check_k<<<1, 1, 0, st>>>(dz, stage, cap, flag);
+    note_launches(1);
+}
+
+void launch_fixed_rows(const uint32_t *counts, int nleaf, uint32_t cap, uint32_t *beg, uint32_t *end,
+                       cudaStream_t st)
+{
+    if (nleaf <= 0) return;
+    fixed_rows_k<<<nblocks(nleaf), kT, 0, st>>>(counts, nleaf, cap, beg, end);
+    note_launches(1);
+}
 
 void launch_set_forces(const State &s, int64_t n, const double *acc, const double *du, cudaStream_t st)
 {

@@ -477,6 +477,37 @@ __device__ __forceinline__ uint32_t stage_cull(Vec4<R> *tile, uint8_t *slot, flo
 
 __device__ __forceinline__ uint32_t chunk_mask(uint32_t K) { return K >= 128u ? 0xfu : (1u << ((K + 31u) / 32u)) - 1u; }
 
+// Work items of a warp pass: groups of up to 32 targets of one leaf.  With
+// no queue the launch has one warp per item (n items known on the host).
+// With a queue the launch is persistent (a fixed grid filling the SMs): each
+// warp takes the next item from a device counter until the item count, read
+// on the device, is exhausted, so a pass over every box of a batch needs
+// neither the host to know how many items there are nor a launch sized to
+// them, and uneven boxes share the SMs item by item.
+enum QueueSlot { Q_HCOUNT, Q_HFILL, Q_DONLY, Q_HBOUND, Q_KEEP, Q_DENS, Q_MOM, Q_HYDRO, Q_GRAV, Q_GSYM, Q_N };
+static_assert(Q_N <= kQueueSlots, "work-queue slots of the device sizes block");
+
+template <class F>
+__device__ __forceinline__ void for_each_item(uint32_t n_host, const uint32_t *n_dev, uint32_t *queue, int slot,
+                                              F &&body)
+{
+    const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
+    if (!queue) {
+        const uint32_t gi = blockIdx.x * kWarps + w;
+        if (gi < (n_dev ? *n_dev : n_host)) body(gi);
+        return;
+    }
+    const uint32_t n = n_dev ? *n_dev : n_host;
+    for (;;) {
+        uint32_t gi = 0;
+        if (lane == 0) gi = atomicAdd(queue + slot, 1u);
+        gi = __shfl_sync(0xffffffffu, gi, 0);
+        if (gi >= n) break;
+        body(gi);
+        __syncwarp();
+    }
+}
+
 // The warp's target group: up to 32 consecutive particles of leaf I.
 struct Group {
     int I;
@@ -685,8 +716,7 @@ __global__ void __launch_bounds__(kBlock) hlist_count_k(PassArgs a)
     using R4 = Vec4<R>;
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-    const uint32_t gi = blockIdx.x * kWarps + w;
-    if (gi >= a.n_ggas) return;
+    for_each_item(a.n_ggas, a.ggas_dev, a.queue, Q_HCOUNT, [&](const uint32_t gi) {
     unsigned char *base = smem + (size_t)w * hlist_warp_bytes<R, JMAX>();
     R4 *tile = reinterpret_cast<R4 *>(base);
     float *h2j = reinterpret_cast<float *>(tile + JMAX);
@@ -703,7 +733,7 @@ __global__ void __launch_bounds__(kBlock) hlist_count_k(PassArgs a)
     const WarpBox wb = warp_box(px, py, pz, G.act);
     const float Hw = warp_max(G.act ? (float)ht.H : 0.f);
     uint32_t cnt = 0;
-    const RowOrder order(a.hrow[I + 1] - a.hrow[I]);
+    const RowOrder order(a.hend[I] - a.hrow[I]);
     for (uint32_t t = 0; t < order.n; ++t) {
         const uint32_t p = a.hrow[I] + order.at(t);
         uint32_t sJ;
@@ -720,6 +750,7 @@ __global__ void __launch_bounds__(kBlock) hlist_count_k(PassArgs a)
     const uint32_t len = __reduce_max_sync(0xffffffffu, cnt);
     if (lane == 0) a.nl_len[gi] = len;
     if (G.act) a.nl_cnt[i] = cnt;
+    });
 }
 
 // V = m/rho, P = (gamma-1) rho u^, c = sqrt(gamma (gamma-1) u^) into the
@@ -750,8 +781,7 @@ __global__ void __launch_bounds__(kBlock) hlist_fill_k(PassArgs a)
     using R4 = Vec4<R>;
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-    const uint32_t gi = blockIdx.x * kWarps + w;
-    if (gi >= a.n_ggas) return;
+    for_each_item(a.n_ggas, a.ggas_dev, a.queue, Q_HFILL, [&](const uint32_t gi) {
     unsigned char *base = smem + (size_t)w * hfill_warp_bytes<R, JMAX>();
     R4 *tile = reinterpret_cast<R4 *>(base);
     float *h2j = reinterpret_cast<float *>(tile + JMAX);
@@ -778,7 +808,7 @@ __global__ void __launch_bounds__(kBlock) hlist_fill_k(PassArgs a)
     uint32_t k = 0;
     uint64_t tested = 0;  // staged candidates of the visits (census)
     R rho = 0;  // without neighbour counts the fill pass also forms the density
-    const RowOrder order(a.hrow[I + 1] - prow);
+    const RowOrder order(a.hend[I] - prow);
     for (uint32_t t = 0; t < order.n; ++t) {
         const uint32_t p = prow + order.at(t);
         uint32_t sJ;
@@ -846,6 +876,7 @@ __global__ void __launch_bounds__(kBlock) hlist_fill_k(PassArgs a)
         set_error(a.err, CRK_EOVERFLOW, a.s.id[i]);
     }
     if (!COUNT && G.act) density_out<R>(a, i, ri, rho);
+    });
 }
 
 // Density alone (no lists) of gas groups whose particles only feed their
@@ -857,8 +888,7 @@ __global__ void __launch_bounds__(kBlock) density_only_k(PassArgs a)
     using R4 = Vec4<R>;
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-    const uint32_t gi = blockIdx.x * kWarps + w;
-    if (gi >= a.n_ggas) return;
+    for_each_item(a.n_ggas, a.ggas_dev, a.queue, Q_DONLY, [&](const uint32_t gi) {
     R4 *tile = reinterpret_cast<R4 *>(smem + (size_t)w * hlist_warp_bytes<R, JMAX>());
     uint8_t *tslot = reinterpret_cast<uint8_t *>(reinterpret_cast<float *>(tile + JMAX) + JMAX);
     const Group G = load_group(a.lv, a.ggas, gi, lane);
@@ -876,7 +906,7 @@ __global__ void __launch_bounds__(kBlock) density_only_k(PassArgs a)
     const float Rc = Hw * 1.0001f + 1e-6f * (float)Ld;
     R rho = 0;
     const uint32_t prow = a.hrow[I];
-    const RowOrder order(a.hrow[I + 1] - prow);
+    const RowOrder order(a.hend[I] - prow);
     for (uint32_t t = 0; t < order.n; ++t) {
         const uint32_t p = prow + order.at(t);
         const uint32_t J = a.hcol[p];
@@ -911,6 +941,7 @@ __global__ void __launch_bounds__(kBlock) density_only_k(PassArgs a)
         }
     }
     if (G.act) density_out<R>(a, i, ri, rho);
+    });
 }
 
 // Rows of every gas group from the previous step's list sizes (by original
@@ -919,22 +950,22 @@ __global__ void __launch_bounds__(kBlock) density_only_k(PassArgs a)
 // count pass.
 __global__ void __launch_bounds__(kBlock) hlist_bound_k(PassArgs a, const uint32_t *__restrict__ cnt_by_id)
 {
-    const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-    const uint32_t gi = blockIdx.x * kWarps + w;
-    if (gi >= a.n_ggas) return;
+    const uint32_t lane = threadIdx.x & 31u;
+    for_each_item(a.n_ggas, a.ggas_dev, a.queue, Q_HBOUND, [&](const uint32_t gi) {
     const Group G = load_group(a.lv, a.ggas, gi, lane);
     const uint32_t c = __reduce_max_sync(0xffffffffu, G.act ? cnt_by_id[a.s.id[G.i]] : 0u);
     if (lane == 0) a.nl_len[gi] = c + (c / 8u > 16u ? c / 8u : 16u);
+    });
 }
 
 // Every gas target's list size, stored by original index for the next step.
 __global__ void keep_counts_k(PassArgs a, uint32_t *cnt_by_id)
 {
-    const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-    const uint32_t gi = blockIdx.x * kWarps + w;
-    if (gi >= a.n_ggas) return;
+    const uint32_t lane = threadIdx.x & 31u;
+    for_each_item(a.n_ggas, a.ggas_dev, a.queue, Q_KEEP, [&](const uint32_t gi) {
     const Group G = load_group(a.lv, a.ggas, gi, lane);
     if (G.act) cnt_by_id[a.s.id[G.i]] = a.nl_cnt[G.i];
+    });
 }
 
 // The neighbour's sorted index and the leaf-pair frame of a list entry.
@@ -1000,9 +1031,8 @@ template <typename R, int JMAX, bool COUNT>
 __global__ void __launch_bounds__(kBlock) density_k(PassArgs a)
 {
     using R4 = Vec4<R>;
-    const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-    const uint32_t gi = blockIdx.x * kWarps + w;
-    if (gi >= a.n_ggas) return;
+    const uint32_t lane = threadIdx.x & 31u;
+    for_each_item(a.n_ggas, a.ggas_dev, a.queue, Q_DENS, [&](const uint32_t gi) {
     const Group G = load_group(a.lv, a.ggas, gi, lane);
     const int I = G.I;
     const uint32_t i = G.i;
@@ -1069,6 +1099,7 @@ __global__ void __launch_bounds__(kBlock) density_k(PassArgs a)
         if (a.nbr_count) a.nbr_count[i] = nc;
         if (a.nbr_hash) a.nbr_hash[i] = hs;
     }
+    });
 }
 
 // ------------------------------------------------------ correction solve C
@@ -1191,9 +1222,8 @@ template <typename R, int JMAX>
 __global__ void __launch_bounds__(kBlock, moments_min_blocks<R>()) moments_k(PassArgs a)
 {
     using R4 = Vec4<R>;
-    const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-    const uint32_t gi = blockIdx.x * kWarps + w;
-    if (gi >= a.n_ggas) return;
+    const uint32_t lane = threadIdx.x & 31u;
+    for_each_item(a.n_ggas, a.ggas_dev, a.queue, Q_MOM, [&](const uint32_t gi) {
     const Group G = load_group(a.lv, a.ggas, gi, lane);
     const int I = G.I;
     const uint32_t i = G.i;
@@ -1271,6 +1301,7 @@ __global__ void __launch_bounds__(kBlock, moments_min_blocks<R>()) moments_k(Pas
     reinterpret_cast<R4 *>(a.hrec[4])[i] = v4;
     reinterpret_cast<R4 *>(a.hrec[5])[i] = v5;
     reinterpret_cast<R4 *>(a.hrec[6])[i] = v6;
+    });
 }
 
 // Hydro state of one particle, unpacked from its 7 records.
@@ -1321,9 +1352,8 @@ template <typename R, int JMAX>
 __global__ void __launch_bounds__(kBlock) hydro_k(PassArgs a)
 {
     using R4 = Vec4<R>;
-    const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-    const uint32_t gi = blockIdx.x * kWarps + w;
-    if (gi >= a.n_ggas) return;
+    const uint32_t lane = threadIdx.x & 31u;
+    for_each_item(a.n_ggas, a.ggas_dev, a.queue, Q_HYDRO, [&](const uint32_t gi) {
     const Group G = load_group(a.lv, a.ggas, gi, lane);
     const int I = G.I;
     const uint32_t i = G.i;
@@ -1414,6 +1444,7 @@ __global__ void __launch_bounds__(kBlock) hydro_k(PassArgs a)
     o.z = az * imi;
     o.w = (R)(-0.5) * du * imi;
     reinterpret_cast<R4 *>(a.acc_h)[i] = o;
+    });
 }
 
 // ------------------------------------------------------------- gravity G
@@ -1492,8 +1523,7 @@ __global__ void __launch_bounds__(kBlock) gravity_k(PassArgs a)
     using R4 = Vec4<R>;
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-    const uint32_t gi = blockIdx.x * kWarps + w;
-    if (gi >= a.n_gall) return;
+    for_each_item(a.n_gall, a.gall_dev, a.queue, Q_GRAV, [&](const uint32_t gi) {
     R4 *tile = reinterpret_cast<R4 *>(smem + (size_t)w * tile_warp_bytes<R, JMAX>());
     uint8_t *tslot = reinterpret_cast<uint8_t *>(tile + JMAX);
     const Group G = load_group(a.lv, a.gall, gi, lane);
@@ -1517,7 +1547,7 @@ __global__ void __launch_bounds__(kBlock) gravity_k(PassArgs a)
     R ax = 0, ay = 0, az = 0;
     int nc = 0;
     uint64_t hs = 0, tested = 0;
-    for (uint32_t p = a.grow[I]; p < a.grow[I + 1]; ++p) {
+    for (uint32_t p = a.grow[I]; p < a.gend[I]; ++p) {
         const uint32_t J = a.gcol[p];
         const float4 fr = a.gfr[p];
         if (out_of_range(wb, fr, a.lv.ex[J], a.lv.ey[J], a.lv.ez[J], Rc)) continue;
@@ -1553,6 +1583,7 @@ __global__ void __launch_bounds__(kBlock) gravity_k(PassArgs a)
         if (a.grav_count) a.grav_count[i] = nc;
         if (a.grav_hash) a.grav_hash[i] = hs;
     }
+    });
 }
 
 // ------------------------------------------- gravity, each pair evaluated once
@@ -1633,8 +1664,7 @@ __global__ void __launch_bounds__(kBlock) gravity_sym_k(const __grid_constant__ 
     using R4 = Vec4<float>;
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
-    const uint32_t gi = blockIdx.x * kWarps + w;
-    if (gi >= a.n_gall) return;
+    for_each_item(a.n_gall, a.gall_dev, a.queue, Q_GSYM, [&](const uint32_t gi) {
     R4 *tile = reinterpret_cast<R4 *>(smem + (size_t)w * tile_warp_bytes<float, JMAX>());
     uint8_t *tslot = reinterpret_cast<uint8_t *>(tile + JMAX);
     const Group G = load_group(a.lv, a.gall, gi, lane);
@@ -1658,7 +1688,7 @@ __global__ void __launch_bounds__(kBlock) gravity_sym_k(const __grid_constant__ 
     const float Rc = (float)bx.r_cut * 1.0001f + 1e-6f * (float)Ld;
     float ax = 0.f, ay = 0.f, az = 0.f;
     // the row is ascending: start at the first J >= I
-    uint32_t p0 = a.grow[I], p1 = a.grow[I + 1];
+    uint32_t p0 = a.grow[I], p1 = a.gend[I];
     {
         uint32_t lo = p0, hi = p1;
         while (lo < hi) {
@@ -1699,6 +1729,7 @@ __global__ void __launch_bounds__(kBlock) gravity_sym_k(const __grid_constant__ 
         }
     }
     if (G.act) atomicAdd(acc + i, make_float4(ax, ay, az, 0.f));
+    });
 }
 
 // ------------------------------------------------- friends-of-friends groups
@@ -1771,7 +1802,7 @@ __global__ void __launch_bounds__(kBlock) fof_link_k(PassArgs a, uint32_t *par, 
     const WarpBox wb = warp_box(px, py, pz, G.act);
     const float Rc = (float)b * 1.0001f + 1e-6f * (float)Ld;
     bool ok = true;
-    for (uint32_t p = a.grow[I]; p < a.grow[I + 1]; ++p) {
+    for (uint32_t p = a.grow[I]; p < a.gend[I]; ++p) {
         const uint32_t J = a.gcol[p];
         if (!((mask >> a.lv.species[J]) & 1)) continue;
         const float4 fr = a.gfr[p];
@@ -1846,7 +1877,18 @@ void launch_warp_kernel(K kernel, uint32_t ngroups, size_t smem, const PassArgs 
 {
     if (ngroups == 0) return;
     if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    kernel<<<nblocks(ngroups, kWarps), kBlock, smem, st>>>(a);
+    unsigned grid = nblocks(ngroups, kWarps);
+    if (a.queue) {
+        // persistent: as many blocks as the SMs hold at once (ngroups is then
+        // an upper bound of the items, whose true count is on the device)
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, smem);
+        const unsigned resident = (unsigned)(sms > 0 ? sms : 1) * (unsigned)(per_sm > 0 ? per_sm : 1);
+        grid = grid < resident ? grid : resident;
+    }
+    kernel<<<grid, kBlock, smem, st>>>(a);
 }
 
 template <typename R, int JMAX>

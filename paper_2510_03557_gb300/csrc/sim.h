@@ -121,6 +121,23 @@ struct crk_sim {
     uint32_t *host_scalars = nullptr;  // pinned: [0] nleaf, [1] hydro pairs, [2] gravity pairs
     int *host_err = nullptr;           // pinned: err[0..1]
 
+    // steps captured as CUDA graphs: a step sized on the device against the
+    // capacities of the last host-sized step, two steps per graph (the state
+    // buffers swap at every sort), the state snapshot a batch restores after
+    // an overflow
+    DBuf dz;                            // device sizes block (DevSize words)
+    DBuf ds_row[4];                     // fixed-row begin / end of the hydro and gravity lists
+    DBuf ds_snap;                       // state snapshot of a batch
+    int ds_cap_leaf = 0;
+    uint32_t ds_cap_items = 0, ds_cap_rows = 0;
+    double ds_margin = 1.25;            // capacity over the last sizes (grows after an overflow)
+    cudaStream_t cap_st = nullptr;      // stream the graph is captured on
+    cudaGraphExec_t graph = nullptr;
+    int64_t graph_launch_nodes = 0;     // kernels of one captured step
+    // counters since the last crk_set_timing: host synchronisations inside
+    // steps, steps run, steps run as graph replays, overflow recoveries
+    int64_t host_syncs = 0, steps_run = 0, graph_steps = 0, graph_overflows = 0;
+
     // timing
     bool timing = false;
     cudaEvent_t ev[crk::PH_N][2] = {};

@@ -343,19 +343,28 @@ __global__ void leaf_flags_k(const uint64_t *__restrict__ keys, int sb,
     }
 }
 
+// Leaves whose index reaches `cap` (the leaf arrays' capacity) are not
+// written; nl_dev (optional) holds the leaf count on the device, capped at
+// the capacity by the caller when it overflows.
+__device__ __forceinline__ int leaves_of(int nleaf, const uint32_t *nl_dev)
+{
+    return nl_dev ? (int)min((uint32_t)nleaf, *nl_dev) : nleaf;
+}
+
 __global__ void leaf_setup_k(const uint32_t *__restrict__ flags, const uint32_t *__restrict__ scan,
-                             int64_t n, uint32_t *start)
+                             int64_t n, uint32_t cap, uint32_t *start)
 {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    if (flags[k]) start[scan[k]] = (uint32_t)k;
+    if (flags[k] && scan[k] < cap) start[scan[k]] = (uint32_t)k;
 }
 
-__global__ void leaf_count_k(Leaves lv, int nleaf, int64_t n)
+__global__ void leaf_count_k(Leaves lv, int nleaf, int64_t n, const uint32_t *nl_dev)
 {
     int L = blockIdx.x * blockDim.x + threadIdx.x;
-    if (L >= nleaf) return;
-    uint32_t end = (L + 1 < nleaf) ? lv.start[L + 1] : (uint32_t)n;
+    const int nl = leaves_of(nleaf, nl_dev);
+    if (L >= nl) return;
+    uint32_t end = (L + 1 < nl) ? lv.start[L + 1] : (uint32_t)n;
     lv.count[L] = end - lv.start[L];
 }
 
@@ -401,11 +410,24 @@ __device__ __forceinline__ double leaf_offset(double x, double ref, double L)
 
 template <int MIXED>
 __global__ void leaf_bounds_k(State s, const BoxDev *__restrict__ boxes, Leaves lv, int nleaf, void *pm,
-                              Nodes nd)
+                              Nodes nd, const uint32_t *nl_dev)
 {
     const int w = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const uint32_t lane = lane_id();
     if (w >= nleaf) return;
+    if (w >= leaves_of(nleaf, nl_dev)) {
+        // an unused slot of the leaf arrays (capacity beyond the leaf count):
+        // an empty leaf whose node box is inverted and belongs to no box, so
+        // that every walk of the hierarchy passes it by
+        if (lane == 0) {
+            lv.count[w] = 0;
+            lv.species[w] = 0xffu;
+            lv.hmax[w] = 0.f;
+            nd.lo[w] = make_float4(1e30f, 1e30f, 1e30f, 0.f);
+            nd.hi[w] = make_float4(-1e30f, -1e30f, -1e30f, __int_as_float(-2));
+        }
+        return;
+    }
     const uint32_t s0 = lv.start[w], c = lv.count[w];
     const double Lb = boxes[s.slot[s0]].L;
     // positions relative to the leaf's first particle (leaves built from a
@@ -546,11 +568,15 @@ template <int MODE>
 __global__ void pair_walk_k(Nodes nd, Leaves lv, const BoxDev *__restrict__ boxes, int nleaf,
                             int hydro, uint32_t *counts, const uint32_t *__restrict__ row,
                             uint32_t *col, float4 *frame, uint32_t *start, uint32_t cap, uint32_t *overflow,
-                            const uint8_t *__restrict__ mask)
+                            const uint8_t *__restrict__ mask, const uint32_t *nl_dev)
 {
     constexpr bool FILL = MODE != 0;
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= nleaf) return;
+    if (I >= leaves_of(nleaf, nl_dev)) {
+        if (MODE != 1) counts[I] = 0;
+        return;
+    }
     // leaves without a row: DM leaves of the hydro list, unmasked leaves
     if ((hydro && lv.species[I] != CRK_GAS) || (mask && !mask[I])) {
         if (MODE != 1) counts[I] = 0;
@@ -691,12 +717,12 @@ __device__ void kd_sort_range(KdScratch &S, uint32_t lo, uint32_t hi, uint32_t l
     __syncwarp();
 }
 
-__global__ void kd_order_k(State s, Leaves lv, int nleaf, uint32_t *perm)
+__global__ void kd_order_k(State s, Leaves lv, int nleaf, uint32_t *perm, const uint32_t *nl_dev)
 {
     __shared__ KdScratch scratch[kKdWarps];
     const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
     const int L = blockIdx.x * kKdWarps + (int)w;
-    if (L >= nleaf) return;
+    if (L >= leaves_of(nleaf, nl_dev)) return;
     const uint32_t s0 = lv.start[L], c = lv.count[L];
     if (c <= 1u) return;
     KdScratch &S = scratch[w];
@@ -723,18 +749,22 @@ __global__ void kd_order_k(State s, Leaves lv, int nleaf, uint32_t *perm)
 
 // Warp work items of the pair passes: every leaf is cut into target groups
 // of at most 32 consecutive particles; (leaf, first particle offset).
-__global__ void group_count_k(Leaves lv, int nleaf, int gas_only, uint32_t *counts)
+__global__ void group_count_k(Leaves lv, int nleaf, int gas_only, uint32_t *counts, const uint32_t *nl_dev)
 {
     const int L = blockIdx.x * blockDim.x + threadIdx.x;
     if (L >= nleaf) return;
+    if (L >= leaves_of(nleaf, nl_dev)) {
+        counts[L] = 0u;
+        return;
+    }
     counts[L] = (gas_only && lv.species[L] != CRK_GAS) ? 0u : (lv.count[L] + 31u) / 32u;
 }
 
 __global__ void group_fill_k(Leaves lv, int nleaf, int gas_only, const uint32_t *__restrict__ off,
-                             uint2 *groups)
+                             uint2 *groups, const uint32_t *nl_dev)
 {
     const int L = blockIdx.x * blockDim.x + threadIdx.x;
-    if (L >= nleaf) return;
+    if (L >= leaves_of(nleaf, nl_dev)) return;
     if (gas_only && lv.species[L] != CRK_GAS) return;
     const uint32_t ng = (lv.count[L] + 31u) / 32u;
     for (uint32_t g = 0; g < ng; ++g) groups[off[L] + g] = make_uint2((uint32_t)L, 32u * g);
@@ -744,26 +774,27 @@ inline unsigned grid_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / b
 
 }  // namespace
 
-void launch_leaf_kd_order(const State &unsorted, const Leaves &lv, int nleaf, uint32_t *perm,
-                          cudaStream_t st)
+void launch_leaf_kd_order(const State &unsorted, const Leaves &lv, int nleaf, uint32_t *perm, cudaStream_t st,
+                          const uint32_t *nl_dev)
 {
     if (nleaf <= 0) return;
-    kd_order_k<<<grid_for(nleaf, kKdWarps), 32 * kKdWarps, 0, st>>>(unsorted, lv, nleaf, perm);
+    kd_order_k<<<grid_for(nleaf, kKdWarps), 32 * kKdWarps, 0, st>>>(unsorted, lv, nleaf, perm, nl_dev);
     note_launches(1);
 }
 
-void launch_group_count(const Leaves &lv, int nleaf, int gas_only, uint32_t *counts, cudaStream_t st)
+void launch_group_count(const Leaves &lv, int nleaf, int gas_only, uint32_t *counts, cudaStream_t st,
+                        const uint32_t *nl_dev)
 {
     if (nleaf <= 0) return;
-    group_count_k<<<grid_for(nleaf, kT), kT, 0, st>>>(lv, nleaf, gas_only, counts);
+    group_count_k<<<grid_for(nleaf, kT), kT, 0, st>>>(lv, nleaf, gas_only, counts, nl_dev);
     note_launches(1);
 }
 
 void launch_group_fill(const Leaves &lv, int nleaf, int gas_only, const uint32_t *off, uint2 *groups,
-                       cudaStream_t st)
+                       cudaStream_t st, const uint32_t *nl_dev)
 {
     if (nleaf <= 0) return;
-    group_fill_k<<<grid_for(nleaf, kT), kT, 0, st>>>(lv, nleaf, gas_only, off, groups);
+    group_fill_k<<<grid_for(nleaf, kT), kT, 0, st>>>(lv, nleaf, gas_only, off, groups, nl_dev);
     note_launches(1);
 }
 
@@ -831,21 +862,21 @@ void launch_leaf_flags(const uint64_t *keys, int slot_bits, const BoxDev *boxes,
 }
 
 void launch_leaf_setup(const uint32_t *flags, const uint32_t *scan, int64_t n, int nleaf,
-                       Leaves lv, cudaStream_t st)
+                       Leaves lv, cudaStream_t st, const uint32_t *nl_dev)
 {
     if (n <= 0 || nleaf <= 0) return;
-    leaf_setup_k<<<grid_for(n, kT), kT, 0, st>>>(flags, scan, n, lv.start);
-    leaf_count_k<<<grid_for(nleaf, kT), kT, 0, st>>>(lv, nleaf, n);
+    leaf_setup_k<<<grid_for(n, kT), kT, 0, st>>>(flags, scan, n, (uint32_t)nleaf, lv.start);
+    leaf_count_k<<<grid_for(nleaf, kT), kT, 0, st>>>(lv, nleaf, n, nl_dev);
     note_launches(2);
 }
 
 void launch_leaf_bounds(const State &s, const BoxDev *boxes, Leaves lv, int nleaf, int mixed,
-                        void *pm, Nodes nd, cudaStream_t st)
+                        void *pm, Nodes nd, cudaStream_t st, const uint32_t *nl_dev)
 {
     if (nleaf <= 0) return;
     unsigned g = grid_for((int64_t)nleaf * 32, kT);
-    if (mixed) leaf_bounds_k<1><<<g, kT, 0, st>>>(s, boxes, lv, nleaf, pm, nd);
-    else leaf_bounds_k<0><<<g, kT, 0, st>>>(s, boxes, lv, nleaf, pm, nd);
+    if (mixed) leaf_bounds_k<1><<<g, kT, 0, st>>>(s, boxes, lv, nleaf, pm, nd, nl_dev);
+    else leaf_bounds_k<0><<<g, kT, 0, st>>>(s, boxes, lv, nleaf, pm, nd, nl_dev);
     note_launches(1);
 }
 
@@ -872,17 +903,18 @@ void launch_pair_count(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, i
 {
     if (nleaf <= 0) return;
     pair_walk_k<0><<<grid_for(nleaf, 128), 128, 0, st>>>(nd, lv, boxes, nleaf, hydro, counts,
-                                                           nullptr, nullptr, nullptr, nullptr, 0u, nullptr, mask);
+                                                           nullptr, nullptr, nullptr, nullptr, 0u, nullptr, mask,
+                                                           nullptr);
     note_launches(1);
 }
 
 void launch_pair_scratch(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, int nleaf, int hydro,
                          uint32_t *counts, uint32_t cap, uint32_t *col, float4 *frame, uint32_t *start,
-                         uint32_t *overflow, cudaStream_t st, const uint8_t *mask)
+                         uint32_t *overflow, cudaStream_t st, const uint8_t *mask, const uint32_t *nl_dev)
 {
     if (nleaf <= 0) return;
     pair_walk_k<2><<<grid_for(nleaf, 128), 128, 0, st>>>(nd, lv, boxes, nleaf, hydro, counts, nullptr, col,
-                                                           frame, start, cap, overflow, mask);
+                                                           frame, start, cap, overflow, mask, nl_dev);
     note_launches(1);
 }
 
@@ -902,7 +934,7 @@ void launch_pair_fill(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, in
 {
     if (nleaf <= 0) return;
     pair_walk_k<1><<<grid_for(nleaf, 128), 128, 0, st>>>(nd, lv, boxes, nleaf, hydro, nullptr,
-                                                           row, col, frame, start, 0u, nullptr, mask);
+                                                           row, col, frame, start, 0u, nullptr, mask, nullptr);
     note_launches(1);
 }
 
