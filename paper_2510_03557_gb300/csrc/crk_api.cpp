@@ -985,7 +985,7 @@ static int ds_capture(crk_sim *s)
     cudaStream_t user = s->st;
     s->st = s->cap_st;
     const int64_t l0 = launches_so_far();
-    cudaError_t e = cudaStreamBeginCapture(s->st, cudaStreamCaptureModeThreadLocal);
+    cudaError_t e = cudaStreamBeginCapture(s->st, cudaStreamCaptureModeRelaxed);
     int rc = e == cudaSuccess ? CRK_OK : fail(CRK_ECUDA, "stream capture failed: %s", cudaGetErrorString(e));
     if (rc == CRK_OK) rc = run_step_ds(s);
     if (rc == CRK_OK) rc = run_step_ds(s);
