@@ -115,7 +115,10 @@ typedef struct {
                           force filtered by the Gaussian split (paper Sec. IV-A: FP64 spectral
                           particle-mesh solver for the long-range force).  One box per handle
                           (crk_load, or crk_load_boxes with nbox = 1); not with the service. */
-    int reserved[1];
+    int graph_margin_pct; /* steps replayed from a CUDA graph (crk_step): the device buffers hold the
+                             sizes of the step before the replays plus this many percent (0: 25);
+                             a replay batch that outgrows them runs again host-sized, and the margin
+                             of the handle's later batches grows by half */
 } crk_params;
 
 /* Outputs of crk_forces.  Every pointer is optional (NULL skips it); all

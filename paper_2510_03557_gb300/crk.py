@@ -62,7 +62,7 @@ class Physics(ctypes.Structure):
 class Params(ctypes.Structure):
     _fields_ = [("phys", Physics), ("kernel", ctypes.c_int), ("leaf_cap", ctypes.c_int),
                 ("precision", ctypes.c_int), ("cm_level", ctypes.c_int), ("flags", ctypes.c_int),
-                ("rebuild_every", ctypes.c_int), ("pm_grid", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("rebuild_every", ctypes.c_int), ("pm_grid", ctypes.c_int), ("graph_margin_pct", ctypes.c_int)]
 
 
 class Outputs(ctypes.Structure):
@@ -147,8 +147,9 @@ def physics(box=1.0, G=1.0, gamma=5.0 / 3.0, r_cut=0.1, r_split=0.02, eps_soft=0
 
 
 def params(phys: Physics | None = None, leaf_cap=64, precision=CRK_MIXED, cm_level=0,
-           kernel=CRK_WENDLAND_C4, rebuild_every=1, pm_grid=0, flags=0) -> Params:
+           kernel=CRK_WENDLAND_C4, rebuild_every=1, pm_grid=0, flags=0, graph_margin_pct=0) -> Params:
     p = Params()
+    p.graph_margin_pct = graph_margin_pct
     p.phys = phys if phys is not None else physics()
     p.kernel = kernel
     p.flags = flags
@@ -504,9 +505,10 @@ class Sim:
     """Owns one crk_sim handle (create / load / forces / step / destroy)."""
 
     def __init__(self, phys: Physics | None = None, leaf_cap=64, precision=CRK_MIXED, cm_level=0,
-                 stream=None, rebuild_every=1, pm_grid=0, flags=0):
+                 stream=None, rebuild_every=1, pm_grid=0, flags=0, graph_margin_pct=0):
         self.handle = crk_create(params(phys, leaf_cap, precision, cm_level, rebuild_every=rebuild_every,
-                                        pm_grid=pm_grid, flags=flags), stream)
+                                        pm_grid=pm_grid, flags=flags, graph_margin_pct=graph_margin_pct),
+                                 stream)
 
     def load(self, box):
         crk_load(self.handle, box.pos, box.vel, box.mass, box.u, box.h, box.species)

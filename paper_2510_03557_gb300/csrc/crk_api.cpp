@@ -731,12 +731,15 @@ extern "C" int crk_create(const crk_params *params, void *cuda_stream, crk_sim *
     if (params->rebuild_every < 0) return fail(CRK_EINVAL, "rebuild_every must be >= 0");
     if (params->flags & ~(CRK_FLAG_GRAVITY_PAIRS_ONCE | CRK_FLAG_NO_GRAPH))
         return fail(CRK_EINVAL, "unknown flags bits 0x%x", params->flags);
+    if (params->graph_margin_pct < 0 || params->graph_margin_pct > 1000)
+        return fail(CRK_EINVAL, "graph_margin_pct must be in [0, 1000]");
     if (params->pm_grid != 0 && (params->pm_grid < 4 || params->pm_grid > 1024 || params->pm_grid % 2))
         return fail(CRK_EINVAL, "pm_grid must be 0 or an even number in [4, 1024] (got %d)", params->pm_grid);
     crk_sim *s = new crk_sim();
     s->prm = *params;
     s->mixed = params->precision == CRK_MIXED;
     s->cap = params->leaf_cap;
+    s->ds_margin = 1.0 + (params->graph_margin_pct > 0 ? params->graph_margin_pct : 25) / 100.0;
     s->st = static_cast<cudaStream_t>(cuda_stream);
     cudaError_t e = cudaGetDevice(&s->device);
     if (e == cudaSuccess) e = cudaMallocHost(&s->host_scalars, 64);
@@ -871,17 +874,18 @@ static int run_step_ds(crk_sim *s)
     // S2: hierarchy over the capacity, pair rows of fixed capacity, groups
     Nodes nd = s->nd;
     launch_build_nodes(nd, capL, st);
-    uint32_t *scol_h = s->pscr_col.as<uint32_t>(), *scol_g = scol_h + nl * kPairCapH;
-    float4 *sfr_h = s->pscr_fr.as<float4>(), *sfr_g = sfr_h + nl * kPairCapH;
-    launch_pair_scratch(nd, s->lv, bd, capL, 1, s->hcnt.as<uint32_t>(), kPairCapH, scol_h, sfr_h,
+    const uint32_t cph = s->ds_cap_ph, cpg = s->ds_cap_pg;
+    uint32_t *scol_h = s->pscr_col.as<uint32_t>(), *scol_g = scol_h + nl * cph;
+    float4 *sfr_h = s->pscr_fr.as<float4>(), *sfr_g = sfr_h + nl * cph;
+    launch_pair_scratch(nd, s->lv, bd, capL, 1, s->hcnt.as<uint32_t>(), cph, scol_h, sfr_h,
                         s->pscr_st.as<uint32_t>(), dz + DZ_PAIR_OVF, st, nullptr, nld);
-    launch_pair_scratch(nd, s->lv, bd, capL, 0, s->gcnt.as<uint32_t>(), kPairCapG, scol_g, sfr_g, nullptr,
+    launch_pair_scratch(nd, s->lv, bd, capL, 0, s->gcnt.as<uint32_t>(), cpg, scol_g, sfr_g, nullptr,
                         dz + DZ_PAIR_OVF, st, nullptr, nld);
     launch_ds_check(dz, 1, 0u, nullptr, st);
     uint32_t *hb = s->ds_row[0].as<uint32_t>(), *he = s->ds_row[1].as<uint32_t>();
     uint32_t *gb = s->ds_row[2].as<uint32_t>(), *ge = s->ds_row[3].as<uint32_t>();
-    launch_fixed_rows(s->hcnt.as<uint32_t>(), capL, kPairCapH, hb, he, st);
-    launch_fixed_rows(s->gcnt.as<uint32_t>(), capL, kPairCapG, gb, ge, st);
+    launch_fixed_rows(s->hcnt.as<uint32_t>(), capL, cph, hb, he, st);
+    launch_fixed_rows(s->gcnt.as<uint32_t>(), capL, cpg, gb, ge, st);
     uint32_t *gc = s->grp_cnt.as<uint32_t>(), *go = s->grp_off.as<uint32_t>();
     launch_group_count(s->lv, capL, 1, gc, st, nld);
     launch_group_count(s->lv, capL, 0, gc + nl, st, nld);
@@ -949,15 +953,33 @@ static int ds_prepare(crk_sim *s)
 {
     const int64_t n = s->n;
     const double m = s->ds_margin;
-    s->ds_cap_leaf = (int)std::min<int64_t>(n, (int64_t)(m * s->nleaf) + 1024);
+    s->ds_cap_leaf = (int)std::min<int64_t>(n, (int64_t)(m * s->nleaf) + 64);
     s->ds_cap_items = (uint32_t)std::min<int64_t>((int64_t)4 * s->ds_cap_leaf, s->ds_cap_leaf + n / 32 + 64);
-    s->ds_cap_rows = (uint32_t)std::max<int64_t>((int64_t)(m * s->nl_rows) + 1024, 1024);
+    s->ds_cap_rows = (uint32_t)((int64_t)(m * s->nl_rows) + 256);
+    // pair rows of fixed capacity: the longest row of the last step with the
+    // margin, in whole 32-entry blocks
+    {
+        const size_t nlh = (size_t)s->nleaf;
+        std::vector<uint32_t> c(2 * nlh);
+        CK(cudaMemcpyAsync(c.data(), s->hcnt.p, nlh * 4, cudaMemcpyDeviceToHost, s->st));
+        CK(cudaMemcpyAsync(c.data() + nlh, s->gcnt.p, nlh * 4, cudaMemcpyDeviceToHost, s->st));
+        CK(cudaStreamSynchronize(s->st));
+        uint32_t mh = 0, mg = 0;
+        for (size_t k = 0; k < nlh; ++k) {
+            mh = std::max(mh, c[k]);
+            mg = std::max(mg, c[nlh + k]);
+        }
+        auto fit = [m](uint32_t v) { return (uint32_t)(((uint64_t)(m * v) + 16 + 31) / 32 * 32); };
+        s->ds_cap_ph = std::min<uint32_t>(fit(mh), kMaxPairRow);
+        s->ds_cap_pg = fit(mg);
+    }
     const size_t nl = (size_t)s->ds_cap_leaf, ni = s->ds_cap_items;
+    const size_t cph = s->ds_cap_ph, cpg = s->ds_cap_pg;
     RET(s->dz.ensure(DZ_WORDS * sizeof(uint32_t)));
     for (int k = 0; k < 4; ++k) RET(s->ds_row[k].ensure(nl * sizeof(uint32_t)));
-    RET(s->pscr_col.ensure(nl * (kPairCapH + kPairCapG) * sizeof(uint32_t)));
-    RET(s->pscr_fr.ensure(nl * (kPairCapH + kPairCapG) * sizeof(float4)));
-    RET(s->pscr_st.ensure(nl * kPairCapH * sizeof(uint32_t)));
+    RET(s->pscr_col.ensure(nl * (cph + cpg) * sizeof(uint32_t)));
+    RET(s->pscr_fr.ensure(nl * (cph + cpg) * sizeof(float4)));
+    RET(s->pscr_st.ensure(nl * cph * sizeof(uint32_t)));
     RET(s->grp_cnt.ensure(nl * 4 * 2));
     RET(s->grp_off.ensure(nl * 4 * 2));
     RET(s->grp_gas.ensure(ni * sizeof(uint2)));

@@ -46,6 +46,8 @@ struct DBuf {
 // Leaf pairs a leaf's hydro and gravity rows hold before the lists are
 // walked twice (count, then fill).
 constexpr uint32_t kPairCapH = 128, kPairCapG = 256;
+// Longest hydro leaf-pair row a list entry can address (24 bits of offset).
+constexpr uint32_t kMaxPairRow = 1u << 24;
 // Octree levels of a 21-bit-per-axis Morton key (all of them).
 constexpr int kAllLevels = 21;
 
@@ -130,6 +132,7 @@ struct crk_sim {
     DBuf ds_snap;                       // state snapshot of a batch
     int ds_cap_leaf = 0;
     uint32_t ds_cap_items = 0, ds_cap_rows = 0;
+    uint32_t ds_cap_ph = 0, ds_cap_pg = 0;  // entries of a leaf's fixed hydro / gravity pair row
     double ds_margin = 1.25;            // capacity over the last sizes (grows after an overflow)
     cudaStream_t cap_st = nullptr;      // stream the graph is captured on
     cudaGraphExec_t graph = nullptr;

@@ -33,11 +33,12 @@ def disp_err(pos, ref, pos0):
     return np.linalg.norm(d) / np.linalg.norm((ref - pos0 + 0.5) % 1.0 - 0.5)
 
 
-def _run(crk, box, precision, nsteps, flags=0, stream=None):
+def _run(crk, box, precision, nsteps, flags=0, stream=None, margin=0):
     import torch
 
     st = stream or torch.cuda.Stream()
-    with crk.Sim(crk.box_physics(box), leaf_cap=64, precision=precision, stream=st, flags=flags) as sim:
+    with crk.Sim(crk.box_physics(box), leaf_cap=64, precision=precision, stream=st, flags=flags,
+                 graph_margin_pct=margin) as sim:
         sim.load(box)
         crk.crk_set_timing(sim.handle, False)
         sim.step(box.dt, nsteps)
@@ -95,15 +96,16 @@ def test_replayed_steps_of_batched_boxes_match_the_oracle(crk):
 
 
 def test_replays_that_outgrow_their_capacities_run_again(crk):
-    """A converging flow compresses the box during the replays, so the hydro
-    lists outgrow the capacities taken from the first step: the batch is
-    restored and stepped host-sized, and the result is still the oracle's."""
+    """A converging flow compresses the box (the gather sets grow by about
+    60% over the steps), so the hydro lists outgrow the capacities of the
+    first step (taken with a 1% margin): the batch is restored and stepped
+    host-sized, and the result is still the oracle's."""
     box = wl.jittered_lattice(16, seed=12)
     d = (box.pos - 0.5 + 0.5) % 1.0 - 0.5
-    box.vel = -60.0 * d
+    box.vel = -15.0 * d
     box.dt = 2e-3
     nsteps = 9
-    g = _run(crk, box, 0, nsteps)
+    g = _run(crk, box, 0, nsteps, margin=1)
     assert g[3]["graph_overflows"] >= 1 and g[3]["steps"] == nsteps
     ref = oracle.kdk(box.pos, box.vel, box.mass, box.u, box.h, box.species,
                      oracle.make_params(**box.params()), box.dt, nsteps)
