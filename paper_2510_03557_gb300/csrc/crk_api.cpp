@@ -834,9 +834,9 @@ extern "C" int crk_forces(crk_sim *s, crk_outputs *out)
 // every launch after them is sized by a capacity fixed on the host (from the
 // last host-sized step, with a margin) and reads the true count on the
 // device; the pass kernels are persistent launches that drain a device work
-// queue of (leaf, target group) items of every box.  Leaf-pair rows stay in
-// the fixed-capacity rows the walk fills (no packing), hydro list rows are
-// sized from the last step's counts.  Nothing is read back, so the step can
+// queue of (leaf, target group) items of every box.  The leaf-pair lists are
+// walked twice (count, fill at scanned offsets), hydro list rows are sized
+// from the last step's counts.  Nothing is read back, so the step can
 // be captured into a CUDA graph; an overflow of a capacity is recorded on the
 // device (and zeroes the counts the rest of the step launches over).
 static int run_step_ds(crk_sim *s)
@@ -851,7 +851,6 @@ static int run_step_ds(crk_sim *s)
     const size_t nl = (size_t)capL;
     const uint32_t capI = s->ds_cap_items;
     CK(cudaMemsetAsync(dz + DZ_QUEUE, 0, kQueueSlots * sizeof(uint32_t), st));
-    CK(cudaMemsetAsync(dz + DZ_PAIR_OVF, 0, sizeof(uint32_t), st));
     launch_kick_drift(s->sa, bd, n, s->nfloor.as<unsigned long long>(), st);
     // S1: keys, sort (the bits the last host-sized sort chose), leaves
     launch_morton_keys(s->sa, bd, n, s->slot_bits, s->keys.as<uint64_t>(), s->vals.as<uint32_t>(), st);
@@ -871,21 +870,23 @@ static int run_step_ds(crk_sim *s)
     std::swap(s->sa, s->sb);
     for (int k = 0; k < 17; ++k) std::swap(s->stA[k], s->stB[k]);
     launch_leaf_bounds(s->sa, bd, s->lv, capL, mixed, s->pm.p, s->nd, st, nld);
-    // S2: hierarchy over the capacity, pair rows of fixed capacity, groups
+    // S2: hierarchy over the capacity; each list walked twice (count, then
+    // fill into CSR rows from a scan whose total is checked on the device)
     Nodes nd = s->nd;
     launch_build_nodes(nd, capL, st);
-    const uint32_t cph = s->ds_cap_ph, cpg = s->ds_cap_pg;
-    uint32_t *scol_h = s->pscr_col.as<uint32_t>(), *scol_g = scol_h + nl * cph;
-    float4 *sfr_h = s->pscr_fr.as<float4>(), *sfr_g = sfr_h + nl * cph;
-    launch_pair_scratch(nd, s->lv, bd, capL, 1, s->hcnt.as<uint32_t>(), cph, scol_h, sfr_h,
-                        s->pscr_st.as<uint32_t>(), dz + DZ_PAIR_OVF, st, nullptr, nld);
-    launch_pair_scratch(nd, s->lv, bd, capL, 0, s->gcnt.as<uint32_t>(), cpg, scol_g, sfr_g, nullptr,
-                        dz + DZ_PAIR_OVF, st, nullptr, nld);
-    launch_ds_check(dz, 1, 0u, nullptr, st);
-    uint32_t *hb = s->ds_row[0].as<uint32_t>(), *he = s->ds_row[1].as<uint32_t>();
-    uint32_t *gb = s->ds_row[2].as<uint32_t>(), *ge = s->ds_row[3].as<uint32_t>();
-    launch_fixed_rows(s->hcnt.as<uint32_t>(), capL, cph, hb, he, st);
-    launch_fixed_rows(s->gcnt.as<uint32_t>(), capL, cpg, gb, ge, st);
+    uint32_t *hrow = s->hrow.as<uint32_t>(), *grow = s->grow.as<uint32_t>();
+    launch_pair_count(nd, s->lv, bd, capL, 1, s->hcnt.as<uint32_t>(), st, nullptr, nld);
+    launch_pair_count(nd, s->lv, bd, capL, 0, s->gcnt.as<uint32_t>(), st, nullptr, nld);
+    scan_exclusive_u32(s->hcnt.as<uint32_t>(), hrow, capL, dz + DZ_NPH, tmp, st);
+    scan_exclusive_u32(s->gcnt.as<uint32_t>(), grow, capL, dz + DZ_NPG, tmp, st);
+    launch_ds_check(dz, 1, s->ds_cap_ph, nullptr, st);
+    launch_ds_check(dz, 5, s->ds_cap_pg, nullptr, st);
+    CK(cudaMemcpyAsync(hrow + capL, dz + DZ_NPH, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(grow + capL, dz + DZ_NPG, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+    launch_pair_fill(nd, s->lv, bd, capL, 1, hrow, s->hcol.as<uint32_t>(), s->hfr.as<float4>(),
+                     s->hsj.as<uint32_t>(), st, nullptr, nld);
+    launch_pair_fill(nd, s->lv, bd, capL, 0, grow, s->gcol.as<uint32_t>(), s->gfr.as<float4>(), nullptr, st,
+                     nullptr, nld);
     uint32_t *gc = s->grp_cnt.as<uint32_t>(), *go = s->grp_off.as<uint32_t>();
     launch_group_count(s->lv, capL, 1, gc, st, nld);
     launch_group_count(s->lv, capL, 0, gc + nl, st, nld);
@@ -897,15 +898,6 @@ static int run_step_ds(crk_sim *s)
     // the passes over device work queues
     PassArgs a = pass_args(s);
     a.nleaf = capL;
-    a.hrow = hb;
-    a.hend = he;
-    a.hcol = scol_h;
-    a.hfr = sfr_h;
-    a.hsj = s->pscr_st.as<uint32_t>();
-    a.grow = gb;
-    a.gend = ge;
-    a.gcol = scol_g;
-    a.gfr = sfr_g;
     a.n_ggas = capI;
     a.n_gall = capI;
     a.ggas_dev = dz + DZ_GGAS;
@@ -956,30 +948,16 @@ static int ds_prepare(crk_sim *s)
     s->ds_cap_leaf = (int)std::min<int64_t>(n, (int64_t)(m * s->nleaf) + 64);
     s->ds_cap_items = (uint32_t)std::min<int64_t>((int64_t)4 * s->ds_cap_leaf, s->ds_cap_leaf + n / 32 + 64);
     s->ds_cap_rows = (uint32_t)((int64_t)(m * s->nl_rows) + 256);
-    // pair rows of fixed capacity: the longest row of the last step with the
-    // margin, in whole 32-entry blocks
-    {
-        const size_t nlh = (size_t)s->nleaf;
-        std::vector<uint32_t> c(2 * nlh);
-        CK(cudaMemcpyAsync(c.data(), s->hcnt.p, nlh * 4, cudaMemcpyDeviceToHost, s->st));
-        CK(cudaMemcpyAsync(c.data() + nlh, s->gcnt.p, nlh * 4, cudaMemcpyDeviceToHost, s->st));
-        CK(cudaStreamSynchronize(s->st));
-        uint32_t mh = 0, mg = 0;
-        for (size_t k = 0; k < nlh; ++k) {
-            mh = std::max(mh, c[k]);
-            mg = std::max(mg, c[nlh + k]);
-        }
-        auto fit = [m](uint32_t v) { return (uint32_t)(((uint64_t)(m * v) + 16 + 31) / 32 * 32); };
-        s->ds_cap_ph = std::min<uint32_t>(fit(mh), kMaxPairRow);
-        s->ds_cap_pg = fit(mg);
-    }
+    s->ds_cap_ph = (uint32_t)std::min<int64_t>((int64_t)(m * s->npair_h) + 256, 0xffffffffll);
+    s->ds_cap_pg = (uint32_t)std::min<int64_t>((int64_t)(m * s->npair_g) + 256, 0xffffffffll);
     const size_t nl = (size_t)s->ds_cap_leaf, ni = s->ds_cap_items;
     const size_t cph = s->ds_cap_ph, cpg = s->ds_cap_pg;
     RET(s->dz.ensure(DZ_WORDS * sizeof(uint32_t)));
-    for (int k = 0; k < 4; ++k) RET(s->ds_row[k].ensure(nl * sizeof(uint32_t)));
-    RET(s->pscr_col.ensure(nl * (cph + cpg) * sizeof(uint32_t)));
-    RET(s->pscr_fr.ensure(nl * (cph + cpg) * sizeof(float4)));
-    RET(s->pscr_st.ensure(nl * cph * sizeof(uint32_t)));
+    RET(s->hcol.ensure(cph * 4));
+    RET(s->hfr.ensure(cph * 16));
+    RET(s->hsj.ensure(cph * 4));
+    RET(s->gcol.ensure(cpg * 4));
+    RET(s->gfr.ensure(cpg * 16));
     RET(s->grp_cnt.ensure(nl * 4 * 2));
     RET(s->grp_off.ensure(nl * 4 * 2));
     RET(s->grp_gas.ensure(ni * sizeof(uint2)));
@@ -1622,7 +1600,7 @@ extern "C" int crk_destroy(crk_sim *s)
                     &s->nl_j, &s->nl_row, &s->nl_len, &s->nl_cnt, &s->hsj, &s->fof_par, &s->acc_pm,
                     &s->bflag, &s->bgrp[0], &s->bgrp[1], &s->bgrp[2], &s->bgrp[3], &s->bmap[0],
                     &s->bmap[1], &s->bkeep, &s->bpos, &s->bcount, &s->cnt_by_id, &s->nl_retry, &s->census, &s->pscr_col, &s->pscr_fr, &s->pscr_st,
-                    &s->dz, &s->ds_row[0], &s->ds_row[1], &s->ds_row[2], &s->ds_row[3], &s->ds_snap};
+                    &s->dz, &s->ds_snap};
     for (DBuf *b : bufs) b->release();
     pm_release(s);
     for (int k = 0; k < 3; ++k) {

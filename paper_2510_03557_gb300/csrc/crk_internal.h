@@ -172,7 +172,8 @@ void launch_group_fill(const Leaves &lv, int nleaf, int gas_only, const uint32_t
                        cudaStream_t st, const uint32_t *nl_dev = nullptr);
 // mask (optional): leaves without a 1 get an empty row
 void launch_pair_count(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, int nleaf,
-                       int hydro, uint32_t *counts, cudaStream_t st, const uint8_t *mask = nullptr);
+                       int hydro, uint32_t *counts, cudaStream_t st, const uint8_t *mask = nullptr,
+                       const uint32_t *nl_dev = nullptr);
 void launch_pair_scratch(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, int nleaf, int hydro,
                          uint32_t *counts, uint32_t cap, uint32_t *col, float4 *frame, uint32_t *start,
                          uint32_t *overflow, cudaStream_t st, const uint8_t *mask = nullptr,
@@ -182,7 +183,7 @@ void launch_pair_compact(int nleaf, uint32_t cap, const uint32_t *counts, const 
                          float4 *frame, uint32_t *start, cudaStream_t st);
 void launch_pair_fill(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, int nleaf,
                       int hydro, const uint32_t *row, uint32_t *col, float4 *frame, uint32_t *start,
-                      cudaStream_t st, const uint8_t *mask = nullptr);
+                      cudaStream_t st, const uint8_t *mask = nullptr, const uint32_t *nl_dev = nullptr);
 
 // ---- passes (passes.cu) ----
 void launch_records(const PassArgs &a, int mixed, cudaStream_t st);
@@ -234,25 +235,22 @@ enum DevSize {
     DZ_GGAS = 2,        // gas target groups (0 after an overflow)
     DZ_GALL = 3,        // all target groups (0 after an overflow)
     DZ_ROWS = 4,        // hydro list rows the groups need
-    DZ_OVF = 5,         // overflow bits: 1 leaves, 2 pair rows, 4 list rows, 8 a list outgrew its rows
-    DZ_PAIR_OVF = 6,    // set by the pair walk when a leaf has more pairs than a row holds
+    DZ_OVF = 5,         // overflow bits: 1 leaves, 2 leaf pairs, 4 list rows, 8 a list outgrew its rows
     DZ_STATS = 7,       // 2 words: statistics of the leaf cut (unused here)
+    DZ_NPH = 10,        // hydro leaf pairs
+    DZ_NPG = 11,        // gravity leaf pairs
     DZ_QUEUE = 16,      // kQueueSlots words: work-queue heads
     DZ_WORDS = 48
 };
 constexpr int kQueueSlots = 16;
-// stage 0 after the leaf scan (cap: leaf capacity), 1 after the pair walk,
-// 2 after the group scans, 3 after the list-row scan (cap: row capacity), 4
-// after the list fill (flag: the fill's retry word).  An overflow zeroes the
+// stage 0 after the leaf scan (cap: leaf capacity), 1 and 5 after the hydro
+// and gravity pair-count scans (cap: their capacities), 2 after the group
+// scans, 3 after the list-row scan (cap: row capacity), 4 after the list fill
+// (flag: the fill's retry word).  An overflow zeroes the
 // counts the rest of the step launches over, so that it touches nothing
 // beyond its buffers; the host then restores the state and steps again with
 // larger buffers.
 void launch_ds_check(uint32_t *dz, int stage, uint32_t cap, const uint32_t *flag, cudaStream_t st);
-// Row begin and end of leaves in rows of fixed capacity: beg = L * cap, end =
-// beg + min(count, cap), for L < nleaf (the capacity of the leaf arrays).
-void launch_fixed_rows(const uint32_t *counts, int nleaf, uint32_t cap, uint32_t *beg, uint32_t *end,
-                       cudaStream_t st);
-
 // ---- hierarchical time steps (bins.cu) ----
 void launch_kick_drift_bins(const State &s, const BoxDev *boxes, int64_t n, int sub, int depth, double d,
                             unsigned long long *nfloor, cudaStream_t st);

@@ -364,7 +364,8 @@ __global__ void ds_check_k(uint32_t *dz, int stage, uint32_t cap, const uint32_t
 {
     uint32_t ovf = dz[DZ_OVF];
     if (stage == 0 && dz[DZ_NLEAF_RAW] > cap) ovf |= 1u;
-    if (stage == 1 && dz[DZ_PAIR_OVF]) ovf |= 2u;
+    if (stage == 1 && dz[DZ_NPH] > cap) ovf |= 2u;
+    if (stage == 5 && dz[DZ_NPG] > cap) ovf |= 2u;
     if (stage == 3 && dz[DZ_ROWS] > cap) ovf |= 4u;
     if (stage == 4 && flag && *flag) ovf |= 8u;
     dz[DZ_OVF] = ovf;
@@ -376,29 +377,11 @@ __global__ void ds_check_k(uint32_t *dz, int stage, uint32_t cap, const uint32_t
     }
 }
 
-__global__ void fixed_rows_k(const uint32_t *__restrict__ counts, int nleaf, uint32_t cap, uint32_t *beg,
-                             uint32_t *end)
-{
-    const int L = blockIdx.x * blockDim.x + threadIdx.x;
-    if (L >= nleaf) return;
-    const uint32_t c = counts[L];
-    beg[L] = (uint32_t)L * cap;
-    end[L] = (uint32_t)L * cap + (c < cap ? c : cap);
-}
-
 }  // namespace
 
 void launch_ds_check(uint32_t *dz, int stage, uint32_t cap, const uint32_t *flag, cudaStream_t st)
 {
     ds_check_k<<<1, 1, 0, st>>>(dz, stage, cap, flag);
-    note_launches(1);
-}
-
-void launch_fixed_rows(const uint32_t *counts, int nleaf, uint32_t cap, uint32_t *beg, uint32_t *end,
-                       cudaStream_t st)
-{
-    if (nleaf <= 0) return;
-    fixed_rows_k<<<nblocks(nleaf), kT, 0, st>>>(counts, nleaf, cap, beg, end);
     note_launches(1);
 }
 

@@ -46,8 +46,6 @@ struct DBuf {
 // Leaf pairs a leaf's hydro and gravity rows hold before the lists are
 // walked twice (count, then fill).
 constexpr uint32_t kPairCapH = 128, kPairCapG = 256;
-// Longest hydro leaf-pair row a list entry can address (24 bits of offset).
-constexpr uint32_t kMaxPairRow = 1u << 24;
 // Octree levels of a 21-bit-per-axis Morton key (all of them).
 constexpr int kAllLevels = 21;
 
@@ -128,11 +126,10 @@ struct crk_sim {
     // buffers swap at every sort), the state snapshot a batch restores after
     // an overflow
     DBuf dz;                            // device sizes block (DevSize words)
-    DBuf ds_row[4];                     // fixed-row begin / end of the hydro and gravity lists
     DBuf ds_snap;                       // state snapshot of a batch
     int ds_cap_leaf = 0;
     uint32_t ds_cap_items = 0, ds_cap_rows = 0;
-    uint32_t ds_cap_ph = 0, ds_cap_pg = 0;  // entries of a leaf's fixed hydro / gravity pair row
+    uint32_t ds_cap_ph = 0, ds_cap_pg = 0;  // entries of the hydro / gravity leaf-pair lists
     double ds_margin = 1.25;            // capacity over the last sizes (grows after an overflow)
     cudaStream_t cap_st = nullptr;      // stream the graph is captured on
     cudaGraphExec_t graph = nullptr;

@@ -899,12 +899,12 @@ void launch_build_nodes(Nodes &nd, int nleaf, cudaStream_t st)
 }
 
 void launch_pair_count(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, int nleaf,
-                       int hydro, uint32_t *counts, cudaStream_t st, const uint8_t *mask)
+                       int hydro, uint32_t *counts, cudaStream_t st, const uint8_t *mask, const uint32_t *nl_dev)
 {
     if (nleaf <= 0) return;
     pair_walk_k<0><<<grid_for(nleaf, 128), 128, 0, st>>>(nd, lv, boxes, nleaf, hydro, counts,
                                                            nullptr, nullptr, nullptr, nullptr, 0u, nullptr, mask,
-                                                           nullptr);
+                                                           nl_dev);
     note_launches(1);
 }
 
@@ -930,11 +930,11 @@ void launch_pair_compact(int nleaf, uint32_t cap, const uint32_t *counts, const 
 
 void launch_pair_fill(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, int nleaf,
                       int hydro, const uint32_t *row, uint32_t *col, float4 *frame, uint32_t *start,
-                      cudaStream_t st, const uint8_t *mask)
+                      cudaStream_t st, const uint8_t *mask, const uint32_t *nl_dev)
 {
     if (nleaf <= 0) return;
     pair_walk_k<1><<<grid_for(nleaf, 128), 128, 0, st>>>(nd, lv, boxes, nleaf, hydro, nullptr,
-                                                           row, col, frame, start, 0u, nullptr, mask, nullptr);
+                                                           row, col, frame, start, 0u, nullptr, mask, nl_dev);
     note_launches(1);
 }
 
