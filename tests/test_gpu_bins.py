@@ -89,7 +89,10 @@ def test_bins_mixed_match_oracle(crk, reference):
 
 def test_depth_zero_is_crk_step(crk):
     box = _box()
-    with crk.Sim(crk.box_physics(box), precision=1) as a, crk.Sim(crk.box_physics(box), precision=1) as b:
+    # host-sized steps on both sides (the hierarchical steps are host-sized)
+    flags = crk.CRK_FLAG_NO_GRAPH
+    with crk.Sim(crk.box_physics(box), precision=1, flags=flags) as a, \
+            crk.Sim(crk.box_physics(box), precision=1, flags=flags) as b:
         a.load(box)
         b.load(box)
         counts = crk.crk_step_bins(a.handle, 1e-3, 0, 3, ETA, COURANT)
