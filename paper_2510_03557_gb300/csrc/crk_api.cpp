@@ -875,18 +875,42 @@ static int run_step_ds(crk_sim *s)
     Nodes nd = s->nd;
     launch_build_nodes(nd, capL, st);
     uint32_t *hrow = s->hrow.as<uint32_t>(), *grow = s->grow.as<uint32_t>();
-    launch_pair_count(nd, s->lv, bd, capL, 1, s->hcnt.as<uint32_t>(), st, nullptr, nld);
-    launch_pair_count(nd, s->lv, bd, capL, 0, s->gcnt.as<uint32_t>(), st, nullptr, nld);
-    scan_exclusive_u32(s->hcnt.as<uint32_t>(), hrow, capL, dz + DZ_NPH, tmp, st);
-    scan_exclusive_u32(s->gcnt.as<uint32_t>(), grow, capL, dz + DZ_NPG, tmp, st);
-    launch_ds_check(dz, 1, s->ds_cap_ph, nullptr, st);
-    launch_ds_check(dz, 5, s->ds_cap_pg, nullptr, st);
-    CK(cudaMemcpyAsync(hrow + capL, dz + DZ_NPH, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
-    CK(cudaMemcpyAsync(grow + capL, dz + DZ_NPG, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
-    launch_pair_fill(nd, s->lv, bd, capL, 1, hrow, s->hcol.as<uint32_t>(), s->hfr.as<float4>(),
-                     s->hsj.as<uint32_t>(), st, nullptr, nld);
-    launch_pair_fill(nd, s->lv, bd, capL, 0, grow, s->gcol.as<uint32_t>(), s->gfr.as<float4>(), nullptr, st,
-                     nullptr, nld);
+    uint32_t *hc = s->hcnt.as<uint32_t>(), *gcn = s->gcnt.as<uint32_t>();
+    if (s->ds_one_walk) {
+        // one walk into rows of fixed capacity (the first step's rows fitted),
+        // packed after the scan; a row that does not fit is an overflow
+        uint32_t *scol_h = s->pscr_col.as<uint32_t>(), *scol_g = scol_h + nl * kPairCapH;
+        float4 *sfr_h = s->pscr_fr.as<float4>(), *sfr_g = sfr_h + nl * kPairCapH;
+        CK(cudaMemsetAsync(dz + DZ_ROW_OVF, 0, sizeof(uint32_t), st));
+        launch_pair_scratch(nd, s->lv, bd, capL, 1, hc, kPairCapH, scol_h, sfr_h, s->pscr_st.as<uint32_t>(),
+                            dz + DZ_ROW_OVF, st, nullptr, nld);
+        launch_pair_scratch(nd, s->lv, bd, capL, 0, gcn, kPairCapG, scol_g, sfr_g, nullptr, dz + DZ_ROW_OVF, st,
+                            nullptr, nld);
+        launch_ds_check(dz, 6, 0u, dz + DZ_ROW_OVF, st);
+        scan_exclusive_u32(hc, hrow, capL, dz + DZ_NPH, tmp, st);
+        scan_exclusive_u32(gcn, grow, capL, dz + DZ_NPG, tmp, st);
+        launch_ds_check(dz, 1, s->ds_cap_ph, nullptr, st);
+        launch_ds_check(dz, 5, s->ds_cap_pg, nullptr, st);
+        CK(cudaMemcpyAsync(hrow + capL, dz + DZ_NPH, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(grow + capL, dz + DZ_NPG, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+        launch_pair_compact(capL, kPairCapH, hc, hrow, scol_h, sfr_h, s->pscr_st.as<uint32_t>(),
+                            s->hcol.as<uint32_t>(), s->hfr.as<float4>(), s->hsj.as<uint32_t>(), st, nld);
+        launch_pair_compact(capL, kPairCapG, gcn, grow, scol_g, sfr_g, nullptr, s->gcol.as<uint32_t>(),
+                            s->gfr.as<float4>(), nullptr, st, nld);
+    } else {
+        launch_pair_count(nd, s->lv, bd, capL, 1, hc, st, nullptr, nld);
+        launch_pair_count(nd, s->lv, bd, capL, 0, gcn, st, nullptr, nld);
+        scan_exclusive_u32(hc, hrow, capL, dz + DZ_NPH, tmp, st);
+        scan_exclusive_u32(gcn, grow, capL, dz + DZ_NPG, tmp, st);
+        launch_ds_check(dz, 1, s->ds_cap_ph, nullptr, st);
+        launch_ds_check(dz, 5, s->ds_cap_pg, nullptr, st);
+        CK(cudaMemcpyAsync(hrow + capL, dz + DZ_NPH, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(grow + capL, dz + DZ_NPG, sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+        launch_pair_fill(nd, s->lv, bd, capL, 1, hrow, s->hcol.as<uint32_t>(), s->hfr.as<float4>(),
+                         s->hsj.as<uint32_t>(), st, nullptr, nld);
+        launch_pair_fill(nd, s->lv, bd, capL, 0, grow, s->gcol.as<uint32_t>(), s->gfr.as<float4>(), nullptr, st,
+                         nullptr, nld);
+    }
     uint32_t *gc = s->grp_cnt.as<uint32_t>(), *go = s->grp_off.as<uint32_t>();
     launch_group_count(s->lv, capL, 1, gc, st, nld);
     launch_group_count(s->lv, capL, 0, gc + nl, st, nld);
@@ -958,6 +982,13 @@ static int ds_prepare(crk_sim *s)
     RET(s->hsj.ensure(cph * 4));
     RET(s->gcol.ensure(cpg * 4));
     RET(s->gfr.ensure(cpg * 16));
+    // the first step's walk fitted its fixed rows: walk once, as it did
+    s->ds_one_walk = s->pair_two_pass_left == 0;
+    if (s->ds_one_walk) {
+        RET(s->pscr_col.ensure(nl * (kPairCapH + kPairCapG) * sizeof(uint32_t)));
+        RET(s->pscr_fr.ensure(nl * (kPairCapH + kPairCapG) * sizeof(float4)));
+        RET(s->pscr_st.ensure(nl * kPairCapH * sizeof(uint32_t)));
+    }
     RET(s->grp_cnt.ensure(nl * 4 * 2));
     RET(s->grp_off.ensure(nl * 4 * 2));
     RET(s->grp_gas.ensure(ni * sizeof(uint2)));

@@ -180,7 +180,7 @@ void launch_pair_scratch(const Nodes &nd, const Leaves &lv, const BoxDev *boxes,
                          const uint32_t *nl_dev = nullptr);
 void launch_pair_compact(int nleaf, uint32_t cap, const uint32_t *counts, const uint32_t *row,
                          const uint32_t *scol, const float4 *sframe, const uint32_t *sstart, uint32_t *col,
-                         float4 *frame, uint32_t *start, cudaStream_t st);
+                         float4 *frame, uint32_t *start, cudaStream_t st, const uint32_t *nl_dev = nullptr);
 void launch_pair_fill(const Nodes &nd, const Leaves &lv, const BoxDev *boxes, int nleaf,
                       int hydro, const uint32_t *row, uint32_t *col, float4 *frame, uint32_t *start,
                       cudaStream_t st, const uint8_t *mask = nullptr, const uint32_t *nl_dev = nullptr);
@@ -239,12 +239,14 @@ enum DevSize {
     DZ_STATS = 7,       // 2 words: statistics of the leaf cut (unused here)
     DZ_NPH = 10,        // hydro leaf pairs
     DZ_NPG = 11,        // gravity leaf pairs
+    DZ_ROW_OVF = 12,    // set by the one-walk pair fill when a leaf's pairs exceed its fixed row
     DZ_QUEUE = 16,      // kQueueSlots words: work-queue heads
     DZ_WORDS = 48
 };
 constexpr int kQueueSlots = 16;
 // stage 0 after the leaf scan (cap: leaf capacity), 1 and 5 after the hydro
-// and gravity pair-count scans (cap: their capacities), 2 after the group
+// and gravity pair-count scans (cap: their capacities), 6 after a one-walk
+// pair fill into fixed rows (flag: its row-overflow word), 2 after the group
 // scans, 3 after the list-row scan (cap: row capacity), 4 after the list fill
 // (flag: the fill's retry word).  An overflow zeroes the
 // counts the rest of the step launches over, so that it touches nothing

@@ -368,6 +368,7 @@ __global__ void ds_check_k(uint32_t *dz, int stage, uint32_t cap, const uint32_t
     if (stage == 5 && dz[DZ_NPG] > cap) ovf |= 2u;
     if (stage == 3 && dz[DZ_ROWS] > cap) ovf |= 4u;
     if (stage == 4 && flag && *flag) ovf |= 8u;
+    if (stage == 6 && flag && *flag) ovf |= 2u;
     dz[DZ_OVF] = ovf;
     if (stage == 0) dz[DZ_NLEAF] = ovf ? 0u : dz[DZ_NLEAF_RAW];
     if (ovf) {

@@ -498,13 +498,15 @@ __device__ __forceinline__ void for_each_item(uint32_t n_host, const uint32_t *n
         return;
     }
     const uint32_t n = n_dev ? *n_dev : n_host;
-    for (;;) {
-        uint32_t gi = 0;
-        if (lane == 0) gi = atomicAdd(queue + slot, 1u);
-        gi = __shfl_sync(0xffffffffu, gi, 0);
-        if (gi >= n) break;
+    // the next item is taken while the current one runs (its latency hidden)
+    uint32_t next = 0;
+    if (lane == 0) next = atomicAdd(queue + slot, 1u);
+    next = __shfl_sync(0xffffffffu, next, 0);
+    while (next < n) {
+        const uint32_t gi = next;
+        if (lane == 0) next = atomicAdd(queue + slot, 1u);
         body(gi);
-        __syncwarp();
+        next = __shfl_sync(0xffffffffu, next, 0);
     }
 }
 

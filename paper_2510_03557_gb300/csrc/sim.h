@@ -130,6 +130,7 @@ struct crk_sim {
     int ds_cap_leaf = 0;
     uint32_t ds_cap_items = 0, ds_cap_rows = 0;
     uint32_t ds_cap_ph = 0, ds_cap_pg = 0;  // entries of the hydro / gravity leaf-pair lists
+    bool ds_one_walk = false;           // leaf pairs walked once into fixed rows, then packed
     double ds_margin = 1.25;            // capacity over the last sizes (grows after an overflow)
     cudaStream_t cap_st = nullptr;      // stream the graph is captured on
     cudaGraphExec_t graph = nullptr;

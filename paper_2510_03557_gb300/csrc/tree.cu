@@ -646,11 +646,11 @@ __global__ void pair_walk_k(Nodes nd, Leaves lv, const BoxDev *__restrict__ boxe
 __global__ void pair_compact_k(int nleaf, uint32_t cap, const uint32_t *__restrict__ counts,
                                const uint32_t *__restrict__ row, const uint32_t *__restrict__ scol,
                                const float4 *__restrict__ sframe, const uint32_t *__restrict__ sstart,
-                               uint32_t *col, float4 *frame, uint32_t *start)
+                               uint32_t *col, float4 *frame, uint32_t *start, const uint32_t *nl_dev)
 {
     const int I = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
     const uint32_t lane = lane_id();
-    if (I >= nleaf) return;
+    if (I >= leaves_of(nleaf, nl_dev)) return;
     const uint32_t c = counts[I], r = row[I];
     const size_t b = (size_t)I * cap;
     for (uint32_t t = lane; t < c; t += 32u) {
@@ -920,11 +920,11 @@ void launch_pair_scratch(const Nodes &nd, const Leaves &lv, const BoxDev *boxes,
 
 void launch_pair_compact(int nleaf, uint32_t cap, const uint32_t *counts, const uint32_t *row,
                          const uint32_t *scol, const float4 *sframe, const uint32_t *sstart, uint32_t *col,
-                         float4 *frame, uint32_t *start, cudaStream_t st)
+                         float4 *frame, uint32_t *start, cudaStream_t st, const uint32_t *nl_dev)
 {
     if (nleaf <= 0) return;
     pair_compact_k<<<grid_for((int64_t)nleaf * 32, kT), kT, 0, st>>>(nleaf, cap, counts, row, scol, sframe,
-                                                                     sstart, col, frame, start);
+                                                                     sstart, col, frame, start, nl_dev);
     note_launches(1);
 }
 
