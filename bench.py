@@ -258,7 +258,17 @@ def serve_bench(crk, wl, args):
         p64 += b.n * steps
         s.close()
     small = np.array(sizes) < 65536
+    bounds = [0, 65536, 524288, 1 << 62]
+    per_class = []
+    for k in range(3):
+        sel = (np.array(sizes) >= bounds[k]) & (np.array(sizes) < bounds[k + 1])
+        if sel.any():
+            per_class.append({"particles": f"[{bounds[k]}, {bounds[k + 1] if k < 2 else 'inf'})",
+                              "requests": int(sel.sum()),
+                              "p50_ms": round(float(np.percentile(lat[sel], 50)), 3),
+                              "p99_ms": round(float(np.percentile(lat[sel], 99)), 3)})
     return {"requests": len(res), "of": 2000, "steps_per_request": steps,
+            "per_size_class": per_class,
             "p50_ms": round(float(np.percentile(lat, 50)), 3),
             "p99_ms": round(float(np.percentile(lat, 99)), 3),
             "p99_over_p50": round(float(np.percentile(lat, 99) / np.percentile(lat, 50)), 3),
