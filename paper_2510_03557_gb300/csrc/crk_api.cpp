@@ -248,6 +248,67 @@ int check_physics(const crk_physics &p)
     return CRK_OK;
 }
 
+// The short-range factor of the Gaussian split, S(u) = erfc(u) + (2/sqrt(pi))
+// u exp(-u^2) with u = r / (2 r_s), has dS/du = -(4/sqrt(pi)) u^2 exp(-u^2)
+// and S(0) = 1, so S(u) = 1 - u^3 Q(u^2) with Q(s) = (4/sqrt(pi)) times the
+// integral over t in [0, 1] of t^2 exp(-s t^2), an entire function of s.
+// Its Taylor coefficients about the middle c of [0, s_max] (s_max the
+// square of the box's largest u, at r_cut) are (4/sqrt(pi)) / k! times the
+// integral of t^2 (-t^2)^k exp(-c t^2), evaluated here by 48-point
+// Gauss-Legendre quadrature (nodes by Newton's method on the Legendre
+// recurrence); the series is cut where a term's bound over the range falls
+// below 1e-18 of Q's smallest value.  Beyond u = 3 (S < 5e-4) the
+// subtraction 1 - u^3 Q would cost more than four digits: erfc is kept.
+static void fit_split_series(BoxDev &b)
+{
+    b.q_deg = 0;
+    if (!(b.r_split > 0.0) || !(b.r_cut > 0.0)) return;
+    const double umax = b.r_cut / (2.0 * b.r_split);
+    if (!(umax <= 3.0)) return;
+    const double smax = umax * umax, c = 0.5 * smax, half = 0.5 * smax;
+    constexpr int NQ = 48;
+    double x[NQ], w[NQ];
+    for (int i = 0; i < NQ; ++i) {
+        double z = std::cos(M_PI * (i + 0.75) / (NQ + 0.5)), dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= NQ; ++k) {
+                const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = NQ * (z * p1 - p0) / (z * z - 1.0);
+            const double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        x[i] = 0.5 * (z + 1.0);                      // node on [0, 1]
+        w[i] = 1.0 / ((1.0 - z * z) * dp * dp);      // half the [-1, 1] weight
+    }
+    const double norm = 4.0 / std::sqrt(M_PI);
+    // smallest Q on the range is at s_max (Q decreases)
+    double qmin = 0.0;
+    for (int i = 0; i < NQ; ++i) qmin += w[i] * x[i] * x[i] * std::exp(-smax * x[i] * x[i]);
+    qmin *= norm;
+    double fact = 1.0;
+    int deg = 0;
+    for (int k = 0; k < kSplitTerms; ++k) {
+        if (k > 0) fact *= k;
+        double sum = 0.0;
+        for (int i = 0; i < NQ; ++i) {
+            const double t2 = x[i] * x[i];
+            sum += w[i] * t2 * std::pow(-t2, k) * std::exp(-c * t2);
+        }
+        b.q_coef[k] = norm * sum / fact;
+        deg = k + 1;
+        if (std::fabs(b.q_coef[k]) * std::pow(half, k) < 1e-18 * qmin && k >= 4) break;
+    }
+    if (std::fabs(b.q_coef[deg - 1]) * std::pow(half, deg - 1) >= 1e-16 * qmin) return;  // series too long
+    b.q_deg = deg;
+    b.q_c = c;
+    b.q_inv4rs2 = 1.0 / (4.0 * b.r_split * b.r_split);
+}
+
 BoxDev box_dev(const crk_physics &p)
 {
     BoxDev b{};
@@ -266,6 +327,7 @@ BoxDev box_dev(const crk_physics &p)
     b.hdt = 0.0;
     b.cm_shift = 63;
     b.active = 1;
+    fit_split_series(b);
     return b;
 }
 

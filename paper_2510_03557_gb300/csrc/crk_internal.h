@@ -17,6 +17,9 @@ struct alignas(4 * sizeof(R)) Vec4 {
     R x, y, z, w;
 };
 
+// Terms of the FP64 short-range factor's polynomial (BoxDev::q_coef).
+constexpr int kSplitTerms = 40;
+
 // Per-box physics as the kernels read it (one entry per box slot).
 struct BoxDev {
     double L, halfL, G, gamma, r_cut, r_split, eps_soft;
@@ -24,6 +27,13 @@ struct BoxDev {
     double dt, hdt;          // step of the current KDK step (0 for a force-only step)
     int cm_shift;            // sort-key shift that leaves (box, species, chaining-mesh bin)
     int active;              // 0: slot holds no live particles (keys sort them last)
+    // the FP64 short-range factor S = 1 - u^3 Q(u^2), u = r / (2 r_s): Q as a
+    // polynomial in (u^2 - q_c) of degree q_deg - 1 over the box's range of
+    // u^2 (q_deg = 0: S from erfc and exp, for ranges where that form loses
+    // too many digits to cancellation)
+    int q_deg;
+    double q_c, q_inv4rs2;
+    double q_coef[kSplitTerms];
 };
 
 // Particle state in sorted order, FP64 masters (structure of arrays).

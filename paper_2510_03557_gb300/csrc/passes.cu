@@ -1478,11 +1478,30 @@ __device__ __forceinline__ R split_S(R r, R inv2rs)
 // G m_j exp(-u^2) = 2^(log2(G m_j) - v^2) in one ex2.
 constexpr float kMinS2 = 1e-24f;
 
+// The plain form's S(r) from the box's series S = 1 - u^3 Q(u^2) (no erfc or
+// exp: Q's coefficients, staged in the warp's shared memory, by Horner's
+// rule about q_c), or from erfc and exp when the box has no series.
+struct SplitSeries {
+    const double *coef;  // warp shared memory
+    int deg;
+    double c, inv4rs2;
+};
+
+__device__ __forceinline__ double split_S_series(double r2, const SplitSeries &ss)
+{
+    const double s = r2 * ss.inv4rs2;  // u^2
+    const double t = s - ss.c;
+    double q = ss.coef[ss.deg - 1];
+    for (int k = ss.deg - 2; k >= 0; --k) q = fma(q, t, ss.coef[k]);
+    return fma(-s * sqrt(s), q, 1.0);
+}
+
 template <typename R, bool WRAP, bool COUNT>
 __device__ __forceinline__ void gravity_tile(const Vec4<R> *tile, const uint8_t *tslot, uint32_t K,
                                              const Target<R> &q, R L, R hL, R rc2, double rc2x, R gb, R e2,
                                              R inv2rs, bool same, bool act, const State &s, uint32_t i,
-                                             uint32_t sJ, double Ld, R &ax, R &ay, R &az, int &nc, uint64_t &hs)
+                                             uint32_t sJ, double Ld, R &ax, R &ay, R &az, int &nc, uint64_t &hs,
+                                             const SplitSeries &ss)
 {
     const float kv = (float)inv2rs * (float)kSqrtLog2e;
 #pragma unroll 4
@@ -1503,6 +1522,10 @@ __device__ __forceinline__ void gravity_tile(const Vec4<R> *tile, const uint8_t 
             const float sw = Real<float>::exp2(fmaf(-v, v, (float)rj.w)) * fmaf(kTwoOverSqrtPiV, v, poly);
             const float is = Real<float>::rsqrt((float)(r2 + e2));
             f = (R)(sw * is * is * is);  // G m_j S(r) (r^2 + eps^2)^{-3/2}
+        } else if (ss.deg > 0) {
+            const double S = split_S_series((double)r2, ss);
+            const double is = rsqrt((double)(r2 + e2));
+            f = (R)(rj.w * S * (is * is * is));  // rj.w = G m_j
         } else {
             const R S = split_S<R>(Real<R>::sqrt_(r2), inv2rs);
             const R s2 = r2 + e2;
@@ -1546,6 +1569,15 @@ __global__ void __launch_bounds__(kBlock) gravity_k(PassArgs a)
     rel_pos(ri, a.lv, I, Ld, px, py, pz);
     const WarpBox wb = warp_box(px, py, pz, G.act);
     const float Rc = (float)bx.r_cut * 1.0001f + 1e-6f * (float)Ld;
+    // the plain form's split series of this box, in the warp's shared memory
+    SplitSeries ss{nullptr, 0, 0.0, 0.0};
+    if (!Real<R>::mixed && bx.q_deg > 0) {
+        __shared__ double qcoef[kWarps][kSplitTerms];
+        __syncwarp();
+        for (int k = (int)lane; k < bx.q_deg; k += 32) qcoef[w][k] = bx.q_coef[k];
+        __syncwarp();
+        ss = SplitSeries{qcoef[w], bx.q_deg, bx.q_c, bx.q_inv4rs2};
+    }
     R ax = 0, ay = 0, az = 0;
     int nc = 0;
     uint64_t hs = 0, tested = 0;
@@ -1569,9 +1601,9 @@ __global__ void __launch_bounds__(kBlock) gravity_k(PassArgs a)
         // force is formed for all and kept where r < r_cut (a select, so that
         // nothing computed for an out-of-range pair reaches the sums)
         if (q.wrap) gravity_tile<R, true, COUNT>(tile, tslot, K, q, L, hL, rc2, rc2x, gb, e2, inv2rs, same,
-                                                 G.act, a.s, i, sJ, Ld, ax, ay, az, nc, hs);
+                                                 G.act, a.s, i, sJ, Ld, ax, ay, az, nc, hs, ss);
         else gravity_tile<R, false, COUNT>(tile, tslot, K, q, L, hL, rc2, rc2x, gb, e2, inv2rs, same,
-                                           G.act, a.s, i, sJ, Ld, ax, ay, az, nc, hs);
+                                           G.act, a.s, i, sJ, Ld, ax, ay, az, nc, hs, ss);
     }
     if (COUNT && a.census && lane == 0) {
         atomicAdd(&a.census[2], 32ull * tested);
