@@ -598,8 +598,8 @@ def headline_config(args, world: int) -> dict:
     """The headline workload's config, as both arms report it: the clustered
     2 x n^3 box of the generator (seed 3), KDK at the box's Courant step."""
     n = 2 * args.n ** 3
-    return {"workload": f"clustered 2x{args.n}^3 (half uniform, half in 512 Plummer spheres of scale 0.002, "
-                        f"kNN h), FP32-mixed, KDK steps at the box's Courant dt",
+    return {"workload": f"clustered 2x{args.n}^3 (half uniform, half in {getattr(args, 'nsphere', 512)} Plummer "
+                        f"spheres of scale 0.002, kNN h), FP32-mixed, KDK steps at the box's Courant dt",
             "particles": n,
             "leaf_cap": "autotuned over (64, 128) with the gravity form" if args.autotune else args.leaf_cap,
             "rebuild_every": args.rebuild_every,
@@ -619,7 +619,7 @@ def run_reference(args):
         return
     from paper_2510_03557_gb300 import workloads as wl
 
-    box = wl.clustered_box(args.n, seed=3)
+    box = wl.clustered_box(args.n, seed=3, nsphere=args.nsphere)
     label = f"clustered 2x{args.n}^3"
     steps = []
     cb = None
@@ -741,6 +741,11 @@ def main():
     ap.add_argument("--bin-courant", type=float, default=0.25)
     ap.add_argument("--sample", type=int, default=64, help="oracle sample of the precision study")
     ap.add_argument("--n", type=int, default=256, help="clustered box: lattice size per species (2 n^3)")
+    ap.add_argument("--nsphere", type=int, default=512,
+                    help="clustered box: Plummer spheres (8 at n = 64 gives the 32,768-particle cores of "
+                         "n = 256 with 512; the small case of the profiles)")
+    ap.add_argument("--pairs-once", action="store_true",
+                    help="with --no-autotune: gravity with each pair evaluated once")
     ap.add_argument("--gauss-n", type=int, default=128, help="Gaussian-field box: 2 n^3 particles")
     ap.add_argument("--leaf-cap", type=int, default=128)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
@@ -825,7 +830,7 @@ def main():
         legs[name] = round(now - t_leg, 1)
         t_leg = now
 
-    box = wl.clustered_box(args.n, seed=3)
+    box = wl.clustered_box(args.n, seed=3, nsphere=args.nsphere)
     leg("setup")
     t_gen = legs["setup"]
     N = box.n
@@ -836,7 +841,8 @@ def main():
 
     # ---------------- mixed form, device-resident (the headline value)
     sim = crk.Sim(phys, leaf_cap=args.leaf_cap, precision=crk.CRK_MIXED, stream=stream,
-                  rebuild_every=args.rebuild_every)
+                  rebuild_every=args.rebuild_every,
+                  flags=crk.CRK_FLAG_GRAVITY_PAIRS_ONCE if (args.pairs_once and not args.autotune) else 0)
     sim.load(box)
     tune = None
     cap = args.leaf_cap

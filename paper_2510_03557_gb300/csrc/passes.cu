@@ -1003,13 +1003,15 @@ struct ListPipe {
         j1 = cnt > 0u ? entry_index(srow, e1) : 0u;
         j2 = cnt > 1u ? entry_index(srow, e2) : 0u;
     }
-    // entry m, (e1, j1), was taken: (e1, j1) becomes entry m + 1
+    // entry m, (e1, j1), was taken: (e1, j1) becomes entry m + 1; with
+    // GATHER_ONLY the index of an entry outside the gather set is not looked up
+    template <bool GATHER_ONLY = false>
     __device__ __forceinline__ void step(const PassArgs &a, const uint32_t *srow, uint32_t m)
     {
         e1 = e2;
         j1 = j2;
         e2 = e3;
-        j2 = m + 2u < cnt ? entry_index(srow, e3) : 0u;
+        j2 = (m + 2u < cnt && (!GATHER_ONLY || (e3 & kGather))) ? entry_index(srow, e3) : 0u;
         e3 = m + 3u < cnt ? a.nl_j[e0 + (size_t)(m + 3u) * 32u] : 0u;
     }
 };
@@ -1243,15 +1245,18 @@ __global__ void __launch_bounds__(kBlock, moments_min_blocks<R>()) moments_k(Pas
     ListPipe pipe(a, gi, lane, G.act ? a.nl_cnt[i] : 0u, srow);
     MomentAcc<R> acc;
     acc.zero();
-    // the neighbour's record and frame one entry ahead
+    // the neighbour's record and frame one entry ahead (gather entries only:
+    // the moments sum over the gather set, the lists hold the union set)
     R4 rn;
     float4 fn;
     uint32_t en = 0;
     if (pipe.cnt > 0u) {
         en = pipe.e1;
-        rn = rec0[pipe.j1];
-        fn = entry_frame(frow, en);
-        pipe.step(a, srow, 0u);
+        if (en & kGather) {
+            rn = rec0[pipe.j1];
+            fn = entry_frame(frow, en);
+        }
+        pipe.template step<true>(a, srow, 0u);
     }
     for (uint32_t k = 0; k < pipe.cnt; ++k) {
         const R4 rj = rn;
@@ -1259,9 +1264,11 @@ __global__ void __launch_bounds__(kBlock, moments_min_blocks<R>()) moments_k(Pas
         const uint32_t e = en;
         if (k + 1u < pipe.cnt) {
             en = pipe.e1;
-            rn = rec0[pipe.j1];
-            fn = entry_frame(frow, en);
-            pipe.step(a, srow, k + 1u);
+            if (en & kGather) {
+                rn = rec0[pipe.j1];
+                fn = entry_frame(frow, en);
+            }
+            pipe.template step<true>(a, srow, k + 1u);
         }
         if (!(e & kGather)) continue;
         R dx, dy, dz;

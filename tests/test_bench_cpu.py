@@ -105,7 +105,7 @@ def test_reference_arm_line(tmp_path):
                          capture_output=True, text=True, check=True,
                          cwd=bench.ROOT, timeout=600).stdout.strip().splitlines()
     line = json.loads(out[-1])
-    args = argparse.Namespace(n=32, leaf_cap=128, rebuild_every=1, autotune=True)
+    args = argparse.Namespace(n=32, nsphere=512, leaf_cap=128, rebuild_every=1, autotune=True)
     assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == bench.UNIT
     assert line["config"] == bench.headline_config(args, 1)
     assert "clustered 2x32^3" in line["config"]["workload"]
