@@ -52,8 +52,8 @@ FLOP_PER_PAIR = {"density": 22, "moments": 125, "hydro": 183, "gravity": 41}
 # leaf capacity 128, scaled to the launch by the particles it processes.  They
 # describe the kernels of the csrc/passes.cu with this SHA-256 only; for any
 # other source the bench reports no traffic.
-TRAFFIC_SOURCE_SHA256 = ""
-TRAFFIC_BYTES_PER_PARTICLE = {}
+TRAFFIC_SOURCE_SHA256 = "1b3a759651a2b9acfc9e824a4c344e2fe445540e9fec0bdefb680b7f94c51a92"
+TRAFFIC_BYTES_PER_PARTICLE = {"gravity_pairs_once": 72.7}
 
 
 def _traffic(kernel: str, particles: int, leaf_cap: int):
@@ -1008,7 +1008,9 @@ def main():
             "config": headline_config(args, world),
             "roofline": {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3),
                          "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                         "traffic": _traffic(dom, N, cap),
+                         "traffic": _traffic(dom + ("_pairs_once" if dom == "gravity" and tune and
+                                                         tune["gravity_form"] == "pairs_once" else "_gather"
+                                                         if dom == "gravity" else ""), N, cap),
                          "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on "
                                            "the clustered generator at 2x64^3 with 8 dense cores, scaled by "
                                            "particles (null when the kernel source or leaf capacity differs from "

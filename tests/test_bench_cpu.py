@@ -72,11 +72,12 @@ def test_traffic_only_for_the_captured_source_and_capacity():
     path = os.path.join(bench.ROOT, "paper_2510_03557_gb300", "csrc", "passes.cu")
     with open(path, "rb") as f:
         same = hashlib.sha256(f.read()).hexdigest() == bench.TRAFFIC_SOURCE_SHA256
-    t = bench._traffic("gravity", 1000, 128)
+    t = bench._traffic("gravity_pairs_once", 1000, 128)
     if same:
-        assert t == round(bench.TRAFFIC_BYTES_PER_PARTICLE["gravity"] * 1000)
+        assert t == round(bench.TRAFFIC_BYTES_PER_PARTICLE["gravity_pairs_once"] * 1000)
     else:
         assert t is None
+    assert bench._traffic("gravity_gather", 1000, 128) is None   # no capture of that kernel's step form
 
 
 def test_fp64_pass_rates():
