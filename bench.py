@@ -525,41 +525,39 @@ def run_precision(args):
     print(json.dumps(line))
 
 
-def run_batched(args):
+def batched_leg(crk, wl, steps: int, warmup: int, stream) -> dict:
     """The batched workload: 64 independent periodic boxes of 2 n^3 particles,
     n drawn (seed 2) from {16, 24, 32, 48, 64}, box b from the Gaussian-field
     generator with seed 1000 + b, all in one handle (one tree and one launch
-    per pass for every box), FP32-mixed, leaf capacity chosen by the library's
-    autotuner.  Beside it the plain FP64 form one box per handle, run one box
-    after another, on the first 8 boxes."""
+    per pass for every box), FP32-mixed, leaf capacity and gravity form chosen
+    by the library's autotuner; the timed steps replayed from a CUDA graph
+    (persistent pass launches draining one device work queue of every box's
+    target groups).  Beside it the plain FP64 form one box per handle, run
+    one box after another, on the first 8 boxes."""
     import torch
 
-    from paper_2510_03557_gb300 import crk
-    from paper_2510_03557_gb300 import workloads as wl
-
-    torch.cuda.set_device(0)
-    crk.lib()
     boxes = wl.batched_boxes(64, seed=2)
     cat = wl.concat_boxes(boxes)
     N = int(cat["offsets"][-1])
     phys = [crk.box_physics(b) for b in boxes]
     dts = [b.dt for b in boxes]
-    stream = torch.cuda.Stream()
     sim = crk.Sim(phys[0], leaf_cap=128, precision=crk.CRK_MIXED, stream=stream)
     crk.crk_load_boxes(sim.handle, [b.n for b in boxes], phys, cat["pos"], cat["vel"], cat["mass"],
                        cat["u"], cat["h"], cat["species"])
     sim.n = N
-    best, tune_ms = crk.crk_autotune(sim.handle, (32, 64, 128))
-    crk.crk_step_boxes(sim.handle, dts, args.warmup)
-    crk.crk_set_timing(sim.handle, True)
+    best, form, grid = crk.crk_autotune_ex(sim.handle, (32, 64, 128))
+    crk.crk_step_boxes(sim.handle, dts, warmup)
+    crk.crk_set_timing(sim.handle, False)
     torch.cuda.synchronize()
-    with ClockSampler(0) as clocks:
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        crk.crk_step_boxes(sim.handle, dts, args.steps)
-        e1.record(stream)
-        torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    crk.crk_step_boxes(sim.handle, dts, steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    tg = crk.crk_get_timings(sim.handle)
+    crk.crk_set_timing(sim.handle, True)        # per-phase times from host-sized steps
+    crk.crk_step_boxes(sim.handle, dts, 2)
     tim = crk.crk_get_timings(sim.handle)
     calls = max(tim["calls"], 1)
     sim.close()
@@ -578,19 +576,40 @@ def run_batched(args):
         t64 += f0.elapsed_time(f1) / 1e3
         p64 += b.n
         s.close()
-    line = {"metric": METRIC, "value": N / (ms / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "batched: 64 Gaussian-field boxes 2 n^3, n in {16,24,32,48,64} "
-                                   "(seed 2), one handle, FP32-mixed, KDK dt=1e-3",
-                       "particles": N, "boxes": len(boxes), "leaf_cap": best},
-            "autotune_ms": {str(k): round(v, 3) for k, v in tune_ms.items()},
+    names = {crk.CRK_GRAVITY_GATHER: "gather", crk.CRK_GRAVITY_PAIRS_ONCE: "pairs_once"}
+    return {"workload": "batched: 64 Gaussian-field boxes 2 n^3, n in {16,24,32,48,64} (seed 2), one handle, "
+                        "FP32-mixed, KDK dt=1e-3",
+            "particles": N, "boxes": len(boxes), "value": N / (ms / 1e3), "unit": UNIT,
+            "ms_per_step": round(ms, 3), "steps": steps,
+            "graph": {"steps": int(tg["steps"]), "graph_steps": int(tg["graph_steps"]),
+                      "host_syncs": int(tg["host_syncs"]), "overflows": int(tg["graph_overflows"])},
+            "autotune": {"leaf_cap": best, "gravity_form": names[form],
+                         "force_evaluation_ms": {f"{c}/{names[f]}": round(v, 3) for (c, f), v in grid.items()}},
             "breakdown_ms": {k: round(tim[k] / calls, 4) for k in
-                             ("tree_ms", "pairs_ms", "density_ms", "moments_ms", "hydro_ms",
-                              "gravity_ms", "kdk_ms")},
-            "gpu_launches_per_step": int(tim["launches"]) // max(args.steps, 1),
-            "fp64_one_box_per_launch": {"value": p64 / t64, "unit": UNIT, "boxes": 8, "steps": 1},
-            "clocks": clocks.summary()}
+                             ("tree_ms", "pairs_ms", "density_ms", "moments_ms", "hydro_ms", "gravity_ms",
+                              "kdk_ms")},
+            "gpu_launches_per_host_sized_step": int(tim["launches"]) // max(int(tim["calls"]), 1),
+            "fp64_one_box_per_launch": {"value": p64 / t64, "unit": UNIT, "boxes": 8, "steps": 1}}
+
+
+def run_batched(args):
+    """The batched workload as its own line (see batched_leg)."""
+    import torch
+
+    from paper_2510_03557_gb300 import crk
+    from paper_2510_03557_gb300 import workloads as wl
+
+    torch.cuda.set_device(0)
+    crk.lib()
+    stream = torch.cuda.Stream()
+    with ClockSampler(0) as clocks:
+        b = batched_leg(crk, wl, args.steps, args.warmup, stream)
+    line = {"metric": METRIC, "value": b["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": b["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "dtype": "f32", "data": "synthetic",
+            "config": {"workload": b["workload"], "particles": b["particles"], "boxes": b["boxes"],
+                       "leaf_cap": b["autotune"]["leaf_cap"]},
+            "batched": b, "clocks": clocks.summary()}
     print(json.dumps(line))
 
 
@@ -763,6 +782,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-gaussian", action="store_true", help="skip the 2 x 128^3 secondary field")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-box batched field")
     ap.add_argument("--no-extras", action="store_true", help="skip the FOF and long-range mesh legs")
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests of the serving stream to run (0: skip)")
@@ -986,6 +1006,11 @@ def main():
         gaussian = run_gaussian(crk, wl, args, stream, max(2, min(args.steps, 10)))
         leg("gaussian")
 
+    batched = None
+    if not args.no_batched:
+        batched = batched_leg(crk, wl, max(3, min(args.steps, 10)), 2, stream)
+        leg("batched")
+
     serving = None
     if args.serve_requests > 0:
         serving = serve_bench(crk, wl, args)
@@ -1038,6 +1063,7 @@ def main():
             "oracle_sample_parity": sample_parity,
             "fof": fof,
             "gaussian_2x128": gaussian,
+            "batched_64_boxes": batched,
             "serving": serving,
             "e2e": e2e,
             "gpu_launches": launches,
