@@ -56,6 +56,28 @@ TRAFFIC_SOURCE_SHA256 = "1b3a759651a2b9acfc9e824a4c344e2fe445540e9fec0bdefb680b7
 TRAFFIC_BYTES_PER_PARTICLE = {"gravity_pairs_once": 72.7}
 
 
+# the crk_create flag that switches each pass to its pairs-once form (0: none)
+_ONCE_FLAG = {"tree": 0, "pairs": 0, "density": 0, "moments": 0, "hydro": 8, "gravity": 2, "kdk": 0}
+
+
+def _form_flags(crk, form: int) -> int:
+    """crk_create flags of an autotuner decomposition (a bit set)."""
+    return ((crk.CRK_FLAG_GRAVITY_PAIRS_ONCE if form & crk.CRK_GRAVITY_PAIRS_ONCE else 0) |
+            (crk.CRK_FLAG_HYDRO_PAIRS_ONCE if form & crk.CRK_HYDRO_PAIRS_ONCE else 0))
+
+
+def _form_names(crk, form: int) -> dict:
+    return {"gravity_form": "pairs_once" if form & crk.CRK_GRAVITY_PAIRS_ONCE else "gather",
+            "hydro_form": "pairs_once" if form & crk.CRK_HYDRO_PAIRS_ONCE else "gather"}
+
+
+def _tune_summary(crk, cap: int, form: int, grid: dict, digits: int) -> dict:
+    """The autotuner's choice and its grid, keys 'capacity/gravity form/hydro form'."""
+    short = lambda f: "/".join(v for v in _form_names(crk, f).values())
+    return dict({"leaf_cap": cap, "flags": _form_flags(crk, form)}, **_form_names(crk, form),
+                force_evaluation_ms={f"{c}/{short(f)}": round(v, digits) for (c, f), v in grid.items()})
+
+
 def _traffic(kernel: str, particles: int, leaf_cap: int):
     import hashlib
 
@@ -576,15 +598,13 @@ def batched_leg(crk, wl, steps: int, warmup: int, stream) -> dict:
         t64 += f0.elapsed_time(f1) / 1e3
         p64 += b.n
         s.close()
-    names = {crk.CRK_GRAVITY_GATHER: "gather", crk.CRK_GRAVITY_PAIRS_ONCE: "pairs_once"}
     return {"workload": "batched: 64 Gaussian-field boxes 2 n^3, n in {16,24,32,48,64} (seed 2), one handle, "
                         "FP32-mixed, KDK dt=1e-3",
             "particles": N, "boxes": len(boxes), "value": N / (ms / 1e3), "unit": UNIT,
             "ms_per_step": round(ms, 3), "steps": steps,
             "graph": {"steps": int(tg["steps"]), "graph_steps": int(tg["graph_steps"]),
                       "host_syncs": int(tg["host_syncs"]), "overflows": int(tg["graph_overflows"])},
-            "autotune": {"leaf_cap": best, "gravity_form": names[form],
-                         "force_evaluation_ms": {f"{c}/{names[f]}": round(v, 3) for (c, f), v in grid.items()}},
+            "autotune": _tune_summary(crk, best, form, grid, 3),
             "breakdown_ms": {k: round(tim[k] / calls, 4) for k in
                              ("tree_ms", "pairs_ms", "density_ms", "moments_ms", "hydro_ms", "gravity_ms",
                               "kdk_ms")},
@@ -620,7 +640,7 @@ def headline_config(args, world: int) -> dict:
     return {"workload": f"clustered 2x{args.n}^3 (half uniform, half in {getattr(args, 'nsphere', 512)} Plummer "
                         f"spheres of scale 0.002, kNN h), FP32-mixed, KDK steps at the box's Courant dt",
             "particles": n,
-            "leaf_cap": "autotuned over (64, 128) with the gravity form" if args.autotune else args.leaf_cap,
+            "leaf_cap": "autotuned over (64, 128) with the pair decompositions" if args.autotune else args.leaf_cap,
             "rebuild_every": args.rebuild_every,
             "parallelism": f"replicas{world}",
             "l2": f"inputs larger than L2 (~{n * 600 / 1e9:.1f} GB resident state)"}
@@ -765,6 +785,8 @@ def main():
                          "n = 256 with 512; the small case of the profiles)")
     ap.add_argument("--pairs-once", action="store_true",
                     help="with --no-autotune: gravity with each pair evaluated once")
+    ap.add_argument("--hydro-once", action="store_true",
+                    help="with --no-autotune: hydro with each union pair evaluated once")
     ap.add_argument("--gauss-n", type=int, default=128, help="Gaussian-field box: 2 n^3 particles")
     ap.add_argument("--leaf-cap", type=int, default=128)
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
@@ -786,7 +808,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the FOF and long-range mesh legs")
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests of the serving stream to run (0: skip)")
-    ap.add_argument("--serve-seconds", type=float, default=240.0,
+    ap.add_argument("--serve-seconds", type=float, default=700.0,
                     help="stop submitting serving requests after this many seconds")
     ap.add_argument("--serve-fp64", type=int, default=4, help="requests solved one by one in plain FP64")
     ap.add_argument("--serve-leaf-cap", type=int, default=64)
@@ -860,18 +882,19 @@ def main():
     sms = torch.cuda.get_device_properties(local).multi_processor_count
 
     # ---------------- mixed form, device-resident (the headline value)
+    head_flags = 0 if args.autotune else ((crk.CRK_FLAG_GRAVITY_PAIRS_ONCE if args.pairs_once else 0) |
+                                          (crk.CRK_FLAG_HYDRO_PAIRS_ONCE if args.hydro_once else 0))
     sim = crk.Sim(phys, leaf_cap=args.leaf_cap, precision=crk.CRK_MIXED, stream=stream,
-                  rebuild_every=args.rebuild_every,
-                  flags=crk.CRK_FLAG_GRAVITY_PAIRS_ONCE if (args.pairs_once and not args.autotune) else 0)
+                  rebuild_every=args.rebuild_every, flags=head_flags)
     sim.load(box)
     tune = None
     cap = args.leaf_cap
     if args.autotune:
-        # the library's autotuner: leaf capacity x gravity pair decomposition
+        # the library's autotuner: leaf capacity x the gravity and hydro pair
+        # decompositions
         cap, form, grid = crk.crk_autotune_ex(sim.handle, (64, 128))
-        names = {crk.CRK_GRAVITY_GATHER: "gather", crk.CRK_GRAVITY_PAIRS_ONCE: "pairs_once"}
-        tune = {"leaf_cap": cap, "gravity_form": names[form],
-                "force_evaluation_ms": {f"{c}/{names[f]}": round(v, 2) for (c, f), v in grid.items()}}
+        tune = _tune_summary(crk, cap, form, grid, 2)
+        head_flags = tune["flags"]
     counts = sim.forces(counts=True)      # untimed: the true pair counts for the roofline
     tim0 = crk.crk_get_timings(sim.handle)
     pairs = algorithmic_pairs(counts, gas, tim0["list_entries"])
@@ -974,7 +997,7 @@ def main():
     e2e = None
     if not args.no_e2e:
         se = crk.Sim(phys, leaf_cap=cap, precision=crk.CRK_MIXED, stream=stream,
-                     flags=crk.CRK_FLAG_GRAVITY_PAIRS_ONCE if tune and tune["gravity_form"] == "pairs_once" else 0)
+                     flags=head_flags)
         se.load(box)
         se.step(dt, 1)
         pin = lambda shape: torch.empty(shape, dtype=torch.float64).pin_memory().numpy()
@@ -1033,9 +1056,8 @@ def main():
             "config": headline_config(args, world),
             "roofline": {"bound": "alu", "kernel": dom, "achieved": round(achieved, 3),
                          "peak": round(peak, 3), "unit": "TFLOP/s", "frac": round(achieved / peak, 4),
-                         "traffic": _traffic(dom + ("_pairs_once" if dom == "gravity" and tune and
-                                                         tune["gravity_form"] == "pairs_once" else "_gather"
-                                                         if dom == "gravity" else ""), N, cap),
+                         "traffic": _traffic(dom + ("_pairs_once" if head_flags & _ONCE_FLAG[dom]
+                                                    else "_gather"), N, cap),
                          "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on "
                                            "the clustered generator at 2x64^3 with 8 dense cores, scaled by "
                                            "particles (null when the kernel source or leaf capacity differs from "

@@ -70,12 +70,19 @@ extern "C" {
                                           service always use the gather form. */
 
 #define CRK_FLAG_NO_GRAPH 4            /* run every step host-sized (see crk_step): no CUDA graph */
+#define CRK_FLAG_HYDRO_PAIRS_ONCE 8    /* mixed form: the CRKSPH hydro rates with each union pair
+                                          evaluated once, by its lower-indexed particle, and the
+                                          partner's side added with an atomic (F_ji = -F_ij and
+                                          the same energy term); results agree with the default
+                                          form to rounding.  Not in the FP64 form, time-step
+                                          bin substeps or the service. */
 
-/* Gravity pair decompositions (crk_autotune_ex) */
-#define CRK_GRAVITY_GATHER 0       /* each target sums its own pairs (32 threads per visit of a
-                                      target group to a neighbour leaf, one per target) */
-#define CRK_GRAVITY_PAIRS_ONCE 1   /* each pair once (32 threads per visit, one pair per thread per
-                                      step, both sides updated) */
+/* Pair decompositions of the mixed form (crk_autotune_ex): bit sets */
+#define CRK_GRAVITY_GATHER 0       /* every pass gathers: each target sums its own pairs (32 threads
+                                      per visit of a target group to a neighbour leaf, one per target) */
+#define CRK_GRAVITY_PAIRS_ONCE 1   /* gravity: each pair once (32 threads per visit, one pair per thread
+                                      per step, both sides updated) */
+#define CRK_HYDRO_PAIRS_ONCE 2     /* hydro: each union pair once (the lower-indexed side) */
 
 #define CRK_DM 0
 #define CRK_GAS 1
@@ -335,11 +342,12 @@ int crk_get_bins(crk_sim *sim, uint8_t *bins, int mem);
 int crk_autotune(crk_sim *sim, const int *caps, int ncaps, int *best_cap, double *ms_out);
 
 /* The autotuner over two axes: leaf capacity (caps, as crk_autotune) and
- * the gravity pair decomposition of the mixed form (forms: CRK_GRAVITY_GATHER
- * or CRK_GRAVITY_PAIRS_ONCE; the FP64 form and the service run the gather
- * form whatever is chosen).  Times one force evaluation at every pair of
- * candidates (after a warm-up one), keeps the fastest for the handle's later
- * calls (its leaf capacity and its CRK_FLAG_GRAVITY_PAIRS_ONCE bit) and
+ * the pair decomposition of the mixed form's gravity and hydro passes (forms:
+ * bit sets of CRK_GRAVITY_PAIRS_ONCE and CRK_HYDRO_PAIRS_ONCE, 0 = gather
+ * everywhere; the FP64 form and the service gather whatever is chosen).
+ * Times one force evaluation at every pair of candidates (after a warm-up
+ * one), keeps the fastest for the handle's later calls (its leaf capacity
+ * and its CRK_FLAG_GRAVITY_PAIRS_ONCE / CRK_FLAG_HYDRO_PAIRS_ONCE bits) and
  * writes it to *best_cap / *best_form (optional); ms_out (optional, ncaps x
  * nforms entries) gets the time of caps[k] with forms[f] at ms_out[k * nforms
  * + f].  Synchronises the stream.  Errors: CRK_EINVAL (bad candidate, no

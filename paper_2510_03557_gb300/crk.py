@@ -32,8 +32,10 @@ CRK_MEM_HOST = 0
 CRK_MEM_DEVICE = 1
 CRK_FLAG_GRAVITY_PAIRS_ONCE = 2
 CRK_FLAG_NO_GRAPH = 4
+CRK_FLAG_HYDRO_PAIRS_ONCE = 8
 CRK_GRAVITY_GATHER = 0
 CRK_GRAVITY_PAIRS_ONCE = 1
+CRK_HYDRO_PAIRS_ONCE = 2
 CRK_DM = 0
 CRK_GAS = 1
 
@@ -388,9 +390,10 @@ def crk_autotune(sim, caps=(32, 64, 128)):
     return int(best.value), {c: float(m) for c, m in zip(caps, ms)}
 
 
-def crk_autotune_ex(sim, caps=(32, 64, 128), forms=(CRK_GRAVITY_GATHER, CRK_GRAVITY_PAIRS_ONCE)):
-    """Times one force evaluation per (leaf capacity, gravity form), keeps the
-    fastest; returns (best capacity, best form, {(capacity, form): ms})."""
+def crk_autotune_ex(sim, caps=(32, 64, 128), forms=(0, 1, 2, 3)):
+    """Times one force evaluation per (leaf capacity, pair decomposition: a bit
+    set of CRK_GRAVITY_PAIRS_ONCE and CRK_HYDRO_PAIRS_ONCE), keeps the fastest;
+    returns (best capacity, best form, {(capacity, form): ms})."""
     ca = (ctypes.c_int * len(caps))(*caps)
     fa = (ctypes.c_int * len(forms))(*forms)
     ms = (ctypes.c_double * (len(caps) * len(forms)))()

@@ -232,6 +232,7 @@ PassArgs pass_args(crk_sim *s)
     // the service's pool (fixed-order sums) and in a hierarchical substep
     // (rows only for active leaves, so a pair may be seen from one side only)
     a.grav_once = s->mixed && (s->prm.flags & CRK_FLAG_GRAVITY_PAIRS_ONCE) && !s->is_pool && s->bins_bmin < 0;
+    a.hydro_once = s->mixed && (s->prm.flags & CRK_FLAG_HYDRO_PAIRS_ONCE) && !s->is_pool && s->bins_bmin < 0;
     return a;
 }
 
@@ -791,7 +792,7 @@ extern "C" int crk_create(const crk_params *params, void *cuda_stream, crk_sim *
     if (params->kernel != CRK_WENDLAND_C4) return fail(CRK_EINVAL, "unsupported kernel");
     if (params->cm_level < 0 || params->cm_level > 10) return fail(CRK_EINVAL, "cm_level in [0, 10]");
     if (params->rebuild_every < 0) return fail(CRK_EINVAL, "rebuild_every must be >= 0");
-    if (params->flags & ~(CRK_FLAG_GRAVITY_PAIRS_ONCE | CRK_FLAG_NO_GRAPH))
+    if (params->flags & ~(CRK_FLAG_GRAVITY_PAIRS_ONCE | CRK_FLAG_NO_GRAPH | CRK_FLAG_HYDRO_PAIRS_ONCE))
         return fail(CRK_EINVAL, "unknown flags bits 0x%x", params->flags);
     if (params->graph_margin_pct < 0 || params->graph_margin_pct > 1000)
         return fail(CRK_EINVAL, "graph_margin_pct must be in [0, 1000]");
@@ -1243,9 +1244,11 @@ static int run_substep(crk_sim *s, int sub, int depth, double dt_long, double et
     a.nbr_hash = nullptr;
     a.grav_count = nullptr;
     a.grav_hash = nullptr;
-    // gravity rows exist only for the active leaves: a pair must be seen from
-    // its own target's side, so the gather form
+    // gravity rows exist only for the active leaves and hydro runs over the
+    // active groups only: a pair must be seen from its own target's side, so
+    // the gather forms
     a.grav_once = 0;
+    a.hydro_once = 0;
     a.bsub = sub;
     a.bdepth = depth;
     a.bd = d;
@@ -1508,9 +1511,9 @@ static int autotune_grid(crk_sim *s, const int *caps, int ncaps, const int *form
         if (caps[k] != 32 && caps[k] != 64 && caps[k] != 128)
             return fail(CRK_EINVAL, "leaf capacity candidates must be 32, 64 or 128 (got %d)", caps[k]);
     for (int f = 0; f < nforms; ++f)
-        if (forms[f] != CRK_GRAVITY_GATHER && forms[f] != CRK_GRAVITY_PAIRS_ONCE)
-            return fail(CRK_EINVAL, "gravity form candidates must be CRK_GRAVITY_GATHER or "
-                                    "CRK_GRAVITY_PAIRS_ONCE (got %d)", forms[f]);
+        if (forms[f] < 0 || forms[f] > (CRK_GRAVITY_PAIRS_ONCE | CRK_HYDRO_PAIRS_ONCE))
+            return fail(CRK_EINVAL, "pair-decomposition candidates are bit sets of CRK_GRAVITY_PAIRS_ONCE "
+                                    "and CRK_HYDRO_PAIRS_ONCE (got %d)", forms[f]);
     CK(cudaSetDevice(s->device));
     if (s->n == 0) return fail(CRK_EINVAL, "no particles loaded");
     cudaEvent_t e0, e1;
@@ -1520,7 +1523,12 @@ static int autotune_grid(crk_sim *s, const int *caps, int ncaps, const int *form
         cudaEventDestroy(e0);
         return fail(CRK_ECUDA, "event creation failed: %s", cudaGetErrorString(ce));
     }
-    const int flags0 = s->prm.flags & ~CRK_FLAG_GRAVITY_PAIRS_ONCE;
+    const int once_bits = CRK_FLAG_GRAVITY_PAIRS_ONCE | CRK_FLAG_HYDRO_PAIRS_ONCE;
+    const int flags0 = s->prm.flags & ~once_bits;
+    auto flags_of = [&](int form) {
+        return flags0 | ((form & CRK_GRAVITY_PAIRS_ONCE) ? CRK_FLAG_GRAVITY_PAIRS_ONCE : 0) |
+               ((form & CRK_HYDRO_PAIRS_ONCE) ? CRK_FLAG_HYDRO_PAIRS_ONCE : 0);
+    };
     int best = -1;
     double best_ms = 0.0;
     int rc = CRK_OK;
@@ -1528,7 +1536,7 @@ static int autotune_grid(crk_sim *s, const int *caps, int ncaps, const int *form
         s->cap = caps[k];
         s->tree_valid = false;  // leaves of another capacity
         for (int f = 0; f < nforms && rc == CRK_OK; ++f) {
-            s->prm.flags = flags0 | (forms[f] == CRK_GRAVITY_PAIRS_ONCE ? CRK_FLAG_GRAVITY_PAIRS_ONCE : 0);
+            s->prm.flags = flags_of(forms[f]);
             rc = run_step(s, nullptr, false);  // warm-up: buffers grow to this layout
             if (rc != CRK_OK) break;
             cudaEventRecord(e0, s->st);
@@ -1552,7 +1560,7 @@ static int autotune_grid(crk_sim *s, const int *caps, int ncaps, const int *form
     if (rc != CRK_OK) return rc;
     const int bc = caps[best / nforms], bf = forms[best % nforms];
     s->cap = bc;
-    s->prm.flags = flags0 | (bf == CRK_GRAVITY_PAIRS_ONCE ? CRK_FLAG_GRAVITY_PAIRS_ONCE : 0);
+    s->prm.flags = flags_of(bf);
     s->tree_valid = false;
     if (best_cap) *best_cap = bc;
     if (best_form) *best_form = bf;
@@ -1563,7 +1571,8 @@ static int autotune_grid(crk_sim *s, const int *caps, int ncaps, const int *form
 extern "C" int crk_autotune(crk_sim *s, const int *caps, int ncaps, int *best_cap, double *ms_out)
 {
     if (!s) return fail(CRK_EINVAL, "null handle");
-    const int form = (s->prm.flags & CRK_FLAG_GRAVITY_PAIRS_ONCE) ? CRK_GRAVITY_PAIRS_ONCE : CRK_GRAVITY_GATHER;
+    const int form = ((s->prm.flags & CRK_FLAG_GRAVITY_PAIRS_ONCE) ? CRK_GRAVITY_PAIRS_ONCE : 0) |
+                     ((s->prm.flags & CRK_FLAG_HYDRO_PAIRS_ONCE) ? CRK_HYDRO_PAIRS_ONCE : 0);
     return autotune_grid(s, caps, ncaps, &form, 1, best_cap, nullptr, ms_out);
 }
 

@@ -136,6 +136,9 @@ struct PassArgs {
     // gravity of the mixed form with each unordered pair evaluated once and
     // the sums added by atomics (1), or the deterministic gather (0)
     int grav_once;
+    // hydro rates of the mixed form with each union pair evaluated once and
+    // the partner's side added by atomics (1), or the gather (0)
+    int hydro_once;
     // pair-work census of a counted evaluation (null otherwise): [0] lane
     // slots of the hydro candidate tests (32 x staged candidates per visit),
     // [1] hydro list entries written, [2] lane slots of the gravity tests,

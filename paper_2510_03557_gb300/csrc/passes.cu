@@ -1305,7 +1305,9 @@ __global__ void __launch_bounds__(kBlock, moments_min_blocks<R>()) moments_k(Pas
     v3.x = (R)o[1]; v3.y = (R)o[2]; v3.z = (R)o[3]; v3.w = (R)o[4];
     v4.x = (R)o[5]; v4.y = (R)o[6]; v4.z = (R)o[7]; v4.w = (R)o[8];
     v5.x = (R)o[9]; v5.y = (R)o[10]; v5.z = (R)o[11]; v5.w = (R)o[12];
-    v6.x = (R)o[13]; v6.y = (R)o[14]; v6.z = (R)o[15]; v6.w = 0;
+    // record 6's free slot carries 1/m_i for the hydro pass's partner side
+    v6.x = (R)o[13]; v6.y = (R)o[14]; v6.z = (R)o[15];
+    v6.w = Real<R>::rcp(reinterpret_cast<const R4 *>(a.pm)[i].w);
     reinterpret_cast<R4 *>(a.hrec[3])[i] = v3;
     reinterpret_cast<R4 *>(a.hrec[4])[i] = v4;
     reinterpret_cast<R4 *>(a.hrec[5])[i] = v5;
@@ -1357,7 +1359,16 @@ __device__ __forceinline__ void corrected_grad(const HState<R> &s, const R x[3],
 //   m_i a_i = sum F_ij,  m_i du_i = -1/2 sum F_ij . v_ij
 // The pairs are the target's list entries; j's seven records are read
 // through L1/L2 (a group's neighbours are a few leaves).
-template <typename R, int JMAX>
+// ONCE (mixed form): each union pair is evaluated by its lower-indexed
+// particle only (the union predicate is symmetric, so the pair is in both
+// lists): entries with j < i are skipped without loading j's records, the
+// target's sums are added once at the end and the partner's side, -F_ij / m_j
+// and the same energy term, with one float4 atomic per pair; the outputs
+// start from zero.  Results agree with the gather form to rounding.  On
+// GB300 the atomics cost more than the halved evaluations save (the lanes of
+// a warp skip different entries, so the warp's loop keeps its length; lists
+// compacted to the j > i entries first were slower still).
+template <typename R, int JMAX, bool ONCE = false>
 __global__ void __launch_bounds__(kBlock) hydro_k(PassArgs a)
 {
     using R4 = Vec4<R>;
@@ -1395,8 +1406,10 @@ __global__ void __launch_bounds__(kBlock) hydro_k(PassArgs a)
     if (pipe.cnt > 0u) {
         jn = pipe.j1;
         fn = entry_frame(frow, pipe.e1);
+        if (!ONCE || jn > i) {
 #pragma unroll
-        for (int q = 0; q < 7; ++q) rn[q] = reinterpret_cast<const R4 *>(a.hrec[q])[jn];
+            for (int q = 0; q < 7; ++q) rn[q] = reinterpret_cast<const R4 *>(a.hrec[q])[jn];
+        }
         pipe.step(a, srow, 0u);
     }
     for (uint32_t k = 0; k < pipe.cnt; ++k) {
@@ -1405,14 +1418,17 @@ __global__ void __launch_bounds__(kBlock) hydro_k(PassArgs a)
         HState<R> sj;
         unpack_hstate(rn, sj);
         const R4 rj0 = rn[0];
+        const R imj = rn[6].w;
         if (k + 1u < pipe.cnt) {
             jn = pipe.j1;
             fn = entry_frame(frow, pipe.e1);
+            if (!ONCE || jn > i) {
 #pragma unroll
-            for (int q = 0; q < 7; ++q) rn[q] = reinterpret_cast<const R4 *>(a.hrec[q])[jn];
+                for (int q = 0; q < 7; ++q) rn[q] = reinterpret_cast<const R4 *>(a.hrec[q])[jn];
+            }
             pipe.step(a, srow, k + 1u);
         }
-        if (j == i) continue;
+        if (ONCE ? j <= i : j == i) continue;
         R dx, dy, dz;
         const R r2 = list_sep2(rj0, ri0, fr, L, hL, dx, dy, dz);
         const R x[3] = {-dx, -dy, -dz};  // x_ij = x_i - x_j
@@ -1442,7 +1458,14 @@ __global__ void __launch_bounds__(kBlock) hydro_k(PassArgs a)
         ax += Fx;
         ay += Fy;
         az += Fz;
-        du += Fx * vxij + Fy * vyij + Fz * vzij;
+        const R e = Fx * vxij + Fy * vyij + Fz * vzij;
+        du += e;
+        if (ONCE) {
+            // the partner's side: m_j a_j -= F_ij; m_j du_j gets the same -1/2 F_ij . v_ij
+            atomicAdd(reinterpret_cast<float4 *>(a.acc_h) + j,
+                      make_float4((float)(-Fx * imj), (float)(-Fy * imj), (float)(-Fz * imj),
+                                  (float)((R)(-0.5) * e * imj)));
+        }
     }
     if (!G.act) return;
     const R mi = reinterpret_cast<const R4 *>(a.pm)[i].w;
@@ -1452,7 +1475,9 @@ __global__ void __launch_bounds__(kBlock) hydro_k(PassArgs a)
     o.y = ay * imi;
     o.z = az * imi;
     o.w = (R)(-0.5) * du * imi;
-    reinterpret_cast<R4 *>(a.acc_h)[i] = o;
+    if (ONCE) atomicAdd(reinterpret_cast<float4 *>(a.acc_h) + i, make_float4((float)o.x, (float)o.y, (float)o.z,
+                                                                           (float)o.w));
+    else reinterpret_cast<R4 *>(a.acc_h)[i] = o;
     });
 }
 
@@ -1978,7 +2003,13 @@ void moments_dispatch(const PassArgs &a, cudaStream_t st)
 template <typename R, int JMAX>
 void hydro_dispatch(const PassArgs &a, cudaStream_t st)
 {
-    launch_warp_kernel(hydro_k<R, JMAX>, a.n_ggas, 0, a, st);
+    if (Real<R>::mixed && a.hydro_once) {
+        // every contribution is added: the rates start from zero
+        cudaMemsetAsync(a.acc_h, 0, (size_t)a.n * sizeof(Vec4<R>), st);
+        launch_warp_kernel(hydro_k<R, JMAX, true>, a.n_ggas, 0, a, st);
+    } else {
+        launch_warp_kernel(hydro_k<R, JMAX, false>, a.n_ggas, 0, a, st);
+    }
 }
 
 }  // namespace

@@ -111,7 +111,7 @@ def test_create_rejects_bad_mesh_sizes_before_touching_the_device(libcrk, pm_gri
                                               ("kernel", 1, "kernel"), ("cm_level", 11, "cm_level"),
                                               ("cm_level", -1, "cm_level"),
                                               ("rebuild_every", -1, "rebuild_every"),
-                                              ("flags", 1, "flags"), ("flags", 8, "flags"),
+                                              ("flags", 1, "flags"), ("flags", 16, "flags"),
                                               ("graph_margin_pct", -1, "graph_margin_pct")])
 def test_create_rejects_bad_params_before_touching_the_device(libcrk, field, value, word):
     """Every create-time parameter is checked before the first CUDA call."""

@@ -69,6 +69,20 @@ def test_replayed_steps_match_host_sized_steps_and_the_oracle(crk, precision):
     assert disp_err(g[0], e[0], box.pos) <= same and rel_l2(g[1], e[1]) <= same
 
 
+def test_replayed_steps_with_pairs_once_forms_match_the_oracle(crk):
+    """The mixed form with gravity and hydro pairs evaluated once (the rates
+    zeroed and accumulated by atomics inside the captured graph)."""
+    box = wl.gaussian_field_box(16, seed=74)
+    box.vel = box.vel * 20.0
+    flags = crk.CRK_FLAG_GRAVITY_PAIRS_ONCE | crk.CRK_FLAG_HYDRO_PAIRS_ONCE
+    g = _run(crk, box, 1, 7, flags=flags)
+    assert g[3]["graph_steps"] == 6 and g[3]["graph_overflows"] == 0
+    ref = oracle.kdk(box.pos, box.vel, box.mass, box.u, box.h, box.species,
+                     oracle.make_params(**box.params()), box.dt, 7)
+    assert disp_err(g[0], ref["pos"], box.pos) <= 2e-4
+    assert rel_l2(g[1], ref["vel"]) <= 2e-4 and rel_l2(g[2], ref["u"]) <= 2e-4
+
+
 def test_replayed_steps_of_batched_boxes_match_the_oracle(crk):
     import torch
 

@@ -257,6 +257,11 @@ def test_clustered_2x64_matches_oracle(crk, precision, nsphere):
                        flags=crk.CRK_FLAG_GRAVITY_PAIRS_ONCE)
         compare(once, ref, {}, 1, sample=sample, label=f"clustered 2x64^3 nsphere={nsphere}, pairs once")
         assert rel_l2(once["acc"], out["acc"]) <= TOL[1]
+        # and the hydro rates with each union pair evaluated once as well
+        both = run_gpu(crk, box_dict(box), crk.box_physics(box), 1, leaf_cap=128, counts=False,
+                       flags=crk.CRK_FLAG_GRAVITY_PAIRS_ONCE | crk.CRK_FLAG_HYDRO_PAIRS_ONCE)
+        compare(both, ref, {}, 1, sample=sample, label=f"clustered 2x64^3 nsphere={nsphere}, both once")
+        assert rel_l2(both["dudt"], out["dudt"]) <= TOL[1]
 
 
 @pytest.mark.parametrize("leaf_cap", [32, 64, 128])
@@ -280,6 +285,33 @@ def test_gravity_pairs_once_matches_the_gather_form(crk, leaf_cap):
     assert rel_l2(once["acc"], d1["acc"]) <= 1e-5
     ma = s["mass"][:, None] * once["acc"]
     assert np.abs(once["momentum_rate"]).max() / np.abs(ma).sum() < 1e-5
+
+
+@pytest.mark.parametrize("leaf_cap", [32, 64, 128])
+def test_hydro_pairs_once_matches_the_gather_form(crk, leaf_cap):
+    """Mixed form: the hydro rates with each union pair evaluated once by its
+    lower-indexed particle (the partner's side, -F_ij / m_j and the same
+    energy term, added by an atomic) against the gather form and the oracle
+    on the clustered inputs with periodic wraps.  The pairwise antisymmetry
+    keeps the total hydro momentum rate at roundoff and the energy rate of
+    the G = 0 box at the oracle's."""
+    s = _clustered(seed=93)
+    phys = dict(box=1.0, G=1.0, gamma=5.0 / 3.0, r_cut=0.12, r_split=0.12 / 4.5, eps_soft=1e-3)
+    op = oracle.make_params(**phys)
+    ref = oracle.forces(s["pos"], s["vel"], s["mass"], s["u"], s["h"], s["species"], op)
+    assert ref["rc"] == 0
+    gat = run_gpu(crk, s, crk.physics(**phys), 1, leaf_cap=leaf_cap, counts=True)
+    once = run_gpu(crk, s, crk.physics(**phys), 1, leaf_cap=leaf_cap, counts=True,
+                   flags=crk.CRK_FLAG_HYDRO_PAIRS_ONCE)
+    compare(once, ref, oracle_counts(s, op), 1, label=f"hydro pairs once cap={leaf_cap}")
+    assert rel_l2(once["dudt"], gat["dudt"]) <= 1e-5 and rel_l2(once["acc"], gat["acc"]) <= 1e-5
+    # G = 0: only hydro moves the particles, so the total momentum rate is the
+    # hydro pass's alone
+    phys0 = dict(phys, G=0.0)
+    h0 = run_gpu(crk, s, crk.physics(**phys0), 1, leaf_cap=leaf_cap, counts=False,
+                 flags=crk.CRK_FLAG_HYDRO_PAIRS_ONCE)
+    ma = s["mass"][:, None] * h0["acc"]
+    assert np.abs(ma.sum(0)).max() / np.abs(ma).sum() < 1e-5
 
 
 def _clustered_smooth_h(seed, n_gas=2500, n_dm=1500, h0=0.09):
@@ -509,8 +541,9 @@ def test_leaves_kept_between_rebuilds_match_the_oracle(crk, precision):
         assert np.array_equal(out[name + "_hash"], cref[name][1]), name
 
 
-def test_autotune_over_capacity_and_gravity_form(crk):
-    """The two-axis autotuner times every (capacity, gravity form) pair,
+def test_autotune_over_capacity_and_pair_decomposition(crk):
+    """The two-axis autotuner times every (capacity, decomposition) pair --
+    the decomposition a bit set of gravity pairs-once and hydro pairs-once --
     keeps the fastest, and the forces of the chosen configuration equal the
     oracle's."""
     box = wl.gaussian_field_box(16, seed=22)
@@ -519,12 +552,12 @@ def test_autotune_over_capacity_and_gravity_form(crk):
     with crk.Sim(crk.box_physics(box), leaf_cap=64, precision=1) as sim:
         sim.load(box)
         cap, form, grid = crk.crk_autotune_ex(sim.handle, (32, 128))
-        assert set(grid) == {(32, 0), (32, 1), (128, 0), (128, 1)} and all(v > 0 for v in grid.values())
-        assert grid[(cap, form)] == min(grid.values())
+        assert set(grid) == {(c, f) for c in (32, 128) for f in range(4)}
+        assert all(v > 0 for v in grid.values()) and grid[(cap, form)] == min(grid.values())
         out = sim.forces(counts=False)
         compare(out, ref, {}, 1, label=f"autotuned cap={cap} form={form}")
         with pytest.raises(crk.CrkError) as e:
-            crk.crk_autotune_ex(sim.handle, (64,), (2,))
+            crk.crk_autotune_ex(sim.handle, (64,), (4,))
         assert e.value.code == crk.CRK_EINVAL
 
 
