@@ -47,13 +47,13 @@ UNIT = "particles/s"
 FLOP_PER_PAIR = {"density": 22, "moments": 125, "hydro": 183, "gravity": 41}
 
 # DRAM bytes (read + write) per particle of one launch of the gravity pass,
-# from an ncu capture of gravity_k on the clustered generator at 2 x 64^3
+# from an ncu capture of gravity_sym_k (each pair once) on the clustered generator at 2 x 64^3
 # with 8 dense cores (32,768 particles per core, as in the 2 x 256^3 box),
 # leaf capacity 128, scaled to the launch by the particles it processes.  They
 # describe the kernels of the csrc/passes.cu with this SHA-256 only; for any
 # other source the bench reports no traffic.
-TRAFFIC_SOURCE_SHA256 = "1b3a759651a2b9acfc9e824a4c344e2fe445540e9fec0bdefb680b7f94c51a92"
-TRAFFIC_BYTES_PER_PARTICLE = {"gravity_pairs_once": 72.7}
+TRAFFIC_SOURCE_SHA256 = "197c514b13efc802764512a5b803b4e5807fe711ea77db9370bb5a06e2ad3bc6"
+TRAFFIC_BYTES_PER_PARTICLE = {"gravity_pairs_once": 80.3}
 
 
 # the crk_create flag that switches each pass to its pairs-once form (0: none)

@@ -39,6 +39,11 @@ namespace crk {
 namespace {
 
 constexpr int kWarps = 4;             // warps (target groups) per CTA
+// Resident CTAs per SM the mixed form's pass kernels are compiled for (a
+// register budget: 65,536 / (128 x blocks) per thread; 0 = no bound)
+constexpr int kMomentsMinBlocks = 5;
+constexpr int kHydroMinBlocks = 0;
+constexpr int kFillMinBlocks = 0;
 constexpr int kBlock = 32 * kWarps;
 
 constexpr double kPi = 3.14159265358979323846;
@@ -778,7 +783,7 @@ __device__ __forceinline__ void density_out(const PassArgs &a, uint32_t i, const
 // Writes every gas particle's hydro neighbour list (the same sets the count
 // pass counted, from the same staging and test).
 template <typename R, int JMAX, bool COUNT>
-__global__ void __launch_bounds__(kBlock) hlist_fill_k(PassArgs a)
+__global__ void __launch_bounds__(kBlock, Real<R>::mixed ? kFillMinBlocks : 0) hlist_fill_k(PassArgs a)
 {
     using R4 = Vec4<R>;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1220,7 +1225,7 @@ struct MomentAcc {
 // list and record loads (4.53 -> 3.78 ms at 2x128^3); the FP64 form keeps
 // its registers.
 template <typename R>
-constexpr int moments_min_blocks() { return Real<R>::mixed ? 5 : 1; }
+constexpr int moments_min_blocks() { return Real<R>::mixed ? kMomentsMinBlocks : 1; }
 
 template <typename R, int JMAX>
 __global__ void __launch_bounds__(kBlock, moments_min_blocks<R>()) moments_k(PassArgs a)
@@ -1369,7 +1374,7 @@ __device__ __forceinline__ void corrected_grad(const HState<R> &s, const R x[3],
 // a warp skip different entries, so the warp's loop keeps its length; lists
 // compacted to the j > i entries first were slower still).
 template <typename R, int JMAX, bool ONCE = false>
-__global__ void __launch_bounds__(kBlock) hydro_k(PassArgs a)
+__global__ void __launch_bounds__(kBlock, Real<R>::mixed ? kHydroMinBlocks : 0) hydro_k(PassArgs a)
 {
     using R4 = Vec4<R>;
     const uint32_t lane = threadIdx.x & 31u;
@@ -1670,17 +1675,24 @@ __global__ void __launch_bounds__(kBlock) gravity_k(PassArgs a)
 // pair force are those of gravity_k; the summation order of the atomics is
 // not fixed, so results agree with the gather form to rounding, not bit for
 // bit.  Staged w: G m_j.
-template <bool WRAP, bool SAME>
+//
+// Candidates of one visit (a leaf J staged alone: the target's own leaf, or
+// a pair that needs a per-pair wrap) are indexed by slot in J (tslot, sJ);
+// MERGED candidates, staged from consecutive visits into one stream already
+// in the target leaf's frame, by particle index (cidx), so that every chunk
+// but the group's last holds 32 candidates.
+template <bool WRAP, bool SAME, bool MERGED>
 __device__ __forceinline__ void gravity_sym_tile(const PassArgs &a, const Vec4<float> *tile, const uint8_t *tslot,
-                                                 uint32_t K, const Target<float> &q, float L, float hL, float rc2,
-                                                 float gb, float e2, float kv, float Gmi, bool act, uint32_t i,
-                                                 uint32_t sJ, uint32_t lane, float &ax, float &ay, float &az,
-                                                 float4 *__restrict__ acc)
+                                                 const uint32_t *cidx, uint32_t K, const Target<float> &q, float L,
+                                                 float hL, float rc2, float gb, float e2, float kv, float Gmi,
+                                                 bool act, uint32_t i, uint32_t sJ, uint32_t lane, float &ax,
+                                                 float &ay, float &az, float4 *__restrict__ acc)
 {
     const uint32_t src = (lane + 1u) & 31u;
     for (uint32_t c0 = 0; c0 < K; c0 += 32u) {
         const Vec4<float> *chunk = tile + c0;
         const uint8_t *cslot = tslot + c0;
+        const uint32_t *cix = cidx + c0;
         float bx = 0.f, by = 0.f, bz = 0.f;
         uint32_t jj = lane;
 #pragma unroll 4
@@ -1694,7 +1706,7 @@ __device__ __forceinline__ void gravity_sym_tile(const PassArgs &a, const Vec4<f
                 // rare: a pair at the cut, re-decided in FP64 (arguments read
                 // from the kernel's parameters, not held in registers)
                 const BoxDev &bxd = a.boxes[a.s.slot[i]];
-                in = exact_lt(a.s, i, sJ + cslot[jj], bxd.L, __dmul_rn(bxd.r_cut, bxd.r_cut));
+                in = exact_lt(a.s, i, MERGED ? cix[jj] : sJ + cslot[jj], bxd.L, __dmul_rn(bxd.r_cut, bxd.r_cut));
             }
             if (SAME) in = in && (sJ + cslot[jj] > i);  // one leaf: the lower index does the pair
             in = in && act;
@@ -1720,19 +1732,65 @@ __device__ __forceinline__ void gravity_sym_tile(const PassArgs &a, const Vec4<f
         }
         // after 32 shifts the partial of candidate c0 + lane is in lane
         if (c0 + lane < K && (bx != 0.f || by != 0.f || bz != 0.f))
-            atomicAdd(acc + (sJ + cslot[lane]), make_float4(bx, by, bz, 0.f));
+            atomicAdd(acc + (MERGED ? cix[lane] : sJ + cslot[lane]), make_float4(bx, by, bz, 0.f));
     }
 }
 
+// Shared memory of a warp of gravity_sym_k: the merged candidate stream
+// (up to 31 carried over plus one leaf's JMAX) with its particle indices, and
+// the slots of a visit staged alone.
 template <int JMAX>
-__global__ void __launch_bounds__(kBlock) gravity_sym_k(const __grid_constant__ PassArgs a)
+constexpr size_t sym_warp_bytes()
+{
+    return (JMAX + 32) * (sizeof(float4) + sizeof(uint32_t)) + JMAX;
+}
+
+// Appends to the merged stream at tile[n0, ...) the candidates of leaf J
+// that can reach the warp's target box, moved into the target leaf's frame
+// (record + pair frame, rounded once), w = G m_j, and their particle indices;
+// returns the new length.  Only for pairs that need no per-pair wrap.
+__device__ __forceinline__ uint32_t stage_append(float4 *tile, uint32_t *cidx, uint32_t n0,
+                                                 const Vec4<float> *__restrict__ src, uint32_t sJ, uint32_t cJ,
+                                                 uint32_t cm, const WarpBox &wb, const float4 &fr, float Rc,
+                                                 uint32_t lane, float Gc)
+{
+    uint32_t K = n0;
+    const uint32_t nch = (cJ + 31u) / 32u;
+    for (uint32_t c = 0; c < nch; ++c) {
+        if (!((cm >> c) & 1u)) continue;
+        const uint32_t k = 32u * c + lane;
+        bool keep = false;
+        float x = 0.f, y = 0.f, z = 0.f, wv = 0.f;
+        if (k < cJ) {
+            const Vec4<float> v = src[sJ + k];
+            x = v.x + fr.x;
+            y = v.y + fr.y;
+            z = v.z + fr.z;
+            wv = Gc * v.w;
+            keep = box_gap2(wb, x, y, z) < Rc * Rc;
+        }
+        const uint32_t bal = __ballot_sync(0xffffffffu, keep);
+        if (keep) {
+            const uint32_t pos = K + __popc(bal & ((1u << lane) - 1u));
+            tile[pos] = make_float4(x, y, z, wv);
+            cidx[pos] = sJ + k;
+        }
+        K += __popc(bal);
+    }
+    return K;
+}
+
+template <int JMAX>
+__global__ void __launch_bounds__(kBlock, 8) gravity_sym_k(const __grid_constant__ PassArgs a)
 {
     using R4 = Vec4<float>;
     extern __shared__ __align__(16) unsigned char smem[];
     const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
     for_each_item(a.n_gall, a.gall_dev, a.queue, Q_GSYM, [&](const uint32_t gi) {
-    R4 *tile = reinterpret_cast<R4 *>(smem + (size_t)w * tile_warp_bytes<float, JMAX>());
-    uint8_t *tslot = reinterpret_cast<uint8_t *>(tile + JMAX);
+    unsigned char *base = smem + (size_t)w * sym_warp_bytes<JMAX>();
+    R4 *tile = reinterpret_cast<R4 *>(base);
+    uint32_t *cidx = reinterpret_cast<uint32_t *>(tile + JMAX + 32);
+    uint8_t *tslot = reinterpret_cast<uint8_t *>(cidx + JMAX + 32);
     const Group G = load_group(a.lv, a.gall, gi, lane);
     const int I = G.I;
     const uint32_t i = G.i;
@@ -1753,24 +1811,94 @@ __global__ void __launch_bounds__(kBlock) gravity_sym_k(const __grid_constant__ 
     const WarpBox wb = warp_box(px, py, pz, G.act);
     const float Rc = (float)bx.r_cut * 1.0001f + 1e-6f * (float)Ld;
     float ax = 0.f, ay = 0.f, az = 0.f;
+    // the merged stream: the target in its own leaf's frame, the guard band
+    // of the largest pair frame staged into it so far
+    Target<float> qI;
+    qI.qx = ri.x;
+    qI.qy = ri.y;
+    qI.qz = ri.z;
+    qI.wrap = false;
+    qI.mag = 0.f;
+    float mag = 0.f;
+    uint32_t nm = 0;  // candidates waiting in the stream (< 32 between visits)
     // the row is ascending: start at the first J >= I
-    uint32_t p0 = a.grow[I], p1 = a.gend[I];
+    uint32_t p = a.grow[I];
+    const uint32_t p1 = a.gend[I];
     {
-        uint32_t lo = p0, hi = p1;
+        uint32_t lo = p, hi = p1;
         while (lo < hi) {
             const uint32_t mid = (lo + hi) >> 1;
             if (a.gcol[mid] < (uint32_t)I) lo = mid + 1;
             else hi = mid;
         }
-        p0 = lo;
+        p = lo;
     }
-    for (uint32_t p = p0; p < p1; ++p) {
-        const uint32_t J = a.gcol[p];
-        const float4 fr = a.gfr[p];
-        if (out_of_range(wb, fr, a.lv.ex[J], a.lv.ey[J], a.lv.ez[J], Rc)) continue;
-        const uint32_t sJ = a.lv.start[J], cJ = a.lv.count[J];
-        const uint32_t cm = chunks_in_range(a.lv, J, cJ, wb, fr, Rc);
-        if (cm == 0u) continue;
+    while (true) {
+        const bool end = p >= p1;
+        bool alone = false;
+        uint32_t J = 0, sJ = 0, cJ = 0, cm = 0;
+        float4 fr = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (!end) {
+            J = a.gcol[p];
+            fr = a.gfr[p];
+            ++p;
+            if (out_of_range(wb, fr, a.lv.ex[J], a.lv.ey[J], a.lv.ez[J], Rc)) continue;
+            sJ = a.lv.start[J];
+            cJ = a.lv.count[J];
+            cm = chunks_in_range(a.lv, J, cJ, wb, fr, Rc);
+            if (cm == 0u) continue;
+            alone = J == (uint32_t)I || fr.w < 0.f;
+            if (!alone) {
+                // into the merged stream
+                __syncwarp();
+                nm = stage_append(reinterpret_cast<float4 *>(tile), cidx, nm, pm, sJ, cJ, cm, wb, fr, Rc, lane,
+                                  Gc);
+                __syncwarp();
+                mag = fmaxf(mag, fr.w);
+                if (nm < 32u) continue;
+            }
+        }
+        // the stream's full chunks; all of it, padded with far sentinels,
+        // before a visit staged alone (the target's own leaf, or a pair that
+        // needs a per-pair wrap) and at the end of the row
+        const bool all = end || alone;
+        const uint32_t full = nm & ~31u;
+        if (all && nm > full) {
+            if (full + lane >= nm) {
+                R4 sv;
+                sv.x = sv.y = sv.z = Real<float>::far;
+                sv.w = 0.f;
+                tile[full + lane] = sv;
+                cidx[full + lane] = i;
+            }
+            __syncwarp();
+        }
+        const uint32_t upto = all ? nm : full;
+        if (upto > 0u)
+            gravity_sym_tile<false, false, true>(a, tile, tslot, cidx, upto, qI, L, hL, rc2, guard_band(rc, mag), e2,
+                                                 kv, Gmi, G.act, i, 0u, lane, ax, ay, az, acc);
+        if (all) {
+            nm = 0;
+        } else if (nm > full) {
+            // the partial chunk moves to the front
+            R4 t;
+            uint32_t ti = 0;
+            const bool mv = full + lane < nm;
+            if (mv) {
+                t = tile[full + lane];
+                ti = cidx[full + lane];
+            }
+            __syncwarp();
+            if (mv) {
+                tile[lane] = t;
+                cidx[lane] = ti;
+            }
+            nm -= full;
+        } else {
+            nm = 0;
+        }
+        if (end) break;
+        if (!alone) continue;
         __syncwarp();
         const uint32_t K = stage_cull<float, false, false>(tile, tslot, nullptr, pm, nullptr, sJ, cJ, cm, wb,
                                                            cand_frame<float>(a.lv, I, fr, Ld), Rc, lane, Gc);
@@ -1780,18 +1908,14 @@ __global__ void __launch_bounds__(kBlock) gravity_sym_k(const __grid_constant__ 
         const float gb = guard_band(rc, q.mag);
         if (J == (uint32_t)I) {
             if (q.wrap)
-                gravity_sym_tile<true, true>(a, tile, tslot, K, q, L, hL, rc2, gb, e2, kv, Gmi, G.act, i, sJ, lane,
-                                             ax, ay, az, acc);
+                gravity_sym_tile<true, true, false>(a, tile, tslot, cidx, K, q, L, hL, rc2, gb, e2, kv, Gmi, G.act,
+                                                    i, sJ, lane, ax, ay, az, acc);
             else
-                gravity_sym_tile<false, true>(a, tile, tslot, K, q, L, hL, rc2, gb, e2, kv, Gmi, G.act, i, sJ, lane,
-                                              ax, ay, az, acc);
+                gravity_sym_tile<false, true, false>(a, tile, tslot, cidx, K, q, L, hL, rc2, gb, e2, kv, Gmi, G.act,
+                                                     i, sJ, lane, ax, ay, az, acc);
         } else {
-            if (q.wrap)
-                gravity_sym_tile<true, false>(a, tile, tslot, K, q, L, hL, rc2, gb, e2, kv, Gmi, G.act, i, sJ, lane,
-                                              ax, ay, az, acc);
-            else
-                gravity_sym_tile<false, false>(a, tile, tslot, K, q, L, hL, rc2, gb, e2, kv, Gmi, G.act, i, sJ,
-                                               lane, ax, ay, az, acc);
+            gravity_sym_tile<true, false, false>(a, tile, tslot, cidx, K, q, L, hL, rc2, gb, e2, kv, Gmi, G.act, i,
+                                                 sJ, lane, ax, ay, az, acc);
         }
     }
     if (G.act) atomicAdd(acc + i, make_float4(ax, ay, az, 0.f));
@@ -2116,11 +2240,11 @@ void launch_gravity(const PassArgs &a, int mixed, int cap, bool count, cudaStrea
         // every contribution is added: the accelerations start from zero
         cudaMemsetAsync(a.acc_g, 0, (size_t)a.n * sizeof(float4), st);
         if (cap == 32)
-            launch_warp_kernel(gravity_sym_k<32>, a.n_gall, (size_t)kWarps * tile_warp_bytes<float, 32>(), a, st);
+            launch_warp_kernel(gravity_sym_k<32>, a.n_gall, (size_t)kWarps * sym_warp_bytes<32>(), a, st);
         else if (cap == 64)
-            launch_warp_kernel(gravity_sym_k<64>, a.n_gall, (size_t)kWarps * tile_warp_bytes<float, 64>(), a, st);
+            launch_warp_kernel(gravity_sym_k<64>, a.n_gall, (size_t)kWarps * sym_warp_bytes<64>(), a, st);
         else
-            launch_warp_kernel(gravity_sym_k<128>, a.n_gall, (size_t)kWarps * tile_warp_bytes<float, 128>(), a, st);
+            launch_warp_kernel(gravity_sym_k<128>, a.n_gall, (size_t)kWarps * sym_warp_bytes<128>(), a, st);
         note_launches(1);
         return;
     }
