@@ -218,6 +218,7 @@ def serve_bench(crk, wl, args):
     handle per request, one box per launch, the same 20 KDK steps) of a few of
     the requests give the FP64 rate."""
     import concurrent.futures as cf
+    import resource
 
     count = args.serve_requests
     reqs = wl.serving_requests(2000)[:count]
@@ -243,21 +244,45 @@ def serve_bench(crk, wl, args):
         capacity = ncal / t_cal                       # requests/s when saturated
         rate = 0.7 * capacity
         arrivals = wl.poisson_arrivals(count, rate, seed=5)
-        futs = [ex.submit(gen, r) for r in reqs]      # generated in order, ahead of arrival
+        # boxes generated in order, at most `ahead` requests before their
+        # arrival, and dropped once submitted (the stream does not fit in
+        # host memory at once)
+        ahead = 48
+        futs = {k: ex.submit(gen, reqs[k]) for k in range(min(ahead, count))}
         tickets, sizes, late = [], [], 0
+        res = {}          # latencies of finished requests, collected as they finish
+        outstanding = []
+
+        def collect(wait: bool):
+            keep = []
+            for k in outstanding:
+                r = crk.crk_poll(svc, tickets[k], sizes[k], -1 if wait else 0, state=False)
+                if r is None:
+                    keep.append(k)
+                else:
+                    res[k] = r
+            outstanding[:] = keep
+
         t0 = time.perf_counter()
-        for a, f in zip(arrivals, futs):
+        for k, a in enumerate(arrivals):
             if time.perf_counter() - t0 > args.serve_seconds:
                 break
             while time.perf_counter() - t0 < a:
                 time.sleep(min(1e-3, max(0.0, a - (time.perf_counter() - t0))))
-            b = f.result()
+            b = futs.pop(k).result()
+            if k + ahead < count:
+                futs[k + ahead] = ex.submit(gen, reqs[k + ahead])
             late += (time.perf_counter() - t0) > a + 0.05
             tickets.append(submit(b))
             sizes.append(b.n)
-        for f in futs[len(tickets):]:
+            outstanding.append(k)
+            del b
+            collect(False)
+        for f in futs.values():
             f.cancel()
-        res = [crk.crk_poll(svc, t, n, -1) for t, n in zip(tickets, sizes)]
+        futs.clear()
+        collect(True)
+        res = [res[k] for k in range(len(tickets))]
         wall = time.perf_counter() - t0
     finally:
         crk.crk_service_destroy(svc)
@@ -298,6 +323,7 @@ def serve_bench(crk, wl, args):
             "queue_p50_ms": round(float(np.percentile(que, 50)), 3),
             "value": psteps / wall, "unit": UNIT, "wall_s": round(wall, 2),
             "arrival_rate_per_s": round(rate, 3), "load": 0.7, "late_submissions": int(late),
+            "host_peak_rss_gb": round(resource.getrusage(resource.RUSAGE_SELF).ru_maxrss / 2**20, 1),
             "calibration": {"requests": ncal, "seconds": round(t_cal, 3)},
             "size_classes": "3 (below 65,536 particles; below 524,288; the rest)",
             "lane_priority": args.serve_priority,

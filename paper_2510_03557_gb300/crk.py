@@ -446,21 +446,23 @@ def crk_submit(svc, phys: Physics, pos, vel, mass, u, h, species, dt: float, nst
     return int(t.value)
 
 
-def crk_poll(svc, ticket: int, n: int, timeout_us: int = -1):
-    """Returns None while pending, else a dict with the final state and
-    latencies (raises CrkError if the job failed)."""
+def crk_poll(svc, ticket: int, n: int, timeout_us: int = -1, state: bool = True):
+    """Returns None while pending, else a dict with the final state (unless
+    state is False: latencies only, the state is not copied) and latencies
+    (raises CrkError if the job failed)."""
     r = JobResult()
-    pos = np.zeros((n, 3))
-    vel = np.zeros((n, 3))
-    u = np.zeros(n)
-    r.pos = pos.ctypes.data_as(ctypes.c_void_p)
-    r.vel = vel.ctypes.data_as(ctypes.c_void_p)
-    r.u = u.ctypes.data_as(ctypes.c_void_p)
+    out = {}
+    if state:
+        out = dict(pos=np.zeros((n, 3)), vel=np.zeros((n, 3)), u=np.zeros(n))
+        r.pos = out["pos"].ctypes.data_as(ctypes.c_void_p)
+        r.vel = out["vel"].ctypes.data_as(ctypes.c_void_p)
+        r.u = out["u"].ctypes.data_as(ctypes.c_void_p)
     rc = lib().crk_poll(svc, ctypes.c_uint64(ticket), ctypes.byref(r), ctypes.c_int64(timeout_us))
     if rc == CRK_EPENDING:
         return None
     _check(rc)
-    return dict(pos=pos, vel=vel, u=u, latency_ns=int(r.latency_ns), queue_ns=int(r.queue_ns))
+    out.update(latency_ns=int(r.latency_ns), queue_ns=int(r.queue_ns))
+    return out
 
 
 def crk_service_destroy(svc):
