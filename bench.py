@@ -52,8 +52,8 @@ FLOP_PER_PAIR = {"density": 22, "moments": 125, "hydro": 183, "gravity": 41}
 # leaf capacity 128, scaled to the launch by the particles it processes.  They
 # describe the kernels of the csrc/passes.cu with this SHA-256 only; for any
 # other source the bench reports no traffic.
-TRAFFIC_SOURCE_SHA256 = "197c514b13efc802764512a5b803b4e5807fe711ea77db9370bb5a06e2ad3bc6"
-TRAFFIC_BYTES_PER_PARTICLE = {"gravity_pairs_once": 80.3}
+TRAFFIC_SOURCE_SHA256 = "8d9a4f37bb7458543ab0255a32c48500d96a20eaf968ae61ceb478b9581bf620"
+TRAFFIC_BYTES_PER_PARTICLE = {"gravity_pairs_once": 79.5}
 
 
 # the crk_create flag that switches each pass to its pairs-once form (0: none)

@@ -1681,27 +1681,30 @@ __global__ void __launch_bounds__(kBlock) gravity_k(PassArgs a)
 // MERGED candidates, staged from consecutive visits into one stream already
 // in the target leaf's frame, by particle index (cidx), so that every chunk
 // but the group's last holds 32 candidates.
-template <bool WRAP, bool SAME, bool MERGED>
-__device__ __forceinline__ void gravity_sym_tile(const PassArgs &a, const Vec4<float> *tile, const uint8_t *tslot,
-                                                 const uint32_t *cidx, uint32_t K, const Target<float> &q, float L,
-                                                 float hL, float rc2, float gb, float e2, float kv, float Gmi,
-                                                 bool act, uint32_t i, uint32_t sJ, uint32_t lane, float &ax,
-                                                 float &ay, float &az, float4 *__restrict__ acc)
+// The 32 steps of one diagonal chunk.  NEAR (a merged chunk whose every
+// candidate lies within r_cut of the whole target box, with the guard band
+// to spare): every pair is in range, so the test, its FP64 re-decision and
+// the select drop out; a lane without a target adds nothing to the
+// candidates' partials through Gmi = 0.
+template <bool WRAP, bool SAME, bool MERGED, bool NEAR>
+__device__ __forceinline__ void gravity_sym_steps(const PassArgs &a, const Vec4<float> *chunk, const uint8_t *cslot,
+                                                  const uint32_t *cix, const Target<float> &q, float L, float hL,
+                                                  float rc2, float gb, float e2, float kv, float Gmi, bool act,
+                                                  uint32_t i, uint32_t sJ, uint32_t lane, float &ax, float &ay,
+                                                  float &az, float &bx, float &by, float &bz)
 {
     const uint32_t src = (lane + 1u) & 31u;
-    for (uint32_t c0 = 0; c0 < K; c0 += 32u) {
-        const Vec4<float> *chunk = tile + c0;
-        const uint8_t *cslot = tslot + c0;
-        const uint32_t *cix = cidx + c0;
-        float bx = 0.f, by = 0.f, bz = 0.f;
-        uint32_t jj = lane;
+    const float Gmj = NEAR ? (act ? Gmi : 0.f) : Gmi;
+    uint32_t jj = lane;
 #pragma unroll 4
-        for (int k = 0; k < 32; ++k) {
-            const Vec4<float> rj = chunk[jj];
-            float dx, dy, dz;
-            const float r2 = sep2<float, WRAP>(rj, q, L, hL, dx, dy, dz);
+    for (int k = 0; k < 32; ++k) {
+        const Vec4<float> rj = chunk[jj];
+        float dx, dy, dz;
+        const float r2 = sep2<float, WRAP>(rj, q, L, hL, dx, dy, dz);
+        bool in = true;
+        if (!NEAR) {
             const float dr = r2 - rc2;
-            bool in = dr < 0.f;
+            in = dr < 0.f;
             if (fabsf(dr) < gb) {
                 // rare: a pair at the cut, re-decided in FP64 (arguments read
                 // from the kernel's parameters, not held in registers)
@@ -1710,26 +1713,48 @@ __device__ __forceinline__ void gravity_sym_tile(const PassArgs &a, const Vec4<f
             }
             if (SAME) in = in && (sJ + cslot[jj] > i);  // one leaf: the lower index does the pair
             in = in && act;
-            const float v = Real<float>::sqrt_(r2) * kv;
-            const float tt = Real<float>::rcp(fmaf(kAsPv, v, 1.0f));
-            const float poly = tt * (kAs1 + tt * (kAs2 + tt * (kAs3 + tt * (kAs4 + tt * kAs5))));
-            const float sw = Real<float>::exp2(-v * v) * fmaf(kTwoOverSqrtPiV, v, poly);  // S(r)
-            const float is = Real<float>::rsqrt(r2 + e2);
-            float f = sw * is * is * is;  // S(r) (r^2 + eps^2)^{-3/2}
-            f = in ? f : 0.f;
-            const float fi = f * rj.w, fj = f * Gmi;
-            ax = fmaf(fi, dx, ax);
-            ay = fmaf(fi, dy, ay);
-            az = fmaf(fi, dz, az);
-            bx = fmaf(-fj, dx, bx);
-            by = fmaf(-fj, dy, by);
-            bz = fmaf(-fj, dz, bz);
-            // hand the candidate's partial to the lane that meets it next
-            bx = __shfl_sync(0xffffffffu, bx, src);
-            by = __shfl_sync(0xffffffffu, by, src);
-            bz = __shfl_sync(0xffffffffu, bz, src);
-            jj = (jj + 1u) & 31u;
         }
+        const float v = Real<float>::sqrt_(r2) * kv;
+        const float tt = Real<float>::rcp(fmaf(kAsPv, v, 1.0f));
+        const float poly = tt * (kAs1 + tt * (kAs2 + tt * (kAs3 + tt * (kAs4 + tt * kAs5))));
+        const float sw = Real<float>::exp2(-v * v) * fmaf(kTwoOverSqrtPiV, v, poly);  // S(r)
+        const float is = Real<float>::rsqrt(r2 + e2);
+        float f = sw * is * is * is;  // S(r) (r^2 + eps^2)^{-3/2}
+        if (!NEAR) f = in ? f : 0.f;
+        const float fi = f * rj.w, fj = f * Gmj;
+        ax = fmaf(fi, dx, ax);
+        ay = fmaf(fi, dy, ay);
+        az = fmaf(fi, dz, az);
+        bx = fmaf(-fj, dx, bx);
+        by = fmaf(-fj, dy, by);
+        bz = fmaf(-fj, dz, bz);
+        // hand the candidate's partial to the lane that meets it next
+        bx = __shfl_sync(0xffffffffu, bx, src);
+        by = __shfl_sync(0xffffffffu, by, src);
+        bz = __shfl_sync(0xffffffffu, bz, src);
+        jj = (jj + 1u) & 31u;
+    }
+}
+
+template <bool WRAP, bool SAME, bool MERGED>
+__device__ __forceinline__ void gravity_sym_tile(const PassArgs &a, const Vec4<float> *tile, const uint8_t *tslot,
+                                                 const uint32_t *cidx, const uint8_t *cnear, uint32_t K,
+                                                 const Target<float> &q, float L, float hL, float rc2, float gb,
+                                                 float e2, float kv, float Gmi, bool act, uint32_t i, uint32_t sJ,
+                                                 uint32_t lane, float &ax, float &ay, float &az,
+                                                 float4 *__restrict__ acc)
+{
+    for (uint32_t c0 = 0; c0 < K; c0 += 32u) {
+        const Vec4<float> *chunk = tile + c0;
+        const uint8_t *cslot = tslot + c0;
+        const uint32_t *cix = cidx + c0;
+        float bx = 0.f, by = 0.f, bz = 0.f;
+        if (MERGED && __all_sync(0xffffffffu, cnear[c0 + lane] != 0))
+            gravity_sym_steps<false, false, true, true>(a, chunk, cslot, cix, q, L, hL, rc2, gb, e2, kv, Gmi, act, i,
+                                                        sJ, lane, ax, ay, az, bx, by, bz);
+        else
+            gravity_sym_steps<WRAP, SAME, MERGED, false>(a, chunk, cslot, cix, q, L, hL, rc2, gb, e2, kv, Gmi, act,
+                                                         i, sJ, lane, ax, ay, az, bx, by, bz);
         // after 32 shifts the partial of candidate c0 + lane is in lane
         if (c0 + lane < K && (bx != 0.f || by != 0.f || bz != 0.f))
             atomicAdd(acc + (MERGED ? cix[lane] : sJ + cslot[lane]), make_float4(bx, by, bz, 0.f));
@@ -1742,17 +1767,20 @@ __device__ __forceinline__ void gravity_sym_tile(const PassArgs &a, const Vec4<f
 template <int JMAX>
 constexpr size_t sym_warp_bytes()
 {
-    return (JMAX + 32) * (sizeof(float4) + sizeof(uint32_t)) + JMAX;
+    return (JMAX + 32) * (sizeof(float4) + sizeof(uint32_t) + 1) + JMAX;
 }
+static_assert(sym_warp_bytes<32>() % 16 == 0 && sym_warp_bytes<64>() % 16 == 0 && sym_warp_bytes<128>() % 16 == 0,
+              "each warp's tile starts 16-byte aligned");
 
 // Appends to the merged stream at tile[n0, ...) the candidates of leaf J
 // that can reach the warp's target box, moved into the target leaf's frame
-// (record + pair frame, rounded once), w = G m_j, and their particle indices;
+// (record + pair frame, rounded once), w = G m_j, their particle indices and
+// whether the farthest point of the target box lies below near2 from them;
 // returns the new length.  Only for pairs that need no per-pair wrap.
-__device__ __forceinline__ uint32_t stage_append(float4 *tile, uint32_t *cidx, uint32_t n0,
+__device__ __forceinline__ uint32_t stage_append(float4 *tile, uint32_t *cidx, uint8_t *cnear, uint32_t n0,
                                                  const Vec4<float> *__restrict__ src, uint32_t sJ, uint32_t cJ,
                                                  uint32_t cm, const WarpBox &wb, const float4 &fr, float Rc,
-                                                 uint32_t lane, float Gc)
+                                                 float near2, uint32_t lane, float Gc)
 {
     uint32_t K = n0;
     const uint32_t nch = (cJ + 31u) / 32u;
@@ -1774,6 +1802,8 @@ __device__ __forceinline__ uint32_t stage_append(float4 *tile, uint32_t *cidx, u
             const uint32_t pos = K + __popc(bal & ((1u << lane) - 1u));
             tile[pos] = make_float4(x, y, z, wv);
             cidx[pos] = sJ + k;
+            const float fx = fabsf(x - wb.cx) + wb.ex, fy = fabsf(y - wb.cy) + wb.ey, fz = fabsf(z - wb.cz) + wb.ez;
+            cnear[pos] = (fx * fx + fy * fy + fz * fz) < near2 ? 1u : 0u;
         }
         K += __popc(bal);
     }
@@ -1781,7 +1811,7 @@ __device__ __forceinline__ uint32_t stage_append(float4 *tile, uint32_t *cidx, u
 }
 
 template <int JMAX>
-__global__ void __launch_bounds__(kBlock, 8) gravity_sym_k(const __grid_constant__ PassArgs a)
+__global__ void __launch_bounds__(kBlock, 7) gravity_sym_k(const __grid_constant__ PassArgs a)
 {
     using R4 = Vec4<float>;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -1790,7 +1820,8 @@ __global__ void __launch_bounds__(kBlock, 8) gravity_sym_k(const __grid_constant
     unsigned char *base = smem + (size_t)w * sym_warp_bytes<JMAX>();
     R4 *tile = reinterpret_cast<R4 *>(base);
     uint32_t *cidx = reinterpret_cast<uint32_t *>(tile + JMAX + 32);
-    uint8_t *tslot = reinterpret_cast<uint8_t *>(cidx + JMAX + 32);
+    uint8_t *cnear = reinterpret_cast<uint8_t *>(cidx + JMAX + 32);
+    uint8_t *tslot = cnear + JMAX + 32;
     const Group G = load_group(a.lv, a.gall, gi, lane);
     const int I = G.I;
     const uint32_t i = G.i;
@@ -1851,10 +1882,13 @@ __global__ void __launch_bounds__(kBlock, 8) gravity_sym_k(const __grid_constant
             if (!alone) {
                 // into the merged stream
                 __syncwarp();
-                nm = stage_append(reinterpret_cast<float4 *>(tile), cidx, nm, pm, sJ, cJ, cm, wb, fr, Rc, lane,
-                                  Gc);
-                __syncwarp();
                 mag = fmaxf(mag, fr.w);
+                // all-in-range: the farthest target below r_cut by the guard
+                // band of this leaf's frame (the FP32 distances err by less)
+                const float near2 = rc2 - guard_band(rc, mag);
+                nm = stage_append(reinterpret_cast<float4 *>(tile), cidx, cnear, nm, pm, sJ, cJ, cm, wb, fr, Rc,
+                                  near2, lane, Gc);
+                __syncwarp();
                 if (nm < 32u) continue;
             }
         }
@@ -1870,12 +1904,13 @@ __global__ void __launch_bounds__(kBlock, 8) gravity_sym_k(const __grid_constant
                 sv.w = 0.f;
                 tile[full + lane] = sv;
                 cidx[full + lane] = i;
+                cnear[full + lane] = 0;
             }
             __syncwarp();
         }
         const uint32_t upto = all ? nm : full;
         if (upto > 0u)
-            gravity_sym_tile<false, false, true>(a, tile, tslot, cidx, upto, qI, L, hL, rc2, guard_band(rc, mag), e2,
+            gravity_sym_tile<false, false, true>(a, tile, tslot, cidx, cnear, upto, qI, L, hL, rc2, guard_band(rc, mag), e2,
                                                  kv, Gmi, G.act, i, 0u, lane, ax, ay, az, acc);
         if (all) {
             nm = 0;
@@ -1883,15 +1918,18 @@ __global__ void __launch_bounds__(kBlock, 8) gravity_sym_k(const __grid_constant
             // the partial chunk moves to the front
             R4 t;
             uint32_t ti = 0;
+            uint8_t tn = 0;
             const bool mv = full + lane < nm;
             if (mv) {
                 t = tile[full + lane];
                 ti = cidx[full + lane];
+                tn = cnear[full + lane];
             }
             __syncwarp();
             if (mv) {
                 tile[lane] = t;
                 cidx[lane] = ti;
+                cnear[lane] = tn;
             }
             nm -= full;
         } else {
@@ -1908,13 +1946,13 @@ __global__ void __launch_bounds__(kBlock, 8) gravity_sym_k(const __grid_constant
         const float gb = guard_band(rc, q.mag);
         if (J == (uint32_t)I) {
             if (q.wrap)
-                gravity_sym_tile<true, true, false>(a, tile, tslot, cidx, K, q, L, hL, rc2, gb, e2, kv, Gmi, G.act,
+                gravity_sym_tile<true, true, false>(a, tile, tslot, cidx, cnear, K, q, L, hL, rc2, gb, e2, kv, Gmi, G.act,
                                                     i, sJ, lane, ax, ay, az, acc);
             else
-                gravity_sym_tile<false, true, false>(a, tile, tslot, cidx, K, q, L, hL, rc2, gb, e2, kv, Gmi, G.act,
+                gravity_sym_tile<false, true, false>(a, tile, tslot, cidx, cnear, K, q, L, hL, rc2, gb, e2, kv, Gmi, G.act,
                                                      i, sJ, lane, ax, ay, az, acc);
         } else {
-            gravity_sym_tile<true, false, false>(a, tile, tslot, cidx, K, q, L, hL, rc2, gb, e2, kv, Gmi, G.act, i,
+            gravity_sym_tile<true, false, false>(a, tile, tslot, cidx, cnear, K, q, L, hL, rc2, gb, e2, kv, Gmi, G.act, i,
                                                  sJ, lane, ax, ay, az, acc);
         }
     }
