@@ -287,7 +287,7 @@ __device__ __forceinline__ void test_tile(const Vec4<R> *tile, const float *thrj
         uint32_t bits = 0;
         m[w] = 0;
         if (!((cm >> w) & 1u)) continue;
-#pragma unroll
+#pragma unroll 8
         for (int b = 0; b < 32; ++b) {
             const int j = 32 * w + b;
             R dx, dy, dz;
@@ -323,7 +323,7 @@ __device__ __forceinline__ void test_tile_union(const Vec4<R> *tile, const float
         mu[w] = 0;
         mg[w] = 0;
         if (!((cm >> w) & 1u)) continue;
-#pragma unroll
+#pragma unroll 8
         for (int b = 0; b < 32; ++b) {
             const int j = 32 * w + b;
             R dx, dy, dz;
@@ -643,11 +643,15 @@ struct ListRing {
         if (k >= base) rj[(k % kRingRows) * 32u + lane] = entry;
         else a.nl_j[e0 + (size_t)k * 32u] = entry;
     }
-    // writes rows [base, upto); a lane's own entries only (k: entries it has put)
-    __device__ __forceinline__ void flush(const PassArgs &a, uint32_t upto, uint32_t k, uint32_t lane)
+    // writes rows [base, upto) below cap (the group's rows) whole: a lane's
+    // own entries (k: entries it has put) and a filler word where it has
+    // none, so that every row leaves as one full 128-byte line (a partly
+    // written line costs the L2 a read of it from DRAM when it is evicted)
+    __device__ __forceinline__ void flush(const PassArgs &a, uint32_t upto, uint32_t k, uint32_t cap, uint32_t lane)
     {
-        for (uint32_t r = base; r < upto; ++r)
-            if (r < k) a.nl_j[e0 + (size_t)r * 32u] = rj[(r % kRingRows) * 32u + lane];
+        const uint32_t end = upto < cap ? upto : cap;
+        for (uint32_t r = base; r < end; ++r)
+            a.nl_j[e0 + (size_t)r * 32u] = r < k ? rj[(r % kRingRows) * 32u + lane] : 0u;
         base = upto;
     }
 };
@@ -812,6 +816,7 @@ __global__ void __launch_bounds__(kBlock, Real<R>::mixed ? kFillMinBlocks : 0) h
     // entries the count pass found, or the group's rows when they were sized
     // from the previous step
     const uint32_t room = G.act ? (a.nl_bound ? a.nl_len[gi] : a.nl_cnt[i]) : 0u;
+    const uint32_t rows = a.nl_len[gi];  // the group's rows (its longest list, or its bound)
     uint32_t k = 0;
     uint64_t tested = 0;  // staged candidates of the visits (census)
     R rho = 0;  // without neighbour counts the fill pass also forms the density
@@ -838,7 +843,7 @@ __global__ void __launch_bounds__(kBlock, Real<R>::mixed ? kFillMinBlocks : 0) h
         for (int ww = 0; ww < JMAX / 32; ++ww) pop += (uint32_t)__popc(mu[ww]);
         // room in the ring for the fastest lane: flush its oldest rows early
         const uint32_t need = __reduce_max_sync(0xffffffffu, k + pop);
-        if (need > ring.base + kRingRows) ring.flush(a, need - kRingRows, k < room ? k : room, lane);
+        if (need > ring.base + kRingRows) ring.flush(a, need - kRingRows, k < room ? k : room, rows, lane);
 #pragma unroll
         for (int ww = 0; ww < JMAX / 32; ++ww) {
             uint32_t bits = mu[ww];
@@ -864,9 +869,9 @@ __global__ void __launch_bounds__(kBlock, Real<R>::mixed ? kFillMinBlocks : 0) h
         }
         // rows every active lane has passed
         const uint32_t done = __reduce_min_sync(0xffffffffu, G.act ? k : 0xffffffffu);
-        if (done > ring.base) ring.flush(a, done, k < room ? k : room, lane);
+        if (done > ring.base) ring.flush(a, done, k < room ? k : room, rows, lane);
     }
-    ring.flush(a, __reduce_max_sync(0xffffffffu, k), k < room ? k : room, lane);
+    ring.flush(a, __reduce_max_sync(0xffffffffu, k), k < room ? k : room, rows, lane);
     if (COUNT && a.census) {
         const uint32_t kept = __reduce_add_sync(0xffffffffu, G.act ? (k < room ? k : room) : 0u);
         if (lane == 0) {
@@ -985,23 +990,45 @@ __device__ __forceinline__ float4 entry_frame(const float4 *frow, uint32_t e)
     return frow[(e >> kRowShift) & kMaxRowOffset];
 }
 
+// Asks the L2 cache to fetch rows [r0, r1) of a group's list block (row 0
+// at g0; rows of 32 entries, 128 bytes, contiguous): one bulk prefetch, no
+// completion to wait for.  The rows lie inside the rows the fill wrote.
+__device__ __forceinline__ void prefetch_rows(const uint32_t *g0, uint32_t r0, uint32_t r1)
+{
+    if (r1 <= r0) return;
+    const size_t ga = __cvta_generic_to_global(g0 + (size_t)r0 * 32u);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(ga), "r"((r1 - r0) * 128u) : "memory");
+}
+
+// Rows of list a consumer asks L2 for ahead of its walk, per prefetch.  The
+// lists are written long before they are read and far exceed L2, so every
+// row comes from DRAM; a row is fetched 32-64 rows before the walk needs it.
+constexpr uint32_t kPrefetchRows = 32;
+
 // Streams a lane's list entries for a consumer that works on entry k while
 // the records of entry k + 1 load: entry k + 1's neighbour index was looked
 // up one step earlier, entry k + 2's lookup and entry k + 3's load are in
-// flight, so that no load is used in the step that issues it.
+// flight, so that no load is used in the step that issues it.  With PF the
+// group's rows themselves are brought to L2 kPrefetchRows at a time, one
+// block ahead (density and moments gain; the hydro pass, whose neighbour
+// records come from L2, loses by it and does not prefetch).
+template <bool PF = true>
 struct ListPipe {
-    size_t e0;
-    uint32_t cnt;
+    size_t e0;           // the lane's entry 0 (row 0 of its group, column lane)
+    uint32_t cnt, rows;  // the lane's entries; the group's longest list
     uint32_t e1, j1;  // the next entry to take and its neighbour index
     uint32_t e2, j2;  // the one after, its index looked up
     uint32_t e3;      // the one after that, loaded
 
-    // on return (e1, j1) is entry 0
+    // on return (e1, j1) is entry 0; every lane of the warp constructs it
     __device__ __forceinline__ ListPipe(const PassArgs &a, uint32_t gi, uint32_t lane, uint32_t n,
                                         const uint32_t *srow)
     {
-        e0 = (size_t)a.nl_row[a.lmap ? a.lmap[gi] : gi] * 32u + lane;
+        const size_t row0 = (size_t)a.nl_row[a.lmap ? a.lmap[gi] : gi];
+        e0 = row0 * 32u + lane;
         cnt = n;
+        rows = PF ? __reduce_max_sync(0xffffffffu, n) : 0u;
+        if (PF && lane == 0) prefetch_rows(a.nl_j + row0 * 32u, 0u, min(rows, 2u * kPrefetchRows));
         e1 = cnt > 0u ? a.nl_j[e0] : 0u;
         e2 = cnt > 1u ? a.nl_j[e0 + 32u] : 0u;
         e3 = cnt > 2u ? a.nl_j[e0 + 64u] : 0u;
@@ -1013,6 +1040,12 @@ struct ListPipe {
     template <bool GATHER_ONLY = false>
     __device__ __forceinline__ void step(const PassArgs &a, const uint32_t *srow, uint32_t m)
     {
+        if (PF && (m % kPrefetchRows) == 0u && m + kPrefetchRows < rows) {
+            // the lowest lane still walking asks for the block after next
+            const uint32_t act = __activemask(), lane = threadIdx.x & 31u;
+            if (lane == (uint32_t)(__ffs(act) - 1))
+                prefetch_rows(a.nl_j + (e0 - lane), m + kPrefetchRows, min(rows, m + 2u * kPrefetchRows));
+        }
         e1 = e2;
         j1 = j2;
         e2 = e3;
@@ -1053,7 +1086,7 @@ __global__ void __launch_bounds__(kBlock) density_k(PassArgs a)
     const HTarget<R> ht = hydro_target<R>(a.s, i);
     const float4 *__restrict__ frow = a.hfr + a.hrow[I];
     const uint32_t *__restrict__ srow = a.hsj + a.hrow[I];
-    ListPipe pipe(a, gi, lane, G.act ? a.nl_cnt[i] : 0u, srow);
+    ListPipe<> pipe(a, gi, lane, G.act ? a.nl_cnt[i] : 0u, srow);
     R rho = 0;
     int nc = 0;
     uint64_t hs = 0;
@@ -1247,7 +1280,7 @@ __global__ void __launch_bounds__(kBlock, moments_min_blocks<R>()) moments_k(Pas
     const R cG = (R)kGn * invH2 * invH2 * invH;
     const float4 *__restrict__ frow = a.hfr + a.hrow[I];
     const uint32_t *__restrict__ srow = a.hsj + a.hrow[I];
-    ListPipe pipe(a, gi, lane, G.act ? a.nl_cnt[i] : 0u, srow);
+    ListPipe<> pipe(a, gi, lane, G.act ? a.nl_cnt[i] : 0u, srow);
     MomentAcc<R> acc;
     acc.zero();
     // the neighbour's record and frame one entry ahead (gather entries only:
@@ -1402,7 +1435,7 @@ __global__ void __launch_bounds__(kBlock, Real<R>::mixed ? kHydroMinBlocks : 0) 
     const R hi2e = eps2 * si.h * si.h;
     const float4 *__restrict__ frow = a.hfr + a.hrow[I];
     const uint32_t *__restrict__ srow = a.hsj + a.hrow[I];
-    ListPipe pipe(a, gi, lane, G.act ? a.nl_cnt[i] : 0u, srow);
+    ListPipe<false> pipe(a, gi, lane, G.act ? a.nl_cnt[i] : 0u, srow);
     R ax = 0, ay = 0, az = 0, du = 0;
     // the neighbour's records and frame one entry ahead
     R4 rn[7];
