@@ -42,7 +42,7 @@ constexpr int kWarps = 4;             // warps (target groups) per CTA
 // Resident CTAs per SM the mixed form's pass kernels are compiled for (a
 // register budget: 65,536 / (128 x blocks) per thread; 0 = no bound)
 constexpr int kMomentsMinBlocks = 5;
-constexpr int kHydroMinBlocks = 0;
+constexpr int kHydroMinBlocks = 4;
 constexpr int kFillMinBlocks = 0;
 constexpr int kBlock = 32 * kWarps;
 
@@ -1397,6 +1397,151 @@ __device__ __forceinline__ void corrected_grad(const HState<R> &s, const R x[3],
 //   m_i a_i = sum F_ij,  m_i du_i = -1/2 sum F_ij . v_ij
 // The pairs are the target's list entries; j's seven records are read
 // through L1/L2 (a group's neighbours are a few leaves).
+
+// Target side of the hydro pair: the target's state and record 0, and the
+// kernel constants of its H = 2h.
+template <typename R>
+struct HTgt {
+    HState<R> s;
+    Vec4<R> r0;
+    R invH, cW, cG, h2e;
+};
+
+template <typename R>
+__device__ __forceinline__ void hydro_tgt(HTgt<R> &t, const Vec4<R> r[7], R eps2)
+{
+    unpack_hstate(r, t.s);
+    t.r0 = r[0];
+    const R H = (R)2 * t.s.h;
+    t.invH = Real<R>::rcp(H);
+    t.cW = (R)kWn * t.invH * t.invH * t.invH;
+    t.cG = (R)kGn * t.invH * t.invH * t.invH * t.invH * t.invH;
+    t.h2e = eps2 * t.s.h * t.s.h;
+}
+
+// F_ij and F_ij . v_ij of one listed pair (rn: j's seven records, fr: the
+// leaf-pair frame).
+template <typename R>
+__device__ __forceinline__ void hydro_pair(const HTgt<R> &ti, const Vec4<R> rn[7], const float4 &fr, R L, R hL,
+                                           R alpha, R beta, R eps2, R &Fx, R &Fy, R &Fz, R &e)
+{
+    HState<R> sj;
+    unpack_hstate(rn, sj);
+    R dx, dy, dz;
+    const R r2 = list_sep2(rn[0], ti.r0, fr, L, hL, dx, dy, dz);
+    const R x[3] = {-dx, -dy, -dz};  // x_ij = x_i - x_j
+    const R xm[3] = {dx, dy, dz};    // x_ji
+    const R r = Real<R>::sqrt_(r2);
+    R Wi, gi_, Wj, gj;
+    kernel_wg(r, ti.invH, ti.cW, ti.cG, Wi, gi_);
+    const R invHj = Real<R>::rcp((R)2 * sj.h);
+    const R invHj2 = invHj * invHj;
+    kernel_wg(r, invHj, (R)kWn * invHj2 * invHj, (R)kGn * invHj2 * invHj2 * invHj, Wj, gj);
+    R dWi[3], dWj[3];
+    corrected_grad(ti.s, x, Wi, gi_, dWi);
+    corrected_grad(sj, xm, Wj, gj, dWj);
+    const R vxij = ti.s.vx - sj.vx, vyij = ti.s.vy - sj.vy, vzij = ti.s.vz - sj.vz;
+    const R vdx = vxij * x[0] + vyij * x[1] + vzij * x[2];
+    R Q = 0;
+    if (vdx < (R)0) {
+        const R mui = Real<R>::div(ti.s.h * vdx, r2 + ti.h2e);
+        const R muj = Real<R>::div(sj.h * vdx, r2 + eps2 * sj.h * sj.h);
+        Q = ti.s.rho * (-alpha * ti.s.c * mui + beta * mui * mui) +
+            sj.rho * (-alpha * sj.c * muj + beta * muj * muj);
+    }
+    const R pre = (R)(-0.5) * ti.s.V * sj.V * (ti.s.P + sj.P + Q);
+    Fx = pre * (dWi[0] - dWj[0]);
+    Fy = pre * (dWi[1] - dWj[1]);
+    Fz = pre * (dWi[2] - dWj[2]);
+    e = Fx * vxij + Fy * vyij + Fz * vzij;
+}
+
+// Walks n list entries of one column of a group's rows, the first at e0,
+// one every `stride` words, with the pipeline of ListPipe (entry k + 4's
+// word loading, entry k + 3's index being looked up and entry k + 1's
+// records loading while entry k is evaluated), and adds the pair sums of
+// target ti (sorted index i) to (ax, ay, az, du).
+template <typename R>
+__device__ __forceinline__ void hydro_walk(const PassArgs &a, const HTgt<R> &ti, uint32_t i, size_t e0,
+                                           uint32_t n, uint32_t stride, const float4 *__restrict__ frow,
+                                           const uint32_t *__restrict__ srow, R L, R hL, R alpha, R beta, R eps2,
+                                           R &ax, R &ay, R &az, R &du)
+{
+    using R4 = Vec4<R>;
+    uint32_t e1 = n > 0u ? a.nl_j[e0] : 0u;
+    uint32_t e2 = n > 1u ? a.nl_j[e0 + stride] : 0u;
+    uint32_t e3 = n > 2u ? a.nl_j[e0 + 2u * (size_t)stride] : 0u;
+    uint32_t j1 = n > 0u ? entry_index(srow, e1) : 0u;
+    uint32_t j2 = n > 1u ? entry_index(srow, e2) : 0u;
+    // entry m, (e1, j1), was taken: (e1, j1) becomes entry m + 1
+    auto step = [&](uint32_t m) {
+        e1 = e2;
+        j1 = j2;
+        e2 = e3;
+        j2 = m + 2u < n ? entry_index(srow, e3) : 0u;
+        e3 = m + 3u < n ? a.nl_j[e0 + (size_t)(m + 3u) * stride] : 0u;
+    };
+    // the neighbour's records and frame one entry ahead
+    R4 rn[7];
+    float4 fn;
+    uint32_t jn = 0;
+    if (n > 0u) {
+        jn = j1;
+        fn = entry_frame(frow, e1);
+#pragma unroll
+        for (int q = 0; q < 7; ++q) rn[q] = reinterpret_cast<const R4 *>(a.hrec[q])[jn];
+        step(0u);
+    }
+    for (uint32_t k = 0; k < n; ++k) {
+        const uint32_t j = jn;
+        const float4 fr = fn;
+        R4 rj[7];
+#pragma unroll
+        for (int q = 0; q < 7; ++q) rj[q] = rn[q];
+        if (k + 1u < n) {
+            jn = j1;
+            fn = entry_frame(frow, e1);
+#pragma unroll
+            for (int q = 0; q < 7; ++q) rn[q] = reinterpret_cast<const R4 *>(a.hrec[q])[jn];
+            step(k + 1u);
+        }
+        if (j == i) continue;
+        R Fx, Fy, Fz, e;
+        hydro_pair(ti, rj, fr, L, hL, alpha, beta, eps2, Fx, Fy, Fz, e);
+        ax += Fx;
+        ay += Fy;
+        az += Fz;
+        du += e;
+    }
+}
+
+// Walk steps a run of the hydro pass's second phase costs beyond its rows
+// (the pipeline's restart, the target's records, the tree of shuffles).
+constexpr uint32_t kRunSteps = 10;
+
+// Shared memory of a warp of the gather hydro pass: the lanes in order of
+// decreasing list length with their lengths, the second phase's sums per
+// rank and the first phase's sums per lane (small, so that the carve-out
+// leaves L1 to the neighbour records).
+template <typename R>
+constexpr size_t hydro_warp_bytes()
+{
+    return 2 * 32 * sizeof(uint32_t) + 2 * 32 * 4 * sizeof(R);
+}
+
+// Gather form (each target sums its own pairs, in a fixed order; results do
+// not depend on what else runs).  A group's lists differ in length (a
+// leaf's last group is often short of targets, and the union sets vary), and
+// a warp walking them one lane per target runs as long as its longest list.
+// So the walk has two phases: first every lane walks its own list up to
+// the length c16 of the 17th longest; then the rows beyond c16 of the 16
+// longest lists are spread over the whole warp: while a lists are left (rows
+// [c_a, c_{a-1}), c_r the length of the r-th longest), the warp takes q =
+// 32 / a rows of them at a time, lane l walking row (l / a) of each q for
+// the list of rank l % a, and the q partial sums of a list are added by a
+// tree of shuffles.  Each target's sum: its own phase, then the runs in
+// order.  A group whose lists are near one length (a uniform box) walks in
+// one phase: the two phases are taken only where they save walk steps.
 // ONCE (mixed form): each union pair is evaluated by its lower-indexed
 // particle only (the union predicate is symmetric, so the pair is in both
 // lists): entries with j < i are skipped without loading j's records, the
@@ -1410,7 +1555,8 @@ template <typename R, int JMAX, bool ONCE = false>
 __global__ void __launch_bounds__(kBlock, Real<R>::mixed ? kHydroMinBlocks : 0) hydro_k(PassArgs a)
 {
     using R4 = Vec4<R>;
-    const uint32_t lane = threadIdx.x & 31u;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const uint32_t w = threadIdx.x >> 5, lane = threadIdx.x & 31u;
     for_each_item(a.n_ggas, a.ggas_dev, a.queue, Q_HYDRO, [&](const uint32_t gi) {
     const Group G = load_group(a.lv, a.ggas, gi, lane);
     const int I = G.I;
@@ -1419,87 +1565,150 @@ __global__ void __launch_bounds__(kBlock, Real<R>::mixed ? kHydroMinBlocks : 0) 
     const double Ld = bx.L;
     const R L = (R)Ld, hL = (R)(0.5 * Ld);
     const R alpha = (R)bx.av_alpha, beta = (R)bx.av_beta, eps2 = (R)bx.av_eps2;
-    HState<R> si;
-    R4 ri0;
-    {
-        R4 r[7];
-#pragma unroll
-        for (int k = 0; k < 7; ++k) r[k] = reinterpret_cast<const R4 *>(a.hrec[k])[i];
-        unpack_hstate(r, si);
-        ri0 = r[0];
-    }
-    const R Hi = (R)2 * si.h;
-    const R invHi = Real<R>::rcp(Hi);
-    const R cWi = (R)kWn * invHi * invHi * invHi;
-    const R cGi = (R)kGn * invHi * invHi * invHi * invHi * invHi;
-    const R hi2e = eps2 * si.h * si.h;
     const float4 *__restrict__ frow = a.hfr + a.hrow[I];
     const uint32_t *__restrict__ srow = a.hsj + a.hrow[I];
-    ListPipe<false> pipe(a, gi, lane, G.act ? a.nl_cnt[i] : 0u, srow);
-    R ax = 0, ay = 0, az = 0, du = 0;
-    // the neighbour's records and frame one entry ahead
-    R4 rn[7];
-    float4 fn;
-    uint32_t jn = 0;
-    if (pipe.cnt > 0u) {
-        jn = pipe.j1;
-        fn = entry_frame(frow, pipe.e1);
-        if (!ONCE || jn > i) {
+    R4 r[7];
 #pragma unroll
-            for (int q = 0; q < 7; ++q) rn[q] = reinterpret_cast<const R4 *>(a.hrec[q])[jn];
+    for (int k = 0; k < 7; ++k) r[k] = reinterpret_cast<const R4 *>(a.hrec[k])[i];
+    const uint32_t cnt = G.act ? a.nl_cnt[i] : 0u;
+    R ax = 0, ay = 0, az = 0, du = 0;
+    if constexpr (!ONCE) {
+        unsigned char *base = smem + (size_t)w * hydro_warp_bytes<R>();
+        uint32_t *sl = reinterpret_cast<uint32_t *>(base);                // lane of rank r
+        uint32_t *sc = sl + 32;                                           // length of rank r
+        R *acc2 = reinterpret_cast<R *>(sc + 32);                         // [rank][4]
+        // rank of the lane's list: longer first, ties by lane
+        uint32_t rank = 0;
+        for (uint32_t l2 = 0; l2 < 32u; ++l2) {
+            const uint32_t c2 = __shfl_sync(0xffffffffu, cnt, (int)l2);
+            rank += (c2 > cnt || (c2 == cnt && l2 < lane)) ? 1u : 0u;
         }
-        pipe.step(a, srow, 0u);
-    }
-    for (uint32_t k = 0; k < pipe.cnt; ++k) {
-        const uint32_t j = jn;
-        const float4 fr = fn;
-        HState<R> sj;
-        unpack_hstate(rn, sj);
-        const R4 rj0 = rn[0];
-        const R imj = rn[6].w;
-        if (k + 1u < pipe.cnt) {
+        sl[rank] = lane;
+        sc[rank] = cnt;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc2[lane * 4 + c] = (R)0;
+        __syncwarp();
+        // the two phases only where they save steps: the plain walk takes c_0
+        // steps, the two phases c16 plus each run's rows / q and a restart
+        // of the pipeline (kRunSteps)
+        uint32_t c16 = sc[16];
+        {
+            uint32_t two = c16;
+            for (uint32_t na = 16u; na >= 1u; --na) {
+                const uint32_t lo = sc[na], hi = sc[na - 1u], q = 32u / na;
+                if (hi > lo) two += (hi - lo + q - 1u) / q + kRunSteps;
+            }
+            if (two >= sc[0]) c16 = sc[0];  // one phase: every lane walks its whole list
+        }
+        const size_t row0 = (size_t)a.nl_row[a.lmap ? a.lmap[gi] : gi];
+        R *own = acc2 + 32 * 4 + lane * 4;  // phase 1's sums of the lane's target
+        // segment 0: phase 1, every lane its own list up to c16; segment s > 0:
+        // the run of na = 17 - s lists left (rows [c_na, c_{na-1})), the warp
+        // on q = 32 / na rows of them at a time
+        for (uint32_t seg = 0; seg <= 16u; ++seg) {
+            const uint32_t na = 17u - seg;
+            const uint32_t lo = seg == 0u ? 0u : (c16 > sc[na] ? c16 : sc[na]), hi = seg == 0u ? c16 : sc[na - 1u];
+            if (seg > 0u && hi <= lo) continue;
+            const uint32_t q = seg == 0u ? 1u : 32u / na;
+            const uint32_t ro = seg == 0u ? 0u : lane / na;
+            const bool on = seg == 0u || lane < q * na;
+            const uint32_t col = seg == 0u ? lane : sl[on ? lane - ro * na : 0u];
+            const uint32_t first = lo + ro;
+            uint32_t n = (on && first < hi) ? (hi - first + q - 1u) / q : 0u;
+            if (seg == 0u) n = cnt < c16 ? cnt : c16;
+            R px = 0, py = 0, pz = 0, pd = 0;
+            {
+                // the target's records (the lane's own in phase 1, the run's
+                // list owner's after it), reread through L1
+                const uint32_t it = seg == 0u ? i : G.s0 + col;
+                HTgt<R> tj;
+                R4 rt[7];
+#pragma unroll
+                for (int k = 0; k < 7; ++k) rt[k] = reinterpret_cast<const R4 *>(a.hrec[k])[it];
+                hydro_tgt(tj, rt, eps2);
+                hydro_walk(a, tj, it, (row0 + first) * 32u + col, n, 32u * q, frow, srow, L, hL, alpha, beta, eps2,
+                           px, py, pz, pd);
+            }
+            if (seg == 0u) {
+                own[0] = px;
+                own[1] = py;
+                own[2] = pz;
+                own[3] = pd;
+                continue;
+            }
+            // the q partial sums of each list, by a tree over the row slots
+            for (uint32_t d = 1u; d < q; d <<= 1) {
+                const R vx = __shfl_down_sync(0xffffffffu, px, (int)(d * na));
+                const R vy = __shfl_down_sync(0xffffffffu, py, (int)(d * na));
+                const R vz = __shfl_down_sync(0xffffffffu, pz, (int)(d * na));
+                const R vd = __shfl_down_sync(0xffffffffu, pd, (int)(d * na));
+                if (on && (ro & (2u * d - 1u)) == 0u && ro + d < q) {
+                    px += vx;
+                    py += vy;
+                    pz += vz;
+                    pd += vd;
+                }
+            }
+            if (lane < na) {
+                acc2[lane * 4 + 0] += px;
+                acc2[lane * 4 + 1] += py;
+                acc2[lane * 4 + 2] += pz;
+                acc2[lane * 4 + 3] += pd;
+            }
+        }
+        __syncwarp();
+        ax = own[0];
+        ay = own[1];
+        az = own[2];
+        du = own[3];
+        if (rank < 16u) {
+            ax += acc2[rank * 4 + 0];
+            ay += acc2[rank * 4 + 1];
+            az += acc2[rank * 4 + 2];
+            du += acc2[rank * 4 + 3];
+        }
+        __syncwarp();
+    } else {
+        HTgt<R> ti;
+        hydro_tgt(ti, r, eps2);
+        ListPipe<false> pipe(a, gi, lane, cnt, srow);
+        // the neighbour's records and frame one entry ahead
+        R4 rn[7];
+        float4 fn;
+        uint32_t jn = 0;
+        if (pipe.cnt > 0u) {
             jn = pipe.j1;
             fn = entry_frame(frow, pipe.e1);
-            if (!ONCE || jn > i) {
+            if (jn > i) {
 #pragma unroll
                 for (int q = 0; q < 7; ++q) rn[q] = reinterpret_cast<const R4 *>(a.hrec[q])[jn];
             }
-            pipe.step(a, srow, k + 1u);
+            pipe.step(a, srow, 0u);
         }
-        if (ONCE ? j <= i : j == i) continue;
-        R dx, dy, dz;
-        const R r2 = list_sep2(rj0, ri0, fr, L, hL, dx, dy, dz);
-        const R x[3] = {-dx, -dy, -dz};  // x_ij = x_i - x_j
-        const R xm[3] = {dx, dy, dz};    // x_ji
-        const R r = Real<R>::sqrt_(r2);
-        R Wi, gi_, Wj, gj;
-        kernel_wg(r, invHi, cWi, cGi, Wi, gi_);
-        const R invHj = Real<R>::rcp((R)2 * sj.h);
-        const R invHj2 = invHj * invHj;
-        kernel_wg(r, invHj, (R)kWn * invHj2 * invHj, (R)kGn * invHj2 * invHj2 * invHj, Wj, gj);
-        R dWi[3], dWj[3];
-        corrected_grad(si, x, Wi, gi_, dWi);
-        corrected_grad(sj, xm, Wj, gj, dWj);
-        const R vxij = si.vx - sj.vx, vyij = si.vy - sj.vy, vzij = si.vz - sj.vz;
-        const R vdx = vxij * x[0] + vyij * x[1] + vzij * x[2];
-        R Q = 0;
-        if (vdx < (R)0) {
-            const R mui = Real<R>::div(si.h * vdx, r2 + hi2e);
-            const R muj = Real<R>::div(sj.h * vdx, r2 + eps2 * sj.h * sj.h);
-            Q = si.rho * (-alpha * si.c * mui + beta * mui * mui) +
-                sj.rho * (-alpha * sj.c * muj + beta * muj * muj);
-        }
-        const R pre = (R)(-0.5) * si.V * sj.V * (si.P + sj.P + Q);
-        const R Fx = pre * (dWi[0] - dWj[0]);
-        const R Fy = pre * (dWi[1] - dWj[1]);
-        const R Fz = pre * (dWi[2] - dWj[2]);
-        ax += Fx;
-        ay += Fy;
-        az += Fz;
-        const R e = Fx * vxij + Fy * vyij + Fz * vzij;
-        du += e;
-        if (ONCE) {
+        for (uint32_t k = 0; k < pipe.cnt; ++k) {
+            const uint32_t j = jn;
+            const float4 fr = fn;
+            R4 rj[7];
+#pragma unroll
+            for (int q = 0; q < 7; ++q) rj[q] = rn[q];
+            if (k + 1u < pipe.cnt) {
+                jn = pipe.j1;
+                fn = entry_frame(frow, pipe.e1);
+                if (jn > i) {
+#pragma unroll
+                    for (int q = 0; q < 7; ++q) rn[q] = reinterpret_cast<const R4 *>(a.hrec[q])[jn];
+                }
+                pipe.step(a, srow, k + 1u);
+            }
+            if (j <= i) continue;
+            R Fx, Fy, Fz, e;
+            hydro_pair(ti, rj, fr, L, hL, alpha, beta, eps2, Fx, Fy, Fz, e);
+            ax += Fx;
+            ay += Fy;
+            az += Fz;
+            du += e;
             // the partner's side: m_j a_j -= F_ij; m_j du_j gets the same -1/2 F_ij . v_ij
+            const R imj = rj[6].w;
             atomicAdd(reinterpret_cast<float4 *>(a.acc_h) + j,
                       make_float4((float)(-Fx * imj), (float)(-Fy * imj), (float)(-Fz * imj),
                                   (float)((R)(-0.5) * e * imj)));
@@ -2203,7 +2412,7 @@ void hydro_dispatch(const PassArgs &a, cudaStream_t st)
         cudaMemsetAsync(a.acc_h, 0, (size_t)a.n * sizeof(Vec4<R>), st);
         launch_warp_kernel(hydro_k<R, JMAX, true>, a.n_ggas, 0, a, st);
     } else {
-        launch_warp_kernel(hydro_k<R, JMAX, false>, a.n_ggas, 0, a, st);
+        launch_warp_kernel(hydro_k<R, JMAX, false>, a.n_ggas, (size_t)kWarps * hydro_warp_bytes<R>(), a, st);
     }
 }
 
