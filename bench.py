@@ -52,8 +52,8 @@ FLOP_PER_PAIR = {"density": 22, "moments": 125, "hydro": 183, "gravity": 41}
 # leaf capacity 128, scaled to the launch by the particles it processes.  They
 # describe the kernels of the csrc/passes.cu with this SHA-256 only; for any
 # other source the bench reports no traffic.
-TRAFFIC_SOURCE_SHA256 = "8d9a4f37bb7458543ab0255a32c48500d96a20eaf968ae61ceb478b9581bf620"
-TRAFFIC_BYTES_PER_PARTICLE = {"gravity_pairs_once": 79.5}
+TRAFFIC_SOURCE_SHA256 = "33fb3598363ca272e92f6cca363c41703564eb8ef8ff1fe9763c9c4ccce7df80"
+TRAFFIC_BYTES_PER_PARTICLE = {"gravity_pairs_once": 79.7}
 
 
 # the crk_create flag that switches each pass to its pairs-once form (0: none)
