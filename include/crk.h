@@ -176,7 +176,9 @@ typedef struct {
     int64_t list_entries;       /* hydro list entries written (union set, self included) */
     int64_t tests_grav;         /* gravity candidate tests (every pair force is formed) */
     int64_t tests_grav_target;  /* of those, the slots of lanes that have a target */
-    int64_t list_slots;         /* lane slots of the list rows the moments and hydro passes walk */
+    int64_t list_slots;         /* lane slots of the list rows (32 per row): the moments pass walks
+                                   all of them, the hydro pass fewer where its second phase spreads
+                                   a group's long lists over the whole warp */
     /* Step counters since the last crk_set_timing (whether timing is on or
      * not): KDK steps run, of those the steps replayed from a CUDA graph,
      * host synchronisations inside host-sized steps and force evaluations
